@@ -1,0 +1,475 @@
+/*
+ * moq_oracle.c -- the CPU oracle for multi-objective MaxCut sampling by noise-injected
+ * simulated bifurcation (NI-SB), "Multi-Objective Optimization by Quantum-Annealing-
+ * Inspired Algorithms" (arXiv 2604.26477).
+ *
+ * TEST INFRASTRUCTURE ONLY. Plain, slow, obviously-correct code: double precision for
+ * the dynamics, int64 for cut values, __int128 for hypervolumes. It shares no code,
+ * header or table with the CUDA library and is called only by the tests, the smoke
+ * check and the CPU-baseline leg of the benchmark. Each function names the passage of
+ * the paper it restates. Where the paper is silent or ambiguous the reading taken is
+ * stated beside the code (the list of readings is kept with the design notes).
+ *
+ * Parity status of each function (what pins it, all in tests/):
+ *   or_philox4x32_10  pinned: published known-answer vectors of Philox4x32-10.
+ *   or_cuts           pinned: brute-force identities, hand-computed golden cuts.
+ *   or_brute_force    pinned: enumeration identities (sum over all s, symmetry).
+ *   or_pareto_filter  pinned: definition-based all-pairs check, hand golden fronts.
+ *   or_hypervolume    pinned: the Appendix A worked example, inclusion-exclusion.
+ *   or_das_dennis     pinned: lattice counts 190 (K=3) and 220 (K=4), binomial counts.
+ *   or_sb             pinned: hand-computed steps, J=0 closed form, symmetry, max-cut
+ *                     on bipartite graphs; trajectories are chaotic, so beyond a few
+ *                     steps parity is statistical only.
+ *   or_normal         pinned: moments and a KS test (the Gaussian is not pinned bitwise:
+ *                     it goes through libm log/cos/sin).
+ *   or_dirichlet      pinned: simplex sums, moments of Dirichlet(1,..,1).
+ *   or_mlp_*          pinned: central finite differences of the loss.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef __int128 i128;
+
+/* ------------------------------------------------------------------------------------
+ * Counter-based RNG: Philox4x32 with 10 rounds, from Salmon, Moraes, Dror and Shaw,
+ * "Parallel random numbers: as easy as 1, 2, 3" (SC'11), Sec. 3.3 / Table 2: each
+ * round multiplies counter words 0 and 2 by two fixed odd constants, XORs the high
+ * halves of the products with the other counter words and the key, and swaps; the
+ * key is advanced by the two Weyl constants between rounds.
+ * ---------------------------------------------------------------------------------- */
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += PHILOX_W0;
+            k1 += PHILOX_W1;
+        }
+        uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Counter layout shared (by definition, not by code) with the CUDA sampler:
+ *   noise of spin i, replica r, step m:  ctr = (m >> 2, i, r, round), key = seed
+ *   initial state of spin i, replica r:  ctr = (0xFFFFFFFF, i, r, round), key = seed
+ * Words (o0,o1) and (o2,o3) each give two normals by Box-Muller; step m uses normal
+ * number (m & 3) of its block: (o0,o1) -> cos, sin; (o2,o3) -> cos, sin. */
+static void philox_at(uint64_t seed, uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3, uint32_t out[4])
+{
+    uint32_t ctr[4] = {w0, w1, w2, w3};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    or_philox4x32_10(ctr, key, out);
+}
+
+/* Gaussian eta_{i,m} of Eq. (NI-SB): Box-Muller on two 24-bit uniforms,
+ * u1 in (0, 1], u2 in [0, 1): rho = sqrt(-2 ln u1), theta = 2 pi u2. */
+double or_normal(uint64_t seed, uint64_t round, uint32_t r, uint32_t i, uint64_t m)
+{
+    uint32_t o[4];
+    philox_at(seed, (uint32_t)(m >> 2), i, r, (uint32_t)round, o);
+    int pair = (int)((m & 3) >> 1);
+    double u1 = ((double)(o[2 * pair] >> 8) + 1.0) * 0x1p-24;
+    double u2 = (double)(o[2 * pair + 1] >> 8) * 0x1p-24;
+    double rho = sqrt(-2.0 * log(u1));
+    double theta = 2.0 * M_PI * u2;
+    return (m & 1) ? rho * sin(theta) : rho * cos(theta);
+}
+
+/* Uniform initial value in [-amp, amp): v = (w >> 8 - 2^23) * 2^-23 is exact in
+ * float; amp * v is one IEEE single-precision product, so the CUDA sampler (which
+ * forms the same product in float) starts from bitwise the same state. */
+static double init_value(uint32_t word, float amp)
+{
+    float v = (float)((int32_t)(word >> 8) - 8388608) * 0x1p-23f;
+    volatile float x = amp * v;
+    return (double)x;
+}
+
+void or_initial_state(uint64_t seed, uint64_t round, uint32_t r, uint32_t i, float amp, double* x0, double* y0)
+{
+    uint32_t o[4];
+    philox_at(seed, 0xFFFFFFFFu, i, r, (uint32_t)round, o);
+    *x0 = init_value(o[0], amp);
+    *y0 = init_value(o[1], amp);
+}
+
+/* ------------------------------------------------------------------------------------
+ * Cut values, Eq. (single_obj): C_k(s) = 1/2 sum_{(i,j) in E} J^(k)_ij (1 - s_i s_j).
+ * Spins are read from packed words: bit (i mod 64) of word i/64 is 1 when s_i = -1.
+ * ---------------------------------------------------------------------------------- */
+static int spin_of(const uint64_t* bits, int i)
+{
+    return ((bits[i >> 6] >> (i & 63)) & 1u) ? -1 : +1;
+}
+
+void or_cuts(int n, int K, int64_t E, const int32_t* ei, const int32_t* ej, const int32_t* w,
+             int64_t M, const uint64_t* bits, int64_t* cuts /* M x K */)
+{
+    int W = (n + 63) / 64;
+    for (int64_t s = 0; s < M; ++s) {
+        const uint64_t* b = bits + s * W;
+        for (int k = 0; k < K; ++k) {
+            int64_t twice = 0;
+            for (int64_t e = 0; e < E; ++e) {
+                int si = spin_of(b, ei[e]), sj = spin_of(b, ej[e]);
+                twice += (int64_t)w[(int64_t)k * E + e] * (int64_t)(1 - si * sj);
+            }
+            cuts[s * K + k] = twice / 2; /* (1 - s_i s_j) is 0 or 2: the sum is even */
+        }
+    }
+}
+
+/* Ising energies H_k(s) = sum_E J^(k)_ij s_i s_j ("Hamiltonian formulation"). */
+void or_energies(int n, int K, int64_t E, const int32_t* ei, const int32_t* ej, const int32_t* w,
+                 int64_t M, const uint64_t* bits, int64_t* H /* M x K */)
+{
+    int W = (n + 63) / 64;
+    for (int64_t s = 0; s < M; ++s)
+        for (int k = 0; k < K; ++k) {
+            int64_t acc = 0;
+            for (int64_t e = 0; e < E; ++e)
+                acc += (int64_t)w[(int64_t)k * E + e] * spin_of(bits + s * W, ei[e]) * spin_of(bits + s * W, ej[e]);
+            H[s * K + k] = acc;
+        }
+}
+
+/* Brute force over the configuration space S = {-1,1}^n ("Hamiltonian formulation",
+ * definition of P*): enumerate the 2^(n-1) configurations with s_0 = +1 (C(s) = C(-s),
+ * so the other half repeats them). Configuration number c sets s_i = -1 for i >= 1
+ * exactly when bit (i-1) of c is 1. Writes packed bits and cut vectors. */
+void or_brute_force(int n, int K, int64_t E, const int32_t* ei, const int32_t* ej, const int32_t* w,
+                    uint64_t* bits /* 2^(n-1) x W */, int64_t* cuts /* 2^(n-1) x K */)
+{
+    int W = (n + 63) / 64;
+    int64_t count = (int64_t)1 << (n - 1);
+    for (int64_t c = 0; c < count; ++c) {
+        uint64_t* b = bits + c * W;
+        memset(b, 0, sizeof(uint64_t) * W);
+        for (int i = 1; i < n; ++i)
+            if ((c >> (i - 1)) & 1)
+                b[i >> 6] |= (uint64_t)1 << (i & 63);
+        or_cuts(n, K, E, ei, ej, w, 1, b, cuts + c * K);
+    }
+}
+
+/* ------------------------------------------------------------------------------------
+ * Pareto dominance in cut-maximisation space ("Pareto filtering" section; the order of
+ * the "Hamiltonian formulation" section written for C = maximised cuts instead of H):
+ * u dominates v iff u_k >= v_k for every k and u_j > v_j for some j.
+ * ---------------------------------------------------------------------------------- */
+int or_dominates(int K, const int64_t* u, const int64_t* v)
+{
+    int strictly = 0;
+    for (int k = 0; k < K; ++k) {
+        if (u[k] < v[k]) return 0;
+        if (u[k] > v[k]) strictly = 1;
+    }
+    return strictly;
+}
+
+static int weakly_dominates(int K, const int64_t* u, const int64_t* v)
+{
+    for (int k = 0; k < K; ++k)
+        if (u[k] < v[k]) return 0;
+    return 1;
+}
+
+/* Pareto filter with deduplication of objective vectors ("Pareto filtering"): keep the
+ * distinct cut vectors of the pool that no pool member dominates; each kept vector is
+ * represented by its lowest pool index. Plain insertion into an archive, in pool order:
+ * a candidate equal to or dominated by a member is dropped; otherwise the members it
+ * dominates leave and it enters. Returns the archive size; keep[] holds pool indices in
+ * ascending order. */
+int64_t or_pareto_filter(int K, int64_t M, const int64_t* cuts, int64_t* keep)
+{
+    int64_t F = 0;
+    for (int64_t c = 0; c < M; ++c) {
+        const int64_t* u = cuts + c * K;
+        int covered = 0;
+        for (int64_t a = 0; a < F && !covered; ++a)
+            covered = weakly_dominates(K, cuts + keep[a] * K, u);
+        if (covered) continue;
+        int64_t out = 0;
+        for (int64_t a = 0; a < F; ++a)
+            if (!or_dominates(K, u, cuts + keep[a] * K))
+                keep[out++] = keep[a];
+        keep[out++] = c;
+        F = out;
+    }
+    return F;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Hypervolume ("Hamiltonian formulation" Eq. HV and Appendix A): the Lebesgue measure
+ * of the union of boxes prod_k [r_k, y_k] over the front. Computed exactly in integers
+ * by slicing the last objective (While, Hingston, Barone, Huband, "A faster algorithm
+ * for calculating hypervolume", IEEE TEVC 2006): sort by y_K descending; the slab
+ * between consecutive y_K values is covered in the first K-1 objectives by exactly the
+ * points above it, so HV_K = sum_t (y_K[t] - y_K[t+1]) * HV_{K-1}(first t+1 points),
+ * with y_K[F] = r_K. In two objectives the slices are the staircase of Appendix A.
+ * A point with some y_k < r_k spans an empty box and is left out.
+ * ---------------------------------------------------------------------------------- */
+static int g_sort_dim;
+static const int64_t* g_sort_pts;
+static int g_sort_stride;
+static int cmp_desc(const void* a, const void* b)
+{
+    int64_t ia = *(const int64_t*)a, ib = *(const int64_t*)b;
+    int64_t va = g_sort_pts[ia * g_sort_stride + g_sort_dim], vb = g_sort_pts[ib * g_sort_stride + g_sort_dim];
+    if (va > vb) return -1;
+    if (va < vb) return 1;
+    return (ia > ib) - (ia < ib);
+}
+
+static void sort_desc(int64_t* idx, int64_t F, const int64_t* pts, int stride, int dim)
+{
+    g_sort_dim = dim;
+    g_sort_pts = pts;
+    g_sort_stride = stride;
+    qsort(idx, (size_t)F, sizeof(int64_t), cmp_desc);
+}
+
+/* HV of points idx[0..F) in objectives 0..D-1 */
+static i128 hv_slice(int D, int64_t F, const int64_t* idx, const int64_t* pts, int stride, const int64_t* ref)
+{
+    if (F == 0) return 0;
+    int64_t* s = (int64_t*)malloc(sizeof(int64_t) * F);
+    memcpy(s, idx, sizeof(int64_t) * F);
+    sort_desc(s, F, pts, stride, D - 1);
+    i128 vol = 0;
+    if (D == 1) {
+        vol = (i128)(pts[s[0] * stride] - ref[0]);
+    } else if (D == 2) {
+        /* staircase: widest first; each point adds the strip above the best y_2 so far */
+        /* (sorted here by y_2 descending, so it is the mirror image: strips in y_1) */
+        int64_t best1 = ref[0];
+        for (int64_t t = 0; t < F; ++t) {
+            const int64_t* p = pts + s[t] * stride;
+            if (p[0] > best1) {
+                vol += (i128)(p[0] - best1) * (i128)(p[1] - ref[1]);
+                best1 = p[0];
+            }
+        }
+    } else {
+        for (int64_t t = 0; t < F; ++t) {
+            int64_t top = pts[s[t] * stride + D - 1];
+            int64_t below = (t + 1 < F) ? pts[s[t + 1] * stride + D - 1] : ref[D - 1];
+            if (top > below)
+                vol += (i128)(top - below) * hv_slice(D - 1, t + 1, s, pts, stride, ref);
+        }
+    }
+    free(s);
+    return vol;
+}
+
+/* out[0] = low 64 bits, out[1] = high 64 bits (two's complement of the __int128) */
+void or_hypervolume(int K, int64_t F, const int64_t* pts /* F x K */, const int64_t* ref, int64_t out[2])
+{
+    int64_t* idx = (int64_t*)malloc(sizeof(int64_t) * (F > 0 ? F : 1));
+    int64_t m = 0;
+    for (int64_t p = 0; p < F; ++p) {
+        int inside = 1;
+        for (int k = 0; k < K; ++k)
+            if (pts[p * K + k] < ref[k]) inside = 0;
+        if (inside) idx[m++] = p;
+    }
+    i128 v = hv_slice(K, m, idx, pts, K, ref);
+    free(idx);
+    out[0] = (int64_t)(uint64_t)v;
+    out[1] = (int64_t)(v >> 64);
+}
+
+/* ------------------------------------------------------------------------------------
+ * Weight vectors ("Scalarization via the weighted sum method", Appendix B): the
+ * Das-Dennis simplex lattice of resolution H, all c in {0, 1/H, ..., 1}^K with
+ * sum c = 1; with interior != 0 only points with every c_k > 0 (the paper removes the
+ * vertices and edges of the simplex). Order: lexicographically ascending (m_1..m_K).
+ * Returns the count; writes c when out != NULL.
+ * ---------------------------------------------------------------------------------- */
+static int64_t dd_rec(int K, int H, int lo, int k, int left, int* m, double* out, int64_t cnt)
+{
+    if (k == K - 1) {
+        if (left < lo) return cnt;
+        m[k] = left;
+        if (out)
+            for (int q = 0; q < K; ++q) out[cnt * K + q] = (double)m[q] / (double)H;
+        return cnt + 1;
+    }
+    for (int v = lo; v <= left; ++v) {
+        m[k] = v;
+        cnt = dd_rec(K, H, lo, k + 1, left - v, m, out, cnt);
+    }
+    return cnt;
+}
+
+int64_t or_das_dennis(int K, int H, int interior, double* out)
+{
+    int m[64];
+    if (K < 1 || K > 64 || H < 1) return 0;
+    return dd_rec(K, H, interior ? 1 : 0, 0, H, m, out, 0);
+}
+
+/* Uniform weight vectors on the simplex (Dirichlet(1,..,1), the alternative to the
+ * lattice shown in Appendix B): c_k = e_k / sum_q e_q with e_k = -ln u_k, u_k uniform
+ * in (0, 1] from Philox ctr = (r, k >> 2, 0x4C414D42, round), word k & 3. */
+void or_dirichlet(int R, int K, uint64_t seed, uint64_t round, double* out /* R x K */)
+{
+    for (int r = 0; r < R; ++r) {
+        double e[64], sum = 0.0;
+        for (int k = 0; k < K; ++k) {
+            uint32_t o[4];
+            philox_at(seed, (uint32_t)r, (uint32_t)(k >> 2), 0x4C414D42u, (uint32_t)round, o);
+            double u = ((double)(o[k & 3] >> 8) + 1.0) * 0x1p-24;
+            e[k] = -log(u);
+            sum += e[k];
+        }
+        for (int k = 0; k < K; ++k) out[(int64_t)r * K + k] = e[k] / sum;
+    }
+}
+
+/* ------------------------------------------------------------------------------------
+ * Noise-injected simulated bifurcation ("Simulated Bifurcation with Gaussian noise",
+ * the SB equations and Eq. NI-SB), one replica per weight vector lambda_r:
+ *
+ *   J(c)_ij = sum_k c_k J^(k)_ij                     (Eq. H_total)
+ *   c0      = 1 / max_i |sum_j J(c)_ij|
+ *   dx_i/dt = a0 y_i
+ *   dy_i/dt = -(a0 - a(t)) x_i + c0 sum_j Jt_ij phi(x_j) + alpha eta_i
+ *   phi(x)  = x (bSB) or sgn(x) (dSB);  s_i = sgn(x_i) at the end
+ *
+ * Readings where the paper is silent or ambiguous:
+ *  - Jt = -J(c): SB as printed climbs sum J phi phi, while H_total is minimised, so the
+ *    dynamics run on the negated coupling (then maximal cuts are the attractors).
+ *  - Integration: Euler with step dt in the symplectic order: y from the current x
+ *    and phi(x), then x from the new y, then the inelastic wall (|x_i| > 1 ->
+ *    x_i = sgn(x_i), y_i = 0).
+ *  - Noise enters as y += dt * alpha * eta (noise_sqrt_dt = 0), the Euler step of the
+ *    printed equation; noise_sqrt_dt = 1 gives the Euler-Maruyama alpha sqrt(dt) eta.
+ *  - a(t): a_m = a0 m / (T - 1) for m = 0..T-1 (a_0 = 0 when T = 1), or a given array.
+ *  - c0: if every row sum of J(c) vanishes, 1 / max_i sum_j |J(c)_ij|; if J(c) = 0, 1.
+ *  - sgn(0) = +1, so spins are exactly +-1; the wall test is strict.
+ *  - Initial x, y uniform in [-init_amp, init_amp) (see init_value).
+ *
+ * lambda: R x K doubles. x_init/y_init (R x n) override the Philox start when given.
+ * Outputs: bits (R x W packed spins), optionally x_out, y_out (R x n) and c0_out (R).
+ * ---------------------------------------------------------------------------------- */
+int or_sb(int n, int K, int64_t E, const int32_t* ei, const int32_t* ej, const int32_t* w,
+          int R, const double* lambda,
+          int variant /* 0 = dSB, 1 = bSB */, int T, double dt, double a0, double alpha,
+          float init_amp, const double* schedule, int noise_sqrt_dt,
+          uint64_t seed, uint64_t round,
+          const double* x_init, const double* y_init,
+          uint64_t* bits, double* x_out, double* y_out, double* c0_out)
+{
+    int W = (n + 63) / 64;
+    int64_t* rowsum = (int64_t*)calloc((size_t)n * K, sizeof(int64_t));
+    for (int64_t e = 0; e < E; ++e)
+        for (int k = 0; k < K; ++k) {
+            rowsum[(int64_t)ei[e] * K + k] += w[(int64_t)k * E + e];
+            rowsum[(int64_t)ej[e] * K + k] += w[(int64_t)k * E + e];
+        }
+    int status = 0;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int r = 0; r < R; ++r) {
+        const double* c = lambda + (int64_t)r * K;
+        double* x = (double*)malloc(sizeof(double) * n);
+        double* y = (double*)malloc(sizeof(double) * n);
+        double* f = (double*)malloc(sizeof(double) * n);
+        double* phi = (double*)malloc(sizeof(double) * n);
+        double* Jc = (double*)malloc(sizeof(double) * (E > 0 ? E : 1));
+        double* absrow = (double*)calloc((size_t)n, sizeof(double));
+
+        /* J(c) per edge, Eq. H_total */
+        for (int64_t e = 0; e < E; ++e) {
+            double v = 0.0;
+            for (int k = 0; k < K; ++k) v += c[k] * (double)w[(int64_t)k * E + e];
+            Jc[e] = v;
+            absrow[ei[e]] += fabs(v);
+            absrow[ej[e]] += fabs(v);
+        }
+        /* c0 = 1 / max_i |sum_j J(c)_ij|, from the integer row sums */
+        double mx = 0.0, mxabs = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int k = 0; k < K; ++k) s += c[k] * (double)rowsum[(int64_t)i * K + k];
+            if (fabs(s) > mx) mx = fabs(s);
+            if (absrow[i] > mxabs) mxabs = absrow[i];
+        }
+        double c0 = mx > 0.0 ? 1.0 / mx : (mxabs > 0.0 ? 1.0 / mxabs : 1.0);
+        if (c0_out) c0_out[r] = c0;
+
+        for (int i = 0; i < n; ++i) {
+            if (x_init) {
+                x[i] = x_init[(int64_t)r * n + i];
+                y[i] = y_init ? y_init[(int64_t)r * n + i] : 0.0;
+            } else {
+                or_initial_state(seed, round, (uint32_t)r, (uint32_t)i, init_amp, &x[i], &y[i]);
+            }
+        }
+        for (int m = 0; m < T; ++m) {
+            double a = schedule ? schedule[m] : (T > 1 ? a0 * (double)m / (double)(T - 1) : 0.0);
+            for (int i = 0; i < n; ++i)
+                phi[i] = (variant == 0) ? (x[i] >= 0.0 ? 1.0 : -1.0) : x[i];
+            for (int i = 0; i < n; ++i) f[i] = 0.0;
+            for (int64_t e = 0; e < E; ++e) { /* Jt = -J(c) */
+                f[ei[e]] += -Jc[e] * phi[ej[e]];
+                f[ej[e]] += -Jc[e] * phi[ei[e]];
+            }
+            for (int i = 0; i < n; ++i) {
+                double drift = -(a0 - a) * x[i] + c0 * f[i];
+                double noise = 0.0;
+                if (alpha != 0.0)
+                    noise = alpha * or_normal(seed, round, (uint32_t)r, (uint32_t)i, (uint64_t)m);
+                if (noise_sqrt_dt)
+                    y[i] = y[i] + dt * drift + sqrt(dt) * noise;
+                else
+                    y[i] = y[i] + dt * (drift + noise);
+                x[i] = x[i] + dt * a0 * y[i];
+                if (fabs(x[i]) > 1.0) {
+                    x[i] = x[i] > 0.0 ? 1.0 : -1.0;
+                    y[i] = 0.0;
+                }
+            }
+        }
+        uint64_t* b = bits + (int64_t)r * W;
+        for (int q = 0; q < W; ++q) b[q] = 0;
+        for (int i = 0; i < n; ++i) {
+            if (x[i] < 0.0) b[i >> 6] |= (uint64_t)1 << (i & 63);
+            if (x_out) x_out[(int64_t)r * n + i] = x[i];
+            if (y_out) y_out[(int64_t)r * n + i] = y[i];
+        }
+        free(x); free(y); free(f); free(phi); free(Jc); free(absrow);
+    }
+    free(rowsum);
+    return status;
+}
+
+/* Reference point r_k = sum_E min(0, J^(k)_e): every cut value satisfies C_k(s) >= r_k
+ * (each edge adds J or 0), so r is dominated by every sample, as the HV definition
+ * requires. */
+void or_reference_point(int K, int64_t E, const int32_t* w, int64_t* ref)
+{
+    for (int k = 0; k < K; ++k) {
+        int64_t s = 0;
+        for (int64_t e = 0; e < E; ++e)
+            if (w[(int64_t)k * E + e] < 0) s += w[(int64_t)k * E + e];
+        ref[k] = s;
+    }
+}
