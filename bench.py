@@ -1,0 +1,376 @@
+"""Benchmark of the NI-SB multi-objective MaxCut hot path on B300.
+
+One step = one pass of the whole path over one batch: NI-dSB sampling of R replicas
+(each on its own weight vector), exact K-objective cuts of every sample, the Pareto
+filter into a fresh device archive, and the exact hypervolume of the front.
+
+Workload (default): heavy-hex-like graph n=42 / E=50, K=4 integer objectives in
+{-10..10}\\{0}, R=16384 replicas with uniform-simplex weight vectors, dSB, T=2000
+steps, dt=0.5, linear pump 0 -> 1, x, y start in U(-0.1, 0.1), noise alpha=0.1.
+
+Printed JSON (rank 0, one line): replica-spin-updates/s of the whole step (R*n*T per
+step / device time of the step) plus roofline, cpu_baseline, e2e, clocks,
+gpu_launches and a time-to-99%-hypervolume comparison with the plain FP32 sampler.
+`--impl reference` times the CPU oracle instead, on a bounded sample of the same
+workload. Under torchrun every rank runs its own shard (weak scaling, no collective
+on the data path); timings are the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="precision", graph="heavy-hex-like n=42 E=50 maxdeg 3", n=42, K=4, wmax=10, R=16384, T=2000,
+                variant="dsb", dt=0.5, a0=1.0, alpha=0.1, init_amp=0.1, instance_seed=1001)
+METRIC = "replica-spin-updates/s"
+# Algorithmic lane operations per replica-spin update of NI-dSB (derivation with the
+# design notes): force d = 2E/n multiply-adds, Euler update + wall + sign 9, one Gaussian
+# from a quarter Philox4x32-10 block (20) and half a Box-Muller pair (7).
+def ops_per_spin_update(n, E):
+    return 2.0 * E / n + 9 + 20 + 7
+
+
+def peak_alu_tops():
+    """FP32/INT32 lane-op peak: 148 SMs x 128 lanes x 2032 MHz (the maximum SM clock)."""
+    return 148 * 128 * 2.032e9 / 1e12
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+def profile_traffic(kernel_file, summary):
+    """Per-launch DRAM bytes recorded in a committed ncu summary, if the kernel source is
+    unchanged since (the summary stores the source hash); else None."""
+    path = os.path.join(ROOT, "profiles", summary)
+    src = os.path.join(ROOT, "paper_2604_26477_b300", "csrc", kernel_file)
+    try:
+        text = open(path).read()
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    hm = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    if not m or not hm or hm.group(1) != h:
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi sampling during the timed region (SM clock and throttle reasons)."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------ oracle
+def cpu_baseline_worker(args):
+    """Runs in a fresh process: times the CPU oracle on a bounded replica sample."""
+    import oracle
+    from paper_2604_26477_b300 import workloads as wl
+
+    w = WORKLOAD
+    src = wl.heavy_hex_like(w["instance_seed"], K=w["K"], wmax=w["wmax"])
+    oracle.build()
+    # calibrate on 32 replicas, then size the sample for about args.cpu_seconds
+    probe = 32
+    lam = wl.dirichlet_lambdas(probe, w["K"], 1).astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.sb(src, lam, variant=w["variant"], steps=w["T"], dt=w["dt"], a0=w["a0"], alpha=w["alpha"], seed=1)
+    per_rep = (time.perf_counter() - t0) / probe
+    Rs = int(max(probe, min(w["R"], args.cpu_seconds / max(per_rep, 1e-9))))
+    results = []
+    for step in range(max(1, args.cpu_steps)):
+        lam = wl.dirichlet_lambdas(Rs, w["K"], 100 + step).astype(np.float64)
+        t0 = time.perf_counter()
+        o = oracle.sb(src, lam, variant=w["variant"], steps=w["T"], dt=w["dt"], a0=w["a0"], alpha=w["alpha"],
+                      seed=step)
+        cuts = oracle.cuts(src, o["bits"])
+        keep = oracle.pareto_filter(cuts)
+        hv = oracle.hypervolume(cuts[keep], oracle.reference_point(src))
+        dt = time.perf_counter() - t0
+        results.append(Rs * src.n * w["T"] / dt)
+    out = {"value": float(np.median(results)), "unit": METRIC, "cores": int(os.environ.get("OMP_NUM_THREADS", "1")),
+           "kind": "oracle", "sample": f"{Rs} of {w['R']} replicas, full T={w['T']} trajectories, "
+           f"then cuts, Pareto filter and hypervolume of those samples (FP64 oracle, OpenMP over replicas)",
+           "seconds_per_step": Rs * src.n * w["T"] / float(np.median(results)), "front": int(len(keep)), "hv": int(hv)}
+    print("CPU_BASELINE " + json.dumps(out), flush=True)
+
+
+def run_cpu_baseline(cpu_seconds=15.0, steps=1):
+    env = dict(os.environ)
+    env["OMP_NUM_THREADS"] = str(os.cpu_count() or 1)
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-worker", "--cpu-seconds", str(cpu_seconds),
+           "--cpu-steps", str(steps)]
+    p = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=1800)
+    for ln in p.stdout.splitlines():
+        if ln.startswith("CPU_BASELINE "):
+            return json.loads(ln[len("CPU_BASELINE "):])
+    return {"value": None, "unit": METRIC, "cores": None, "kind": "oracle", "sample": "failed: " + p.stderr[-300:]}
+
+
+# ------------------------------------------------------------------------------ GPU arm
+def gpu_arm(args, rank, world):
+    import torch
+
+    from paper_2604_26477_b300 import moqaia as M
+    from paper_2604_26477_b300 import pipeline as P
+    from paper_2604_26477_b300 import workloads as wl
+
+    w = WORKLOAD
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    src = wl.heavy_hex_like(w["instance_seed"], K=w["K"], wmax=w["wmax"])
+    R, T, n, K = w["R"], w["T"], src.n, src.K
+    inst = P.Instance(src)
+    arch = P.Archive(n, K, capacity=1 << 18, max_batch=R)
+    buf = P.RoundBuffers(R, n, K)
+    params = M.moq_default_params(variant=w["variant"], steps=T, dt=w["dt"], a0=w["a0"], alpha=w["alpha"],
+                                  init_amp=w["init_amp"])
+    nsteps = args.warmup + args.steps
+    # inputs resident in HBM before the timed region: one weight-vector batch per step
+    lam_all = torch.from_numpy(np.stack([wl.dirichlet_lambdas(R, K, 10_000 * rank + s) for s in range(nsteps)])).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 126 MB L2
+    launches_per_step = 1 + 1 + 6 + 3  # sample, cuts, Pareto merge (6), hypervolume (3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+    fronts, hvs = [], []
+
+    def step(s):
+        arch.reset()
+        e0, e1, e2 = ev[s]
+        e0.record(stream)
+        M.moq_sample(inst.handle, lam_all[s], R, params, 1 + rank, s, buf.bits)
+        e1.record(stream)
+        M.moq_evaluate_cuts(inst.handle, buf.bits, R, buf.cuts)
+        arch.merge(buf.cuts, buf.bits, R, 0)
+        hvs.append(arch.hypervolume(inst.ref))  # synchronises: the step's result is on the host
+        e2.record(stream)
+
+    for s in range(args.warmup):
+        flush.zero_()
+        step(s)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        t_wall = time.perf_counter()
+        for s in range(args.warmup, nsteps):
+            flush.zero_()
+            step(s)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    fronts.append(arch.size())
+    step_ms = [ev[s][0].elapsed_time(ev[s][2]) for s in range(args.warmup, nsteps)]
+    sample_ms = [ev[s][0].elapsed_time(ev[s][1]) for s in range(args.warmup, nsteps)]
+    dev_s = sum(step_ms) / 1e3
+    times = torch.tensor([dev_s, t_wall, sum(sample_ms) / 1e3], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(times, op=torch.distributed.ReduceOp.MAX)
+    dev_s, t_wall, samp_s = times.tolist()
+    units = R * n * T * args.steps * world
+    value = units / dev_s
+
+    # e2e through the C ABI with host buffers: weight vectors copied in from pinned host
+    # memory every step, hypervolume and front size read back every step
+    lam_host = torch.from_numpy(wl.dirichlet_lambdas(R, K, 777 + rank)).pin_memory()
+    lam_dev = torch.empty_like(lam_host, device=dev)
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for s in range(e2e_steps):
+        lam_dev.copy_(lam_host, non_blocking=True)
+        arch.reset()
+        M.moq_sample(inst.handle, lam_dev, R, params, 99 + rank, s, buf.bits)
+        M.moq_evaluate_cuts(inst.handle, buf.bits, R, buf.cuts)
+        arch.merge(buf.cuts, buf.bits, R, 0)
+        arch.hypervolume(inst.ref)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": R * n * T * e2e_steps / e2e_s * world, "unit": METRIC,
+           "h2d_bytes_per_step": R * K * 4, "d2h_bytes_per_step": 8 + 4 + 8 + 4 + 16 + 4}
+
+    peaks = measured_peaks()
+    ops = ops_per_spin_update(n, src.E)
+    sample_avg = samp_s / args.steps
+    achieved = ops * R * n * T / sample_avg / 1e12
+    roofline = {"bound": "alu", "kernel": "k_sb_sparse", "achieved": achieved, "peak": peak_alu_tops(),
+                "unit": "Tops/s", "frac": achieved / peak_alu_tops(),
+                "traffic": profile_traffic("sb_sparse.cu", "sb_sparse_precision_n42_K4.txt"),
+                "peak_source": "derived: 148 SMs x 128 FP32/INT32 lanes x 2032 MHz max SM clock",
+                "ops_per_spin_update": ops, "kernel_ms": sample_avg * 1e3,
+                "hbm_peak_measured_gbs": peaks.get("hbm_gbs")}
+    return {"value": value, "ms_per_step": dev_s / args.steps * 1e3, "wall_s": t_wall, "e2e": e2e,
+            "roofline": roofline, "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps,
+            "front_last": fronts[-1], "hv_last": int(hvs[-1]), "sampling_only_value": units / samp_s,
+            "inst": inst, "src": src, "params": params}
+
+
+def time_to_target_block(args, src):
+    """Time to 99% of the plain sampler's final hypervolume, plain vs the timed form."""
+    import torch
+
+    from paper_2604_26477_b300 import moqaia as M
+    from paper_2604_26477_b300 import pipeline as P
+
+    w = WORKLOAD
+    plain = M.moq_default_params(variant="dsb", steps=1000, dt=0.5, alpha=0.0)
+    # plain FP32 uniform-lambda dSB, 1024 replicas per round, fixed budget of rounds
+    inst = P.Instance(src)
+    arch = P.Archive(src.n, src.K, capacity=1 << 18, max_batch=w["R"])
+    buf = P.RoundBuffers(1024, src.n, src.K)
+    for rnd in range(args.ttt_rounds):
+        P.sample_round(inst, arch, buf, plain, seed=4242, round_=rnd)
+    hv_plain_final = arch.hypervolume(inst.ref)
+    target = (hv_plain_final * 99 + 99) // 100
+    arch.close()
+    inst.close()
+    torch.cuda.synchronize()
+    res = {"target_hv": int(target), "hv_plain_final": int(hv_plain_final), "plain_budget_rounds": args.ttt_rounds}
+    for label, params, R in [("plain_fp32_dsb_R1024_T1000", plain, 1024),
+                             ("chosen_dsb_R16384_T2000_alpha0.1", M.moq_default_params(
+                                 variant="dsb", steps=w["T"], dt=w["dt"], alpha=w["alpha"]), w["R"])]:
+        runs = [P.time_to_target(src, target, params, R, seed=s, max_rounds=4 * args.ttt_rounds) for s in range(3)]
+        res[label] = {"seconds_median": float(np.median([r["seconds"] for r in runs])),
+                      "samples_median": int(np.median([r["samples"] for r in runs])),
+                      "reached": all(r["reached"] for r in runs)}
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ttt-rounds", type=int, default=64)
+    ap.add_argument("--no-ttt", action="store_true")
+    ap.add_argument("--cpu-baseline-worker", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours" and not args.cpu_baseline_worker:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+
+    if args.cpu_baseline_worker:
+        cpu_baseline_worker(args)
+        return
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    w = WORKLOAD
+    config = {"workload": f"{w['name']}: {w['graph']}, K={w['K']} weights in {{-{w['wmax']}..{w['wmax']}}}\\{{0}}, "
+                          f"R={w['R']} uniform-simplex lambda, {w['variant']} T={w['T']} dt={w['dt']} "
+                          f"alpha={w['alpha']}, cuts + Pareto + hypervolume per step",
+              "n": w["n"], "K": w["K"], "R": w["R"], "T": w["T"], "variant": w["variant"], "dt": w["dt"],
+              "alpha": w["alpha"], "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas x{world}"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps = max(1, args.steps)
+        cb = run_cpu_baseline(cpu_seconds=min(args.cpu_seconds, 60.0 / steps + 5), steps=steps)
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": METRIC, "n_gpus": args.gpus,
+                "steps": steps, "warmup": args.warmup, "ms_per_step": cb.get("seconds_per_step", 0) * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": config,
+                "cpu_baseline": {k: cb.get(k) for k in ("value", "unit", "cores", "kind", "sample")},
+                "e2e": {"value": cb["value"], "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    cpu_base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_base = run_cpu_baseline(cpu_seconds=args.cpu_seconds)  # before any CUDA work in this process
+    import torch
+
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    res = gpu_arm(args, rank, world)
+    ttt = None
+    if rank == 0 and not args.no_ttt:
+        ttt = time_to_target_block(args, res["src"])
+    if rank == 0:
+        line = {"metric": METRIC, "value": res["value"], "unit": METRIC, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+                "roofline": res["roofline"], "cpu_baseline": cpu_base, "e2e": res["e2e"], "clocks": res["clocks"],
+                "gpu_launches": res["gpu_launches"], "sampling_only_value": res["sampling_only_value"],
+                "front_points_last_step": res["front_last"], "hv_last_step": res["hv_last"],
+                "time_to_99pct_hv": ttt}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

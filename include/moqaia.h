@@ -1,0 +1,194 @@
+/*
+ * moqaia.h -- C ABI of the B300 library for multi-objective MaxCut sampled by
+ * noise-injected simulated bifurcation (NI-SB), after "Multi-Objective Optimization
+ * by Quantum-Annealing-Inspired Algorithms" (arXiv 2604.26477).
+ *
+ * Pipeline (one round): weight vectors -> moq_sample (SB replicas, packed spins)
+ * -> moq_evaluate_cuts (exact K-objective cut values) -> moq_pareto_front (dedup +
+ * non-dominated filter merged into a device archive) -> moq_hypervolume (exact).
+ *
+ * Conventions shared by every call:
+ *  - Return value: MOQ_OK (0) or a negative MOQ_ERR_* code. No C++ exception and no
+ *    abort crosses this interface. moq_last_error_message() gives a per-thread text.
+ *  - Memory: pointers documented "device" are caller-owned device memory of the
+ *    current CUDA device; "host" pointers are ordinary host memory. The library
+ *    allocates device memory only inside instance and archive handles, at creation,
+ *    and frees it in the matching destroy call.
+ *  - Streams: `stream` is a cudaStream_t (NULL = legacy default stream). Calls are
+ *    stream-ordered and asynchronous unless documented as synchronising.
+ *  - Spin packing: a configuration s in {-1,+1}^n is W = ceil(n/64) uint64 words;
+ *    bit (i mod 64) of word i/64 is 1 exactly when s_i = -1. Bits >= n are 0.
+ *    Arrays of configurations are row-major: sample m occupies words [m*W, m*W+W).
+ *  - Cut vectors are int64, row-major M x K.
+ *  - Limits: 2 <= n, n <= 2^24 (sampler: n <= 1024 per replica block), 2 <= K <= 8,
+ *    weights are int32, E < 2^31.
+ */
+#ifndef MOQAIA_H
+#define MOQAIA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+#if defined(__GNUC__)
+#pragma GCC visibility push(default) /* the library is built with hidden visibility */
+#endif
+
+/* ---- status codes ------------------------------------------------------------- */
+#define MOQ_OK 0
+#define MOQ_ERR_ARG -1         /* invalid argument (range, duplicate edge, NULL) */
+#define MOQ_ERR_OOM -2         /* device allocation failed */
+#define MOQ_ERR_CUDA -3        /* a CUDA runtime call or kernel launch failed */
+#define MOQ_ERR_TIMEOUT -4     /* a device-side wait ran out of its budget */
+#define MOQ_ERR_CAPACITY -5    /* the archive (or a buffer) is too small */
+#define MOQ_ERR_OVERFLOW -6    /* a result would leave the exact integer range */
+#define MOQ_ERR_UNSUPPORTED -7 /* valid request outside what this build implements */
+
+/* ---- SB variants ("Simulated Bifurcation with Gaussian noise") ----------------- */
+#define MOQ_DSB 0 /* discrete SB: phi(x) = sgn(x) */
+#define MOQ_BSB 1 /* ballistic SB: phi(x) = x */
+
+typedef struct moq_instance moq_instance;
+typedef struct moq_archive moq_archive;
+
+/* Summary of an instance, filled by moq_instance_get_info. */
+typedef struct moq_instance_info {
+    int32_t n, K;
+    int64_t E;
+    int32_t max_degree;
+    int32_t words;            /* W = ceil(n/64) */
+    int64_t weight_sum[8];    /* W_k = sum_E J^(k) */
+    int64_t abs_sum[8];       /* sum_E |J^(k)|, bounds every cut range */
+    int64_t ref_point[8];     /* r_k = sum_E min(0, J^(k)): C_k(s) >= r_k for every s */
+} moq_instance_info;
+
+/* Parameters of one sampling call ("Simulated Bifurcation with Gaussian noise"). */
+typedef struct moq_sample_params {
+    int32_t variant;       /* MOQ_DSB or MOQ_BSB */
+    int32_t steps;         /* T >= 0 Euler steps */
+    float dt;              /* time step (paper: 1) */
+    float a0;              /* pump ceiling a0 (paper: 1) */
+    float alpha;           /* noise amplitude of Eq. NI-SB (0 = plain SB) */
+    float init_amp;        /* x, y start uniform in [-init_amp, init_amp) */
+    int32_t noise_sqrt_dt; /* 0: y += dt*alpha*eta (Euler of Eq. NI-SB); 1: alpha*sqrt(dt)*eta */
+    const float* schedule; /* device, T entries a_m, or NULL for a_m = a0*m/(T-1) */
+    const float* x_init;   /* device R x n, or NULL (Philox start) */
+    const float* y_init;   /* device R x n, or NULL (zero when x_init is given) */
+    float* x_out;          /* device R x n final positions, or NULL */
+    float* y_out;          /* device R x n final momenta, or NULL */
+} moq_sample_params;
+
+/* Result of moq_hypervolume: value = hi * 2^64 + (uint64)lo (a signed 128-bit int). */
+typedef struct moq_hv {
+    int64_t lo;
+    int64_t hi;
+    double approx; /* the same value rounded to double */
+} moq_hv;
+
+/* Fills p with the paper's defaults: dSB, T = 1000, dt = 1, a0 = 1, alpha = 0,
+ * init_amp = 0.1, noise y += dt*alpha*eta, linear pump, no optional arrays. */
+void moq_default_params(moq_sample_params* p);
+
+/* ---- a1: instance build ("Hamiltonian formulation of multi-objective MaxCut") ---
+ * Graph G = (V, E), |V| = n, edge e = (ei[e], ej[e]) with 0 <= ei[e] < ej[e] < n, and K
+ * integer weight sets: w[k*E + e] = J^(k) of edge e (host, row k = objective k).
+ * Builds the device graph (both-direction CSR with per-entry weights, integer row
+ * sums sum_j J^(k)_ij, W_k, sum |J^(k)|, r_k). Synchronises `stream`.
+ * Errors: MOQ_ERR_ARG (n < 2, K outside [2, 8], E < 0, an endpoint out of range,
+ * ei >= ej, a repeated edge, NULL pointers with E > 0), MOQ_ERR_OOM, MOQ_ERR_CUDA.
+ * Ownership: inputs are copied; *out is owned by the caller until destroyed. */
+int moq_create_instance(int32_t n, int32_t K, int64_t E, const int32_t* ei, const int32_t* ej,
+                        const int32_t* w, void* stream, moq_instance** out);
+void moq_destroy_instance(moq_instance* inst);
+int moq_instance_get_info(const moq_instance* inst, moq_instance_info* out);
+
+/* ---- a2..a5: sampling ("Simulated Bifurcation with Gaussian noise", Eq. NI-SB) ---
+ * R replicas; replica r runs SB on J(c) = sum_k c_k J^(k) with c = lambda[r*K..r*K+K)
+ * (device, float, Eq. H_total; rows are used as given, the paper takes sum c = 1):
+ *   c0 = 1/max_i |sum_j J(c)_ij| (1/max_i sum_j |J(c)_ij| if all row sums vanish,
+ *   1 if J(c) = 0); force c0 * sum_j (-J(c)_ij) phi(x_j) (the negated coupling, so that
+ *   the attractors minimise H_total, i.e. maximise the weighted cut);
+ *   y += dt*(-(a0 - a_m) x + force + alpha*eta); x += dt*a0*y; |x| > 1 -> x = sgn x, y = 0;
+ *   s = sgn(x) with sgn(0) = +1, written to bits (device, R x W words).
+ * eta comes from Philox4x32-10 with key = seed and counter (m >> 2, i, r, round) through
+ * Box-Muller; the start state from counter (0xFFFFFFFF, i, r, round). `seed` and
+ * `round` fully determine the output on a given GPU build.
+ * Errors: MOQ_ERR_ARG (R < 0, steps < 0, bad variant, NULL lambda/bits with R > 0),
+ * MOQ_ERR_UNSUPPORTED (n > 1024 or max degree > 16), MOQ_ERR_CUDA. Asynchronous. */
+int moq_sample(const moq_instance* inst, const float* lambda, int32_t R, const moq_sample_params* p,
+               uint64_t seed, uint64_t round, uint64_t* bits, void* stream);
+
+/* ---- a6: exact cut values, Eq. (single_obj) -------------------------------------
+ * cuts[m*K + k] = C_k(s^(m)) = sum over edges with s_i != s_j of J^(k)_ij, for the M
+ * packed configurations bits (device, M x W) into cuts (device, M x K int64).
+ * Exact (integer). Errors: MOQ_ERR_ARG, MOQ_ERR_CUDA. Asynchronous. */
+int moq_evaluate_cuts(const moq_instance* inst, const uint64_t* bits, int64_t M, int64_t* cuts, void* stream);
+
+/* ---- a7: Pareto filter with dedup into a device archive ("Pareto filtering") ----
+ * The archive holds the distinct non-dominated cut vectors seen so far (maximisation:
+ * u dominates v iff u_k >= v_k for all k and u_j > v_j for some j), each with one
+ * representative configuration -- the one with the lowest global sample index,
+ * canonicalised to s_0 = +1 (C(s) = C(-s)) -- and that index.
+ * capacity: most vectors the archive can hold; max_batch: most candidates per call.
+ * Device memory for both is allocated here. Errors: MOQ_ERR_ARG, MOQ_ERR_OOM. */
+int moq_archive_create(int32_t n, int32_t K, int64_t capacity, int64_t max_batch, moq_archive** out);
+void moq_archive_destroy(moq_archive* a);
+/* Empties the archive (stream-ordered). */
+int moq_archive_reset(moq_archive* a, void* stream);
+/* Merges M candidates (cuts: device M x K int64; bits: device M x W) whose global
+ * sample indices are index_base + m; callers give increasing index_base across calls,
+ * so earlier members win ties. If front_size_out is non-NULL the call synchronises and
+ * writes the new archive size there (and reports a capacity overflow as
+ * MOQ_ERR_CAPACITY); otherwise it is asynchronous and an overflow -- which leaves
+ * the archive unchanged -- is reported by the next synchronising archive call.
+ * Errors: MOQ_ERR_ARG (M < 0 or M > max_batch, NULL), MOQ_ERR_CAPACITY, MOQ_ERR_CUDA. */
+int moq_pareto_front(moq_archive* a, const int64_t* cuts, const uint64_t* bits, int64_t M, int64_t index_base,
+                     int64_t* front_size_out, void* stream);
+/* Archive size (synchronises). Returns a pending capacity error, if any. */
+int moq_archive_size(const moq_archive* a, int64_t* size_out, void* stream);
+/* Copies up to cap members to host arrays (cuts_host cap x K, bits_host cap x W,
+ * index_host cap; any may be NULL) and the size to *n_out. Synchronises. */
+int moq_archive_copy_out(const moq_archive* a, int64_t* cuts_host, uint64_t* bits_host, int64_t* index_host,
+                         int64_t cap, int64_t* n_out, void* stream);
+/* Device pointers to the current archive arrays (valid until the next merge/reset). */
+int moq_archive_device_view(const moq_archive* a, const int64_t** cuts, const uint64_t** bits,
+                            const int64_t** index, const int64_t** size_dev);
+
+/* ---- a8: hypervolume ("Hamiltonian formulation" Eq. HV, Appendix A) -------------
+ * Exact Lebesgue measure of the union of boxes prod_k [ref_k, y_k] over the archive
+ * front (maximisation), in 128-bit integers; points with some y_k < ref_k span an
+ * empty box and are left out. ref: host, K int64. *out: host. K in {2, 3, 4}.
+ * Synchronises. Errors: MOQ_ERR_ARG, MOQ_ERR_UNSUPPORTED (K > 4),
+ * MOQ_ERR_OVERFLOW (product of the K side lengths >= 2^125), MOQ_ERR_CUDA. */
+int moq_hypervolume(const moq_archive* a, const int64_t* ref, moq_hv* out, void* stream);
+/* The same for an arbitrary point set: pts device F x K int64 (need not be
+ * non-dominated). workspace: device scratch of moq_hypervolume_workspace_size(F, K)
+ * bytes, 256-byte aligned, owned by the caller. */
+int64_t moq_hypervolume_workspace_size(int64_t F, int32_t K);
+int moq_hypervolume_points(const int64_t* pts, int64_t F, int32_t K, const int64_t* ref, void* workspace,
+                           moq_hv* out, void* stream);
+
+/* ---- a2: weight vectors ("Scalarization via the weighted sum method", App. B) ----
+ * Das-Dennis lattice of resolution H: c in {0, 1/H, .., 1}^K with sum 1 (interior != 0:
+ * every c_k > 0, the paper's choice), lexicographically ascending in (m_1..m_K), c = m/H.
+ * Writes min(count, capacity) rows to lambda (device, float) and count to *count_out.
+ * Errors: MOQ_ERR_ARG, MOQ_ERR_CAPACITY (count > capacity). Asynchronous. */
+int moq_lambda_das_dennis(int32_t K, int32_t H, int32_t interior, float* lambda, int64_t capacity,
+                          int64_t* count_out, void* stream);
+/* R vectors uniform on the simplex (Dirichlet(1,..,1)): c_k = e_k / sum e, e_k = -ln u_k,
+ * u_k = ((word >> 8) + 1) 2^-24 with word k & 3 of Philox4x32-10(key = seed,
+ * counter = (r, k >> 2, 0x4C414D42, round)). lambda: device R x K float. Asynchronous. */
+int moq_lambda_dirichlet(int32_t K, int32_t R, uint64_t seed, uint64_t round, float* lambda, void* stream);
+
+/* ---- errors -------------------------------------------------------------------- */
+const char* moq_strerror(int code);
+const char* moq_last_error_message(void);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
+#ifdef __cplusplus
+}
+#endif
+#endif /* MOQAIA_H */

@@ -1,0 +1,374 @@
+// a8: exact hypervolume ("Hamiltonian formulation" Eq. HV and Appendix A): the measure
+// of the union of boxes prod_k [r_k, y_k] over a point set (maximisation), in 128-bit
+// integers, for K = 2, 3, 4.
+//
+// Slicing: with the points ranked by y_{K-1} descending, the slab between the t-th and
+// the (t+1)-th value is covered, in the first K-1 objectives, by exactly the points of
+// rank <= t, so HV = sum_t (y_{K-1}[t] - y_{K-1}[t+1]) * HV_{K-1}(rank <= t). Every slab
+// is independent, which is what the GPU parallelises:
+//   K = 2: one thread per slab; its length is a prefix maximum of y_0.
+//   K = 3: one thread per slab; its area is the 2-D staircase over the points sorted by
+//          y_0 descending, restricted to rank_2 <= t. All threads walk the same sorted
+//          sequence in lockstep from shared memory (broadcast reads).
+//   K = 4: one block per slab of y_3 and one thread per sub-slab of y_2; the area walk is
+//          the same staircase restricted to rank_3 <= t and rank_2 <= s.
+// Ranks come from counting (O(F^2) comparisons, deterministic), ties broken by index.
+// Slab contributions are reduced per block in int128 and summed by a final block.
+// Points with some y_k < r_k span an empty box and are left out.
+#include <algorithm>
+
+#include "moq_common.cuh"
+
+namespace moq {
+namespace {
+
+typedef __int128 i128;
+constexpr int kThreads = 256;
+constexpr int kChunk = 1024;
+
+struct HvWs {
+    int32_t* rank;   // K x F, -1 for left-out points
+    int32_t* order;  // K x F, order[d*F + rank] = point
+    i128* partial;   // one per block of the slab kernels
+    int32_t* fv;     // number of points kept
+    i128* result;
+    int32_t* flags;
+};
+
+__host__ __device__ inline size_t al256(size_t v) { return (v + 255) / 256 * 256; }
+
+__host__ __device__ inline HvWs carve(void* base, int64_t F, int K)
+{
+    if (F < 1) F = 1;
+    unsigned char* p = static_cast<unsigned char*>(base);
+    HvWs w;
+    w.rank = reinterpret_cast<int32_t*>(p);
+    p += al256(sizeof(int32_t) * (size_t)K * F);
+    w.order = reinterpret_cast<int32_t*>(p);
+    p += al256(sizeof(int32_t) * (size_t)K * F);
+    w.partial = reinterpret_cast<i128*>(p);
+    p += al256(sizeof(i128) * (size_t)F);
+    w.fv = reinterpret_cast<int32_t*>(p);
+    w.result = reinterpret_cast<i128*>(p + 16);
+    w.flags = reinterpret_cast<int32_t*>(p + 32);
+    return w;
+}
+
+struct Ref4 {
+    int64_t r[4];
+};
+
+template <int KT>
+__global__ void __launch_bounds__(kThreads) k_hv_rank(const int64_t* __restrict__ pts, int64_t F, Ref4 ref, HvWs ws)
+{
+    __shared__ int64_t tile[kThreads][KT];
+    __shared__ int32_t tvalid[kThreads];
+    const int tid = threadIdx.x;
+    const int64_t p = blockIdx.x * (int64_t)kThreads + tid;
+    const bool act = p < F;
+    int64_t u[KT];
+    bool valid = act;
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+        u[k] = act ? pts[p * KT + k] : 0;
+        valid &= u[k] >= ref.r[k];
+    }
+    int32_t rank[KT];
+#pragma unroll
+    for (int k = 0; k < KT; ++k) rank[k] = 0;
+    for (int64_t base = 0; base < F; base += kThreads) {
+        const int cnt = (int)min((int64_t)kThreads, F - base);
+        __syncthreads();
+        if (tid < cnt) {
+            bool v = true;
+#pragma unroll
+            for (int k = 0; k < KT; ++k) {
+                tile[tid][k] = pts[(base + tid) * KT + k];
+                v &= tile[tid][k] >= ref.r[k];
+            }
+            tvalid[tid] = v;
+        }
+        __syncthreads();
+        if (valid) {
+            for (int t = 0; t < cnt; ++t) {
+                if (!tvalid[t]) continue;
+                const int64_t q = base + t;
+#pragma unroll
+                for (int k = 0; k < KT; ++k) rank[k] += (tile[t][k] > u[k]) || (tile[t][k] == u[k] && q < p);
+            }
+        }
+    }
+    if (act) {
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            ws.rank[k * F + p] = valid ? rank[k] : -1;
+            if (valid) ws.order[k * F + rank[k]] = (int32_t)p;
+        }
+        if (valid) atomicAdd(ws.fv, 1);
+    }
+}
+
+__device__ i128 block_sum(i128 v, i128* red)
+{
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    const i128 out = red[0];
+    __syncthreads();
+    return out;
+}
+
+// K = 2: slab t along y_1 (order_1); length = max of y_0 over ranks <= t.
+__global__ void __launch_bounds__(kThreads) k_hv2(const int64_t* __restrict__ pts, int64_t F, Ref4 ref, HvWs ws)
+{
+    __shared__ int64_t s_u0[kChunk];
+    __shared__ i128 red[kThreads];
+    const int Fv = *ws.fv;
+    const int64_t t = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+    const int32_t* ord1 = ws.order + F;
+    int64_t h = 0;
+    if (t < Fv) {
+        const int64_t top = pts[(int64_t)ord1[t] * 2 + 1];
+        const int64_t below = (t + 1 < Fv) ? pts[(int64_t)ord1[t + 1] * 2 + 1] : ref.r[1];
+        h = top - below;
+    }
+    int64_t best = ref.r[0];
+    const int64_t lim = min((int64_t)Fv, blockIdx.x * (int64_t)kThreads + kThreads);
+    for (int64_t base = 0; base < lim; base += kChunk) {
+        const int cnt = (int)min((int64_t)kChunk, lim - base);
+        __syncthreads();
+        for (int q = threadIdx.x; q < cnt; q += kThreads) s_u0[q] = pts[(int64_t)ord1[base + q] * 2];
+        __syncthreads();
+        if (h > 0) {
+            const int upto = (int)min((int64_t)cnt, t - base + 1);
+            for (int q = 0; q < upto; ++q) best = max(best, s_u0[q]);
+        }
+    }
+    const i128 c = (h > 0) ? (i128)h * (i128)(best - ref.r[0]) : (i128)0;
+    const i128 s = block_sum(c, red);
+    if (threadIdx.x == 0) ws.partial[blockIdx.x] = s;
+}
+
+// K = 3: slab t along y_2 (order_2); area = staircase over order_0 restricted to rank_2 <= t.
+__global__ void __launch_bounds__(kThreads) k_hv3(const int64_t* __restrict__ pts, int64_t F, Ref4 ref, HvWs ws)
+{
+    __shared__ int64_t s_u0[kChunk], s_u1[kChunk];
+    __shared__ int32_t s_r2[kChunk];
+    __shared__ i128 red[kThreads];
+    const int Fv = *ws.fv;
+    const int64_t t = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+    const int32_t* ord0 = ws.order;
+    const int32_t* ord2 = ws.order + 2 * F;
+    const int32_t* rank2 = ws.rank + 2 * F;
+    int64_t h = 0;
+    if (t < Fv) {
+        const int64_t top = pts[(int64_t)ord2[t] * 3 + 2];
+        const int64_t below = (t + 1 < Fv) ? pts[(int64_t)ord2[t + 1] * 3 + 2] : ref.r[2];
+        h = top - below;
+    }
+    i128 area = 0;
+    int64_t best1 = ref.r[1];
+    const bool any = __syncthreads_or(h > 0);
+    if (any) {
+        for (int64_t base = 0; base < Fv; base += kChunk) {
+            const int cnt = (int)min((int64_t)kChunk, Fv - base);
+            __syncthreads();
+            for (int q = threadIdx.x; q < cnt; q += kThreads) {
+                const int64_t p = ord0[base + q];
+                s_u0[q] = pts[p * 3];
+                s_u1[q] = pts[p * 3 + 1];
+                s_r2[q] = rank2[p];
+            }
+            __syncthreads();
+            if (h > 0) {
+                for (int q = 0; q < cnt; ++q) {
+                    if (s_r2[q] <= t && s_u1[q] > best1) {
+                        area += (i128)(s_u0[q] - ref.r[0]) * (i128)(s_u1[q] - best1);
+                        best1 = s_u1[q];
+                    }
+                }
+            }
+        }
+    }
+    const i128 c = (h > 0) ? (i128)h * area : (i128)0;
+    const i128 s = block_sum(c, red);
+    if (threadIdx.x == 0) ws.partial[blockIdx.x] = s;
+}
+
+// K = 4: block t = slab along y_3 (order_3); thread s = sub-slab along y_2 (order_2)
+// among points of rank_3 <= t; area = staircase over order_0 restricted to
+// rank_3 <= t and rank_2 <= s.
+__global__ void __launch_bounds__(kThreads) k_hv4(const int64_t* __restrict__ pts, int64_t F, Ref4 ref, HvWs ws)
+{
+    __shared__ int64_t s_u0[kChunk], s_u1[kChunk];
+    __shared__ int32_t s_r2[kChunk], s_r3[kChunk];
+    __shared__ i128 red[kThreads];
+    const int Fv = *ws.fv;
+    const int64_t t = blockIdx.x;
+    const int32_t* ord0 = ws.order;
+    const int32_t* ord2 = ws.order + 2 * F;
+    const int32_t* ord3 = ws.order + 3 * F;
+    const int32_t* rank2 = ws.rank + 2 * F;
+    const int32_t* rank3 = ws.rank + 3 * F;
+    int64_t h4 = 0;
+    if (t < Fv) {
+        const int64_t top = pts[(int64_t)ord3[t] * 4 + 3];
+        const int64_t below = (t + 1 < Fv) ? pts[(int64_t)ord3[t + 1] * 4 + 3] : ref.r[3];
+        h4 = top - below;
+    }
+    if (h4 <= 0) {  // uniform over the block
+        if (threadIdx.x == 0) ws.partial[blockIdx.x] = 0;
+        return;
+    }
+    i128 acc = 0;
+    for (int64_t sbase = 0; sbase < Fv; sbase += kThreads) {
+        const int64_t s = sbase + threadIdx.x;
+        int64_t h3 = 0;
+        int32_t srank = -1;
+        if (s < Fv) {
+            const int32_t ps = ord2[s];
+            if (rank3[ps] <= t) {
+                int64_t below = ref.r[2];
+                for (int64_t s2 = s + 1; s2 < Fv; ++s2) {
+                    const int32_t q = ord2[s2];
+                    if (rank3[q] <= t) {
+                        below = pts[(int64_t)q * 4 + 2];
+                        break;
+                    }
+                }
+                h3 = pts[(int64_t)ps * 4 + 2] - below;
+                srank = (int32_t)s;
+            }
+        }
+        const bool any = __syncthreads_or(h3 > 0);
+        if (!any) continue;
+        i128 area = 0;
+        int64_t best1 = ref.r[1];
+        for (int64_t base = 0; base < Fv; base += kChunk) {
+            const int cnt = (int)min((int64_t)kChunk, Fv - base);
+            __syncthreads();
+            for (int q = threadIdx.x; q < cnt; q += kThreads) {
+                const int64_t p = ord0[base + q];
+                s_u0[q] = pts[p * 4];
+                s_u1[q] = pts[p * 4 + 1];
+                s_r2[q] = rank2[p];
+                s_r3[q] = rank3[p];
+            }
+            __syncthreads();
+            if (h3 > 0) {
+                for (int q = 0; q < cnt; ++q) {
+                    if (s_r3[q] <= t && s_r2[q] <= srank && s_u1[q] > best1) {
+                        area += (i128)(s_u0[q] - ref.r[0]) * (i128)(s_u1[q] - best1);
+                        best1 = s_u1[q];
+                    }
+                }
+            }
+        }
+        if (h3 > 0) acc += (i128)h3 * area;
+    }
+    const i128 s = block_sum(acc, red);
+    if (threadIdx.x == 0) ws.partial[blockIdx.x] = (i128)h4 * s;
+}
+
+// Sum of the block partials; flags bit 0 = the side-length product reaches 2^125.
+__global__ void __launch_bounds__(kThreads) k_hv_final(const int64_t* __restrict__ pts, int64_t F, int K, Ref4 ref,
+                                                       int64_t nparts, HvWs ws)
+{
+    __shared__ i128 red[kThreads];
+    i128 acc = 0;
+    for (int64_t q = threadIdx.x; q < nparts; q += kThreads) acc += ws.partial[q];
+    const i128 s = block_sum(acc, red);
+    if (threadIdx.x == 0) {
+        const int Fv = *ws.fv;
+        int32_t flags = 0;
+        if (Fv > 0) {
+            double prod = 1.0;
+            for (int k = 0; k < K; ++k) prod *= (double)(pts[(int64_t)ws.order[k * F] * K + k] - ref.r[k]);
+            if (prod >= 0x1p125) flags |= 1;
+        }
+        *ws.result = s;
+        *ws.flags = flags;
+    }
+}
+
+}  // namespace
+}  // namespace moq
+
+extern "C" {
+
+int64_t moq_hypervolume_workspace_size(int64_t F, int32_t K)
+{
+    using namespace moq;
+    if (F < 1) F = 1;
+    if (K < 1) K = 1;
+    return (int64_t)(al256(sizeof(int32_t) * (size_t)K * F) * 2 + al256(16 * (size_t)F) + 256);
+}
+
+int moq_hypervolume_points(const int64_t* pts, int64_t F, int32_t K, const int64_t* ref, void* workspace, moq_hv* out,
+                           void* stream)
+{
+    using namespace moq;
+    if (!ref || !out || !workspace) return fail(MOQ_ERR_ARG, "moq_hypervolume_points: NULL argument");
+    if (F < 0 || F >= ((int64_t)1 << 31)) return fail(MOQ_ERR_ARG, "moq_hypervolume_points: F out of range");
+    if (K < 2) return fail(MOQ_ERR_ARG, "moq_hypervolume_points: K=%d < 2", K);
+    if (K > 4) return fail(MOQ_ERR_UNSUPPORTED, "moq_hypervolume_points: K=%d > 4", K);
+    if (F > 0 && !pts) return fail(MOQ_ERR_ARG, "moq_hypervolume_points: NULL points");
+    if (((uintptr_t)workspace) % 256) return fail(MOQ_ERR_ARG, "moq_hypervolume_points: workspace not 256-byte aligned");
+    out->lo = out->hi = 0;
+    out->approx = 0.0;
+    if (F == 0) return MOQ_OK;
+    cudaStream_t st = as_stream(stream);
+    HvWs ws = carve(workspace, F, K);
+    Ref4 r{};
+    for (int k = 0; k < K; ++k) r.r[k] = ref[k];
+    MOQ_CUDA_TRY(cudaMemsetAsync(ws.fv, 0, sizeof(int32_t), st));
+    const unsigned gF = (unsigned)ceil_div(F, kThreads);
+    int64_t nparts = 0;
+    switch (K) {
+    case 2:
+        k_hv_rank<2><<<gF, kThreads, 0, st>>>(pts, F, r, ws);
+        k_hv2<<<gF, kThreads, 0, st>>>(pts, F, r, ws);
+        nparts = gF;
+        break;
+    case 3:
+        k_hv_rank<3><<<gF, kThreads, 0, st>>>(pts, F, r, ws);
+        k_hv3<<<gF, kThreads, 0, st>>>(pts, F, r, ws);
+        nparts = gF;
+        break;
+    default:
+        k_hv_rank<4><<<gF, kThreads, 0, st>>>(pts, F, r, ws);
+        k_hv4<<<(unsigned)F, kThreads, 0, st>>>(pts, F, r, ws);
+        nparts = F;
+        break;
+    }
+    k_hv_final<<<1, kThreads, 0, st>>>(pts, F, K, r, nparts, ws);
+    MOQ_LAUNCH_CHECK("moq_hypervolume launch");
+    struct {
+        i128 v;
+        int32_t flags;
+    } host;
+    MOQ_CUDA_TRY(cudaMemcpyAsync(&host.v, ws.result, sizeof(i128), cudaMemcpyDeviceToHost, st));
+    MOQ_CUDA_TRY(cudaMemcpyAsync(&host.flags, ws.flags, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MOQ_CUDA_TRY(cudaStreamSynchronize(st));
+    if (host.flags & 1) return fail(MOQ_ERR_OVERFLOW, "moq_hypervolume: side-length product reaches 2^125");
+    out->lo = (int64_t)(uint64_t)host.v;
+    out->hi = (int64_t)(host.v >> 64);
+    out->approx = (double)host.v;
+    return MOQ_OK;
+}
+
+int moq_hypervolume(const moq_archive* a, const int64_t* ref, moq_hv* out, void* stream)
+{
+    using namespace moq;
+    if (!a || !ref || !out) return fail(MOQ_ERR_ARG, "moq_hypervolume: NULL argument");
+    if (a->K > 4) return fail(MOQ_ERR_UNSUPPORTED, "moq_hypervolume: K=%d > 4", a->K);
+    int64_t F = 0;
+    int rc = moq_archive_size(a, &F, stream);
+    if (rc != MOQ_OK) return rc;
+    return moq_hypervolume_points(a->cuts[a->cur], F, a->K, ref, a->hv_ws, out, stream);
+}
+
+}  // extern "C"

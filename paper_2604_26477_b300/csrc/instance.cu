@@ -1,0 +1,292 @@
+// a1: instance build ("Hamiltonian formulation of multi-objective MaxCut").
+// The edge list and K integer weight sets are copied to the device and turned into a
+// both-direction CSR (rows sorted by column) with per-entry weights, integer row sums
+// sum_j J^(k)_ij (used for c0 of every weight vector), and the per-objective sums
+// W_k, sum |J^(k)| and r_k = sum min(0, J^(k)).
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "moq_common.cuh"
+
+namespace moq {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__global__ void k_degree(const int32_t* __restrict__ ei, const int32_t* __restrict__ ej, int64_t E, int32_t n,
+                         int32_t* deg, int32_t* status)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = ei[e], b = ej[e];
+        if (a < 0 || b >= n || a >= b) {
+            atomicOr(status, kStatusBadEdge);
+            continue;
+        }
+        atomicAdd(&deg[a], 1);
+        atomicAdd(&deg[b], 1);
+    }
+}
+
+// rowptr[0] = 0, rowptr[i+1] = deg[0] + .. + deg[i]; one block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_scan_rowptr(const int32_t* __restrict__ deg, int32_t n, int32_t* rowptr)
+{
+    __shared__ int32_t warp_sums[32];
+    __shared__ int32_t carry;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        carry = 0;
+        rowptr[0] = 0;
+    }
+    __syncthreads();
+    for (int32_t base = 0; base < n; base += 1024) {
+        const int32_t i = base + threadIdx.x;
+        int32_t v = i < n ? deg[i] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t t = __shfl_up_sync(kFull, v, o);
+            if (lane >= o) v += t;
+        }
+        if (lane == 31) warp_sums[wid] = v;
+        __syncthreads();
+        if (wid == 0) {
+            int32_t s = warp_sums[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t t = __shfl_up_sync(kFull, s, o);
+                if (lane >= o) s += t;
+            }
+            warp_sums[lane] = s;
+        }
+        __syncthreads();
+        const int32_t incl = v + (wid > 0 ? warp_sums[wid - 1] : 0) + carry;
+        if (i < n) rowptr[i + 1] = incl;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = incl;
+        __syncthreads();
+    }
+}
+
+__global__ void k_fill(const int32_t* __restrict__ ei, const int32_t* __restrict__ ej, int64_t E, int32_t n,
+                       const int32_t* __restrict__ rowptr, int32_t* cursor, int32_t* col_tmp, int32_t* eid_tmp)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = ei[e], b = ej[e];
+        if (a < 0 || b >= n || a >= b) continue;
+        const int32_t pa = rowptr[a] + atomicAdd(&cursor[a], 1);
+        col_tmp[pa] = b;
+        eid_tmp[pa] = (int32_t)e;
+        const int32_t pb = rowptr[b] + atomicAdd(&cursor[b], 1);
+        col_tmp[pb] = a;
+        eid_tmp[pb] = (int32_t)e;
+    }
+}
+
+// One warp per row: each entry's final slot is the number of row entries with a smaller
+// column (deterministic, whatever order the atomics filled the row in). Equal columns
+// mean a repeated edge.
+__global__ void k_sort_rows(int32_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col_tmp,
+                            const int32_t* __restrict__ eid_tmp, int32_t* col, int32_t* eid, int32_t* status)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t row = warp; row < n; row += nwarps) {
+        const int32_t p0 = rowptr[row], p1 = rowptr[row + 1];
+        for (int32_t p = p0 + lane; p < p1; p += 32) {
+            const int32_t c = col_tmp[p];
+            int32_t rank = 0;
+            bool dup = false;
+            for (int32_t q = p0; q < p1; ++q) {
+                const int32_t cq = col_tmp[q];
+                rank += (cq < c);
+                dup |= (cq == c) && (q != p);
+            }
+            col[p0 + rank] = c;
+            eid[p0 + rank] = eid_tmp[p];
+            if (dup) atomicOr(status, kStatusDuplicateEdge);
+        }
+    }
+}
+
+__global__ void k_entry_weights(int32_t K, int64_t nnz, int64_t E, const int32_t* __restrict__ eid,
+                                const int32_t* __restrict__ w, int32_t* wn)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e = eid[p];
+        for (int k = 0; k < K; ++k) wn[k * nnz + p] = w[k * E + e];
+    }
+}
+
+__global__ void k_row_sums(int32_t n, int32_t K, int64_t nnz, const int32_t* __restrict__ rowptr,
+                           const int32_t* __restrict__ wn, int64_t* rowsum, int32_t* maxdeg)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p0 = rowptr[i], p1 = rowptr[i + 1];
+        for (int k = 0; k < K; ++k) {
+            int64_t s = 0;
+            for (int32_t p = p0; p < p1; ++p) s += wn[k * nnz + p];
+            rowsum[i * K + k] = s;
+        }
+        atomicMax(maxdeg, p1 - p0);
+    }
+}
+
+// sums[0..K): sum J, sums[K..2K): sum |J|, sums[2K..3K): sum min(0, J). Two's complement
+// addition of the unsigned atomics gives the exact signed sums.
+__global__ void k_weight_sums(int32_t K, int64_t E, const int32_t* __restrict__ w, unsigned long long* sums)
+{
+    int64_t s[kMaxK], a[kMaxK], m[kMaxK];
+    for (int k = 0; k < K; ++k) s[k] = a[k] = m[k] = 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        for (int k = 0; k < K; ++k) {
+            const int64_t v = w[k * E + e];
+            s[k] += v;
+            a[k] += v < 0 ? -v : v;
+            m[k] += v < 0 ? v : 0;
+        }
+    }
+    for (int k = 0; k < K; ++k) {
+        atomicAdd(&sums[k], (unsigned long long)s[k]);
+        atomicAdd(&sums[K + k], (unsigned long long)a[k]);
+        atomicAdd(&sums[2 * K + k], (unsigned long long)m[k]);
+    }
+}
+
+void free_instance(moq_instance* h)
+{
+    if (!h) return;
+    cudaFree(h->ei);
+    cudaFree(h->ej);
+    cudaFree(h->w);
+    cudaFree(h->rowptr);
+    cudaFree(h->col);
+    cudaFree(h->wn);
+    cudaFree(h->rowsum);
+    delete h;
+}
+
+template <class T>
+int dalloc(T** p, int64_t count)
+{
+    *p = nullptr;
+    if (count <= 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (size_t)count);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(e, "cudaMalloc");
+    }
+    return MOQ_OK;
+}
+
+}  // namespace
+}  // namespace moq
+
+extern "C" {
+
+int moq_create_instance(int32_t n, int32_t K, int64_t E, const int32_t* ei, const int32_t* ej, const int32_t* w,
+                        void* stream, moq_instance** out)
+{
+    using namespace moq;
+    if (!out) return fail(MOQ_ERR_ARG, "moq_create_instance: out is NULL");
+    *out = nullptr;
+    if (n < 2 || n > (1 << 24)) return fail(MOQ_ERR_ARG, "moq_create_instance: n=%d outside [2, 2^24]", n);
+    if (K < 2 || K > kMaxK) return fail(MOQ_ERR_ARG, "moq_create_instance: K=%d outside [2, %d]", K, kMaxK);
+    if (E < 0 || E >= ((int64_t)1 << 30)) return fail(MOQ_ERR_ARG, "moq_create_instance: E=%lld outside [0, 2^30)", (long long)E);
+    if (E > 0 && (!ei || !ej || !w)) return fail(MOQ_ERR_ARG, "moq_create_instance: NULL edge or weight array");
+    cudaStream_t st = as_stream(stream);
+
+    moq_instance* h = new moq_instance();
+    h->n = n;
+    h->K = K;
+    h->E = E;
+    h->nnz = 2 * E;
+    h->words = (n + 63) / 64;
+    cudaGetDevice(&h->device);
+
+    int32_t *deg = nullptr, *cursor = nullptr, *col_tmp = nullptr, *eid_tmp = nullptr, *eid = nullptr, *status = nullptr;
+    unsigned long long* sums = nullptr;
+    int rc = MOQ_OK;
+    auto cleanup_tmp = [&]() {
+        cudaFree(deg); cudaFree(cursor); cudaFree(col_tmp); cudaFree(eid_tmp); cudaFree(eid); cudaFree(status); cudaFree(sums);
+    };
+#define MOQ_STEP(x) do { rc = (x); if (rc != MOQ_OK) { cleanup_tmp(); free_instance(h); return rc; } } while (0)
+    MOQ_STEP(dalloc(&h->ei, E));
+    MOQ_STEP(dalloc(&h->ej, E));
+    MOQ_STEP(dalloc(&h->w, K * E));
+    MOQ_STEP(dalloc(&h->rowptr, n + 1));
+    MOQ_STEP(dalloc(&h->col, h->nnz));
+    MOQ_STEP(dalloc(&h->wn, K * h->nnz));
+    MOQ_STEP(dalloc(&h->rowsum, (int64_t)n * K));
+    MOQ_STEP(dalloc(&deg, n + 1));
+    MOQ_STEP(dalloc(&cursor, n));
+    MOQ_STEP(dalloc(&col_tmp, h->nnz));
+    MOQ_STEP(dalloc(&eid_tmp, h->nnz));
+    MOQ_STEP(dalloc(&eid, h->nnz));
+    MOQ_STEP(dalloc(&status, 2));
+    MOQ_STEP(dalloc(&sums, 3 * K));
+
+    auto cu = [&](cudaError_t e, const char* what) { return e == cudaSuccess ? MOQ_OK : cuda_fail(e, what); };
+    if (E > 0) {
+        MOQ_STEP(cu(cudaMemcpyAsync(h->ei, ei, sizeof(int32_t) * E, cudaMemcpyHostToDevice, st), "copy ei"));
+        MOQ_STEP(cu(cudaMemcpyAsync(h->ej, ej, sizeof(int32_t) * E, cudaMemcpyHostToDevice, st), "copy ej"));
+        MOQ_STEP(cu(cudaMemcpyAsync(h->w, w, sizeof(int32_t) * K * E, cudaMemcpyHostToDevice, st), "copy w"));
+    }
+    MOQ_STEP(cu(cudaMemsetAsync(deg, 0, sizeof(int32_t) * (n + 1), st), "memset"));
+    MOQ_STEP(cu(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * n, st), "memset"));
+    MOQ_STEP(cu(cudaMemsetAsync(status, 0, sizeof(int32_t) * 2, st), "memset"));
+    MOQ_STEP(cu(cudaMemsetAsync(sums, 0, sizeof(unsigned long long) * 3 * K, st), "memset"));
+
+    const int tb = 256;
+    const int gE = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(E, tb), 148 * 16));
+    const int gN = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, tb), 148 * 16));
+    const int gNNZ = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(h->nnz, tb), 148 * 16));
+    k_degree<<<gE, tb, 0, st>>>(h->ei, h->ej, E, n, deg, status);
+    k_scan_rowptr<<<1, 1024, 0, st>>>(deg, n, h->rowptr);
+    k_fill<<<gE, tb, 0, st>>>(h->ei, h->ej, E, n, h->rowptr, cursor, col_tmp, eid_tmp);
+    const int gRows = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)n * 32, tb), 148 * 16));
+    k_sort_rows<<<gRows, tb, 0, st>>>(n, h->rowptr, col_tmp, eid_tmp, h->col, eid, status);
+    k_entry_weights<<<gNNZ, tb, 0, st>>>(K, h->nnz, E, eid, h->w, h->wn);
+    k_row_sums<<<gN, tb, 0, st>>>(n, K, h->nnz, h->rowptr, h->wn, h->rowsum, status + 1);
+    k_weight_sums<<<gE, tb, 0, st>>>(K, E, h->w, sums);
+    {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) MOQ_STEP(cuda_fail(e, "instance build launch"));
+    }
+    int32_t hstatus[2] = {0, 0};
+    long long hsums[3 * kMaxK];
+    MOQ_STEP(cu(cudaMemcpyAsync(hstatus, status, sizeof(hstatus), cudaMemcpyDeviceToHost, st), "read status"));
+    MOQ_STEP(cu(cudaMemcpyAsync(hsums, sums, sizeof(long long) * 3 * K, cudaMemcpyDeviceToHost, st), "read sums"));
+    MOQ_STEP(cu(cudaStreamSynchronize(st), "instance build"));
+    if (hstatus[0] & kStatusBadEdge) MOQ_STEP(fail(MOQ_ERR_ARG, "moq_create_instance: an edge has i >= j or an endpoint outside [0, n)"));
+    if (hstatus[0] & kStatusDuplicateEdge) MOQ_STEP(fail(MOQ_ERR_ARG, "moq_create_instance: repeated edge"));
+    cleanup_tmp();
+#undef MOQ_STEP
+    h->max_degree = hstatus[1];
+    moq_instance_info& inf = h->info;
+    memset(&inf, 0, sizeof(inf));
+    inf.n = n;
+    inf.K = K;
+    inf.E = E;
+    inf.max_degree = h->max_degree;
+    inf.words = h->words;
+    for (int k = 0; k < K; ++k) {
+        inf.weight_sum[k] = hsums[k];
+        inf.abs_sum[k] = hsums[K + k];
+        inf.ref_point[k] = hsums[2 * K + k];
+    }
+    *out = h;
+    return MOQ_OK;
+}
+
+void moq_destroy_instance(moq_instance* inst) { moq::free_instance(inst); }
+
+int moq_instance_get_info(const moq_instance* inst, moq_instance_info* out)
+{
+    if (!inst || !out) return moq::fail(MOQ_ERR_ARG, "moq_instance_get_info: NULL argument");
+    *out = inst->info;
+    return MOQ_OK;
+}
+
+}  // extern "C"

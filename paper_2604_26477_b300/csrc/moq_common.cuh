@@ -1,0 +1,121 @@
+// Internal definitions shared by the library's translation units (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "moqaia.h"
+
+namespace moq {
+
+constexpr int kMaxK = 8;
+
+// ---- error plumbing ----------------------------------------------------------------
+// Records a per-thread message and returns `code`, so call sites read
+// `return fail(MOQ_ERR_ARG, "...")`.
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t err, const char* what);
+
+#define MOQ_CUDA_TRY(expr)                                 \
+    do {                                                   \
+        cudaError_t _e = (expr);                           \
+        if (_e != cudaSuccess) return ::moq::cuda_fail(_e, #expr); \
+    } while (0)
+
+#define MOQ_LAUNCH_CHECK(what)                             \
+    do {                                                   \
+        cudaError_t _e = cudaGetLastError();               \
+        if (_e != cudaSuccess) return ::moq::cuda_fail(_e, what); \
+    } while (0)
+
+inline cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Device status bits latched by kernels and read back by synchronising calls.
+enum : int32_t {
+    kStatusDuplicateEdge = 1,
+    kStatusBadEdge = 2,
+    kStatusCapacity = 4,
+    kStatusOverflow = 8,
+};
+
+// ---- counter-based RNG --------------------------------------------------------------
+// Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11): per round the two
+// products M0*c0 and M1*c2 are split into high and low halves; the high halves are
+// XORed with the other two counter words and the key, the words are permuted, and the
+// key advances by the Weyl increments before every round after the first.
+struct Philox4x32 {
+    static constexpr uint32_t kM0 = 0xD2511F53u, kM1 = 0xCD9E8D57u;
+    static constexpr uint32_t kW0 = 0x9E3779B9u, kW1 = 0xBB67AE85u;
+
+    __device__ __forceinline__ static uint4 block(uint4 c, uint32_t k0, uint32_t k1)
+    {
+#pragma unroll
+        for (int rnd = 0; rnd < 10; ++rnd) {
+            const uint32_t lo0 = kM0 * c.x, hi0 = __umulhi(kM0, c.x);
+            const uint32_t lo1 = kM1 * c.z, hi1 = __umulhi(kM1, c.z);
+            c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+            k0 += kW0;
+            k1 += kW1;
+        }
+        return c;
+    }
+};
+
+// Uniform in [-1, 1): (word >> 8 - 2^23) * 2^-23, exact in float.
+__device__ __forceinline__ float signed_unit(uint32_t word)
+{
+    return (float)((int32_t)(word >> 8) - 8388608) * 0x1p-23f;
+}
+
+// Two standard normals from two 32-bit words by Box-Muller: u1 in (0,1], u2 in [0,1),
+// rho = sqrt(-2 ln u1), theta = 2 pi u2 -> (rho cos theta, rho sin theta). The angle is
+// evaluated as 2 pi (u2 - 1/2) + pi so the fast sine/cosine see [-pi, pi).
+__device__ __forceinline__ float2 box_muller(uint32_t w_a, uint32_t w_b)
+{
+    const float u1 = (float)((w_a >> 8) + 1u) * 0x1p-24f;
+    const float u2c = (float)(w_b >> 8) * 0x1p-24f - 0.5f;
+    const float rho = sqrtf(-2.0f * __logf(u1));
+    float s, c;
+    __sincosf(6.2831853071795864f * u2c, &s, &c);
+    return make_float2(-rho * c, -rho * s);
+}
+
+}  // namespace moq
+
+// ---- handles ---------------------------------------------------------------------------
+struct moq_instance {
+    int32_t n = 0, K = 0;
+    int64_t E = 0;
+    int64_t nnz = 0;
+    int32_t max_degree = 0;
+    int32_t words = 0;
+    int device = 0;
+    int32_t* ei = nullptr;      // E
+    int32_t* ej = nullptr;      // E
+    int32_t* w = nullptr;       // K x E (objective-major)
+    int32_t* rowptr = nullptr;  // n + 1
+    int32_t* col = nullptr;     // nnz, rows sorted by column
+    int32_t* wn = nullptr;      // K x nnz weights of the CSR entries (objective-major)
+    int64_t* rowsum = nullptr;  // n x K integer row sums sum_j J^(k)_ij
+    moq_instance_info info{};
+};
+
+struct moq_archive {
+    int32_t n = 0, K = 0, W = 0;
+    int64_t cap = 0, max_batch = 0;
+    int device = 0;
+    int cur = 0;                   // which of the double buffers holds the archive
+    int64_t* cuts[2] = {nullptr, nullptr};   // cap x K
+    uint64_t* bits[2] = {nullptr, nullptr};  // cap x W
+    int64_t* index[2] = {nullptr, nullptr};  // cap
+    int64_t* d_count = nullptr;    // archive size (device)
+    int32_t* d_status = nullptr;   // latched status bits (device)
+    int32_t* flag_arch = nullptr;  // cap
+    int32_t* flag_cand = nullptr;  // max_batch
+    int64_t* blocksum = nullptr;   // scan partials
+    int64_t n_blocksum = 0;
+    void* hv_ws = nullptr;         // hypervolume workspace sized for cap
+    int64_t* h_pinned = nullptr;   // pinned host words for read-backs
+};

@@ -1,0 +1,486 @@
+// a7: deduplication + Pareto filter merged into a device archive ("Pareto filtering").
+//
+// Maximisation order: u dominates v iff u_k >= v_k for all k and u_j > v_j for some j.
+// The archive A holds the distinct non-dominated vectors of every earlier call, each with
+// its lowest global sample index. For a batch X of M candidates:
+//  - candidate u survives iff no member of A weakly dominates it (>= everywhere: either
+//    it dominates u or equals u and has a lower index), no candidate dominates it, and no
+//    equal candidate has a lower index;
+//  - member a survives iff no candidate dominates it (a dominated member is dominated by
+//    some surviving vector too, since domination is transitive and the sets are finite).
+// Both tests are all-pairs over shared-memory tiles with a block-wide early exit once
+// every thread's vector is known to be dominated. Survivors are compacted in order --
+// old members first, then candidates by index -- into the second buffer of the archive
+// by a block scan, so the result is deterministic. Candidate representatives are
+// canonicalised to s_0 = +1 (C(s) = C(-s)).
+#include <algorithm>
+
+#include "moq_common.cuh"
+
+namespace moq {
+namespace {
+
+constexpr int kTile = 256;
+constexpr int kScanBlock = 1024;
+constexpr unsigned kFull = 0xffffffffu;
+
+template <int KT>
+__global__ void __launch_bounds__(kTile) k_filter_candidates(const int64_t* __restrict__ arch, const int64_t* __restrict__ d_count,
+                                                             const int64_t* __restrict__ cand, int64_t M, int32_t* flag_cand)
+{
+    __shared__ int64_t tile[kTile][KT];
+    const int tid = threadIdx.x;
+    const int64_t c = blockIdx.x * (int64_t)kTile + tid;
+    const bool act = c < M;
+    int64_t u[KT];
+#pragma unroll
+    for (int k = 0; k < KT; ++k) u[k] = act ? cand[c * KT + k] : 0;
+    bool dropped = !act;
+    const int64_t F = *d_count;
+
+    for (int64_t base = 0; base < F; base += kTile) {
+        if (__syncthreads_and(dropped)) break;
+        const int cnt = (int)min((int64_t)kTile, F - base);
+        if (tid < cnt) {
+#pragma unroll
+            for (int k = 0; k < KT; ++k) tile[tid][k] = arch[(base + tid) * KT + k];
+        }
+        __syncthreads();
+        if (!dropped) {
+            for (int t = 0; t < cnt; ++t) {
+                bool ge = true;
+#pragma unroll
+                for (int k = 0; k < KT; ++k) ge &= tile[t][k] >= u[k];
+                if (ge) {
+                    dropped = true;
+                    break;
+                }
+            }
+        }
+    }
+    for (int64_t base = 0; base < M; base += kTile) {
+        if (__syncthreads_and(dropped)) break;
+        const int cnt = (int)min((int64_t)kTile, M - base);
+        if (tid < cnt) {
+#pragma unroll
+            for (int k = 0; k < KT; ++k) tile[tid][k] = cand[(base + tid) * KT + k];
+        }
+        __syncthreads();
+        if (!dropped) {
+            for (int t = 0; t < cnt; ++t) {
+                bool ge = true, gt = false;
+#pragma unroll
+                for (int k = 0; k < KT; ++k) {
+                    ge &= tile[t][k] >= u[k];
+                    gt |= tile[t][k] > u[k];
+                }
+                if (ge && (gt || base + t < c)) {
+                    dropped = true;
+                    break;
+                }
+            }
+        }
+    }
+    if (act) flag_cand[c] = dropped ? 0 : 1;
+}
+
+template <int KT>
+__global__ void __launch_bounds__(kTile) k_filter_archive(const int64_t* __restrict__ arch, const int64_t* __restrict__ d_count,
+                                                          const int64_t* __restrict__ cand, int64_t M, int32_t* flag_arch)
+{
+    __shared__ int64_t tile[kTile][KT];
+    const int tid = threadIdx.x;
+    const int64_t F = *d_count;
+    for (int64_t blk = blockIdx.x; blk * kTile < F; blk += gridDim.x) {
+        const int64_t a = blk * kTile + tid;
+        const bool act = a < F;
+        int64_t u[KT];
+#pragma unroll
+        for (int k = 0; k < KT; ++k) u[k] = act ? arch[a * KT + k] : 0;
+        bool dropped = !act;
+        for (int64_t base = 0; base < M; base += kTile) {
+            if (__syncthreads_and(dropped)) break;
+            const int cnt = (int)min((int64_t)kTile, M - base);
+            if (tid < cnt) {
+#pragma unroll
+                for (int k = 0; k < KT; ++k) tile[tid][k] = cand[(base + tid) * KT + k];
+            }
+            __syncthreads();
+            if (!dropped) {
+                for (int t = 0; t < cnt; ++t) {
+                    bool ge = true, gt = false;
+#pragma unroll
+                    for (int k = 0; k < KT; ++k) {
+                        ge &= tile[t][k] >= u[k];
+                        gt |= tile[t][k] > u[k];
+                    }
+                    if (ge && gt) {
+                        dropped = true;
+                        break;
+                    }
+                }
+            }
+        }
+        if (act) flag_arch[a] = dropped ? 0 : 1;
+        __syncthreads();
+    }
+}
+
+// Flag of virtual position b*1024+t: blocks [0, nbA) cover archive slots, blocks
+// [nbA, nbA+nbC) cover candidates.
+__device__ __forceinline__ int32_t flag_at(int64_t b, int t, int64_t nbA, int64_t F, int64_t M,
+                                           const int32_t* flag_arch, const int32_t* flag_cand)
+{
+    if (b < nbA) {
+        const int64_t q = b * kScanBlock + t;
+        return q < F ? flag_arch[q] : 0;
+    }
+    const int64_t c = (b - nbA) * kScanBlock + t;
+    return c < M ? flag_cand[c] : 0;
+}
+
+__device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t* warp_sums, int32_t* total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_sums[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int32_t s = warp_sums[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t t = __shfl_up_sync(kFull, s, o);
+            if (lane >= o) s += t;
+        }
+        warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const int32_t res = incl - v + (wid > 0 ? warp_sums[wid - 1] : 0);
+    *total = warp_sums[31];
+    return res;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_count_flags(int64_t nbA, int64_t M, const int64_t* __restrict__ d_count,
+                                                           const int32_t* __restrict__ flag_arch, const int32_t* __restrict__ flag_cand,
+                                                           int64_t* blocksum)
+{
+    __shared__ int32_t warp_sums[32];
+    const int64_t F = *d_count;
+    const int64_t b = blockIdx.x;
+    if (b < nbA && b * kScanBlock >= F) {
+        if (threadIdx.x == 0) blocksum[b] = 0;
+        return;
+    }
+    const int32_t v = flag_at(b, threadIdx.x, nbA, F, M, flag_arch, flag_cand);
+    int32_t total;
+    block_excl_scan(v, warp_sums, &total);
+    if (threadIdx.x == 0) blocksum[b] = total;
+}
+
+// Exclusive scan of nb block sums in place; blocksum[nb] receives the total.
+__global__ void __launch_bounds__(kScanBlock) k_scan_blocksums(int64_t nb, int64_t* blocksum)
+{
+    __shared__ int64_t warp_sums[32];
+    __shared__ int64_t carry;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < nb; base += kScanBlock) {
+        const int64_t i = base + threadIdx.x;
+        const int64_t v = i < nb ? blocksum[i] : 0;
+        int64_t incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) warp_sums[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            int64_t s = warp_sums[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t t = __shfl_up_sync(kFull, s, o);
+                if (lane >= o) s += t;
+            }
+            warp_sums[lane] = s;
+        }
+        __syncthreads();
+        const int64_t excl = incl - v + (wid > 0 ? warp_sums[wid - 1] : 0) + carry;
+        if (i < nb) blocksum[i] = excl;
+        __syncthreads();
+        if (threadIdx.x == kScanBlock - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) blocksum[nb] = carry;
+}
+
+struct ScatterArgs {
+    int32_t K, W, n;
+    int64_t cap, nbA, M, index_base;
+    const int64_t* d_count;
+    const int32_t* flag_arch;
+    const int32_t* flag_cand;
+    const int64_t* blockoff;  // nb + 1
+    int64_t nb;
+    const int64_t* old_cuts;
+    const uint64_t* old_bits;
+    const int64_t* old_index;
+    const int64_t* cand_cuts;
+    const uint64_t* cand_bits;
+    int64_t* new_cuts;
+    uint64_t* new_bits;
+    int64_t* new_index;
+    int32_t* status;
+};
+
+__global__ void __launch_bounds__(kScanBlock) k_scatter(const ScatterArgs s)
+{
+    __shared__ int32_t warp_sums[32];
+    const int64_t F = *s.d_count;
+    const int64_t b = blockIdx.x;
+    const int64_t total = s.blockoff[s.nb];
+    const bool overflow = total > s.cap;
+    if (b < s.nbA && b * kScanBlock >= F) return;  // empty archive slots
+    if (overflow) {
+        // keep the archive as it was: copy members to the same slots
+        if (b >= s.nbA) return;
+        const int64_t q = b * kScanBlock + threadIdx.x;
+        if (q < F) {
+            for (int k = 0; k < s.K; ++k) s.new_cuts[q * s.K + k] = s.old_cuts[q * s.K + k];
+            for (int w = 0; w < s.W; ++w) s.new_bits[q * s.W + w] = s.old_bits[q * s.W + w];
+            s.new_index[q] = s.old_index[q];
+        }
+        if (b == 0 && threadIdx.x == 0) atomicOr(s.status, kStatusCapacity);
+        return;
+    }
+    const int32_t v = flag_at(b, threadIdx.x, s.nbA, F, s.M, s.flag_arch, s.flag_cand);
+    int32_t tot;
+    const int32_t local = block_excl_scan(v, warp_sums, &tot);
+    if (!v) return;
+    const int64_t pos = s.blockoff[b] + local;
+    if (b < s.nbA) {
+        const int64_t q = b * kScanBlock + threadIdx.x;
+        for (int k = 0; k < s.K; ++k) s.new_cuts[pos * s.K + k] = s.old_cuts[q * s.K + k];
+        for (int w = 0; w < s.W; ++w) s.new_bits[pos * s.W + w] = s.old_bits[q * s.W + w];
+        s.new_index[pos] = s.old_index[q];
+    } else {
+        const int64_t c = (b - s.nbA) * kScanBlock + threadIdx.x;
+        for (int k = 0; k < s.K; ++k) s.new_cuts[pos * s.K + k] = s.cand_cuts[c * s.K + k];
+        const bool flip = s.cand_bits[c * s.W] & 1ull;  // s_0 = -1 -> store -s
+        for (int w = 0; w < s.W; ++w) {
+            uint64_t word = s.cand_bits[c * s.W + w];
+            if (flip) {
+                const int lo = w * 64;
+                const int nbits = min(64, s.n - lo);
+                const uint64_t mask = nbits >= 64 ? ~0ull : ((1ull << nbits) - 1ull);
+                word ^= mask;
+            }
+            s.new_bits[pos * s.W + w] = word;
+        }
+        s.new_index[pos] = s.index_base + c;
+    }
+}
+
+__global__ void k_set_count(int64_t cap, int64_t nb, const int64_t* blockoff, int64_t* d_count)
+{
+    const int64_t total = blockoff[nb];
+    if (total <= cap) *d_count = total;
+}
+
+template <int KT>
+cudaError_t launch_filters(moq_archive* a, const int64_t* cuts, int64_t M, cudaStream_t st)
+{
+    if (M > 0)
+        k_filter_candidates<KT><<<(unsigned)ceil_div(M, kTile), kTile, 0, st>>>(a->cuts[a->cur], a->d_count, cuts, M, a->flag_cand);
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(a->cap, kTile), 148 * 8));
+    k_filter_archive<KT><<<g, kTile, 0, st>>>(a->cuts[a->cur], a->d_count, cuts, M, a->flag_arch);
+    return cudaGetLastError();
+}
+
+int read_status(const moq_archive* a, cudaStream_t st, int64_t* size_out)
+{
+    MOQ_CUDA_TRY(cudaMemcpyAsync(a->h_pinned, a->d_count, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    MOQ_CUDA_TRY(cudaMemcpyAsync(a->h_pinned + 1, a->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MOQ_CUDA_TRY(cudaStreamSynchronize(st));
+    if (size_out) *size_out = a->h_pinned[0];
+    const int32_t status = (int32_t)a->h_pinned[1];
+    if (status & kStatusCapacity) {
+        MOQ_CUDA_TRY(cudaMemsetAsync(a->d_status, 0, sizeof(int32_t), st));
+        return fail(MOQ_ERR_CAPACITY, "archive capacity %lld exceeded; the archive was left unchanged", (long long)a->cap);
+    }
+    return MOQ_OK;
+}
+
+}  // namespace
+
+void free_archive(moq_archive* a)
+{
+    if (!a) return;
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(a->cuts[b]);
+        cudaFree(a->bits[b]);
+        cudaFree(a->index[b]);
+    }
+    cudaFree(a->d_count);
+    cudaFree(a->d_status);
+    cudaFree(a->flag_arch);
+    cudaFree(a->flag_cand);
+    cudaFree(a->blocksum);
+    cudaFree(a->hv_ws);
+    if (a->h_pinned) cudaFreeHost(a->h_pinned);
+    delete a;
+}
+
+}  // namespace moq
+
+extern "C" {
+
+int moq_archive_create(int32_t n, int32_t K, int64_t capacity, int64_t max_batch, moq_archive** out)
+{
+    using namespace moq;
+    if (!out) return fail(MOQ_ERR_ARG, "moq_archive_create: out is NULL");
+    *out = nullptr;
+    if (n < 2 || n > (1 << 24) || K < 2 || K > kMaxK) return fail(MOQ_ERR_ARG, "moq_archive_create: bad n=%d or K=%d", n, K);
+    if (capacity < 1 || capacity > ((int64_t)1 << 30) || max_batch < 1 || max_batch > ((int64_t)1 << 30))
+        return fail(MOQ_ERR_ARG, "moq_archive_create: capacity and max_batch must be in [1, 2^30]");
+    moq_archive* a = new moq_archive();
+    a->n = n;
+    a->K = K;
+    a->W = (n + 63) / 64;
+    a->cap = capacity;
+    a->max_batch = max_batch;
+    cudaGetDevice(&a->device);
+    a->n_blocksum = ceil_div(capacity, kScanBlock) + ceil_div(max_batch, kScanBlock) + 1;
+    cudaError_t e = cudaSuccess;
+    auto al = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
+    for (int b = 0; b < 2; ++b) {
+        al((void**)&a->cuts[b], sizeof(int64_t) * capacity * K);
+        al((void**)&a->bits[b], sizeof(uint64_t) * capacity * a->W);
+        al((void**)&a->index[b], sizeof(int64_t) * capacity);
+    }
+    al((void**)&a->d_count, sizeof(int64_t));
+    al((void**)&a->d_status, sizeof(int32_t));
+    al((void**)&a->flag_arch, sizeof(int32_t) * capacity);
+    al((void**)&a->flag_cand, sizeof(int32_t) * max_batch);
+    al((void**)&a->blocksum, sizeof(int64_t) * a->n_blocksum);
+    al(&a->hv_ws, (size_t)moq_hypervolume_workspace_size(capacity, K));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&a->h_pinned, 64);
+    if (e == cudaSuccess) e = cudaMemset(a->d_count, 0, sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMemset(a->d_status, 0, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        free_archive(a);
+        return cuda_fail(e, "moq_archive_create");
+    }
+    *out = a;
+    return MOQ_OK;
+}
+
+void moq_archive_destroy(moq_archive* a) { moq::free_archive(a); }
+
+int moq_archive_reset(moq_archive* a, void* stream)
+{
+    using namespace moq;
+    if (!a) return fail(MOQ_ERR_ARG, "moq_archive_reset: NULL archive");
+    MOQ_CUDA_TRY(cudaMemsetAsync(a->d_count, 0, sizeof(int64_t), as_stream(stream)));
+    MOQ_CUDA_TRY(cudaMemsetAsync(a->d_status, 0, sizeof(int32_t), as_stream(stream)));
+    return MOQ_OK;
+}
+
+int moq_pareto_front(moq_archive* a, const int64_t* cuts, const uint64_t* bits, int64_t M, int64_t index_base,
+                     int64_t* front_size_out, void* stream)
+{
+    using namespace moq;
+    if (!a) return fail(MOQ_ERR_ARG, "moq_pareto_front: NULL archive");
+    if (M < 0 || M > a->max_batch) return fail(MOQ_ERR_ARG, "moq_pareto_front: M=%lld outside [0, max_batch=%lld]", (long long)M, (long long)a->max_batch);
+    if (M > 0 && (!cuts || !bits)) return fail(MOQ_ERR_ARG, "moq_pareto_front: NULL cuts or bits");
+    cudaStream_t st = as_stream(stream);
+    cudaError_t e;
+    switch (a->K) {
+    case 2: e = launch_filters<2>(a, cuts, M, st); break;
+    case 3: e = launch_filters<3>(a, cuts, M, st); break;
+    case 4: e = launch_filters<4>(a, cuts, M, st); break;
+    case 5: e = launch_filters<5>(a, cuts, M, st); break;
+    case 6: e = launch_filters<6>(a, cuts, M, st); break;
+    case 7: e = launch_filters<7>(a, cuts, M, st); break;
+    default: e = launch_filters<8>(a, cuts, M, st); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "moq_pareto_front filter launch");
+    const int64_t nbA = ceil_div(a->cap, kScanBlock), nbC = ceil_div(M, kScanBlock), nb = nbA + nbC;
+    k_count_flags<<<(unsigned)nb, kScanBlock, 0, st>>>(nbA, M, a->d_count, a->flag_arch, a->flag_cand, a->blocksum);
+    k_scan_blocksums<<<1, kScanBlock, 0, st>>>(nb, a->blocksum);
+    ScatterArgs s{};
+    s.K = a->K;
+    s.W = a->W;
+    s.n = a->n;
+    s.cap = a->cap;
+    s.nbA = nbA;
+    s.M = M;
+    s.index_base = index_base;
+    s.d_count = a->d_count;
+    s.flag_arch = a->flag_arch;
+    s.flag_cand = a->flag_cand;
+    s.blockoff = a->blocksum;
+    s.nb = nb;
+    s.old_cuts = a->cuts[a->cur];
+    s.old_bits = a->bits[a->cur];
+    s.old_index = a->index[a->cur];
+    s.cand_cuts = cuts;
+    s.cand_bits = bits;
+    s.new_cuts = a->cuts[1 - a->cur];
+    s.new_bits = a->bits[1 - a->cur];
+    s.new_index = a->index[1 - a->cur];
+    s.status = a->d_status;
+    k_scatter<<<(unsigned)nb, kScanBlock, 0, st>>>(s);
+    k_set_count<<<1, 1, 0, st>>>(a->cap, nb, a->blocksum, a->d_count);
+    MOQ_LAUNCH_CHECK("moq_pareto_front launch");
+    a->cur = 1 - a->cur;
+    if (front_size_out) return read_status(a, st, front_size_out);
+    return MOQ_OK;
+}
+
+int moq_archive_size(const moq_archive* a, int64_t* size_out, void* stream)
+{
+    using namespace moq;
+    if (!a || !size_out) return fail(MOQ_ERR_ARG, "moq_archive_size: NULL argument");
+    return read_status(a, as_stream(stream), size_out);
+}
+
+int moq_archive_copy_out(const moq_archive* a, int64_t* cuts_host, uint64_t* bits_host, int64_t* index_host, int64_t cap,
+                         int64_t* n_out, void* stream)
+{
+    using namespace moq;
+    if (!a || !n_out) return fail(MOQ_ERR_ARG, "moq_archive_copy_out: NULL argument");
+    cudaStream_t st = as_stream(stream);
+    int64_t F = 0;
+    int rc = read_status(a, st, &F);
+    if (rc != MOQ_OK) return rc;
+    *n_out = F;
+    const int64_t m = std::min(F, cap);
+    if (m > 0) {
+        if (cuts_host) MOQ_CUDA_TRY(cudaMemcpyAsync(cuts_host, a->cuts[a->cur], sizeof(int64_t) * m * a->K, cudaMemcpyDeviceToHost, st));
+        if (bits_host) MOQ_CUDA_TRY(cudaMemcpyAsync(bits_host, a->bits[a->cur], sizeof(uint64_t) * m * a->W, cudaMemcpyDeviceToHost, st));
+        if (index_host) MOQ_CUDA_TRY(cudaMemcpyAsync(index_host, a->index[a->cur], sizeof(int64_t) * m, cudaMemcpyDeviceToHost, st));
+        MOQ_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return MOQ_OK;
+}
+
+int moq_archive_device_view(const moq_archive* a, const int64_t** cuts, const uint64_t** bits, const int64_t** index,
+                            const int64_t** size_dev)
+{
+    if (!a) return moq::fail(MOQ_ERR_ARG, "moq_archive_device_view: NULL archive");
+    if (cuts) *cuts = a->cuts[a->cur];
+    if (bits) *bits = a->bits[a->cur];
+    if (index) *index = a->index[a->cur];
+    if (size_dev) *size_dev = a->d_count;
+    return MOQ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,270 @@
+"""Python binding of the ``libmoqaia.so`` C ABI (``include/moqaia.h``).
+
+Argument marshalling only: every function forwards to the C entry point of the same
+name. Device buffers are torch CUDA tensors (their ``data_ptr()`` is passed), host
+buffers are numpy arrays, and ``stream`` defaults to torch's current CUDA stream.
+Failures raise ``MoqError`` carrying the library's status code and message. Importing
+this module without the built library raises ImportError: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmoqaia.so")
+
+MOQ_OK = 0
+MOQ_ERR_ARG = -1
+MOQ_ERR_OOM = -2
+MOQ_ERR_CUDA = -3
+MOQ_ERR_TIMEOUT = -4
+MOQ_ERR_CAPACITY = -5
+MOQ_ERR_OVERFLOW = -6
+MOQ_ERR_UNSUPPORTED = -7
+MOQ_DSB = 0
+MOQ_BSB = 1
+
+
+class MoqError(RuntimeError):
+    def __init__(self, code: int, where: str, message: str):
+        super().__init__(f"{where} failed with {code}: {message}")
+        self.code = code
+
+
+class moq_instance_info(C.Structure):
+    _fields_ = [("n", C.c_int32), ("K", C.c_int32), ("E", C.c_int64), ("max_degree", C.c_int32),
+                ("words", C.c_int32), ("weight_sum", C.c_int64 * 8), ("abs_sum", C.c_int64 * 8),
+                ("ref_point", C.c_int64 * 8)]
+
+
+class moq_sample_params(C.Structure):
+    _fields_ = [("variant", C.c_int32), ("steps", C.c_int32), ("dt", C.c_float), ("a0", C.c_float),
+                ("alpha", C.c_float), ("init_amp", C.c_float), ("noise_sqrt_dt", C.c_int32),
+                ("schedule", C.c_void_p), ("x_init", C.c_void_p), ("y_init", C.c_void_p),
+                ("x_out", C.c_void_p), ("y_out", C.c_void_p)]
+
+
+class moq_hv(C.Structure):
+    _fields_ = [("lo", C.c_int64), ("hi", C.c_int64), ("approx", C.c_double)]
+
+    def value(self) -> int:
+        return (int(self.hi) << 64) | (int(self.lo) & ((1 << 64) - 1))
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built; run `python paper_2604_26477_b300/build.py` (needs nvcc)")
+_lib = C.CDLL(LIB_PATH)
+
+_vp, _i32, _i64, _u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+_sigs = {
+    "moq_default_params": (None, [C.POINTER(moq_sample_params)]),
+    "moq_create_instance": (C.c_int, [_i32, _i32, _i64, _vp, _vp, _vp, _vp, C.POINTER(_vp)]),
+    "moq_destroy_instance": (None, [_vp]),
+    "moq_instance_get_info": (C.c_int, [_vp, C.POINTER(moq_instance_info)]),
+    "moq_sample": (C.c_int, [_vp, _vp, _i32, C.POINTER(moq_sample_params), _u64, _u64, _vp, _vp]),
+    "moq_evaluate_cuts": (C.c_int, [_vp, _vp, _i64, _vp, _vp]),
+    "moq_archive_create": (C.c_int, [_i32, _i32, _i64, _i64, C.POINTER(_vp)]),
+    "moq_archive_destroy": (None, [_vp]),
+    "moq_archive_reset": (C.c_int, [_vp, _vp]),
+    "moq_pareto_front": (C.c_int, [_vp, _vp, _vp, _i64, _i64, C.POINTER(_i64), _vp]),
+    "moq_archive_size": (C.c_int, [_vp, C.POINTER(_i64), _vp]),
+    "moq_archive_copy_out": (C.c_int, [_vp, _vp, _vp, _vp, _i64, C.POINTER(_i64), _vp]),
+    "moq_archive_device_view": (C.c_int, [_vp, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp)]),
+    "moq_hypervolume": (C.c_int, [_vp, _vp, C.POINTER(moq_hv), _vp]),
+    "moq_hypervolume_workspace_size": (_i64, [_i64, _i32]),
+    "moq_hypervolume_points": (C.c_int, [_vp, _i64, _i32, _vp, _vp, C.POINTER(moq_hv), _vp]),
+    "moq_lambda_das_dennis": (C.c_int, [_i32, _i32, _i32, _vp, _i64, C.POINTER(_i64), _vp]),
+    "moq_lambda_dirichlet": (C.c_int, [_i32, _i32, _u64, _u64, _vp, _vp]),
+    "moq_strerror": (C.c_char_p, [C.c_int]),
+    "moq_last_error_message": (C.c_char_p, []),
+}
+for _name, (_res, _args) in _sigs.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_sigs)
+
+
+def _check(rc: int, where: str):
+    if rc != MOQ_OK:
+        raise MoqError(rc, where, _lib.moq_last_error_message().decode(errors="replace"))
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dptr(t, name, dtypes=None, numel=None):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not getattr(t, "is_cuda", False):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtypes is not None and t.dtype not in dtypes:
+        raise TypeError(f"{name} has dtype {t.dtype}, expected one of {dtypes}")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} has {t.numel()} elements, needs {numel}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _hptr(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(C.c_void_p)
+
+
+def _torch_types():
+    import torch
+    f32 = (torch.float32,)
+    i64 = (torch.int64,)
+    u64 = (torch.int64,) + ((torch.uint64,) if hasattr(torch, "uint64") else ())
+    return f32, i64, u64
+
+
+# ---------------------------------------------------------------------------- C ABI
+def moq_strerror(code: int) -> str:
+    return _lib.moq_strerror(code).decode()
+
+
+def moq_last_error_message() -> str:
+    return _lib.moq_last_error_message().decode(errors="replace")
+
+
+def moq_default_params(**overrides) -> moq_sample_params:
+    p = moq_sample_params()
+    _lib.moq_default_params(C.byref(p))
+    p._tensors = {}  # keeps the tensors behind the optional device pointers alive
+    for k, v in overrides.items():
+        if k == "variant" and isinstance(v, str):
+            v = {"dsb": MOQ_DSB, "bsb": MOQ_BSB}[v.lower()]
+        if k in ("schedule", "x_init", "y_init", "x_out", "y_out"):
+            p._tensors[k] = v
+            v = None if v is None else _dptr(v, k, _torch_types()[0])
+        setattr(p, k, v)
+    return p
+
+
+def moq_create_instance(n, K, E, ei, ej, w, stream=None) -> C.c_void_p:
+    ei_, pei = _hptr(ei, np.int32)
+    ej_, pej = _hptr(ej, np.int32)
+    w_, pw = _hptr(w, np.int32)
+    if ei_.size != E or ej_.size != E or w_.size != K * E:
+        raise ValueError("edge arrays must have E entries and w K*E")
+    h = C.c_void_p()
+    _check(_lib.moq_create_instance(n, K, E, pei, pej, pw, _stream(stream), C.byref(h)), "moq_create_instance")
+    return h
+
+
+def moq_destroy_instance(h):
+    _lib.moq_destroy_instance(h)
+
+
+def moq_instance_get_info(h) -> dict:
+    info = moq_instance_info()
+    _check(_lib.moq_instance_get_info(h, C.byref(info)), "moq_instance_get_info")
+    K = info.K
+    return {"n": info.n, "K": K, "E": info.E, "max_degree": info.max_degree, "words": info.words,
+            "weight_sum": list(info.weight_sum[:K]), "abs_sum": list(info.abs_sum[:K]),
+            "ref_point": list(info.ref_point[:K])}
+
+
+def moq_sample(inst, lam, R, params, seed, round_, bits, stream=None):
+    f32, _, u64 = _torch_types()
+    _check(_lib.moq_sample(inst, _dptr(lam, "lambda", f32), R, C.byref(params), seed, round_,
+                           _dptr(bits, "bits", u64), _stream(stream)), "moq_sample")
+
+
+def moq_evaluate_cuts(inst, bits, M, cuts, stream=None):
+    _, i64, u64 = _torch_types()
+    _check(_lib.moq_evaluate_cuts(inst, _dptr(bits, "bits", u64), M, _dptr(cuts, "cuts", i64), _stream(stream)),
+           "moq_evaluate_cuts")
+
+
+def moq_archive_create(n, K, capacity, max_batch) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(_lib.moq_archive_create(n, K, capacity, max_batch, C.byref(h)), "moq_archive_create")
+    return h
+
+
+def moq_archive_destroy(h):
+    _lib.moq_archive_destroy(h)
+
+
+def moq_archive_reset(a, stream=None):
+    _check(_lib.moq_archive_reset(a, _stream(stream)), "moq_archive_reset")
+
+
+def moq_pareto_front(a, cuts, bits, M, index_base, want_size=False, stream=None):
+    _, i64, u64 = _torch_types()
+    size = C.c_int64(-1)
+    _check(_lib.moq_pareto_front(a, _dptr(cuts, "cuts", i64), _dptr(bits, "bits", u64), M, index_base,
+                                 C.byref(size) if want_size else None, _stream(stream)), "moq_pareto_front")
+    return int(size.value) if want_size else None
+
+
+def moq_archive_size(a, stream=None) -> int:
+    s = C.c_int64()
+    _check(_lib.moq_archive_size(a, C.byref(s), _stream(stream)), "moq_archive_size")
+    return int(s.value)
+
+
+def moq_archive_copy_out(a, K, W, stream=None):
+    """Returns (cuts (F,K) int64, bits (F,W) uint64, index (F,) int64) as numpy arrays."""
+    F = moq_archive_size(a, stream)
+    cuts = np.zeros((max(F, 1), K), np.int64)
+    bits = np.zeros((max(F, 1), W), np.uint64)
+    idx = np.zeros(max(F, 1), np.int64)
+    n = C.c_int64()
+    _check(_lib.moq_archive_copy_out(a, cuts.ctypes.data_as(_vp), bits.ctypes.data_as(_vp), idx.ctypes.data_as(_vp),
+                                     F, C.byref(n), _stream(stream)), "moq_archive_copy_out")
+    F = int(n.value)
+    return cuts[:F], bits[:F], idx[:F]
+
+
+def moq_archive_device_view(a):
+    cuts, bits, idx, size = _vp(), _vp(), _vp(), _vp()
+    _check(_lib.moq_archive_device_view(a, C.byref(cuts), C.byref(bits), C.byref(idx), C.byref(size)),
+           "moq_archive_device_view")
+    return cuts.value, bits.value, idx.value, size.value
+
+
+def moq_hypervolume(a, ref, stream=None) -> int:
+    ref_, pref = _hptr(ref, np.int64)
+    out = moq_hv()
+    _check(_lib.moq_hypervolume(a, pref, C.byref(out), _stream(stream)), "moq_hypervolume")
+    return out.value()
+
+
+def moq_hypervolume_workspace_size(F, K) -> int:
+    return int(_lib.moq_hypervolume_workspace_size(F, K))
+
+
+def moq_hypervolume_points(pts, F, K, ref, workspace, stream=None) -> int:
+    _, i64, _ = _torch_types()
+    ref_, pref = _hptr(ref, np.int64)
+    out = moq_hv()
+    _check(_lib.moq_hypervolume_points(_dptr(pts, "pts", i64), F, K, pref, _dptr(workspace, "workspace"),
+                                       C.byref(out), _stream(stream)), "moq_hypervolume_points")
+    return out.value()
+
+
+def moq_lambda_das_dennis(K, H, interior, lam, capacity, stream=None) -> int:
+    f32, _, _ = _torch_types()
+    cnt = C.c_int64()
+    _check(_lib.moq_lambda_das_dennis(K, H, int(interior), _dptr(lam, "lambda", f32), capacity, C.byref(cnt),
+                                      _stream(stream)), "moq_lambda_das_dennis")
+    return int(cnt.value)
+
+
+def moq_lambda_dirichlet(K, R, seed, round_, lam, stream=None):
+    f32, _, _ = _torch_types()
+    _check(_lib.moq_lambda_dirichlet(K, R, seed, round_, _dptr(lam, "lambda", f32), _stream(stream)),
+           "moq_lambda_dirichlet")

@@ -1,0 +1,453 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Exact parts (instance sums, cuts, Pareto archive, hypervolume, lattice counts) must
+match bit for bit; SB forces match the double-precision oracle within the normwise
+FP32 bound |f - f64| <= 1e-5 * c0 * sum_j |J(c)_ij phi(x_j)| per spin; trajectories
+(chaotic) are compared by the distribution of final hypervolumes over 32 seeds.
+"""
+import numpy as np
+import pytest
+import torch
+from scipy import stats
+
+from conftest import golden_lines, parse_points
+from paper_2604_26477_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+FORCE_RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def M():
+    from paper_2604_26477_b300 import build
+    build.build()
+    from paper_2604_26477_b300 import moqaia
+    assert torch.cuda.is_available()
+    return moqaia
+
+
+@pytest.fixture(scope="module")
+def P(M):
+    from paper_2604_26477_b300 import pipeline
+    return pipeline
+
+
+def _dev(a, dtype):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype=dtype, device="cuda")
+
+
+def _bits_dev(bits):
+    return torch.from_numpy(np.ascontiguousarray(bits).view(np.int64)).cuda()
+
+
+def _bits_host(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+def _canonical(bits, n):
+    """Flip configurations with s_0 = -1 (C(s) = C(-s))."""
+    out = bits.copy()
+    W = out.shape[1]
+    flip = (out[:, 0] & np.uint64(1)) == 1
+    for w in range(W):
+        nb = min(64, n - 64 * w)
+        mask = np.uint64((1 << nb) - 1) if nb < 64 else np.uint64(0xFFFFFFFFFFFFFFFF)
+        out[flip, w] ^= mask
+    return out
+
+
+INSTANCES = {
+    "heavyhex_K3": lambda: wl.heavy_hex_like(1000, K=3),
+    "heavyhex_K4": lambda: wl.heavy_hex_like(1001, K=4),
+    "reg3_n150_K3": lambda: wl.random_regular(150, 7, K=3),
+    "reg3_n1024_K3": lambda: wl.random_regular(1024, 8, K=3),
+    "gnp_n40_K2": lambda: wl.random_graph(40, 0.2, 3, K=2),
+    "gnp_n70_K8": lambda: wl.random_graph(70, 0.1, 4, K=8),
+    "complete_n100_K3": lambda: wl.complete_graph(100, 5, K=3),
+}
+
+
+# ----------------------------------------------------------------------------- a1
+@pytest.mark.parametrize("name", list(INSTANCES))
+def test_instance_info(M, P, oracle, name):
+    src = INSTANCES[name]()
+    inst = P.Instance(src)
+    info = inst.info
+    w = src.w.astype(np.int64)
+    deg = np.bincount(np.concatenate([src.ei, src.ej]), minlength=src.n)
+    assert info["n"] == src.n and info["K"] == src.K and info["E"] == src.E and info["words"] == (src.n + 63) // 64
+    assert info["max_degree"] == deg.max()
+    assert info["weight_sum"] == list(w.sum(axis=1))
+    assert info["abs_sum"] == list(np.abs(w).sum(axis=1))
+    assert info["ref_point"] == list(oracle.reference_point(src))
+
+
+def test_instance_rejects_bad_input(M):
+    ei = np.array([0, 1], np.int32)
+    with pytest.raises(M.MoqError) as e:
+        M.moq_create_instance(4, 2, 2, ei, np.array([1, 1], np.int32), np.ones(4, np.int32))  # 1 >= 1
+    assert e.value.code == M.MOQ_ERR_ARG
+    with pytest.raises(M.MoqError) as e:
+        M.moq_create_instance(4, 2, 2, ei, np.array([2, 4], np.int32), np.ones(4, np.int32))  # 4 >= n
+    assert e.value.code == M.MOQ_ERR_ARG
+    with pytest.raises(M.MoqError) as e:
+        M.moq_create_instance(4, 2, 2, np.array([0, 0], np.int32), np.array([2, 2], np.int32), np.ones(4, np.int32))
+    assert e.value.code == M.MOQ_ERR_ARG and "repeated" in str(e.value)
+    with pytest.raises(M.MoqError) as e:
+        M.moq_create_instance(4, 9, 0, [], [], [])
+    assert e.value.code == M.MOQ_ERR_ARG
+
+
+# ----------------------------------------------------------------------------- a6
+@pytest.mark.parametrize("name", list(INSTANCES))
+def test_cuts_bit_exact(M, P, oracle, name):
+    src = INSTANCES[name]()
+    inst = P.Instance(src)
+    Mn = 1000 + 37  # several blocks and a ragged tail
+    bits = wl.random_sign_bits(Mn, src.n, 11)
+    cuts = torch.zeros((Mn, src.K), dtype=torch.int64, device="cuda")
+    M.moq_evaluate_cuts(inst.handle, _bits_dev(bits), Mn, cuts)
+    assert np.array_equal(cuts.cpu().numpy(), oracle.cuts(src, bits))
+    M.moq_evaluate_cuts(inst.handle, _bits_dev(bits), 0, cuts)  # M = 0 is a no-op
+
+
+def test_cuts_every_configuration(M, P, oracle):
+    src = wl.random_graph(14, 0.4, 9, K=3)
+    inst = P.Instance(src)
+    bits, want = oracle.brute_force(src)
+    cuts = torch.zeros(want.shape, dtype=torch.int64, device="cuda")
+    M.moq_evaluate_cuts(inst.handle, _bits_dev(bits), bits.shape[0], cuts)
+    assert np.array_equal(cuts.cpu().numpy(), want)
+
+
+def test_cuts_golden_triangle(M, P):
+    lines = golden_lines("triangle_cuts.txt")
+    rows = [[int(t) for t in l.split()[1:]] for l in lines if l.startswith("edge")]
+    src = wl.Instance(3, np.array([r[0] for r in rows], np.int32), np.array([r[1] for r in rows], np.int32),
+                      np.array([r[2:] for r in rows], np.int32).T.copy())
+    inst = P.Instance(src)
+    cfgs = [l for l in lines if l.startswith("config")]
+    s = np.array([[1 if t == "+" else -1 for t in c.split("->")[0].split()[1:]] for c in cfgs])
+    want = np.array([[int(t) for t in c.split("->")[1].split()] for c in cfgs])
+    cuts = torch.zeros(want.shape, dtype=torch.int64, device="cuda")
+    M.moq_evaluate_cuts(inst.handle, _bits_dev(wl.signs_to_bits(s)), len(cfgs), cuts)
+    assert np.array_equal(cuts.cpu().numpy(), want)
+
+
+# ----------------------------------------------------------------------------- a7
+def _run_archive(M, P, oracle, cuts, bits, n, batches, capacity=1 << 14):
+    K = cuts.shape[1]
+    arch = P.Archive(n, K, capacity=capacity, max_batch=max(max(b) - min(b) for b in batches) + 1)
+    for b in batches:
+        lo, hi = b[0], b[-1] + 1
+        size = arch.merge(_dev(cuts[lo:hi], torch.int64), _bits_dev(bits[lo:hi]), hi - lo, lo, want_size=True)
+    gc, gb, gi = arch.copy_out()
+    keep = oracle.pareto_filter(cuts)
+    assert size == len(keep)
+    assert np.array_equal(gi, keep)
+    assert np.array_equal(gc, cuts[keep])
+    assert np.array_equal(gb, _canonical(bits[keep], n))
+    return arch
+
+
+@pytest.mark.parametrize("K,span,Mtot", [(2, 40, 3000), (3, 12, 5000), (4, 6, 4000), (8, 3, 2000), (3, 1000, 20000)])
+def test_pareto_archive_bit_exact(M, P, oracle, K, span, Mtot):
+    rng = np.random.default_rng(K * 7 + span)
+    cuts = rng.integers(-span, span, size=(Mtot, K)).astype(np.int64)
+    n = 70
+    bits = wl.random_sign_bits(Mtot, n, K)
+    cuts[::17] = cuts[5]  # many exact duplicates
+    edges = sorted({0, Mtot} | set(rng.integers(1, Mtot, size=5).tolist()))
+    batches = [list(range(a, b)) for a, b in zip(edges[:-1], edges[1:])]
+    _run_archive(M, P, oracle, cuts, bits, n, batches)
+
+
+def test_pareto_edge_cases(M, P, oracle):
+    n, K = 42, 3
+    arch = P.Archive(n, K, capacity=8, max_batch=64)
+    empty = torch.zeros((1, K), dtype=torch.int64, device="cuda")
+    assert arch.merge(empty, torch.zeros((1, 1), dtype=torch.int64, device="cuda"), 0, 0, want_size=True) == 0
+    # all candidates equal: one survivor, the lowest index
+    c = np.tile(np.array([[3, 4, 5]], np.int64), (50, 1))
+    b = wl.random_sign_bits(50, n, 1)
+    assert arch.merge(_dev(c, torch.int64), _bits_dev(b), 50, 100, want_size=True) == 1
+    gc, gb, gi = arch.copy_out()
+    assert gi.tolist() == [100] and np.array_equal(gb, _canonical(b[:1], n))
+    # an equal vector in a later batch does not replace the member
+    assert arch.merge(_dev(c[:3], torch.int64), _bits_dev(b[:3]), 3, 200, want_size=True) == 1
+    assert arch.copy_out()[2].tolist() == [100]
+    # capacity: 9 mutually non-dominated vectors do not fit in 8 slots; archive unchanged
+    anti = np.array([[i, 20 - i, 0] for i in range(9)], np.int64)
+    with pytest.raises(M.MoqError) as e:
+        arch.merge(_dev(anti, torch.int64), _bits_dev(wl.random_sign_bits(9, n, 2)), 9, 300, want_size=True)
+    assert e.value.code == M.MOQ_ERR_CAPACITY
+    assert arch.copy_out()[2].tolist() == [100]
+    with pytest.raises(M.MoqError):
+        arch.merge(_dev(np.zeros((65, K), np.int64), torch.int64), _bits_dev(wl.random_sign_bits(65, n, 3)), 65, 0)
+
+
+# ----------------------------------------------------------------------------- a8
+def _hv_points(M, pts, ref):
+    F, K = pts.shape
+    ws = torch.zeros(M.moq_hypervolume_workspace_size(F, K), dtype=torch.uint8, device="cuda")
+    return M.moq_hypervolume_points(_dev(pts, torch.int64), F, K, ref, ws)
+
+
+def test_hv_appendix_a(M):
+    lines = golden_lines("app_a_hypervolume.txt")
+    ref = [int(t) for t in lines[0].split()[1:]]
+    for fl, hl in zip(lines[1::2], lines[2::2]):
+        assert _hv_points(M, parse_points(fl[6:]), ref) == int(hl.split()[1])
+
+
+@pytest.mark.parametrize("K,F,span", [(2, 700, 10000), (3, 1500, 300), (3, 2100, 20), (4, 300, 100), (4, 260, 8)])
+def test_hv_bit_exact(M, oracle, K, F, span):
+    rng = np.random.default_rng(K * 100 + F)
+    pts = rng.integers(-span // 10, span, size=(F, K)).astype(np.int64)
+    ref = np.zeros(K, np.int64)
+    # keep it mostly a front: project onto a noisy simplex surface, plus dominated points
+    if K >= 3:
+        pts[: F // 2, -1] = span * 2 - pts[: F // 2, :-1].sum(axis=1)
+    assert _hv_points(M, pts, ref) == oracle.hypervolume(pts, ref)
+
+
+def test_hv_edge_cases(M, oracle):
+    ref = np.zeros(3, np.int64)
+    assert _hv_points(M, np.zeros((0, 3), np.int64), ref) == 0
+    assert _hv_points(M, np.array([[5, 6, 7]], np.int64), ref) == 210
+    assert _hv_points(M, np.array([[5, 6, 7], [5, 6, 7], [1, 1, 1]], np.int64), ref) == 210
+    assert _hv_points(M, np.array([[5, -1, 7], [2, 2, 2]], np.int64), ref) == 8  # first spans nothing
+    side = 1_500_000_000
+    big = np.array([[side, side, side, side], [side + 7, 3, side, side]], np.int64)
+    assert _hv_points(M, big, np.zeros(4, np.int64)) == side ** 4 + 7 * 3 * side * side
+    with pytest.raises(M.MoqError) as e:
+        _hv_points(M, np.ones((2, 5), np.int64), np.zeros(5, np.int64))
+    assert e.value.code == M.MOQ_ERR_UNSUPPORTED
+
+
+# ----------------------------------------------------------------------------- a2..a5
+def _abs_force_scale(src, lam, phi, c0):
+    """c0 * sum_j |J(c)_ij phi_j| per replica and spin (the normwise force bound)."""
+    Jc = lam.astype(np.float64) @ src.w.astype(np.float64)  # (R, E)
+    out = np.zeros(phi.shape)
+    np.add.at(out.T, src.ei, (np.abs(Jc * phi[:, src.ej])).T)
+    np.add.at(out.T, src.ej, (np.abs(Jc * phi[:, src.ei])).T)
+    return out * c0[:, None]
+
+
+@pytest.mark.parametrize("name", ["heavyhex_K3", "heavyhex_K4", "reg3_n1024_K3", "gnp_n40_K2", "gnp_n70_K8"])
+@pytest.mark.parametrize("variant", ["dsb", "bsb"])
+def test_force_matches_fp64(M, P, oracle, name, variant):
+    # one step with a_0 = a0 (no linear term), y0 = 0, alpha = 0 and dt = 2^-10: the
+    # momentum after the step is dt * force exactly, so y_out / dt exposes the force
+    src = INSTANCES[name]()
+    inst = P.Instance(src)
+    R = 67
+    lam = wl.dirichlet_lambdas(R, src.K, 3)
+    rng = np.random.default_rng(1)
+    x0 = rng.uniform(-0.5, 0.5, (R, src.n)).astype(np.float32)
+    dt = 2.0 ** -10
+    y_out = torch.zeros((R, src.n), dtype=torch.float32, device="cuda")
+    x_out = torch.zeros_like(y_out)
+    p = M.moq_default_params(variant=variant, steps=1, dt=dt, a0=1.0, alpha=0.0,
+                             schedule=torch.ones(1, device="cuda"), x_init=_dev(x0, torch.float32),
+                             y_init=torch.zeros((R, src.n), device="cuda"), x_out=x_out, y_out=y_out)
+    bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+    M.moq_sample(inst.handle, _dev(lam, torch.float32), R, p, 0, 0, bits)
+    ref = oracle.sb(src, lam.astype(np.float64), variant=variant, steps=1, dt=dt, a0=1.0, alpha=0.0,
+                    schedule=[1.0], x_init=x0.astype(np.float64), y_init=np.zeros((R, src.n)))
+    f_gpu = y_out.cpu().numpy().astype(np.float64) / dt
+    f_ref = ref["y"] / dt
+    phi = np.where(x0 >= 0, 1.0, -1.0) if variant == "dsb" else x0.astype(np.float64)
+    scale = _abs_force_scale(src, lam, phi, ref["c0"])
+    err = np.abs(f_gpu - f_ref)
+    assert np.all(err <= FORCE_RTOL * scale + 1e-30), float((err / np.maximum(scale, 1e-30)).max())
+    assert np.allclose(x_out.cpu().numpy(), ref["x"], rtol=0, atol=1e-6)
+
+
+def test_one_step_golden(M, P):
+    lines = golden_lines("sb_one_step.txt")
+    rows = [[int(t) for t in l.split()[1:]] for l in lines if l.startswith("edge")]
+    src = wl.Instance(3, np.array([r[0] for r in rows], np.int32), np.array([r[1] for r in rows], np.int32),
+                      np.array([r[2:] for r in rows], np.int32).T.copy())
+    inst = P.Instance(src)
+    lam = np.array([[float(v) for v in [l for l in lines if l.startswith("lambda")][0].split()[1:]]], np.float32)
+    for c in [l for l in lines if l.startswith("case")]:
+        parts = c[4:].split("|")
+        x0, y0, y1, x1 = (np.array([float(v) for v in q.split()], np.float32) for q in parts[1:])
+        xo = torch.zeros((1, 3), device="cuda")
+        yo = torch.zeros((1, 3), device="cuda")
+        p = M.moq_default_params(variant=parts[0].strip(), steps=1, dt=0.5, a0=1.0, alpha=0.0,
+                                 schedule=torch.full((1,), 0.5, device="cuda"), x_init=_dev(x0[None], torch.float32),
+                                 y_init=_dev(y0[None], torch.float32), x_out=xo, y_out=yo)
+        M.moq_sample(inst.handle, _dev(lam, torch.float32), 1, p, 0, 0, torch.zeros((1, 1), dtype=torch.int64, device="cuda"))
+        assert np.allclose(yo.cpu().numpy()[0], y1, atol=1e-6)
+        assert np.allclose(xo.cpu().numpy()[0], x1, atol=1e-6)
+
+
+def test_initial_state_bit_exact(M, P, oracle):
+    src = INSTANCES["heavyhex_K3"]()
+    inst = P.Instance(src)
+    R = 40
+    xo = torch.zeros((R, src.n), device="cuda")
+    yo = torch.zeros((R, src.n), device="cuda")
+    p = M.moq_default_params(steps=0, init_amp=0.1, x_out=xo, y_out=yo)
+    bits = torch.zeros((R, 1), dtype=torch.int64, device="cuda")
+    M.moq_sample(inst.handle, _dev(wl.dirichlet_lambdas(R, 3, 0), torch.float32), R, p, 12345, 6, bits)
+    want = np.array([[oracle.initial_state(12345, 6, r, i, 0.1) for i in range(src.n)] for r in range(R)])
+    assert np.array_equal(xo.cpu().numpy().astype(np.float64), want[..., 0])
+    assert np.array_equal(yo.cpu().numpy().astype(np.float64), want[..., 1])
+    s = wl.bits_to_signs(_bits_host(bits), src.n)
+    assert np.array_equal(s, np.where(want[..., 0] >= 0, 1, -1))
+
+
+def test_bsb_short_trajectory(M, P, oracle):
+    # without noise bSB is smooth: 25 FP32 steps stay close to the FP64 trajectory
+    src = INSTANCES["heavyhex_K4"]()
+    inst = P.Instance(src)
+    R = 64
+    lam = wl.dirichlet_lambdas(R, 4, 5)
+    xo = torch.zeros((R, src.n), device="cuda")
+    yo = torch.zeros((R, src.n), device="cuda")
+    p = M.moq_default_params(variant="bsb", steps=25, dt=0.5, x_out=xo, y_out=yo)
+    bits = torch.zeros((R, 1), dtype=torch.int64, device="cuda")
+    M.moq_sample(inst.handle, _dev(lam, torch.float32), R, p, 3, 0, bits)
+    ref = oracle.sb(src, lam.astype(np.float64), variant="bsb", steps=25, dt=0.5, seed=3)
+    assert np.abs(xo.cpu().numpy() - ref["x"]).max() < 1e-4
+    assert np.abs(yo.cpu().numpy() - ref["y"]).max() < 1e-4
+
+
+@pytest.mark.parametrize("variant", ["dsb", "bsb"])
+def test_sampler_invariants_and_determinism(M, P, variant):
+    src = INSTANCES["reg3_n150_K3"]()
+    inst = P.Instance(src)
+    R = 300
+    lam = _dev(wl.dirichlet_lambdas(R, 3, 9), torch.float32)
+    xo = torch.zeros((R, src.n), device="cuda")
+    yo = torch.zeros((R, src.n), device="cuda")
+    p = M.moq_default_params(variant=variant, steps=500, dt=0.5, alpha=0.15, x_out=xo, y_out=yo)
+    b1 = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+    b2 = torch.zeros_like(b1)
+    b3 = torch.zeros_like(b1)
+    M.moq_sample(inst.handle, lam, R, p, 77, 1, b1)
+    x, y = xo.cpu().numpy(), yo.cpu().numpy()
+    assert np.all(np.abs(x) <= 1.0) and np.all(y[np.abs(x) == 1.0] == 0.0)
+    assert np.array_equal(wl.bits_to_signs(_bits_host(b1), src.n), np.where(x >= 0, 1, -1))
+    M.moq_sample(inst.handle, lam, R, p, 77, 1, b2)
+    assert torch.equal(b1, b2)  # same seed and round: identical
+    M.moq_sample(inst.handle, lam, R, p, 77, 2, b3)
+    assert not torch.equal(b1, b3)
+
+
+@pytest.mark.parametrize("variant", ["dsb", "bsb"])
+def test_bipartite_reaches_max_cut(M, P, variant):
+    rows, cols = 6, 7
+    e = []
+    rng = np.random.default_rng(3)
+    for r in range(rows):
+        for c in range(cols):
+            v = r * cols + c
+            if c + 1 < cols:
+                e.append((v, v + 1))
+            if r + 1 < rows:
+                e.append((v, v + cols))
+    ei = np.array([a for a, _ in e], np.int32)
+    ej = np.array([b for _, b in e], np.int32)
+    w = np.stack([rng.integers(1, 6, len(e)), rng.integers(-5, 6, len(e))]).astype(np.int32)
+    src = wl.Instance(rows * cols, ei, ej, w)
+    inst = P.Instance(src)
+    R = 64
+    lam = torch.tensor([[1.0, 0.0]] * R, device="cuda")
+    bits = torch.zeros((R, 1), dtype=torch.int64, device="cuda")
+    M.moq_sample(inst.handle, lam, R, M.moq_default_params(variant=variant, steps=600, dt=0.5), 5, 0, bits)
+    cuts = torch.zeros((R, 2), dtype=torch.int64, device="cuda")
+    M.moq_evaluate_cuts(inst.handle, bits, R, cuts)
+    c1 = cuts[:, 0].cpu().numpy()
+    assert c1.max() == w[0].sum() and np.mean(c1 == w[0].sum()) >= 0.5
+
+
+def test_sampler_recovers_bruteforce_front(M, P, oracle):
+    src = wl.random_graph(12, 0.5, 21, K=3, wmax=10)
+    bf_bits, bf_cuts = oracle.brute_force(src)
+    front = bf_cuts[oracle.pareto_filter(bf_cuts)]
+    inst = P.Instance(src)
+    R = 4096
+    arch = P.Archive(src.n, 3, capacity=4096, max_batch=R)
+    buf = P.RoundBuffers(R, src.n, 3)
+    params = M.moq_default_params(steps=200, dt=0.5, alpha=0.3)
+    for rnd in range(2):
+        P.sample_round(inst, arch, buf, params, seed=2, round_=rnd)
+    gc, gb, gi = arch.copy_out()
+    fset = {tuple(v) for v in front}
+    assert {tuple(v) for v in gc} <= fset  # every archived vector is a true front vector
+    assert len(gc) >= 0.8 * len(fset)
+    assert arch.hypervolume(inst.ref) >= 0.98 * oracle.hypervolume(front, inst.ref)
+    # the archived representatives have exactly the archived cut vectors
+    assert np.array_equal(oracle.cuts(src, gb), gc)
+
+
+def test_final_hv_distribution_matches_oracle(M, P, oracle):
+    # chaotic trajectories: compare the distribution of the final front's hypervolume
+    # over 32 seeds (two-sample Mann-Whitney U) between the GPU and the FP64 oracle
+    src = INSTANCES["heavyhex_K3"]()
+    inst = P.Instance(src)
+    R, T = 128, 300
+    lam = wl.dirichlet_lambdas(R, 3, 77)
+    lam_d = _dev(lam, torch.float32)
+    params = M.moq_default_params(steps=T, dt=0.5, alpha=0.15)
+    bits = torch.zeros((R, 1), dtype=torch.int64, device="cuda")
+    hv_gpu, hv_cpu = [], []
+    for seed in range(32):
+        M.moq_sample(inst.handle, lam_d, R, params, seed, 0, bits)
+        c = oracle.cuts(src, _bits_host(bits))
+        hv_gpu.append(oracle.hypervolume(c[oracle.pareto_filter(c)], inst.ref))
+        o = oracle.sb(src, lam.astype(np.float64), steps=T, dt=0.5, alpha=0.15, seed=1000 + seed)
+        c = oracle.cuts(src, o["bits"])
+        hv_cpu.append(oracle.hypervolume(c[oracle.pareto_filter(c)], inst.ref))
+    p = stats.mannwhitneyu(hv_gpu, hv_cpu).pvalue
+    assert p > 0.01, (p, np.median(hv_gpu), np.median(hv_cpu))
+    assert abs(np.median(hv_gpu) / np.median(hv_cpu) - 1) < 0.02
+
+
+# ----------------------------------------------------------------------------- lambda
+def test_das_dennis_lattice(M, oracle):
+    for K, H in [(3, 21), (4, 13), (2, 9), (5, 7)]:
+        want = oracle.das_dennis(K, H, True)
+        buf = torch.zeros((len(want) + 5, K), device="cuda")
+        cnt = M.moq_lambda_das_dennis(K, H, True, buf, len(want) + 5)
+        assert cnt == len(want)
+        assert np.abs(buf[:cnt].cpu().numpy() - want).max() < 1e-6
+        assert np.array_equal(np.rint(buf[:cnt].cpu().numpy() * H).astype(int), np.rint(want * H).astype(int))
+    with pytest.raises(M.MoqError) as e:
+        M.moq_lambda_das_dennis(3, 21, True, torch.zeros((10, 3), device="cuda"), 10)
+    assert e.value.code == M.MOQ_ERR_CAPACITY
+
+
+def test_dirichlet_matches_oracle(M, oracle):
+    R, K = 5000, 4
+    buf = torch.zeros((R, K), device="cuda")
+    M.moq_lambda_dirichlet(K, R, 99, 3, buf)
+    want = oracle.dirichlet(R, K, 99, 3)
+    assert np.abs(buf.cpu().numpy() - want).max() < 2e-6
+
+
+# ----------------------------------------------------------------------------- full path
+def test_full_round_matches_oracle(M, P, oracle):
+    # the benchmark's launch configuration: n=42, K=4, 16384 replicas, dSB; cuts, front
+    # and hypervolume of the GPU samples must equal the oracle's on the same samples
+    src = wl.heavy_hex_like(1001, K=4)
+    inst = P.Instance(src)
+    R = 16384
+    arch = P.Archive(src.n, 4, capacity=1 << 16, max_batch=R)
+    buf = P.RoundBuffers(R, src.n, 4)
+    params = M.moq_default_params(steps=200, dt=0.5, alpha=0.1)
+    P.sample_round(inst, arch, buf, params, seed=1, round_=0)
+    bits = _bits_host(buf.bits)
+    cuts = oracle.cuts(src, bits)
+    assert np.array_equal(buf.cuts.cpu().numpy(), cuts)
+    keep = oracle.pareto_filter(cuts)
+    gc, gb, gi = arch.copy_out()
+    assert np.array_equal(gi, keep) and np.array_equal(gc, cuts[keep])
+    if len(keep) <= 400:
+        assert arch.hypervolume(inst.ref) == oracle.hypervolume(cuts[keep], inst.ref)
