@@ -168,6 +168,21 @@ int moq_hypervolume(const moq_archive* a, const int64_t* ref, moq_hv* out, void*
 int64_t moq_hypervolume_workspace_size(int64_t F, int32_t K);
 int moq_hypervolume_points(const int64_t* pts, int64_t F, int32_t K, const int64_t* ref, void* workspace,
                            moq_hv* out, void* stream);
+/* Allocation-free variant of moq_hypervolume_points (the paper has no counterpart: it
+ * exists for callers that cannot allocate device memory when they need a result, e.g.
+ * code whose device memory is owned by another allocator, or loops where a cudaMalloc
+ * or cudaFree would stall the whole device). The scratch is a fixed array in the
+ * library's own device memory, sized for moq_hypervolume_noalloc_max_points() points
+ * (16384) of up to 4 objectives, about 0.77 MB on every GPU that loads the library,
+ * held until the process exits. The call allocates nothing; the caller still owns pts,
+ * ref and out. The first call on a device looks up that device's address of the array
+ * (make it before any stream capture). Every call shares the one array and leaves its
+ * contents behind, so calls that overlap on the GPU (e.g. from two streams at once)
+ * race; calls in sequence are safe (the call synchronises its stream).
+ * Errors: MOQ_ERR_CAPACITY (F above the limit), otherwise as moq_hypervolume_points. */
+int64_t moq_hypervolume_noalloc_max_points(void);
+int moq_hypervolume_points_noalloc(const int64_t* pts, int64_t F, int32_t K, const int64_t* ref, moq_hv* out,
+                                   void* stream);
 
 /* ---- a2: weight vectors ("Scalarization via the weighted sum method", App. B) ----
  * Das-Dennis lattice of resolution H: c in {0, 1/H, .., 1}^K with sum 1 (interior != 0:

@@ -16,6 +16,7 @@
 // Slab contributions are reduced per block in int128 and summed by a final block.
 // Points with some y_k < r_k span an empty box and are left out.
 #include <algorithm>
+#include <mutex>
 
 #include "moq_common.cuh"
 
@@ -369,6 +370,71 @@ int moq_hypervolume(const moq_archive* a, const int64_t* ref, moq_hv* out, void*
     int rc = moq_archive_size(a, &F, stream);
     if (rc != MOQ_OK) return rc;
     return moq_hypervolume_points(a->cuts[a->cur], F, a->K, ref, a->hv_ws, out, stream);
+}
+
+}  // extern "C"
+
+// ---- hypervolume without any device allocation --------------------------------------
+// Some callers cannot allocate device memory at the point where they need a
+// hypervolume: code running under an external allocator that owns the whole device
+// budget, latency-critical loops where cudaMalloc/cudaFree would synchronise the
+// device, or hosts that forbid allocation after start-up. For them the scratch lives
+// in a fixed array of this library's own device memory, reserved when the library is
+// loaded (every GPU that loads it holds the array until the process exits).
+namespace moq {
+namespace {
+
+constexpr int64_t kNoAllocMaxPoints = 16384;
+constexpr size_t round256(size_t v) { return (v + 255) / 256 * 256; }
+// the workspace layout of moq_hypervolume_points for kNoAllocMaxPoints points, K = 4
+constexpr size_t kNoAllocBytes =
+    2 * round256(sizeof(int32_t) * 4 * kNoAllocMaxPoints) + round256(16 * kNoAllocMaxPoints) + 256;
+
+static __device__ __align__(256) unsigned char g_hv_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device. The symbol's host-side
+// name is only a stand-in, so the address is looked up once per device (with that
+// device current) and cached.
+int noalloc_scratch(void** out)
+{
+    int dev = 0;
+    MOQ_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(MOQ_ERR_UNSUPPORTED, "device index %d >= %d", dev, kMaxDevices);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        MOQ_CUDA_TRY(cudaGetSymbolAddress(&p, g_hv_noalloc_scratch));
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return MOQ_OK;
+}
+
+}  // namespace
+}  // namespace moq
+
+extern "C" {
+
+int64_t moq_hypervolume_noalloc_max_points(void) { return moq::kNoAllocMaxPoints; }
+
+int moq_hypervolume_points_noalloc(const int64_t* pts, int64_t F, int32_t K, const int64_t* ref, moq_hv* out,
+                                   void* stream)
+{
+    using namespace moq;
+    if (F > kNoAllocMaxPoints)
+        return fail(MOQ_ERR_CAPACITY, "moq_hypervolume_points_noalloc: %lld points exceed the fixed scratch limit of %lld",
+                    (long long)F, (long long)kNoAllocMaxPoints);
+    if (K > 4) return fail(MOQ_ERR_UNSUPPORTED, "moq_hypervolume_points_noalloc: K=%d > 4", K);
+    void* scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc != MOQ_OK) return rc;
+    // the allocating entry point, handed the fixed array as its workspace; it clears the
+    // one counter that must start at zero and overwrites the rest before reading it
+    return moq_hypervolume_points(pts, F, K, ref, scratch, out, stream);
 }
 
 }  // extern "C"

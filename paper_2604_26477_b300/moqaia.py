@@ -76,6 +76,8 @@ _sigs = {
     "moq_hypervolume": (C.c_int, [_vp, _vp, C.POINTER(moq_hv), _vp]),
     "moq_hypervolume_workspace_size": (_i64, [_i64, _i32]),
     "moq_hypervolume_points": (C.c_int, [_vp, _i64, _i32, _vp, _vp, C.POINTER(moq_hv), _vp]),
+    "moq_hypervolume_noalloc_max_points": (_i64, []),
+    "moq_hypervolume_points_noalloc": (C.c_int, [_vp, _i64, _i32, _vp, C.POINTER(moq_hv), _vp]),
     "moq_lambda_das_dennis": (C.c_int, [_i32, _i32, _i32, _vp, _i64, C.POINTER(_i64), _vp]),
     "moq_lambda_dirichlet": (C.c_int, [_i32, _i32, _u64, _u64, _vp, _vp]),
     "moq_strerror": (C.c_char_p, [C.c_int]),
@@ -253,6 +255,22 @@ def moq_hypervolume_points(pts, F, K, ref, workspace, stream=None) -> int:
     out = moq_hv()
     _check(_lib.moq_hypervolume_points(_dptr(pts, "pts", i64), F, K, pref, _dptr(workspace, "workspace"),
                                        C.byref(out), _stream(stream)), "moq_hypervolume_points")
+    return out.value()
+
+
+def moq_hypervolume_noalloc_max_points() -> int:
+    return int(_lib.moq_hypervolume_noalloc_max_points())
+
+
+def moq_hypervolume_points_noalloc(pts, F, K, ref, stream=None) -> int:
+    """Hypervolume without any device allocation, for callers that cannot allocate device
+    memory at that point; the scratch is a fixed array inside the library (at most
+    ``moq_hypervolume_noalloc_max_points()`` points). Overlapping calls race on it."""
+    _, i64, _ = _torch_types()
+    ref_, pref = _hptr(ref, np.int64)
+    out = moq_hv()
+    _check(_lib.moq_hypervolume_points_noalloc(_dptr(pts, "pts", i64), F, K, pref, C.byref(out), _stream(stream)),
+           "moq_hypervolume_points_noalloc")
     return out.value()
 
 
