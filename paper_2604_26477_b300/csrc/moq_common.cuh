@@ -53,9 +53,10 @@ struct Philox4x32 {
     {
 #pragma unroll
         for (int rnd = 0; rnd < 10; ++rnd) {
-            const uint32_t lo0 = kM0 * c.x, hi0 = __umulhi(kM0, c.x);
-            const uint32_t lo1 = kM1 * c.z, hi1 = __umulhi(kM1, c.z);
-            c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+            // one 32x32 -> 64-bit multiply per product gives both halves
+            const uint64_t p0 = (uint64_t)kM0 * c.x;
+            const uint64_t p1 = (uint64_t)kM1 * c.z;
+            c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
             k0 += kW0;
             k1 += kW1;
         }
@@ -69,14 +70,22 @@ __device__ __forceinline__ float signed_unit(uint32_t word)
     return (float)((int32_t)(word >> 8) - 8388608) * 0x1p-23f;
 }
 
+__device__ __forceinline__ float sqrt_approx(float v)
+{
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
 // Two standard normals from two 32-bit words by Box-Muller: u1 in (0,1], u2 in [0,1),
 // rho = sqrt(-2 ln u1), theta = 2 pi u2 -> (rho cos theta, rho sin theta). The angle is
-// evaluated as 2 pi (u2 - 1/2) + pi so the fast sine/cosine see [-pi, pi).
+// evaluated as 2 pi (u2 - 1/2) + pi so the fast sine/cosine see [-pi, pi); u1 and
+// u2 - 1/2 are exact in float ((w >> 8) < 2^24).
 __device__ __forceinline__ float2 box_muller(uint32_t w_a, uint32_t w_b)
 {
-    const float u1 = (float)((w_a >> 8) + 1u) * 0x1p-24f;
-    const float u2c = (float)(w_b >> 8) * 0x1p-24f - 0.5f;
-    const float rho = sqrtf(-2.0f * __logf(u1));
+    const float u1 = fmaf((float)(w_a >> 8), 0x1p-24f, 0x1p-24f);
+    const float u2c = fmaf((float)(w_b >> 8), 0x1p-24f, -0.5f);
+    const float rho = sqrt_approx(-2.0f * __logf(u1));
     float s, c;
     __sincosf(6.2831853071795864f * u2c, &s, &c);
     return make_float2(-rho * c, -rho * s);

@@ -2,13 +2,14 @@
 // with Gaussian noise", SB equations and Eq. NI-SB), the whole trajectory on-chip.
 //
 // A block owns Rb replicas of one instance for all T steps. Thread t handles spin
-// i = t / Rb of replica t % Rb (spin-major), so the 32 threads of a warp read the
-// same neighbour columns of different replicas: phi(x_j) lives in shared memory as
-// phi[j * Rb + replica] and a warp's gathers hit consecutive words (no bank conflicts).
-// Each thread keeps x_i, y_i and its row of -c0 * J(c) (at most DMAX entries) in
-// registers; the only per-step traffic is the shared-memory gather and one barrier.
-// The state never touches HBM: the kernel reads the CSR row and lambda once and writes
-// the packed signs once.
+// i = t / Rb of replica t % Rb (spin-major), so the threads of a warp read the same
+// neighbour columns of different replicas: phi(x_j) lives in shared memory as
+// phi[j * Rb + replica] and a warp's gathers hit consecutive words. Each thread keeps
+// x_i, y_i and its row of -c0 * J(c) (DMAX entries, zero-padded) in registers; per step
+// the only memory traffic is the shared-memory gather, one store and one barrier.
+// The step loop is unrolled by four: one Philox4x32-10 block gives the four Gaussians
+// of four consecutive steps, and the two phi buffers alternate at a fixed offset.
+// HBM sees the CSR rows and lambda once (in) and the packed signs once (out).
 #include <algorithm>
 #include <stdlib.h>
 
@@ -16,6 +17,8 @@
 
 namespace moq {
 namespace {
+
+constexpr int kPhiStride = 1024;  // floats per phi buffer (a block has at most 1024 threads)
 
 struct SbArgs {
     int32_t n, K, R, Rb, T, W;
@@ -25,8 +28,9 @@ struct SbArgs {
     const int32_t* wn;
     const int64_t* rowsum;
     const float* lambda;
-    float dt, a0, alpha, init_amp, inv_Tm1, sqrt_dt;
-    int32_t noise_sqrt_dt;
+    float dt, a0, init_amp;
+    float kappa;  // coefficient of eta in the y update: dt*alpha (Euler) or sqrt(dt)*alpha
+    float a0inv;  // a0 / (T - 1): the linear pump gives a_m - a0 = a0inv * m - a0
     const float* schedule;
     const float* x_init;
     const float* y_init;
@@ -38,21 +42,52 @@ struct SbArgs {
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-__host__ __device__ inline size_t sb_smem_bytes(int n, int Rb, int W)
+__host__ __device__ inline size_t sb_smem_bytes(int Rb, int W)
 {
-    return align_up(sizeof(float) * 2 * (size_t)n * Rb + sizeof(unsigned) * 2 * Rb, 16) + sizeof(unsigned long long) * (size_t)Rb * W;
+    return sizeof(float) * 2 * kPhiStride + align_up(sizeof(unsigned) * 2 * Rb, 16) + sizeof(unsigned long long) * (size_t)Rb * W;
 }
 
+// phi(x): sgn(x) with sgn(0) = +1 for dSB (x is never -0 here: the start state is
+// sanitised and the update cannot produce -0 from +-nonzero or +0), x for bSB.
+template <int VARIANT>
+__device__ __forceinline__ float phi_of(float x)
+{
+    if (VARIANT == MOQ_DSB) return __int_as_float(0x3f800000 | (__float_as_int(x) & 0x80000000));
+    return x;
+}
+
+// One Euler step of one spin: force from the shared-memory phi buffer `rd`, symplectic
+// update, inelastic wall, phi into `wr`, then the block barrier.
 template <int VARIANT, int DMAX, bool NOISE>
+__device__ __forceinline__ void sb_step(const float* rd, float* wr, int tid, const float (&jc)[DMAX],
+                                        const int (&nb)[DMAX], float cm, float eta, float dt, float kappa, float dta0,
+                                        float& x, float& y)
+{
+    float f = 0.0f;
+#pragma unroll
+    for (int d = 0; d < DMAX; ++d) f = fmaf(jc[d], rd[nb[d]], f);
+    const float drift = fmaf(cm, x, f);  // -(a0 - a_m) x + c0 sum_j (-J(c)_ij) phi(x_j)
+    y = fmaf(dt, drift, y);
+    if (NOISE) y = fmaf(kappa, eta, y);
+    x = fmaf(dta0, y, x);
+    if (fabsf(x) > 1.0f) {  // inelastic wall
+        x = copysignf(1.0f, x);
+        y = 0.0f;
+    }
+    wr[tid] = phi_of<VARIANT>(x);
+    __syncthreads();
+}
+
+template <int VARIANT, int DMAX, bool NOISE, bool LINEAR>
 __global__ void __launch_bounds__(1024) k_sb_sparse(const SbArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = a.n, Rb = a.Rb;
-    const int nt = n * Rb;  // == blockDim.x
-    float* phi_a = reinterpret_cast<float*>(smem_raw);
-    float* phi_b = phi_a + nt;
-    unsigned* red = reinterpret_cast<unsigned*>(phi_b + nt);  // 2 * Rb
-    unsigned long long* wb = reinterpret_cast<unsigned long long*>(smem_raw + align_up(sizeof(float) * 2 * nt + sizeof(unsigned) * 2 * Rb, 16));
+    float* phiA = reinterpret_cast<float*>(smem_raw);
+    float* phiB = phiA + kPhiStride;
+    unsigned* red = reinterpret_cast<unsigned*>(phiB + kPhiStride);  // 2 * Rb
+    unsigned long long* wb = reinterpret_cast<unsigned long long*>(smem_raw + sizeof(float) * 2 * kPhiStride +
+                                                                   align_up(sizeof(unsigned) * 2 * Rb, 16));
 
     const int tid = threadIdx.x;
     const int i = tid / Rb;       // spin
@@ -66,7 +101,7 @@ __global__ void __launch_bounds__(1024) k_sb_sparse(const SbArgs a)
 #pragma unroll
     for (int k = 0; k < kMaxK; ++k) lam[k] = (k < a.K) ? a.lambda[(int64_t)rs * a.K + k] : 0.0f;
 
-    // row i of J(c) = sum_k c_k J^(k), kept in registers
+    // row i of J(c) = sum_k c_k J^(k) in registers, zero-padded to DMAX entries
     const int p0 = a.rowptr[i];
     const int deg = a.rowptr[i + 1] - p0;
     float jc[DMAX];
@@ -100,56 +135,47 @@ __global__ void __launch_bounds__(1024) k_sb_sparse(const SbArgs a)
 #pragma unroll
     for (int d = 0; d < DMAX; ++d) jc[d] *= -c0;  // the force acts on the negated coupling
 
-    // start state
+    // start state (+0.0f turns a caller's -0 into +0, which phi_of relies on)
     float x, y;
     if (a.x_init) {
-        x = active ? a.x_init[(int64_t)r * n + i] : 0.0f;
+        x = (active ? a.x_init[(int64_t)r * n + i] : 0.0f) + 0.0f;
         y = (active && a.y_init) ? a.y_init[(int64_t)r * n + i] : 0.0f;
     } else {
         const uint4 o = Philox4x32::block(make_uint4(0xFFFFFFFFu, (uint32_t)i, (uint32_t)r, a.round32), a.key0, a.key1);
-        x = __fmul_rn(a.init_amp, signed_unit(o.x));
+        x = __fmul_rn(a.init_amp, signed_unit(o.x)) + 0.0f;
         y = __fmul_rn(a.init_amp, signed_unit(o.y));
     }
-
-    float* cur = phi_a;
-    float* nxt = phi_b;
-    cur[tid] = (VARIANT == MOQ_DSB) ? (x >= 0.0f ? 1.0f : -1.0f) : x;
+    phiA[tid] = phi_of<VARIANT>(x);
     __syncthreads();
 
-    const float dta0 = a.dt * a.a0;
-    float z0 = 0.0f, z1 = 0.0f, z2 = 0.0f, z3 = 0.0f;
-    for (int m = 0; m < a.T; ++m) {
+    const float dt = a.dt, kappa = a.kappa, dta0 = a.dt * a.a0, a0 = a.a0, a0inv = a.a0inv;
+    const float* sched = a.schedule;
+    const int T = a.T;
+    auto cm_at = [&](int m, float mf) -> float { return LINEAR ? fmaf(a0inv, mf, -a0) : (__ldg(sched + m) - a0); };
+    auto noise4 = [&](int m, float& e0, float& e1, float& e2, float& e3) {
         if (NOISE) {
-            if ((m & 3) == 0) {
-                const uint4 o = Philox4x32::block(make_uint4((uint32_t)(m >> 2), (uint32_t)i, (uint32_t)r, a.round32), a.key0, a.key1);
-                const float2 p = box_muller(o.x, o.y), q = box_muller(o.z, o.w);
-                z0 = p.x; z1 = p.y; z2 = q.x; z3 = q.y;
-            } else {
-                z0 = z1; z1 = z2; z2 = z3;
-            }
+            const uint4 o = Philox4x32::block(make_uint4((uint32_t)(m >> 2), (uint32_t)i, (uint32_t)r, a.round32), a.key0, a.key1);
+            const float2 p = box_muller(o.x, o.y), q = box_muller(o.z, o.w);
+            e0 = p.x; e1 = p.y; e2 = q.x; e3 = q.y;
         }
-        const float am = a.schedule ? __ldg(a.schedule + m) : a.a0 * (float)m * a.inv_Tm1;
-        float f = 0.0f;
-#pragma unroll
-        for (int d = 0; d < DMAX; ++d)
-            if (d < deg) f = fmaf(jc[d], cur[nb[d]], f);
-        const float drift = fmaf(-(a.a0 - am), x, f);
-        if (NOISE) {
-            const float nz = a.alpha * z0;
-            y = a.noise_sqrt_dt ? fmaf(a.sqrt_dt, nz, fmaf(a.dt, drift, y)) : fmaf(a.dt, drift + nz, y);
-        } else {
-            y = fmaf(a.dt, drift, y);
-        }
-        x = fmaf(dta0, y, x);
-        if (fabsf(x) > 1.0f) {  // inelastic wall
-            x = copysignf(1.0f, x);
-            y = 0.0f;
-        }
-        nxt[tid] = (VARIANT == MOQ_DSB) ? (x >= 0.0f ? 1.0f : -1.0f) : x;
-        __syncthreads();
-        float* t = cur;
-        cur = nxt;
-        nxt = t;
+    };
+    int m = 0;
+    float mf = 0.0f;
+    for (; m + 4 <= T; m += 4) {
+        float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f, e3 = 0.0f;
+        noise4(m, e0, e1, e2, e3);
+        sb_step<VARIANT, DMAX, NOISE>(phiA, phiB, tid, jc, nb, cm_at(m, mf), e0, dt, kappa, dta0, x, y);
+        sb_step<VARIANT, DMAX, NOISE>(phiB, phiA, tid, jc, nb, cm_at(m + 1, mf + 1.0f), e1, dt, kappa, dta0, x, y);
+        sb_step<VARIANT, DMAX, NOISE>(phiA, phiB, tid, jc, nb, cm_at(m + 2, mf + 2.0f), e2, dt, kappa, dta0, x, y);
+        sb_step<VARIANT, DMAX, NOISE>(phiB, phiA, tid, jc, nb, cm_at(m + 3, mf + 3.0f), e3, dt, kappa, dta0, x, y);
+        mf += 4.0f;
+    }
+    if (m < T) {  // the last T mod 4 steps (uniform over the block)
+        float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f, e3 = 0.0f;
+        noise4(m, e0, e1, e2, e3);
+        sb_step<VARIANT, DMAX, NOISE>(phiA, phiB, tid, jc, nb, cm_at(m, mf), e0, dt, kappa, dta0, x, y);
+        if (m + 1 < T) sb_step<VARIANT, DMAX, NOISE>(phiB, phiA, tid, jc, nb, cm_at(m + 1, mf + 1.0f), e1, dt, kappa, dta0, x, y);
+        if (m + 2 < T) sb_step<VARIANT, DMAX, NOISE>(phiA, phiB, tid, jc, nb, cm_at(m + 2, mf + 2.0f), e2, dt, kappa, dta0, x, y);
     }
 
     // readout s_i = sgn(x_i), sgn(0) = +1; bit set for s_i = -1
@@ -168,36 +194,43 @@ __global__ void __launch_bounds__(1024) k_sb_sparse(const SbArgs a)
     }
 }
 
-template <int VARIANT, int DMAX>
-cudaError_t launch_noise(const SbArgs& a, bool noise, dim3 grid, dim3 block, size_t smem, cudaStream_t st)
+template <int VARIANT, int DMAX, bool NOISE, bool LINEAR>
+cudaError_t launch_one(const SbArgs& a, dim3 grid, dim3 block, size_t smem, cudaStream_t st)
 {
-    if (noise) {
-        auto k = k_sb_sparse<VARIANT, DMAX, true>;
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<grid, block, smem, st>>>(a);
-    } else {
-        auto k = k_sb_sparse<VARIANT, DMAX, false>;
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<grid, block, smem, st>>>(a);
-    }
+    auto k = k_sb_sparse<VARIANT, DMAX, NOISE, LINEAR>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, block, smem, st>>>(a);
     return cudaGetLastError();
 }
 
+template <int VARIANT, int DMAX>
+cudaError_t launch_flags(const SbArgs& a, bool noise, bool linear, dim3 grid, dim3 block, size_t smem, cudaStream_t st)
+{
+    if (noise) return linear ? launch_one<VARIANT, DMAX, true, true>(a, grid, block, smem, st)
+                             : launch_one<VARIANT, DMAX, true, false>(a, grid, block, smem, st);
+    return linear ? launch_one<VARIANT, DMAX, false, true>(a, grid, block, smem, st)
+                  : launch_one<VARIANT, DMAX, false, false>(a, grid, block, smem, st);
+}
+
 template <int VARIANT>
-cudaError_t launch_variant(const SbArgs& a, int dmax, bool noise, dim3 grid, dim3 block, size_t smem, cudaStream_t st)
+cudaError_t launch_variant(const SbArgs& a, int dmax, bool noise, bool linear, dim3 grid, dim3 block, size_t smem,
+                           cudaStream_t st)
 {
     switch (dmax) {
-    case 4: return launch_noise<VARIANT, 4>(a, noise, grid, block, smem, st);
-    case 8: return launch_noise<VARIANT, 8>(a, noise, grid, block, smem, st);
-    default: return launch_noise<VARIANT, 16>(a, noise, grid, block, smem, st);
+    case 3: return launch_flags<VARIANT, 3>(a, noise, linear, grid, block, smem, st);
+    case 4: return launch_flags<VARIANT, 4>(a, noise, linear, grid, block, smem, st);
+    case 8: return launch_flags<VARIANT, 8>(a, noise, linear, grid, block, smem, st);
+    default: return launch_flags<VARIANT, 16>(a, noise, linear, grid, block, smem, st);
     }
 }
 
-// Replicas per block: the spin-major layout wants whole warps of one spin (Rb up to 32)
-// but also enough blocks to cover the 148 SMs when R is small.
+// Replicas per block: blocks of about 256 threads (several resident blocks per SM hide
+// each other's step barriers; measured best at n = 42), at most 32 replicas, and enough
+// blocks to cover the 148 SMs when R is small.
 int choose_rb(int n, int R)
 {
-    int rb = std::max(1, std::min(32, 1024 / n));
+    int rb = std::max(1, std::min(32, (256 + n / 2) / n));
     if (const char* env = getenv("MOQ_SB_RB")) {
         int v = atoi(env);
         if (v >= 1) rb = std::min(v, 1024 / n);
@@ -237,11 +270,9 @@ extern "C" int moq_sample(const moq_instance* inst, const float* lambda, int32_t
     a.lambda = lambda;
     a.dt = p->dt;
     a.a0 = p->a0;
-    a.alpha = p->alpha;
     a.init_amp = p->init_amp;
-    a.inv_Tm1 = p->steps > 1 ? 1.0f / (float)(p->steps - 1) : 0.0f;
-    a.sqrt_dt = sqrtf(p->dt);
-    a.noise_sqrt_dt = p->noise_sqrt_dt;
+    a.kappa = (p->noise_sqrt_dt ? sqrtf(p->dt) : p->dt) * p->alpha;
+    a.a0inv = p->steps > 1 ? p->a0 / (float)(p->steps - 1) : 0.0f;
     a.schedule = p->schedule;
     a.x_init = p->x_init;
     a.y_init = p->y_init;
@@ -252,12 +283,14 @@ extern "C" int moq_sample(const moq_instance* inst, const float* lambda, int32_t
     a.round32 = (uint32_t)round;
     a.bits = bits;
     a.Rb = choose_rb(a.n, R);
-    const int dmax = inst->max_degree <= 4 ? 4 : (inst->max_degree <= 8 ? 8 : 16);
+    const int md = inst->max_degree;
+    const int dmax = md <= 3 ? 3 : (md <= 4 ? 4 : (md <= 8 ? 8 : 16));
     const dim3 block(a.n * a.Rb), grid((unsigned)ceil_div(R, a.Rb));
-    const size_t smem = sb_smem_bytes(a.n, a.Rb, a.W);
+    const size_t smem = sb_smem_bytes(a.Rb, a.W);
     const bool noise = p->alpha != 0.0f;
-    cudaError_t e = (p->variant == MOQ_DSB) ? launch_variant<MOQ_DSB>(a, dmax, noise, grid, block, smem, as_stream(stream))
-                                            : launch_variant<MOQ_BSB>(a, dmax, noise, grid, block, smem, as_stream(stream));
+    const bool linear = p->schedule == nullptr;
+    cudaError_t e = (p->variant == MOQ_DSB) ? launch_variant<MOQ_DSB>(a, dmax, noise, linear, grid, block, smem, as_stream(stream))
+                                            : launch_variant<MOQ_BSB>(a, dmax, noise, linear, grid, block, smem, as_stream(stream));
     if (e != cudaSuccess) return cuda_fail(e, "moq_sample launch");
     return MOQ_OK;
 }

@@ -212,6 +212,19 @@ def test_hv_bit_exact(M, oracle, K, F, span):
     assert _hv_points(M, pts, ref) == oracle.hypervolume(pts, ref)
 
 
+@pytest.mark.parametrize("K,F", [(3, 7000), (4, 7000)])
+def test_hv_large_mostly_dominated(M, oracle, K, F):
+    # beyond the shared-memory fast path: many points, few of them on the front; the
+    # hypervolume of the whole set equals the oracle's on the oracle-filtered front
+    rng = np.random.default_rng(F + K)
+    pts = rng.integers(0, 1000, size=(F, K)).astype(np.int64)
+    front = rng.integers(900, 1100, size=(40, K)).astype(np.int64)
+    pts[rng.choice(F, size=40, replace=False)] = front
+    ref = np.zeros(K, np.int64)
+    keep = oracle.pareto_filter(pts)
+    assert _hv_points(M, pts, ref) == oracle.hypervolume(pts[keep], ref)
+
+
 def test_hv_edge_cases(M, oracle):
     ref = np.zeros(3, np.int64)
     assert _hv_points(M, np.zeros((0, 3), np.int64), ref) == 0
@@ -302,20 +315,33 @@ def test_initial_state_bit_exact(M, P, oracle):
     assert np.array_equal(s, np.where(want[..., 0] >= 0, 1, -1))
 
 
-def test_bsb_short_trajectory(M, P, oracle):
-    # without noise bSB is smooth: 25 FP32 steps stay close to the FP64 trajectory
+@pytest.mark.parametrize("T,variant,schedule", [(1, "bsb", False), (2, "bsb", False), (3, "bsb", True),
+                                                 (6, "bsb", False), (7, "bsb", True), (25, "bsb", False),
+                                                 (9, "dsb", False), (11, "dsb", True)])
+def test_short_trajectory(M, P, oracle, T, variant, schedule):
+    # without noise a few FP32 steps stay close to the FP64 trajectory (step counts that
+    # are not multiples of four exercise the unrolled loop's tail); dSB is compared only
+    # on replicas whose start has no spin within 1e-3 of the sign switch
     src = INSTANCES["heavyhex_K4"]()
     inst = P.Instance(src)
     R = 64
     lam = wl.dirichlet_lambdas(R, 4, 5)
     xo = torch.zeros((R, src.n), device="cuda")
     yo = torch.zeros((R, src.n), device="cuda")
-    p = M.moq_default_params(variant="bsb", steps=25, dt=0.5, x_out=xo, y_out=yo)
+    sched = np.linspace(0.0, 1.0, T) ** 2 if schedule else None
+    p = M.moq_default_params(variant=variant, steps=T, dt=0.5, x_out=xo, y_out=yo,
+                             schedule=None if sched is None else _dev(sched, torch.float32))
     bits = torch.zeros((R, 1), dtype=torch.int64, device="cuda")
     M.moq_sample(inst.handle, _dev(lam, torch.float32), R, p, 3, 0, bits)
-    ref = oracle.sb(src, lam.astype(np.float64), variant="bsb", steps=25, dt=0.5, seed=3)
-    assert np.abs(xo.cpu().numpy() - ref["x"]).max() < 1e-4
-    assert np.abs(yo.cpu().numpy() - ref["y"]).max() < 1e-4
+    ref = oracle.sb(src, lam.astype(np.float64), variant=variant, steps=T, dt=0.5, seed=3,
+                    schedule=None if sched is None else sched.astype(np.float32).astype(np.float64))
+    ok = np.ones(R, bool)
+    if variant == "dsb":
+        x0 = np.array([[oracle.initial_state(3, 0, r, i)[0] for i in range(src.n)] for r in range(R)])
+        ok = np.all(np.abs(x0) > 1e-3, axis=1)
+        assert ok.sum() >= R // 4
+    assert np.abs(xo.cpu().numpy()[ok] - ref["x"][ok]).max() < 1e-4
+    assert np.abs(yo.cpu().numpy()[ok] - ref["y"][ok]).max() < 1e-4
 
 
 @pytest.mark.parametrize("variant", ["dsb", "bsb"])
