@@ -274,6 +274,109 @@ __global__ void __launch_bounds__(kThreads) k_hv4(const int64_t* __restrict__ pt
     if (threadIdx.x == 0) ws.partial[blockIdx.x] = (i128)h4 * s;
 }
 
+__device__ __forceinline__ int block_excl_scan_int(int v, int* warp_sums, int* total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_sums[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int s = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += t;
+        }
+        if (lane < nw) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const int res = incl - v + (wid > 0 ? warp_sums[wid - 1] : 0);
+    *total = warp_sums[nw - 1];
+    __syncthreads();
+    return res;
+}
+
+// K = 4 with the slab's points compacted: block t first gathers the t+1 points of rank_3
+// <= t into shared memory twice -- in y_0 order (the staircase walk) and in y_2 order
+// (the sub-slabs) -- so every walk touches only those points. Shared memory: 32 B per point.
+constexpr int kHv4CompactMax = 6144;
+
+__global__ void __launch_bounds__(kThreads) k_hv4_compact(const int64_t* __restrict__ pts, int64_t F, Ref4 ref, HvWs ws)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    int64_t* s_u0 = reinterpret_cast<int64_t*>(sm);
+    int64_t* s_u1 = s_u0 + F;
+    int64_t* s_v2 = s_u1 + F;
+    int32_t* s_r2 = reinterpret_cast<int32_t*>(s_v2 + F);
+    int32_t* s_q2 = s_r2 + F;
+    __shared__ i128 red[kThreads];
+    __shared__ int warp_sums[kThreads / 32];
+    const int Fv = *ws.fv;
+    const int64_t t = blockIdx.x;
+    const int32_t* ord0 = ws.order;
+    const int32_t* ord2 = ws.order + 2 * F;
+    const int32_t* ord3 = ws.order + 3 * F;
+    const int32_t* rank2 = ws.rank + 2 * F;
+    const int32_t* rank3 = ws.rank + 3 * F;
+    int64_t h4 = 0;
+    if (t < Fv) {
+        const int64_t top = pts[(int64_t)ord3[t] * 4 + 3];
+        const int64_t below = (t + 1 < Fv) ? pts[(int64_t)ord3[t + 1] * 4 + 3] : ref.r[3];
+        h4 = top - below;
+    }
+    if (h4 <= 0) {  // uniform over the block
+        if (threadIdx.x == 0) ws.partial[blockIdx.x] = 0;
+        return;
+    }
+    int cnt0 = 0, cnt2 = 0;
+    for (int base = 0; base < Fv; base += kThreads) {
+        const int q = base + threadIdx.x;
+        const int p0 = q < Fv ? ord0[q] : 0, p2 = q < Fv ? ord2[q] : 0;
+        const int f0 = (q < Fv && rank3[p0] <= t) ? 1 : 0, f2 = (q < Fv && rank3[p2] <= t) ? 1 : 0;
+        int tot0, tot2;
+        const int pos0 = cnt0 + block_excl_scan_int(f0, warp_sums, &tot0);
+        const int pos2 = cnt2 + block_excl_scan_int(f2, warp_sums, &tot2);
+        if (f0) {
+            s_u0[pos0] = pts[(int64_t)p0 * 4];
+            s_u1[pos0] = pts[(int64_t)p0 * 4 + 1];
+            s_r2[pos0] = rank2[p0];
+        }
+        if (f2) {
+            s_v2[pos2] = pts[(int64_t)p2 * 4 + 2];
+            s_q2[pos2] = rank2[p2];
+        }
+        cnt0 += tot0;
+        cnt2 += tot2;
+    }
+    __syncthreads();
+    const int c = cnt0;  // == t + 1
+    i128 acc = 0;
+    for (int s = threadIdx.x; s < c; s += kThreads) {
+        const int64_t below = s + 1 < c ? s_v2[s + 1] : ref.r[2];
+        const int64_t h3 = s_v2[s] - below;
+        if (h3 > 0) {
+            const int32_t rs = s_q2[s];
+            i128 area = 0;
+            int64_t best1 = ref.r[1];
+            for (int q = 0; q < c; ++q) {
+                const int64_t u1 = s_u1[q];
+                if (s_r2[q] <= rs && u1 > best1) {
+                    area += (i128)(s_u0[q] - ref.r[0]) * (i128)(u1 - best1);
+                    best1 = u1;
+                }
+            }
+            acc += (i128)h3 * area;
+        }
+    }
+    const i128 sum = block_sum(acc, red);
+    if (threadIdx.x == 0) ws.partial[blockIdx.x] = (i128)h4 * sum;
+}
+
 // Sum of the block partials; flags bit 0 = the side-length product reaches 2^125.
 __global__ void __launch_bounds__(kThreads) k_hv_final(const int64_t* __restrict__ pts, int64_t F, int K, Ref4 ref,
                                                        int64_t nparts, HvWs ws)
@@ -341,7 +444,13 @@ int moq_hypervolume_points(const int64_t* pts, int64_t F, int32_t K, const int64
         break;
     default:
         k_hv_rank<4><<<gF, kThreads, 0, st>>>(pts, F, r, ws);
-        k_hv4<<<(unsigned)F, kThreads, 0, st>>>(pts, F, r, ws);
+        if (F <= kHv4CompactMax) {
+            const size_t smem = (size_t)32 * F;
+            MOQ_CUDA_TRY(cudaFuncSetAttribute(k_hv4_compact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_hv4_compact<<<(unsigned)F, kThreads, smem, st>>>(pts, F, r, ws);
+        } else {
+            k_hv4<<<(unsigned)F, kThreads, 0, st>>>(pts, F, r, ws);
+        }
         nparts = F;
         break;
     }

@@ -8,8 +8,10 @@
 //    equal candidate has a lower index;
 //  - member a survives iff no candidate dominates it (a dominated member is dominated by
 //    some surviving vector too, since domination is transitive and the sets are finite).
-// Both tests are all-pairs over shared-memory tiles with a block-wide early exit once
-// every thread's vector is known to be dominated. Survivors are compacted in order --
+// Both tests are all-pairs over shared-memory tiles on a 2-D grid (a tile of vectors x a
+// chunk of the vectors they are compared with, so even one tile of candidates fills the
+// GPU), with a block-wide early exit once every thread's vector is known to be dominated;
+// blocks only ever set "dominated" flags (zeroed per call). Survivors are compacted in order --
 // old members first, then candidates by index -- into the second buffer of the archive
 // by a block scan, so the result is deterministic. Candidate representatives are
 // canonicalised to s_0 = +1 (C(s) = C(-s)).
@@ -24,9 +26,33 @@ constexpr int kTile = 256;
 constexpr int kScanBlock = 1024;
 constexpr unsigned kFull = 0xffffffffu;
 
+constexpr int kChunk = 1024;   // candidates compared by one block of the 2-D grid
+constexpr int kArchChunks = 8; // archive slices per candidate tile
+
+// Dominance of one candidate u (registers) by any vector of a shared-memory tile.
+template <int KT, bool ARCHIVE>
+__device__ __forceinline__ bool tile_dominates(const int64_t (*tile)[KT], int cnt, const int64_t (&u)[KT], int64_t tile_base,
+                                               int64_t c)
+{
+    for (int t = 0; t < cnt; ++t) {
+        bool ge = true, gt = false;
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            ge &= tile[t][k] >= u[k];
+            gt |= tile[t][k] > u[k];
+        }
+        // archive members win ties (lower global index); among candidates the lower index wins
+        if (ge && (ARCHIVE || gt || tile_base + t < c)) return true;
+    }
+    return false;
+}
+
+// Candidates: blockIdx.x = tile of 256 candidates, blockIdx.y = what they are compared
+// with: y < kArchChunks strides over archive tiles, y >= kArchChunks takes candidate
+// chunk y - kArchChunks. Any block that finds a dominator sets dom_cand (zeroed per call).
 template <int KT>
-__global__ void __launch_bounds__(kTile) k_filter_candidates(const int64_t* __restrict__ arch, const int64_t* __restrict__ d_count,
-                                                             const int64_t* __restrict__ cand, int64_t M, int32_t* flag_cand)
+__global__ void __launch_bounds__(kTile) k_dominated_candidates(const int64_t* __restrict__ arch, const int64_t* __restrict__ d_count,
+                                                                const int64_t* __restrict__ cand, int64_t M, int32_t* dom_cand)
 {
     __shared__ int64_t tile[kTile][KT];
     const int tid = threadIdx.x;
@@ -35,72 +61,57 @@ __global__ void __launch_bounds__(kTile) k_filter_candidates(const int64_t* __re
     int64_t u[KT];
 #pragma unroll
     for (int k = 0; k < KT; ++k) u[k] = act ? cand[c * KT + k] : 0;
-    bool dropped = !act;
-    const int64_t F = *d_count;
-
-    for (int64_t base = 0; base < F; base += kTile) {
-        if (__syncthreads_and(dropped)) break;
-        const int cnt = (int)min((int64_t)kTile, F - base);
-        if (tid < cnt) {
+    bool dropped = !act || dom_cand[c];
+    const bool was = dropped;
+    if (blockIdx.y < kArchChunks) {
+        const int64_t F = *d_count;
+        for (int64_t base = (int64_t)blockIdx.y * kTile; base < F; base += (int64_t)kArchChunks * kTile) {
+            if (__syncthreads_and(dropped)) break;
+            const int cnt = (int)min((int64_t)kTile, F - base);
+            if (tid < cnt) {
 #pragma unroll
-            for (int k = 0; k < KT; ++k) tile[tid][k] = arch[(base + tid) * KT + k];
-        }
-        __syncthreads();
-        if (!dropped) {
-            for (int t = 0; t < cnt; ++t) {
-                bool ge = true;
-#pragma unroll
-                for (int k = 0; k < KT; ++k) ge &= tile[t][k] >= u[k];
-                if (ge) {
-                    dropped = true;
-                    break;
-                }
+                for (int k = 0; k < KT; ++k) tile[tid][k] = arch[(base + tid) * KT + k];
             }
+            __syncthreads();
+            if (!dropped) dropped = tile_dominates<KT, true>(tile, cnt, u, base, c);
+        }
+    } else {
+        const int64_t lo = (int64_t)(blockIdx.y - kArchChunks) * kChunk, hi = min(M, lo + kChunk);
+        for (int64_t base = lo; base < hi; base += kTile) {
+            if (__syncthreads_and(dropped)) break;
+            const int cnt = (int)min((int64_t)kTile, hi - base);
+            if (tid < cnt) {
+#pragma unroll
+                for (int k = 0; k < KT; ++k) tile[tid][k] = cand[(base + tid) * KT + k];
+            }
+            __syncthreads();
+            if (!dropped) dropped = tile_dominates<KT, false>(tile, cnt, u, base, c);
         }
     }
-    for (int64_t base = 0; base < M; base += kTile) {
-        if (__syncthreads_and(dropped)) break;
-        const int cnt = (int)min((int64_t)kTile, M - base);
-        if (tid < cnt) {
-#pragma unroll
-            for (int k = 0; k < KT; ++k) tile[tid][k] = cand[(base + tid) * KT + k];
-        }
-        __syncthreads();
-        if (!dropped) {
-            for (int t = 0; t < cnt; ++t) {
-                bool ge = true, gt = false;
-#pragma unroll
-                for (int k = 0; k < KT; ++k) {
-                    ge &= tile[t][k] >= u[k];
-                    gt |= tile[t][k] > u[k];
-                }
-                if (ge && (gt || base + t < c)) {
-                    dropped = true;
-                    break;
-                }
-            }
-        }
-    }
-    if (act) flag_cand[c] = dropped ? 0 : 1;
+    if (act && dropped && !was) dom_cand[c] = 1;
 }
 
+// Archive members: blockIdx.x strides over archive tiles, blockIdx.y = candidate chunk;
+// a member is dropped when a candidate dominates it strictly.
 template <int KT>
-__global__ void __launch_bounds__(kTile) k_filter_archive(const int64_t* __restrict__ arch, const int64_t* __restrict__ d_count,
-                                                          const int64_t* __restrict__ cand, int64_t M, int32_t* flag_arch)
+__global__ void __launch_bounds__(kTile) k_dominated_archive(const int64_t* __restrict__ arch, const int64_t* __restrict__ d_count,
+                                                             const int64_t* __restrict__ cand, int64_t M, int32_t* dom_arch)
 {
     __shared__ int64_t tile[kTile][KT];
     const int tid = threadIdx.x;
     const int64_t F = *d_count;
+    const int64_t lo = (int64_t)blockIdx.y * kChunk, hi = min(M, lo + kChunk);
     for (int64_t blk = blockIdx.x; blk * kTile < F; blk += gridDim.x) {
         const int64_t a = blk * kTile + tid;
         const bool act = a < F;
         int64_t u[KT];
 #pragma unroll
         for (int k = 0; k < KT; ++k) u[k] = act ? arch[a * KT + k] : 0;
-        bool dropped = !act;
-        for (int64_t base = 0; base < M; base += kTile) {
+        bool dropped = !act || dom_arch[a];
+        const bool was = dropped;
+        for (int64_t base = lo; base < hi; base += kTile) {
             if (__syncthreads_and(dropped)) break;
-            const int cnt = (int)min((int64_t)kTile, M - base);
+            const int cnt = (int)min((int64_t)kTile, hi - base);
             if (tid < cnt) {
 #pragma unroll
                 for (int k = 0; k < KT; ++k) tile[tid][k] = cand[(base + tid) * KT + k];
@@ -121,7 +132,7 @@ __global__ void __launch_bounds__(kTile) k_filter_archive(const int64_t* __restr
                 }
             }
         }
-        if (act) flag_arch[a] = dropped ? 0 : 1;
+        if (act && dropped && !was) dom_arch[a] = 1;
         __syncthreads();
     }
 }
@@ -133,10 +144,10 @@ __device__ __forceinline__ int32_t flag_at(int64_t b, int t, int64_t nbA, int64_
 {
     if (b < nbA) {
         const int64_t q = b * kScanBlock + t;
-        return q < F ? flag_arch[q] : 0;
+        return q < F ? 1 - flag_arch[q] : 0;
     }
     const int64_t c = (b - nbA) * kScanBlock + t;
-    return c < M ? flag_cand[c] : 0;
+    return c < M ? 1 - flag_cand[c] : 0;
 }
 
 __device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t* warp_sums, int32_t* total)
@@ -296,10 +307,16 @@ __global__ void k_set_count(int64_t cap, int64_t nb, const int64_t* blockoff, in
 template <int KT>
 cudaError_t launch_filters(moq_archive* a, const int64_t* cuts, int64_t M, cudaStream_t st)
 {
-    if (M > 0)
-        k_filter_candidates<KT><<<(unsigned)ceil_div(M, kTile), kTile, 0, st>>>(a->cuts[a->cur], a->d_count, cuts, M, a->flag_cand);
-    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(a->cap, kTile), 148 * 8));
-    k_filter_archive<KT><<<g, kTile, 0, st>>>(a->cuts[a->cur], a->d_count, cuts, M, a->flag_arch);
+    cudaError_t e = cudaMemsetAsync(a->flag_arch, 0, sizeof(int32_t) * a->cap, st);
+    if (e == cudaSuccess && M > 0) e = cudaMemsetAsync(a->flag_cand, 0, sizeof(int32_t) * M, st);
+    if (e != cudaSuccess) return e;
+    if (M > 0) {
+        const unsigned nchunks = (unsigned)ceil_div(M, kChunk);
+        k_dominated_candidates<KT><<<dim3((unsigned)ceil_div(M, kTile), kArchChunks + nchunks), kTile, 0, st>>>(
+            a->cuts[a->cur], a->d_count, cuts, M, a->flag_cand);
+        const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(a->cap, kTile), 32));
+        k_dominated_archive<KT><<<dim3(gx, nchunks), kTile, 0, st>>>(a->cuts[a->cur], a->d_count, cuts, M, a->flag_arch);
+    }
     return cudaGetLastError();
 }
 
