@@ -77,6 +77,7 @@ typedef struct moq_sample_params {
     const float* y_init;   /* device R x n, or NULL (zero when x_init is given) */
     float* x_out;          /* device R x n final positions, or NULL */
     float* y_out;          /* device R x n final momenta, or NULL */
+    uint32_t replica_offset; /* added to r in the Philox replica counter (batches: the instance's offset) */
 } moq_sample_params;
 
 /* Result of moq_hypervolume: value = hi * 2^64 + (uint64)lo (a signed 128-bit int). */
@@ -111,13 +112,40 @@ int moq_instance_get_info(const moq_instance* inst, moq_instance_info* out);
  *   the attractors minimise H_total, i.e. maximise the weighted cut);
  *   y += dt*(-(a0 - a_m) x + force + alpha*eta); x += dt*a0*y; |x| > 1 -> x = sgn x, y = 0;
  *   s = sgn(x) with sgn(0) = +1, written to bits (device, R x W words).
- * eta comes from Philox4x32-10 with key = seed and counter (m >> 2, i, r, round) through
- * Box-Muller; the start state from counter (0xFFFFFFFF, i, r, round). `seed` and
+ * eta comes from Philox4x32-10 with key = seed and counter (m >> 2, i, o + r, round) through
+ * Box-Muller (o = p->replica_offset); the start state from counter (0xFFFFFFFF, i, o + r, round). `seed` and
  * `round` fully determine the output on a given GPU build.
  * Errors: MOQ_ERR_ARG (R < 0, steps < 0, bad variant, NULL lambda/bits with R > 0),
  * MOQ_ERR_UNSUPPORTED (n > 1024 or max degree > 16), MOQ_ERR_CUDA. Asynchronous. */
 int moq_sample(const moq_instance* inst, const float* lambda, int32_t R, const moq_sample_params* p,
                uint64_t seed, uint64_t round, uint64_t* bits, void* stream);
+
+/* ---- batched sampling of many instances (the paper runs every weight vector and replica
+ * "in parallel in a single run", "Results and discussion") ------------------------------
+ * A batch fixes `count` instances (same K, n <= 1024, max degree <= 8; host array of
+ * handles, kept alive by the caller) and replicas[b] replicas of each. Inputs and outputs are
+ * concatenated: lambda_all holds sum_b replicas[b] rows of K floats, instance b starting at
+ * row replica_offsets[b]; bits_all holds instance b's replicas[b] x W_b words from word
+ * word_offsets[b] (moq_batch_layout fills both arrays, count + 1 entries each). One
+ * persistent launch runs every (instance, replica block) work item, longest first, from a
+ * device queue; instance b's replicas use Philox replica counters replica_offsets[b] + r, so
+ * the result equals moq_sample on instance b with p->replica_offset = replica_offsets[b].
+ * The tile shape (threads per block, spin slots per thread) affects speed only; results
+ * do not depend on it. moq_batch_create allocates the work tables (device); errors:
+ * MOQ_ERR_ARG, MOQ_ERR_UNSUPPORTED, MOQ_ERR_OOM. */
+typedef struct moq_batch moq_batch;
+int moq_batch_create(const moq_instance* const* insts, int32_t count, const int32_t* replicas, moq_batch** out);
+void moq_batch_destroy(moq_batch* b);
+int moq_batch_layout(const moq_batch* b, int64_t* replica_offsets, int64_t* word_offsets);
+/* block_threads in {256, 512, 1024}, slots_per_thread in {1, 2}, block_threads *
+ * slots_per_thread >= the largest n; *items_out (may be NULL) = work items. Synchronous. */
+int moq_batch_set_tiles(moq_batch* b, int32_t block_threads, int32_t slots_per_thread, int32_t* items_out);
+/* Samples every replica of every instance (asynchronous; p's state arrays must be NULL). */
+int moq_sample_batch(moq_batch* b, const float* lambda_all, const moq_sample_params* p, uint64_t seed, uint64_t round,
+                     uint64_t* bits_all, void* stream);
+/* Exact cut values (Eq. single_obj) of every sample: cuts_all row replica_offsets[b] + m
+ * holds C(s) of instance b's sample m (device, sum replicas x K int64). Asynchronous. */
+int moq_evaluate_cuts_batch(const moq_batch* b, const uint64_t* bits_all, int64_t* cuts_all, void* stream);
 
 /* ---- a6: exact cut values, Eq. (single_obj) -------------------------------------
  * cuts[m*K + k] = C_k(s^(m)) = sum over edges with s_i != s_j of J^(k)_ij, for the M

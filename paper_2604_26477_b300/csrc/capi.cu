@@ -62,6 +62,7 @@ void moq_default_params(moq_sample_params* p)
     p->y_init = nullptr;
     p->x_out = nullptr;
     p->y_out = nullptr;
+    p->replica_offset = 0;
 }
 
 }  // extern "C"

@@ -13,7 +13,7 @@
 #include <algorithm>
 #include <stdlib.h>
 
-#include "moq_common.cuh"
+#include "sb_common.cuh"
 
 namespace moq {
 namespace {
@@ -36,7 +36,7 @@ struct SbArgs {
     const float* y_init;
     float* x_out;
     float* y_out;
-    uint32_t key0, key1, round32;
+    uint32_t key0, key1, round32, rep_off;
     uint64_t* bits;
 };
 
@@ -47,15 +47,6 @@ __host__ __device__ inline size_t sb_smem_bytes(int Rb, int W)
     return sizeof(float) * 2 * kPhiStride + align_up(sizeof(unsigned) * 2 * Rb, 16) + sizeof(unsigned long long) * (size_t)Rb * W;
 }
 
-// phi(x): sgn(x) with sgn(0) = +1 for dSB (x is never -0 here: the start state is
-// sanitised and the update cannot produce -0 from +-nonzero or +0), x for bSB.
-template <int VARIANT>
-__device__ __forceinline__ float phi_of(float x)
-{
-    if (VARIANT == MOQ_DSB) return __int_as_float(0x3f800000 | (__float_as_int(x) & 0x80000000));
-    return x;
-}
-
 // One Euler step of one spin: force from the shared-memory phi buffer `rd`, symplectic
 // update, inelastic wall, phi into `wr`, then the block barrier.
 template <int VARIANT, int DMAX, bool NOISE>
@@ -63,17 +54,10 @@ __device__ __forceinline__ void sb_step(const float* rd, float* wr, int tid, con
                                         const int (&nb)[DMAX], float cm, float eta, float dt, float kappa, float dta0,
                                         float& x, float& y)
 {
-    float f = 0.0f;
+    float f = 0.0f;  // c0 sum_j (-J(c)_ij) phi(x_j)
 #pragma unroll
     for (int d = 0; d < DMAX; ++d) f = fmaf(jc[d], rd[nb[d]], f);
-    const float drift = fmaf(cm, x, f);  // -(a0 - a_m) x + c0 sum_j (-J(c)_ij) phi(x_j)
-    y = fmaf(dt, drift, y);
-    if (NOISE) y = fmaf(kappa, eta, y);
-    x = fmaf(dta0, y, x);
-    if (fabsf(x) > 1.0f) {  // inelastic wall
-        x = copysignf(1.0f, x);
-        y = 0.0f;
-    }
+    sb_update<NOISE>(f, cm, eta, dt, kappa, dta0, x, y);
     wr[tid] = phi_of<VARIANT>(x);
     __syncthreads();
 }
@@ -141,7 +125,7 @@ __global__ void __launch_bounds__(1024) k_sb_sparse(const SbArgs a)
         x = (active ? a.x_init[(int64_t)r * n + i] : 0.0f) + 0.0f;
         y = (active && a.y_init) ? a.y_init[(int64_t)r * n + i] : 0.0f;
     } else {
-        const uint4 o = Philox4x32::block(make_uint4(0xFFFFFFFFu, (uint32_t)i, (uint32_t)r, a.round32), a.key0, a.key1);
+        const uint4 o = Philox4x32::block(make_uint4(0xFFFFFFFFu, (uint32_t)i, a.rep_off + (uint32_t)r, a.round32), a.key0, a.key1);
         x = __fmul_rn(a.init_amp, signed_unit(o.x)) + 0.0f;
         y = __fmul_rn(a.init_amp, signed_unit(o.y));
     }
@@ -154,7 +138,7 @@ __global__ void __launch_bounds__(1024) k_sb_sparse(const SbArgs a)
     auto cm_at = [&](int m, float mf) -> float { return LINEAR ? fmaf(a0inv, mf, -a0) : (__ldg(sched + m) - a0); };
     auto noise4 = [&](int m, float& e0, float& e1, float& e2, float& e3) {
         if (NOISE) {
-            const uint4 o = Philox4x32::block(make_uint4((uint32_t)(m >> 2), (uint32_t)i, (uint32_t)r, a.round32), a.key0, a.key1);
+            const uint4 o = Philox4x32::block(make_uint4((uint32_t)(m >> 2), (uint32_t)i, a.rep_off + (uint32_t)r, a.round32), a.key0, a.key1);
             const float2 p = box_muller(o.x, o.y), q = box_muller(o.z, o.w);
             e0 = p.x; e1 = p.y; e2 = q.x; e3 = q.y;
         }
@@ -281,6 +265,7 @@ extern "C" int moq_sample(const moq_instance* inst, const float* lambda, int32_t
     a.key0 = (uint32_t)seed;
     a.key1 = (uint32_t)(seed >> 32);
     a.round32 = (uint32_t)round;
+    a.rep_off = p->replica_offset;
     a.bits = bits;
     a.Rb = choose_rb(a.n, R);
     const int md = inst->max_degree;

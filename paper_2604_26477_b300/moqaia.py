@@ -44,7 +44,7 @@ class moq_sample_params(C.Structure):
     _fields_ = [("variant", C.c_int32), ("steps", C.c_int32), ("dt", C.c_float), ("a0", C.c_float),
                 ("alpha", C.c_float), ("init_amp", C.c_float), ("noise_sqrt_dt", C.c_int32),
                 ("schedule", C.c_void_p), ("x_init", C.c_void_p), ("y_init", C.c_void_p),
-                ("x_out", C.c_void_p), ("y_out", C.c_void_p)]
+                ("x_out", C.c_void_p), ("y_out", C.c_void_p), ("replica_offset", C.c_uint32)]
 
 
 class moq_hv(C.Structure):
@@ -80,6 +80,12 @@ _sigs = {
     "moq_hypervolume_points_noalloc": (C.c_int, [_vp, _i64, _i32, _vp, C.POINTER(moq_hv), _vp]),
     "moq_lambda_das_dennis": (C.c_int, [_i32, _i32, _i32, _vp, _i64, C.POINTER(_i64), _vp]),
     "moq_lambda_dirichlet": (C.c_int, [_i32, _i32, _u64, _u64, _vp, _vp]),
+    "moq_batch_create": (C.c_int, [_vp, _i32, _vp, C.POINTER(_vp)]),
+    "moq_batch_destroy": (None, [_vp]),
+    "moq_batch_layout": (C.c_int, [_vp, _vp, _vp]),
+    "moq_batch_set_tiles": (C.c_int, [_vp, _i32, _i32, C.POINTER(_i32)]),
+    "moq_sample_batch": (C.c_int, [_vp, _vp, C.POINTER(moq_sample_params), _u64, _u64, _vp, _vp]),
+    "moq_evaluate_cuts_batch": (C.c_int, [_vp, _vp, _vp, _vp]),
     "moq_strerror": (C.c_char_p, [C.c_int]),
     "moq_last_error_message": (C.c_char_p, []),
 }
@@ -256,6 +262,44 @@ def moq_hypervolume_points(pts, F, K, ref, workspace, stream=None) -> int:
     _check(_lib.moq_hypervolume_points(_dptr(pts, "pts", i64), F, K, pref, _dptr(workspace, "workspace"),
                                        C.byref(out), _stream(stream)), "moq_hypervolume_points")
     return out.value()
+
+
+def moq_batch_create(instances, replicas) -> C.c_void_p:
+    arr = (C.c_void_p * len(instances))(*[h.value if isinstance(h, C.c_void_p) else h for h in instances])
+    reps, preps = _hptr(replicas, np.int32)
+    h = C.c_void_p()
+    _check(_lib.moq_batch_create(arr, len(instances), preps, C.byref(h)), "moq_batch_create")
+    return h
+
+
+def moq_batch_destroy(h):
+    _lib.moq_batch_destroy(h)
+
+
+def moq_batch_layout(h, count):
+    """(replica_offsets, word_offsets), each count + 1 int64 entries."""
+    ro = np.zeros(count + 1, np.int64)
+    wo = np.zeros(count + 1, np.int64)
+    _check(_lib.moq_batch_layout(h, ro.ctypes.data_as(_vp), wo.ctypes.data_as(_vp)), "moq_batch_layout")
+    return ro, wo
+
+
+def moq_batch_set_tiles(h, block_threads, slots_per_thread) -> int:
+    items = C.c_int32()
+    _check(_lib.moq_batch_set_tiles(h, block_threads, slots_per_thread, C.byref(items)), "moq_batch_set_tiles")
+    return int(items.value)
+
+
+def moq_sample_batch(h, lam_all, params, seed, round_, bits_all, stream=None):
+    f32, _, u64 = _torch_types()
+    _check(_lib.moq_sample_batch(h, _dptr(lam_all, "lambda_all", f32), C.byref(params), seed, round_,
+                                 _dptr(bits_all, "bits_all", u64), _stream(stream)), "moq_sample_batch")
+
+
+def moq_evaluate_cuts_batch(h, bits_all, cuts_all, stream=None):
+    _, i64, u64 = _torch_types()
+    _check(_lib.moq_evaluate_cuts_batch(h, _dptr(bits_all, "bits_all", u64), _dptr(cuts_all, "cuts_all", i64),
+                                        _stream(stream)), "moq_evaluate_cuts_batch")
 
 
 def moq_hypervolume_noalloc_max_points() -> int:

@@ -72,6 +72,57 @@ class Archive:
             pass
 
 
+class Batch:
+    """Many instances sampled by one persistent launch (``moq_batch_create``)."""
+
+    def __init__(self, instances, replicas, device="cuda"):
+        self.instances = instances  # Instance objects, kept alive for the batch's lifetime
+        self.replicas = np.asarray(replicas, np.int32)
+        self.K = instances[0].K
+        self.handle = M.moq_batch_create([h.handle for h in instances], self.replicas)
+        self.rep_off, self.word_off = M.moq_batch_layout(self.handle, len(instances))
+        self.total_R = int(self.rep_off[-1])
+        self.lam = torch.zeros((self.total_R, self.K), dtype=torch.float32, device=device)
+        self.bits = torch.zeros(int(self.word_off[-1]), dtype=torch.int64, device=device)
+        self.cuts = torch.zeros((self.total_R, self.K), dtype=torch.int64, device=device)
+        self.tile = None
+
+    def tune(self, params, probe_steps=64):
+        from . import autotune
+        self.tile, timings = autotune.tune_batch(self.handle, [h.n for h in self.instances], self.replicas, self.K,
+                                                 self.lam, self.bits, params, probe_steps=probe_steps)
+        return self.tile, timings
+
+    def set_tiles(self, block_threads, slots_per_thread):
+        self.tile = (block_threads, slots_per_thread)
+        return M.moq_batch_set_tiles(self.handle, block_threads, slots_per_thread)
+
+    def sample(self, params, seed, round_, stream=None):
+        M.moq_sample_batch(self.handle, self.lam, params, seed, round_, self.bits, stream)
+
+    def evaluate_cuts(self, stream=None):
+        M.moq_evaluate_cuts_batch(self.handle, self.bits, self.cuts, stream)
+
+    def bits_of(self, b):
+        """Instance b's packed samples as a (replicas, W) view."""
+        W = self.instances[b].W
+        return self.bits[int(self.word_off[b]):int(self.word_off[b + 1])].view(int(self.replicas[b]), W)
+
+    def cuts_of(self, b):
+        return self.cuts[int(self.rep_off[b]):int(self.rep_off[b + 1])]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            M.moq_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class RoundBuffers:
     """Device buffers of one sampling round of R replicas."""
 
