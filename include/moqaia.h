@@ -147,6 +147,28 @@ int moq_sample_batch(moq_batch* b, const float* lambda_all, const moq_sample_par
  * holds C(s) of instance b's sample m (device, sum replicas x K int64). Asynchronous. */
 int moq_evaluate_cuts_batch(const moq_batch* b, const uint64_t* bits_all, int64_t* cuts_all, void* stream);
 
+/* ---- a3 dense: tensor-core sampler (same dynamics as moq_sample; the force
+ * c0 sum_k c_k (J^(k) Phi)_i is a matrix product) -----------------------------------------
+ * moq_dense_create copies the instance's couplings into K zero-padded n_pad x n_pad BF16
+ * matrices (n_pad = n rounded up to 128; integers |J| <= 256 are exact) and allocates the
+ * replica state for up to max_replicas (x, y FP32 and two BF16 phi buffers, each
+ * ceil(max_replicas/128)*128 x n_pad). K <= 4, n <= 16384. The instance must outlive it.
+ * moq_sample_dense runs T step kernels (tcgen05.mma BF16 -> FP32 products for every
+ * objective, fused update/wall/phi epilogue) on `stream`, then writes the packed signs
+ * (and x_out/y_out if given). Differences from moq_sample: phi is rounded to BF16 for the
+ * products (exact for dSB), the force is combined as -c0 sum_k c_k G_k, and the noise of
+ * step m for replica r is Gaussian number r & 3 of Philox(key = seed, counter = (m, i,
+ * 2^30 + (r >> 2), round)); the start state uses the same counter as moq_sample.
+ * replica_offset must be 0. Errors: MOQ_ERR_ARG, MOQ_ERR_UNSUPPORTED, MOQ_ERR_OOM,
+ * MOQ_ERR_CUDA; a device wait that ran out of its 2 s budget is reported as
+ * MOQ_ERR_TIMEOUT by moq_dense_status (synchronises, clears the flag). */
+typedef struct moq_dense moq_dense;
+int moq_dense_create(const moq_instance* inst, int32_t max_replicas, moq_dense** out);
+void moq_dense_destroy(moq_dense* d);
+int moq_sample_dense(moq_dense* d, const float* lambda, int32_t R, const moq_sample_params* p, uint64_t seed, uint64_t round,
+                     uint64_t* bits, void* stream);
+int moq_dense_status(moq_dense* d, void* stream);
+
 /* ---- a6: exact cut values, Eq. (single_obj) -------------------------------------
  * cuts[m*K + k] = C_k(s^(m)) = sum over edges with s_i != s_j of J^(k)_ij, for the M
  * packed configurations bits (device, M x W) into cuts (device, M x K int64).

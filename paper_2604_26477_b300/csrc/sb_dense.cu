@@ -1,0 +1,503 @@
+// Dense NI-SB on the 5th-generation tensor cores (SB equations and Eq. NI-SB,
+// "Simulated Bifurcation with Gaussian noise"): for dense couplings the force
+// c0 sum_j J(c)_ij phi(x_j) = c0 sum_k c_k (J^(k) Phi)_i is a matrix product, so every
+// step computes G_k = J^(k) Phi for all K objectives with tcgen05.mma and applies the
+// symplectic update, the wall and the next phi in the epilogue.
+//
+// Step kernel, one CTA per tile of 128 spins (M) x 128 replicas (N):
+//  - the K-dimension (spins j) is walked in chunks of 64: J^(k)[i0:+128, j0:+64] for each
+//    objective and Phi[r0:+128, j0:+64] are copied into shared memory (cp.async, 16 B per
+//    thread, two stages) in the 128-byte-swizzled K-major layout the tensor core reads;
+//  - one thread issues tcgen05.mma (BF16 x BF16 -> FP32, M=128, N=128, K=16) into one TMEM
+//    accumulator per objective (K x 128 of the 512 columns) and tcgen05.commit signals an
+//    mbarrier per stage, so the copy of chunk c+1 overlaps the products of chunk c;
+//  - the epilogue (8 warps; warp w reads TMEM lanes 32*(w%4).. of columns 64*(w/4)..) forms
+//    f = -c0_r sum_k c_rk G_k[i, r], updates x, y (FP32, in HBM), applies the wall and
+//    writes phi(x) as BF16 for the next step.
+// Every wait on an mbarrier is bounded in time (globaltimer); on time-out the kernel records
+// an error flag, waits (bounded) for the products it issued, frees its TMEM and returns.
+//
+// Exactness: J^(k) is rounded to BF16 (integers |J| <= 256 are exact); with dSB phi = +-1
+// is exact, so G_k is an exact integer sum below 2^24 for |J| <= 256; bSB rounds x to BF16.
+// Noise: Gaussian number (r & 3) of Philox4x32-10(key = seed, counter = (m, i, 2^30 +
+// (r >> 2), round)), i.e. the four replicas of an aligned quad share one block per step.
+// Start state: the same counter (0xFFFFFFFF, i, r, round) as the sparse sampler.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <stdlib.h>
+
+#include "sb_common.cuh"
+
+struct moq_dense {
+    int32_t n = 0, K = 0, n_pad = 0, max_R = 0, R_pad = 0;
+    const moq_instance* inst = nullptr;
+    __nv_bfloat16* J = nullptr;                  // K x n_pad x n_pad, row-major, zero-padded
+    float* x = nullptr;                          // R_pad x n_pad
+    float* y = nullptr;                          // R_pad x n_pad
+    __nv_bfloat16* phi[2] = {nullptr, nullptr};  // R_pad x n_pad
+    float* c0 = nullptr;                         // R_pad
+    int32_t* status = nullptr;                   // device error flags
+    int32_t* h_status = nullptr;                 // pinned
+};
+
+namespace moq {
+namespace {
+
+constexpr int kTileM = 128, kTileN = 128, kChunkK = 64;
+constexpr int kTileBytes = kTileM * kChunkK * 2;  // 16 KB per operand tile
+constexpr int kThreads = 256;
+constexpr uint64_t kWaitNs = 2000000000ull;        // bound of every mbarrier wait (2 s)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// tcgen05 shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B
+// apart (stride byte offset), descriptor version 1 (bits 46-47), layout type 2 (bits 61-63).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr)
+{
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) |
+           ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9, 10-12 = 1),
+// both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTileN >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for the phase of the given parity: gives up after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+{
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        uint32_t ok;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok)
+                     : "r"(mbar), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+        if (global_ns() - t0 > kWaitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate)
+{
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+                 "l"(da), "l"(db), "r"(kIdescBf16), "r"(accumulate)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t u[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]), "=r"(u[8]), "=r"(u[9]),
+          "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(u[q]);
+}
+
+struct DenseStepArgs {
+    const __nv_bfloat16* J;
+    const __nv_bfloat16* phi_in;
+    __nv_bfloat16* phi_out;
+    float* x;
+    float* y;
+    const float* lambda;  // R x K
+    const float* c0;
+    int32_t n, n_pad, R, K, m;
+    float cm;  // a_m - a0 (when schedule is NULL)
+    const float* schedule;
+    float a0, dt, kappa, dta0;
+    uint32_t key0, key1, round32;
+    int32_t* status;
+};
+
+template <int VARIANT, int KOBJ, bool NOISE>
+__global__ void __launch_bounds__(kThreads, 1) k_dense_step(const DenseStepArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // 1024-aligned operand stages: stage s holds KOBJ J tiles then the Phi tile
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char* gbase = smem_raw + (base - raw);
+    constexpr int kStageBytes = (KOBJ + 1) * kTileBytes;
+    float* lam_s = reinterpret_cast<float*>(gbase + 2 * kStageBytes);  // kTileN x KOBJ
+    float* c0_s = lam_s + kTileN * KOBJ;                                // kTileN
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(c0_s + kTileN);        // 2 (8-aligned: offsets are multiples of 8)
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int i0 = blockIdx.x * kTileM, r0 = blockIdx.y * kTileN;
+    const int np = a.n_pad;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)), "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    for (int q = tid; q < kTileN; q += kThreads) {
+        const int r = r0 + q;
+        c0_s[q] = r < a.R ? a.c0[r] : 0.0f;
+#pragma unroll
+        for (int k = 0; k < KOBJ; ++k) lam_s[q * KOBJ + k] = r < a.R ? a.lambda[(int64_t)r * KOBJ + k] : 0.0f;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tmem_slot;
+
+    // ---- main loop: products of all objectives over the spin chunks ----
+    const int nchunks = np / kChunkK;
+    bool ok = true;
+    int last = -1;  // last chunk whose products were committed
+    for (int c = 0; c < nchunks; ++c) {
+        const int s = c & 1;
+        if (c >= 2) {  // the products that last read this stage must be done
+            if (!mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((c - 2) >> 1) & 1))) ok = false;
+        }
+        if (!__syncthreads_and(ok)) break;
+        const uint32_t stage = base + s * kStageBytes;
+        const int j0 = c * kChunkK;
+        constexpr int kChunks16 = (KOBJ + 1) * kTileM * (kChunkK * 2 / 16);
+        for (int q = tid; q < kChunks16; q += kThreads) {
+            const int tile = q / (kTileM * 8), rem = q - tile * kTileM * 8, row = rem >> 3, cc = rem & 7;
+            const __nv_bfloat16* src = tile < KOBJ ? a.J + ((int64_t)tile * np + i0 + row) * np + j0 + cc * 8
+                                                   : a.phi_in + (int64_t)(r0 + row) * np + j0 + cc * 8;
+            const uint32_t dst = stage + tile * kTileBytes + (row >> 3) * 1024 + (row & 7) * 128 + ((cc ^ (row & 7)) << 4);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+            for (int k = 0; k < KOBJ; ++k)
+#pragma unroll
+                for (int ks = 0; ks < kChunkK / 16; ++ks)
+                    mma_bf16(tmem + k * kTileN, sw128_desc(stage + k * kTileBytes + ks * 32),
+                             sw128_desc(stage + KOBJ * kTileBytes + ks * 32), (c > 0 || ks > 0) ? 1u : 0u);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&mbar[s]))
+                         : "memory");
+        }
+        last = c;
+    }
+    // the last commit covers every product issued before it
+    if (ok && last >= 0) ok = mbar_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1));
+    ok = __syncthreads_and(ok);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+
+    if (ok) {
+        // ---- epilogue: force, update, wall, next phi ----
+        const int quarter = warp & 3, half = warp >> 2;
+        const int i = i0 + quarter * 32 + lane;
+        const float cm = a.schedule ? (__ldg(a.schedule + a.m) - a.a0) : a.cm;
+#pragma unroll 1
+        for (int cc = 0; cc < 4; ++cc) {
+            const int col0 = half * 64 + cc * 16;
+            float g[KOBJ][16];
+#pragma unroll
+            for (int k = 0; k < KOBJ; ++k) tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + k * kTileN + col0, g[k]);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            float eta[16];
+#pragma unroll
+            for (int q4 = 0; q4 < 4; ++q4) {
+                eta[4 * q4] = eta[4 * q4 + 1] = eta[4 * q4 + 2] = eta[4 * q4 + 3] = 0.0f;
+                if (NOISE) {
+                    const uint32_t quad = (uint32_t)((r0 + col0) >> 2) + q4;
+                    const uint4 o = Philox4x32::block(make_uint4((uint32_t)a.m, (uint32_t)i, 0x40000000u + quad, a.round32), a.key0, a.key1);
+                    const float2 p = box_muller(o.x, o.y), h = box_muller(o.z, o.w);
+                    eta[4 * q4] = p.x; eta[4 * q4 + 1] = p.y; eta[4 * q4 + 2] = h.x; eta[4 * q4 + 3] = h.y;
+                }
+            }
+            if (i < a.n) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int rl = col0 + q, r = r0 + rl;
+                    if (r < a.R) {
+                        float f = 0.0f;
+#pragma unroll
+                        for (int k = 0; k < KOBJ; ++k) f = fmaf(lam_s[rl * KOBJ + k], g[k][q], f);
+                        f *= -c0_s[rl];  // the force acts on the negated coupling
+                        const int64_t at = (int64_t)r * np + i;
+                        float xv = a.x[at], yv = a.y[at];
+                        sb_update<NOISE>(f, cm, eta[q], a.dt, a.kappa, a.dta0, xv, yv);
+                        a.x[at] = xv;
+                        a.y[at] = yv;
+                        a.phi_out[at] = __float2bfloat16_rn(phi_of<VARIANT>(xv));
+                    }
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicOr(a.status, 1);
+        // give the products already issued a bounded chance to finish before the TMEM is freed
+        if (last >= 0) mbar_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1));
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+// J^(k) rows from the CSR, rounded to BF16, into the zero-padded dense matrices.
+__global__ void k_dense_fill(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, const int32_t* __restrict__ wn,
+                             int64_t nnz, int32_t n, int32_t K, int32_t np, __nv_bfloat16* J)
+{
+    for (int64_t i = blockIdx.x; i < n; i += gridDim.x)
+        for (int32_t p = rowptr[i] + threadIdx.x; p < rowptr[i + 1]; p += blockDim.x)
+            for (int k = 0; k < K; ++k) J[((int64_t)k * np + i) * np + col[p]] = __float2bfloat16_rn((float)wn[(int64_t)k * nnz + p]);
+}
+
+// c0_r = 1 / max_i |sum_j J(c)_ij| (fallback 1 / max_i sum_j |J(c)_ij|, then 1); one block per replica.
+__global__ void k_dense_c0(const int64_t* __restrict__ rowsum, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ wn,
+                           int64_t nnz, int32_t n, int32_t K, const float* __restrict__ lambda, int32_t R, float* c0)
+{
+    __shared__ unsigned red[2];
+    const int r = blockIdx.x;
+    if (r >= R) return;
+    float lam[kMaxK];
+#pragma unroll
+    for (int k = 0; k < kMaxK; ++k) lam[k] = k < K ? lambda[(int64_t)r * K + k] : 0.0f;
+    if (threadIdx.x == 0) red[0] = red[1] = 0u;
+    __syncthreads();
+    float mx = 0.0f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        float s = 0.0f;
+#pragma unroll
+        for (int k = 0; k < kMaxK; ++k)
+            if (k < K) s = fmaf(lam[k], (float)rowsum[(int64_t)i * K + k], s);
+        mx = fmaxf(mx, fabsf(s));
+    }
+    atomicMax(&red[0], __float_as_uint(mx));
+    __syncthreads();
+    float m = __uint_as_float(red[0]);
+    if (m == 0.0f) {  // every row sum vanishes: the rare fallback walks the rows
+        float ma = 0.0f;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            float s = 0.0f;
+            for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+                float v = 0.0f;
+                for (int k = 0; k < K; ++k) v = fmaf(lam[k], (float)wn[(int64_t)k * nnz + p], v);
+                s += fabsf(v);
+            }
+            ma = fmaxf(ma, s);
+        }
+        atomicMax(&red[1], __float_as_uint(ma));
+        __syncthreads();
+        m = __uint_as_float(red[1]);
+    }
+    if (threadIdx.x == 0) c0[r] = m > 0.0f ? 1.0f / m : 1.0f;
+}
+
+template <int VARIANT>
+__global__ void k_dense_init(int32_t n, int32_t np, int32_t R, int32_t R_pad, float init_amp, const float* __restrict__ x_init,
+                             const float* __restrict__ y_init, uint32_t key0, uint32_t key1, uint32_t round32, float* x, float* y,
+                             __nv_bfloat16* phi)
+{
+    const int64_t total = (int64_t)R_pad * np;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(q / np), i = (int)(q - (int64_t)r * np);
+        float xv = 0.0f, yv = 0.0f;
+        if (r < R && i < n) {
+            if (x_init) {
+                xv = x_init[(int64_t)r * n + i] + 0.0f;
+                yv = y_init ? y_init[(int64_t)r * n + i] : 0.0f;
+            } else {
+                const uint4 o = Philox4x32::block(make_uint4(0xFFFFFFFFu, (uint32_t)i, (uint32_t)r, round32), key0, key1);
+                xv = __fmul_rn(init_amp, signed_unit(o.x)) + 0.0f;
+                yv = __fmul_rn(init_amp, signed_unit(o.y));
+            }
+        }
+        x[q] = xv;
+        y[q] = yv;
+        phi[q] = __float2bfloat16_rn((r < R && i < n) ? phi_of<VARIANT>(xv) : 0.0f);
+    }
+}
+
+__global__ void k_dense_readout(int32_t n, int32_t np, int32_t R, int32_t W, const float* __restrict__ x, const float* __restrict__ y,
+                                uint64_t* bits, float* x_out, float* y_out)
+{
+    const int r = blockIdx.x;
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+        uint64_t word = 0;
+        for (int b = 0; b < 64 && w * 64 + b < n; ++b)
+            if (x[(int64_t)r * np + w * 64 + b] < 0.0f) word |= 1ull << b;
+        bits[(int64_t)r * W + w] = word;
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        if (x_out) x_out[(int64_t)r * n + i] = x[(int64_t)r * np + i];
+        if (y_out) y_out[(int64_t)r * n + i] = y[(int64_t)r * np + i];
+    }
+}
+
+size_t dense_smem_bytes(int K) { return 1024 + 2 * (size_t)(K + 1) * kTileBytes + (size_t)kTileN * (K + 1) * 4 + 64; }
+
+template <int VARIANT, int KOBJ, bool NOISE>
+cudaError_t launch_step(const DenseStepArgs& a, dim3 grid, cudaStream_t st)
+{
+    auto k = k_dense_step<VARIANT, KOBJ, NOISE>;
+    const size_t smem = dense_smem_bytes(KOBJ);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, kThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int VARIANT, bool NOISE>
+cudaError_t launch_step_k(const DenseStepArgs& a, dim3 grid, cudaStream_t st)
+{
+    switch (a.K) {
+    case 2: return launch_step<VARIANT, 2, NOISE>(a, grid, st);
+    case 3: return launch_step<VARIANT, 3, NOISE>(a, grid, st);
+    default: return launch_step<VARIANT, 4, NOISE>(a, grid, st);
+    }
+}
+
+void free_dense(moq_dense* d)
+{
+    if (!d) return;
+    cudaFree(d->J);
+    cudaFree(d->x);
+    cudaFree(d->y);
+    cudaFree(d->phi[0]);
+    cudaFree(d->phi[1]);
+    cudaFree(d->c0);
+    cudaFree(d->status);
+    if (d->h_status) cudaFreeHost(d->h_status);
+    delete d;
+}
+
+}  // namespace
+}  // namespace moq
+
+extern "C" {
+
+int moq_dense_create(const moq_instance* inst, int32_t max_replicas, moq_dense** out)
+{
+    using namespace moq;
+    if (!out) return fail(MOQ_ERR_ARG, "moq_dense_create: out is NULL");
+    *out = nullptr;
+    if (!inst || max_replicas < 1) return fail(MOQ_ERR_ARG, "moq_dense_create: NULL instance or max_replicas < 1");
+    if (inst->K > 4) return fail(MOQ_ERR_UNSUPPORTED, "moq_dense_create: K=%d > 4 (one TMEM accumulator per objective)", inst->K);
+    if (inst->n > 16384) return fail(MOQ_ERR_UNSUPPORTED, "moq_dense_create: n=%d > 16384", inst->n);
+    moq_dense* d = new moq_dense();
+    d->n = inst->n;
+    d->K = inst->K;
+    d->inst = inst;
+    d->n_pad = (int)ceil_div(inst->n, kTileM) * kTileM;
+    d->max_R = max_replicas;
+    d->R_pad = (int)ceil_div(max_replicas, kTileN) * kTileN;
+    const size_t cells = (size_t)d->R_pad * d->n_pad;
+    cudaError_t e = cudaMalloc((void**)&d->J, sizeof(__nv_bfloat16) * (size_t)d->K * d->n_pad * d->n_pad);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d->x, sizeof(float) * cells);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d->y, sizeof(float) * cells);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d->phi[0], sizeof(__nv_bfloat16) * cells);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d->phi[1], sizeof(__nv_bfloat16) * cells);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d->c0, sizeof(float) * d->R_pad);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d->status, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&d->h_status, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(d->J, 0, sizeof(__nv_bfloat16) * (size_t)d->K * d->n_pad * d->n_pad);
+    if (e == cudaSuccess) e = cudaMemset(d->status, 0, sizeof(int32_t));
+    if (e == cudaSuccess) {
+        k_dense_fill<<<std::min(d->n, 148 * 8), 128>>>(inst->rowptr, inst->col, inst->wn, inst->nnz, d->n, d->K, d->n_pad, d->J);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        free_dense(d);
+        return cuda_fail(e, "moq_dense_create");
+    }
+    *out = d;
+    return MOQ_OK;
+}
+
+void moq_dense_destroy(moq_dense* d) { moq::free_dense(d); }
+
+int moq_sample_dense(moq_dense* d, const float* lambda, int32_t R, const moq_sample_params* p, uint64_t seed, uint64_t round,
+                     uint64_t* bits, void* stream)
+{
+    using namespace moq;
+    if (!d || !p) return fail(MOQ_ERR_ARG, "moq_sample_dense: NULL handle or params");
+    if (R < 0 || R > d->max_R) return fail(MOQ_ERR_ARG, "moq_sample_dense: R=%d outside [0, max_replicas=%d]", R, d->max_R);
+    if (p->steps < 0 || (p->variant != MOQ_DSB && p->variant != MOQ_BSB)) return fail(MOQ_ERR_ARG, "moq_sample_dense: bad steps or variant");
+    if (R == 0) return MOQ_OK;
+    if (!lambda || !bits) return fail(MOQ_ERR_ARG, "moq_sample_dense: NULL lambda or bits");
+    if (p->replica_offset != 0) return fail(MOQ_ERR_UNSUPPORTED, "moq_sample_dense: replica_offset must be 0");
+    cudaStream_t st = as_stream(stream);
+    const moq_instance* h = d->inst;
+    const int np = d->n_pad, Rp = (int)ceil_div(R, kTileN) * kTileN;
+    const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32), rnd = (uint32_t)round;
+    k_dense_c0<<<R, 256, 0, st>>>(h->rowsum, h->rowptr, h->wn, h->nnz, d->n, d->K, lambda, R, d->c0);
+    const int gi = (int)std::min<int64_t>(ceil_div((int64_t)Rp * np, 256), 148 * 32);
+    if (p->variant == MOQ_DSB)
+        k_dense_init<MOQ_DSB><<<gi, 256, 0, st>>>(d->n, np, R, Rp, p->init_amp, p->x_init, p->y_init, key0, key1, rnd, d->x, d->y, d->phi[0]);
+    else
+        k_dense_init<MOQ_BSB><<<gi, 256, 0, st>>>(d->n, np, R, Rp, p->init_amp, p->x_init, p->y_init, key0, key1, rnd, d->x, d->y, d->phi[0]);
+    MOQ_CUDA_TRY(cudaMemsetAsync(d->phi[1], 0, sizeof(__nv_bfloat16) * (size_t)Rp * np, st));  // padded entries stay 0
+    MOQ_LAUNCH_CHECK("moq_sample_dense prologue");
+    DenseStepArgs a{};
+    a.J = d->J;
+    a.x = d->x;
+    a.y = d->y;
+    a.lambda = lambda;
+    a.c0 = d->c0;
+    a.n = d->n;
+    a.n_pad = np;
+    a.R = R;
+    a.K = d->K;
+    a.schedule = p->schedule;
+    a.a0 = p->a0;
+    a.dt = p->dt;
+    a.kappa = (p->noise_sqrt_dt ? sqrtf(p->dt) : p->dt) * p->alpha;
+    a.dta0 = p->dt * p->a0;
+    a.key0 = key0;
+    a.key1 = key1;
+    a.round32 = rnd;
+    a.status = d->status;
+    const float a0inv = p->steps > 1 ? p->a0 / (float)(p->steps - 1) : 0.0f;
+    const dim3 grid(np / kTileM, Rp / kTileN);
+    const bool noise = p->alpha != 0.0f;
+    for (int m = 0; m < p->steps; ++m) {
+        a.m = m;
+        a.cm = fmaf(a0inv, (float)m, -p->a0);
+        a.phi_in = d->phi[m & 1];
+        a.phi_out = d->phi[(m + 1) & 1];
+        cudaError_t e;
+        if (p->variant == MOQ_DSB) e = noise ? launch_step_k<MOQ_DSB, true>(a, grid, st) : launch_step_k<MOQ_DSB, false>(a, grid, st);
+        else e = noise ? launch_step_k<MOQ_BSB, true>(a, grid, st) : launch_step_k<MOQ_BSB, false>(a, grid, st);
+        if (e != cudaSuccess) return cuda_fail(e, "moq_sample_dense step launch");
+    }
+    k_dense_readout<<<R, 128, 0, st>>>(d->n, np, R, h->words, d->x, d->y, bits, p->x_out, p->y_out);
+    MOQ_LAUNCH_CHECK("moq_sample_dense readout");
+    return MOQ_OK;
+}
+
+int moq_dense_status(moq_dense* d, void* stream)
+{
+    using namespace moq;
+    if (!d) return fail(MOQ_ERR_ARG, "moq_dense_status: NULL handle");
+    cudaStream_t st = as_stream(stream);
+    MOQ_CUDA_TRY(cudaMemcpyAsync(d->h_status, d->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MOQ_CUDA_TRY(cudaStreamSynchronize(st));
+    if (*d->h_status) {
+        MOQ_CUDA_TRY(cudaMemsetAsync(d->status, 0, sizeof(int32_t), st));
+        return fail(MOQ_ERR_TIMEOUT, "moq_sample_dense: a tensor-core wait ran out of its budget");
+    }
+    return MOQ_OK;
+}
+
+}  // extern "C"

@@ -86,6 +86,10 @@ _sigs = {
     "moq_batch_set_tiles": (C.c_int, [_vp, _i32, _i32, C.POINTER(_i32)]),
     "moq_sample_batch": (C.c_int, [_vp, _vp, C.POINTER(moq_sample_params), _u64, _u64, _vp, _vp]),
     "moq_evaluate_cuts_batch": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "moq_dense_create": (C.c_int, [_vp, _i32, C.POINTER(_vp)]),
+    "moq_dense_destroy": (None, [_vp]),
+    "moq_sample_dense": (C.c_int, [_vp, _vp, _i32, C.POINTER(moq_sample_params), _u64, _u64, _vp, _vp]),
+    "moq_dense_status": (C.c_int, [_vp, _vp]),
     "moq_strerror": (C.c_char_p, [C.c_int]),
     "moq_last_error_message": (C.c_char_p, []),
 }
@@ -300,6 +304,26 @@ def moq_evaluate_cuts_batch(h, bits_all, cuts_all, stream=None):
     _, i64, u64 = _torch_types()
     _check(_lib.moq_evaluate_cuts_batch(h, _dptr(bits_all, "bits_all", u64), _dptr(cuts_all, "cuts_all", i64),
                                         _stream(stream)), "moq_evaluate_cuts_batch")
+
+
+def moq_dense_create(inst, max_replicas) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(_lib.moq_dense_create(inst, max_replicas, C.byref(h)), "moq_dense_create")
+    return h
+
+
+def moq_dense_destroy(h):
+    _lib.moq_dense_destroy(h)
+
+
+def moq_sample_dense(h, lam, R, params, seed, round_, bits, stream=None):
+    f32, _, u64 = _torch_types()
+    _check(_lib.moq_sample_dense(h, _dptr(lam, "lambda", f32), R, C.byref(params), seed, round_,
+                                 _dptr(bits, "bits", u64), _stream(stream)), "moq_sample_dense")
+
+
+def moq_dense_status(h, stream=None):
+    _check(_lib.moq_dense_status(h, _stream(stream)), "moq_sample_dense")
 
 
 def moq_hypervolume_noalloc_max_points() -> int:

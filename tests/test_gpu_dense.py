@@ -1,0 +1,151 @@
+"""The tensor-core (tcgen05) dense sampler against the CPU oracle.
+
+dSB with integer couplings |J| <= 256 is exact in BF16 and phi = +-1 is exact, so the
+per-objective products are exact and the force must match the FP64 oracle within the
+FP32 normwise bound (1e-5). bSB rounds x to BF16 for the products: the stated bound is
+|f - f64| <= 4e-3 * c0 * sum_j |J(c)_ij x_j| (BF16 has a 2^-9 relative rounding).
+"""
+import numpy as np
+import pytest
+import torch
+from scipy import stats
+
+from paper_2604_26477_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    from paper_2604_26477_b300 import build
+    build.build()
+    from paper_2604_26477_b300 import moqaia
+    return moqaia
+
+
+@pytest.fixture(scope="module")
+def P(M):
+    from paper_2604_26477_b300 import pipeline
+    return pipeline
+
+
+def _dev(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype=dtype, device="cuda")
+
+
+def _abs_force_scale(src, lam, phi, c0):
+    Jc = lam.astype(np.float64) @ src.w.astype(np.float64)
+    out = np.zeros(phi.shape)
+    np.add.at(out.T, src.ei, (np.abs(Jc * phi[:, src.ej])).T)
+    np.add.at(out.T, src.ej, (np.abs(Jc * phi[:, src.ei])).T)
+    return out * c0[:, None]
+
+
+def _force(M, P, src, variant, R, seed=1):
+    inst = P.Instance(src)
+    d = M.moq_dense_create(inst.handle, R)
+    try:
+        lam = wl.dirichlet_lambdas(R, src.K, seed)
+        rng = np.random.default_rng(seed)
+        x0 = rng.uniform(-0.5, 0.5, (R, src.n)).astype(np.float32)
+        dt = 2.0 ** -10
+        yo = torch.zeros((R, src.n), device="cuda")
+        xo = torch.zeros((R, src.n), device="cuda")
+        p = M.moq_default_params(variant=variant, steps=1, dt=dt, alpha=0.0, schedule=torch.ones(1, device="cuda"),
+                                 x_init=_dev(x0), y_init=torch.zeros((R, src.n), device="cuda"), x_out=xo, y_out=yo)
+        bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+        M.moq_sample_dense(d, _dev(lam), R, p, 0, 0, bits)
+        M.moq_dense_status(d)
+        torch.cuda.synchronize()
+    finally:
+        M.moq_dense_destroy(d)
+    return lam, x0, yo.cpu().numpy().astype(np.float64) / dt, xo.cpu().numpy()
+
+
+@pytest.mark.parametrize("n,R,K", [(200, 300, 3), (128, 128, 4), (70, 130, 2), (300, 64, 3)])
+def test_dense_dsb_force_exact(M, P, oracle, n, R, K):
+    src = wl.random_graph(n, 1.0, n + R, K=K, wmax=100)  # complete graph, |J| <= 100
+    lam, x0, f_gpu, _ = _force(M, P, src, "dsb", R)
+    ref = oracle.sb(src, lam.astype(np.float64), variant="dsb", steps=1, dt=2.0 ** -10, alpha=0.0, schedule=[1.0],
+                    x_init=x0.astype(np.float64), y_init=np.zeros((R, n)))
+    f_ref = ref["y"] / 2.0 ** -10
+    scale = _abs_force_scale(src, lam, np.where(x0 >= 0, 1.0, -1.0), ref["c0"])
+    err = np.abs(f_gpu - f_ref)
+    assert np.all(err <= 1e-5 * scale + 1e-30), float((err / np.maximum(scale, 1e-30)).max())
+
+
+def test_dense_bsb_force_bf16_bound(M, P, oracle):
+    src = wl.random_graph(260, 0.7, 5, K=3, wmax=100)
+    R = 200
+    lam, x0, f_gpu, _ = _force(M, P, src, "bsb", R)
+    ref = oracle.sb(src, lam.astype(np.float64), variant="bsb", steps=1, dt=2.0 ** -10, alpha=0.0, schedule=[1.0],
+                    x_init=x0.astype(np.float64), y_init=np.zeros((R, src.n)))
+    scale = _abs_force_scale(src, lam, x0.astype(np.float64), ref["c0"])
+    err = np.abs(f_gpu - ref["y"] / 2.0 ** -10)
+    assert np.all(err <= 4e-3 * scale + 1e-30), float((err / np.maximum(scale, 1e-30)).max())
+
+
+def test_dense_short_trajectory(M, P, oracle):
+    # dSB, no noise: products are exact, so a few steps follow the FP64 trajectory closely
+    # (replicas with a spin within 1e-3 of the sign switch at the start are left out)
+    src = wl.random_graph(150, 1.0, 8, K=3, wmax=50)
+    inst = P.Instance(src)
+    R, T = 256, 6
+    d = M.moq_dense_create(inst.handle, R)
+    lam = wl.dirichlet_lambdas(R, 3, 2)
+    xo = torch.zeros((R, src.n), device="cuda")
+    yo = torch.zeros((R, src.n), device="cuda")
+    p = M.moq_default_params(variant="dsb", steps=T, dt=0.5, x_out=xo, y_out=yo)
+    bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+    M.moq_sample_dense(d, _dev(lam), R, p, 4, 0, bits)
+    M.moq_dense_status(d)
+    ref = oracle.sb(src, lam.astype(np.float64), variant="dsb", steps=T, dt=0.5, seed=4)
+    x0 = np.array([[oracle.initial_state(4, 0, r, i)[0] for i in range(src.n)] for r in range(R)])
+    ok = np.all(np.abs(x0) > 1e-3, axis=1)
+    assert ok.sum() >= 8
+    assert np.abs(xo.cpu().numpy()[ok] - ref["x"][ok]).max() < 1e-4
+    s = np.where(xo.cpu().numpy() >= 0, 1, -1)
+    assert np.array_equal(wl.bits_to_signs(bits.cpu().numpy().view(np.uint64), src.n), s)
+    M.moq_dense_destroy(d)
+
+
+def test_dense_noise_is_gaussian(M, P):
+    # J = 0 (all weights zero), x = y = 0, a = a0: after one step y = dt * alpha * eta
+    n, R = 130, 260
+    iu, ju = np.triu_indices(n, 1)
+    src = wl.Instance(n, iu.astype(np.int32), ju.astype(np.int32), np.zeros((2, iu.size), np.int32))
+    inst = P.Instance(src)
+    d = M.moq_dense_create(inst.handle, R)
+    yo = torch.zeros((R, n), device="cuda")
+    z = torch.zeros((R, n), device="cuda")
+    p = M.moq_default_params(steps=1, dt=0.5, alpha=0.2, schedule=torch.ones(1, device="cuda"), x_init=z, y_init=z, y_out=yo)
+    M.moq_sample_dense(d, _dev(np.full((R, 2), 0.5)), R, p, 9, 0, torch.zeros((R, 3), dtype=torch.int64, device="cuda"))
+    eta = yo.cpu().numpy().ravel() / (0.5 * 0.2)
+    assert abs(eta.mean()) < 0.02 and abs(eta.var() - 1) < 0.03
+    assert stats.kstest(eta[:20000], "norm").pvalue > 1e-3
+    assert len(np.unique(eta)) > 0.99 * eta.size
+    M.moq_dense_destroy(d)
+
+
+def test_dense_final_hv_distribution(M, P, oracle):
+    # chaotic trajectories: the final front's hypervolume over 16 seeds is distributed
+    # like the FP64 oracle's
+    src = wl.app_e_correlated(25, 1.0, 3)
+    inst = P.Instance(src)
+    R, T = 256, 120
+    d = M.moq_dense_create(inst.handle, R)
+    lam = wl.dirichlet_lambdas(R, 3, 5)
+    params = M.moq_default_params(steps=T, dt=0.5, alpha=0.1)
+    bits = torch.zeros((R, 1), dtype=torch.int64, device="cuda")
+    hv_g, hv_c = [], []
+    for seed in range(16):
+        M.moq_sample_dense(d, _dev(lam), R, params, seed, 0, bits)
+        c = oracle.cuts(src, bits.cpu().numpy().view(np.uint64))
+        hv_g.append(oracle.hypervolume(c[oracle.pareto_filter(c)], inst.ref))
+        o = oracle.sb(src, lam.astype(np.float64), steps=T, dt=0.5, alpha=0.1, seed=500 + seed)
+        c = oracle.cuts(src, o["bits"])
+        hv_c.append(oracle.hypervolume(c[oracle.pareto_filter(c)], inst.ref))
+    M.moq_dense_status(d)
+    M.moq_dense_destroy(d)
+    assert stats.mannwhitneyu(hv_g, hv_c).pvalue > 0.01
+    assert abs(np.median(hv_g) / np.median(hv_c) - 1) < 0.03
