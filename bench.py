@@ -384,6 +384,76 @@ def batching_arm(args, rank, world):
             "front_points_mean": float(np.mean(fronts))}
 
 
+def dense_arm(args, rank, world):
+    """Dense configuration: complete graph n=2000, K=3, J = round(1000 N(0,1)), R=8192
+    uniform-simplex replicas, bSB, T=3000 (--dense-steps), dt=0.5, alpha=0.1; one step =
+    the tensor-core sampler (T step kernels) + exact cuts + Pareto filter + hypervolume."""
+    import torch
+
+    from paper_2604_26477_b300 import moqaia as M
+    from paper_2604_26477_b300 import pipeline as P
+    from paper_2604_26477_b300 import workloads as wl
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    n, K, R, T = args.dense_n, 3, args.dense_replicas, args.dense_steps
+    src = wl.complete_graph(n, 2000 + rank, K=K)
+    inst = P.Instance(src)
+    d = M.moq_dense_create(inst.handle, R)
+    arch = P.Archive(n, K, capacity=1 << 16, max_batch=R)
+    lam = torch.from_numpy(wl.dirichlet_lambdas(R, K, 5 + rank)).to(dev)
+    bits = torch.zeros((R, inst.W), dtype=torch.int64, device=dev)
+    cuts = torch.zeros((R, K), dtype=torch.int64, device=dev)
+    params = M.moq_default_params(variant="bsb", steps=T, dt=0.5, alpha=0.1)
+    stream = torch.cuda.current_stream()
+    hv = [0]
+
+    def step(s, evs):
+        arch.reset()
+        evs[0].record(stream)
+        M.moq_sample_dense(d, lam, R, params, 1 + rank, s, bits)
+        evs[1].record(stream)
+        M.moq_evaluate_cuts(inst.handle, bits, R, cuts)
+        arch.merge(cuts, bits, R, 0)
+        hv[0] = arch.hypervolume(inst.ref)
+        evs[2].record(stream)
+
+    mk = lambda: [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for s in range(args.warmup):
+        step(s, mk())
+    M.moq_dense_status(d)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ev = [mk() for _ in range(args.steps)]
+    with ClockSampler(dev.index) as clk:
+        for s in range(args.steps):
+            step(args.warmup + s, ev[s])
+        torch.cuda.synchronize()
+    M.moq_dense_status(d)
+    step_s = sum(e[0].elapsed_time(e[2]) for e in ev) / 1e3
+    samp_s = sum(e[0].elapsed_time(e[1]) for e in ev) / 1e3
+    units = float(n) * R * T * args.steps
+    flops = 2.0 * K * n * n * R * T * args.steps  # algorithmic: K products (n x n)(n x R) per step
+    peaks = measured_peaks()
+    peak = peaks.get("bf16_tflops_sustained", 1392.4)
+    achieved = flops / samp_s / 1e12
+    front = arch.size()
+    M.moq_dense_destroy(d)
+    return {"metric": METRIC, "value": units / step_s * world, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_s / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 products, f32 state", "data": "synthetic",
+            "config": {"workload": f"dense: complete graph n={n}, K=3, J=round(1000 N(0,1)), R={R} uniform-simplex "
+                                   f"lambda, bsb T={T} dt=0.5 alpha=0.1; tcgen05 BF16 products, FP32 accumulate; "
+                                   "exact cuts + Pareto + hypervolume per step",
+                       "n": n, "R": R, "T": T},
+            "roofline": {"bound": "tensor", "kernel": "k_dense_step (all T launches)", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak,
+                         "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16, seconds-long loop)"},
+            "sampling_only_value": units / samp_s * world, "sampler_ms": samp_s / args.steps * 1e3,
+            "clocks": clk.summary(), "front_points_last_step": front, "hv_last_step": int(hv[0])}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -396,8 +466,11 @@ def main():
     ap.add_argument("--ttt-rounds", type=int, default=64)
     ap.add_argument("--no-ttt", action="store_true")
     ap.add_argument("--cpu-baseline-worker", action="store_true")
-    ap.add_argument("--workload", default="precision", choices=["precision", "batching"],
-                    help="precision (the default line) or the batching configuration")
+    ap.add_argument("--workload", default="precision", choices=["precision", "batching", "dense"],
+                    help="precision (the default line), or the batching or dense configuration")
+    ap.add_argument("--dense-n", type=int, default=2000)
+    ap.add_argument("--dense-replicas", type=int, default=8192)
+    ap.add_argument("--dense-steps", type=int, default=3000)
     ap.add_argument("--batch-instances", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and not args.cpu_baseline_worker:
@@ -430,8 +503,8 @@ def main():
         print(json.dumps(line), flush=True)
         return
 
-    if args.workload == "batching":
-        line = batching_arm(args, rank, world)
+    if args.workload in ("batching", "dense"):
+        line = (batching_arm if args.workload == "batching" else dense_arm)(args, rank, world)
         if rank == 0:
             print(json.dumps(line), flush=True)
         return

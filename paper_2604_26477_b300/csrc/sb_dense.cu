@@ -7,11 +7,12 @@
 // Step kernel, one CTA per tile of 128 spins (M) x 128 replicas (N):
 //  - the K-dimension (spins j) is walked in chunks of 64: J^(k)[i0:+128, j0:+64] for each
 //    objective and Phi[r0:+128, j0:+64] are copied into shared memory (cp.async, 16 B per
-//    thread, two stages) in the 128-byte-swizzled K-major layout the tensor core reads;
+//    thread; three stages for K <= 3, two for K = 4, copies issued that many chunks minus
+//    one ahead) in the 128-byte-swizzled K-major layout the tensor core reads;
 //  - one thread issues tcgen05.mma (BF16 x BF16 -> FP32, M=128, N=128, K=16) into one TMEM
 //    accumulator per objective (K x 128 of the 512 columns) and tcgen05.commit signals an
-//    mbarrier per stage, so the copy of chunk c+1 overlaps the products of chunk c;
-//  - the epilogue (8 warps; warp w reads TMEM lanes 32*(w%4).. of columns 64*(w/4)..) forms
+//    mbarrier per stage, so copies of later chunks overlap the products of chunk c;
+//  - the epilogue (16 warps; warp w reads TMEM lanes 32*(w%4).. of columns 32*(w/4)..) forms
 //    f = -c0_r sum_k c_rk G_k[i, r], updates x, y (FP32, in HBM), applies the wall and
 //    writes phi(x) as BF16 for the next step.
 // Every wait on an mbarrier is bounded in time (globaltimer); on time-out the kernel records
@@ -46,7 +47,9 @@ namespace {
 
 constexpr int kTileM = 128, kTileN = 128, kChunkK = 64;
 constexpr int kTileBytes = kTileM * kChunkK * 2;  // 16 KB per operand tile
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
+// three operand stages (prefetch distance 2) when they fit in shared memory, else two
+__host__ __device__ constexpr int dense_stages(int K) { return K <= 3 ? 3 : 2; }
 constexpr uint64_t kWaitNs = 2000000000ull;        // bound of every mbarrier wait (2 s)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -130,10 +133,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_step(const DenseStepArgs 
     const uint32_t base = (raw + 1023u) & ~1023u;
     unsigned char* gbase = smem_raw + (base - raw);
     constexpr int kStageBytes = (KOBJ + 1) * kTileBytes;
-    float* lam_s = reinterpret_cast<float*>(gbase + 2 * kStageBytes);  // kTileN x KOBJ
+    constexpr int S = dense_stages(KOBJ), D = S - 1;  // stages and prefetch distance
+    float* lam_s = reinterpret_cast<float*>(gbase + S * kStageBytes);  // kTileN x KOBJ
     float* c0_s = lam_s + kTileN * KOBJ;                                // kTileN
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(c0_s + kTileN);        // 2 (8-aligned: offsets are multiples of 8)
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(c0_s + kTileN);        // S (8-aligned: offsets are multiples of 8)
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + S);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int i0 = blockIdx.x * kTileM, r0 = blockIdx.y * kTileN;
@@ -144,8 +148,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_step(const DenseStepArgs 
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
+        for (int s = 0; s < S; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[s])), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     for (int q = tid; q < kTileN; q += kThreads) {
@@ -160,16 +163,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_step(const DenseStepArgs 
     const uint32_t tmem = *tmem_slot;
 
     // ---- main loop: products of all objectives over the spin chunks ----
+    // Chunk c lives in stage c % S; its copy is issued D chunks ahead, after the products
+    // that last read the stage (chunk c - 1) are done. Every iteration commits exactly one
+    // cp.async group (possibly empty), so "all but the newest D groups" is chunk c.
     const int nchunks = np / kChunkK;
-    bool ok = true;
-    int last = -1;  // last chunk whose products were committed
-    for (int c = 0; c < nchunks; ++c) {
-        const int s = c & 1;
-        if (c >= 2) {  // the products that last read this stage must be done
-            if (!mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((c - 2) >> 1) & 1))) ok = false;
-        }
-        if (!__syncthreads_and(ok)) break;
-        const uint32_t stage = base + s * kStageBytes;
+    auto issue_copy = [&](int c) {
+        const uint32_t stage = base + (c % S) * kStageBytes;
         const int j0 = c * kChunkK;
         constexpr int kChunks16 = (KOBJ + 1) * kTileM * (kChunkK * 2 / 16);
         for (int q = tid; q < kChunks16; q += kThreads) {
@@ -179,11 +178,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_step(const DenseStepArgs 
             const uint32_t dst = stage + tile * kTileBytes + (row >> 3) * 1024 + (row & 7) * 128 + ((cc ^ (row & 7)) << 4);
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
         }
+    };
+    for (int c = 0; c < D; ++c) {
+        if (c < nchunks) issue_copy(c);
         asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    bool ok = true;
+    int last = -1;  // last chunk whose products were committed
+    for (int c = 0; c < nchunks; ++c) {
+        const int cn = c + D;
+        if (cn < nchunks && cn >= S) {  // stage cn % S was last read by chunk cn - S
+            if (!mbar_wait(smem_u32(&mbar[cn % S]), (uint32_t)(((cn - S) / S) & 1))) ok = false;
+        }
+        if (!__syncthreads_and(ok)) break;
+        if (cn < nchunks) issue_copy(cn);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group %0;" ::"n"(D) : "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
+            const uint32_t stage = base + (c % S) * kStageBytes;
             asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
             for (int k = 0; k < KOBJ; ++k)
@@ -191,24 +205,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_step(const DenseStepArgs 
                 for (int ks = 0; ks < kChunkK / 16; ++ks)
                     mma_bf16(tmem + k * kTileN, sw128_desc(stage + k * kTileBytes + ks * 32),
                              sw128_desc(stage + KOBJ * kTileBytes + ks * 32), (c > 0 || ks > 0) ? 1u : 0u);
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&mbar[s]))
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&mbar[c % S]))
                          : "memory");
         }
         last = c;
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     // the last commit covers every product issued before it
-    if (ok && last >= 0) ok = mbar_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1));
+    if (ok && last >= 0) ok = mbar_wait(smem_u32(&mbar[last % S]), (uint32_t)((last / S) & 1));
     ok = __syncthreads_and(ok);
     asm volatile("tcgen05.fence::after_thread_sync;");
 
     if (ok) {
         // ---- epilogue: force, update, wall, next phi ----
-        const int quarter = warp & 3, half = warp >> 2;
+        // warp w reads TMEM lanes 32*(w % 4).. (its spins) and columns 32*(w / 4).. (replicas)
+        const int quarter = warp & 3, part = warp >> 2;
         const int i = i0 + quarter * 32 + lane;
         const float cm = a.schedule ? (__ldg(a.schedule + a.m) - a.a0) : a.cm;
 #pragma unroll 1
-        for (int cc = 0; cc < 4; ++cc) {
-            const int col0 = half * 64 + cc * 16;
+        for (int cc = 0; cc < 2; ++cc) {
+            const int col0 = part * 32 + cc * 16;
             float g[KOBJ][16];
 #pragma unroll
             for (int k = 0; k < KOBJ; ++k) tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + k * kTileN + col0, g[k]);
@@ -246,7 +262,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_step(const DenseStepArgs 
     } else if (tid == 0) {
         atomicOr(a.status, 1);
         // give the products already issued a bounded chance to finish before the TMEM is freed
-        if (last >= 0) mbar_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1));
+        if (last >= 0) mbar_wait(smem_u32(&mbar[last % S]), (uint32_t)((last / S) & 1));
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -344,7 +360,7 @@ __global__ void k_dense_readout(int32_t n, int32_t np, int32_t R, int32_t W, con
     }
 }
 
-size_t dense_smem_bytes(int K) { return 1024 + 2 * (size_t)(K + 1) * kTileBytes + (size_t)kTileN * (K + 1) * 4 + 64; }
+size_t dense_smem_bytes(int K) { return 1024 + dense_stages(K) * (size_t)(K + 1) * kTileBytes + (size_t)kTileN * (K + 1) * 4 + 64; }
 
 template <int VARIANT, int KOBJ, bool NOISE>
 cudaError_t launch_step(const DenseStepArgs& a, dim3 grid, cudaStream_t st)
