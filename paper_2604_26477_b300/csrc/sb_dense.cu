@@ -211,6 +211,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_step(const DenseStepArgs 
         last = c;
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
+    // warp w owns TMEM lanes 32*(w % 4).. (its spins) and columns 32*(w / 4).. (replicas);
+    // each lane's state for the first 16 columns is loaded while the last products finish
+    const int quarter = warp & 3, part = warp >> 2;
+    const int i = i0 + quarter * 32 + lane;
+    float xs[16], ys[16];
+    auto load_state = [&](int col0) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int r = r0 + col0 + q;
+            const bool v = i < a.n && r < a.R;
+            xs[q] = v ? a.x[(int64_t)r * np + i] : 0.0f;
+            ys[q] = v ? a.y[(int64_t)r * np + i] : 0.0f;
+        }
+    };
+    load_state(part * 32);
     // the last commit covers every product issued before it
     if (ok && last >= 0) ok = mbar_wait(smem_u32(&mbar[last % S]), (uint32_t)((last / S) & 1));
     ok = __syncthreads_and(ok);
@@ -218,13 +233,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_step(const DenseStepArgs 
 
     if (ok) {
         // ---- epilogue: force, update, wall, next phi ----
-        // warp w reads TMEM lanes 32*(w % 4).. (its spins) and columns 32*(w / 4).. (replicas)
-        const int quarter = warp & 3, part = warp >> 2;
-        const int i = i0 + quarter * 32 + lane;
         const float cm = a.schedule ? (__ldg(a.schedule + a.m) - a.a0) : a.cm;
 #pragma unroll 1
         for (int cc = 0; cc < 2; ++cc) {
             const int col0 = part * 32 + cc * 16;
+            if (cc > 0) load_state(col0);  // all 32 loads in flight together
             float g[KOBJ][16];
 #pragma unroll
             for (int k = 0; k < KOBJ; ++k) tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + k * kTileN + col0, g[k]);
@@ -250,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_step(const DenseStepArgs 
                         for (int k = 0; k < KOBJ; ++k) f = fmaf(lam_s[rl * KOBJ + k], g[k][q], f);
                         f *= -c0_s[rl];  // the force acts on the negated coupling
                         const int64_t at = (int64_t)r * np + i;
-                        float xv = a.x[at], yv = a.y[at];
+                        float xv = xs[q], yv = ys[q];
                         sb_update<NOISE>(f, cm, eta[q], a.dt, a.kappa, a.dta0, xv, yv);
                         a.x[at] = xv;
                         a.y[at] = yv;
