@@ -69,6 +69,11 @@ def _load():
                                   C.c_uint64, C.c_uint64, vp, vp, u64p, vp, vp, vp]
             lib.or_sb.restype = C.c_int
             lib.or_reference_point.argtypes = [C.c_int, C.c_int64, i32p, i64p]
+            lib.or_mlp_param_count.argtypes = [C.c_int, C.c_int, C.c_int]
+            lib.or_mlp_param_count.restype = C.c_int64
+            lib.or_mlp_forward.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.c_int64, dp, dp]
+            lib.or_mlp_loss_grad.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.c_int64, dp, dp, dp]
+            lib.or_mlp_loss_grad.restype = C.c_double
             _lib = lib
     return _lib
 
@@ -194,3 +199,24 @@ def sb(inst, lam, *, variant: str = "dsb", steps: int = 1000, dt: float = 0.5, a
                   init_amp, _ptr(sched), int(noise_sqrt_dt), seed, round_, _ptr(xi), _ptr(yi), bits,
                   _ptr(x), _ptr(y), _ptr(c0))
     return {"bits": bits, "x": x, "y": y, "c0": c0}
+
+
+def mlp_param_count(din: int, h: int, dout: int) -> int:
+    return int(_load().or_mlp_param_count(din, h, dout))
+
+
+def mlp_forward(params, X, din: int, h: int, dout: int) -> np.ndarray:
+    """Surrogate MLP forward in double precision: (B, din) -> (B, dout)."""
+    X = np.ascontiguousarray(np.asarray(X, np.float64).reshape(-1, din))
+    Y = np.zeros((X.shape[0], dout), np.float64)
+    _load().or_mlp_forward(din, h, dout, np.ascontiguousarray(params, np.float64), X.shape[0], X, Y)
+    return Y
+
+
+def mlp_loss_grad(params, X, T, din: int, h: int, dout: int):
+    """Mean squared error and its gradient with respect to the flat parameter vector."""
+    X = np.ascontiguousarray(np.asarray(X, np.float64).reshape(-1, din))
+    T = np.ascontiguousarray(np.asarray(T, np.float64).reshape(-1, dout))
+    g = np.zeros(mlp_param_count(din, h, dout), np.float64)
+    loss = _load().or_mlp_loss_grad(din, h, dout, np.ascontiguousarray(params, np.float64), X.shape[0], X, T, g)
+    return loss, g

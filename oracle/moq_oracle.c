@@ -473,3 +473,114 @@ void or_reference_point(int K, int64_t E, const int32_t* w, int64_t* ref)
         ref[k] = s;
     }
 }
+
+/* ------------------------------------------------------------------------------------
+ * Learned weight-vector proposal (not in the paper: the surrogate model of the learned
+ * proposal). A multilayer perceptron maps an input row x (D_in values: the weight vector
+ * and graph statistics) to D_out predictions:
+ *   h1 = relu(W1 x + b1),  h2 = relu(W2 h1 + b2),  y = W3 h2 + b3
+ * with W1: H x D_in, W2: H x H, W3: D_out x H. Parameters are one flat vector in the order
+ * W1, b1, W2, b2, W3, b3 (row-major). Loss over a batch of B rows with targets t:
+ *   L = 1 / (B D_out) sum_b sum_k (y_bk - t_bk)^2.
+ * or_mlp_forward writes y (B x D_out); or_mlp_loss_grad returns L and writes dL/dparams.
+ * ---------------------------------------------------------------------------------- */
+static void mlp_layer_offsets(int din, int h, int dout, int64_t off[6])
+{
+    off[0] = 0;                          /* W1 */
+    off[1] = off[0] + (int64_t)h * din;  /* b1 */
+    off[2] = off[1] + h;                 /* W2 */
+    off[3] = off[2] + (int64_t)h * h;    /* b2 */
+    off[4] = off[3] + h;                 /* W3 */
+    off[5] = off[4] + (int64_t)dout * h; /* b3 */
+}
+
+int64_t or_mlp_param_count(int din, int h, int dout)
+{
+    int64_t off[6];
+    mlp_layer_offsets(din, h, dout, off);
+    return off[5] + dout;
+}
+
+static void mlp_forward_row(int din, int h, int dout, const double* p, const double* x, double* a1, double* h1,
+                            double* a2, double* h2, double* y)
+{
+    int64_t off[6];
+    mlp_layer_offsets(din, h, dout, off);
+    for (int j = 0; j < h; ++j) {
+        double s = p[off[1] + j];
+        for (int i = 0; i < din; ++i) s += p[off[0] + (int64_t)j * din + i] * x[i];
+        a1[j] = s;
+        h1[j] = s > 0.0 ? s : 0.0;
+    }
+    for (int j = 0; j < h; ++j) {
+        double s = p[off[3] + j];
+        for (int i = 0; i < h; ++i) s += p[off[2] + (int64_t)j * h + i] * h1[i];
+        a2[j] = s;
+        h2[j] = s > 0.0 ? s : 0.0;
+    }
+    for (int k = 0; k < dout; ++k) {
+        double s = p[off[5] + k];
+        for (int i = 0; i < h; ++i) s += p[off[4] + (int64_t)k * h + i] * h2[i];
+        y[k] = s;
+    }
+}
+
+void or_mlp_forward(int din, int h, int dout, const double* p, int64_t B, const double* X, double* Y)
+{
+    double* buf = (double*)malloc(sizeof(double) * 4 * h);
+    for (int64_t b = 0; b < B; ++b)
+        mlp_forward_row(din, h, dout, p, X + b * din, buf, buf + h, buf + 2 * h, buf + 3 * h, Y + b * dout);
+    free(buf);
+}
+
+/* Backpropagation written out per row: dy = 2 (y - t) / (B D_out); the gradient of each
+ * layer is the outer product of the incoming gradient and the layer input; relu passes
+ * the gradient where its pre-activation is positive. */
+double or_mlp_loss_grad(int din, int h, int dout, const double* p, int64_t B, const double* X, const double* T, double* grad)
+{
+    int64_t off[6];
+    mlp_layer_offsets(din, h, dout, off);
+    const int64_t P = off[5] + dout;
+    for (int64_t q = 0; q < P; ++q) grad[q] = 0.0;
+    double* a1 = (double*)malloc(sizeof(double) * 7 * h + sizeof(double) * dout * 2);
+    double *h1 = a1 + h, *a2 = h1 + h, *h2 = a2 + h, *d2 = h2 + h, *d1 = d2 + h, *tmp = d1 + h;
+    double *y = tmp + h, *dy = y + dout;
+    double loss = 0.0;
+    const double scale = 1.0 / ((double)B * dout);
+    for (int64_t b = 0; b < B; ++b) {
+        const double* x = X + b * din;
+        mlp_forward_row(din, h, dout, p, x, a1, h1, a2, h2, y);
+        for (int k = 0; k < dout; ++k) {
+            const double e = y[k] - T[b * dout + k];
+            loss += e * e * scale;
+            dy[k] = 2.0 * e * scale;
+        }
+        /* layer 3 */
+        for (int k = 0; k < dout; ++k) {
+            grad[off[5] + k] += dy[k];
+            for (int i = 0; i < h; ++i) grad[off[4] + (int64_t)k * h + i] += dy[k] * h2[i];
+        }
+        for (int i = 0; i < h; ++i) {
+            double s = 0.0;
+            for (int k = 0; k < dout; ++k) s += p[off[4] + (int64_t)k * h + i] * dy[k];
+            d2[i] = a2[i] > 0.0 ? s : 0.0;
+        }
+        /* layer 2 */
+        for (int j = 0; j < h; ++j) {
+            grad[off[3] + j] += d2[j];
+            for (int i = 0; i < h; ++i) grad[off[2] + (int64_t)j * h + i] += d2[j] * h1[i];
+        }
+        for (int i = 0; i < h; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < h; ++j) s += p[off[2] + (int64_t)j * h + i] * d2[j];
+            d1[i] = a1[i] > 0.0 ? s : 0.0;
+        }
+        /* layer 1 */
+        for (int j = 0; j < h; ++j) {
+            grad[off[1] + j] += d1[j];
+            for (int i = 0; i < din; ++i) grad[off[0] + (int64_t)j * din + i] += d1[j] * x[i];
+        }
+    }
+    free(a1);
+    return loss;
+}
