@@ -61,6 +61,10 @@ typedef struct moq_instance_info {
     int64_t weight_sum[8];    /* W_k = sum_E J^(k) */
     int64_t abs_sum[8];       /* sum_E |J^(k)|, bounds every cut range */
     int64_t ref_point[8];     /* r_k = sum_E min(0, J^(k)): C_k(s) >= r_k for every s */
+    float features[8];        /* graph statistics of the learned proposal (not in the paper):
+                                 log n, mean degree / 10, mean_k mean|w_k| / rms(w_k),
+                                 mean_k std(w_k) / rms(w_k), fraction of positive weights,
+                                 mean, min, max pairwise Pearson correlation of the w_k */
 } moq_instance_info;
 
 /* Parameters of one sampling call ("Simulated Bifurcation with Gaussian noise"). */
@@ -245,6 +249,42 @@ int moq_lambda_das_dennis(int32_t K, int32_t H, int32_t interior, float* lambda,
  * u_k = ((word >> 8) + 1) 2^-24 with word k & 3 of Philox4x32-10(key = seed,
  * counter = (r, k >> 2, 0x4C414D42, round)). lambda: device R x K float. Asynchronous. */
 int moq_lambda_dirichlet(int32_t K, int32_t R, uint64_t seed, uint64_t round, float* lambda, void* stream);
+
+/* ---- a9 learned weight-vector proposal (not in the paper) ----------------------------
+ * A surrogate MLP (d_in -> 128 -> 128 -> d_out, ReLU; d_in <= 16, d_out <= 8) predicts the
+ * normalised cut vector an SB replica reaches for a given weight vector and graph
+ * statistics: y = W3 relu(W2 relu(W1 x + b1) + b2) + b3. Parameters are one flat vector
+ * (W1 [128 x d_in], b1, W2 [128 x 128], b2, W3 [d_out x 128], b3, row-major): an FP32
+ * master copy for the optimiser and a BF16 copy that every kernel computes with (FP32
+ * accumulation). moq_mlp_create allocates parameters, Adam state, per-block gradient slots
+ * for up to max_batch rows and proposal scratch for up to max_candidates, and initialises
+ * the weights He-uniform from Philox(seed) (biases 0). */
+typedef struct moq_mlp moq_mlp;
+int moq_mlp_create(int32_t d_in, int32_t d_out, int32_t max_batch, int32_t max_candidates, uint64_t seed, moq_mlp** out);
+void moq_mlp_destroy(moq_mlp* m);
+int64_t moq_mlp_param_count(const moq_mlp* m);
+/* Host copies of the parameters (synchronous): set writes the FP32 master and refreshes the
+ * BF16 copy; get reads the master, or the BF16 copy widened to float if bf16_rounded. */
+int moq_mlp_set_params(moq_mlp* m, const float* params_host);
+int moq_mlp_get_params(const moq_mlp* m, float* params_host, int32_t bf16_rounded);
+/* Y (device B x d_out) = MLP(X) for X (device B x d_in). Asynchronous. */
+int moq_mlp_forward(const moq_mlp* m, const float* X, int32_t B, float* Y, void* stream);
+/* Mean squared error L = 1/(B d_out) sum (y - t)^2 of the batch X, T (device, B <= max_batch)
+ * and its gradient, kept for moq_mlp_adam_step; grad_out (device, P floats) and loss_out
+ * (device, 1 float) receive copies when non-NULL. Deterministic (fixed reduction order). */
+int moq_mlp_gradient(moq_mlp* m, const float* X, const float* T, int32_t B, float* grad_out, float* loss_out, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with the last gradient. */
+int moq_mlp_adam_step(moq_mlp* m, float lr, void* stream);
+/* Proposes R weight vectors: n_candidates uniform-simplex candidates (moq_lambda_dirichlet
+ * with seed, round) get the MLP prediction p from [candidate, features]; each is scored by
+ * gap(p) = min over archive members f of max_k (p_k - (f_k - offset_k) / scale_k), the
+ * distance by which the prediction reaches beyond the nearest front member, and the R best
+ * (ties: lower candidate index) are written to lambda_out (device R x K) in score order.
+ * d_in must equal K + n_features. offset, scale: host K int64 (the cut normalisation used for
+ * the targets). Asynchronous. */
+int moq_lambda_propose(moq_mlp* m, const moq_archive* a, const float* features, int32_t n_features, const int64_t* offset,
+                       const int64_t* scale, int32_t n_candidates, uint64_t seed, uint64_t round, float* lambda_out, int32_t R,
+                       void* stream);
 
 /* ---- errors -------------------------------------------------------------------- */
 const char* moq_strerror(int code);

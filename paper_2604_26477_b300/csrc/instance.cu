@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 
 #include "moq_common.cuh"
 
@@ -154,6 +155,52 @@ __global__ void k_weight_sums(int32_t K, int64_t E, const int32_t* __restrict__ 
     }
 }
 
+// Integer weight moments for the graph statistics: per k: sum w^2, #(w > 0); per pair k < l:
+// sum w_k w_l (exact in 64-bit atomics, so the result does not depend on the order).
+__global__ void k_weight_moments(int32_t K, int64_t E, const int32_t* __restrict__ w, unsigned long long* acc)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        int q = 2 * K;
+        for (int k = 0; k < K; ++k) {
+            const int64_t v = w[k * E + e];
+            atomicAdd(&acc[2 * k], (unsigned long long)(v * v));
+            atomicAdd(&acc[2 * k + 1], (unsigned long long)(v > 0));
+            for (int l = k + 1; l < K; ++l) atomicAdd(&acc[q++], (unsigned long long)(v * (int64_t)w[l * E + e]));
+        }
+    }
+}
+
+// The 8 graph statistics of the learned proposal's input: log n, mean degree / 10, mean over
+// objectives of mean|w|/rms(w) and of std(w)/rms(w), the fraction of positive weights, and
+// the mean, min and max pairwise Pearson correlation of the objectives' weight vectors.
+void graph_features(int n, int K, int64_t E, const long long* sums, const long long* mom, float* out)
+{
+    const double e = (double)std::max<int64_t>(E, 1);
+    double shape = 0.0, spread = 0.0, pos = 0.0;
+    double mean[kMaxK], sd[kMaxK];
+    for (int k = 0; k < K; ++k) {
+        mean[k] = (double)sums[k] / e;
+        const double ms = (double)mom[2 * k] / e, rms = std::sqrt(std::max(ms, 1e-300));
+        sd[k] = std::sqrt(std::max(ms - mean[k] * mean[k], 0.0));
+        shape += ((double)sums[K + k] / e) / rms / K;
+        spread += sd[k] / rms / K;
+        pos += (double)mom[2 * k + 1] / e / K;
+    }
+    double cmean = 0.0, cmin = 1.0, cmax = -1.0;
+    int q = 2 * K, pairs = 0;
+    for (int k = 0; k < K; ++k)
+        for (int l = k + 1; l < K; ++l, ++q, ++pairs) {
+            const double cov = (double)mom[q] / e - mean[k] * mean[l];
+            const double c = (sd[k] > 0 && sd[l] > 0) ? cov / (sd[k] * sd[l]) : 0.0;
+            cmean += c;
+            cmin = std::min(cmin, c);
+            cmax = std::max(cmax, c);
+        }
+    cmean /= std::max(pairs, 1);
+    const double f[8] = {std::log((double)n), 2.0 * (double)E / n / 10.0, shape, spread, pos, cmean, cmin, cmax};
+    for (int k = 0; k < 8; ++k) out[k] = (float)f[k];
+}
+
 void free_instance(moq_instance* h)
 {
     if (!h) return;
@@ -225,7 +272,8 @@ int moq_create_instance(int32_t n, int32_t K, int64_t E, const int32_t* ei, cons
     MOQ_STEP(dalloc(&eid_tmp, h->nnz));
     MOQ_STEP(dalloc(&eid, h->nnz));
     MOQ_STEP(dalloc(&status, 2));
-    MOQ_STEP(dalloc(&sums, 3 * K));
+    const int nmom = 2 * K + K * (K - 1) / 2;  // weight moments after the 3K sums
+    MOQ_STEP(dalloc(&sums, 3 * K + nmom));
 
     auto cu = [&](cudaError_t e, const char* what) { return e == cudaSuccess ? MOQ_OK : cuda_fail(e, what); };
     if (E > 0) {
@@ -236,7 +284,7 @@ int moq_create_instance(int32_t n, int32_t K, int64_t E, const int32_t* ei, cons
     MOQ_STEP(cu(cudaMemsetAsync(deg, 0, sizeof(int32_t) * (n + 1), st), "memset"));
     MOQ_STEP(cu(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * n, st), "memset"));
     MOQ_STEP(cu(cudaMemsetAsync(status, 0, sizeof(int32_t) * 2, st), "memset"));
-    MOQ_STEP(cu(cudaMemsetAsync(sums, 0, sizeof(unsigned long long) * 3 * K, st), "memset"));
+    MOQ_STEP(cu(cudaMemsetAsync(sums, 0, sizeof(unsigned long long) * (3 * K + nmom), st), "memset"));
 
     const int tb = 256;
     const int gE = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(E, tb), 148 * 16));
@@ -250,14 +298,15 @@ int moq_create_instance(int32_t n, int32_t K, int64_t E, const int32_t* ei, cons
     k_entry_weights<<<gNNZ, tb, 0, st>>>(K, h->nnz, E, eid, h->w, h->wn);
     k_row_sums<<<gN, tb, 0, st>>>(n, K, h->nnz, h->rowptr, h->wn, h->rowsum, status + 1);
     k_weight_sums<<<gE, tb, 0, st>>>(K, E, h->w, sums);
+    k_weight_moments<<<gE, tb, 0, st>>>(K, E, h->w, sums + 3 * K);
     {
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) MOQ_STEP(cuda_fail(e, "instance build launch"));
     }
     int32_t hstatus[2] = {0, 0};
-    long long hsums[3 * kMaxK];
+    long long hsums[3 * kMaxK + 2 * kMaxK + kMaxK * (kMaxK - 1) / 2];
     MOQ_STEP(cu(cudaMemcpyAsync(hstatus, status, sizeof(hstatus), cudaMemcpyDeviceToHost, st), "read status"));
-    MOQ_STEP(cu(cudaMemcpyAsync(hsums, sums, sizeof(long long) * 3 * K, cudaMemcpyDeviceToHost, st), "read sums"));
+    MOQ_STEP(cu(cudaMemcpyAsync(hsums, sums, sizeof(long long) * (3 * K + nmom), cudaMemcpyDeviceToHost, st), "read sums"));
     MOQ_STEP(cu(cudaStreamSynchronize(st), "instance build"));
     if (hstatus[0] & kStatusBadEdge) MOQ_STEP(fail(MOQ_ERR_ARG, "moq_create_instance: an edge has i >= j or an endpoint outside [0, n)"));
     if (hstatus[0] & kStatusDuplicateEdge) MOQ_STEP(fail(MOQ_ERR_ARG, "moq_create_instance: repeated edge"));
@@ -276,6 +325,7 @@ int moq_create_instance(int32_t n, int32_t K, int64_t E, const int32_t* ei, cons
         inf.abs_sum[k] = hsums[K + k];
         inf.ref_point[k] = hsums[2 * K + k];
     }
+    graph_features(n, K, E, hsums, hsums + 3 * K, inf.features);
     *out = h;
     return MOQ_OK;
 }

@@ -1,0 +1,539 @@
+// Learned weight-vector proposal (not in the paper): a small surrogate MLP maps a weight
+// vector plus graph statistics to the expected normalised cut vector of an SB sample,
+// is trained on the (lambda, cut) pairs the sampler produces, and proposes the candidate
+// weight vectors whose predicted cuts lie furthest beyond the current front.
+//
+//   h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), y = W3 h2 + b3      (H = 128 hidden units)
+//   L  = 1 / (B D_out) sum (y - t)^2
+// Parameters: one flat FP32 master vector (W1, b1, W2, b2, W3, b3, row-major) for the
+// optimiser and its BF16 copy, which is what every kernel computes with (accumulation in
+// FP32). The fused training kernel takes a tile of 32 rows per block, keeps the weights
+// (converted from BF16) and the tile's activations in shared memory (rows padded by one
+// word against bank conflicts), runs the forward pass and backpropagation, and writes the
+// block's gradient to its own slot; a second kernel sums the slots in a fixed order, so the
+// gradient is deterministic.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <stdlib.h>
+#include <vector>
+
+#include "moq_common.cuh"
+
+namespace moq {
+namespace {
+
+constexpr int kH = 128;       // hidden width
+constexpr int kMaxIn = 16;    // D_in <= 16
+constexpr int kMaxOut = 8;    // D_out <= 8
+constexpr int kRows = 32;     // rows per block
+constexpr int kThreads = 256;
+constexpr int kLd = kH + 1;   // padded row stride of H-wide smem matrices
+
+struct MlpShape {
+    int din, dout;
+    int64_t oW1, ob1, oW2, ob2, oW3, ob3, P;
+};
+
+__host__ __device__ inline MlpShape mlp_shape(int din, int dout)
+{
+    MlpShape s;
+    s.din = din;
+    s.dout = dout;
+    s.oW1 = 0;
+    s.ob1 = s.oW1 + (int64_t)kH * din;
+    s.oW2 = s.ob1 + kH;
+    s.ob2 = s.oW2 + (int64_t)kH * kH;
+    s.oW3 = s.ob2 + kH;
+    s.ob3 = s.oW3 + (int64_t)dout * kH;
+    s.P = s.ob3 + dout;
+    return s;
+}
+
+// shared-memory layout (floats) of the fused kernels
+struct MlpSmem {
+    float* W1;  // kH x (kMaxIn + 1)
+    float* b1;
+    float* W2;  // kH x kLd
+    float* b2;
+    float* W3;  // kMaxOut x kLd
+    float* b3;
+    float* x;   // kRows x (kMaxIn + 1)
+    float* a1;  // kRows x kLd (pre-activation 1)
+    float* a2;  // kRows x kLd (pre-activation 2)
+    float* d1;  // kRows x kLd
+    float* d2;  // kRows x kLd
+    float* dy;  // kRows x kMaxOut
+};
+
+__host__ __device__ inline size_t mlp_smem_floats()
+{
+    return (size_t)kH * (kMaxIn + 1) + kH + (size_t)kH * kLd + kH + (size_t)kMaxOut * kLd + kMaxOut + (size_t)kRows * (kMaxIn + 1) +
+           4 * (size_t)kRows * kLd + (size_t)kRows * kMaxOut;
+}
+
+__device__ MlpSmem carve_mlp(float* s)
+{
+    MlpSmem m;
+    m.W1 = s; s += kH * (kMaxIn + 1);
+    m.b1 = s; s += kH;
+    m.W2 = s; s += kH * kLd;
+    m.b2 = s; s += kH;
+    m.W3 = s; s += kMaxOut * kLd;
+    m.b3 = s; s += kMaxOut;
+    m.x = s; s += kRows * (kMaxIn + 1);
+    m.a1 = s; s += kRows * kLd;
+    m.a2 = s; s += kRows * kLd;
+    m.d1 = s; s += kRows * kLd;
+    m.d2 = s; s += kRows * kLd;
+    m.dy = s;
+    return m;
+}
+
+__device__ void load_weights(const __nv_bfloat16* __restrict__ w, const MlpShape& sh, MlpSmem& m)
+{
+    for (int q = threadIdx.x; q < kH * sh.din; q += blockDim.x) m.W1[(q / sh.din) * (kMaxIn + 1) + q % sh.din] = __bfloat162float(w[sh.oW1 + q]);
+    for (int q = threadIdx.x; q < kH * kH; q += blockDim.x) m.W2[(q / kH) * kLd + q % kH] = __bfloat162float(w[sh.oW2 + q]);
+    for (int q = threadIdx.x; q < sh.dout * kH; q += blockDim.x) m.W3[(q / kH) * kLd + q % kH] = __bfloat162float(w[sh.oW3 + q]);
+    for (int q = threadIdx.x; q < kH; q += blockDim.x) {
+        m.b1[q] = __bfloat162float(w[sh.ob1 + q]);
+        m.b2[q] = __bfloat162float(w[sh.ob2 + q]);
+    }
+    for (int q = threadIdx.x; q < sh.dout; q += blockDim.x) m.b3[q] = __bfloat162float(w[sh.ob3 + q]);
+}
+
+// forward pass of the rows [row0, row0 + nr) into m.a1, m.a2 (pre-activations) and y (registers -> out)
+__device__ void forward_tile(const MlpShape& sh, MlpSmem& m, const float* __restrict__ X, int64_t row0, int nr, float* Yout,
+                             float* ysm)
+{
+    for (int q = threadIdx.x; q < kRows * sh.din; q += blockDim.x) {
+        const int r = q / sh.din, i = q % sh.din;
+        m.x[r * (kMaxIn + 1) + i] = r < nr ? X[(row0 + r) * sh.din + i] : 0.0f;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < kRows * kH; q += blockDim.x) {  // layer 1
+        const int r = q / kH, j = q % kH;
+        float s = m.b1[j];
+        for (int i = 0; i < sh.din; ++i) s = fmaf(m.W1[j * (kMaxIn + 1) + i], m.x[r * (kMaxIn + 1) + i], s);
+        m.a1[r * kLd + j] = s;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < kRows * kH; q += blockDim.x) {  // layer 2
+        const int r = q / kH, j = q % kH;
+        float s = m.b2[j];
+        const float* w = m.W2 + j * kLd;
+        const float* a = m.a1 + r * kLd;
+#pragma unroll 8
+        for (int i = 0; i < kH; ++i) s = fmaf(w[i], fmaxf(a[i], 0.0f), s);
+        m.a2[r * kLd + j] = s;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < kRows * sh.dout; q += blockDim.x) {  // layer 3
+        const int r = q / sh.dout, k = q % sh.dout;
+        float s = m.b3[k];
+        const float* w = m.W3 + k * kLd;
+        const float* a = m.a2 + r * kLd;
+        for (int i = 0; i < kH; ++i) s = fmaf(w[i], fmaxf(a[i], 0.0f), s);
+        if (ysm) ysm[r * kMaxOut + k] = s;
+        if (Yout && r < nr) Yout[(row0 + r) * sh.dout + k] = s;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads) k_mlp_forward(const __nv_bfloat16* __restrict__ w, int din, int dout, const float* __restrict__ X,
+                                                          int64_t B, float* Y)
+{
+    extern __shared__ float smem_f[];
+    const MlpShape sh = mlp_shape(din, dout);
+    MlpSmem m = carve_mlp(smem_f);
+    load_weights(w, sh, m);
+    __syncthreads();
+    for (int64_t row0 = (int64_t)blockIdx.x * kRows; row0 < B; row0 += (int64_t)gridDim.x * kRows)
+        forward_tile(sh, m, X, row0, (int)std::min<int64_t>(kRows, B - row0), Y, nullptr);
+}
+
+// Forward + backward of one tile per block; partial[block][P] gets the block's gradient,
+// loss_part[block] its share of the loss.
+__global__ void __launch_bounds__(kThreads) k_mlp_grad(const __nv_bfloat16* __restrict__ w, int din, int dout, const float* __restrict__ X,
+                                                       const float* __restrict__ T, int64_t B, float* partial, float* loss_part)
+{
+    extern __shared__ float smem_f[];
+    __shared__ float red[kThreads];
+    const MlpShape sh = mlp_shape(din, dout);
+    MlpSmem m = carve_mlp(smem_f);
+    load_weights(w, sh, m);
+    __syncthreads();
+    const int64_t row0 = (int64_t)blockIdx.x * kRows;
+    const int nr = (int)std::min<int64_t>(kRows, B - row0);
+    forward_tile(sh, m, X, row0, nr, nullptr, m.dy);
+    // dy = 2 (y - t) / (B D_out); rows beyond the batch contribute nothing
+    const float scale = 1.0f / ((float)B * dout);
+    float lsum = 0.0f;
+    for (int q = threadIdx.x; q < kRows * dout; q += blockDim.x) {
+        const int r = q / dout, k = q % dout;
+        float e = 0.0f;
+        if (r < nr) e = m.dy[r * kMaxOut + k] - T[(row0 + r) * dout + k];
+        lsum += e * e * scale;
+        m.dy[r * kMaxOut + k] = 2.0f * e * scale;
+    }
+    red[threadIdx.x] = lsum;
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) loss_part[blockIdx.x] = red[0];
+    // d2 = (W3^T dy) * [a2 > 0]
+    for (int q = threadIdx.x; q < kRows * kH; q += blockDim.x) {
+        const int r = q / kH, i = q % kH;
+        float s = 0.0f;
+        for (int k = 0; k < dout; ++k) s = fmaf(m.W3[k * kLd + i], m.dy[r * kMaxOut + k], s);
+        m.d2[r * kLd + i] = m.a2[r * kLd + i] > 0.0f ? s : 0.0f;
+    }
+    __syncthreads();
+    // d1 = (W2^T d2) * [a1 > 0]
+    for (int q = threadIdx.x; q < kRows * kH; q += blockDim.x) {
+        const int r = q / kH, i = q % kH;
+        float s = 0.0f;
+#pragma unroll 8
+        for (int j = 0; j < kH; ++j) s = fmaf(m.W2[j * kLd + i], m.d2[r * kLd + j], s);
+        m.d1[r * kLd + i] = m.a1[r * kLd + i] > 0.0f ? s : 0.0f;
+    }
+    __syncthreads();
+    float* g = partial + (int64_t)blockIdx.x * sh.P;
+    // layer 3: dW3[k][i] = sum_r dy[r][k] h2[r][i]; db3
+    for (int q = threadIdx.x; q < dout * kH; q += blockDim.x) {
+        const int k = q / kH, i = q % kH;
+        float s = 0.0f;
+        for (int r = 0; r < kRows; ++r) s = fmaf(m.dy[r * kMaxOut + k], fmaxf(m.a2[r * kLd + i], 0.0f), s);
+        g[sh.oW3 + q] = s;
+    }
+    for (int k = threadIdx.x; k < dout; k += blockDim.x) {
+        float s = 0.0f;
+        for (int r = 0; r < kRows; ++r) s += m.dy[r * kMaxOut + k];
+        g[sh.ob3 + k] = s;
+    }
+    // layer 2: dW2[j][i] = sum_r d2[r][j] h1[r][i]; db2
+    for (int q = threadIdx.x; q < kH * kH; q += blockDim.x) {
+        const int j = q / kH, i = q % kH;
+        float s = 0.0f;
+        for (int r = 0; r < kRows; ++r) s = fmaf(m.d2[r * kLd + j], fmaxf(m.a1[r * kLd + i], 0.0f), s);
+        g[sh.oW2 + q] = s;
+    }
+    for (int j = threadIdx.x; j < kH; j += blockDim.x) {
+        float s2 = 0.0f, s1 = 0.0f;
+        for (int r = 0; r < kRows; ++r) {
+            s2 += m.d2[r * kLd + j];
+            s1 += m.d1[r * kLd + j];
+        }
+        g[sh.ob2 + j] = s2;
+        g[sh.ob1 + j] = s1;
+    }
+    // layer 1: dW1[j][i] = sum_r d1[r][j] x[r][i]
+    for (int q = threadIdx.x; q < kH * din; q += blockDim.x) {
+        const int j = q / din, i = q % din;
+        float s = 0.0f;
+        for (int r = 0; r < kRows; ++r) s = fmaf(m.d1[r * kLd + j], m.x[r * (kMaxIn + 1) + i], s);
+        g[sh.oW1 + q] = s;
+    }
+}
+
+// grad[q] = sum over blocks (fixed order) of partial[b][q]; loss = sum of loss_part
+__global__ void k_mlp_reduce(const float* __restrict__ partial, const float* __restrict__ loss_part, int nblocks, int64_t P, float* grad,
+                             float* loss)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < P; q += (int64_t)gridDim.x * blockDim.x) {
+        float s = 0.0f;
+        for (int b = 0; b < nblocks; ++b) s += partial[(int64_t)b * P + q];
+        grad[q] = s;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && loss) {
+        float s = 0.0f;
+        for (int b = 0; b < nblocks; ++b) s += loss_part[b];
+        *loss = s;
+    }
+}
+
+// Adam (Kingma & Ba): m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+// p -= lr_t m / (sqrt(v) + eps) with the bias corrections folded into lr_t; BF16 copy refreshed.
+__global__ void k_mlp_adam(float* p, float* mo, float* ve, const float* __restrict__ g, int64_t P, float lr_t, float b1, float b2, float eps,
+                           __nv_bfloat16* w)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < P; q += (int64_t)gridDim.x * blockDim.x) {
+        const float gq = g[q];
+        const float mq = b1 * mo[q] + (1.0f - b1) * gq;
+        const float vq = b2 * ve[q] + (1.0f - b2) * gq * gq;
+        mo[q] = mq;
+        ve[q] = vq;
+        const float pq = p[q] - lr_t * mq / (sqrtf(vq) + eps);
+        p[q] = pq;
+        w[q] = __float2bfloat16_rn(pq);
+    }
+}
+
+// He-uniform start: W ~ U(-s, s), s = sqrt(6 / fan_in), from Philox; biases 0.
+__global__ void k_mlp_init(float* p, __nv_bfloat16* w, int din, int dout, uint32_t key0, uint32_t key1)
+{
+    const MlpShape sh = mlp_shape(din, dout);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < sh.P; q += (int64_t)gridDim.x * blockDim.x) {
+        float fan = 0.0f;
+        if (q < sh.ob1) fan = (float)din;
+        else if (q >= sh.oW2 && q < sh.ob2) fan = (float)kH;
+        else if (q >= sh.oW3 && q < sh.ob3) fan = (float)kH;
+        float v = 0.0f;
+        if (fan > 0.0f) {
+            const uint4 o = Philox4x32::block(make_uint4((uint32_t)q, 0x4D4C5031u, 0u, 0u), key0, key1);
+            v = signed_unit(o.x) * sqrtf(6.0f / fan);
+        }
+        p[q] = v;
+        w[q] = __float2bfloat16_rn(v);
+    }
+}
+
+__global__ void k_refresh_bf16(const float* __restrict__ p, int64_t P, __nv_bfloat16* w)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < P; q += (int64_t)gridDim.x * blockDim.x) w[q] = __float2bfloat16_rn(p[q]);
+}
+
+// ---- proposal ----------------------------------------------------------------------------
+// inputs of the candidates: [lambda (K), features (din - K)]
+__global__ void k_mlp_inputs(const float* __restrict__ lam, int K, int din, const float* __restrict__ feat, int C, float* X)
+{
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < C * din; q += gridDim.x * blockDim.x) {
+        const int c = q / din, i = q % din;
+        X[q] = i < K ? lam[(int64_t)c * K + i] : feat[i - K];
+    }
+}
+
+// gap(p) = min over front members f of max_k (p_k - fhat_k), fhat = (f - offset) * inv_scale:
+// how far the predicted point reaches beyond the nearest front member (> 0: undominated).
+__global__ void __launch_bounds__(256) k_front_gap(const float* __restrict__ pred, int C, int K, const int64_t* __restrict__ front,
+                                                   const int64_t* __restrict__ d_count, const float* __restrict__ offset,
+                                                   const float* __restrict__ inv_scale, float* score)
+{
+    __shared__ float tile[256][kMaxOut];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    float p[kMaxOut];
+    for (int k = 0; k < kMaxOut; ++k) p[k] = (c < C && k < K) ? pred[(int64_t)c * K + k] : 0.0f;
+    const int64_t F = *d_count;
+    float gap = INFINITY;
+    for (int64_t base = 0; base < F; base += 256) {
+        const int cnt = (int)min((int64_t)256, F - base);
+        __syncthreads();
+        if (threadIdx.x < cnt)
+            for (int k = 0; k < K; ++k) tile[threadIdx.x][k] = ((float)front[(base + threadIdx.x) * K + k] - offset[k]) * inv_scale[k];
+        __syncthreads();
+        for (int t = 0; t < cnt; ++t) {
+            float mx = -INFINITY;
+            for (int k = 0; k < K; ++k) mx = fmaxf(mx, p[k] - tile[t][k]);
+            gap = fminf(gap, mx);
+        }
+    }
+    if (c < C) score[c] = isnan(gap) ? -INFINITY : gap;
+}
+
+// rank = number of candidates with a higher score (ties: lower index first); the R best go out in rank order
+__global__ void k_top_r(const float* __restrict__ score, const float* __restrict__ lam, int C, int K, int R, float* out)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    const float s = score[c];
+    int rank = 0;
+    for (int q = 0; q < C; ++q) {
+        const float t = score[q];
+        rank += (t > s) || (t == s && q < c);
+    }
+    if (rank < R)
+        for (int k = 0; k < K; ++k) out[(int64_t)rank * K + k] = lam[(int64_t)c * K + k];
+}
+
+}  // namespace
+}  // namespace moq
+
+struct moq_mlp {
+    int din = 0, dout = 0, max_batch = 0, max_cand = 0, max_blocks = 0;
+    int64_t P = 0, step = 0;
+    float* master = nullptr;
+    __nv_bfloat16* w16 = nullptr;
+    float* grad = nullptr;
+    float* adam_m = nullptr;
+    float* adam_v = nullptr;
+    float* partial = nullptr;
+    float* loss_part = nullptr;
+    float* cand = nullptr;  // candidate lambda, inputs, predictions, scores, feature/normalisation constants
+    float* cand_in = nullptr;
+    float* cand_pred = nullptr;
+    float* cand_score = nullptr;
+    float* consts = nullptr;
+};
+
+namespace moq {
+namespace {
+
+void free_mlp(moq_mlp* m)
+{
+    if (!m) return;
+    for (void* p : {(void*)m->master, (void*)m->w16, (void*)m->grad, (void*)m->adam_m, (void*)m->adam_v, (void*)m->partial,
+                    (void*)m->loss_part, (void*)m->cand, (void*)m->cand_in, (void*)m->cand_pred, (void*)m->cand_score, (void*)m->consts})
+        cudaFree(p);
+    delete m;
+}
+
+size_t mlp_smem_bytes() { return sizeof(float) * mlp_smem_floats(); }
+
+}  // namespace
+}  // namespace moq
+
+extern "C" {
+
+int moq_mlp_create(int32_t d_in, int32_t d_out, int32_t max_batch, int32_t max_candidates, uint64_t seed, moq_mlp** out)
+{
+    using namespace moq;
+    if (!out) return fail(MOQ_ERR_ARG, "moq_mlp_create: out is NULL");
+    *out = nullptr;
+    if (d_in < 1 || d_in > kMaxIn || d_out < 1 || d_out > kMaxOut || max_batch < 1 || max_candidates < 1)
+        return fail(MOQ_ERR_ARG, "moq_mlp_create: need 1 <= d_in <= %d, 1 <= d_out <= %d, max_batch, max_candidates >= 1", kMaxIn, kMaxOut);
+    moq_mlp* m = new moq_mlp();
+    m->din = d_in;
+    m->dout = d_out;
+    m->max_batch = max_batch;
+    m->max_cand = max_candidates;
+    m->max_blocks = (int)ceil_div(max_batch, kRows);
+    m->P = mlp_shape(d_in, d_out).P;
+    cudaError_t e = cudaSuccess;
+    auto al = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
+    al((void**)&m->master, sizeof(float) * m->P);
+    al((void**)&m->w16, sizeof(__nv_bfloat16) * m->P);
+    al((void**)&m->grad, sizeof(float) * m->P);
+    al((void**)&m->adam_m, sizeof(float) * m->P);
+    al((void**)&m->adam_v, sizeof(float) * m->P);
+    al((void**)&m->partial, sizeof(float) * m->P * m->max_blocks);
+    al((void**)&m->loss_part, sizeof(float) * (m->max_blocks + 1));
+    al((void**)&m->cand, sizeof(float) * max_candidates * d_out);
+    al((void**)&m->cand_in, sizeof(float) * max_candidates * d_in);
+    al((void**)&m->cand_pred, sizeof(float) * max_candidates * d_out);
+    al((void**)&m->cand_score, sizeof(float) * max_candidates);
+    al((void**)&m->consts, sizeof(float) * 64);
+    if (e == cudaSuccess) e = cudaMemset(m->adam_m, 0, sizeof(float) * m->P);
+    if (e == cudaSuccess) e = cudaMemset(m->adam_v, 0, sizeof(float) * m->P);
+    if (e == cudaSuccess) e = cudaMemset(m->grad, 0, sizeof(float) * m->P);
+    if (e == cudaSuccess) {
+        k_mlp_init<<<64, 256>>>(m->master, m->w16, d_in, d_out, (uint32_t)seed, (uint32_t)(seed >> 32));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_smem_bytes());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_smem_bytes());
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        free_mlp(m);
+        return cuda_fail(e, "moq_mlp_create");
+    }
+    *out = m;
+    return MOQ_OK;
+}
+
+void moq_mlp_destroy(moq_mlp* m) { moq::free_mlp(m); }
+
+int64_t moq_mlp_param_count(const moq_mlp* m) { return m ? m->P : 0; }
+
+int moq_mlp_set_params(moq_mlp* m, const float* params_host)
+{
+    using namespace moq;
+    if (!m || !params_host) return fail(MOQ_ERR_ARG, "moq_mlp_set_params: NULL argument");
+    MOQ_CUDA_TRY(cudaMemcpy(m->master, params_host, sizeof(float) * m->P, cudaMemcpyHostToDevice));
+    k_refresh_bf16<<<64, 256>>>(m->master, m->P, m->w16);
+    MOQ_LAUNCH_CHECK("moq_mlp_set_params");
+    MOQ_CUDA_TRY(cudaDeviceSynchronize());
+    return MOQ_OK;
+}
+
+int moq_mlp_get_params(const moq_mlp* m, float* params_host, int32_t bf16_rounded)
+{
+    using namespace moq;
+    if (!m || !params_host) return fail(MOQ_ERR_ARG, "moq_mlp_get_params: NULL argument");
+    if (!bf16_rounded) {
+        MOQ_CUDA_TRY(cudaMemcpy(params_host, m->master, sizeof(float) * m->P, cudaMemcpyDeviceToHost));
+        return MOQ_OK;
+    }
+    std::vector<__nv_bfloat16> tmp(m->P);
+    MOQ_CUDA_TRY(cudaMemcpy(tmp.data(), m->w16, sizeof(__nv_bfloat16) * m->P, cudaMemcpyDeviceToHost));
+    for (int64_t q = 0; q < m->P; ++q) params_host[q] = __bfloat162float(tmp[q]);
+    return MOQ_OK;
+}
+
+int moq_mlp_forward(const moq_mlp* m, const float* X, int32_t B, float* Y, void* stream)
+{
+    using namespace moq;
+    if (!m || B < 0 || (B > 0 && (!X || !Y))) return fail(MOQ_ERR_ARG, "moq_mlp_forward: bad argument");
+    if (B == 0) return MOQ_OK;
+    const int grid = (int)std::min<int64_t>(ceil_div(B, kRows), 148 * 2);
+    k_mlp_forward<<<grid, kThreads, mlp_smem_bytes(), as_stream(stream)>>>(m->w16, m->din, m->dout, X, B, Y);
+    MOQ_LAUNCH_CHECK("moq_mlp_forward");
+    return MOQ_OK;
+}
+
+int moq_mlp_gradient(moq_mlp* m, const float* X, const float* T, int32_t B, float* grad_out, float* loss_out, void* stream)
+{
+    using namespace moq;
+    if (!m || B < 1 || B > m->max_batch || !X || !T) return fail(MOQ_ERR_ARG, "moq_mlp_gradient: need 1 <= B <= max_batch and inputs");
+    cudaStream_t st = as_stream(stream);
+    const int nb = (int)ceil_div(B, kRows);
+    k_mlp_grad<<<nb, kThreads, mlp_smem_bytes(), st>>>(m->w16, m->din, m->dout, X, T, B, m->partial, m->loss_part);
+    k_mlp_reduce<<<(unsigned)std::min<int64_t>(ceil_div(m->P, 256), 148), 256, 0, st>>>(m->partial, m->loss_part, nb, m->P, m->grad,
+                                                                                       loss_out ? loss_out : m->loss_part + m->max_blocks);
+    MOQ_LAUNCH_CHECK("moq_mlp_gradient");
+    if (grad_out) MOQ_CUDA_TRY(cudaMemcpyAsync(grad_out, m->grad, sizeof(float) * m->P, cudaMemcpyDeviceToDevice, st));
+    return MOQ_OK;
+}
+
+int moq_mlp_adam_step(moq_mlp* m, float lr, void* stream)
+{
+    using namespace moq;
+    if (!m || !(lr > 0.0f)) return fail(MOQ_ERR_ARG, "moq_mlp_adam_step: bad argument");
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    m->step += 1;
+    const double t = (double)m->step;
+    const float lr_t = (float)(lr * std::sqrt(1.0 - std::pow(b2, t)) / (1.0 - std::pow(b1, t)));
+    k_mlp_adam<<<(unsigned)std::min<int64_t>(ceil_div(m->P, 256), 148), 256, 0, as_stream(stream)>>>(m->master, m->adam_m, m->adam_v, m->grad,
+                                                                                                       m->P, lr_t, b1, b2, eps, m->w16);
+    MOQ_LAUNCH_CHECK("moq_mlp_adam_step");
+    return MOQ_OK;
+}
+
+int moq_lambda_propose(moq_mlp* m, const moq_archive* a, const float* features, int32_t n_features, const int64_t* offset,
+                       const int64_t* scale, int32_t n_candidates, uint64_t seed, uint64_t round, float* lambda_out, int32_t R,
+                       void* stream)
+{
+    using namespace moq;
+    if (!m || !a || !lambda_out || !offset || !scale) return fail(MOQ_ERR_ARG, "moq_lambda_propose: NULL argument");
+    const int K = m->dout;
+    if (a->K != K || n_features != m->din - K || n_features < 0 || (n_features > 0 && !features))
+        return fail(MOQ_ERR_ARG, "moq_lambda_propose: the MLP must map K + n_features inputs to the archive's K objectives");
+    if (n_candidates < 1 || n_candidates > m->max_cand || R < 0 || R > n_candidates)
+        return fail(MOQ_ERR_ARG, "moq_lambda_propose: need 1 <= R <= n_candidates <= max_candidates");
+    if (R == 0) return MOQ_OK;
+    cudaStream_t st = as_stream(stream);
+    float hc[64];
+    for (int i = 0; i < n_features; ++i) hc[i] = features[i];
+    for (int k = 0; k < K; ++k) {
+        hc[16 + k] = (float)offset[k];
+        hc[24 + k] = scale[k] > 0 ? 1.0f / (float)scale[k] : 1.0f;
+    }
+    MOQ_CUDA_TRY(cudaMemcpyAsync(m->consts, hc, sizeof(hc), cudaMemcpyHostToDevice, st));
+    int rc = moq_lambda_dirichlet(K, n_candidates, seed, round, m->cand, stream);
+    if (rc != MOQ_OK) return rc;
+    const int C = n_candidates;
+    k_mlp_inputs<<<(unsigned)ceil_div((int64_t)C * m->din, 256), 256, 0, st>>>(m->cand, K, m->din, m->consts, C, m->cand_in);
+    MOQ_LAUNCH_CHECK("moq_lambda_propose inputs");
+    rc = moq_mlp_forward(m, m->cand_in, C, m->cand_pred, stream);
+    if (rc != MOQ_OK) return rc;
+    const int64_t *fc = nullptr, *cnt = nullptr;
+    moq_archive_device_view(a, &fc, nullptr, nullptr, &cnt);
+    k_front_gap<<<(unsigned)ceil_div(C, 256), 256, 0, st>>>(m->cand_pred, C, K, fc, cnt, m->consts + 16, m->consts + 24, m->cand_score);
+    k_top_r<<<(unsigned)ceil_div(C, 256), 256, 0, st>>>(m->cand_score, m->cand, C, K, R, lambda_out);
+    MOQ_LAUNCH_CHECK("moq_lambda_propose select");
+    return MOQ_OK;
+}
+
+}  // extern "C"

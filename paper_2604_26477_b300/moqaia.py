@@ -37,7 +37,7 @@ class MoqError(RuntimeError):
 class moq_instance_info(C.Structure):
     _fields_ = [("n", C.c_int32), ("K", C.c_int32), ("E", C.c_int64), ("max_degree", C.c_int32),
                 ("words", C.c_int32), ("weight_sum", C.c_int64 * 8), ("abs_sum", C.c_int64 * 8),
-                ("ref_point", C.c_int64 * 8)]
+                ("ref_point", C.c_int64 * 8), ("features", C.c_float * 8)]
 
 
 class moq_sample_params(C.Structure):
@@ -90,6 +90,15 @@ _sigs = {
     "moq_dense_destroy": (None, [_vp]),
     "moq_sample_dense": (C.c_int, [_vp, _vp, _i32, C.POINTER(moq_sample_params), _u64, _u64, _vp, _vp]),
     "moq_dense_status": (C.c_int, [_vp, _vp]),
+    "moq_mlp_create": (C.c_int, [_i32, _i32, _i32, _i32, _u64, C.POINTER(_vp)]),
+    "moq_mlp_destroy": (None, [_vp]),
+    "moq_mlp_param_count": (_i64, [_vp]),
+    "moq_mlp_set_params": (C.c_int, [_vp, _vp]),
+    "moq_mlp_get_params": (C.c_int, [_vp, _vp, _i32]),
+    "moq_mlp_forward": (C.c_int, [_vp, _vp, _i32, _vp, _vp]),
+    "moq_mlp_gradient": (C.c_int, [_vp, _vp, _vp, _i32, _vp, _vp, _vp]),
+    "moq_mlp_adam_step": (C.c_int, [_vp, C.c_float, _vp]),
+    "moq_lambda_propose": (C.c_int, [_vp, _vp, _vp, _i32, _vp, _vp, _i32, _u64, _u64, _vp, _i32, _vp]),
     "moq_strerror": (C.c_char_p, [C.c_int]),
     "moq_last_error_message": (C.c_char_p, []),
 }
@@ -185,7 +194,7 @@ def moq_instance_get_info(h) -> dict:
     K = info.K
     return {"n": info.n, "K": K, "E": info.E, "max_degree": info.max_degree, "words": info.words,
             "weight_sum": list(info.weight_sum[:K]), "abs_sum": list(info.abs_sum[:K]),
-            "ref_point": list(info.ref_point[:K])}
+            "ref_point": list(info.ref_point[:K]), "features": list(info.features)}
 
 
 def moq_sample(inst, lam, R, params, seed, round_, bits, stream=None):
@@ -324,6 +333,55 @@ def moq_sample_dense(h, lam, R, params, seed, round_, bits, stream=None):
 
 def moq_dense_status(h, stream=None):
     _check(_lib.moq_dense_status(h, _stream(stream)), "moq_sample_dense")
+
+
+def moq_mlp_create(d_in, d_out, max_batch, max_candidates, seed) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(_lib.moq_mlp_create(d_in, d_out, max_batch, max_candidates, seed, C.byref(h)), "moq_mlp_create")
+    return h
+
+
+def moq_mlp_destroy(h):
+    _lib.moq_mlp_destroy(h)
+
+
+def moq_mlp_param_count(h) -> int:
+    return int(_lib.moq_mlp_param_count(h))
+
+
+def moq_mlp_set_params(h, params):
+    p, pp = _hptr(params, np.float32)
+    _check(_lib.moq_mlp_set_params(h, pp), "moq_mlp_set_params")
+
+
+def moq_mlp_get_params(h, bf16_rounded=False) -> np.ndarray:
+    out = np.zeros(moq_mlp_param_count(h), np.float32)
+    _check(_lib.moq_mlp_get_params(h, out.ctypes.data_as(_vp), int(bf16_rounded)), "moq_mlp_get_params")
+    return out
+
+
+def moq_mlp_forward(h, X, B, Y, stream=None):
+    f32, _, _ = _torch_types()
+    _check(_lib.moq_mlp_forward(h, _dptr(X, "X", f32), B, _dptr(Y, "Y", f32), _stream(stream)), "moq_mlp_forward")
+
+
+def moq_mlp_gradient(h, X, T, B, grad=None, loss=None, stream=None):
+    f32, _, _ = _torch_types()
+    _check(_lib.moq_mlp_gradient(h, _dptr(X, "X", f32), _dptr(T, "T", f32), B, _dptr(grad, "grad", f32),
+                                 _dptr(loss, "loss", f32), _stream(stream)), "moq_mlp_gradient")
+
+
+def moq_mlp_adam_step(h, lr, stream=None):
+    _check(_lib.moq_mlp_adam_step(h, lr, _stream(stream)), "moq_mlp_adam_step")
+
+
+def moq_lambda_propose(h, archive, features, offset, scale, n_candidates, seed, round_, lam_out, R, stream=None):
+    f32, _, _ = _torch_types()
+    feat, pf = _hptr(features, np.float32)
+    off, po = _hptr(offset, np.int64)
+    sc, ps = _hptr(scale, np.int64)
+    _check(_lib.moq_lambda_propose(h, archive, pf, feat.size, po, ps, n_candidates, seed, round_,
+                                   _dptr(lam_out, "lambda_out", f32), R, _stream(stream)), "moq_lambda_propose")
 
 
 def moq_hypervolume_noalloc_max_points() -> int:
