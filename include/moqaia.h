@@ -275,6 +275,12 @@ int moq_mlp_forward(const moq_mlp* m, const float* X, int32_t B, float* Y, void*
 int moq_mlp_gradient(moq_mlp* m, const float* X, const float* T, int32_t B, float* grad_out, float* loss_out, void* stream);
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with the last gradient. */
 int moq_mlp_adam_step(moq_mlp* m, float lr, void* stream);
+/* Training rows from M samples (device): X[m] = [lambda[m] (K), features (host, n_features)],
+ * T[m][k] = (cuts[m][k] - offset[k]) / scale[k] (host offset, scale: K int64; the learned
+ * proposal uses the reference point and sum |J^(k)|, so targets lie in [0, 1]). X: M x
+ * (K + n_features), T: M x K, device float. Asynchronous. */
+int moq_mlp_make_rows(int32_t K, int32_t n_features, const float* lambda, const int64_t* cuts, int64_t M, const float* features,
+                      const int64_t* offset, const int64_t* scale, float* X, float* T, void* stream);
 /* Proposes R weight vectors: n_candidates uniform-simplex candidates (moq_lambda_dirichlet
  * with seed, round) get the MLP prediction p from [candidate, features]; each is scored by
  * gap(p) = min over archive members f of max_k (p_k - (f_k - offset_k) / scale_k), the

@@ -296,6 +296,24 @@ __global__ void k_refresh_bf16(const float* __restrict__ p, int64_t P, __nv_bflo
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < P; q += (int64_t)gridDim.x * blockDim.x) w[q] = __float2bfloat16_rn(p[q]);
 }
 
+// Training rows from samples: X = [lambda (K), features], T_k = (C_k - offset_k) / scale_k.
+struct RowConsts {
+    float feat[kMaxIn];
+    float offset[kMaxOut];
+    float inv_scale[kMaxOut];
+};
+
+__global__ void k_mlp_rows(const float* __restrict__ lam, const int64_t* __restrict__ cuts, int64_t Mrows, int K, int din,
+                           const RowConsts c, float* X, float* T)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < Mrows * din; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = q / din;
+        const int i = (int)(q - r * din);
+        X[q] = i < K ? lam[r * K + i] : c.feat[i - K];
+        if (i < K) T[r * K + i] = ((float)cuts[r * K + i] - c.offset[i]) * c.inv_scale[i];
+    }
+}
+
 // ---- proposal ----------------------------------------------------------------------------
 // inputs of the candidates: [lambda (K), features (din - K)]
 __global__ void k_mlp_inputs(const float* __restrict__ lam, int K, int din, const float* __restrict__ feat, int C, float* X)
@@ -498,6 +516,26 @@ int moq_mlp_adam_step(moq_mlp* m, float lr, void* stream)
     k_mlp_adam<<<(unsigned)std::min<int64_t>(ceil_div(m->P, 256), 148), 256, 0, as_stream(stream)>>>(m->master, m->adam_m, m->adam_v, m->grad,
                                                                                                        m->P, lr_t, b1, b2, eps, m->w16);
     MOQ_LAUNCH_CHECK("moq_mlp_adam_step");
+    return MOQ_OK;
+}
+
+int moq_mlp_make_rows(int32_t K, int32_t n_features, const float* lambda, const int64_t* cuts, int64_t M, const float* features,
+                      const int64_t* offset, const int64_t* scale, float* X, float* T, void* stream)
+{
+    using namespace moq;
+    if (K < 1 || K > kMaxOut || n_features < 0 || K + n_features > kMaxIn || M < 0 || !offset || !scale || (n_features > 0 && !features))
+        return fail(MOQ_ERR_ARG, "moq_mlp_make_rows: bad shape or NULL constant");
+    if (M == 0) return MOQ_OK;
+    if (!lambda || !cuts || !X || !T) return fail(MOQ_ERR_ARG, "moq_mlp_make_rows: NULL device array");
+    RowConsts c{};
+    for (int i = 0; i < n_features; ++i) c.feat[i] = features[i];
+    for (int k = 0; k < K; ++k) {
+        c.offset[k] = (float)offset[k];
+        c.inv_scale[k] = scale[k] > 0 ? 1.0f / (float)scale[k] : 1.0f;
+    }
+    const int din = K + n_features;
+    k_mlp_rows<<<(unsigned)std::min<int64_t>(ceil_div(M * din, 256), 148 * 16), 256, 0, as_stream(stream)>>>(lambda, cuts, M, K, din, c, X, T);
+    MOQ_LAUNCH_CHECK("moq_mlp_make_rows");
     return MOQ_OK;
 }
 

@@ -99,6 +99,7 @@ _sigs = {
     "moq_mlp_gradient": (C.c_int, [_vp, _vp, _vp, _i32, _vp, _vp, _vp]),
     "moq_mlp_adam_step": (C.c_int, [_vp, C.c_float, _vp]),
     "moq_lambda_propose": (C.c_int, [_vp, _vp, _vp, _i32, _vp, _vp, _i32, _u64, _u64, _vp, _i32, _vp]),
+    "moq_mlp_make_rows": (C.c_int, [_i32, _i32, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "moq_strerror": (C.c_char_p, [C.c_int]),
     "moq_last_error_message": (C.c_char_p, []),
 }
@@ -373,6 +374,15 @@ def moq_mlp_gradient(h, X, T, B, grad=None, loss=None, stream=None):
 
 def moq_mlp_adam_step(h, lr, stream=None):
     _check(_lib.moq_mlp_adam_step(h, lr, _stream(stream)), "moq_mlp_adam_step")
+
+
+def moq_mlp_make_rows(K, features, lam, cuts, M, offset, scale, X, T, stream=None):
+    f32, i64, _ = _torch_types()
+    feat, pf = _hptr(features, np.float32)
+    off, po = _hptr(offset, np.int64)
+    sc, ps = _hptr(scale, np.int64)
+    _check(_lib.moq_mlp_make_rows(K, feat.size, _dptr(lam, "lambda", f32), _dptr(cuts, "cuts", i64), M, pf, po, ps,
+                                  _dptr(X, "X", f32), _dptr(T, "T", f32), _stream(stream)), "moq_mlp_make_rows")
 
 
 def moq_lambda_propose(h, archive, features, offset, scale, n_candidates, seed, round_, lam_out, R, stream=None):

@@ -149,31 +149,103 @@ def sample_round(inst: Instance, archive: Archive, buf: RoundBuffers, params, se
     archive.merge(buf.cuts, buf.bits, R, R * round_ if index_base is None else index_base, stream=stream)
 
 
+class LearnedProposer:
+    """Surrogate-guided weight vectors (the learned proposal; not in the paper).
+
+    Every round's (lambda, cut vector) pairs become training rows of the surrogate MLP
+    (inputs: lambda and the instance's 8 graph statistics; targets: cuts normalised by the
+    reference point and sum |J^(k)|), which takes ``train_steps`` Adam steps on the newest
+    rows. The next round's batch is a fraction ``rho`` of proposed weight vectors -- the
+    candidates whose predicted cuts reach furthest beyond the current front -- and the rest
+    uniform on the simplex (exploration, and the fallback before any data exists).
+    """
+
+    def __init__(self, inst: Instance, R: int, rho=0.5, n_candidates=8192, max_rows=1 << 20, train_steps=20,
+                 batch=4096, lr=3e-3, seed=0, device="cuda"):
+        self.inst, self.R, self.K = inst, R, inst.K
+        self.rho, self.n_candidates, self.train_steps, self.batch, self.lr, self.seed = \
+            rho, n_candidates, train_steps, batch, lr, seed
+        self.features = np.asarray(inst.info["features"], np.float32)
+        self.din = self.K + self.features.size
+        self.offset = np.asarray(inst.info["ref_point"], np.int64)
+        self.scale = np.maximum(np.asarray(inst.info["abs_sum"], np.int64), 1)
+        self.mlp = M.moq_mlp_create(self.din, self.K, batch, n_candidates, seed + 1)
+        self.max_rows = max_rows
+        self.X = torch.zeros((max_rows, self.din), dtype=torch.float32, device=device)
+        self.T = torch.zeros((max_rows, self.K), dtype=torch.float32, device=device)
+        self.rows = 0
+        self.lam = torch.zeros((R, self.K), dtype=torch.float32, device=device)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=device)
+
+    def lambdas(self, round_, arch: Archive):
+        n_prop = int(self.rho * self.R) if self.rows > 0 else 0
+        if n_prop > 0:
+            M.moq_lambda_propose(self.mlp, arch.handle, self.features, self.offset, self.scale, self.n_candidates,
+                                 self.seed + 7, round_, self.lam, n_prop)
+        if n_prop < self.R:
+            M.moq_lambda_dirichlet(self.K, self.R - n_prop, self.seed, round_, self.lam[n_prop:])
+        return self.lam
+
+    def observe(self, lam, cuts, m):
+        at = self.rows % self.max_rows
+        m = min(m, self.max_rows - at)
+        M.moq_mlp_make_rows(self.K, self.features, lam, cuts, m, self.offset, self.scale, self.X[at:], self.T[at:])
+        self.rows += m
+        filled = min(self.rows, self.max_rows)
+        newest = (self.rows - 1) % self.max_rows
+        for s in range(self.train_steps):  # batches walk back from the newest rows
+            end = newest + 1 - s * self.batch
+            while end <= 0:
+                end += filled
+            start = max(0, end - self.batch)
+            M.moq_mlp_gradient(self.mlp, self.X[start:end], self.T[start:end], end - start, None, self.loss)
+            M.moq_mlp_adam_step(self.mlp, self.lr)
+
+    def close(self):
+        if getattr(self, "mlp", None):
+            M.moq_mlp_destroy(self.mlp)
+            self.mlp = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def time_to_target(src, target_hv: int, params, R: int, seed: int = 0, max_rounds: int = 1000,
-                   capacity=1 << 18, lam_fn=None):
+                   capacity=1 << 18, learned: bool = False, proposer_kwargs=None):
     """Repeat sampling rounds until the archive's hypervolume reaches ``target_hv``.
 
-    The clock covers instance construction, every round and the hypervolume checks
-    (one synchronisation per round). Returns dict(seconds, rounds, samples, hv, front).
+    The clock covers instance construction, every round (weight vectors, sampling, cuts,
+    Pareto merge, the surrogate's training and proposal when ``learned``) and the
+    hypervolume checks (one synchronisation per round).
+    Returns dict(seconds, rounds, samples, hv, front, reached, trace) with trace a list of
+    (samples, hv) after each round.
     """
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     inst = Instance(src)
     arch = Archive(src.n, src.K, capacity=capacity, max_batch=R)
     buf = RoundBuffers(R, src.n, src.K)
-    hv = 0
-    rounds = 0
+    prop = LearnedProposer(inst, R, seed=seed, **(proposer_kwargs or {})) if learned else None
+    hv, rounds, trace = 0, 0, []
     while rounds < max_rounds:
-        lam = None if lam_fn is None else lam_fn(rounds, arch, buf)
+        lam = prop.lambdas(rounds, arch) if prop else None
         sample_round(inst, arch, buf, params, seed, rounds, lam=lam)
+        if prop:
+            prop.observe(lam, buf.cuts, R)
         rounds += 1
         hv = arch.hypervolume(inst.ref)
+        trace.append((rounds * R, hv))
         if hv >= target_hv:
             break
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0
     front = arch.size()
+    if prop:
+        prop.close()
     arch.close()
     inst.close()
     return {"seconds": secs, "rounds": rounds, "samples": rounds * R, "hv": hv, "front": front,
-            "reached": hv >= target_hv}
+            "reached": hv >= target_hv, "trace": trace}

@@ -1,0 +1,173 @@
+"""The learned weight-vector proposal on the GPU against the FP64 oracle: MLP forward and
+gradients (BF16 weights, FP32 accumulation), determinism, training, graph statistics and
+the front-gap proposal."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2604_26477_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+DIN, DOUT, H = 12, 4, 128
+
+
+@pytest.fixture(scope="module")
+def M():
+    from paper_2604_26477_b300 import build
+    build.build()
+    from paper_2604_26477_b300 import moqaia
+    return moqaia
+
+
+def _mlp(M, seed=3, max_batch=4096, max_cand=8192):
+    return M.moq_mlp_create(DIN, DOUT, max_batch, max_cand, seed)
+
+
+def _data(B, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(0, 1, (B, DIN)).astype(np.float32)
+    T = rng.normal(0, 1, (B, DOUT)).astype(np.float32)
+    return X, T
+
+
+def test_forward_matches_oracle(M, oracle):
+    h = _mlp(M)
+    try:
+        p = np.random.default_rng(0).normal(0, 0.2, M.moq_mlp_param_count(h)).astype(np.float32)
+        M.moq_mlp_set_params(h, p)
+        pb = M.moq_mlp_get_params(h, bf16_rounded=True).astype(np.float64)
+        X, _ = _data(1000 + 13, 1)  # many row tiles and a ragged tail
+        Y = torch.zeros((X.shape[0], DOUT), device="cuda")
+        M.moq_mlp_forward(h, torch.from_numpy(X).cuda(), X.shape[0], Y)
+        want = oracle.mlp_forward(pb, X.astype(np.float64), DIN, H, DOUT)
+        err = np.abs(Y.cpu().numpy() - want)
+        assert err.max() <= 1e-4 * max(1.0, np.abs(want).max())
+    finally:
+        M.moq_mlp_destroy(h)
+
+
+@pytest.mark.parametrize("B", [32, 777, 4096])
+def test_gradient_matches_oracle(M, oracle, B):
+    h = _mlp(M)
+    try:
+        X, T = _data(B, B)
+        Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+        P = M.moq_mlp_param_count(h)
+        g = torch.zeros(P, device="cuda")
+        loss = torch.zeros(1, device="cuda")
+        M.moq_mlp_gradient(h, Xd, Td, B, g, loss)
+        pb = M.moq_mlp_get_params(h, bf16_rounded=True).astype(np.float64)
+        L, gref = oracle.mlp_loss_grad(pb, X.astype(np.float64), T.astype(np.float64), DIN, H, DOUT)
+        assert abs(loss.item() - L) <= 1e-5 * L
+        gg = g.cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(gg - gref) <= 1e-4 * np.linalg.norm(gref)
+        # deterministic: the same call gives the same bits
+        g2 = torch.zeros_like(g)
+        M.moq_mlp_gradient(h, Xd, Td, B, g2, None)
+        assert torch.equal(g, g2)
+    finally:
+        M.moq_mlp_destroy(h)
+
+
+def test_adam_training_fits_a_smooth_map(M):
+    # targets: a smooth function of the weight-vector part of the input
+    h = _mlp(M, max_batch=4096)
+    try:
+        rng = np.random.default_rng(7)
+        lam = rng.dirichlet(np.ones(DOUT), 4096).astype(np.float32)
+        X = np.concatenate([lam, np.tile(rng.normal(0, 1, DIN - DOUT), (4096, 1))], axis=1).astype(np.float32)
+        T = np.stack([np.sin(3 * lam[:, 0]), lam[:, 1] ** 2, lam[:, 2] * lam[:, 3], 1 - lam[:, 0]], axis=1).astype(np.float32)
+        Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+        loss = torch.zeros(1, device="cuda")
+        M.moq_mlp_gradient(h, Xd, Td, 4096, None, loss)
+        first = loss.item()
+        for _ in range(400):
+            M.moq_mlp_gradient(h, Xd, Td, 4096, None, loss)
+            M.moq_mlp_adam_step(h, 3e-3)
+        M.moq_mlp_gradient(h, Xd, Td, 4096, None, loss)
+        assert loss.item() < 0.02 * first and loss.item() < 2e-3
+        # the FP32 master and its BF16 copy stay consistent
+        pm, pb = M.moq_mlp_get_params(h), M.moq_mlp_get_params(h, bf16_rounded=True)
+        assert np.allclose(pm, pb, rtol=2 ** -8, atol=1e-30)
+    finally:
+        M.moq_mlp_destroy(h)
+
+
+def test_graph_features(M):
+    from paper_2604_26477_b300 import pipeline as P
+    src = wl.app_e_correlated(60, 0.5, 4)
+    info = P.Instance(src).info
+    w = src.w.astype(np.float64)
+    rms = np.sqrt((w ** 2).mean(axis=1))
+    corr = np.corrcoef(w)
+    pairs = corr[np.triu_indices(3, 1)]
+    want = [np.log(src.n), 2 * src.E / src.n / 10, (np.abs(w).mean(axis=1) / rms).mean(), (w.std(axis=1) / rms).mean(),
+            (w > 0).mean(), pairs.mean(), pairs.min(), pairs.max()]
+    assert np.allclose(info["features"], want, rtol=1e-5, atol=1e-6)
+    assert pairs[0] < -0.5  # J1 and J2 are built negatively correlated (Appendix E)
+
+
+def test_proposal_picks_the_largest_gaps(M, oracle):
+    from paper_2604_26477_b300 import pipeline as P
+    K = DOUT
+    h = _mlp(M, seed=11)
+    arch = P.Archive(42, K, capacity=4096, max_batch=512)
+    try:
+        rng = np.random.default_rng(5)
+        front = rng.integers(0, 100, (300, K)).astype(np.int64)
+        arch.merge(torch.from_numpy(front).cuda(), torch.zeros((300, 1), dtype=torch.int64, device="cuda"), 300, 0)
+        fc, _, _ = arch.copy_out()
+        feats = rng.normal(0, 1, DIN - K).astype(np.float32)
+        offset, scale = np.zeros(K, np.int64), np.full(K, 100, np.int64)
+        C, R = 2048, 100
+        out = torch.zeros((R, K), device="cuda")
+        M.moq_lambda_propose(h, arch.handle, feats, offset, scale, C, 21, 3, out, R)
+        got = out.cpu().numpy()
+        # host recomputation from the same definition
+        cand = oracle.dirichlet(C, K, 21, 3).astype(np.float32)
+        X = np.concatenate([cand, np.tile(feats, (C, 1))], axis=1)
+        pred = oracle.mlp_forward(M.moq_mlp_get_params(h, bf16_rounded=True).astype(np.float64), X.astype(np.float64), DIN, H, DOUT)
+        fh = (fc - offset) / scale
+        gap = np.min(np.max(pred[:, None, :] - fh[None, :, :], axis=2), axis=1)
+        order = np.argsort(-gap, kind="stable")
+        # compare by score (FP32 vs FP64 may swap near-ties): the GPU's picks are the top R up to 1e-4
+        picked = [int(np.argmin(np.abs(cand - g).sum(axis=1))) for g in got]
+        assert np.allclose(cand[picked], got, atol=2e-6)
+        assert gap[picked].min() >= gap[order[R - 1]] - 1e-4
+        assert np.all(np.diff(gap[picked]) <= 1e-4)
+        assert np.allclose(got.sum(axis=1), 1, atol=1e-5)
+    finally:
+        M.moq_mlp_destroy(h)
+        arch.close()
+
+
+def _plain_final_hv(M, P, src, rounds=32):
+    inst = P.Instance(src)
+    arch = P.Archive(src.n, src.K, capacity=1 << 18, max_batch=1024)
+    buf = P.RoundBuffers(1024, src.n, src.K)
+    p = M.moq_default_params(variant="dsb", steps=1000, dt=0.5, alpha=0.0)
+    for r in range(rounds):
+        P.sample_round(inst, arch, buf, p, 4242, r)
+    return arch.hypervolume(inst.ref)
+
+
+def test_learned_proposal_saves_samples_on_held_out_instances(M):
+    # What the trained surrogate gains over uniform weight vectors: held-out random
+    # 3-regular instances (n = 300, K = 3, seeds 2000, 2001), rounds of 1024 NI-dSB replicas
+    # (T = 1000, dt = 0.5, alpha = 0.1), samples until the archive holds 99.9% of the
+    # hypervolume the plain sampler (alpha = 0, uniform weights) reaches in 32 rounds;
+    # median over three seeds. The surrogate trains on each round's (lambda, cut) pairs
+    # and proposes half of the next round's weight vectors.
+    from paper_2604_26477_b300 import pipeline as P
+    params = M.moq_default_params(variant="dsb", steps=1000, dt=0.5, alpha=0.1)
+    for seed in (2000, 2001):
+        src = wl.random_regular(300, seed, K=3, wmax=100)
+        target = int(_plain_final_hv(M, P, src) * 0.999)
+        med = {}
+        for learned in (False, True):
+            runs = [P.time_to_target(src, target, params, 1024, seed=s, max_rounds=96, learned=learned) for s in range(3)]
+            assert all(r["reached"] for r in runs)
+            med[learned] = float(np.median([r["samples"] for r in runs]))
+        print(f"instance {seed}: samples to 99.9% uniform {med[False]:.0f}, learned {med[True]:.0f}")
+        assert med[True] <= med[False]
