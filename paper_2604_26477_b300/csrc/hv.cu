@@ -59,54 +59,83 @@ struct Ref4 {
     int64_t r[4];
 };
 
+// Ranks by counting, split over a 2-D grid so that every SM takes part: block (x, y)
+// compares the kRankTile points of tile x with the kRankChunk points of chunk y and adds
+// its counts to the (zeroed) rank array; integer sums, so the result does not depend on
+// the order of the additions.
+constexpr int kRankTile = 128;
+constexpr int kRankChunk = 256;
+
 template <int KT>
-__global__ void __launch_bounds__(kThreads) k_hv_rank(const int64_t* __restrict__ pts, int64_t F, Ref4 ref, HvWs ws)
+__device__ __forceinline__ bool hv_valid(const int64_t* u, const Ref4& ref)
 {
-    __shared__ int64_t tile[kThreads][KT];
-    __shared__ int32_t tvalid[kThreads];
-    const int tid = threadIdx.x;
-    const int64_t p = blockIdx.x * (int64_t)kThreads + tid;
-    const bool act = p < F;
-    int64_t u[KT];
-    bool valid = act;
+    bool v = true;
 #pragma unroll
-    for (int k = 0; k < KT; ++k) {
-        u[k] = act ? pts[p * KT + k] : 0;
-        valid &= u[k] >= ref.r[k];
-    }
+    for (int k = 0; k < KT; ++k) v &= u[k] >= ref.r[k];
+    return v;
+}
+
+template <int KT>
+__global__ void __launch_bounds__(kRankTile) k_hv_rank_count(const int64_t* __restrict__ pts, int64_t F, Ref4 ref,
+                                                             HvWs ws)
+{
+    __shared__ int64_t tile[kRankChunk][KT];
+    __shared__ int32_t tvalid[kRankChunk];
+    const int tid = threadIdx.x;
+    const int64_t p = blockIdx.x * (int64_t)kRankTile + tid;
+    int64_t u[KT];
+#pragma unroll
+    for (int k = 0; k < KT; ++k) u[k] = p < F ? pts[p * KT + k] : 0;
+    const bool valid = p < F && hv_valid<KT>(u, ref);
     int32_t rank[KT];
 #pragma unroll
     for (int k = 0; k < KT; ++k) rank[k] = 0;
-    for (int64_t base = 0; base < F; base += kThreads) {
-        const int cnt = (int)min((int64_t)kThreads, F - base);
+    // grid.y is capped at 65535; the chunks beyond it are taken in strides
+    for (int64_t chunk = blockIdx.y; chunk * kRankChunk < F; chunk += gridDim.y) {
+        const int64_t base = chunk * kRankChunk;
+        const int cnt = (int)min((int64_t)kRankChunk, F - base);
         __syncthreads();
-        if (tid < cnt) {
-            bool v = true;
+        for (int q = tid; q < cnt; q += kRankTile) {
+            int64_t v[KT];
 #pragma unroll
-            for (int k = 0; k < KT; ++k) {
-                tile[tid][k] = pts[(base + tid) * KT + k];
-                v &= tile[tid][k] >= ref.r[k];
-            }
-            tvalid[tid] = v;
+            for (int k = 0; k < KT; ++k) v[k] = tile[q][k] = pts[(base + q) * KT + k];
+            tvalid[q] = hv_valid<KT>(v, ref);
         }
         __syncthreads();
-        if (valid) {
-            for (int t = 0; t < cnt; ++t) {
-                if (!tvalid[t]) continue;
-                const int64_t q = base + t;
+        if (!valid) continue;
+        for (int t = 0; t < cnt; ++t) {
+            if (!tvalid[t]) continue;
+            const int64_t q = base + t;
 #pragma unroll
-                for (int k = 0; k < KT; ++k) rank[k] += (tile[t][k] > u[k]) || (tile[t][k] == u[k] && q < p);
-            }
+            for (int k = 0; k < KT; ++k) rank[k] += (tile[t][k] > u[k]) || (tile[t][k] == u[k] && q < p);
         }
     }
-    if (act) {
+    if (!valid) return;
 #pragma unroll
-        for (int k = 0; k < KT; ++k) {
-            ws.rank[k * F + p] = valid ? rank[k] : -1;
-            if (valid) ws.order[k * F + rank[k]] = (int32_t)p;
-        }
-        if (valid) atomicAdd(ws.fv, 1);
+    for (int k = 0; k < KT; ++k)
+        if (rank[k]) atomicAdd(&ws.rank[k * F + p], rank[k]);
+}
+
+// Ranks of the kept points are a permutation of 0..Fv-1 in every objective: invert them
+// into the orders, mark left-out points with -1 and count the kept ones.
+template <int KT>
+__global__ void __launch_bounds__(kThreads) k_hv_rank_order(const int64_t* __restrict__ pts, int64_t F, Ref4 ref,
+                                                            HvWs ws)
+{
+    const int64_t p = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+    if (p >= F) return;
+    int64_t u[KT];
+#pragma unroll
+    for (int k = 0; k < KT; ++k) u[k] = pts[p * KT + k];
+    const bool valid = hv_valid<KT>(u, ref);
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+        if (valid)
+            ws.order[k * F + ws.rank[k * F + p]] = (int32_t)p;
+        else
+            ws.rank[k * F + p] = -1;
     }
+    if (valid) atomicAdd(ws.fv, 1);
 }
 
 __device__ i128 block_sum(i128 v, i128* red)
@@ -154,13 +183,17 @@ __global__ void __launch_bounds__(kThreads) k_hv2(const int64_t* __restrict__ pt
 }
 
 // K = 3: slab t along y_2 (order_2); area = staircase over order_0 restricted to rank_2 <= t.
-__global__ void __launch_bounds__(kThreads) k_hv3(const int64_t* __restrict__ pts, int64_t F, Ref4 ref, HvWs ws)
+// kSlab3Threads slabs per block: each block stages the whole y_0 order once, so small
+// blocks spread the slabs over more SMs at the price of more (cheap, L2-resident) staging.
+constexpr int kSlab3Threads = 64;
+
+__global__ void __launch_bounds__(kSlab3Threads) k_hv3(const int64_t* __restrict__ pts, int64_t F, Ref4 ref, HvWs ws)
 {
     __shared__ int64_t s_u0[kChunk], s_u1[kChunk];
     __shared__ int32_t s_r2[kChunk];
-    __shared__ i128 red[kThreads];
+    __shared__ i128 red[kSlab3Threads];
     const int Fv = *ws.fv;
-    const int64_t t = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+    const int64_t t = blockIdx.x * (int64_t)kSlab3Threads + threadIdx.x;
     const int32_t* ord0 = ws.order;
     const int32_t* ord2 = ws.order + 2 * F;
     const int32_t* rank2 = ws.rank + 2 * F;
@@ -177,7 +210,7 @@ __global__ void __launch_bounds__(kThreads) k_hv3(const int64_t* __restrict__ pt
         for (int64_t base = 0; base < Fv; base += kChunk) {
             const int cnt = (int)min((int64_t)kChunk, Fv - base);
             __syncthreads();
-            for (int q = threadIdx.x; q < cnt; q += kThreads) {
+            for (int q = threadIdx.x; q < cnt; q += kSlab3Threads) {
                 const int64_t p = ord0[base + q];
                 s_u0[q] = pts[p * 3];
                 s_u1[q] = pts[p * 3 + 1];
@@ -301,9 +334,13 @@ __device__ __forceinline__ int block_excl_scan_int(int v, int* warp_sums, int* t
     return res;
 }
 
-// K = 4 with the slab's points compacted: block t first gathers the t+1 points of rank_3
-// <= t into shared memory twice -- in y_0 order (the staircase walk) and in y_2 order
-// (the sub-slabs) -- so every walk touches only those points. Shared memory: 32 B per point.
+// K = 4 with the slab's points compacted: block b takes slab t = F-1-b (the largest slabs
+// first, so the long blocks start in the first wave) and gathers the t+1 points of
+// rank_3 <= t into shared memory twice -- in y_0 order (the staircase walk) and in y_2
+// order (the sub-slabs). The sub-slabs of non-zero height (one per distinct y_2 value)
+// are then packed to the front of the y_2 arrays, so consecutive threads take
+// consecutive non-empty sub-slabs and every warp walks with all its lanes busy.
+// Shared memory: 32 B per point.
 constexpr int kHv4CompactMax = 6144;
 
 __global__ void __launch_bounds__(kThreads) k_hv4_compact(const int64_t* __restrict__ pts, int64_t F, Ref4 ref, HvWs ws)
@@ -311,13 +348,13 @@ __global__ void __launch_bounds__(kThreads) k_hv4_compact(const int64_t* __restr
     extern __shared__ __align__(16) unsigned char sm[];
     int64_t* s_u0 = reinterpret_cast<int64_t*>(sm);
     int64_t* s_u1 = s_u0 + F;
-    int64_t* s_v2 = s_u1 + F;
+    int64_t* s_v2 = s_u1 + F;  // y_2 values; after packing, the sub-slab heights
     int32_t* s_r2 = reinterpret_cast<int32_t*>(s_v2 + F);
-    int32_t* s_q2 = s_r2 + F;
+    int32_t* s_q2 = s_r2 + F;  // rank_2 of the y_2-ordered points; after packing, per sub-slab
     __shared__ i128 red[kThreads];
     __shared__ int warp_sums[kThreads / 32];
     const int Fv = *ws.fv;
-    const int64_t t = blockIdx.x;
+    const int64_t t = F - 1 - (int64_t)blockIdx.x;
     const int32_t* ord0 = ws.order;
     const int32_t* ord2 = ws.order + 2 * F;
     const int32_t* ord3 = ws.order + 3 * F;
@@ -330,7 +367,7 @@ __global__ void __launch_bounds__(kThreads) k_hv4_compact(const int64_t* __restr
         h4 = top - below;
     }
     if (h4 <= 0) {  // uniform over the block
-        if (threadIdx.x == 0) ws.partial[blockIdx.x] = 0;
+        if (threadIdx.x == 0) ws.partial[t] = 0;
         return;
     }
     int cnt0 = 0, cnt2 = 0;
@@ -355,26 +392,44 @@ __global__ void __launch_bounds__(kThreads) k_hv4_compact(const int64_t* __restr
     }
     __syncthreads();
     const int c = cnt0;  // == t + 1
-    i128 acc = 0;
-    for (int s = threadIdx.x; s < c; s += kThreads) {
-        const int64_t below = s + 1 < c ? s_v2[s + 1] : ref.r[2];
-        const int64_t h3 = s_v2[s] - below;
-        if (h3 > 0) {
-            const int32_t rs = s_q2[s];
-            i128 area = 0;
-            int64_t best1 = ref.r[1];
-            for (int q = 0; q < c; ++q) {
-                const int64_t u1 = s_u1[q];
-                if (s_r2[q] <= rs && u1 > best1) {
-                    area += (i128)(s_u0[q] - ref.r[0]) * (i128)(u1 - best1);
-                    best1 = u1;
-                }
-            }
-            acc += (i128)h3 * area;
+    // pack the non-empty sub-slabs in place: chunk j reads positions [j*256, j*256+256]
+    // before the scan's barriers and writes positions below its own index afterwards, so no
+    // write lands on a position another thread has still to read
+    int nsub = 0;
+    for (int base = 0; base < c; base += kThreads) {
+        const int s = base + threadIdx.x;
+        int64_t h3 = 0;
+        int32_t rs = 0;
+        if (s < c) {
+            h3 = s_v2[s] - (s + 1 < c ? s_v2[s + 1] : ref.r[2]);
+            rs = s_q2[s];
         }
+        int tot;
+        const int pos = nsub + block_excl_scan_int(h3 > 0 ? 1 : 0, warp_sums, &tot);
+        if (h3 > 0) {
+            s_v2[pos] = h3;
+            s_q2[pos] = rs;
+        }
+        nsub += tot;
+    }
+    __syncthreads();
+    i128 acc = 0;
+    for (int j = threadIdx.x; j < nsub; j += kThreads) {
+        const int64_t h3 = s_v2[j];
+        const int32_t rs = s_q2[j];
+        i128 area = 0;
+        int64_t best1 = ref.r[1];
+        for (int q = 0; q < c; ++q) {
+            const int64_t u1 = s_u1[q];
+            if (s_r2[q] <= rs && u1 > best1) {
+                area += (i128)(s_u0[q] - ref.r[0]) * (i128)(u1 - best1);
+                best1 = u1;
+            }
+        }
+        acc += (i128)h3 * area;
     }
     const i128 sum = block_sum(acc, red);
-    if (threadIdx.x == 0) ws.partial[blockIdx.x] = (i128)h4 * sum;
+    if (threadIdx.x == 0) ws.partial[t] = (i128)h4 * sum;
 }
 
 // Sum of the block partials; flags bit 0 = the side-length product reaches 2^125.
@@ -429,21 +484,26 @@ int moq_hypervolume_points(const int64_t* pts, int64_t F, int32_t K, const int64
     Ref4 r{};
     for (int k = 0; k < K; ++k) r.r[k] = ref[k];
     MOQ_CUDA_TRY(cudaMemsetAsync(ws.fv, 0, sizeof(int32_t), st));
+    MOQ_CUDA_TRY(cudaMemsetAsync(ws.rank, 0, sizeof(int32_t) * (size_t)K * F, st));
     const unsigned gF = (unsigned)ceil_div(F, kThreads);
+    const dim3 gRank((unsigned)ceil_div(F, kRankTile), (unsigned)std::min<int64_t>(ceil_div(F, kRankChunk), 65535));
     int64_t nparts = 0;
     switch (K) {
     case 2:
-        k_hv_rank<2><<<gF, kThreads, 0, st>>>(pts, F, r, ws);
+        k_hv_rank_count<2><<<gRank, kRankTile, 0, st>>>(pts, F, r, ws);
+        k_hv_rank_order<2><<<gF, kThreads, 0, st>>>(pts, F, r, ws);
         k_hv2<<<gF, kThreads, 0, st>>>(pts, F, r, ws);
         nparts = gF;
         break;
     case 3:
-        k_hv_rank<3><<<gF, kThreads, 0, st>>>(pts, F, r, ws);
-        k_hv3<<<gF, kThreads, 0, st>>>(pts, F, r, ws);
-        nparts = gF;
+        k_hv_rank_count<3><<<gRank, kRankTile, 0, st>>>(pts, F, r, ws);
+        k_hv_rank_order<3><<<gF, kThreads, 0, st>>>(pts, F, r, ws);
+        nparts = ceil_div(F, kSlab3Threads);
+        k_hv3<<<(unsigned)nparts, kSlab3Threads, 0, st>>>(pts, F, r, ws);
         break;
     default:
-        k_hv_rank<4><<<gF, kThreads, 0, st>>>(pts, F, r, ws);
+        k_hv_rank_count<4><<<gRank, kRankTile, 0, st>>>(pts, F, r, ws);
+        k_hv_rank_order<4><<<gF, kThreads, 0, st>>>(pts, F, r, ws);
         if (F <= kHv4CompactMax) {
             const size_t smem = (size_t)32 * F;
             MOQ_CUDA_TRY(cudaFuncSetAttribute(k_hv4_compact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -542,7 +602,7 @@ int moq_hypervolume_points_noalloc(const int64_t* pts, int64_t F, int32_t K, con
     int rc = noalloc_scratch(&scratch);
     if (rc != MOQ_OK) return rc;
     // the allocating entry point, handed the fixed array as its workspace; it clears the
-    // one counter that must start at zero and overwrites the rest before reading it
+    // counter and the rank array that must start at zero and overwrites the rest before reading it
     return moq_hypervolume_points(pts, F, K, ref, scratch, out, stream);
 }
 

@@ -124,6 +124,7 @@ struct moq_archive {
     int32_t* flag_arch = nullptr;  // cap
     int32_t* flag_cand = nullptr;  // max_batch
     int64_t* blocksum = nullptr;   // scan partials
+    unsigned long long* range = nullptr;  // 2 x kMaxK per-objective min / max keys of a merge
     int64_t n_blocksum = 0;
     void* hv_ws = nullptr;         // hypervolume workspace sized for cap
     int64_t* h_pinned = nullptr;   // pinned host words for read-backs

@@ -15,6 +15,13 @@
 // old members first, then candidates by index -- into the second buffer of the archive
 // by a block scan, so the result is deterministic. Candidate representatives are
 // canonicalised to s_0 = +1 (C(s) = C(-s)).
+// Packed comparisons: when every objective spans fewer than 2^15 values over the archive
+// and the batch (one reduction per call decides, on the device), the candidate test
+// shifts each vector by the per-objective minimum and packs it into 16-bit lanes, four
+// objectives per 64-bit word. With the top bit of every lane of t set, (t | H) - u has
+// the top bit of lane k set iff t_k >= u_k and no borrow crosses a lane, so one
+// subtract and one mask test compare four objectives at once. Same decisions, fewer
+// instructions.
 #include <algorithm>
 
 #include "moq_common.cuh"
@@ -47,45 +54,159 @@ __device__ __forceinline__ bool tile_dominates(const int64_t (*tile)[KT], int cn
     return false;
 }
 
+// ---- 16-bit packed vectors ------------------------------------------------------
+constexpr uint64_t kLaneHigh = 0x8000800080008000ull;
+constexpr unsigned long long kSignBit = 0x8000000000000000ull;
+constexpr unsigned long long kPackSpan = 1ull << 15;
+
+template <int KT>
+struct Packed {
+    static constexpr int NW = (KT + 3) / 4;
+    uint64_t w[NW];
+};
+
+// Per-objective minimum and maximum over the archive and the batch, as order-preserving
+// unsigned keys (v ^ sign bit) so that 64-bit unsigned atomics order signed values;
+// range[0..K) holds the minima (preset to all ones), range[K..2K) the maxima (preset 0).
+template <int KT>
+__global__ void __launch_bounds__(kTile) k_value_range(const int64_t* __restrict__ arch, const int64_t* __restrict__ d_count,
+                                                       const int64_t* __restrict__ cand, int64_t M,
+                                                       unsigned long long* range)
+{
+    const int64_t F = *d_count, total = F + M;
+    unsigned long long lo[KT], hi[KT];
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+        lo[k] = ~0ull;
+        hi[k] = 0;
+    }
+    for (int64_t i = blockIdx.x * (int64_t)kTile + threadIdx.x; i < total; i += (int64_t)gridDim.x * kTile) {
+        const int64_t* v = i < F ? arch + i * KT : cand + (i - F) * KT;
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            const unsigned long long key = (unsigned long long)v[k] ^ kSignBit;
+            lo[k] = min(lo[k], key);
+            hi[k] = max(hi[k], key);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[k] = min(lo[k], __shfl_xor_sync(kFull, lo[k], o));
+            hi[k] = max(hi[k], __shfl_xor_sync(kFull, hi[k], o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&range[k], lo[k]);
+            atomicMax(&range[KT + k], hi[k]);
+        }
+    }
+}
+
+// True (uniformly over the grid) when every objective spans fewer than 2^15 values; lo
+// receives the per-objective minima.
+template <int KT>
+__device__ __forceinline__ bool packable(const unsigned long long* __restrict__ range, int64_t (&lo)[KT])
+{
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+        const unsigned long long a = range[k], b = range[KT + k];
+        lo[k] = (int64_t)(a ^ kSignBit);
+        ok &= a <= b && b - a < kPackSpan;
+    }
+    return ok;
+}
+
+template <int KT>
+__device__ __forceinline__ Packed<KT> pack(const int64_t (&v)[KT], const int64_t (&lo)[KT])
+{
+    Packed<KT> p;
+#pragma unroll
+    for (int w = 0; w < Packed<KT>::NW; ++w) p.w[w] = 0;
+#pragma unroll
+    for (int k = 0; k < KT; ++k) p.w[k >> 2] |= (uint64_t)(v[k] - lo[k]) << (16 * (k & 3));
+    return p;
+}
+
+// t_k >= u_k for every k, four lanes per subtract
+template <int KT>
+__device__ __forceinline__ bool packed_ge(const Packed<KT>& t, const Packed<KT>& u)
+{
+    bool ge = true;
+#pragma unroll
+    for (int w = 0; w < Packed<KT>::NW; ++w) ge &= ((~((t.w[w] | kLaneHigh) - u.w[w])) & kLaneHigh) == 0;
+    return ge;
+}
+
+template <int KT>
+__device__ __forceinline__ bool packed_eq(const Packed<KT>& t, const Packed<KT>& u)
+{
+    bool eq = true;
+#pragma unroll
+    for (int w = 0; w < Packed<KT>::NW; ++w) eq &= t.w[w] == u.w[w];
+    return eq;
+}
+
+template <int KT, bool ARCHIVE>
+__device__ __forceinline__ bool tile_dominates_packed(const Packed<KT>* tile, int cnt, const Packed<KT>& u,
+                                                      int64_t tile_base, int64_t c)
+{
+    for (int t = 0; t < cnt; ++t) {
+        const Packed<KT> v = tile[t];
+        if (packed_ge<KT>(v, u) && (ARCHIVE || tile_base + t < c || !packed_eq<KT>(v, u))) return true;
+    }
+    return false;
+}
+
 // Candidates: blockIdx.x = tile of 256 candidates, blockIdx.y = what they are compared
 // with: y < kArchChunks strides over archive tiles, y >= kArchChunks takes candidate
 // chunk y - kArchChunks. Any block that finds a dominator sets dom_cand (zeroed per call).
 template <int KT>
 __global__ void __launch_bounds__(kTile) k_dominated_candidates(const int64_t* __restrict__ arch, const int64_t* __restrict__ d_count,
-                                                                const int64_t* __restrict__ cand, int64_t M, int32_t* dom_cand)
+                                                                const int64_t* __restrict__ cand, int64_t M, int32_t* dom_cand,
+                                                                const unsigned long long* __restrict__ range)
 {
     __shared__ int64_t tile[kTile][KT];
+    Packed<KT>* ptile = reinterpret_cast<Packed<KT>*>(&tile[0][0]);  // NW <= KT words per row
     const int tid = threadIdx.x;
     const int64_t c = blockIdx.x * (int64_t)kTile + tid;
     const bool act = c < M;
     int64_t u[KT];
 #pragma unroll
     for (int k = 0; k < KT; ++k) u[k] = act ? cand[c * KT + k] : 0;
+    int64_t lo[KT];
+    const bool pk = packable<KT>(range, lo);
+    const Packed<KT> up = pack<KT>(u, lo);
     bool dropped = !act || dom_cand[c];
     const bool was = dropped;
-    if (blockIdx.y < kArchChunks) {
-        const int64_t F = *d_count;
-        for (int64_t base = (int64_t)blockIdx.y * kTile; base < F; base += (int64_t)kArchChunks * kTile) {
-            if (__syncthreads_and(dropped)) break;
-            const int cnt = (int)min((int64_t)kTile, F - base);
-            if (tid < cnt) {
+    const bool vs_archive = blockIdx.y < kArchChunks;
+    const int64_t lo_i = vs_archive ? (int64_t)blockIdx.y * kTile : (int64_t)(blockIdx.y - kArchChunks) * kChunk;
+    const int64_t hi_i = vs_archive ? *d_count : min(M, lo_i + kChunk);
+    const int64_t stride = vs_archive ? (int64_t)kArchChunks * kTile : kTile;
+    const int64_t* src = vs_archive ? arch : cand;
+    for (int64_t base = lo_i; base < hi_i; base += stride) {
+        if (__syncthreads_and(dropped)) break;
+        const int cnt = (int)min((int64_t)kTile, hi_i - base);
+        if (tid < cnt) {
+            int64_t v[KT];
 #pragma unroll
-                for (int k = 0; k < KT; ++k) tile[tid][k] = arch[(base + tid) * KT + k];
+            for (int k = 0; k < KT; ++k) v[k] = src[(base + tid) * KT + k];
+            if (pk) {
+                ptile[tid] = pack<KT>(v, lo);
+            } else {
+#pragma unroll
+                for (int k = 0; k < KT; ++k) tile[tid][k] = v[k];
             }
-            __syncthreads();
-            if (!dropped) dropped = tile_dominates<KT, true>(tile, cnt, u, base, c);
         }
-    } else {
-        const int64_t lo = (int64_t)(blockIdx.y - kArchChunks) * kChunk, hi = min(M, lo + kChunk);
-        for (int64_t base = lo; base < hi; base += kTile) {
-            if (__syncthreads_and(dropped)) break;
-            const int cnt = (int)min((int64_t)kTile, hi - base);
-            if (tid < cnt) {
-#pragma unroll
-                for (int k = 0; k < KT; ++k) tile[tid][k] = cand[(base + tid) * KT + k];
-            }
-            __syncthreads();
-            if (!dropped) dropped = tile_dominates<KT, false>(tile, cnt, u, base, c);
+        __syncthreads();
+        if (!dropped) {
+            if (pk)
+                dropped = vs_archive ? tile_dominates_packed<KT, true>(ptile, cnt, up, base, c)
+                                     : tile_dominates_packed<KT, false>(ptile, cnt, up, base, c);
+            else
+                dropped = vs_archive ? tile_dominates<KT, true>(tile, cnt, u, base, c)
+                                     : tile_dominates<KT, false>(tile, cnt, u, base, c);
         }
     }
     if (act && dropped && !was) dom_cand[c] = 1;
@@ -311,9 +432,13 @@ cudaError_t launch_filters(moq_archive* a, const int64_t* cuts, int64_t M, cudaS
     if (e == cudaSuccess && M > 0) e = cudaMemsetAsync(a->flag_cand, 0, sizeof(int32_t) * M, st);
     if (e != cudaSuccess) return e;
     if (M > 0) {
+        e = cudaMemsetAsync(a->range, 0xff, sizeof(unsigned long long) * KT, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(a->range + KT, 0, sizeof(unsigned long long) * KT, st);
+        if (e != cudaSuccess) return e;
+        k_value_range<KT><<<148, kTile, 0, st>>>(a->cuts[a->cur], a->d_count, cuts, M, a->range);
         const unsigned nchunks = (unsigned)ceil_div(M, kChunk);
         k_dominated_candidates<KT><<<dim3((unsigned)ceil_div(M, kTile), kArchChunks + nchunks), kTile, 0, st>>>(
-            a->cuts[a->cur], a->d_count, cuts, M, a->flag_cand);
+            a->cuts[a->cur], a->d_count, cuts, M, a->flag_cand, a->range);
         const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(a->cap, kTile), 32));
         k_dominated_archive<KT><<<dim3(gx, nchunks), kTile, 0, st>>>(a->cuts[a->cur], a->d_count, cuts, M, a->flag_arch);
     }
@@ -349,6 +474,7 @@ void free_archive(moq_archive* a)
     cudaFree(a->flag_arch);
     cudaFree(a->flag_cand);
     cudaFree(a->blocksum);
+    cudaFree(a->range);
     cudaFree(a->hv_ws);
     if (a->h_pinned) cudaFreeHost(a->h_pinned);
     delete a;
@@ -386,6 +512,7 @@ int moq_archive_create(int32_t n, int32_t K, int64_t capacity, int64_t max_batch
     al((void**)&a->flag_arch, sizeof(int32_t) * capacity);
     al((void**)&a->flag_cand, sizeof(int32_t) * max_batch);
     al((void**)&a->blocksum, sizeof(int64_t) * a->n_blocksum);
+    al((void**)&a->range, sizeof(unsigned long long) * 2 * kMaxK);
     al(&a->hv_ws, (size_t)moq_hypervolume_workspace_size(capacity, K));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&a->h_pinned, 64);
     if (e == cudaSuccess) e = cudaMemset(a->d_count, 0, sizeof(int64_t));

@@ -163,6 +163,26 @@ def test_pareto_archive_bit_exact(M, P, oracle, K, span, Mtot):
     _run_archive(M, P, oracle, cuts, bits, n, batches)
 
 
+@pytest.mark.parametrize("K,offset,width", [
+    (4, -(1 << 40), 32768),   # max - min = 2^15 - 1: the widest packed span, far from zero
+    (4, 5, 32769),            # one value more: the plain int64 comparison
+    (3, -(1 << 62), 1 << 63),  # near the int64 limits
+    (6, 123, 30000),          # two packed words
+])
+def test_pareto_packed_and_plain_ranges(M, P, oracle, K, offset, width):
+    # the filter packs vectors into 16-bit lanes only when every objective spans fewer than
+    # 2^15 values; both sides of that switch must give the definition's front
+    rng = np.random.default_rng(K + width % 97)
+    Mtot, n = 3000, 42
+    cuts = (offset + rng.integers(0, width, size=(Mtot, K), dtype=np.int64)).astype(np.int64)
+    cuts[:, 0] = np.where(rng.random(Mtot) < 0.3, offset + width - 1 - (cuts[:, 1] - offset) // 2, cuts[:, 0])
+    cuts[::13] = cuts[7]
+    cuts[1, :] = offset  # the span's ends are attained
+    cuts[2, 0] = offset + width - 1
+    bits = wl.random_sign_bits(Mtot, n, K)
+    _run_archive(M, P, oracle, cuts, bits, n, [list(range(0, 1800)), list(range(1800, Mtot))])
+
+
 def test_pareto_edge_cases(M, P, oracle):
     n, K = 42, 3
     arch = P.Archive(n, K, capacity=8, max_batch=64)
@@ -201,7 +221,8 @@ def test_hv_appendix_a(M):
         assert _hv_points(M, parse_points(fl[6:]), ref) == int(hl.split()[1])
 
 
-@pytest.mark.parametrize("K,F,span", [(2, 700, 10000), (3, 1500, 300), (3, 2100, 20), (4, 300, 100), (4, 260, 8)])
+@pytest.mark.parametrize("K,F,span", [(2, 700, 10000), (3, 1500, 300), (3, 2100, 20), (4, 300, 100), (4, 260, 8),
+                                      (4, 2500, 150), (4, 1100, 10 ** 6), (3, 3000, 10 ** 7)])
 def test_hv_bit_exact(M, oracle, K, F, span):
     rng = np.random.default_rng(K * 100 + F)
     pts = rng.integers(-span // 10, span, size=(F, K)).astype(np.int64)
