@@ -162,7 +162,7 @@ def cpu_baseline_worker(args):
            "kind": "oracle", "sample": f"{Rs} of {w['R']} replicas, full T={w['T']} trajectories, "
            f"then cuts, Pareto filter and hypervolume of those samples (FP64 oracle, OpenMP over replicas)",
            "seconds_per_step": Rs * src.n * w["T"] / float(np.median(results)), "front": int(len(keep)), "hv": int(hv)}
-    print("CPU_BASELINE " + json.dumps(out), flush=True)
+    print("CPU_ORACLE_RESULT " + json.dumps(out), flush=True)
 
 
 def run_cpu_baseline(cpu_seconds=15.0, steps=1):
@@ -173,8 +173,8 @@ def run_cpu_baseline(cpu_seconds=15.0, steps=1):
            "--cpu-steps", str(steps)]
     p = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=1800)
     for ln in p.stdout.splitlines():
-        if ln.startswith("CPU_BASELINE "):
-            return json.loads(ln[len("CPU_BASELINE "):])
+        if ln.startswith("CPU_ORACLE_RESULT "):
+            return json.loads(ln[len("CPU_ORACLE_RESULT "):])
     return {"value": None, "unit": METRIC, "cores": None, "kind": "oracle", "sample": "failed: " + p.stderr[-300:]}
 
 
