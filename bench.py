@@ -184,6 +184,7 @@ def gpu_arm(args, rank, world):
 
     from paper_2604_26477_b300 import moqaia as M
     from paper_2604_26477_b300 import pipeline as P
+    from paper_2604_26477_b300 import shard
     from paper_2604_26477_b300 import workloads as wl
 
     w = WORKLOAD
@@ -195,13 +196,17 @@ def gpu_arm(args, rank, world):
     inst = P.Instance(src)
     arch = P.Archive(n, K, capacity=1 << 18, max_batch=R)
     buf = P.RoundBuffers(R, n, K)
+    # weak scaling: every rank takes its own R replicas of one job of R * world replicas;
+    # the replica offset keys the noise so the shards equal one call over the whole range
+    first, _ = shard.replica_shard(R * world, rank, world)
     params = M.moq_default_params(variant=w["variant"], steps=T, dt=w["dt"], a0=w["a0"], alpha=w["alpha"],
-                                  init_amp=w["init_amp"])
+                                  init_amp=w["init_amp"], replica_offset=first)
     nsteps = args.warmup + args.steps
     # inputs resident in HBM before the timed region: one weight-vector batch per step
-    lam_all = torch.from_numpy(np.stack([wl.dirichlet_lambdas(R, K, 10_000 * rank + s) for s in range(nsteps)])).to(dev)
+    lam_all = torch.from_numpy(np.stack([wl.dirichlet_lambdas(R * world, K, 10_000 + s)[first:first + R]
+                                         for s in range(nsteps)])).to(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 126 MB L2
-    launches_per_step = 1 + 1 + 6 + 3  # sample, cuts, Pareto merge (6), hypervolume (3)
+    launches_per_step = 1 + 1 + 7 + 4  # sample, cuts, Pareto merge (7), hypervolume (4)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
     fronts, hvs = [], []
@@ -210,7 +215,7 @@ def gpu_arm(args, rank, world):
         arch.reset()
         e0, e1, e2 = ev[s]
         e0.record(stream)
-        M.moq_sample(inst.handle, lam_all[s], R, params, 1 + rank, s, buf.bits)
+        M.moq_sample(inst.handle, lam_all[s], R, params, 1, s, buf.bits)
         e1.record(stream)
         M.moq_evaluate_cuts(inst.handle, buf.bits, R, buf.cuts)
         arch.merge(buf.cuts, buf.bits, R, 0)
@@ -235,10 +240,7 @@ def gpu_arm(args, rank, world):
     step_ms = [ev[s][0].elapsed_time(ev[s][2]) for s in range(args.warmup, nsteps)]
     sample_ms = [ev[s][0].elapsed_time(ev[s][1]) for s in range(args.warmup, nsteps)]
     dev_s = sum(step_ms) / 1e3
-    times = torch.tensor([dev_s, t_wall, sum(sample_ms) / 1e3], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(times, op=torch.distributed.ReduceOp.MAX)
-    dev_s, t_wall, samp_s = times.tolist()
+    dev_s, t_wall, samp_s = shard.max_over_ranks([dev_s, t_wall, sum(sample_ms) / 1e3])
     units = R * n * T * args.steps * world
     value = units / dev_s
 
@@ -252,7 +254,7 @@ def gpu_arm(args, rank, world):
     for s in range(e2e_steps):
         lam_dev.copy_(lam_host, non_blocking=True)
         arch.reset()
-        M.moq_sample(inst.handle, lam_dev, R, params, 99 + rank, s, buf.bits)
+        M.moq_sample(inst.handle, lam_dev, R, params, 99, s, buf.bits)
         M.moq_evaluate_cuts(inst.handle, buf.bits, R, buf.cuts)
         arch.merge(buf.cuts, buf.bits, R, 0)
         arch.hypervolume(inst.ref)
@@ -330,6 +332,7 @@ def batching_arm(args, rank, world):
 
     from paper_2604_26477_b300 import moqaia as M
     from paper_2604_26477_b300 import pipeline as P
+    from paper_2604_26477_b300 import shard
     from paper_2604_26477_b300 import workloads as wl
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
@@ -375,9 +378,10 @@ def batching_arm(args, rank, world):
                 g.replay()
                 ev[k][1].record(s)
         torch.cuda.synchronize()
-    dev_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    # each rank samples its own instance set: all ranks' units over the slowest rank's time
+    dev_s = shard.max_over_ranks([sum(a.elapsed_time(b) for a, b in ev) / 1e3])[0]
     units = float(sum(src.n for src in srcs)) * R * T * args.steps
-    value = units / dev_s * world
+    value = shard.sum_over_ranks([units])[0] / dev_s
     E_mean = float(np.mean([2.0 * src.E / src.n for src in srcs]))
     ops = E_mean + 9 + 20 + 7
     achieved = ops * units / dev_s / 1e12
@@ -405,6 +409,7 @@ def dense_arm(args, rank, world):
 
     from paper_2604_26477_b300 import moqaia as M
     from paper_2604_26477_b300 import pipeline as P
+    from paper_2604_26477_b300 import shard
     from paper_2604_26477_b300 import workloads as wl
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
@@ -444,8 +449,8 @@ def dense_arm(args, rank, world):
             step(args.warmup + s, ev[s])
         torch.cuda.synchronize()
     M.moq_dense_status(d)
-    step_s = sum(e[0].elapsed_time(e[2]) for e in ev) / 1e3
-    samp_s = sum(e[0].elapsed_time(e[1]) for e in ev) / 1e3
+    step_s, samp_s = shard.max_over_ranks([sum(e[0].elapsed_time(e[2]) for e in ev) / 1e3,
+                                           sum(e[0].elapsed_time(e[1]) for e in ev) / 1e3])
     units = float(n) * R * T * args.steps
     flops = 2.0 * K * n * n * R * T * args.steps  # algorithmic: K products (n x n)(n x R) per step
     peaks = measured_peaks()
@@ -516,19 +521,22 @@ def main():
         print(json.dumps(line), flush=True)
         return
 
-    if args.workload in ("batching", "dense"):
-        line = (batching_arm if args.workload == "batching" else dense_arm)(args, rank, world)
-        if rank == 0:
-            print(json.dumps(line), flush=True)
-        return
-
     cpu_base = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if args.workload == "precision" and rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu_base = run_cpu_baseline(cpu_seconds=args.cpu_seconds)  # before any CUDA work in this process
     import torch
 
     if world > 1:
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         torch.distributed.init_process_group("nccl")
+    if args.workload in ("batching", "dense"):
+        line = (batching_arm if args.workload == "batching" else dense_arm)(args, rank, world)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
     res = gpu_arm(args, rank, world)
     ttt = None
     if rank == 0 and not args.no_ttt:

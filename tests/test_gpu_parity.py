@@ -387,6 +387,25 @@ def test_sampler_invariants_and_determinism(M, P, variant):
     assert not torch.equal(b1, b3)
 
 
+@pytest.mark.parametrize("world", [2, 3])
+def test_replica_shards_reproduce_one_call(M, P, world):
+    # the multi-GPU path: each rank samples a contiguous replica shard with the shard's first
+    # replica as offset; together the shards are bit-identical to one call over all replicas
+    from paper_2604_26477_b300.shard import replica_shard
+    src = INSTANCES["heavyhex_K4"]()
+    inst = P.Instance(src)
+    R = 1001
+    lam = _dev(wl.dirichlet_lambdas(R, 4, 12), torch.float32)
+    whole = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+    M.moq_sample(inst.handle, lam, R, M.moq_default_params(variant="dsb", steps=400, dt=0.5, alpha=0.1), 5, 3, whole)
+    for q in range(world):
+        first, count = replica_shard(R, q, world)
+        part = torch.zeros((count, inst.W), dtype=torch.int64, device="cuda")
+        p = M.moq_default_params(variant="dsb", steps=400, dt=0.5, alpha=0.1, replica_offset=first)
+        M.moq_sample(inst.handle, lam[first:first + count].contiguous(), count, p, 5, 3, part)
+        assert torch.equal(part, whole[first:first + count])
+
+
 @pytest.mark.parametrize("variant", ["dsb", "bsb"])
 def test_bipartite_reaches_max_cut(M, P, variant):
     rows, cols = 6, 7
