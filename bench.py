@@ -39,9 +39,10 @@ WORKLOAD = dict(name="precision", graph="heavy-hex-like n=42 E=50 maxdeg 3", n=4
 METRIC = "replica-spin-updates/s"
 # Algorithmic lane operations per replica-spin update of NI-dSB (derivation with the
 # design notes): force d = 2E/n multiply-adds, Euler update + wall + sign 9, one Gaussian
-# from a quarter Philox4x32-10 block (20) and half a Box-Muller pair (7).
-def ops_per_spin_update(n, E):
-    return 2.0 * E / n + 9 + 20 + 7
+# from an eighth of a Philox4x32-10 block (10 rounds x 8 ops / 8) and half a Box-Muller
+# pair on 16-bit uniforms (7).
+def ops_per_spin_update(mean_degree):
+    return mean_degree + 9 + 10 + 7
 
 
 def peak_alu_tops():
@@ -264,7 +265,7 @@ def gpu_arm(args, rank, world):
            "h2d_bytes_per_step": R * K * 4, "d2h_bytes_per_step": 8 + 4 + 8 + 4 + 16 + 4}
 
     peaks = measured_peaks()
-    ops = ops_per_spin_update(n, src.E)
+    ops = ops_per_spin_update(2.0 * src.E / n)
     sample_avg = samp_s / args.steps
     achieved = ops * R * n * T / sample_avg / 1e12
     roofline = {"bound": "alu", "kernel": "k_sb_sparse", "achieved": achieved, "peak": peak_alu_tops(),
@@ -382,8 +383,7 @@ def batching_arm(args, rank, world):
     dev_s = shard.max_over_ranks([sum(a.elapsed_time(b) for a, b in ev) / 1e3])[0]
     units = float(sum(src.n for src in srcs)) * R * T * args.steps
     value = shard.sum_over_ranks([units])[0] / dev_s
-    E_mean = float(np.mean([2.0 * src.E / src.n for src in srcs]))
-    ops = E_mean + 9 + 20 + 7
+    ops = ops_per_spin_update(float(np.mean([2.0 * src.E / src.n for src in srcs])))
     achieved = ops * units / dev_s / 1e12
     fronts = [a.size() for a in archives]
     return {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,

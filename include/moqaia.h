@@ -116,9 +116,11 @@ int moq_instance_get_info(const moq_instance* inst, moq_instance_info* out);
  *   the attractors minimise H_total, i.e. maximise the weighted cut);
  *   y += dt*(-(a0 - a_m) x + force + alpha*eta); x += dt*a0*y; |x| > 1 -> x = sgn x, y = 0;
  *   s = sgn(x) with sgn(0) = +1, written to bits (device, R x W words).
- * eta comes from Philox4x32-10 with key = seed and counter (m >> 2, i, o + r, round) through
- * Box-Muller (o = p->replica_offset); the start state from counter (0xFFFFFFFF, i, o + r, round). `seed` and
- * `round` fully determine the output on a given GPU build.
+ * eta comes from Philox4x32-10 with key = seed and counter (m >> 3, i, o + r, round)
+ * (o = p->replica_offset): word (m & 7) >> 1 gives two Gaussians by Box-Muller on its
+ * 16-bit halves, u1 = (low + 1) 2^-16, u2 = high 2^-16 (cosine for even m, sine for odd m);
+ * the start state from counter (0xFFFFFFFF, i, o + r, round). `seed` and `round` fully
+ * determine the output on a given GPU build.
  * Errors: MOQ_ERR_ARG (R < 0, steps < 0, bad variant, NULL lambda/bits with R > 0),
  * MOQ_ERR_UNSUPPORTED (n > 1024 or max degree > 16), MOQ_ERR_CUDA. Asynchronous. */
 int moq_sample(const moq_instance* inst, const float* lambda, int32_t R, const moq_sample_params* p,
@@ -161,8 +163,9 @@ int moq_evaluate_cuts_batch(const moq_batch* b, const uint64_t* bits_all, int64_
  * objective, fused update/wall/phi epilogue) on `stream`, then writes the packed signs
  * (and x_out/y_out if given). Differences from moq_sample: phi is rounded to BF16 for the
  * products (exact for dSB), the force is combined as -c0 sum_k c_k G_k, and the noise of
- * step m for replica r is Gaussian number r & 3 of Philox(key = seed, counter = (m, i,
- * 2^30 + (r >> 2), round)); the start state uses the same counter as moq_sample.
+ * step m for replica r is Gaussian number r & 7 of Philox(key = seed, counter = (m, i,
+ * 2^30 + (r >> 3), round)) (word (r & 7) >> 1, Box-Muller on 16-bit halves as in
+ * moq_sample); the start state uses the same counter as moq_sample.
  * replica_offset must be 0. Errors: MOQ_ERR_ARG, MOQ_ERR_UNSUPPORTED, MOQ_ERR_OOM,
  * MOQ_ERR_CUDA; a device wait that ran out of its 2 s budget is reported as
  * MOQ_ERR_TIMEOUT by moq_dense_status (synchronises, clears the flag). */

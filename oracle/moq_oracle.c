@@ -67,10 +67,10 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
 }
 
 /* Counter layout shared (by definition, not by code) with the CUDA sampler:
- *   noise of spin i, replica r, step m:  ctr = (m >> 2, i, r, round), key = seed
+ *   noise of spin i, replica r, step m:  ctr = (m >> 3, i, r, round), key = seed
  *   initial state of spin i, replica r:  ctr = (0xFFFFFFFF, i, r, round), key = seed
- * Words (o0,o1) and (o2,o3) each give two normals by Box-Muller; step m uses normal
- * number (m & 3) of its block: (o0,o1) -> cos, sin; (o2,o3) -> cos, sin. */
+ * Each of the four words of a block gives two normals by Box-Muller on its two 16-bit
+ * halves; step m uses word (m & 7) >> 1, the cosine for even m and the sine for odd m. */
 static void philox_at(uint64_t seed, uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3, uint32_t out[4])
 {
     uint32_t ctr[4] = {w0, w1, w2, w3};
@@ -78,15 +78,16 @@ static void philox_at(uint64_t seed, uint32_t w0, uint32_t w1, uint32_t w2, uint
     or_philox4x32_10(ctr, key, out);
 }
 
-/* Gaussian eta_{i,m} of Eq. (NI-SB): Box-Muller on two 24-bit uniforms,
- * u1 in (0, 1], u2 in [0, 1): rho = sqrt(-2 ln u1), theta = 2 pi u2. */
+/* Gaussian eta_{i,m} of Eq. (NI-SB): Box-Muller on two 16-bit uniforms of one word,
+ * u1 = (low half + 1) 2^-16 in (0, 1], u2 = (high half) 2^-16 in [0, 1):
+ * rho = sqrt(-2 ln u1), theta = 2 pi u2, eta = rho cos theta or rho sin theta. */
 double or_normal(uint64_t seed, uint64_t round, uint32_t r, uint32_t i, uint64_t m)
 {
     uint32_t o[4];
-    philox_at(seed, (uint32_t)(m >> 2), i, r, (uint32_t)round, o);
-    int pair = (int)((m & 3) >> 1);
-    double u1 = ((double)(o[2 * pair] >> 8) + 1.0) * 0x1p-24;
-    double u2 = (double)(o[2 * pair + 1] >> 8) * 0x1p-24;
+    philox_at(seed, (uint32_t)(m >> 3), i, r, (uint32_t)round, o);
+    uint32_t word = o[(m & 7) >> 1];
+    double u1 = ((double)(word & 0xFFFFu) + 1.0) * 0x1p-16;
+    double u2 = (double)(word >> 16) * 0x1p-16;
     double rho = sqrt(-2.0 * log(u1));
     double theta = 2.0 * M_PI * u2;
     return (m & 1) ? rho * sin(theta) : rho * cos(theta);

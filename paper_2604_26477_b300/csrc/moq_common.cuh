@@ -77,14 +77,22 @@ __device__ __forceinline__ float sqrt_approx(float v)
     return r;
 }
 
-// Two standard normals from two 32-bit words by Box-Muller: u1 in (0,1], u2 in [0,1),
-// rho = sqrt(-2 ln u1), theta = 2 pi u2 -> (rho cos theta, rho sin theta). The angle is
-// evaluated as 2 pi (u2 - 1/2) + pi so the fast sine/cosine see [-pi, pi); u1 and
-// u2 - 1/2 are exact in float ((w >> 8) < 2^24).
-__device__ __forceinline__ float2 box_muller(uint32_t w_a, uint32_t w_b)
+// Word q (0..3) of a Philox block; a chain of selects, so no local array is needed when
+// q is not a compile-time constant.
+__device__ __forceinline__ uint32_t word_of(const uint4& o, int q)
 {
-    const float u1 = fmaf((float)(w_a >> 8), 0x1p-24f, 0x1p-24f);
-    const float u2c = fmaf((float)(w_b >> 8), 0x1p-24f, -0.5f);
+    return q == 0 ? o.x : (q == 1 ? o.y : (q == 2 ? o.z : o.w));
+}
+
+// Two standard normals from one 32-bit word by Box-Muller on its 16-bit halves:
+// u1 = (low + 1) 2^-16 in (0, 1], u2 = high 2^-16 in [0, 1), rho = sqrt(-2 ln u1),
+// theta = 2 pi u2 -> (rho cos theta, rho sin theta). Each uniform is built exactly from
+// the bits of 1 + h 2^-16 (no integer conversion); the angle is evaluated as
+// 2 pi (u2 - 1/2) + pi so the fast sine/cosine see [-pi, pi).
+__device__ __forceinline__ float2 box_muller16(uint32_t w)
+{
+    const float u1 = __uint_as_float(0x3F800000u | ((w & 0xFFFFu) << 7)) - (1.0f - 0x1p-16f);
+    const float u2c = __uint_as_float(0x3F800000u | ((w >> 9) & 0x7FFF80u)) - 1.5f;
     const float rho = sqrt_approx(-2.0f * __logf(u1));
     float s, c;
     __sincosf(6.2831853071795864f * u2c, &s, &c);

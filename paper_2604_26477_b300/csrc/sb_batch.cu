@@ -147,16 +147,22 @@ __global__ void __launch_bounds__(SPT == 2 ? 512 : 1024) k_sb_batch(const BatchA
 
         const float dt = a.dt, kappa = a.kappa, dta0 = a.dt * a.a0, a0 = a.a0, a0inv = a.a0inv;
         const int T = a.T;
-        float e[SPT][4];
-        auto noise4 = [&](int m) {
+        // one Philox4x32-10 block per slot and eight steps: word q gives the Gaussians of
+        // steps 2q and 2q+1 (the single-instance sampler's layout)
+        uint4 blk[SPT];
+        float e[SPT][2];
+        auto block8 = [&](int m) {
+#pragma unroll
+            for (int q = 0; q < SPT; ++q)
+                blk[q] = NOISE ? Philox4x32::block(make_uint4((uint32_t)(m >> 3), (uint32_t)ii[q], rc[q], a.round32), a.key0, a.key1)
+                               : make_uint4(0u, 0u, 0u, 0u);
+        };
+        auto pairs = [&](int w) {
 #pragma unroll
             for (int q = 0; q < SPT; ++q) {
-                e[q][0] = e[q][1] = e[q][2] = e[q][3] = 0.0f;
-                if (NOISE) {
-                    const uint4 o = Philox4x32::block(make_uint4((uint32_t)(m >> 2), (uint32_t)ii[q], rc[q], a.round32), a.key0, a.key1);
-                    const float2 p = box_muller(o.x, o.y), h = box_muller(o.z, o.w);
-                    e[q][0] = p.x; e[q][1] = p.y; e[q][2] = h.x; e[q][3] = h.y;
-                }
+                const float2 p = NOISE ? box_muller16(word_of(blk[q], w)) : make_float2(0.0f, 0.0f);
+                e[q][0] = p.x;
+                e[q][1] = p.y;
             }
         };
         auto step = [&](const float* rd, float* wr, int m, float mf, int j) {
@@ -175,19 +181,27 @@ __global__ void __launch_bounds__(SPT == 2 ? 512 : 1024) k_sb_batch(const BatchA
         };
         int m = 0;
         float mf = 0.0f;
-        for (; m + 4 <= T; m += 4) {
-            noise4(m);
-            step(phiA, phiB, m, mf, 0);
-            step(phiB, phiA, m + 1, mf + 1.0f, 1);
-            step(phiA, phiB, m + 2, mf + 2.0f, 2);
-            step(phiB, phiA, m + 3, mf + 3.0f, 3);
-            mf += 4.0f;
+        for (; m + 8 <= T; m += 8) {
+            block8(m);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                pairs(w);
+                step(phiA, phiB, m + 2 * w, mf, 0);
+                step(phiB, phiA, m + 2 * w + 1, mf + 1.0f, 1);
+                mf += 2.0f;
+            }
         }
-        if (m < T) {
-            noise4(m);
-            step(phiA, phiB, m, mf, 0);
-            if (m + 1 < T) step(phiB, phiA, m + 1, mf + 1.0f, 1);
-            if (m + 2 < T) step(phiA, phiB, m + 2, mf + 2.0f, 2);
+        if (m < T) {  // the last T mod 8 steps (uniform over the block)
+            block8(m);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                if (m + 2 * w < T) {
+                    pairs(w);
+                    step(phiA, phiB, m + 2 * w, mf, 0);
+                    if (m + 2 * w + 1 < T) step(phiB, phiA, m + 2 * w + 1, mf + 1.0f, 1);
+                    mf += 2.0f;
+                }
+            }
         }
 
         // readout s_i = sgn(x_i), bit set for s_i = -1

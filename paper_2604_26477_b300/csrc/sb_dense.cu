@@ -20,8 +20,9 @@
 //
 // Exactness: J^(k) is rounded to BF16 (integers |J| <= 256 are exact); with dSB phi = +-1
 // is exact, so G_k is an exact integer sum below 2^24 for |J| <= 256; bSB rounds x to BF16.
-// Noise: Gaussian number (r & 3) of Philox4x32-10(key = seed, counter = (m, i, 2^30 +
-// (r >> 2), round)), i.e. the four replicas of an aligned quad share one block per step.
+// Noise: Gaussian number (r & 7) of Philox4x32-10(key = seed, counter = (m, i, 2^30 +
+// (r >> 3), round)) -- word (r & 7) >> 1, cosine for even r, sine for odd r, Box-Muller on
+// 16-bit halves -- i.e. the eight replicas of an aligned octet share one block per step.
 // Start state: the same counter (0xFFFFFFFF, i, r, round) as the sparse sampler.
 #include <cuda_bf16.h>
 
@@ -244,13 +245,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_step(const DenseStepArgs 
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             float eta[16];
 #pragma unroll
-            for (int q4 = 0; q4 < 4; ++q4) {
-                eta[4 * q4] = eta[4 * q4 + 1] = eta[4 * q4 + 2] = eta[4 * q4 + 3] = 0.0f;
+            for (int q8 = 0; q8 < 2; ++q8) {
+#pragma unroll
+                for (int t = 0; t < 8; ++t) eta[8 * q8 + t] = 0.0f;
                 if (NOISE) {
-                    const uint32_t quad = (uint32_t)((r0 + col0) >> 2) + q4;
-                    const uint4 o = Philox4x32::block(make_uint4((uint32_t)a.m, (uint32_t)i, 0x40000000u + quad, a.round32), a.key0, a.key1);
-                    const float2 p = box_muller(o.x, o.y), h = box_muller(o.z, o.w);
-                    eta[4 * q4] = p.x; eta[4 * q4 + 1] = p.y; eta[4 * q4 + 2] = h.x; eta[4 * q4 + 3] = h.y;
+                    const uint32_t octet = (uint32_t)((r0 + col0) >> 3) + q8;
+                    const uint4 o = Philox4x32::block(make_uint4((uint32_t)a.m, (uint32_t)i, 0x40000000u + octet, a.round32), a.key0, a.key1);
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) {
+                        const float2 p = box_muller16(word_of(o, w));
+                        eta[8 * q8 + 2 * w] = p.x;
+                        eta[8 * q8 + 2 * w + 1] = p.y;
+                    }
                 }
             }
             if (i < a.n) {

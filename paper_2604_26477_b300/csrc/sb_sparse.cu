@@ -7,8 +7,9 @@
 // phi[j * Rb + replica] and a warp's gathers hit consecutive words. Each thread keeps
 // x_i, y_i and its row of -c0 * J(c) (DMAX entries, zero-padded) in registers; per step
 // the only memory traffic is the shared-memory gather, one store and one barrier.
-// The step loop is unrolled by four: one Philox4x32-10 block gives the four Gaussians
-// of four consecutive steps, and the two phi buffers alternate at a fixed offset.
+// The step loop is unrolled by eight: one Philox4x32-10 block gives the eight Gaussians
+// of eight consecutive steps (two per word), and the two phi buffers alternate at a fixed
+// offset.
 // HBM sees the CSR rows and lambda once (in) and the packed signs once (out).
 #include <algorithm>
 #include <stdlib.h>
@@ -98,14 +99,18 @@ __global__ void __launch_bounds__(1024) k_sb_sparse(const SbArgs a)
         if (d < deg) {
             const int p = p0 + d;
             c = a.col[p];
-            for (int k = 0; k < a.K; ++k) v = fmaf(lam[k], (float)a.wn[(int64_t)k * a.nnz + p], v);
+#pragma unroll
+            for (int k = 0; k < kMaxK; ++k)  // constant indices keep lam in registers
+                if (k < a.K) v = fmaf(lam[k], (float)a.wn[(int64_t)k * a.nnz + p], v);
         }
         jc[d] = v;
         nb[d] = c * Rb + lr;
         sabs += fabsf(v);
     }
     float srow = 0.0f;
-    for (int k = 0; k < a.K; ++k) srow = fmaf(lam[k], (float)a.rowsum[(int64_t)i * a.K + k], srow);
+#pragma unroll
+    for (int k = 0; k < kMaxK; ++k)
+        if (k < a.K) srow = fmaf(lam[k], (float)a.rowsum[(int64_t)i * a.K + k], srow);
 
     // c0 = 1 / max_i |sum_j J(c)_ij| per replica (fallbacks: sum |J(c)_ij|, then 1);
     // non-negative floats order like their bit patterns, so an integer max reduces them
@@ -136,27 +141,55 @@ __global__ void __launch_bounds__(1024) k_sb_sparse(const SbArgs a)
     const float* sched = a.schedule;
     const int T = a.T;
     auto cm_at = [&](int m, float mf) -> float { return LINEAR ? fmaf(a0inv, mf, -a0) : (__ldg(sched + m) - a0); };
-    auto noise4 = [&](int m, float& e0, float& e1, float& e2, float& e3) {
+    // one Philox4x32-10 block per eight steps: word q gives the Gaussians of steps 2q, 2q+1
+    auto block8 = [&](int m) -> uint4 {
+        return NOISE ? Philox4x32::block(make_uint4((uint32_t)(m >> 3), (uint32_t)i, a.rep_off + (uint32_t)r, a.round32),
+                                         a.key0, a.key1)
+                     : make_uint4(0u, 0u, 0u, 0u);
+    };
+    // the Gaussians of four consecutive steps from two words
+    auto noise4 = [&](uint32_t wa, uint32_t wb, float& e0, float& e1, float& e2, float& e3) {
         if (NOISE) {
-            const uint4 o = Philox4x32::block(make_uint4((uint32_t)(m >> 2), (uint32_t)i, a.rep_off + (uint32_t)r, a.round32), a.key0, a.key1);
-            const float2 p = box_muller(o.x, o.y), q = box_muller(o.z, o.w);
+            const float2 p = box_muller16(wa), q = box_muller16(wb);
             e0 = p.x; e1 = p.y; e2 = q.x; e3 = q.y;
         }
     };
-    int m = 0;
-    float mf = 0.0f;
-    for (; m + 4 <= T; m += 4) {
-        float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f, e3 = 0.0f;
-        noise4(m, e0, e1, e2, e3);
+    auto four_steps = [&](int m, float mf, float e0, float e1, float e2, float e3) {
         sb_step<VARIANT, DMAX, NOISE>(phiA, phiB, tid, jc, nb, cm_at(m, mf), e0, dt, kappa, dta0, x, y);
         sb_step<VARIANT, DMAX, NOISE>(phiB, phiA, tid, jc, nb, cm_at(m + 1, mf + 1.0f), e1, dt, kappa, dta0, x, y);
         sb_step<VARIANT, DMAX, NOISE>(phiA, phiB, tid, jc, nb, cm_at(m + 2, mf + 2.0f), e2, dt, kappa, dta0, x, y);
         sb_step<VARIANT, DMAX, NOISE>(phiB, phiA, tid, jc, nb, cm_at(m + 3, mf + 3.0f), e3, dt, kappa, dta0, x, y);
+    };
+    // the Gaussians of steps m..m+3 (m a multiple of 4): words (x, y) or (z, w) of the block
+    auto noise_at = [&](int m, float& e0, float& e1, float& e2, float& e3) {
+        if (NOISE) {
+            const uint4 o = block8(m);
+            noise4((m & 4) ? o.z : o.x, (m & 4) ? o.w : o.y, e0, e1, e2, e3);
+        }
+    };
+    int m = 0;
+    float mf = 0.0f;
+    if (NOISE) {
+        for (; m + 8 <= T; m += 8) {
+            const uint4 o = block8(m);
+            float e0, e1, e2, e3;
+            noise4(o.x, o.y, e0, e1, e2, e3);
+            four_steps(m, mf, e0, e1, e2, e3);
+            noise4(o.z, o.w, e0, e1, e2, e3);
+            four_steps(m + 4, mf + 4.0f, e0, e1, e2, e3);
+            mf += 8.0f;
+        }
+    }
+    // without noise the whole run; with noise at most one pass (T mod 8 >= 4)
+    for (; m + 4 <= T; m += 4) {
+        float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f, e3 = 0.0f;
+        noise_at(m, e0, e1, e2, e3);
+        four_steps(m, mf, e0, e1, e2, e3);
         mf += 4.0f;
     }
     if (m < T) {  // the last T mod 4 steps (uniform over the block)
         float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f, e3 = 0.0f;
-        noise4(m, e0, e1, e2, e3);
+        noise_at(m, e0, e1, e2, e3);
         sb_step<VARIANT, DMAX, NOISE>(phiA, phiB, tid, jc, nb, cm_at(m, mf), e0, dt, kappa, dta0, x, y);
         if (m + 1 < T) sb_step<VARIANT, DMAX, NOISE>(phiB, phiA, tid, jc, nb, cm_at(m + 1, mf + 1.0f), e1, dt, kappa, dta0, x, y);
         if (m + 2 < T) sb_step<VARIANT, DMAX, NOISE>(phiA, phiB, tid, jc, nb, cm_at(m + 2, mf + 2.0f), e2, dt, kappa, dta0, x, y);

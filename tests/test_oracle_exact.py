@@ -31,9 +31,18 @@ def test_normal_moments_and_ks(oracle):
     z = np.array([oracle.normal(7, 3, r, i, m) for r in range(4) for i in range(50) for m in range(100)])
     assert abs(z.mean()) < 0.03 and abs(z.var() - 1.0) < 0.04
     assert stats.kstest(z, "norm").pvalue > 1e-3
-    # the four normals of one Philox block are distinct draws (cos/sin of two pairs)
-    blk = [oracle.normal(1, 0, 0, 0, m) for m in range(4)]
-    assert len(set(blk)) == 4
+    assert abs(stats.kurtosis(z, fisher=False) - 3.0) < 0.2
+    # the eight normals of one Philox block are distinct draws (cos/sin of four pairs)
+    blk = [oracle.normal(1, 0, 0, 0, m) for m in range(8)]
+    assert len(set(blk)) == 8
+    # 16-bit uniforms: u1 >= 2^-16 bounds every pair's radius by sqrt(32 ln 2); the pair's
+    # angle is uniform on the circle
+    pairs = z.reshape(-1, 2)
+    rad2 = (pairs ** 2).sum(axis=1)
+    assert rad2.max() <= 32 * np.log(2) + 1e-9
+    assert stats.kstest(1 - np.exp(-rad2 / 2), "uniform").pvalue > 1e-3  # rho^2 / 2 ~ Exp(1)
+    ang = (np.arctan2(pairs[:, 1], pairs[:, 0]) + np.pi) / (2 * np.pi)
+    assert stats.kstest(ang, "uniform").pvalue > 1e-3
 
 
 def test_initial_state_uniform(oracle):
