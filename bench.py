@@ -467,6 +467,8 @@ def dense_arm(args, rank, world):
                        "n": n, "R": R, "T": T},
             "roofline": {"bound": "tensor", "kernel": "k_dense_step (all T launches)", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": profile_traffic("sb_dense.cu", "dense_step_n2000_K3_R8192.txt")
+                         if (n, R) == (2000, 8192) else None,
                          "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16, seconds-long loop)"},
             "sampling_only_value": units / samp_s * world, "sampler_ms": samp_s / args.steps * 1e3,
             "clocks": clk.summary(), "front_points_last_step": front, "hv_last_step": int(hv[0])}

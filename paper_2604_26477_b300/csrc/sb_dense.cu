@@ -4,14 +4,18 @@
 // step computes G_k = J^(k) Phi for all K objectives with tcgen05.mma and applies the
 // symplectic update, the wall and the next phi in the epilogue.
 //
-// Step kernel, one CTA per tile of 128 spins (M) x 128 replicas (N):
-//  - the K-dimension (spins j) is walked in chunks of 64: J^(k)[i0:+128, j0:+64] for each
-//    objective and Phi[r0:+128, j0:+64] are copied into shared memory (cp.async, 16 B per
-//    thread; three stages for K <= 3, two for K = 4, copies issued that many chunks minus
-//    one ahead) in the 128-byte-swizzled K-major layout the tensor core reads;
-//  - one thread issues tcgen05.mma (BF16 x BF16 -> FP32, M=128, N=128, K=16) into one TMEM
-//    accumulator per objective (K x 128 of the 512 columns) and tcgen05.commit signals an
-//    mbarrier per stage, so copies of later chunks overlap the products of chunk c;
+// Step kernel, one CTA per tile of 128 spins (M) x 128 replicas (N), launched in clusters
+// of CL CTAs that share the spin tile (consecutive replica tiles):
+//  - the K-dimension (spins j) is walked in chunks of 64. A producer thread loads the
+//    chunk's operands with TMA into the 128-byte-swizzled K-major layout the tensor core
+//    reads: J^(k)[i0:+128, j0:+64] of every objective is shared by the cluster, so each CTA
+//    loads 128/CL of its rows and multicasts them to all CL CTAs (one L2 read feeds CL
+//    SMs); Phi[r0:+128, j0:+64] is the CTA's own. Three stages for K <= 3, two for K = 4;
+//  - an MMA thread waits for a stage's "full" barrier (own and peers' bytes landed),
+//    issues tcgen05.mma (BF16 x BF16 -> FP32, M=128, N=128, K=16) into one TMEM
+//    accumulator per objective (K x 128 of the 512 columns), and tcgen05.commit arrives on
+//    the stage's "empty" barrier of every CTA in the cluster; a producer refills a stage
+//    only when all CL CTAs have released it;
 //  - the epilogue (16 warps; warp w reads TMEM lanes 32*(w%4).. of columns 32*(w/4)..) forms
 //    f = -c0_r sum_k c_rk G_k[i, r], updates x, y (FP32, in HBM), applies the wall and
 //    writes phi(x) as BF16 for the next step.
@@ -24,7 +28,9 @@
 // (r >> 3), round)) -- word (r & 7) >> 1, cosine for even r, sine for odd r, Box-Muller on
 // 16-bit halves -- i.e. the eight replicas of an aligned octet share one block per step.
 // Start state: the same counter (0xFFFFFFFF, i, r, round) as the sparse sampler.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <stdlib.h>
@@ -39,6 +45,9 @@ struct moq_dense {
     float* y = nullptr;                          // R_pad x n_pad
     __nv_bfloat16* phi[2] = {nullptr, nullptr};  // R_pad x n_pad
     float* c0 = nullptr;                         // R_pad
+    CUtensorMap tm_J;                            // K x n_pad x n_pad, box 64 x (128 / CL) x 1
+    CUtensorMap tm_phi[2];                       // R_pad x n_pad, box 64 x 128
+    int32_t cluster = 1;                         // CTAs per cluster sharing J tiles
     int32_t* status = nullptr;                   // device error flags
     int32_t* h_status = nullptr;                 // pinned
 };
@@ -52,6 +61,7 @@ constexpr int kThreads = 512;
 // three operand stages (prefetch distance 2) when they fit in shared memory, else two
 __host__ __device__ constexpr int dense_stages(int K) { return K <= 3 ? 3 : 2; }
 constexpr uint64_t kWaitNs = 2000000000ull;        // bound of every mbarrier wait (2 s)
+constexpr int kMaxCluster = 4;                     // replica tiles sharing one J tile
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -96,6 +106,42 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t 
                  : "memory");
 }
 
+// TMA tiled loads into shared memory, completing bytes on an mbarrier; the multicast form
+// writes the same box (and signals the barrier at the same offset) in every CTA of mask.
+__device__ __forceinline__ void tma_load_3d_mc(uint32_t dst, const CUtensorMap* tm, int c0, int c1, int c2, uint32_t mbar,
+                                               uint16_t mask)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%2, %3, %4}], "
+        "[%5], %6;" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(mbar), "h"(mask)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, int c2, uint32_t mbar)
+{
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+                 "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, uint32_t mbar)
+{
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+                 "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 {
     uint32_t u[16];
@@ -110,8 +156,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 }
 
 struct DenseStepArgs {
-    const __nv_bfloat16* J;
-    const __nv_bfloat16* phi_in;
     __nv_bfloat16* phi_out;
     float* x;
     float* y;
@@ -125,32 +169,47 @@ struct DenseStepArgs {
     int32_t* status;
 };
 
-template <int VARIANT, int KOBJ, bool NOISE>
-__global__ void __launch_bounds__(kThreads, 1) k_dense_step(const DenseStepArgs a)
+template <int VARIANT, int KOBJ, bool NOISE, int CL>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_dense_step(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmPhi, const DenseStepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // 1024-aligned operand stages: stage s holds KOBJ J tiles then the Phi tile
+    // 1024-aligned operand stages: stage s holds KOBJ J tiles then the Phi tile. The offset
+    // of every buffer below is the same in all CTAs (same kernel, same dynamic size), which
+    // the multicast copies and commits rely on.
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     unsigned char* gbase = smem_raw + (base - raw);
     constexpr int kStageBytes = (KOBJ + 1) * kTileBytes;
-    constexpr int S = dense_stages(KOBJ), D = S - 1;  // stages and prefetch distance
+    constexpr int S = dense_stages(KOBJ);
+    constexpr int kSliceRows = kTileM / CL;  // J rows each CTA of the cluster loads and multicasts
+    constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
     float* lam_s = reinterpret_cast<float*>(gbase + S * kStageBytes);  // kTileN x KOBJ
     float* c0_s = lam_s + kTileN * KOBJ;                                // kTileN
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(c0_s + kTileN);        // S (8-aligned: offsets are multiples of 8)
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + S);
+    uint64_t* full = reinterpret_cast<uint64_t*>(c0_s + kTileN);        // S (8-aligned: offsets are multiples of 8)
+    uint64_t* empty = full + S;                                         // S
+    uint64_t* done = empty + S;                                         // 1
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int i0 = blockIdx.x * kTileM, r0 = blockIdx.y * kTileN;
     const int np = a.n_pad;
+    uint32_t rank = 0;
+    if (CL > 1) asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)), "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[s])), "r"(1));
+        for (int s = 0; s < S; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[s])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[s])), "r"(CL));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(done)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmJ)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmPhi)) : "memory");
     }
     for (int q = tid; q < kTileN; q += kThreads) {
         const int r = r0 + q;
@@ -160,58 +219,67 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_step(const DenseStepArgs 
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
+    if (CL > 1) cluster_sync();  // every CTA's barriers are initialised before any copy targets them
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
 
     // ---- main loop: products of all objectives over the spin chunks ----
-    // Chunk c lives in stage c % S; its copy is issued D chunks ahead, after the products
-    // that last read the stage (chunk c - 1) are done. Every iteration commits exactly one
-    // cp.async group (possibly empty), so "all but the newest D groups" is chunk c.
     const int nchunks = np / kChunkK;
-    auto issue_copy = [&](int c) {
-        const uint32_t stage = base + (c % S) * kStageBytes;
-        const int j0 = c * kChunkK;
-        constexpr int kChunks16 = (KOBJ + 1) * kTileM * (kChunkK * 2 / 16);
-        for (int q = tid; q < kChunks16; q += kThreads) {
-            const int tile = q / (kTileM * 8), rem = q - tile * kTileM * 8, row = rem >> 3, cc = rem & 7;
-            const __nv_bfloat16* src = tile < KOBJ ? a.J + ((int64_t)tile * np + i0 + row) * np + j0 + cc * 8
-                                                   : a.phi_in + (int64_t)(r0 + row) * np + j0 + cc * 8;
-            const uint32_t dst = stage + tile * kTileBytes + (row >> 3) * 1024 + (row & 7) * 128 + ((cc ^ (row & 7)) << 4);
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-        }
-    };
-    for (int c = 0; c < D; ++c) {
-        if (c < nchunks) issue_copy(c);
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    }
     bool ok = true;
-    int last = -1;  // last chunk whose products were committed
-    for (int c = 0; c < nchunks; ++c) {
-        const int cn = c + D;
-        if (cn < nchunks && cn >= S) {  // stage cn % S was last read by chunk cn - S
-            if (!mbar_wait(smem_u32(&mbar[cn % S]), (uint32_t)(((cn - S) / S) & 1))) ok = false;
+    if (tid == 0) {
+        // producer: chunk c goes to stage c % S once every CTA of the cluster has released
+        // the stage's previous contents (chunk c - S)
+        for (int c = 0; c < nchunks && ok; ++c) {
+            const int st = c % S;
+            if (c >= S && !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((c - S) / S) & 1))) {
+                ok = false;
+                break;
+            }
+            const uint32_t stage = base + st * kStageBytes, fb = smem_u32(&full[st]);
+            mbar_expect_tx(fb, (uint32_t)kStageBytes);
+            const int j0 = c * kChunkK;
+#pragma unroll
+            for (int k = 0; k < KOBJ; ++k) {
+                const uint32_t dst = stage + k * kTileBytes + rank * (kSliceRows * kChunkK * 2);
+                if (CL > 1) tma_load_3d_mc(dst, &tmJ, j0, i0 + (int)rank * kSliceRows, k, fb, kMask);
+                else tma_load_3d(dst, &tmJ, j0, i0, k, fb);
+            }
+            tma_load_2d(stage + KOBJ * kTileBytes, &tmPhi, j0, r0, fb);
         }
-        if (!__syncthreads_and(ok)) break;
-        if (cn < nchunks) issue_copy(cn);
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group %0;" ::"n"(D) : "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            const uint32_t stage = base + (c % S) * kStageBytes;
+        // every peer's release of every stage has arrived before this CTA may leave
+        for (int st = 0; st < S && st < nchunks && ok; ++st) {
+            const int c_last = st + ((nchunks - 1 - st) / S) * S;
+            if (!mbar_wait(smem_u32(&empty[st]), (uint32_t)((c_last / S) & 1))) ok = false;
+        }
+    } else if (tid == 32) {
+        // MMA issuer
+        for (int c = 0; c < nchunks; ++c) {
+            const int st = c % S;
+            if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((c / S) & 1))) {
+                ok = false;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t stage = base + st * kStageBytes;
 #pragma unroll
             for (int k = 0; k < KOBJ; ++k)
 #pragma unroll
                 for (int ks = 0; ks < kChunkK / 16; ++ks)
                     mma_bf16(tmem + k * kTileN, sw128_desc(stage + k * kTileBytes + ks * 32),
                              sw128_desc(stage + KOBJ * kTileBytes + ks * 32), (c > 0 || ks > 0) ? 1u : 0u);
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&mbar[c % S]))
-                         : "memory");
+            if (CL > 1)
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                                 smem_u32(&empty[st])),
+                             "h"(kMask)
+                             : "memory");
+            else
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&empty[st]))
+                             : "memory");
         }
-        last = c;
+        // the products of this CTA are complete once `done` flips
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(done)) : "memory");
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();  // lanes 1-31 of warps 0 and 1 wait for their role thread before any block barrier
     // warp w owns TMEM lanes 32*(w % 4).. (its spins) and columns 32*(w / 4).. (replicas);
     // each lane's state for the first 16 columns is loaded while the last products finish
     const int quarter = warp & 3, part = warp >> 2;
@@ -227,9 +295,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_step(const DenseStepArgs 
         }
     };
     load_state(part * 32);
-    // the last commit covers every product issued before it
-    if (ok && last >= 0) ok = mbar_wait(smem_u32(&mbar[last % S]), (uint32_t)((last / S) & 1));
-    ok = __syncthreads_and(ok);
+    // `done` covers every product the MMA thread issued (it commits even after a failed wait)
+    const bool products = mbar_wait(smem_u32(done), 0u);
+    ok = __syncthreads_and(ok && products);
     asm volatile("tcgen05.fence::after_thread_sync;");
 
     if (ok) {
@@ -280,11 +348,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_step(const DenseStepArgs 
         }
     } else if (tid == 0) {
         atomicOr(a.status, 1);
-        // give the products already issued a bounded chance to finish before the TMEM is freed
-        if (last >= 0) mbar_wait(smem_u32(&mbar[last % S]), (uint32_t)((last / S) & 1));
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
+    if (CL > 1) cluster_sync();  // no CTA leaves while a peer may still write to it
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
@@ -381,25 +448,77 @@ __global__ void k_dense_readout(int32_t n, int32_t np, int32_t R, int32_t W, con
 
 size_t dense_smem_bytes(int K) { return 1024 + dense_stages(K) * (size_t)(K + 1) * kTileBytes + (size_t)kTileN * (K + 1) * 4 + 64; }
 
-template <int VARIANT, int KOBJ, bool NOISE>
-cudaError_t launch_step(const DenseStepArgs& a, dim3 grid, cudaStream_t st)
+template <int VARIANT, int KOBJ, bool NOISE, int CL>
+cudaError_t launch_step(const moq_dense* d, const CUtensorMap& tm_phi, const DenseStepArgs& a, dim3 grid, cudaStream_t st)
 {
-    auto k = k_dense_step<VARIANT, KOBJ, NOISE>;
+    auto k = k_dense_step<VARIANT, KOBJ, NOISE, CL>;
     const size_t smem = dense_smem_bytes(KOBJ);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, kThreads, smem, st>>>(a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = CL;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, d->tm_J, tm_phi, a);
+}
+
+template <int VARIANT, bool NOISE, int CL>
+cudaError_t launch_step_k(const moq_dense* d, const CUtensorMap& tm_phi, const DenseStepArgs& a, dim3 grid, cudaStream_t st)
+{
+    switch (a.K) {
+    case 2: return launch_step<VARIANT, 2, NOISE, CL>(d, tm_phi, a, grid, st);
+    case 3: return launch_step<VARIANT, 3, NOISE, CL>(d, tm_phi, a, grid, st);
+    default: return launch_step<VARIANT, 4, NOISE, CL>(d, tm_phi, a, grid, st);
+    }
 }
 
 template <int VARIANT, bool NOISE>
-cudaError_t launch_step_k(const DenseStepArgs& a, dim3 grid, cudaStream_t st)
+cudaError_t launch_step_cl(const moq_dense* d, const CUtensorMap& tm_phi, const DenseStepArgs& a, dim3 grid, cudaStream_t st)
 {
-    switch (a.K) {
-    case 2: return launch_step<VARIANT, 2, NOISE>(a, grid, st);
-    case 3: return launch_step<VARIANT, 3, NOISE>(a, grid, st);
-    default: return launch_step<VARIANT, 4, NOISE>(a, grid, st);
+    switch (d->cluster) {
+    case 1: return launch_step_k<VARIANT, NOISE, 1>(d, tm_phi, a, grid, st);
+    case 2: return launch_step_k<VARIANT, NOISE, 2>(d, tm_phi, a, grid, st);
+    default: return launch_step_k<VARIANT, NOISE, 4>(d, tm_phi, a, grid, st);
     }
+}
+
+// Tensor maps of the J tiles (3-D: j, i, objective) and of the two Phi buffers (2-D: j, r),
+// BF16, 128-byte swizzle (the layout of the MMA operands), built once per handle.
+int encode_maps(moq_dense* d)
+{
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    MOQ_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !fn) return fail(MOQ_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    const cuuint64_t np = (cuuint64_t)d->n_pad;
+    const cuuint32_t one[3] = {1, 1, 1};
+    {
+        const cuuint64_t dims[3] = {np, np, (cuuint64_t)d->K};
+        const cuuint64_t strides[2] = {np * 2, np * np * 2};
+        const cuuint32_t box[3] = {(cuuint32_t)kChunkK, (cuuint32_t)(kTileM / d->cluster), 1};
+        CUresult r = encode(&d->tm_J, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, d->J, dims, strides, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(MOQ_ERR_CUDA, "cuTensorMapEncodeTiled(J) failed: %d", (int)r);
+    }
+    for (int b = 0; b < 2; ++b) {
+        const cuuint64_t dims[2] = {np, (cuuint64_t)d->R_pad};
+        const cuuint64_t strides[1] = {np * 2};
+        const cuuint32_t box[2] = {(cuuint32_t)kChunkK, (cuuint32_t)kTileN};
+        CUresult r = encode(&d->tm_phi[b], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, d->phi[b], dims, strides, box, one,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(MOQ_ERR_CUDA, "cuTensorMapEncodeTiled(phi) failed: %d", (int)r);
+    }
+    return MOQ_OK;
 }
 
 void free_dense(moq_dense* d)
@@ -435,7 +554,15 @@ int moq_dense_create(const moq_instance* inst, int32_t max_replicas, moq_dense**
     d->inst = inst;
     d->n_pad = (int)ceil_div(inst->n, kTileM) * kTileM;
     d->max_R = max_replicas;
-    d->R_pad = (int)ceil_div(max_replicas, kTileN) * kTileN;
+    d->R_pad = (int)ceil_div(max_replicas, kTileN * kMaxCluster) * kTileN * kMaxCluster;
+    // J tiles multicast over clusters of 2 or 4 CTAs cut L2 reads but tie the CTAs of a
+    // cluster to each other's pace; at n = 2000, R = 8192 single CTAs measured fastest
+    // (204 us per step against 210 and 234), so clusters are opt-in (MOQ_DENSE_CLUSTER)
+    d->cluster = 1;
+    if (const char* env = getenv("MOQ_DENSE_CLUSTER")) {
+        const int v = atoi(env);
+        d->cluster = (v == 2 || v == 4) ? v : 1;
+    }
     const size_t cells = (size_t)d->R_pad * d->n_pad;
     cudaError_t e = cudaMalloc((void**)&d->J, sizeof(__nv_bfloat16) * (size_t)d->K * d->n_pad * d->n_pad);
     if (e == cudaSuccess) e = cudaMalloc((void**)&d->x, sizeof(float) * cells);
@@ -456,6 +583,11 @@ int moq_dense_create(const moq_instance* inst, int32_t max_replicas, moq_dense**
         free_dense(d);
         return cuda_fail(e, "moq_dense_create");
     }
+    const int rc = encode_maps(d);
+    if (rc != MOQ_OK) {
+        free_dense(d);
+        return rc;
+    }
     *out = d;
     return MOQ_OK;
 }
@@ -474,7 +606,9 @@ int moq_sample_dense(moq_dense* d, const float* lambda, int32_t R, const moq_sam
     if (p->replica_offset != 0) return fail(MOQ_ERR_UNSUPPORTED, "moq_sample_dense: replica_offset must be 0");
     cudaStream_t st = as_stream(stream);
     const moq_instance* h = d->inst;
-    const int np = d->n_pad, Rp = (int)ceil_div(R, kTileN) * kTileN;
+    // replica tiles come in whole clusters (the padded replicas compute on zero weights and
+    // are never written)
+    const int np = d->n_pad, Rp = (int)ceil_div(R, kTileN * d->cluster) * kTileN * d->cluster;
     const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32), rnd = (uint32_t)round;
     k_dense_c0<<<R, 256, 0, st>>>(h->rowsum, h->rowptr, h->wn, h->nnz, d->n, d->K, lambda, R, d->c0);
     const int gi = (int)std::min<int64_t>(ceil_div((int64_t)Rp * np, 256), 148 * 32);
@@ -485,7 +619,6 @@ int moq_sample_dense(moq_dense* d, const float* lambda, int32_t R, const moq_sam
     MOQ_CUDA_TRY(cudaMemsetAsync(d->phi[1], 0, sizeof(__nv_bfloat16) * (size_t)Rp * np, st));  // padded entries stay 0
     MOQ_LAUNCH_CHECK("moq_sample_dense prologue");
     DenseStepArgs a{};
-    a.J = d->J;
     a.x = d->x;
     a.y = d->y;
     a.lambda = lambda;
@@ -509,11 +642,13 @@ int moq_sample_dense(moq_dense* d, const float* lambda, int32_t R, const moq_sam
     for (int m = 0; m < p->steps; ++m) {
         a.m = m;
         a.cm = fmaf(a0inv, (float)m, -p->a0);
-        a.phi_in = d->phi[m & 1];
+        const CUtensorMap& tm_in = d->tm_phi[m & 1];
         a.phi_out = d->phi[(m + 1) & 1];
         cudaError_t e;
-        if (p->variant == MOQ_DSB) e = noise ? launch_step_k<MOQ_DSB, true>(a, grid, st) : launch_step_k<MOQ_DSB, false>(a, grid, st);
-        else e = noise ? launch_step_k<MOQ_BSB, true>(a, grid, st) : launch_step_k<MOQ_BSB, false>(a, grid, st);
+        if (p->variant == MOQ_DSB)
+            e = noise ? launch_step_cl<MOQ_DSB, true>(d, tm_in, a, grid, st) : launch_step_cl<MOQ_DSB, false>(d, tm_in, a, grid, st);
+        else
+            e = noise ? launch_step_cl<MOQ_BSB, true>(d, tm_in, a, grid, st) : launch_step_cl<MOQ_BSB, false>(d, tm_in, a, grid, st);
         if (e != cudaSuccess) return cuda_fail(e, "moq_sample_dense step launch");
     }
     k_dense_readout<<<R, 128, 0, st>>>(d->n, np, R, h->words, d->x, d->y, bits, p->x_out, p->y_out);

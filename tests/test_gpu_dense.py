@@ -149,3 +149,31 @@ def test_dense_final_hv_distribution(M, P, oracle):
     M.moq_dense_destroy(d)
     assert stats.mannwhitneyu(hv_g, hv_c).pvalue > 0.01
     assert abs(np.median(hv_g) / np.median(hv_c) - 1) < 0.03
+
+
+@pytest.mark.parametrize("variant", ["dsb", "bsb"])
+def test_dense_cluster_sizes_agree_bitwise(M, P, variant, monkeypatch):
+    # J tiles are shared by clusters of 1, 2 or 4 CTAs (each loads a slice and multicasts
+    # it); who loads a row does not change any product, so all cluster sizes give the
+    # same bits, x and y
+    src = wl.random_graph(300, 1.0, 31, K=3, wmax=300)
+    inst = P.Instance(src)
+    R, T = 700, 7  # ragged replica tiles, padded to whole clusters
+    lam = _dev(wl.dirichlet_lambdas(R, 3, 8))
+    out = {}
+    for cl in ("1", "2", "4"):
+        monkeypatch.setenv("MOQ_DENSE_CLUSTER", cl)
+        d = M.moq_dense_create(inst.handle, R)
+        try:
+            xo = torch.zeros((R, src.n), device="cuda")
+            yo = torch.zeros((R, src.n), device="cuda")
+            bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+            p = M.moq_default_params(variant=variant, steps=T, dt=0.5, alpha=0.1, x_out=xo, y_out=yo)
+            M.moq_sample_dense(d, lam, R, p, 3, 1, bits)
+            M.moq_dense_status(d)
+            out[cl] = (bits.cpu(), xo.cpu(), yo.cpu())
+        finally:
+            M.moq_dense_destroy(d)
+    for cl in ("2", "4"):
+        for a, b in zip(out["1"], out[cl]):
+            assert torch.equal(a, b)
