@@ -431,7 +431,7 @@ def dense_arm(args, rank, world):
         evs[0].record(stream)
         M.moq_sample_dense(d, lam, R, params, 1 + rank, s, bits)
         evs[1].record(stream)
-        M.moq_evaluate_cuts(inst.handle, bits, R, cuts)
+        M.moq_dense_evaluate_cuts(d, bits, R, cuts)  # exact, on the tensor cores
         arch.merge(cuts, bits, R, 0)
         hv[0] = arch.hypervolume(inst.ref)
         evs[2].record(stream)
@@ -471,7 +471,9 @@ def dense_arm(args, rank, world):
                          if (n, R) == (2000, 8192) else None,
                          "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16, seconds-long loop)"},
             "sampling_only_value": units / samp_s * world, "sampler_ms": samp_s / args.steps * 1e3,
-            "clocks": clk.summary(), "front_points_last_step": front, "hv_last_step": int(hv[0])}
+            "clocks": clk.summary(), "front_points_last_step": front, "hv_last_step": int(hv[0]),
+            # c0, init, T steps, readout; cuts: signs, two products, finish; merge 7; HV 4
+            "gpu_launches": (T + 3 + 4 + 7 + 4) * args.steps}
 
 
 def main():

@@ -176,6 +176,17 @@ int moq_sample_dense(moq_dense* d, const float* lambda, int32_t R, const moq_sam
                      uint64_t* bits, void* stream);
 int moq_dense_status(moq_dense* d, void* stream);
 
+/* a6 for dense instances on the tensor cores, exact: C_k(s) (Eq. single_obj) of M packed
+ * configurations bits (device, M x W words, bit set for s_i = -1; M <= max_replicas) into
+ * cuts (device, M x K int64, row-major), the same values as moq_evaluate_cuts. Uses
+ * s^T J_k s = 2 sum_E J_e s_i s_j, so C_k = (2 W_k - s^T J_k s) / 4, with J_k split as
+ * 256 J_hi + J_lo (both exact in BF16) and products accumulated exactly in FP32 tiles then
+ * 64-bit integers. Reuses the handle's buffers: stream-ordered with moq_sample_dense on
+ * the same handle. Errors: MOQ_ERR_ARG (M out of range, NULL pointers),
+ * MOQ_ERR_UNSUPPORTED (some |J| > 65408: use moq_evaluate_cuts), MOQ_ERR_CUDA.
+ * Asynchronous; a device wait that ran out of its budget shows in moq_dense_status. */
+int moq_dense_evaluate_cuts(moq_dense* d, const uint64_t* bits, int32_t M, int64_t* cuts, void* stream);
+
 /* ---- a6: exact cut values, Eq. (single_obj) -------------------------------------
  * cuts[m*K + k] = C_k(s^(m)) = sum over edges with s_i != s_j of J^(k)_ij, for the M
  * packed configurations bits (device, M x W) into cuts (device, M x K int64).

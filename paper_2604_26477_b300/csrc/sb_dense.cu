@@ -45,7 +45,13 @@ struct moq_dense {
     float* y = nullptr;                          // R_pad x n_pad
     __nv_bfloat16* phi[2] = {nullptr, nullptr};  // R_pad x n_pad
     float* c0 = nullptr;                         // R_pad
+    __nv_bfloat16* J_hi = nullptr;               // J = 256 J_hi + J_lo, both exact in BF16 (|J| <= kSplitMax)
+    __nv_bfloat16* J_lo = nullptr;
+    unsigned long long* acc = nullptr;           // R_pad x K: s^T J_k s of the configurations being evaluated
+    int32_t* maxabs = nullptr;                   // max |J| (device), read back at create
+    int32_t max_abs_weight = 0;
     CUtensorMap tm_J;                            // K x n_pad x n_pad, box 64 x (128 / CL) x 1
+    CUtensorMap tm_Jhi, tm_Jlo;                  // the two halves, box 64 x 128 x 1
     CUtensorMap tm_phi[2];                       // R_pad x n_pad, box 64 x 128
     int32_t cluster = 1;                         // CTAs per cluster sharing J tiles
     int32_t* status = nullptr;                   // device error flags
@@ -62,6 +68,7 @@ constexpr int kThreads = 512;
 __host__ __device__ constexpr int dense_stages(int K) { return K <= 3 ? 3 : 2; }
 constexpr uint64_t kWaitNs = 2000000000ull;        // bound of every mbarrier wait (2 s)
 constexpr int kMaxCluster = 4;                     // replica tiles sharing one J tile
+constexpr int32_t kSplitMax = 65408;               // |J| bound of the exact two-part split (256 * 255 + 128)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -169,6 +176,79 @@ struct DenseStepArgs {
     int32_t* status;
 };
 
+// The products G_k = A_k B^T of one 128 x 128 tile for every objective k, accumulated in
+// TMEM columns k * 128..: thread 0 is the TMA producer (A_k tiles shared by the CL CTAs of
+// a cluster, each loading 128 / CL rows and multicasting them; the B tile its own), thread
+// 32 issues the MMAs and releases each stage to every CTA of the cluster; `done` flips once
+// all products of this CTA are complete. Returns false on a timed-out wait (roles only).
+template <int KOBJ, int CL>
+__device__ __forceinline__ bool dense_products(const CUtensorMap* tmA, const CUtensorMap* tmB, uint32_t base, uint64_t* full,
+                                               uint64_t* empty, uint64_t* done, uint32_t tmem, int i0, int r0, int nchunks,
+                                               uint32_t rank)
+{
+    constexpr int kStageBytes = (KOBJ + 1) * kTileBytes;
+    constexpr int S = dense_stages(KOBJ);
+    constexpr int kSliceRows = kTileM / CL;
+    constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
+    const int tid = threadIdx.x;
+    bool ok = true;
+    if (tid == 0) {
+        // producer: chunk c goes to stage c % S once every CTA of the cluster has released
+        // the stage's previous contents (chunk c - S)
+        for (int c = 0; c < nchunks && ok; ++c) {
+            const int st = c % S;
+            if (c >= S && !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((c - S) / S) & 1))) {
+                ok = false;
+                break;
+            }
+            const uint32_t stage = base + st * kStageBytes, fb = smem_u32(&full[st]);
+            mbar_expect_tx(fb, (uint32_t)kStageBytes);
+            const int j0 = c * kChunkK;
+#pragma unroll
+            for (int k = 0; k < KOBJ; ++k) {
+                const uint32_t dst = stage + k * kTileBytes + rank * (kSliceRows * kChunkK * 2);
+                if (CL > 1) tma_load_3d_mc(dst, tmA, j0, i0 + (int)rank * kSliceRows, k, fb, kMask);
+                else tma_load_3d(dst, tmA, j0, i0, k, fb);
+            }
+            tma_load_2d(stage + KOBJ * kTileBytes, tmB, j0, r0, fb);
+        }
+        // every peer's release of every stage has arrived before this CTA may leave
+        for (int st = 0; st < S && st < nchunks && ok; ++st) {
+            const int c_last = st + ((nchunks - 1 - st) / S) * S;
+            if (!mbar_wait(smem_u32(&empty[st]), (uint32_t)((c_last / S) & 1))) ok = false;
+        }
+    } else if (tid == 32) {
+        // MMA issuer
+        for (int c = 0; c < nchunks; ++c) {
+            const int st = c % S;
+            if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((c / S) & 1))) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t stage = base + st * kStageBytes;
+#pragma unroll
+            for (int k = 0; k < KOBJ; ++k)
+#pragma unroll
+                for (int ks = 0; ks < kChunkK / 16; ++ks)
+                    mma_bf16(tmem + k * kTileN, sw128_desc(stage + k * kTileBytes + ks * 32),
+                             sw128_desc(stage + KOBJ * kTileBytes + ks * 32), (c > 0 || ks > 0) ? 1u : 0u);
+            if (CL > 1)
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                                 smem_u32(&empty[st])),
+                             "h"(kMask)
+                             : "memory");
+            else
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&empty[st]))
+                             : "memory");
+        }
+        // the products of this CTA are complete once `done` flips
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(done)) : "memory");
+    }
+    __syncwarp();  // lanes 1-31 of warps 0 and 1 wait for their role thread before any block barrier
+    return ok;
+}
+
 template <int VARIANT, int KOBJ, bool NOISE, int CL>
 __global__ void __launch_bounds__(kThreads, 1)
     k_dense_step(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmPhi, const DenseStepArgs a)
@@ -182,8 +262,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     unsigned char* gbase = smem_raw + (base - raw);
     constexpr int kStageBytes = (KOBJ + 1) * kTileBytes;
     constexpr int S = dense_stages(KOBJ);
-    constexpr int kSliceRows = kTileM / CL;  // J rows each CTA of the cluster loads and multicasts
-    constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
     float* lam_s = reinterpret_cast<float*>(gbase + S * kStageBytes);  // kTileN x KOBJ
     float* c0_s = lam_s + kTileN * KOBJ;                                // kTileN
     uint64_t* full = reinterpret_cast<uint64_t*>(c0_s + kTileN);        // S (8-aligned: offsets are multiples of 8)
@@ -224,62 +302,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = *tmem_slot;
 
     // ---- main loop: products of all objectives over the spin chunks ----
-    const int nchunks = np / kChunkK;
-    bool ok = true;
-    if (tid == 0) {
-        // producer: chunk c goes to stage c % S once every CTA of the cluster has released
-        // the stage's previous contents (chunk c - S)
-        for (int c = 0; c < nchunks && ok; ++c) {
-            const int st = c % S;
-            if (c >= S && !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((c - S) / S) & 1))) {
-                ok = false;
-                break;
-            }
-            const uint32_t stage = base + st * kStageBytes, fb = smem_u32(&full[st]);
-            mbar_expect_tx(fb, (uint32_t)kStageBytes);
-            const int j0 = c * kChunkK;
-#pragma unroll
-            for (int k = 0; k < KOBJ; ++k) {
-                const uint32_t dst = stage + k * kTileBytes + rank * (kSliceRows * kChunkK * 2);
-                if (CL > 1) tma_load_3d_mc(dst, &tmJ, j0, i0 + (int)rank * kSliceRows, k, fb, kMask);
-                else tma_load_3d(dst, &tmJ, j0, i0, k, fb);
-            }
-            tma_load_2d(stage + KOBJ * kTileBytes, &tmPhi, j0, r0, fb);
-        }
-        // every peer's release of every stage has arrived before this CTA may leave
-        for (int st = 0; st < S && st < nchunks && ok; ++st) {
-            const int c_last = st + ((nchunks - 1 - st) / S) * S;
-            if (!mbar_wait(smem_u32(&empty[st]), (uint32_t)((c_last / S) & 1))) ok = false;
-        }
-    } else if (tid == 32) {
-        // MMA issuer
-        for (int c = 0; c < nchunks; ++c) {
-            const int st = c % S;
-            if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((c / S) & 1))) {
-                ok = false;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t stage = base + st * kStageBytes;
-#pragma unroll
-            for (int k = 0; k < KOBJ; ++k)
-#pragma unroll
-                for (int ks = 0; ks < kChunkK / 16; ++ks)
-                    mma_bf16(tmem + k * kTileN, sw128_desc(stage + k * kTileBytes + ks * 32),
-                             sw128_desc(stage + KOBJ * kTileBytes + ks * 32), (c > 0 || ks > 0) ? 1u : 0u);
-            if (CL > 1)
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                                 smem_u32(&empty[st])),
-                             "h"(kMask)
-                             : "memory");
-            else
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&empty[st]))
-                             : "memory");
-        }
-        // the products of this CTA are complete once `done` flips
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(done)) : "memory");
-    }
-    __syncwarp();  // lanes 1-31 of warps 0 and 1 wait for their role thread before any block barrier
+    bool ok = dense_products<KOBJ, CL>(&tmJ, &tmPhi, base, full, empty, done, tmem, i0, r0, np / kChunkK, rank);
     // warp w owns TMEM lanes 32*(w % 4).. (its spins) and columns 32*(w / 4).. (replicas);
     // each lane's state for the first 16 columns is loaded while the last products finish
     const int quarter = warp & 3, part = warp >> 2;
@@ -355,13 +378,130 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
+// ---- exact cut values on the tensor cores (Eq. single_obj) ----------------------------
+// For a configuration s (+-1 per spin) and a symmetric J_k with zero diagonal,
+// s^T J_k s = 2 sum_E J_e s_i s_j, so C_k(s) = 1/2 sum_E J_e (1 - s_i s_j) = (2 W_k - s^T J_k s) / 4.
+// With J_k = 256 J_hi + J_lo (both parts integers exactly representable in BF16) and S the
+// +-1 matrix of the configurations, the tiles G = J_part S^T are sums of at most n_pad
+// products of magnitude <= 256, so the FP32 accumulators hold them exactly (below 2^24).
+// The epilogue multiplies each row i of G by s_i (integer arithmetic), sums the 128 spins of
+// the tile and adds it, scaled by 256 for J_hi, into a 64-bit accumulator per (sample, k).
+
+// S[r][j] = +-1 (BF16) for r < M, j < n; 0 in the padding.
+__global__ void k_dense_signs(const uint64_t* __restrict__ bits, int32_t M, int32_t W, int32_t n, int32_t np, int32_t Rp,
+                              __nv_bfloat16* S)
+{
+    const int64_t total = (int64_t)Rp * np;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(q / np), j = (int)(q - (int64_t)r * np);
+        float v = 0.0f;
+        if (r < M && j < n) v = ((bits[(int64_t)r * W + (j >> 6)] >> (j & 63)) & 1ull) ? -1.0f : 1.0f;
+        S[q] = __float2bfloat16_rn(v);
+    }
+}
+
+template <int KOBJ>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_dense_cuts(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmS, const uint64_t* __restrict__ bits,
+                 int32_t M, int32_t W, int32_t n, int32_t np, int64_t scale, unsigned long long* acc, int32_t* status)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char* gbase = smem_raw + (base - raw);
+    constexpr int kStageBytes = (KOBJ + 1) * kTileBytes;
+    constexpr int S = dense_stages(KOBJ);
+    uint64_t* full = reinterpret_cast<uint64_t*>(gbase + S * kStageBytes + (size_t)kTileN * (KOBJ + 1) * 4);
+    uint64_t* empty = full + S;
+    uint64_t* done = empty + S;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int i0 = blockIdx.x * kTileM, r0 = blockIdx.y * kTileN;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)), "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int st = 0; st < S; ++st) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[st])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[st])), "r"(1));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(done)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tmem_slot;
+
+    bool ok = dense_products<KOBJ, 1>(&tmA, &tmS, base, full, empty, done, tmem, i0, r0, np / kChunkK, 0u);
+    const bool products = mbar_wait(smem_u32(done), 0u);
+    ok = __syncthreads_and(ok && products);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok) {
+        const int quarter = warp & 3, part = warp >> 2;
+        const int i = i0 + quarter * 32 + lane;
+#pragma unroll 1
+        for (int cc = 0; cc < 2; ++cc) {
+            const int col0 = part * 32 + cc * 16;
+            float g[KOBJ][16];
+#pragma unroll
+            for (int k = 0; k < KOBJ; ++k) tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + k * kTileN + col0, g[k]);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int r = r0 + col0 + q;
+                int sgn = 0;
+                if (i < n && r < M) sgn = ((bits[(int64_t)r * W + (i >> 6)] >> (i & 63)) & 1ull) ? -1 : 1;
+#pragma unroll
+                for (int k = 0; k < KOBJ; ++k) {
+                    const int v = __reduce_add_sync(0xffffffffu, sgn * __float2int_rn(g[k][q]));
+                    if (lane == 0 && r < M) atomicAdd(&acc[(int64_t)r * KOBJ + k], (unsigned long long)(scale * (int64_t)v));
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicOr(status, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+struct WeightSums {
+    int64_t w[4];
+};
+
+// C_k = (2 W_k - s^T J_k s) / 4, exact in 64-bit integers.
+__global__ void k_dense_cuts_finish(const unsigned long long* __restrict__ acc, int32_t M, int32_t K, WeightSums ws, int64_t* cuts)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= (int64_t)M * K) return;
+    const int k = (int)(q % K);
+    cuts[q] = (2 * ws.w[k] - (int64_t)acc[q]) / 4;
+}
+
 // J^(k) rows from the CSR, rounded to BF16, into the zero-padded dense matrices.
 __global__ void k_dense_fill(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, const int32_t* __restrict__ wn,
-                             int64_t nnz, int32_t n, int32_t K, int32_t np, __nv_bfloat16* J)
+                             int64_t nnz, int32_t n, int32_t K, int32_t np, __nv_bfloat16* J, __nv_bfloat16* J_hi,
+                             __nv_bfloat16* J_lo, int32_t* maxabs)
 {
+    int32_t mx = 0;
     for (int64_t i = blockIdx.x; i < n; i += gridDim.x)
         for (int32_t p = rowptr[i] + threadIdx.x; p < rowptr[i + 1]; p += blockDim.x)
-            for (int k = 0; k < K; ++k) J[((int64_t)k * np + i) * np + col[p]] = __float2bfloat16_rn((float)wn[(int64_t)k * nnz + p]);
+            for (int k = 0; k < K; ++k) {
+                const int32_t w = wn[(int64_t)k * nnz + p];
+                const int64_t at = ((int64_t)k * np + i) * np + col[p];
+                J[at] = __float2bfloat16_rn((float)w);
+                // J = 256 hi + lo with lo in [-128, 127]: both are integers of magnitude <= 256
+                // (exact in BF16) whenever |J| <= kSplitMax
+                const int32_t hi = (int32_t)(((int64_t)w + 128) >> 8);  // floor((w + 128) / 256)
+                J_hi[at] = __float2bfloat16_rn((float)hi);
+                J_lo[at] = __float2bfloat16_rn((float)(w - 256 * hi));
+                mx = max(mx, abs(w));
+            }
+    if (mx > 0) atomicMax(maxabs, mx);
 }
 
 // c0_r = 1 / max_i |sum_j J(c)_ij| (fallback 1 / max_i sum_j |J(c)_ij|, then 1); one block per replica.
@@ -509,6 +649,15 @@ int encode_maps(moq_dense* d)
                             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(MOQ_ERR_CUDA, "cuTensorMapEncodeTiled(J) failed: %d", (int)r);
     }
+    for (int h = 0; h < 2; ++h) {
+        const cuuint64_t dims[3] = {np, np, (cuuint64_t)d->K};
+        const cuuint64_t strides[2] = {np * 2, np * np * 2};
+        const cuuint32_t box[3] = {(cuuint32_t)kChunkK, (cuuint32_t)kTileM, 1};
+        CUresult r = encode(h ? &d->tm_Jlo : &d->tm_Jhi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, h ? d->J_lo : d->J_hi, dims, strides,
+                            box, one, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(MOQ_ERR_CUDA, "cuTensorMapEncodeTiled(J split) failed: %d", (int)r);
+    }
     for (int b = 0; b < 2; ++b) {
         const cuuint64_t dims[2] = {np, (cuuint64_t)d->R_pad};
         const cuuint64_t strides[1] = {np * 2};
@@ -525,6 +674,10 @@ void free_dense(moq_dense* d)
 {
     if (!d) return;
     cudaFree(d->J);
+    cudaFree(d->J_hi);
+    cudaFree(d->J_lo);
+    cudaFree(d->acc);
+    cudaFree(d->maxabs);
     cudaFree(d->x);
     cudaFree(d->y);
     cudaFree(d->phi[0]);
@@ -564,7 +717,12 @@ int moq_dense_create(const moq_instance* inst, int32_t max_replicas, moq_dense**
         d->cluster = (v == 2 || v == 4) ? v : 1;
     }
     const size_t cells = (size_t)d->R_pad * d->n_pad;
-    cudaError_t e = cudaMalloc((void**)&d->J, sizeof(__nv_bfloat16) * (size_t)d->K * d->n_pad * d->n_pad);
+    const size_t jbytes = sizeof(__nv_bfloat16) * (size_t)d->K * d->n_pad * d->n_pad;
+    cudaError_t e = cudaMalloc((void**)&d->J, jbytes);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d->J_hi, jbytes);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d->J_lo, jbytes);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d->acc, sizeof(unsigned long long) * (size_t)d->R_pad * d->K);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d->maxabs, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc((void**)&d->x, sizeof(float) * cells);
     if (e == cudaSuccess) e = cudaMalloc((void**)&d->y, sizeof(float) * cells);
     if (e == cudaSuccess) e = cudaMalloc((void**)&d->phi[0], sizeof(__nv_bfloat16) * cells);
@@ -572,13 +730,18 @@ int moq_dense_create(const moq_instance* inst, int32_t max_replicas, moq_dense**
     if (e == cudaSuccess) e = cudaMalloc((void**)&d->c0, sizeof(float) * d->R_pad);
     if (e == cudaSuccess) e = cudaMalloc((void**)&d->status, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&d->h_status, sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMemset(d->J, 0, sizeof(__nv_bfloat16) * (size_t)d->K * d->n_pad * d->n_pad);
+    if (e == cudaSuccess) e = cudaMemset(d->J, 0, jbytes);
+    if (e == cudaSuccess) e = cudaMemset(d->J_hi, 0, jbytes);
+    if (e == cudaSuccess) e = cudaMemset(d->J_lo, 0, jbytes);
+    if (e == cudaSuccess) e = cudaMemset(d->maxabs, 0, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(d->status, 0, sizeof(int32_t));
     if (e == cudaSuccess) {
-        k_dense_fill<<<std::min(d->n, 148 * 8), 128>>>(inst->rowptr, inst->col, inst->wn, inst->nnz, d->n, d->K, d->n_pad, d->J);
+        k_dense_fill<<<std::min(d->n, 148 * 8), 128>>>(inst->rowptr, inst->col, inst->wn, inst->nnz, d->n, d->K, d->n_pad, d->J,
+                                                       d->J_hi, d->J_lo, d->maxabs);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&d->max_abs_weight, d->maxabs, sizeof(int32_t), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) {
         free_dense(d);
         return cuda_fail(e, "moq_dense_create");
@@ -653,6 +816,57 @@ int moq_sample_dense(moq_dense* d, const float* lambda, int32_t R, const moq_sam
     }
     k_dense_readout<<<R, 128, 0, st>>>(d->n, np, R, h->words, d->x, d->y, bits, p->x_out, p->y_out);
     MOQ_LAUNCH_CHECK("moq_sample_dense readout");
+    return MOQ_OK;
+}
+
+int moq_dense_evaluate_cuts(moq_dense* d, const uint64_t* bits, int32_t M, int64_t* cuts, void* stream)
+{
+    using namespace moq;
+    if (!d) return fail(MOQ_ERR_ARG, "moq_dense_evaluate_cuts: NULL handle");
+    if (M < 0 || M > d->max_R) return fail(MOQ_ERR_ARG, "moq_dense_evaluate_cuts: M=%d outside [0, max_replicas=%d]", M, d->max_R);
+    if (M == 0) return MOQ_OK;
+    if (!bits || !cuts) return fail(MOQ_ERR_ARG, "moq_dense_evaluate_cuts: NULL bits or cuts");
+    if (d->max_abs_weight > kSplitMax)
+        return fail(MOQ_ERR_UNSUPPORTED, "moq_dense_evaluate_cuts: max |J| = %d exceeds the exact split bound %d (use moq_evaluate_cuts)",
+                    d->max_abs_weight, kSplitMax);
+    cudaStream_t st = as_stream(stream);
+    const moq_instance* h = d->inst;
+    const int np = d->n_pad, Rp = (int)ceil_div(M, kTileN) * kTileN, W = h->words;
+    MOQ_CUDA_TRY(cudaMemsetAsync(d->acc, 0, sizeof(unsigned long long) * (size_t)M * d->K, st));
+    const int gi = (int)std::min<int64_t>(ceil_div((int64_t)Rp * np, 256), 148 * 32);
+    k_dense_signs<<<gi, 256, 0, st>>>(bits, M, W, d->n, np, Rp, d->phi[0]);
+    MOQ_LAUNCH_CHECK("moq_dense_evaluate_cuts signs");
+    const dim3 grid(np / kTileM, Rp / kTileN);
+    const size_t smem = dense_smem_bytes(d->K);
+    // the high part floor((J + 128) / 256) is all zero when every |J| <= 127
+    for (int part = (d->max_abs_weight > 127 ? 0 : 1); part < 2; ++part) {
+        const CUtensorMap& tmA = part == 0 ? d->tm_Jhi : d->tm_Jlo;
+        const int64_t scale = part == 0 ? 256 : 1;
+        cudaError_t e = cudaSuccess;
+        switch (d->K) {
+        case 2:
+            e = cudaFuncSetAttribute(k_dense_cuts<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                k_dense_cuts<2><<<grid, kThreads, smem, st>>>(tmA, d->tm_phi[0], bits, M, W, d->n, np, scale, d->acc, d->status);
+            break;
+        case 3:
+            e = cudaFuncSetAttribute(k_dense_cuts<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                k_dense_cuts<3><<<grid, kThreads, smem, st>>>(tmA, d->tm_phi[0], bits, M, W, d->n, np, scale, d->acc, d->status);
+            break;
+        default:
+            e = cudaFuncSetAttribute(k_dense_cuts<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                k_dense_cuts<4><<<grid, kThreads, smem, st>>>(tmA, d->tm_phi[0], bits, M, W, d->n, np, scale, d->acc, d->status);
+            break;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "moq_dense_evaluate_cuts attribute");
+        MOQ_LAUNCH_CHECK("moq_dense_evaluate_cuts products");
+    }
+    WeightSums ws{};
+    for (int k = 0; k < d->K; ++k) ws.w[k] = h->info.weight_sum[k];
+    k_dense_cuts_finish<<<(unsigned)ceil_div((int64_t)M * d->K, 256), 256, 0, st>>>(d->acc, M, d->K, ws, cuts);
+    MOQ_LAUNCH_CHECK("moq_dense_evaluate_cuts finish");
     return MOQ_OK;
 }
 

@@ -90,6 +90,7 @@ _sigs = {
     "moq_dense_destroy": (None, [_vp]),
     "moq_sample_dense": (C.c_int, [_vp, _vp, _i32, C.POINTER(moq_sample_params), _u64, _u64, _vp, _vp]),
     "moq_dense_status": (C.c_int, [_vp, _vp]),
+    "moq_dense_evaluate_cuts": (C.c_int, [_vp, _vp, _i32, _vp, _vp]),
     "moq_mlp_create": (C.c_int, [_i32, _i32, _i32, _i32, _u64, C.POINTER(_vp)]),
     "moq_mlp_destroy": (None, [_vp]),
     "moq_mlp_param_count": (_i64, [_vp]),
@@ -334,6 +335,12 @@ def moq_sample_dense(h, lam, R, params, seed, round_, bits, stream=None):
 
 def moq_dense_status(h, stream=None):
     _check(_lib.moq_dense_status(h, _stream(stream)), "moq_sample_dense")
+
+
+def moq_dense_evaluate_cuts(h, bits, M, cuts, stream=None):
+    _, i64, u64 = _torch_types()
+    _check(_lib.moq_dense_evaluate_cuts(h, _dptr(bits, "bits", u64), M, _dptr(cuts, "cuts", i64), _stream(stream)),
+           "moq_dense_evaluate_cuts")
 
 
 def moq_mlp_create(d_in, d_out, max_batch, max_candidates, seed) -> C.c_void_p:

@@ -177,3 +177,44 @@ def test_dense_cluster_sizes_agree_bitwise(M, P, variant, monkeypatch):
     for cl in ("2", "4"):
         for a, b in zip(out["1"], out[cl]):
             assert torch.equal(a, b)
+
+
+
+@pytest.mark.parametrize("n,Mn,K,wmax", [(150, 300, 3, 50), (257, 129, 2, 60000), (128, 700, 4, 5000), (90, 1, 3, 128),
+                                         (100, 40, 3, 127)])
+def test_dense_cuts_bit_exact(M, P, oracle, n, Mn, K, wmax):
+    # exact cuts on the tensor cores (J = 256 J_hi + J_lo, +-1 operands, integer epilogue)
+    # against the oracle's literal sum and the CUDA-core edge walk; ragged n and M, weights
+    # up to the split bound, and weights small enough for the single-part path
+    src = wl.random_graph(n, 0.9, n + Mn, K=K, wmax=wmax)
+    inst = P.Instance(src)
+    d = M.moq_dense_create(inst.handle, max(Mn, 64))
+    try:
+        bits = wl.random_sign_bits(Mn, n, 5)
+        bits[0] = 0  # all s = +1: every cut is 0
+        bd = torch.from_numpy(bits.view(np.int64)).cuda()
+        cuts = torch.zeros((Mn, K), dtype=torch.int64, device="cuda")
+        M.moq_dense_evaluate_cuts(d, bd, Mn, cuts)
+        M.moq_dense_status(d)
+        got = cuts.cpu().numpy()
+        assert np.array_equal(got, oracle.cuts(src, bits))
+        ref = torch.zeros_like(cuts)
+        M.moq_evaluate_cuts(inst.handle, bd, Mn, ref)
+        assert torch.equal(cuts, ref)
+        assert np.all(got[0] == 0)
+    finally:
+        M.moq_dense_destroy(d)
+
+
+def test_dense_cuts_reject_large_weights(M, P):
+    src = wl.random_graph(40, 1.0, 3, K=2, wmax=10)
+    src.w[0, 0] = 70000
+    inst = P.Instance(src)
+    d = M.moq_dense_create(inst.handle, 16)
+    try:
+        cuts = torch.zeros((4, 2), dtype=torch.int64, device="cuda")
+        with pytest.raises(M.MoqError) as e:
+            M.moq_dense_evaluate_cuts(d, torch.zeros((4, 1), dtype=torch.int64, device="cuda"), 4, cuts)
+        assert e.value.code == M.MOQ_ERR_UNSUPPORTED
+    finally:
+        M.moq_dense_destroy(d)
