@@ -207,7 +207,7 @@ def gpu_arm(args, rank, world):
     lam_all = torch.from_numpy(np.stack([wl.dirichlet_lambdas(R * world, K, 10_000 + s)[first:first + R]
                                          for s in range(nsteps)])).to(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 126 MB L2
-    launches_per_step = 1 + 1 + 7 + 4  # sample, cuts, Pareto merge (7), hypervolume (4)
+    launches_per_step = 1 + 1 + 12 + 4  # sample, cuts, Pareto merge (12: dedup path), hypervolume (4)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
     fronts, hvs = [], []
@@ -472,8 +472,8 @@ def dense_arm(args, rank, world):
                          "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16, seconds-long loop)"},
             "sampling_only_value": units / samp_s * world, "sampler_ms": samp_s / args.steps * 1e3,
             "clocks": clk.summary(), "front_points_last_step": front, "hv_last_step": int(hv[0]),
-            # c0, init, T steps, readout; cuts: signs, two products, finish; merge 7; HV 4
-            "gpu_launches": (T + 3 + 4 + 7 + 4) * args.steps}
+            # c0, init, T steps, readout; cuts: signs, two products, finish; merge 12; HV 4
+            "gpu_launches": (T + 3 + 4 + 12 + 4) * args.steps}
 
 
 def main():

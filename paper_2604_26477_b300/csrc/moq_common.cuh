@@ -133,6 +133,13 @@ struct moq_archive {
     int32_t* flag_cand = nullptr;  // max_batch
     int64_t* blocksum = nullptr;   // scan partials
     unsigned long long* range = nullptr;  // 2 x kMaxK per-objective min / max keys of a merge
+    int32_t* table = nullptr;      // large batches: hash table of lowest indices (power of two slots)
+    uint32_t table_mask = 0;
+    int64_t* ccuts = nullptr;      // large batches: compacted survivors (max_batch x K)
+    int32_t* cidx = nullptr;       // their candidate indices
+    int32_t* cflag = nullptr;      // their "dominated" flags
+    int64_t* d_m = nullptr;        // number of survivors (device)
+    int64_t large_min = 0;         // batches from this size take the dedup / survivor path
     int64_t n_blocksum = 0;
     void* hv_ws = nullptr;         // hypervolume workspace sized for cap
     int64_t* h_pinned = nullptr;   // pinned host words for read-backs

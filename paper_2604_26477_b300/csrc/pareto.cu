@@ -23,6 +23,7 @@
 // subtract and one mask test compare four objectives at once. Same decisions, fewer
 // instructions.
 #include <algorithm>
+#include <stdlib.h>
 
 #include "moq_common.cuh"
 
@@ -34,6 +35,7 @@ constexpr int kScanBlock = 1024;
 constexpr unsigned kFull = 0xffffffffu;
 
 constexpr int kChunk = 1024;   // candidates compared by one block of the 2-D grid
+constexpr int64_t kLargeBatch = 1 << 13;  // batches from this size take the dedup / survivor path (MOQ_LARGE_BATCH)
 constexpr int kArchChunks = 8; // archive slices per candidate tile
 
 // Dominance of one candidate u (registers) by any vector of a shared-memory tile.
@@ -165,8 +167,11 @@ __device__ __forceinline__ bool tile_dominates_packed(const Packed<KT>* tile, in
 template <int KT>
 __global__ void __launch_bounds__(kTile) k_dominated_candidates(const int64_t* __restrict__ arch, const int64_t* __restrict__ d_count,
                                                                 const int64_t* __restrict__ cand, int64_t M, int32_t* dom_cand,
-                                                                const unsigned long long* __restrict__ range)
+                                                                const unsigned long long* __restrict__ range, int arch_chunks,
+                                                                const int64_t* __restrict__ d_m)
 {
+    if (d_m) M = min(M, *d_m);  // the compacted survivors of the large-batch path
+    if (blockIdx.x * (int64_t)kTile >= M) return;
     __shared__ int64_t tile[kTile][KT];
     Packed<KT>* ptile = reinterpret_cast<Packed<KT>*>(&tile[0][0]);  // NW <= KT words per row
     const int tid = threadIdx.x;
@@ -180,10 +185,10 @@ __global__ void __launch_bounds__(kTile) k_dominated_candidates(const int64_t* _
     const Packed<KT> up = pack<KT>(u, lo);
     bool dropped = !act || dom_cand[c];
     const bool was = dropped;
-    const bool vs_archive = blockIdx.y < kArchChunks;
-    const int64_t lo_i = vs_archive ? (int64_t)blockIdx.y * kTile : (int64_t)(blockIdx.y - kArchChunks) * kChunk;
+    const bool vs_archive = (int)blockIdx.y < arch_chunks;
+    const int64_t lo_i = vs_archive ? (int64_t)blockIdx.y * kTile : (int64_t)(blockIdx.y - arch_chunks) * kChunk;
     const int64_t hi_i = vs_archive ? *d_count : min(M, lo_i + kChunk);
-    const int64_t stride = vs_archive ? (int64_t)kArchChunks * kTile : kTile;
+    const int64_t stride = vs_archive ? (int64_t)arch_chunks * kTile : kTile;
     const int64_t* src = vs_archive ? arch : cand;
     for (int64_t base = lo_i; base < hi_i; base += stride) {
         if (__syncthreads_and(dropped)) break;
@@ -216,11 +221,13 @@ __global__ void __launch_bounds__(kTile) k_dominated_candidates(const int64_t* _
 // a member is dropped when a candidate dominates it strictly.
 template <int KT>
 __global__ void __launch_bounds__(kTile) k_dominated_archive(const int64_t* __restrict__ arch, const int64_t* __restrict__ d_count,
-                                                             const int64_t* __restrict__ cand, int64_t M, int32_t* dom_arch)
+                                                             const int64_t* __restrict__ cand, int64_t M, int32_t* dom_arch,
+                                                             const int64_t* __restrict__ d_m)
 {
     __shared__ int64_t tile[kTile][KT];
     const int tid = threadIdx.x;
     const int64_t F = *d_count;
+    if (d_m) M = min(M, *d_m);
     const int64_t lo = (int64_t)blockIdx.y * kChunk, hi = min(M, lo + kChunk);
     for (int64_t blk = blockIdx.x; blk * kTile < F; blk += gridDim.x) {
         const int64_t a = blk * kTile + tid;
@@ -256,6 +263,107 @@ __global__ void __launch_bounds__(kTile) k_dominated_archive(const int64_t* __re
         if (act && dropped && !was) dom_arch[a] = 1;
         __syncthreads();
     }
+}
+
+// ---- large batches: deduplication and survivors ----------------------------------
+// A batch of many samples holds few distinct cut vectors and, once the archive has grown,
+// few that the archive does not already cover. Before the all-pairs test, (1) an open-
+// addressing hash table keeps, for every distinct vector, its lowest candidate index
+// (later copies are flagged), (2) the candidates are tested against the archive alone,
+// and (3) the survivors are compacted, so the candidate-candidate test runs on distinct,
+// uncovered vectors only. Among distinct vectors dominance does not depend on order, so
+// the compaction may be unordered; flags go back to the original positions.
+constexpr int32_t kEmptySlot = -1;
+
+template <int KT>
+__device__ __forceinline__ uint64_t vec_hash(const int64_t* v)
+{
+    uint64_t h = 0x9E3779B97F4A7C15ull;
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+        uint64_t z = (uint64_t)v[k] + h + 0x9E3779B97F4A7C15ull * (k + 1);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        h = z ^ (z >> 31);
+    }
+    return h;
+}
+
+template <int KT>
+__device__ __forceinline__ bool vec_eq(const int64_t* a, const int64_t* b)
+{
+    bool eq = true;
+#pragma unroll
+    for (int k = 0; k < KT; ++k) eq &= a[k] == b[k];
+    return eq;
+}
+
+// Insert every candidate; a slot ends holding the lowest index of its vector. Probing is
+// linear and bounded by the table size (the table has at least twice the batch's slots).
+template <int KT>
+__global__ void k_dedup_insert(const int64_t* __restrict__ cand, int64_t M, int32_t* table, uint32_t mask)
+{
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= M) return;
+    const int64_t* v = cand + c * KT;
+    uint32_t slot = (uint32_t)vec_hash<KT>(v) & mask;
+    for (uint32_t probe = 0; probe <= mask; ++probe, slot = (slot + 1) & mask) {
+        int32_t cur = table[slot];
+        if (cur == kEmptySlot) {
+            cur = atomicCAS(&table[slot], kEmptySlot, (int32_t)c);
+            if (cur == kEmptySlot) return;
+        }
+        if (vec_eq<KT>(cand + (int64_t)cur * KT, v)) {
+            atomicMin(&table[slot], (int32_t)c);
+            return;
+        }
+    }
+}
+
+// Flag every candidate whose vector's slot holds a lower index.
+template <int KT>
+__global__ void k_dedup_mark(const int64_t* __restrict__ cand, int64_t M, const int32_t* __restrict__ table, uint32_t mask,
+                             int32_t* dom_cand)
+{
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= M) return;
+    const int64_t* v = cand + c * KT;
+    uint32_t slot = (uint32_t)vec_hash<KT>(v) & mask;
+    for (uint32_t probe = 0; probe <= mask; ++probe, slot = (slot + 1) & mask) {
+        const int32_t cur = table[slot];
+        if (cur == kEmptySlot) return;  // not reachable: every candidate was inserted
+        if (vec_eq<KT>(cand + (int64_t)cur * KT, v)) {
+            if (cur != (int32_t)c) dom_cand[c] = 1;
+            return;
+        }
+    }
+}
+
+// Survivors (unflagged candidates) into a compact buffer, in any order; *d_m counts them.
+template <int KT>
+__global__ void k_compact_survivors(const int64_t* __restrict__ cand, int64_t M, const int32_t* __restrict__ dom_cand,
+                                    int64_t* ccuts, int32_t* cidx, unsigned long long* d_m)
+{
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool keep = c < M && !dom_cand[c];
+    const unsigned ballot = __ballot_sync(kFull, keep);
+    if (!ballot) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(ballot) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(d_m, (unsigned long long)__popc(ballot));
+    base = __shfl_sync(kFull, base, leader);
+    if (!keep) return;
+    const int64_t pos = (int64_t)base + __popc(ballot & ((1u << lane) - 1u));
+#pragma unroll
+    for (int k = 0; k < KT; ++k) ccuts[pos * KT + k] = cand[c * KT + k];
+    cidx[pos] = (int32_t)c;
+}
+
+__global__ void k_survivor_flags_back(const int64_t* __restrict__ d_m, const int32_t* __restrict__ cflag,
+                                      const int32_t* __restrict__ cidx, int32_t* dom_cand)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < *d_m && cflag[q]) dom_cand[cidx[q]] = 1;
 }
 
 // Flag of virtual position b*1024+t: blocks [0, nbA) cover archive slots, blocks
@@ -436,11 +544,30 @@ cudaError_t launch_filters(moq_archive* a, const int64_t* cuts, int64_t M, cudaS
         if (e == cudaSuccess) e = cudaMemsetAsync(a->range + KT, 0, sizeof(unsigned long long) * KT, st);
         if (e != cudaSuccess) return e;
         k_value_range<KT><<<148, kTile, 0, st>>>(a->cuts[a->cur], a->d_count, cuts, M, a->range);
-        const unsigned nchunks = (unsigned)ceil_div(M, kChunk);
-        k_dominated_candidates<KT><<<dim3((unsigned)ceil_div(M, kTile), kArchChunks + nchunks), kTile, 0, st>>>(
-            a->cuts[a->cur], a->d_count, cuts, M, a->flag_cand, a->range);
+        const unsigned nchunks = (unsigned)ceil_div(M, kChunk), gtiles = (unsigned)ceil_div(M, kTile);
         const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(a->cap, kTile), 32));
-        k_dominated_archive<KT><<<dim3(gx, nchunks), kTile, 0, st>>>(a->cuts[a->cur], a->d_count, cuts, M, a->flag_arch);
+        if (M < a->large_min) {
+            k_dominated_candidates<KT><<<dim3(gtiles, kArchChunks + nchunks), kTile, 0, st>>>(
+                a->cuts[a->cur], a->d_count, cuts, M, a->flag_cand, a->range, kArchChunks, nullptr);
+            k_dominated_archive<KT><<<dim3(gx, nchunks), kTile, 0, st>>>(a->cuts[a->cur], a->d_count, cuts, M, a->flag_arch, nullptr);
+        } else {
+            const unsigned g256 = (unsigned)ceil_div(M, 256);
+            e = cudaMemsetAsync(a->table, 0xff, sizeof(int32_t) * ((size_t)a->table_mask + 1), st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(a->d_m, 0, sizeof(int64_t), st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(a->cflag, 0, sizeof(int32_t) * M, st);
+            if (e != cudaSuccess) return e;
+            k_dedup_insert<KT><<<g256, 256, 0, st>>>(cuts, M, a->table, a->table_mask);
+            k_dedup_mark<KT><<<g256, 256, 0, st>>>(cuts, M, a->table, a->table_mask, a->flag_cand);
+            k_dominated_candidates<KT><<<dim3(gtiles, kArchChunks), kTile, 0, st>>>(a->cuts[a->cur], a->d_count, cuts, M,
+                                                                                   a->flag_cand, a->range, kArchChunks, nullptr);
+            k_compact_survivors<KT><<<g256, 256, 0, st>>>(cuts, M, a->flag_cand, a->ccuts, a->cidx,
+                                                          reinterpret_cast<unsigned long long*>(a->d_m));
+            k_dominated_candidates<KT><<<dim3(gtiles, nchunks), kTile, 0, st>>>(a->cuts[a->cur], a->d_count, a->ccuts, M, a->cflag,
+                                                                               a->range, 0, a->d_m);
+            k_dominated_archive<KT><<<dim3(gx, nchunks), kTile, 0, st>>>(a->cuts[a->cur], a->d_count, a->ccuts, M, a->flag_arch,
+                                                                         a->d_m);
+            k_survivor_flags_back<<<g256, 256, 0, st>>>(a->d_m, a->cflag, a->cidx, a->flag_cand);
+        }
     }
     return cudaGetLastError();
 }
@@ -475,6 +602,11 @@ void free_archive(moq_archive* a)
     cudaFree(a->flag_cand);
     cudaFree(a->blocksum);
     cudaFree(a->range);
+    cudaFree(a->table);
+    cudaFree(a->ccuts);
+    cudaFree(a->cidx);
+    cudaFree(a->cflag);
+    cudaFree(a->d_m);
     cudaFree(a->hv_ws);
     if (a->h_pinned) cudaFreeHost(a->h_pinned);
     delete a;
@@ -513,6 +645,18 @@ int moq_archive_create(int32_t n, int32_t K, int64_t capacity, int64_t max_batch
     al((void**)&a->flag_cand, sizeof(int32_t) * max_batch);
     al((void**)&a->blocksum, sizeof(int64_t) * a->n_blocksum);
     al((void**)&a->range, sizeof(unsigned long long) * 2 * kMaxK);
+    a->large_min = kLargeBatch;
+    if (const char* env = getenv("MOQ_LARGE_BATCH")) a->large_min = std::max<int64_t>(1, atoll(env));
+    if (max_batch >= a->large_min) {
+        uint32_t slots = 1;
+        while (slots < 2 * (uint64_t)max_batch) slots <<= 1;
+        a->table_mask = slots - 1;
+        al((void**)&a->table, sizeof(int32_t) * (size_t)slots);
+        al((void**)&a->ccuts, sizeof(int64_t) * (size_t)max_batch * K);
+        al((void**)&a->cidx, sizeof(int32_t) * (size_t)max_batch);
+        al((void**)&a->cflag, sizeof(int32_t) * (size_t)max_batch);
+        al((void**)&a->d_m, sizeof(int64_t));
+    }
     al(&a->hv_ws, (size_t)moq_hypervolume_workspace_size(capacity, K));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&a->h_pinned, 64);
     if (e == cudaSuccess) e = cudaMemset(a->d_count, 0, sizeof(int64_t));

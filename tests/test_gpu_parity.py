@@ -151,7 +151,9 @@ def _run_archive(M, P, oracle, cuts, bits, n, batches, capacity=1 << 14):
     return arch
 
 
-@pytest.mark.parametrize("K,span,Mtot", [(2, 40, 3000), (3, 12, 5000), (4, 6, 4000), (8, 3, 2000), (3, 1000, 20000)])
+@pytest.mark.parametrize("K,span,Mtot", [(2, 40, 3000), (3, 12, 5000), (4, 6, 4000), (8, 3, 2000), (3, 1000, 20000),
+                                         # batches of 2^13 and more take the dedup / survivor path
+                                         (2, 40, 90000), (4, 6, 150000), (3, 1000, 120000), (6, 4, 70000)])
 def test_pareto_archive_bit_exact(M, P, oracle, K, span, Mtot):
     rng = np.random.default_rng(K * 7 + span)
     cuts = rng.integers(-span, span, size=(Mtot, K)).astype(np.int64)
@@ -161,6 +163,21 @@ def test_pareto_archive_bit_exact(M, P, oracle, K, span, Mtot):
     edges = sorted({0, Mtot} | set(rng.integers(1, Mtot, size=5).tolist()))
     batches = [list(range(a, b)) for a, b in zip(edges[:-1], edges[1:])]
     _run_archive(M, P, oracle, cuts, bits, n, batches)
+
+
+@pytest.mark.parametrize("K,Mtot,span,noise", [(3, 100000, 100, 6), (4, 80000, 30, 3)])
+def test_pareto_large_batches_with_large_fronts(M, P, oracle, K, Mtot, span, noise):
+    # candidates near a simplex surface (fronts of thousands of points) with many exact
+    # duplicates, merged in batches above and below 2^13: the dedup / survivor path and the
+    # plain path must both keep the definition's front and the lowest index per vector
+    rng = np.random.default_rng(K)
+    cuts = rng.integers(0, span, size=(Mtot, K)).astype(np.int64)
+    cuts[:, -1] = span * (K - 1) - cuts[:, :-1].sum(axis=1) + rng.integers(0, noise, Mtot)
+    cuts[::11] = cuts[3]
+    bits = wl.random_sign_bits(Mtot, 42, K + 1)
+    cut_at = [0, 40000, 45000, Mtot]  # 40000 (dedup path), 5000 (plain path), the rest (dedup)
+    batches = [list(range(a, b)) for a, b in zip(cut_at[:-1], cut_at[1:])]
+    _run_archive(M, P, oracle, cuts, bits, 42, batches, capacity=1 << 15)
 
 
 @pytest.mark.parametrize("K,offset,width", [
