@@ -476,6 +476,93 @@ def dense_arm(args, rank, world):
             "gpu_launches": (T + 3 + 4 + 12 + 4) * args.steps}
 
 
+def paper_arm(args, rank, world):
+    """The paper's sampling protocol ("Sampling time advantage", "Sample quality and end-to-end
+    solution time", Appendix C) on the synthetic heavy-hex-like instances: every interior
+    Das-Dennis weight vector (190 for K = 3, 220 for K = 4) with a batch of 3000 NI-dSB
+    replicas, T = 50, dt = 1, alpha = 0.15 (K = 3) / 0.1 (K = 4), repeated with fresh noise
+    until the hypervolume stops growing; the same protocol without noise (alpha = 0); a
+    random-sampling sanity baseline with the same sample budget (uniform configurations:
+    the sampler's start state read out after zero steps); and an alpha sweep at a fixed
+    budget. The clock covers instance build, sampling, cuts, Pareto merge and one HV check
+    per round (end to end)."""
+    import torch
+
+    from paper_2604_26477_b300 import moqaia as M
+    from paper_2604_26477_b300 import pipeline as P
+    from paper_2604_26477_b300 import workloads as wl
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    batch, T, dt, rounds = 3000, 50, 1.0, args.paper_rounds
+    out = {"protocol": "interior Das-Dennis weights x 3000 replicas, NI-dSB T=50 dt=1, rounds with fresh noise",
+           "instances": {}}
+    total_units, total_s = 0.0, 0.0
+    for K, H, alpha_paper in ((3, 21, 0.15), (4, 13, 0.1)):
+        src = wl.heavy_hex_like(1000 + K, K=K, wmax=10)
+        cap = 1 << 20
+        lam_dd = torch.zeros((cap, K), dtype=torch.float32, device=dev)
+        nw = M.moq_lambda_das_dennis(K, H, 1, lam_dd, cap)
+        lam = lam_dd[:nw].repeat_interleave(batch, dim=0).contiguous()  # weight vector w for replicas w*3000..
+        R = lam.shape[0]
+
+        def run(alpha, n_rounds, steps=T, seed=7):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            inst = P.Instance(src)
+            arch = P.Archive(src.n, K, capacity=1 << 18, max_batch=R)
+            buf = P.RoundBuffers(R, src.n, K)
+            params = M.moq_default_params(variant="dsb", steps=steps, dt=dt, alpha=alpha)
+            trace = []
+            for rnd in range(n_rounds):
+                P.sample_round(inst, arch, buf, params, seed, rnd, lam=lam)
+                trace.append((time.perf_counter() - t0, (rnd + 1) * R, arch.hypervolume(inst.ref)))
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+            front = arch.size()
+            ref = inst.ref
+            arch.close()
+            inst.close()
+            return trace, front, secs, ref
+
+        res = {"weight_vectors": nw, "replicas_per_round": R}
+        tr_noise, front_noise, secs_noise, ref = run(alpha_paper, rounds)
+        tr_plain, front_plain, _, _ = run(0.0, rounds)
+        tr_rand, front_rand, _, _ = run(0.0, rounds, steps=0)  # uniform random configurations
+        total_units += float(R) * src.n * T * rounds
+        total_s += secs_noise
+        hv_best = max(tr_noise[-1][2], tr_plain[-1][2], tr_rand[-1][2])
+
+        def reach(trace, frac_num, frac_den):
+            target = (hv_best * frac_num + frac_den - 1) // frac_den
+            for t, smp, hv in trace:
+                if hv >= target:
+                    return {"seconds": round(t, 5), "samples": smp}
+            return None
+
+        for label, tr, fr in (("ni_dsb_alpha%.2f" % alpha_paper, tr_noise, front_noise), ("dsb_alpha0", tr_plain, front_plain),
+                              ("random_sampling", tr_rand, front_rand)):
+            res[label] = {"hv_final": int(tr[-1][2]), "hv_ratio": tr[-1][2] / hv_best, "front_points": int(fr),
+                          "samples_per_front_point": tr[-1][1] / max(fr, 1),
+                          "to_best_hv": reach(tr, 1, 1), "to_99.9pct": reach(tr, 999, 1000),
+                          "hv_gap_after_round": [int(hv_best - hv + 1) for _, _, hv in tr[: min(len(tr), 8)]]}
+        # noise amplitude sweep at a fixed budget of 3 rounds (Appendix C)
+        sweep = {}
+        for a in (0.0, 0.05, 0.1, 0.15, 0.2, 0.3):
+            tr, fr, _, _ = run(a, 3)
+            sweep["%.2f" % a] = {"hv_ratio": tr[-1][2] / hv_best, "front_points": int(fr)}
+        res["alpha_sweep_3_rounds"] = sweep
+        res["reference_point"] = [int(v) for v in ref]
+        out["instances"]["heavy_hex_like_n42_K%d" % K] = res
+    return {"metric": METRIC, "value": total_units / total_s, "unit": METRIC, "n_gpus": world, "steps": rounds,
+            "warmup": 0, "ms_per_step": total_s / (2 * rounds) * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "paper protocol: heavy-hex-like n=42, K=3 (190 weights) and K=4 (220 weights) x "
+                                   "3000 replicas, NI-dSB T=50 dt=1; value = spin updates of the noisy runs over "
+                                   "their end-to-end time", "rounds": rounds},
+            "paper_mode": out}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -488,8 +575,9 @@ def main():
     ap.add_argument("--ttt-rounds", type=int, default=64)
     ap.add_argument("--no-ttt", action="store_true")
     ap.add_argument("--cpu-baseline-worker", action="store_true")
-    ap.add_argument("--workload", default="precision", choices=["precision", "batching", "dense"],
-                    help="precision (the default line), or the batching or dense configuration")
+    ap.add_argument("--workload", default="precision", choices=["precision", "batching", "dense", "paper"],
+                    help="precision (the default line), the batching or dense configuration, or the paper's protocol")
+    ap.add_argument("--paper-rounds", type=int, default=20)
     ap.add_argument("--dense-n", type=int, default=2000)
     ap.add_argument("--dense-replicas", type=int, default=8192)
     ap.add_argument("--dense-steps", type=int, default=3000)
@@ -533,8 +621,9 @@ def main():
     if world > 1:
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         torch.distributed.init_process_group("nccl")
-    if args.workload in ("batching", "dense"):
-        line = (batching_arm if args.workload == "batching" else dense_arm)(args, rank, world)
+    if args.workload in ("batching", "dense", "paper"):
+        arm = {"batching": batching_arm, "dense": dense_arm, "paper": paper_arm}[args.workload]
+        line = arm(args, rank, world)
         if rank == 0:
             print(json.dumps(line), flush=True)
         if world > 1:

@@ -232,81 +232,6 @@ __global__ void __launch_bounds__(kSlab3Threads) k_hv3(const int64_t* __restrict
     if (threadIdx.x == 0) ws.partial[blockIdx.x] = s;
 }
 
-// K = 4: block t = slab along y_3 (order_3); thread s = sub-slab along y_2 (order_2)
-// among points of rank_3 <= t; area = staircase over order_0 restricted to
-// rank_3 <= t and rank_2 <= s.
-__global__ void __launch_bounds__(kThreads) k_hv4(const int64_t* __restrict__ pts, int64_t F, Ref4 ref, HvWs ws)
-{
-    __shared__ int64_t s_u0[kChunk], s_u1[kChunk];
-    __shared__ int32_t s_r2[kChunk], s_r3[kChunk];
-    __shared__ i128 red[kThreads];
-    const int Fv = *ws.fv;
-    const int64_t t = blockIdx.x;
-    const int32_t* ord0 = ws.order;
-    const int32_t* ord2 = ws.order + 2 * F;
-    const int32_t* ord3 = ws.order + 3 * F;
-    const int32_t* rank2 = ws.rank + 2 * F;
-    const int32_t* rank3 = ws.rank + 3 * F;
-    int64_t h4 = 0;
-    if (t < Fv) {
-        const int64_t top = pts[(int64_t)ord3[t] * 4 + 3];
-        const int64_t below = (t + 1 < Fv) ? pts[(int64_t)ord3[t + 1] * 4 + 3] : ref.r[3];
-        h4 = top - below;
-    }
-    if (h4 <= 0) {  // uniform over the block
-        if (threadIdx.x == 0) ws.partial[blockIdx.x] = 0;
-        return;
-    }
-    i128 acc = 0;
-    for (int64_t sbase = 0; sbase < Fv; sbase += kThreads) {
-        const int64_t s = sbase + threadIdx.x;
-        int64_t h3 = 0;
-        int32_t srank = -1;
-        if (s < Fv) {
-            const int32_t ps = ord2[s];
-            if (rank3[ps] <= t) {
-                int64_t below = ref.r[2];
-                for (int64_t s2 = s + 1; s2 < Fv; ++s2) {
-                    const int32_t q = ord2[s2];
-                    if (rank3[q] <= t) {
-                        below = pts[(int64_t)q * 4 + 2];
-                        break;
-                    }
-                }
-                h3 = pts[(int64_t)ps * 4 + 2] - below;
-                srank = (int32_t)s;
-            }
-        }
-        const bool any = __syncthreads_or(h3 > 0);
-        if (!any) continue;
-        i128 area = 0;
-        int64_t best1 = ref.r[1];
-        for (int64_t base = 0; base < Fv; base += kChunk) {
-            const int cnt = (int)min((int64_t)kChunk, Fv - base);
-            __syncthreads();
-            for (int q = threadIdx.x; q < cnt; q += kThreads) {
-                const int64_t p = ord0[base + q];
-                s_u0[q] = pts[p * 4];
-                s_u1[q] = pts[p * 4 + 1];
-                s_r2[q] = rank2[p];
-                s_r3[q] = rank3[p];
-            }
-            __syncthreads();
-            if (h3 > 0) {
-                for (int q = 0; q < cnt; ++q) {
-                    if (s_r3[q] <= t && s_r2[q] <= srank && s_u1[q] > best1) {
-                        area += (i128)(s_u0[q] - ref.r[0]) * (i128)(s_u1[q] - best1);
-                        best1 = s_u1[q];
-                    }
-                }
-            }
-        }
-        if (h3 > 0) acc += (i128)h3 * area;
-    }
-    const i128 s = block_sum(acc, red);
-    if (threadIdx.x == 0) ws.partial[blockIdx.x] = (i128)h4 * s;
-}
-
 __device__ __forceinline__ int block_excl_scan_int(int v, int* warp_sums, int* total)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -432,6 +357,167 @@ __global__ void __launch_bounds__(kThreads) k_hv4_compact(const int64_t* __restr
     if (threadIdx.x == 0) ws.partial[t] = (i128)h4 * sum;
 }
 
+// K = 4 for fronts beyond the shared-memory form: block b takes slab t = F-1-b and streams
+// the points twice, in chunks of kChunk, keeping only those of rank_3 <= t:
+//  - in y_2 order, to find the non-empty sub-slabs (the last point of every run of equal
+//    y_2 values; its successor may sit in the next chunk, so the last kept point of a chunk
+//    is carried over), which are collected in batches of up to kSubBatch;
+//  - for every batch, in y_0 order, where each thread walks the staircases of its
+//    kSubPerThread sub-slabs together over the shared chunk.
+constexpr int kSubPerThread = 8;
+constexpr int kSubBatch = kThreads * kSubPerThread;
+
+__global__ void __launch_bounds__(kThreads) k_hv4_stream(const int64_t* __restrict__ pts, int64_t F, Ref4 ref, HvWs ws)
+{
+    __shared__ int64_t s_sub_h[kSubBatch];
+    __shared__ int32_t s_sub_r[kSubBatch];
+    __shared__ int64_t s_a[kChunk + 1], s_b[kChunk];  // y_2 (+ carry) / y_0, and y_1
+    __shared__ int32_t s_r[kChunk + 1];                // rank_2
+    __shared__ i128 red[kThreads];
+    __shared__ int warp_sums[kThreads / 32];
+    const int Fv = *ws.fv;
+    const int64_t t = F - 1 - (int64_t)blockIdx.x;
+    const int32_t* ord0 = ws.order;
+    const int32_t* ord2 = ws.order + 2 * F;
+    const int32_t* ord3 = ws.order + 3 * F;
+    const int32_t* rank2 = ws.rank + 2 * F;
+    const int32_t* rank3 = ws.rank + 3 * F;
+    int64_t h4 = 0;
+    if (t < Fv) {
+        const int64_t top = pts[(int64_t)ord3[t] * 4 + 3];
+        const int64_t below = (t + 1 < Fv) ? pts[(int64_t)ord3[t + 1] * 4 + 3] : ref.r[3];
+        h4 = top - below;
+    }
+    if (h4 <= 0) {  // uniform over the block
+        if (threadIdx.x == 0) ws.partial[t] = 0;
+        return;
+    }
+    i128 acc = 0;
+    int nsub = 0;  // sub-slabs collected in the current batch
+
+    // walk all kept points in y_0 order for the batch of nsub sub-slabs
+    auto walk_batch = [&]() {
+        int64_t h3[kSubPerThread], best1[kSubPerThread];
+        int32_t rs[kSubPerThread];
+        i128 area[kSubPerThread];
+#pragma unroll
+        for (int q = 0; q < kSubPerThread; ++q) {
+            const int j = threadIdx.x + q * kThreads;
+            h3[q] = j < nsub ? s_sub_h[j] : 0;
+            rs[q] = j < nsub ? s_sub_r[j] : -1;
+            best1[q] = ref.r[1];
+            area[q] = 0;
+        }
+        for (int base = 0; base < Fv; base += kChunk) {
+            __syncthreads();  // the previous chunk is consumed
+            int cnt = 0;
+            for (int sub = 0; sub < kChunk; sub += kThreads) {
+                const int q = base + sub + threadIdx.x;
+                const int p = q < Fv ? ord0[q] : 0;
+                const int f = (q < Fv && rank3[p] <= t) ? 1 : 0;
+                int tot;
+                const int pos = cnt + block_excl_scan_int(f, warp_sums, &tot);
+                if (f) {
+                    s_a[pos] = pts[(int64_t)p * 4];
+                    s_b[pos] = pts[(int64_t)p * 4 + 1];
+                    s_r[pos] = rank2[p];
+                }
+                cnt += tot;
+            }
+            __syncthreads();
+            for (int q = 0; q < cnt; ++q) {
+                const int64_t u0 = s_a[q], u1 = s_b[q];
+                const int32_t r2 = s_r[q];
+#pragma unroll
+                for (int k = 0; k < kSubPerThread; ++k) {
+                    if (r2 <= rs[k] && u1 > best1[k]) {
+                        area[k] += (i128)(u0 - ref.r[0]) * (i128)(u1 - best1[k]);
+                        best1[k] = u1;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kSubPerThread; ++k) acc += (i128)h3[k] * area[k];
+        __syncthreads();  // the batch list is consumed
+        nsub = 0;
+    };
+
+    // y_2 order: a kept point closes a non-empty sub-slab when the next kept point has a
+    // smaller y_2 (or it is the last one: the sub-slab reaches r_2)
+    int carry = 0;  // s_a[0] / s_r[0] hold the carried point when 1
+    for (int base = 0; base < Fv; base += kChunk) {
+        int cnt = carry;
+        for (int sub = 0; sub < kChunk; sub += kThreads) {
+            const int q = base + sub + threadIdx.x;
+            const int p = q < Fv ? ord2[q] : 0;
+            const int f = (q < Fv && rank3[p] <= t) ? 1 : 0;
+            int tot;
+            const int pos = cnt + block_excl_scan_int(f, warp_sums, &tot);
+            if (f) {
+                s_a[pos] = pts[(int64_t)p * 4 + 2];
+                s_r[pos] = rank2[p];
+            }
+            cnt += tot;
+        }
+        __syncthreads();
+        const bool last_chunk = base + kChunk >= Fv;
+        const int closed = last_chunk ? cnt : cnt - 1;  // points whose successor is known
+        for (int sub = 0; sub < closed; sub += kThreads) {
+            const int q = sub + threadIdx.x;
+            int64_t h3 = 0;
+            int32_t rq = 0;
+            if (q < closed) {
+                h3 = s_a[q] - (q + 1 < cnt ? s_a[q + 1] : ref.r[2]);
+                rq = s_r[q];
+            }
+            int tot;
+            const int pos = nsub + block_excl_scan_int(h3 > 0 ? 1 : 0, warp_sums, &tot);
+            if (h3 > 0) {
+                s_sub_h[pos] = h3;
+                s_sub_r[pos] = rq;
+            }
+            nsub += tot;
+        }
+        __syncthreads();
+        if (!last_chunk && cnt > 0) {  // carry the last kept point to the front
+            int64_t ca = 0;
+            int32_t cr = 0;
+            if (threadIdx.x == 0) {
+                ca = s_a[cnt - 1];
+                cr = s_r[cnt - 1];
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                s_a[0] = ca;
+                s_r[0] = cr;
+            }
+            carry = 1;
+        } else {
+            carry = 0;
+        }
+        // a full chunk adds at most kChunk sub-slabs: walk once the batch could overflow
+        if (nsub > kSubBatch - kChunk || (last_chunk && nsub > 0)) {
+            // the carried y_2 point is restored after the walk reuses the chunk buffers
+            int64_t ca = 0;
+            int32_t cr = 0;
+            if (carry) {
+                ca = s_a[0];
+                cr = s_r[0];
+            }
+            __syncthreads();
+            walk_batch();
+            if (carry && threadIdx.x == 0) {
+                s_a[0] = ca;
+                s_r[0] = cr;
+            }
+        }
+        __syncthreads();
+    }
+    const i128 sum = block_sum(acc, red);
+    if (threadIdx.x == 0) ws.partial[t] = (i128)h4 * sum;
+}
+
 // Sum of the block partials; flags bit 0 = the side-length product reaches 2^125.
 __global__ void __launch_bounds__(kThreads) k_hv_final(const int64_t* __restrict__ pts, int64_t F, int K, Ref4 ref,
                                                        int64_t nparts, HvWs ws)
@@ -509,7 +595,7 @@ int moq_hypervolume_points(const int64_t* pts, int64_t F, int32_t K, const int64
             MOQ_CUDA_TRY(cudaFuncSetAttribute(k_hv4_compact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             k_hv4_compact<<<(unsigned)F, kThreads, smem, st>>>(pts, F, r, ws);
         } else {
-            k_hv4<<<(unsigned)F, kThreads, 0, st>>>(pts, F, r, ws);
+            k_hv4_stream<<<(unsigned)F, kThreads, 0, st>>>(pts, F, r, ws);
         }
         nparts = F;
         break;

@@ -263,6 +263,21 @@ def test_hv_large_mostly_dominated(M, oracle, K, F):
     assert _hv_points(M, pts, ref) == oracle.hypervolume(pts[keep], ref)
 
 
+@pytest.mark.parametrize("span,F,noise", [(25, 30000, 3), (40, 30000, 2)])
+def test_hv4_large_fronts_streamed(M, oracle, span, F, noise):
+    # K = 4 fronts of about 8000 and 19000 points (beyond the shared-memory form: the slabs
+    # are streamed in chunks, sub-slabs walked in batches), with ties in every objective
+    rng = np.random.default_rng(span)
+    pts = rng.integers(0, span, size=(F, 4)).astype(np.int64)
+    pts[:, -1] = span * 3 - pts[:, :-1].sum(axis=1) + rng.integers(0, noise, F)
+    ref = np.zeros(4, np.int64)
+    front = pts[oracle.pareto_filter(pts)]
+    assert len(front) > 6144
+    want = oracle.hypervolume(front, ref)
+    assert _hv_points(M, front, ref) == want
+    assert _hv_points(M, pts, ref) == want  # dominated points add nothing
+
+
 def test_hv_edge_cases(M, oracle):
     ref = np.zeros(3, np.int64)
     assert _hv_points(M, np.zeros((0, 3), np.int64), ref) == 0
