@@ -563,6 +563,123 @@ def paper_arm(args, rank, world):
             "paper_mode": out}
 
 
+def appendix_e_arm(args, rank, world):
+    """The protocol of "Comparison to evolutionary algorithm-based heuristics" for NI-SB alone
+    (the comparison algorithms are out of scope) on Appendix E's correlated three-objective
+    instances (n = 25, 100, 200; densities 0.5 and 1): 190 interior Das-Dennis weight vectors x
+    3000 replicas per round (570,000 candidates), alpha = 0.1, dt = 1, T = 50 (n = 25) or 1000,
+    rounds of sampling, cuts and Pareto merge repeated until a runtime limit (5 s for n = 25,
+    else 10 s; scaled by --time-scale); NI-bSB, NI-dSB and a random-sampling baseline. The
+    reference front is the exhaustive front for n = 25 (all 2^24 configurations with s_0 = +1,
+    evaluated and filtered by the same kernels) and the composite front of the three arms
+    otherwise; the reference point is the per-objective minimum over every evaluated sample.
+    Graphs with a vertex of degree > 16 run on the dense tensor-core sampler."""
+    import torch
+
+    from paper_2604_26477_b300 import moqaia as M
+    from paper_2604_26477_b300 import pipeline as P
+    from paper_2604_26477_b300 import workloads as wl
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    K, batch = 3, 3000
+    lam_dd = torch.zeros((4096, K), dtype=torch.float32, device=dev)
+    nw = M.moq_lambda_das_dennis(K, 21, 1, lam_dd, 4096)
+    lam = lam_dd[:nw].repeat_interleave(batch, dim=0).contiguous()
+    # the instances carry J2 = A - 25 B (integers, 5x the paper's 0.2 A - 5 B); the weight on
+    # objective 2 is divided by 5 so that J(c) is the paper's scalarisation
+    lam[:, 1] *= 0.2
+    R = lam.shape[0]
+    results, units, busy = {}, 0.0, 0.0
+    for n, d in ((25, 0.5), (25, 1.0), (100, 0.5), (100, 1.0), (200, 0.5), (200, 1.0)):
+        src = wl.app_e_correlated(n, d, 500 + n + int(10 * d))
+        inst = P.Instance(src)
+        T = 50 if n <= 42 else 1000
+        limit = (5.0 if n <= 42 else 10.0) * args.time_scale
+        dense = inst.info["max_degree"] > 16
+        dh = M.moq_dense_create(inst.handle, R) if dense else None
+        bits = torch.zeros((R, inst.W), dtype=torch.int64, device=dev)
+        cuts = torch.zeros((R, K), dtype=torch.int64, device=dev)
+        lo = torch.full((K,), 2 ** 62, dtype=torch.int64, device=dev)  # running minimum of every objective
+
+        def sample(params, seed, rnd):
+            if dense:
+                M.moq_sample_dense(dh, lam, R, params, seed, rnd, bits)
+                M.moq_dense_evaluate_cuts(dh, bits, R, cuts)
+            else:
+                M.moq_sample(inst.handle, lam, R, params, seed, rnd, bits)
+                M.moq_evaluate_cuts(inst.handle, bits, R, cuts)
+
+        arms = {"ni_bsb": ("bsb", 0.1, T), "ni_dsb": ("dsb", 0.1, T), "random": ("dsb", 0.0, 0)}
+        fronts, res = {}, {}
+        for name, (variant, alpha, steps) in arms.items():
+            params = M.moq_default_params(variant=variant, steps=steps, dt=1.0, alpha=alpha)
+            arch = P.Archive(n, K, capacity=1 << 19, max_batch=R)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rnd = 0
+            while True:
+                sample(params, 11, rnd)
+                torch.minimum(lo, cuts.min(dim=0).values, out=lo)
+                arch.merge(cuts, bits, R, rnd * R)
+                rnd += 1
+                torch.cuda.synchronize()
+                if time.perf_counter() - t0 >= limit:
+                    break
+            secs = time.perf_counter() - t0
+            if dense:
+                M.moq_dense_status(dh)
+            fronts[name] = arch.copy_out()[0]
+            res[name] = {"rounds": rnd, "samples": rnd * R, "seconds": round(secs, 3)}
+            if steps > 0:
+                units += float(R) * n * steps * rnd
+                busy += secs
+            arch.close()
+        if n == 25:  # exhaustive front: every configuration with s_0 = +1
+            ref_arch = P.Archive(n, K, capacity=1 << 19, max_batch=1 << 20)
+            chunk = torch.zeros((1 << 20, 1), dtype=torch.int64, device=dev)
+            ccut = torch.zeros((1 << 20, K), dtype=torch.int64, device=dev)
+            for c in range(1 << 4):
+                chunk[:, 0] = (torch.arange(1 << 20, device=dev, dtype=torch.int64) + (c << 20)) << 1
+                M.moq_evaluate_cuts(inst.handle, chunk, 1 << 20, ccut)
+                torch.minimum(lo, ccut.min(dim=0).values, out=lo)
+                ref_arch.merge(ccut, chunk, 1 << 20, c << 20)
+            ref_type = "exhaustive (2^24 configurations)"
+        else:  # composite front of the arms
+            ref_arch = P.Archive(n, K, capacity=1 << 19, max_batch=1 << 19)
+            for name, f in fronts.items():
+                if len(f):
+                    ref_arch.merge(torch.from_numpy(f).to(dev), torch.zeros((len(f), inst.W), dtype=torch.int64, device=dev),
+                                   len(f), 0)
+            ref_type = "composite of the arms' fronts"
+        ref_front = ref_arch.copy_out()[0]
+        ref_pt = lo.cpu().numpy() - 1  # strictly below every sample
+        hv_ref = ref_arch.hypervolume(ref_pt)
+        ref_set = {tuple(v) for v in ref_front.tolist()}
+        for name, f in fronts.items():
+            a = P.Archive(n, K, capacity=1 << 19, max_batch=max(1, len(f)))
+            if len(f):
+                a.merge(torch.from_numpy(f).to(dev), torch.zeros((len(f), inst.W), dtype=torch.int64, device=dev), len(f), 0)
+            res[name]["front_points"] = int(len(f))
+            res[name]["reference_points_found"] = int(sum(tuple(v) in ref_set for v in f.tolist()))
+            res[name]["hv_ratio"] = a.hypervolume(ref_pt) / hv_ref
+            a.close()
+        results[f"n{n}_d{d}"] = {"reference": ref_type, "reference_front_size": int(len(ref_front)),
+                                 "reference_point": [int(v) for v in ref_pt], "sampler": "dense tcgen05" if dense else "sparse",
+                                 "T": T, "time_limit_s": limit, **res}
+        ref_arch.close()
+        if dh is not None:
+            M.moq_dense_destroy(dh)
+        inst.close()
+    return {"metric": METRIC, "value": units / max(busy, 1e-9), "unit": METRIC, "n_gpus": world, "steps": 1, "warmup": 0,
+            "ms_per_step": busy * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (sparse) / bf16 products, f32 state (dense)", "data": "synthetic",
+            "config": {"workload": "Appendix E correlated K=3 instances, 190 Das-Dennis weights x 3000 replicas per round, "
+                                   "runtime-limited rounds; value = spin updates of the SB arms over their time",
+                       "time_scale": args.time_scale},
+            "appendix_e": results}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -575,9 +692,10 @@ def main():
     ap.add_argument("--ttt-rounds", type=int, default=64)
     ap.add_argument("--no-ttt", action="store_true")
     ap.add_argument("--cpu-baseline-worker", action="store_true")
-    ap.add_argument("--workload", default="precision", choices=["precision", "batching", "dense", "paper"],
+    ap.add_argument("--workload", default="precision", choices=["precision", "batching", "dense", "paper", "appendix_e"],
                     help="precision (the default line), the batching or dense configuration, or the paper's protocol")
     ap.add_argument("--paper-rounds", type=int, default=20)
+    ap.add_argument("--time-scale", type=float, default=1.0, help="scales the appendix_e runtime limits (5 s / 10 s)")
     ap.add_argument("--dense-n", type=int, default=2000)
     ap.add_argument("--dense-replicas", type=int, default=8192)
     ap.add_argument("--dense-steps", type=int, default=3000)
@@ -621,8 +739,8 @@ def main():
     if world > 1:
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         torch.distributed.init_process_group("nccl")
-    if args.workload in ("batching", "dense", "paper"):
-        arm = {"batching": batching_arm, "dense": dense_arm, "paper": paper_arm}[args.workload]
+    if args.workload in ("batching", "dense", "paper", "appendix_e"):
+        arm = {"batching": batching_arm, "dense": dense_arm, "paper": paper_arm, "appendix_e": appendix_e_arm}[args.workload]
         line = arm(args, rank, world)
         if rank == 0:
             print(json.dumps(line), flush=True)
