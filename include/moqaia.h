@@ -144,7 +144,10 @@ int moq_batch_create(const moq_instance* const* insts, int32_t count, const int3
 void moq_batch_destroy(moq_batch* b);
 int moq_batch_layout(const moq_batch* b, int64_t* replica_offsets, int64_t* word_offsets);
 /* block_threads in {256, 512, 1024}, slots_per_thread in {1, 2}, block_threads *
- * slots_per_thread >= the largest n; *items_out (may be NULL) = work items. Synchronous. */
+ * slots_per_thread >= the largest n; *items_out (may be NULL) = work items. (0, 0) selects
+ * per-instance mode: moq_sample_batch then launches the single-instance sampler once per
+ * instance (largest first, replica counters from the instance's offset), whose blocks are
+ * sized per instance; the samples are the same bits either way. Synchronous. */
 int moq_batch_set_tiles(moq_batch* b, int32_t block_threads, int32_t slots_per_thread, int32_t* items_out);
 /* Samples every replica of every instance (asynchronous; p's state arrays must be NULL). */
 int moq_sample_batch(moq_batch* b, const float* lambda_all, const moq_sample_params* p, uint64_t seed, uint64_t round,

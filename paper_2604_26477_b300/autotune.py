@@ -2,7 +2,8 @@
 
 For a batch of instances the persistent sampler can run with blocks of 256, 512 or 1024
 threads and one or two spin slots per thread; the replicas per work item follow from the
-tile (Rb = min(32, threads * slots / n)). Results do not depend on the tile, only speed
+tile (Rb = min(32, threads * slots / n)). The alternative is one launch of the
+single-instance sampler per instance, whose block shape follows each instance's n. Results do not depend on the tile, only speed
 does, so the tuner times every legal shape on the batch itself with a short probe
 trajectory (CUDA events on the launching stream, after one warm-up launch) and keeps
 the fastest. Winners are cached in a JSON file keyed by the batch's shape signature
@@ -20,7 +21,8 @@ import torch
 
 from . import moqaia as M
 
-CANDIDATES = [(1024, 1), (512, 2), (512, 1), (256, 2), (256, 1)]
+# (0, 0): one launch of the single-instance sampler per instance (blocks sized per instance)
+CANDIDATES = [(1024, 1), (512, 2), (512, 1), (256, 2), (256, 1), (0, 0)]
 _CACHE_PATH = os.environ.get("MOQ_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "moqaia_tiles.json"))
 _lock = threading.Lock()
 
@@ -47,7 +49,8 @@ def _store(cache):
 
 
 def legal(max_n):
-    return [(bd, spt) for bd, spt in CANDIDATES if bd * spt >= max_n and not (spt == 2 and bd > 512)]
+    return [(bd, spt) for bd, spt in CANDIDATES
+            if (bd, spt) == (0, 0) or (bd * spt >= max_n and not (spt == 2 and bd > 512))]
 
 
 def tune_batch(batch_handle, ns, reps, K, lam_all, bits_all, params, probe_steps=64, use_cache=True):

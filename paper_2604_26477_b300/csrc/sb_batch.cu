@@ -270,6 +270,7 @@ struct moq_batch {
     int32_t nitems = 0;
     std::vector<moq::BatchInst> h_insts;
     std::vector<int64_t> h_E;
+    std::vector<const moq_instance*> h_handles;  // for the per-instance mode (bd == 0)
     moq::BatchInst* d_insts = nullptr;
     moq::BatchItem* d_items = nullptr;
     int64_t items_cap = 0;
@@ -400,6 +401,7 @@ int moq_batch_create(const moq_instance* const* insts, int32_t count, const int3
         items_cap += in.R;  // at most one item per replica
         b->h_insts.push_back(in);
         b->h_E.push_back(h->E);
+        b->h_handles.push_back(h);
         b->max_degree = std::max(b->max_degree, h->max_degree);
         b->max_n = std::max(b->max_n, h->n);
     }
@@ -462,8 +464,14 @@ int moq_batch_set_tiles(moq_batch* b, int32_t block_threads, int32_t slots_per_t
 {
     using namespace moq;
     if (!b) return fail(MOQ_ERR_ARG, "moq_batch_set_tiles: NULL batch");
+    if (block_threads == 0 && slots_per_thread == 0) {  // per-instance launches of the single-instance sampler
+        b->bd = 0;
+        b->spt = 0;
+        if (items_out) *items_out = b->count;
+        return MOQ_OK;
+    }
     if ((block_threads != 256 && block_threads != 512 && block_threads != 1024) || (slots_per_thread != 1 && slots_per_thread != 2))
-        return fail(MOQ_ERR_ARG, "moq_batch_set_tiles: block_threads in {256, 512, 1024}, slots_per_thread in {1, 2}");
+        return fail(MOQ_ERR_ARG, "moq_batch_set_tiles: block_threads in {256, 512, 1024}, slots_per_thread in {1, 2} (or 0, 0)");
     if (slots_per_thread == 2 && block_threads > 512)
         return fail(MOQ_ERR_ARG, "moq_batch_set_tiles: two slots per thread need block_threads <= 512");
     if (block_threads * slots_per_thread < b->max_n)
@@ -483,6 +491,22 @@ int moq_sample_batch(moq_batch* b, const float* lambda_all, const moq_sample_par
     if (p->steps < 0 || (p->variant != MOQ_DSB && p->variant != MOQ_BSB)) return fail(MOQ_ERR_ARG, "moq_sample_batch: bad steps or variant");
     if (p->x_init || p->y_init || p->x_out || p->y_out) return fail(MOQ_ERR_UNSUPPORTED, "moq_sample_batch: state arrays are single-instance only");
     cudaStream_t st = as_stream(stream);
+    if (b->bd == 0) {
+        // one launch of the single-instance sampler per instance, largest first; replica
+        // counters start at the instance's offset, as in the persistent kernel
+        std::vector<int> order(b->count);
+        for (int i = 0; i < b->count; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->h_insts[x].n > b->h_insts[y].n; });
+        for (int i : order) {
+            const BatchInst& in = b->h_insts[i];
+            moq_sample_params pi = *p;
+            pi.replica_offset = (uint32_t)in.rep_off;
+            const int rc = moq_sample(b->h_handles[i], lambda_all + in.rep_off * b->K, in.R, &pi, seed, round,
+                                      bits_all + in.bits_off, stream);
+            if (rc != MOQ_OK) return rc;
+        }
+        return MOQ_OK;
+    }
     MOQ_CUDA_TRY(cudaMemsetAsync(b->d_queue, 0, sizeof(int32_t), st));
     BatchArgs a{};
     a.insts = b->d_insts;

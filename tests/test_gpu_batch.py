@@ -41,7 +41,7 @@ def batch(P):
 
 
 @pytest.mark.parametrize("variant,alpha", [("dsb", 0.15), ("bsb", 0.0)])
-@pytest.mark.parametrize("tile", [(1024, 1), (512, 2)])
+@pytest.mark.parametrize("tile", [(1024, 1), (512, 2), (0, 0)])
 def test_batch_matches_single_instance(M, P, batch, variant, alpha, tile):
     srcs, insts, b = batch
     b.set_tiles(*tile)
@@ -76,15 +76,16 @@ def test_batch_tiles_and_tuner(M, P, batch, tmp_path, monkeypatch):
     from paper_2604_26477_b300 import autotune
     monkeypatch.setattr(autotune, "_CACHE_PATH", str(tmp_path / "tiles.json"))
     tile, timings = b.tune(M.moq_default_params(steps=200, dt=0.5, alpha=0.1), probe_steps=32)
-    assert tile in [(1024, 1), (512, 2)] and set(timings) == {"1024x1", "512x2"}
+    assert tile in [(1024, 1), (512, 2), (0, 0)] and set(timings) == {"1024x1", "512x2", "0x0"}
     assert timings[f"{tile[0]}x{tile[1]}"] == min(timings.values())
     tile2, _ = b.tune(M.moq_default_params(steps=200, dt=0.5, alpha=0.1))  # from the cache
     assert tile2 == tile
 
 
-def test_batch_round_in_cuda_graph(M, P, batch):
+@pytest.mark.parametrize("tile", [(512, 2), (0, 0)])
+def test_batch_round_in_cuda_graph(M, P, batch, tile):
     srcs, insts, b = batch
-    b.set_tiles(512, 2)
+    b.set_tiles(*tile)
     params = M.moq_default_params(steps=64, dt=0.5, alpha=0.1)
     b.sample(params, seed=3, round_=0)
     b.evaluate_cuts()
