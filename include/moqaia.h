@@ -105,6 +105,12 @@ void moq_default_params(moq_sample_params* p);
  * Ownership: inputs are copied; *out is owned by the caller until destroyed. */
 int moq_create_instance(int32_t n, int32_t K, int64_t E, const int32_t* ei, const int32_t* ej,
                         const int32_t* w, void* stream, moq_instance** out);
+/* a1 for a dense weight matrix: J_upper (host, K x n(n-1)/2, row k = objective k) holds
+ * J^(k)_ij for the pairs i < j in row order ((0,1), (0,2), .., (0,n-1), (1,2), ..). The
+ * pairs with a non-zero weight in some objective become the edges, in that order; the
+ * rest is moq_create_instance. Errors: MOQ_ERR_ARG (n outside [2, 65536], K outside
+ * [2, 8], NULL), then those of moq_create_instance. Synchronises `stream`. */
+int moq_create_instance_dense(int32_t n, int32_t K, const int32_t* J_upper, void* stream, moq_instance** out);
 void moq_destroy_instance(moq_instance* inst);
 int moq_instance_get_info(const moq_instance* inst, moq_instance_info* out);
 

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <vector>
 #include <cmath>
 
 #include "moq_common.cuh"
@@ -337,6 +338,37 @@ int moq_instance_get_info(const moq_instance* inst, moq_instance_info* out)
     if (!inst || !out) return moq::fail(MOQ_ERR_ARG, "moq_instance_get_info: NULL argument");
     *out = inst->info;
     return MOQ_OK;
+}
+
+int moq_create_instance_dense(int32_t n, int32_t K, const int32_t* J_upper, void* stream, moq_instance** out)
+{
+    using namespace moq;
+    if (!out) return fail(MOQ_ERR_ARG, "moq_create_instance_dense: out is NULL");
+    *out = nullptr;
+    if (n < 2 || n > (1 << 16)) return fail(MOQ_ERR_ARG, "moq_create_instance_dense: n=%d outside [2, 65536]", n);
+    if (K < 2 || K > kMaxK) return fail(MOQ_ERR_ARG, "moq_create_instance_dense: K=%d outside [2, %d]", K, kMaxK);
+    if (!J_upper) return fail(MOQ_ERR_ARG, "moq_create_instance_dense: NULL weights");
+    // pairs (i, j), i < j, row by row: the edges are the pairs with a non-zero weight in
+    // some objective, in that order
+    const int64_t P = (int64_t)n * (n - 1) / 2;
+    std::vector<int32_t> ei, ej;
+    std::vector<int64_t> at;
+    int64_t q = 0;
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t j = i + 1; j < n; ++j, ++q) {
+            bool any = false;
+            for (int k = 0; k < K && !any; ++k) any = J_upper[(int64_t)k * P + q] != 0;
+            if (any) {
+                ei.push_back(i);
+                ej.push_back(j);
+                at.push_back(q);
+            }
+        }
+    const int64_t E = (int64_t)ei.size();
+    std::vector<int32_t> w((size_t)K * E);
+    for (int k = 0; k < K; ++k)
+        for (int64_t e = 0; e < E; ++e) w[(size_t)k * E + e] = J_upper[(int64_t)k * P + at[e]];
+    return moq_create_instance(n, K, E, ei.data(), ej.data(), w.data(), stream, out);
 }
 
 }  // extern "C"

@@ -62,6 +62,7 @@ _vp, _i32, _i64, _u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
 _sigs = {
     "moq_default_params": (None, [C.POINTER(moq_sample_params)]),
     "moq_create_instance": (C.c_int, [_i32, _i32, _i64, _vp, _vp, _vp, _vp, C.POINTER(_vp)]),
+    "moq_create_instance_dense": (C.c_int, [_i32, _i32, _vp, _vp, C.POINTER(_vp)]),
     "moq_destroy_instance": (None, [_vp]),
     "moq_instance_get_info": (C.c_int, [_vp, C.POINTER(moq_instance_info)]),
     "moq_sample": (C.c_int, [_vp, _vp, _i32, C.POINTER(moq_sample_params), _u64, _u64, _vp, _vp]),
@@ -183,6 +184,15 @@ def moq_create_instance(n, K, E, ei, ej, w, stream=None) -> C.c_void_p:
         raise ValueError("edge arrays must have E entries and w K*E")
     h = C.c_void_p()
     _check(_lib.moq_create_instance(n, K, E, pei, pej, pw, _stream(stream), C.byref(h)), "moq_create_instance")
+    return h
+
+
+def moq_create_instance_dense(n, K, J_upper, stream=None) -> C.c_void_p:
+    J_, pj = _hptr(J_upper, np.int32)
+    if J_.size != K * n * (n - 1) // 2:
+        raise ValueError("J_upper must hold K * n(n-1)/2 weights")
+    h = C.c_void_p()
+    _check(_lib.moq_create_instance_dense(n, K, pj, _stream(stream), C.byref(h)), "moq_create_instance_dense")
     return h
 
 

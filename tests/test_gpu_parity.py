@@ -83,6 +83,32 @@ def test_instance_info(M, P, oracle, name):
     assert info["ref_point"] == list(oracle.reference_point(src))
 
 
+def test_dense_constructor_matches_edge_list(M, P, oracle):
+    # an upper-triangle weight matrix (zeros where no objective has an edge) gives the
+    # instance of its non-zero pairs in row order
+    src = wl.random_graph(37, 0.3, 21, K=3, wmax=9)
+    n, K = src.n, src.K
+    iu, ju = np.triu_indices(n, 1)
+    pos = {(int(a), int(b)): q for q, (a, b) in enumerate(zip(iu, ju))}
+    J = np.zeros((K, iu.size), np.int32)
+    for e in range(src.E):
+        J[:, pos[(int(src.ei[e]), int(src.ej[e]))]] = src.w[:, e]
+    h = M.moq_create_instance_dense(n, K, J)
+    try:
+        info = M.moq_instance_get_info(h)
+        assert info["E"] == src.E and info["weight_sum"] == list(src.w.astype(np.int64).sum(axis=1))
+        assert info["ref_point"] == list(oracle.reference_point(src))
+        bits = wl.random_sign_bits(300, n, 4)
+        cuts = torch.zeros((300, K), dtype=torch.int64, device="cuda")
+        M.moq_evaluate_cuts(h, _bits_dev(bits), 300, cuts)
+        assert np.array_equal(cuts.cpu().numpy(), oracle.cuts(src, bits))
+    finally:
+        M.moq_destroy_instance(h)
+    with pytest.raises(M.MoqError) as e:
+        M.moq_create_instance_dense(1, K, np.zeros(0, np.int32))
+    assert e.value.code == M.MOQ_ERR_ARG
+
+
 def test_instance_rejects_bad_input(M):
     ei = np.array([0, 1], np.int32)
     with pytest.raises(M.MoqError) as e:
