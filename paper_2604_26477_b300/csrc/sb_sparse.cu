@@ -43,9 +43,16 @@ struct SbArgs {
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-__host__ __device__ inline size_t sb_smem_bytes(int Rb, int W)
+// Pump: 0 = caller's schedule array, 1 = linear pump computed per step, 2 = linear pump
+// read from a per-block table of the T values (one shared-memory load per step instead of
+// a multiply-add and a counter update; the same single-rounding formula fills it)
+constexpr int kPumpSchedule = 0, kPumpInline = 1, kPumpTable = 2;
+constexpr int kPumpTableMax = 8192;
+
+__host__ __device__ inline size_t sb_smem_bytes(int Rb, int W, int pump_table_steps)
 {
-    return sizeof(float) * 2 * kPhiStride + align_up(sizeof(unsigned) * 2 * Rb, 16) + sizeof(unsigned long long) * (size_t)Rb * W;
+    return sizeof(float) * 2 * kPhiStride + align_up(sizeof(unsigned) * 2 * Rb, 16) +
+           align_up(sizeof(unsigned long long) * (size_t)Rb * W, 16) + sizeof(float) * (size_t)pump_table_steps;
 }
 
 // One Euler step of one spin: force from the shared-memory phi buffer `rd`, symplectic
@@ -63,7 +70,7 @@ __device__ __forceinline__ void sb_step(const float* rd, float* wr, int tid, con
     __syncthreads();
 }
 
-template <int VARIANT, int DMAX, bool NOISE, bool LINEAR>
+template <int VARIANT, int DMAX, bool NOISE, int PUMP>
 __global__ void __launch_bounds__(1024) k_sb_sparse(const SbArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -73,6 +80,8 @@ __global__ void __launch_bounds__(1024) k_sb_sparse(const SbArgs a)
     unsigned* red = reinterpret_cast<unsigned*>(phiB + kPhiStride);  // 2 * Rb
     unsigned long long* wb = reinterpret_cast<unsigned long long*>(smem_raw + sizeof(float) * 2 * kPhiStride +
                                                                    align_up(sizeof(unsigned) * 2 * Rb, 16));
+    float* pump_t = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(wb) +
+                                             align_up(sizeof(unsigned long long) * (size_t)Rb * a.W, 16));
 
     const int tid = threadIdx.x;
     const int i = tid / Rb;       // spin
@@ -140,7 +149,13 @@ __global__ void __launch_bounds__(1024) k_sb_sparse(const SbArgs a)
     const float dt = a.dt, kappa = a.kappa, dta0 = a.dt * a.a0, a0 = a.a0, a0inv = a.a0inv;
     const float* sched = a.schedule;
     const int T = a.T;
-    auto cm_at = [&](int m, float mf) -> float { return LINEAR ? fmaf(a0inv, mf, -a0) : (__ldg(sched + m) - a0); };
+    if (PUMP == kPumpTable) {
+        for (int q = tid; q < T; q += blockDim.x) pump_t[q] = fmaf(a0inv, (float)q, -a0);
+        __syncthreads();
+    }
+    auto cm_at = [&](int m, float mf) -> float {
+        return PUMP == kPumpTable ? pump_t[m] : (PUMP == kPumpInline ? fmaf(a0inv, mf, -a0) : (__ldg(sched + m) - a0));
+    };
     // one Philox4x32-10 block per eight steps: word q gives the Gaussians of steps 2q, 2q+1
     auto block8 = [&](int m) -> uint4 {
         return NOISE ? Philox4x32::block(make_uint4((uint32_t)(m >> 3), (uint32_t)i, a.rep_off + (uint32_t)r, a.round32),
@@ -211,34 +226,42 @@ __global__ void __launch_bounds__(1024) k_sb_sparse(const SbArgs a)
     }
 }
 
-template <int VARIANT, int DMAX, bool NOISE, bool LINEAR>
+template <int VARIANT, int DMAX, bool NOISE, int PUMP>
 cudaError_t launch_one(const SbArgs& a, dim3 grid, dim3 block, size_t smem, cudaStream_t st)
 {
-    auto k = k_sb_sparse<VARIANT, DMAX, NOISE, LINEAR>;
+    auto k = k_sb_sparse<VARIANT, DMAX, NOISE, PUMP>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, block, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int VARIANT, int DMAX>
-cudaError_t launch_flags(const SbArgs& a, bool noise, bool linear, dim3 grid, dim3 block, size_t smem, cudaStream_t st)
+template <int VARIANT, int DMAX, bool NOISE>
+cudaError_t launch_pump(const SbArgs& a, int pump, dim3 grid, dim3 block, size_t smem, cudaStream_t st)
 {
-    if (noise) return linear ? launch_one<VARIANT, DMAX, true, true>(a, grid, block, smem, st)
-                             : launch_one<VARIANT, DMAX, true, false>(a, grid, block, smem, st);
-    return linear ? launch_one<VARIANT, DMAX, false, true>(a, grid, block, smem, st)
-                  : launch_one<VARIANT, DMAX, false, false>(a, grid, block, smem, st);
+    switch (pump) {
+    case kPumpTable: return launch_one<VARIANT, DMAX, NOISE, kPumpTable>(a, grid, block, smem, st);
+    case kPumpInline: return launch_one<VARIANT, DMAX, NOISE, kPumpInline>(a, grid, block, smem, st);
+    default: return launch_one<VARIANT, DMAX, NOISE, kPumpSchedule>(a, grid, block, smem, st);
+    }
+}
+
+template <int VARIANT, int DMAX>
+cudaError_t launch_flags(const SbArgs& a, bool noise, int pump, dim3 grid, dim3 block, size_t smem, cudaStream_t st)
+{
+    return noise ? launch_pump<VARIANT, DMAX, true>(a, pump, grid, block, smem, st)
+                 : launch_pump<VARIANT, DMAX, false>(a, pump, grid, block, smem, st);
 }
 
 template <int VARIANT>
-cudaError_t launch_variant(const SbArgs& a, int dmax, bool noise, bool linear, dim3 grid, dim3 block, size_t smem,
+cudaError_t launch_variant(const SbArgs& a, int dmax, bool noise, int pump, dim3 grid, dim3 block, size_t smem,
                            cudaStream_t st)
 {
     switch (dmax) {
-    case 3: return launch_flags<VARIANT, 3>(a, noise, linear, grid, block, smem, st);
-    case 4: return launch_flags<VARIANT, 4>(a, noise, linear, grid, block, smem, st);
-    case 8: return launch_flags<VARIANT, 8>(a, noise, linear, grid, block, smem, st);
-    default: return launch_flags<VARIANT, 16>(a, noise, linear, grid, block, smem, st);
+    case 3: return launch_flags<VARIANT, 3>(a, noise, pump, grid, block, smem, st);
+    case 4: return launch_flags<VARIANT, 4>(a, noise, pump, grid, block, smem, st);
+    case 8: return launch_flags<VARIANT, 8>(a, noise, pump, grid, block, smem, st);
+    default: return launch_flags<VARIANT, 16>(a, noise, pump, grid, block, smem, st);
     }
 }
 
@@ -316,11 +339,11 @@ extern "C" int moq_sample(const moq_instance* inst, const float* lambda, int32_t
     const int md = inst->max_degree;
     const int dmax = md <= 3 ? 3 : (md <= 4 ? 4 : (md <= 8 ? 8 : 16));
     const dim3 block(a.n * a.Rb), grid((unsigned)ceil_div(R, a.Rb));
-    const size_t smem = sb_smem_bytes(a.Rb, a.W);
     const bool noise = p->alpha != 0.0f;
-    const bool linear = p->schedule == nullptr;
-    cudaError_t e = (p->variant == MOQ_DSB) ? launch_variant<MOQ_DSB>(a, dmax, noise, linear, grid, block, smem, as_stream(stream))
-                                            : launch_variant<MOQ_BSB>(a, dmax, noise, linear, grid, block, smem, as_stream(stream));
+    const int pump = p->schedule ? kPumpSchedule : (a.T <= kPumpTableMax ? kPumpTable : kPumpInline);
+    const size_t smem = sb_smem_bytes(a.Rb, a.W, pump == kPumpTable ? a.T : 0);
+    cudaError_t e = (p->variant == MOQ_DSB) ? launch_variant<MOQ_DSB>(a, dmax, noise, pump, grid, block, smem, as_stream(stream))
+                                            : launch_variant<MOQ_BSB>(a, dmax, noise, pump, grid, block, smem, as_stream(stream));
     if (e != cudaSuccess) return cuda_fail(e, "moq_sample launch");
     return MOQ_OK;
 }
