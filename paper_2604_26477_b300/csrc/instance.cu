@@ -212,6 +212,8 @@ void free_instance(moq_instance* h)
     cudaFree(h->col);
     cudaFree(h->wn);
     cudaFree(h->rowsum);
+    cudaFree(h->slot_spin);
+    cudaFree(h->spin_slot);
     delete h;
 }
 
@@ -327,6 +329,26 @@ int moq_create_instance(int32_t n, int32_t K, int64_t E, const int32_t* ei, cons
         inf.ref_point[k] = hsums[2 * K + k];
     }
     graph_features(n, K, E, hsums, hsums + 3 * K, inf.features);
+    // sampler slots in order of decreasing degree (stable), so that warps of the on-chip
+    // sampler hold spins of equal degree where the graph allows it
+    {
+        std::vector<int32_t> dgr(n, 0), order(n), inv(n);
+        for (int64_t e = 0; e < E; ++e) {
+            ++dgr[ei[e]];
+            ++dgr[ej[e]];
+        }
+        for (int32_t i = 0; i < n; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return dgr[a] > dgr[b]; });
+        for (int32_t q = 0; q < n; ++q) inv[order[q]] = q;
+        cudaError_t e = cudaMalloc((void**)&h->slot_spin, sizeof(int32_t) * n);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&h->spin_slot, sizeof(int32_t) * n);
+        if (e == cudaSuccess) e = cudaMemcpy(h->slot_spin, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(h->spin_slot, inv.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            free_instance(h);
+            return cuda_fail(e, "moq_create_instance slot order");
+        }
+    }
     *out = h;
     return MOQ_OK;
 }
