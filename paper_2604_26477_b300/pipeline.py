@@ -158,9 +158,12 @@ class LearnedProposer:
     rows. The next round's batch is a fraction ``rho`` of proposed weight vectors -- the
     candidates whose predicted cuts reach furthest beyond the current front -- and the rest
     uniform on the simplex (exploration, and the fallback before any data exists).
+    Defaults (2048 candidates, 5 Adam steps per round) were picked on a held-out n = 300
+    instance: 8192 candidates and 20 steps gave about as many samples to the target but
+    twice the time per round.
     """
 
-    def __init__(self, inst: Instance, R: int, rho=0.5, n_candidates=8192, max_rows=1 << 20, train_steps=20,
+    def __init__(self, inst: Instance, R: int, rho=0.5, n_candidates=2048, max_rows=1 << 20, train_steps=5,
                  batch=4096, lr=3e-3, seed=0, device="cuda"):
         self.inst, self.R, self.K = inst, R, inst.K
         self.rho, self.n_candidates, self.train_steps, self.batch, self.lr, self.seed = \
