@@ -135,17 +135,23 @@ class RoundBuffers:
 
 
 def sample_round(inst: Instance, archive: Archive, buf: RoundBuffers, params, seed: int, round_: int,
-                 lam=None, index_base=None, stream=None):
+                 lam=None, index_base=None, stream=None, dense=None):
     """One pass of the hot path: (lambda) -> sample -> cuts -> Pareto merge. Asynchronous.
 
     With ``lam=None`` the round draws its own uniform-simplex weight vectors on the GPU.
+    With ``dense`` (a ``moq_dense_create`` handle for ``inst``) the round runs the
+    tensor-core sampler and the tensor-core cut evaluation.
     """
     R = buf.R
     if lam is None:
         M.moq_lambda_dirichlet(inst.K, R, seed, round_, buf.lam, stream)
         lam = buf.lam
-    M.moq_sample(inst.handle, lam, R, params, seed, round_, buf.bits, stream)
-    M.moq_evaluate_cuts(inst.handle, buf.bits, R, buf.cuts, stream)
+    if dense is not None:
+        M.moq_sample_dense(dense, lam, R, params, seed, round_, buf.bits, stream)
+        M.moq_dense_evaluate_cuts(dense, buf.bits, R, buf.cuts, stream)
+    else:
+        M.moq_sample(inst.handle, lam, R, params, seed, round_, buf.bits, stream)
+        M.moq_evaluate_cuts(inst.handle, buf.bits, R, buf.cuts, stream)
     archive.merge(buf.cuts, buf.bits, R, R * round_ if index_base is None else index_base, stream=stream)
 
 
@@ -217,7 +223,7 @@ class LearnedProposer:
 
 
 def time_to_target(src, target_hv: int, params, R: int, seed: int = 0, max_rounds: int = 1000,
-                   capacity=1 << 18, learned: bool = False, proposer_kwargs=None):
+                   capacity=1 << 18, learned: bool = False, proposer_kwargs=None, dense: bool = False):
     """Repeat sampling rounds until the archive's hypervolume reaches ``target_hv``.
 
     The clock covers instance construction, every round (weight vectors, sampling, cuts,
@@ -231,11 +237,12 @@ def time_to_target(src, target_hv: int, params, R: int, seed: int = 0, max_round
     inst = Instance(src)
     arch = Archive(src.n, src.K, capacity=capacity, max_batch=R)
     buf = RoundBuffers(R, src.n, src.K)
+    dh = M.moq_dense_create(inst.handle, R) if dense else None
     prop = LearnedProposer(inst, R, seed=seed, **(proposer_kwargs or {})) if learned else None
     hv, rounds, trace = 0, 0, []
     while rounds < max_rounds:
         lam = prop.lambdas(rounds, arch) if prop else None
-        sample_round(inst, arch, buf, params, seed, rounds, lam=lam)
+        sample_round(inst, arch, buf, params, seed, rounds, lam=lam, dense=dh)
         if prop:
             prop.observe(lam, buf.cuts, R)
         rounds += 1
@@ -248,6 +255,9 @@ def time_to_target(src, target_hv: int, params, R: int, seed: int = 0, max_round
     front = arch.size()
     if prop:
         prop.close()
+    if dh is not None:
+        M.moq_dense_status(dh)
+        M.moq_dense_destroy(dh)
     arch.close()
     inst.close()
     return {"seconds": secs, "rounds": rounds, "samples": rounds * R, "hv": hv, "front": front,

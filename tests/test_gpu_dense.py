@@ -218,3 +218,26 @@ def test_dense_cuts_reject_large_weights(M, P):
         assert e.value.code == M.MOQ_ERR_UNSUPPORTED
     finally:
         M.moq_dense_destroy(d)
+
+
+def test_round_driver_on_the_dense_sampler(M, P):
+    # the round driver runs the tensor-core sampler and cut evaluation when asked; the
+    # archive it fills reaches the hypervolume of a reference run on the same sampler
+    src = wl.complete_graph(150, 12, K=3)
+    inst = P.Instance(src)
+    dh = M.moq_dense_create(inst.handle, 512)
+    arch = P.Archive(src.n, 3, capacity=1 << 16, max_batch=512)
+    buf = P.RoundBuffers(512, src.n, 3)
+    params = M.moq_default_params(variant="dsb", steps=300, dt=0.5, alpha=0.1)
+    for rnd in range(4):
+        P.sample_round(inst, arch, buf, params, 7, rnd, dense=dh)
+    M.moq_dense_status(dh)
+    target = arch.hypervolume(inst.ref)
+    c, _, _ = arch.copy_out()
+    ref_cuts = torch.zeros((512, 3), dtype=torch.int64, device="cuda")
+    M.moq_evaluate_cuts(inst.handle, buf.bits, 512, ref_cuts)  # the last round's cuts, CUDA-core path
+    assert torch.equal(ref_cuts, buf.cuts)
+    M.moq_dense_destroy(dh)
+    arch.close()
+    out = P.time_to_target(src, target, params, 512, seed=7, max_rounds=4, dense=True)
+    assert out["reached"] and out["rounds"] <= 4 and out["hv"] >= target
