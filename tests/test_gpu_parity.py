@@ -534,6 +534,28 @@ def test_final_hv_distribution_matches_oracle(M, P, oracle):
     assert abs(np.median(hv_gpu) / np.median(hv_cpu) - 1) < 0.02
 
 
+def test_sampler_rejects_what_it_does_not_run(M, P):
+    lam = torch.full((8, 3), 1.0 / 3, device="cuda")
+    bits = torch.zeros((8, 17), dtype=torch.int64, device="cuda")
+    big = P.Instance(wl.random_regular(1026, 3, K=3))  # n > 1024: beyond the on-chip sampler
+    with pytest.raises(M.MoqError) as e:
+        M.moq_sample(big.handle, lam, 8, M.moq_default_params(steps=4), 1, 0, bits)
+    assert e.value.code == M.MOQ_ERR_UNSUPPORTED
+    star = wl.Instance(20, np.zeros(19, np.int32), np.arange(1, 20, dtype=np.int32), np.ones((3, 19), np.int32))
+    hub = P.Instance(star)  # a vertex of degree 19 > 16
+    with pytest.raises(M.MoqError) as e:
+        M.moq_sample(hub.handle, lam, 8, M.moq_default_params(steps=4), 1, 0, bits)
+    assert e.value.code == M.MOQ_ERR_UNSUPPORTED
+    small = P.Instance(INSTANCES["heavyhex_K3"]())
+    with pytest.raises(M.MoqError) as e:
+        M.moq_sample(small.handle, lam, 8, M.moq_default_params(steps=4, variant=7), 1, 0, bits)
+    assert e.value.code == M.MOQ_ERR_ARG
+    with pytest.raises(M.MoqError) as e:
+        M.moq_sample(small.handle, lam, -1, M.moq_default_params(steps=4), 1, 0, bits)
+    assert e.value.code == M.MOQ_ERR_ARG
+    M.moq_sample(small.handle, lam, 0, M.moq_default_params(steps=4), 1, 0, bits)  # R = 0: nothing to do
+
+
 # ----------------------------------------------------------------------------- lambda
 def test_das_dennis_lattice(M, oracle):
     for K, H in [(3, 21), (4, 13), (2, 9), (5, 7)]:
