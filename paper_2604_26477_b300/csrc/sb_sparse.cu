@@ -164,7 +164,9 @@ __global__ void __launch_bounds__(1024) k_sb_sparse(const SbArgs a)
     };
     // warps whose spins all have fewer than DMAX neighbours run the shorter force loop
     // (the degree order of the slots makes most warps uniform)
-    const int deg_w = __reduce_max_sync(__activemask(), deg);
+    const int lanes_here = (int)blockDim.x - (tid & ~31);  // the last warp of a block may be partial
+    const unsigned warp_mask = lanes_here >= 32 ? 0xffffffffu : ((1u << lanes_here) - 1u);
+    const int deg_w = __reduce_max_sync(warp_mask, deg);  // every thread of the block reaches this line
     auto run = [&](auto nd_const) {
         constexpr int ND = decltype(nd_const)::value;
         // one Philox4x32-10 block per eight steps: word q gives the Gaussians of steps 2q, 2q+1
