@@ -12,7 +12,6 @@
 // offset.
 // HBM sees the CSR rows and lambda once (in) and the packed signs once (out).
 #include <algorithm>
-#include <type_traits>
 #include <stdlib.h>
 
 #include "sb_common.cuh"
@@ -51,6 +50,7 @@ __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a -
 // a multiply-add and a counter update; the same single-rounding formula fills it)
 constexpr int kPumpSchedule = 0, kPumpInline = 1, kPumpTable = 2;
 constexpr int kPumpTableMax = 8192;
+constexpr int kPumpTableMaxThreads = 256;
 
 __host__ __device__ inline size_t sb_smem_bytes(int Rb, int W, int pump_table_steps)
 {
@@ -60,16 +60,14 @@ __host__ __device__ inline size_t sb_smem_bytes(int Rb, int W, int pump_table_st
 
 // One Euler step of one spin: force from the shared-memory phi buffer `rd`, symplectic
 // update, inelastic wall, phi into `wr`, then the block barrier.
-// ND <= DMAX terms of the force are summed (a warp whose spins all have fewer than DMAX
-// neighbours skips the zero padding).
-template <int VARIANT, int DMAX, int ND, bool NOISE>
+template <int VARIANT, int DMAX, bool NOISE>
 __device__ __forceinline__ void sb_step(const float* rd, float* wr, int tid, const float (&jc)[DMAX],
                                         const int (&nb)[DMAX], float cm, float eta, float dt, float kappa, float dta0,
                                         float& x, float& y)
 {
     float f = 0.0f;  // c0 sum_j (-J(c)_ij) phi(x_j)
 #pragma unroll
-    for (int d = 0; d < ND; ++d) f = fmaf(jc[d], rd[nb[d]], f);
+    for (int d = 0; d < DMAX; ++d) f = fmaf(jc[d], rd[nb[d]], f);
     sb_update<NOISE>(f, cm, eta, dt, kappa, dta0, x, y);
     wr[tid] = phi_of<VARIANT>(x);
     __syncthreads();
@@ -162,71 +160,59 @@ __global__ void __launch_bounds__(1024) k_sb_sparse(const SbArgs a)
     auto cm_at = [&](int m, float mf) -> float {
         return PUMP == kPumpTable ? pump_t[m] : (PUMP == kPumpInline ? fmaf(a0inv, mf, -a0) : (__ldg(sched + m) - a0));
     };
-    // warps whose spins all have fewer than DMAX neighbours run the shorter force loop
-    // (the degree order of the slots makes most warps uniform)
-    const int lanes_here = (int)blockDim.x - (tid & ~31);  // the last warp of a block may be partial
-    const unsigned warp_mask = lanes_here >= 32 ? 0xffffffffu : ((1u << lanes_here) - 1u);
-    const int deg_w = __reduce_max_sync(warp_mask, deg);  // every thread of the block reaches this line
-    auto run = [&](auto nd_const) {
-        constexpr int ND = decltype(nd_const)::value;
-        // one Philox4x32-10 block per eight steps: word q gives the Gaussians of steps 2q, 2q+1
-        auto block8 = [&](int m) -> uint4 {
-            return NOISE ? Philox4x32::block(make_uint4((uint32_t)(m >> 3), (uint32_t)i, a.rep_off + (uint32_t)r, a.round32),
-                                             a.key0, a.key1)
-                         : make_uint4(0u, 0u, 0u, 0u);
-        };
-        // the Gaussians of four consecutive steps from two words
-        auto noise4 = [&](uint32_t wa, uint32_t wb, float& e0, float& e1, float& e2, float& e3) {
-            if (NOISE) {
-                const float2 p = box_muller16(wa), q = box_muller16(wb);
-                e0 = p.x; e1 = p.y; e2 = q.x; e3 = q.y;
-            }
-        };
-        auto four_steps = [&](int m, float mf, float e0, float e1, float e2, float e3) {
-            sb_step<VARIANT, DMAX, ND, NOISE>(phiA, phiB, tid, jc, nb, cm_at(m, mf), e0, dt, kappa, dta0, x, y);
-            sb_step<VARIANT, DMAX, ND, NOISE>(phiB, phiA, tid, jc, nb, cm_at(m + 1, mf + 1.0f), e1, dt, kappa, dta0, x, y);
-            sb_step<VARIANT, DMAX, ND, NOISE>(phiA, phiB, tid, jc, nb, cm_at(m + 2, mf + 2.0f), e2, dt, kappa, dta0, x, y);
-            sb_step<VARIANT, DMAX, ND, NOISE>(phiB, phiA, tid, jc, nb, cm_at(m + 3, mf + 3.0f), e3, dt, kappa, dta0, x, y);
-        };
-        // the Gaussians of steps m..m+3 (m a multiple of 4): words (x, y) or (z, w) of the block
-        auto noise_at = [&](int m, float& e0, float& e1, float& e2, float& e3) {
-            if (NOISE) {
-                const uint4 o = block8(m);
-                noise4((m & 4) ? o.z : o.x, (m & 4) ? o.w : o.y, e0, e1, e2, e3);
-            }
-        };
-        int m = 0;
-        float mf = 0.0f;
+    // one Philox4x32-10 block per eight steps: word q gives the Gaussians of steps 2q, 2q+1
+    auto block8 = [&](int m) -> uint4 {
+        return NOISE ? Philox4x32::block(make_uint4((uint32_t)(m >> 3), (uint32_t)i, a.rep_off + (uint32_t)r, a.round32),
+                                         a.key0, a.key1)
+                     : make_uint4(0u, 0u, 0u, 0u);
+    };
+    // the Gaussians of four consecutive steps from two words
+    auto noise4 = [&](uint32_t wa, uint32_t wb, float& e0, float& e1, float& e2, float& e3) {
         if (NOISE) {
-            for (; m + 8 <= T; m += 8) {
-                const uint4 o = block8(m);
-                float e0, e1, e2, e3;
-                noise4(o.x, o.y, e0, e1, e2, e3);
-                four_steps(m, mf, e0, e1, e2, e3);
-                noise4(o.z, o.w, e0, e1, e2, e3);
-                four_steps(m + 4, mf + 4.0f, e0, e1, e2, e3);
-                mf += 8.0f;
-            }
-        }
-        // without noise the whole run; with noise at most one pass (T mod 8 >= 4)
-        for (; m + 4 <= T; m += 4) {
-            float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f, e3 = 0.0f;
-            noise_at(m, e0, e1, e2, e3);
-            four_steps(m, mf, e0, e1, e2, e3);
-            mf += 4.0f;
-        }
-        if (m < T) {  // the last T mod 4 steps (uniform over the block)
-            float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f, e3 = 0.0f;
-            noise_at(m, e0, e1, e2, e3);
-            sb_step<VARIANT, DMAX, ND, NOISE>(phiA, phiB, tid, jc, nb, cm_at(m, mf), e0, dt, kappa, dta0, x, y);
-            if (m + 1 < T) sb_step<VARIANT, DMAX, ND, NOISE>(phiB, phiA, tid, jc, nb, cm_at(m + 1, mf + 1.0f), e1, dt, kappa, dta0, x, y);
-            if (m + 2 < T) sb_step<VARIANT, DMAX, ND, NOISE>(phiA, phiB, tid, jc, nb, cm_at(m + 2, mf + 2.0f), e2, dt, kappa, dta0, x, y);
+            const float2 p = box_muller16(wa), q = box_muller16(wb);
+            e0 = p.x; e1 = p.y; e2 = q.x; e3 = q.y;
         }
     };
-    if (DMAX <= 4 && deg_w < DMAX)
-        run(std::integral_constant<int, (DMAX <= 4 ? DMAX - 1 : DMAX)>{});
-    else
-        run(std::integral_constant<int, DMAX>{});
+    auto four_steps = [&](int m, float mf, float e0, float e1, float e2, float e3) {
+        sb_step<VARIANT, DMAX, NOISE>(phiA, phiB, tid, jc, nb, cm_at(m, mf), e0, dt, kappa, dta0, x, y);
+        sb_step<VARIANT, DMAX, NOISE>(phiB, phiA, tid, jc, nb, cm_at(m + 1, mf + 1.0f), e1, dt, kappa, dta0, x, y);
+        sb_step<VARIANT, DMAX, NOISE>(phiA, phiB, tid, jc, nb, cm_at(m + 2, mf + 2.0f), e2, dt, kappa, dta0, x, y);
+        sb_step<VARIANT, DMAX, NOISE>(phiB, phiA, tid, jc, nb, cm_at(m + 3, mf + 3.0f), e3, dt, kappa, dta0, x, y);
+    };
+    // the Gaussians of steps m..m+3 (m a multiple of 4): words (x, y) or (z, w) of the block
+    auto noise_at = [&](int m, float& e0, float& e1, float& e2, float& e3) {
+        if (NOISE) {
+            const uint4 o = block8(m);
+            noise4((m & 4) ? o.z : o.x, (m & 4) ? o.w : o.y, e0, e1, e2, e3);
+        }
+    };
+    int m = 0;
+    float mf = 0.0f;
+    if (NOISE) {
+        for (; m + 8 <= T; m += 8) {
+            const uint4 o = block8(m);
+            float e0, e1, e2, e3;
+            noise4(o.x, o.y, e0, e1, e2, e3);
+            four_steps(m, mf, e0, e1, e2, e3);
+            noise4(o.z, o.w, e0, e1, e2, e3);
+            four_steps(m + 4, mf + 4.0f, e0, e1, e2, e3);
+            mf += 8.0f;
+        }
+    }
+    // without noise the whole run; with noise at most one pass (T mod 8 >= 4)
+    for (; m + 4 <= T; m += 4) {
+        float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f, e3 = 0.0f;
+        noise_at(m, e0, e1, e2, e3);
+        four_steps(m, mf, e0, e1, e2, e3);
+        mf += 4.0f;
+    }
+    if (m < T) {  // the last T mod 4 steps (uniform over the block)
+        float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f, e3 = 0.0f;
+        noise_at(m, e0, e1, e2, e3);
+        sb_step<VARIANT, DMAX, NOISE>(phiA, phiB, tid, jc, nb, cm_at(m, mf), e0, dt, kappa, dta0, x, y);
+        if (m + 1 < T) sb_step<VARIANT, DMAX, NOISE>(phiB, phiA, tid, jc, nb, cm_at(m + 1, mf + 1.0f), e1, dt, kappa, dta0, x, y);
+        if (m + 2 < T) sb_step<VARIANT, DMAX, NOISE>(phiA, phiB, tid, jc, nb, cm_at(m + 2, mf + 2.0f), e2, dt, kappa, dta0, x, y);
+    }
 
     // readout s_i = sgn(x_i), sgn(0) = +1; bit set for s_i = -1
     const int W = a.W;
@@ -360,7 +346,11 @@ extern "C" int moq_sample(const moq_instance* inst, const float* lambda, int32_t
     const int dmax = md <= 3 ? 3 : (md <= 4 ? 4 : (md <= 8 ? 8 : 16));
     const dim3 block(a.n * a.Rb), grid((unsigned)ceil_div(R, a.Rb));
     const bool noise = p->alpha != 0.0f;
-    const int pump = p->schedule ? kPumpSchedule : (a.T <= kPumpTableMax ? kPumpTable : kPumpInline);
+    // the table trades a multiply-add for a shared-memory load: a gain for small blocks, a
+    // loss for blocks of more than 256 threads, whose gathers already keep the shared-memory
+    // pipe busy (measured: n = 42..150 3-5 % faster, n = 300..1024 2-5 % slower)
+    const bool small_block = a.n * a.Rb <= kPumpTableMaxThreads;
+    const int pump = p->schedule ? kPumpSchedule : (a.T <= kPumpTableMax && small_block ? kPumpTable : kPumpInline);
     const size_t smem = sb_smem_bytes(a.Rb, a.W, pump == kPumpTable ? a.T : 0);
     cudaError_t e = (p->variant == MOQ_DSB) ? launch_variant<MOQ_DSB>(a, dmax, noise, pump, grid, block, smem, as_stream(stream))
                                             : launch_variant<MOQ_BSB>(a, dmax, noise, pump, grid, block, smem, as_stream(stream));
