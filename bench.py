@@ -207,7 +207,7 @@ def gpu_arm(args, rank, world):
     lam_all = torch.from_numpy(np.stack([wl.dirichlet_lambdas(R * world, K, 10_000 + s)[first:first + R]
                                          for s in range(nsteps)])).to(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 126 MB L2
-    launches_per_step = 1 + 1 + 12 + 4  # sample, cuts, Pareto merge (12: dedup path), hypervolume (4)
+    launches_per_step = 1 + 1 + 12 + 5  # sample, cuts, Pareto merge (12: dedup path), hypervolume (5 for K = 4)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
     fronts, hvs = [], []

@@ -250,7 +250,7 @@ int moq_hypervolume_points(const int64_t* pts, int64_t F, int32_t K, const int64
  * code whose device memory is owned by another allocator, or loops where a cudaMalloc
  * or cudaFree would stall the whole device). The scratch is a fixed array in the
  * library's own device memory, sized for moq_hypervolume_noalloc_max_points() points
- * (16384) of up to 4 objectives, about 0.77 MB on every GPU that loads the library,
+ * (16384) of up to 4 objectives, about 1.4 MB on every GPU that loads the library,
  * held until the process exits. The call allocates nothing; the caller still owns pts,
  * ref and out. The first call on a device looks up that device's address of the array
  * (make it before any stream capture). Every call shares the one array and leaves its

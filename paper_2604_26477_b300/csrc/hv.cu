@@ -31,6 +31,10 @@ struct HvWs {
     int32_t* rank;   // K x F, -1 for left-out points
     int32_t* order;  // K x F, order[d*F + rank] = point
     i128* partial;   // one per block of the slab kernels
+    // K = 4: the points laid out in y_0 order (y_0, y_1, rank_2, rank_3) and in y_2 order
+    // (y_2, rank_2, rank_3), so the slab kernels read them contiguously
+    int64_t *o0_y0, *o0_y1, *o2_y2;
+    int32_t *o0_r2, *o0_r3, *o2_r2, *o2_r3;
     int32_t* fv;     // number of points kept
     i128* result;
     int32_t* flags;
@@ -49,6 +53,14 @@ __host__ __device__ inline HvWs carve(void* base, int64_t F, int K)
     p += al256(sizeof(int32_t) * (size_t)K * F);
     w.partial = reinterpret_cast<i128*>(p);
     p += al256(sizeof(i128) * (size_t)F);
+    w.o0_y0 = reinterpret_cast<int64_t*>(p);
+    w.o0_y1 = w.o0_y0 + F;
+    w.o2_y2 = w.o0_y1 + F;
+    w.o0_r2 = reinterpret_cast<int32_t*>(w.o2_y2 + F);
+    w.o0_r3 = w.o0_r2 + F;
+    w.o2_r2 = w.o0_r3 + F;
+    w.o2_r3 = w.o2_r2 + F;
+    p += al256(40 * (size_t)F);
     w.fv = reinterpret_cast<int32_t*>(p);
     w.result = reinterpret_cast<i128*>(p + 16);
     w.flags = reinterpret_cast<int32_t*>(p + 32);
@@ -259,6 +271,21 @@ __device__ __forceinline__ int block_excl_scan_int(int v, int* warp_sums, int* t
     return res;
 }
 
+// The K = 4 point data in y_0 order and in y_2 order (positions past the kept count unused).
+__global__ void __launch_bounds__(kThreads) k_hv_permute4(const int64_t* __restrict__ pts, int64_t F, HvWs ws)
+{
+    const int64_t q = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+    if (q >= *ws.fv) return;
+    const int32_t p0 = ws.order[q], p2 = ws.order[2 * F + q];
+    ws.o0_y0[q] = pts[(int64_t)p0 * 4];
+    ws.o0_y1[q] = pts[(int64_t)p0 * 4 + 1];
+    ws.o0_r2[q] = ws.rank[2 * F + p0];
+    ws.o0_r3[q] = ws.rank[3 * F + p0];
+    ws.o2_y2[q] = pts[(int64_t)p2 * 4 + 2];
+    ws.o2_r2[q] = ws.rank[2 * F + p2];
+    ws.o2_r3[q] = ws.rank[3 * F + p2];
+}
+
 // K = 4 with the slab's points compacted: block b takes slab t = F-1-b (the largest slabs
 // first, so the long blocks start in the first wave) and gathers the t+1 points of
 // rank_3 <= t into shared memory twice -- in y_0 order (the staircase walk) and in y_2
@@ -280,11 +307,7 @@ __global__ void __launch_bounds__(kThreads) k_hv4_compact(const int64_t* __restr
     __shared__ int warp_sums[kThreads / 32];
     const int Fv = *ws.fv;
     const int64_t t = F - 1 - (int64_t)blockIdx.x;
-    const int32_t* ord0 = ws.order;
-    const int32_t* ord2 = ws.order + 2 * F;
     const int32_t* ord3 = ws.order + 3 * F;
-    const int32_t* rank2 = ws.rank + 2 * F;
-    const int32_t* rank3 = ws.rank + 3 * F;
     int64_t h4 = 0;
     if (t < Fv) {
         const int64_t top = pts[(int64_t)ord3[t] * 4 + 3];
@@ -295,25 +318,51 @@ __global__ void __launch_bounds__(kThreads) k_hv4_compact(const int64_t* __restr
         if (threadIdx.x == 0) ws.partial[t] = 0;
         return;
     }
-    int cnt0 = 0, cnt2 = 0;
-    for (int base = 0; base < Fv; base += kThreads) {
-        const int q = base + threadIdx.x;
-        const int p0 = q < Fv ? ord0[q] : 0, p2 = q < Fv ? ord2[q] : 0;
-        const int f0 = (q < Fv && rank3[p0] <= t) ? 1 : 0, f2 = (q < Fv && rank3[p2] <= t) ? 1 : 0;
-        int tot0, tot2;
-        const int pos0 = cnt0 + block_excl_scan_int(f0, warp_sums, &tot0);
-        const int pos2 = cnt2 + block_excl_scan_int(f2, warp_sums, &tot2);
+    // gather the points of rank_3 <= t in both orders: warp w owns a contiguous segment of
+    // positions; it counts its kept points (ballots), the segment offsets come from the
+    // eight counts, then it writes its points in order -- reads are contiguous and only two
+    // barriers are needed
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int kWarps = kThreads / 32;
+    const int seg = ((Fv + kWarps - 1) / kWarps + 31) & ~31;
+    const int lo = wid * seg, hi = min(Fv, lo + seg);
+    __shared__ int wc0[kWarps], wc2[kWarps];
+    int n0 = 0, n2 = 0;
+    for (int q = lo + lane; q < lo + seg; q += 32) {
+        const bool f0 = q < hi && ws.o0_r3[q] <= t, f2 = q < hi && ws.o2_r3[q] <= t;
+        n0 += __popc(__ballot_sync(0xffffffffu, f0));
+        n2 += __popc(__ballot_sync(0xffffffffu, f2));
+    }
+    if (lane == 0) {
+        wc0[wid] = n0;
+        wc2[wid] = n2;
+    }
+    __syncthreads();
+    int pos0 = 0, pos2 = 0, cnt0 = 0;
+    for (int w = 0; w < kWarps; ++w) {
+        if (w < wid) {
+            pos0 += wc0[w];
+            pos2 += wc2[w];
+        }
+        cnt0 += wc0[w];
+    }
+    const unsigned below = (1u << lane) - 1u;
+    for (int q = lo + lane; q < lo + seg; q += 32) {
+        const bool f0 = q < hi && ws.o0_r3[q] <= t, f2 = q < hi && ws.o2_r3[q] <= t;
+        const unsigned b0 = __ballot_sync(0xffffffffu, f0), b2 = __ballot_sync(0xffffffffu, f2);
         if (f0) {
-            s_u0[pos0] = pts[(int64_t)p0 * 4];
-            s_u1[pos0] = pts[(int64_t)p0 * 4 + 1];
-            s_r2[pos0] = rank2[p0];
+            const int at = pos0 + __popc(b0 & below);
+            s_u0[at] = ws.o0_y0[q];
+            s_u1[at] = ws.o0_y1[q];
+            s_r2[at] = ws.o0_r2[q];
         }
         if (f2) {
-            s_v2[pos2] = pts[(int64_t)p2 * 4 + 2];
-            s_q2[pos2] = rank2[p2];
+            const int at = pos2 + __popc(b2 & below);
+            s_v2[at] = ws.o2_y2[q];
+            s_q2[at] = ws.o2_r2[q];
         }
-        cnt0 += tot0;
-        cnt2 += tot2;
+        pos0 += __popc(b0);
+        pos2 += __popc(b2);
     }
     __syncthreads();
     const int c = cnt0;  // == t + 1
@@ -549,7 +598,7 @@ int64_t moq_hypervolume_workspace_size(int64_t F, int32_t K)
     using namespace moq;
     if (F < 1) F = 1;
     if (K < 1) K = 1;
-    return (int64_t)(al256(sizeof(int32_t) * (size_t)K * F) * 2 + al256(16 * (size_t)F) + 256);
+    return (int64_t)(al256(sizeof(int32_t) * (size_t)K * F) * 2 + al256(16 * (size_t)F) + al256(40 * (size_t)F) + 256);
 }
 
 int moq_hypervolume_points(const int64_t* pts, int64_t F, int32_t K, const int64_t* ref, void* workspace, moq_hv* out,
@@ -590,6 +639,7 @@ int moq_hypervolume_points(const int64_t* pts, int64_t F, int32_t K, const int64
     default:
         k_hv_rank_count<4><<<gRank, kRankTile, 0, st>>>(pts, F, r, ws);
         k_hv_rank_order<4><<<gF, kThreads, 0, st>>>(pts, F, r, ws);
+        k_hv_permute4<<<gF, kThreads, 0, st>>>(pts, F, ws);
         if (F <= kHv4CompactMax) {
             const size_t smem = (size_t)32 * F;
             MOQ_CUDA_TRY(cudaFuncSetAttribute(k_hv4_compact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -642,8 +692,8 @@ namespace {
 constexpr int64_t kNoAllocMaxPoints = 16384;
 constexpr size_t round256(size_t v) { return (v + 255) / 256 * 256; }
 // the workspace layout of moq_hypervolume_points for kNoAllocMaxPoints points, K = 4
-constexpr size_t kNoAllocBytes =
-    2 * round256(sizeof(int32_t) * 4 * kNoAllocMaxPoints) + round256(16 * kNoAllocMaxPoints) + 256;
+constexpr size_t kNoAllocBytes = 2 * round256(sizeof(int32_t) * 4 * kNoAllocMaxPoints) + round256(16 * kNoAllocMaxPoints) +
+                                 round256(40 * kNoAllocMaxPoints) + 256;
 
 static __device__ __align__(256) unsigned char g_hv_noalloc_scratch[kNoAllocBytes];
 
