@@ -170,7 +170,9 @@ int moq_evaluate_cuts_batch(const moq_batch* b, const uint64_t* bits_all, int64_
  * ceil(max_replicas/128)*128 x n_pad). K <= 4, n <= 16384. The instance must outlive it.
  * moq_sample_dense runs T step kernels (tcgen05.mma BF16 -> FP32 products for every
  * objective, fused update/wall/phi epilogue) on `stream`, then writes the packed signs
- * (and x_out/y_out if given). Differences from moq_sample: phi is rounded to BF16 for the
+ * (and x_out/y_out if given); with n_pad = 128 and K <= 3 one launch runs all T steps with
+ * J, phi and the state held on chip (same results; MOQ_DENSE_RESIDENT=0 at create time keeps
+ * the per-step kernels). Differences from moq_sample: phi is rounded to BF16 for the
  * products (exact for dSB), the force is combined as -c0 sum_k c_k G_k, and the noise of
  * step m for replica r is Gaussian number r & 7 of Philox(key = seed, counter = (m, i,
  * 2^30 + (r >> 3), round)) (word (r & 7) >> 1, Box-Muller on 16-bit halves as in

@@ -52,6 +52,8 @@ struct moq_dense {
     int32_t max_abs_weight = 0;
     CUtensorMap tm_J;                            // K x n_pad x n_pad, box 64 x (128 / CL) x 1
     CUtensorMap tm_Jhi, tm_Jlo;                  // the two halves, box 64 x 128 x 1
+    CUtensorMap tm_J128;                         // J with box 64 x 128 x 1 (the resident kernel)
+    bool resident = false;                       // all steps in one launch (n_pad = 128, K <= 3)
     CUtensorMap tm_phi[2];                       // R_pad x n_pad, box 64 x 128
     int32_t cluster = 1;                         // CTAs per cluster sharing J tiles
     int32_t* status = nullptr;                   // device error flags
@@ -378,6 +380,220 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
+// ---- the whole trajectory in one CTA: dense graphs of at most 128 spins ----------------
+// With n_pad = 128 a CTA holds everything a block of 128 replicas needs for all T steps:
+// J^(k) (K x 128 x 128 BF16) and the phi tile (128 replicas x 128 spins BF16) in shared
+// memory in the operand layout, y in shared memory, x in the TMEM columns the K
+// accumulators leave free (384..511 for K <= 3). Every step is: one thread issues the K
+// products into TMEM, the 16 warps read G_k and x from TMEM, update x, y, write x back to
+// TMEM and phi into the operand tile, then a block barrier -- no HBM traffic between the
+// first load and the final state. The arithmetic and the noise counters are those of the
+// step kernel, so both give the same bits.
+struct ResidentArgs {
+    float* x;
+    float* y;
+    const float* lambda;  // R x K
+    const float* c0;
+    int32_t n, n_pad, R, K, T;
+    const float* schedule;
+    float a0, a0inv, dt, kappa, dta0;
+    uint32_t key0, key1, round32;
+    int32_t* status;
+};
+
+constexpr int kResidentStateCol = 384;  // first TMEM column of x
+
+__host__ __device__ constexpr size_t resident_smem_bytes(int K)
+{
+    return 1024 + (size_t)K * 2 * kTileBytes + 2 * kTileBytes + sizeof(float) * kTileM * kTileN + sizeof(float) * kTileN * (K + 1) + 64;
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+        "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+        "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+
+// byte offset of element (row r, column j) in a 128-row x 128-column BF16 operand tile stored
+// as two 64-column chunks in the 128-byte-swizzled K-major layout
+__device__ __forceinline__ uint32_t sw128_offset(int r, int j)
+{
+    const int c = j >> 6, jj = j & 63;
+    return (uint32_t)(c * kTileBytes + (r >> 3) * 1024 + (r & 7) * 128 + (((jj >> 3) ^ (r & 7)) << 4) + (jj & 7) * 2);
+}
+
+template <int VARIANT, int KOBJ, bool NOISE>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_dense_resident(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmPhi, const ResidentArgs a)
+{
+    static_assert(KOBJ * kTileN <= kResidentStateCol, "x needs the TMEM columns after the accumulators");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char* gbase = smem_raw + (base - raw);
+    const uint32_t sJ = base, sPhi = base + KOBJ * 2 * kTileBytes;
+    unsigned char* phi_tile = gbase + KOBJ * 2 * kTileBytes;
+    float* y_s = reinterpret_cast<float*>(gbase + (KOBJ + 1) * 2 * kTileBytes);  // [replica][spin]
+    float* lam_s = y_s + kTileM * kTileN;                                          // kTileN x KOBJ
+    float* c0_s = lam_s + kTileN * KOBJ;                                           // kTileN
+    uint64_t* bars = reinterpret_cast<uint64_t*>(c0_s + kTileN);                   // load, mma (8-aligned)
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r0 = blockIdx.x * kTileN;
+    const int quarter = warp & 3, part = warp >> 2;
+    const int i = quarter * 32 + lane;  // spin (n_pad = 128)
+    const int np = a.n_pad;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)), "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars[0])), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars[1])), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    for (int q = tid; q < kTileN; q += kThreads) {
+        const int r = r0 + q;
+        c0_s[q] = r < a.R ? a.c0[r] : 0.0f;
+#pragma unroll
+        for (int k = 0; k < KOBJ; ++k) lam_s[q * KOBJ + k] = r < a.R ? a.lambda[(int64_t)r * KOBJ + k] : 0.0f;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
+
+    // operands (J^(k) and the start phi) by TMA, state (x into TMEM, y into shared memory)
+    if (tid == 0) {
+        const uint32_t lb = smem_u32(&bars[0]);
+        mbar_expect_tx(lb, (uint32_t)((KOBJ + 1) * 2 * kTileBytes));
+#pragma unroll
+        for (int k = 0; k < KOBJ; ++k)
+            for (int c = 0; c < 2; ++c) tma_load_3d(sJ + (k * 2 + c) * kTileBytes, &tmJ, c * kChunkK, 0, k, lb);
+        for (int c = 0; c < 2; ++c) tma_load_2d(sPhi + c * kTileBytes, &tmPhi, c * kChunkK, r0, lb);
+    }
+    __syncwarp();  // warp 0 converges before the warp-wide TMEM stores
+#pragma unroll 1
+    for (int cc = 0; cc < 2; ++cc) {
+        const int col0 = part * 32 + cc * 16;
+        float xs[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int64_t at = (int64_t)(r0 + col0 + q) * np + i;
+            xs[q] = a.x[at];
+            y_s[(col0 + q) * kTileM + i] = a.y[at];
+        }
+        tmem_st16(lane_addr + kResidentStateCol + col0, xs);
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    bool ok = mbar_wait(smem_u32(&bars[0]), 0u);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    ok = __syncthreads_and(ok);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+
+#pragma unroll 1
+    for (int m = 0; m < a.T && ok; ++m) {
+        if (tid == 0) {
+#pragma unroll
+            for (int k = 0; k < KOBJ; ++k)
+#pragma unroll
+                for (int c = 0; c < 2; ++c)
+#pragma unroll
+                    for (int ks = 0; ks < kChunkK / 16; ++ks)
+                        mma_bf16(tmem + k * kTileN, sw128_desc(sJ + (k * 2 + c) * kTileBytes + ks * 32),
+                                 sw128_desc(sPhi + c * kTileBytes + ks * 32), (c > 0 || ks > 0) ? 1u : 0u);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&bars[1]))
+                         : "memory");
+        }
+        // warp-uniform outcome: the TMEM loads and stores below are warp-wide
+        const bool step_ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&bars[1]), (uint32_t)(m & 1)));
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const float cm = a.schedule ? (__ldg(a.schedule + m) - a.a0) : fmaf(a.a0inv, (float)m, -a.a0);
+        if (step_ok) {
+#pragma unroll 1
+            for (int cc = 0; cc < 2; ++cc) {
+                const int col0 = part * 32 + cc * 16;
+                float g[KOBJ][16], xs[16];
+#pragma unroll
+                for (int k = 0; k < KOBJ; ++k) tmem_ld16(lane_addr + k * kTileN + col0, g[k]);
+                tmem_ld16(lane_addr + kResidentStateCol + col0, xs);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                float eta[16];
+#pragma unroll
+                for (int q8 = 0; q8 < 2; ++q8) {
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) eta[8 * q8 + t] = 0.0f;
+                    if (NOISE) {
+                        const uint32_t octet = (uint32_t)((r0 + col0) >> 3) + q8;
+                        const uint4 o = Philox4x32::block(make_uint4((uint32_t)m, (uint32_t)i, 0x40000000u + octet, a.round32),
+                                                          a.key0, a.key1);
+#pragma unroll
+                        for (int w = 0; w < 4; ++w) {
+                            const float2 p = box_muller16(word_of(o, w));
+                            eta[8 * q8 + 2 * w] = p.x;
+                            eta[8 * q8 + 2 * w + 1] = p.y;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int rl = col0 + q, r = r0 + rl;
+                    if (i < a.n && r < a.R) {
+                        float f = 0.0f;
+#pragma unroll
+                        for (int k = 0; k < KOBJ; ++k) f = fmaf(lam_s[rl * KOBJ + k], g[k][q], f);
+                        f *= -c0_s[rl];  // the force acts on the negated coupling
+                        float xv = xs[q], yv = y_s[rl * kTileM + i];
+                        sb_update<NOISE>(f, cm, eta[q], a.dt, a.kappa, a.dta0, xv, yv);
+                        xs[q] = xv;
+                        y_s[rl * kTileM + i] = yv;
+                        *reinterpret_cast<__nv_bfloat16*>(phi_tile + sw128_offset(rl, i)) =
+                            __float2bfloat16_rn(phi_of<VARIANT>(xv));
+                    }
+                }
+                tmem_st16(lane_addr + kResidentStateCol + col0, xs);
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        }
+        // phi written through the generic proxy is read by the next products (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        ok = __syncthreads_and(step_ok);
+        asm volatile("tcgen05.fence::after_thread_sync;");
+    }
+    if (ok) {  // the final state back to HBM for the readout
+#pragma unroll 1
+        for (int cc = 0; cc < 2; ++cc) {
+            const int col0 = part * 32 + cc * 16;
+            float xs[16];
+            tmem_ld16(lane_addr + kResidentStateCol + col0, xs);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int r = r0 + col0 + q;
+                if (r < a.R) {
+                    const int64_t at = (int64_t)r * np + i;
+                    a.x[at] = xs[q];
+                    a.y[at] = y_s[(col0 + q) * kTileM + i];
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicOr(a.status, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
 // ---- exact cut values on the tensor cores (Eq. single_obj) ----------------------------
 // For a configuration s (+-1 per spin) and a symmetric J_k with zero diagonal,
 // s^T J_k s = 2 sum_E J_e s_i s_j, so C_k(s) = 1/2 sum_E J_e (1 - s_i s_j) = (2 W_k - s^T J_k s) / 4.
@@ -630,6 +846,23 @@ cudaError_t launch_step_cl(const moq_dense* d, const CUtensorMap& tm_phi, const 
     }
 }
 
+template <int VARIANT, int KOBJ, bool NOISE>
+cudaError_t launch_resident(const moq_dense* d, const ResidentArgs& a, int tiles, cudaStream_t st)
+{
+    auto k = k_dense_resident<VARIANT, KOBJ, NOISE>;
+    const size_t smem = resident_smem_bytes(KOBJ);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<tiles, kThreads, smem, st>>>(d->tm_J128, d->tm_phi[0], a);
+    return cudaGetLastError();
+}
+
+template <int VARIANT, bool NOISE>
+cudaError_t launch_resident_k(const moq_dense* d, const ResidentArgs& a, int tiles, cudaStream_t st)
+{
+    return a.K == 2 ? launch_resident<VARIANT, 2, NOISE>(d, a, tiles, st) : launch_resident<VARIANT, 3, NOISE>(d, a, tiles, st);
+}
+
 // Tensor maps of the J tiles (3-D: j, i, objective) and of the two Phi buffers (2-D: j, r),
 // BF16, 128-byte swizzle (the layout of the MMA operands), built once per handle.
 int encode_maps(moq_dense* d)
@@ -648,6 +881,10 @@ int encode_maps(moq_dense* d)
         CUresult r = encode(&d->tm_J, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, d->J, dims, strides, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
                             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(MOQ_ERR_CUDA, "cuTensorMapEncodeTiled(J) failed: %d", (int)r);
+        const cuuint32_t box128[3] = {(cuuint32_t)kChunkK, (cuuint32_t)kTileM, 1};
+        r = encode(&d->tm_J128, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, d->J, dims, strides, box128, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(MOQ_ERR_CUDA, "cuTensorMapEncodeTiled(J full tile) failed: %d", (int)r);
     }
     for (int h = 0; h < 2; ++h) {
         const cuuint64_t dims[3] = {np, np, (cuuint64_t)d->K};
@@ -716,6 +953,11 @@ int moq_dense_create(const moq_instance* inst, int32_t max_replicas, moq_dense**
         const int v = atoi(env);
         d->cluster = (v == 2 || v == 4) ? v : 1;
     }
+    // graphs of at most 128 spins with K <= 3 run all steps in one launch from shared
+    // memory and TMEM (MOQ_DENSE_RESIDENT=0 keeps the per-step kernel)
+    d->resident = d->n_pad == kTileM && (d->K == 2 || d->K == 3);
+    if (const char* env = getenv("MOQ_DENSE_RESIDENT"))
+        if (atoi(env) == 0) d->resident = false;
     const size_t cells = (size_t)d->R_pad * d->n_pad;
     const size_t jbytes = sizeof(__nv_bfloat16) * (size_t)d->K * d->n_pad * d->n_pad;
     cudaError_t e = cudaMalloc((void**)&d->J, jbytes);
@@ -802,6 +1044,39 @@ int moq_sample_dense(moq_dense* d, const float* lambda, int32_t R, const moq_sam
     const float a0inv = p->steps > 1 ? p->a0 / (float)(p->steps - 1) : 0.0f;
     const dim3 grid(np / kTileM, Rp / kTileN);
     const bool noise = p->alpha != 0.0f;
+    if (d->resident && p->steps > 0) {
+        // one launch runs every step (n_pad = 128, K <= 3): same arithmetic, same bits
+        ResidentArgs ra{};
+        ra.x = d->x;
+        ra.y = d->y;
+        ra.lambda = lambda;
+        ra.c0 = d->c0;
+        ra.n = d->n;
+        ra.n_pad = np;
+        ra.R = R;
+        ra.K = d->K;
+        ra.T = p->steps;
+        ra.schedule = p->schedule;
+        ra.a0 = a.a0;
+        ra.a0inv = a0inv;
+        ra.dt = a.dt;
+        ra.kappa = a.kappa;
+        ra.dta0 = a.dta0;
+        ra.key0 = key0;
+        ra.key1 = key1;
+        ra.round32 = rnd;
+        ra.status = d->status;
+        const int tiles = (int)ceil_div(R, kTileN);
+        cudaError_t e;
+        if (p->variant == MOQ_DSB)
+            e = noise ? launch_resident_k<MOQ_DSB, true>(d, ra, tiles, st) : launch_resident_k<MOQ_DSB, false>(d, ra, tiles, st);
+        else
+            e = noise ? launch_resident_k<MOQ_BSB, true>(d, ra, tiles, st) : launch_resident_k<MOQ_BSB, false>(d, ra, tiles, st);
+        if (e != cudaSuccess) return cuda_fail(e, "moq_sample_dense resident launch");
+        k_dense_readout<<<R, 128, 0, st>>>(d->n, np, R, h->words, d->x, d->y, bits, p->x_out, p->y_out);
+        MOQ_LAUNCH_CHECK("moq_sample_dense readout");
+        return MOQ_OK;
+    }
     for (int m = 0; m < p->steps; ++m) {
         a.m = m;
         a.cm = fmaf(a0inv, (float)m, -p->a0);

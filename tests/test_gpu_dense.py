@@ -180,6 +180,38 @@ def test_dense_cluster_sizes_agree_bitwise(M, P, variant, monkeypatch):
 
 
 
+@pytest.mark.parametrize("n,R,K,variant,alpha,sched", [(25, 300, 3, "dsb", 0.1, False), (128, 129, 2, "bsb", 0.1, False),
+                                                      (100, 1, 3, "bsb", 0.0, True), (70, 640, 2, "dsb", 0.0, False),
+                                                      (128, 256, 3, "dsb", 0.2, True)])
+def test_dense_resident_matches_step_kernel(M, P, monkeypatch, n, R, K, variant, alpha, sched):
+    # graphs of at most 128 spins run all steps in one launch from shared memory and TMEM;
+    # the per-step kernel (MOQ_DENSE_RESIDENT=0) does the same arithmetic, so bits, x and y
+    # agree bit for bit (ragged and single replica tiles, both variants, with and without
+    # noise and an explicit pump schedule)
+    src = wl.random_graph(n, 1.0, 40 + n + R, K=K, wmax=200)
+    inst = P.Instance(src)
+    T = 60
+    lam = _dev(wl.dirichlet_lambdas(R, K, 3))
+    schedule = torch.linspace(0.0, 1.0, T, device="cuda") ** 2 if sched else None
+    out = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("MOQ_DENSE_RESIDENT", mode)
+        d = M.moq_dense_create(inst.handle, R)
+        try:
+            xo = torch.zeros((R, n), device="cuda")
+            yo = torch.zeros((R, n), device="cuda")
+            bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+            p = M.moq_default_params(variant=variant, steps=T, dt=0.5, alpha=alpha, schedule=schedule, x_out=xo, y_out=yo)
+            M.moq_sample_dense(d, lam, R, p, 11, 2, bits)
+            M.moq_dense_status(d)
+            out[mode] = (bits.cpu(), xo.cpu(), yo.cpu())
+        finally:
+            M.moq_dense_destroy(d)
+    for a, b in zip(out["1"], out["0"]):
+        assert torch.equal(a, b)
+    assert len(torch.unique(out["1"][0], dim=0)) > 1 or R == 1
+
+
 @pytest.mark.parametrize("n,Mn,K,wmax", [(150, 300, 3, 50), (257, 129, 2, 60000), (128, 700, 4, 5000), (90, 1, 3, 128),
                                          (100, 40, 3, 127)])
 def test_dense_cuts_bit_exact(M, P, oracle, n, Mn, K, wmax):
