@@ -477,7 +477,7 @@ def dense_arm(args, rank, world):
                                    f"lambda, bsb T={T} dt=0.5 alpha=0.1; tcgen05 BF16 products, FP32 accumulate; "
                                    "exact cuts + Pareto + hypervolume per step",
                        "n": n, "R": R, "T": T},
-            "roofline": {"bound": "tensor", "kernel": "k_dense_step (all T launches)", "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "tensor", "kernel": "k_dense_step_ws (all T launches)", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": profile_traffic("sb_dense.cu", "dense_step_n2000_K3_R8192.txt")
                          if (n, R) == (2000, 8192) else None,

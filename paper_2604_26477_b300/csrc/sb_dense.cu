@@ -56,6 +56,7 @@ struct moq_dense {
     bool resident = false;                       // all steps in one launch (n_pad = 128, K <= 3)
     CUtensorMap tm_phi[2];                       // R_pad x n_pad, box 64 x 128
     int32_t cluster = 1;                         // CTAs per cluster sharing J tiles
+    int32_t sms = 148;                           // persistent step kernel: one CTA per SM
     int32_t* status = nullptr;                   // device error flags
     int32_t* h_status = nullptr;                 // pinned
 };
@@ -162,6 +163,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
         : "memory");
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(u[q]);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
+{
+    uint32_t u[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7])
+                 : "r"(taddr)
+                 : "memory");
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(u[q]);
 }
 
 struct DenseStepArgs {
@@ -379,6 +391,238 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (CL > 1) cluster_sync();  // no CTA leaves while a peer may still write to it
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
+
+// ---- one step, persistent and warp-specialised (single-CTA clusters) -----------------
+// One CTA per SM walks the tiles b, b + G, ...; warp 0 is the TMA producer, warp 1 issues
+// the MMAs, warps 2..17 run the epilogue. The epilogue reads the K accumulators of a tile,
+// combines them into the force (32 values per thread, in registers) and releases TMEM at
+// once, so the products of the next tile run on the tensor cores while the same warps
+// stream the state update (x, y in, x, y, phi out) through HBM. The force, update and noise
+// are those of k_dense_step, so both give the same bits.
+constexpr int kWsEpiWarps = 16;
+constexpr int kWsThreads = 32 * (2 + kWsEpiWarps);
+
+template <int VARIANT, int KOBJ, bool NOISE>
+__global__ void __launch_bounds__(kWsThreads, 1)
+    k_dense_step_ws(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmPhi, const DenseStepArgs a,
+                    int32_t n_ib, int32_t n_tiles)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char* gbase = smem_raw + (base - raw);
+    constexpr int kStageBytes = (KOBJ + 1) * kTileBytes;
+    constexpr int S = dense_stages(KOBJ);
+    uint64_t* full = reinterpret_cast<uint64_t*>(gbase + S * kStageBytes);  // S
+    uint64_t* empty = full + S;                                             // S
+    uint64_t* tfull = empty + S;     // products of a tile complete (MMA -> epilogue)
+    uint64_t* tempty = tfull + 1;    // accumulators read (epilogue -> MMA), one arrival per epilogue warp
+    uint64_t* drained = tempty + 1;  // every issued product complete (teardown)
+    uint64_t* lready = drained + 1;  // 2: lambda / c0 buffer filled, one arrival per epilogue warp
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(lready + 2);
+    float* lam_s = reinterpret_cast<float*>(gbase + S * kStageBytes + 128);  // 2 x kTileN x KOBJ
+    float* c0_s = lam_s + 2 * kTileN * KOBJ;                                 // 2 x kTileN
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int np = a.n_pad, nchunks = np / kChunkK;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)), "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 32) {
+        for (int st = 0; st < S; ++st) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[st])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[st])), "r"(1));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(tfull)), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(tempty)), "r"(kWsEpiWarps));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(drained)), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&lready[0])), "r"(kWsEpiWarps));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&lready[1])), "r"(kWsEpiWarps));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmJ)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmPhi)) : "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tmem_slot;
+    bool ok = true;
+
+    if (warp == 0) {
+        if (lane == 0) {  // producer
+            int gc = 0;
+            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+                const int i0 = (t % n_ib) * kTileM, r0 = (t / n_ib) * kTileN;
+                for (int c = 0; c < nchunks; ++c, ++gc) {
+                    const int st = gc % S;
+                    if (gc >= S && !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((gc - S) / S) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t stage = base + st * kStageBytes, fb = smem_u32(&full[st]);
+                    mbar_expect_tx(fb, (uint32_t)kStageBytes);
+                    const int j0 = c * kChunkK;
+#pragma unroll
+                    for (int k = 0; k < KOBJ; ++k) tma_load_3d(stage + k * kTileBytes, &tmJ, j0, i0, k, fb);
+                    tma_load_2d(stage + KOBJ * kTileBytes, &tmPhi, j0, r0, fb);
+                }
+            }
+            // no copy of this CTA is still in flight when it leaves (gc chunks were issued)
+            for (int st = 0; st < S && st < gc; ++st) {
+                const int c_last = st + ((gc - 1 - st) / S) * S;
+                if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((c_last / S) & 1))) ok = false;
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            int gc = 0, lt = 0;
+            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++lt) {
+                // the epilogue has read the previous tile's accumulators
+                if (lt > 0 && !mbar_wait(smem_u32(tempty), (uint32_t)((lt - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                for (int c = 0; c < nchunks; ++c, ++gc) {
+                    const int st = gc % S;
+                    if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((gc / S) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint32_t stage = base + st * kStageBytes;
+#pragma unroll
+                    for (int k = 0; k < KOBJ; ++k)
+#pragma unroll
+                        for (int ks = 0; ks < kChunkK / 16; ++ks)
+                            mma_bf16(tmem + k * kTileN, sw128_desc(stage + k * kTileBytes + ks * 32),
+                                     sw128_desc(stage + KOBJ * kTileBytes + ks * 32), (c > 0 || ks > 0) ? 1u : 0u);
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     smem_u32(&empty[st]))
+                                 : "memory");
+                }
+                if (!ok) break;
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(tfull))
+                             : "memory");
+            }
+            // teardown: everything issued is complete before TMEM is freed
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(drained))
+                         : "memory");
+            if (!mbar_wait(smem_u32(drained), 0u)) ok = false;
+        }
+        __syncwarp();
+    } else {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4).. (its spins) and columns 32 part..
+        const int quarter = warp & 3, part = (warp - 2) >> 2;
+        const float cm = a.schedule ? (__ldg(a.schedule + a.m) - a.a0) : a.cm;
+        // lambda and c0 of a tile's replicas go to shared memory one tile ahead (buffer lt & 1);
+        // buffer reuse is ordered by the TMEM hand-off: a warp fills buffer b for tile lt + 2
+        // only after the products of tile lt + 1, which wait for every warp to read tile lt
+        const int e = tid - 64;
+        auto stage_lambda = [&](int t, int b) {
+            const int r0 = (t / n_ib) * kTileN;
+            for (int q = e; q < kTileN * (KOBJ + 1); q += 32 * kWsEpiWarps) {
+                const int rl = q / (KOBJ + 1), k = q - rl * (KOBJ + 1), r = r0 + rl;
+                const float v = r < a.R ? (k < KOBJ ? a.lambda[(int64_t)r * KOBJ + k] : a.c0[r]) : 0.0f;
+                if (k < KOBJ) lam_s[b * kTileN * KOBJ + rl * KOBJ + k] = v;
+                else c0_s[b * kTileN + rl] = v;
+            }
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&lready[b])) : "memory");
+        };
+        stage_lambda(blockIdx.x, 0);
+        int lt = 0;
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++lt) {
+            const int i0 = (t % n_ib) * kTileM, r0 = (t / n_ib) * kTileN;
+            const int i = i0 + quarter * 32 + lane;
+            const int b = lt & 1;
+            const bool got = __all_sync(0xffffffffu, mbar_wait(smem_u32(tfull), (uint32_t)(lt & 1)) &&
+                                                         mbar_wait(smem_u32(&lready[b]), (uint32_t)((lt >> 1) & 1)));
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (!got) {
+                ok = false;
+                break;
+            }
+            const float* lam_t = lam_s + b * kTileN * KOBJ;
+            const float* c0_t = c0_s + b * kTileN;
+            // the force of the warp's 32 replica columns, 8 at a time (registers stay under the
+            // limit 18 warps per SM leave)
+            float f[32];
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+                const int col0 = part * 32 + cc * 8;
+                float g[KOBJ][8];
+#pragma unroll
+                for (int k = 0; k < KOBJ; ++k) tmem_ld8(tmem + ((uint32_t)(quarter * 32) << 16) + k * kTileN + col0, g[k]);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int rl = col0 + q;
+                    float v = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < KOBJ; ++k) v = fmaf(lam_t[rl * KOBJ + k], g[k][q], v);
+                    f[cc * 8 + q] = v * -c0_t[rl];  // the force acts on the negated coupling
+                }
+            }
+            // accumulators free: the next tile's products start while the state streams
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tempty)) : "memory");
+            if (t + (int)gridDim.x < n_tiles) stage_lambda(t + gridDim.x, b ^ 1);
+            if (i < a.n) {
+                // one octet of columns per pass; the force of the next octet moves to f[0..7]
+#pragma unroll 1
+                for (int cc = 0; cc < 4; ++cc) {
+                    const int col0 = part * 32 + cc * 8;  // one noise octet
+                    float xs[8], ys[8], eta[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int r = r0 + col0 + q;
+                        const bool v = r < a.R;
+                        xs[q] = v ? a.x[(int64_t)r * np + i] : 0.0f;
+                        ys[q] = v ? a.y[(int64_t)r * np + i] : 0.0f;
+                        eta[q] = 0.0f;
+                    }
+                    if (NOISE) {
+                        const uint32_t octet = (uint32_t)((r0 + col0) >> 3);
+                        const uint4 o =
+                            Philox4x32::block(make_uint4((uint32_t)a.m, (uint32_t)i, 0x40000000u + octet, a.round32), a.key0, a.key1);
+#pragma unroll
+                        for (int w = 0; w < 4; ++w) {
+                            const float2 pr = box_muller16(word_of(o, w));
+                            eta[2 * w] = pr.x;
+                            eta[2 * w + 1] = pr.y;
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int r = r0 + col0 + q;
+                        if (r < a.R) {
+                            const int64_t at = (int64_t)r * np + i;
+                            float xv = xs[q], yv = ys[q];
+                            sb_update<NOISE>(f[q], cm, eta[q], a.dt, a.kappa, a.dta0, xv, yv);
+                            a.x[at] = xv;
+                            a.y[at] = yv;
+                            a.phi_out[at] = __float2bfloat16_rn(phi_of<VARIANT>(xv));
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 24; ++q) f[q] = f[q + 8];
+                }
+            }
+        }
+    }
+    if (!ok) atomicOr(a.status, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+// operand stages, 128 B of barriers (2S + 5) and the TMEM slot, then two lambda / c0 buffers
+size_t ws_smem_bytes(int K) { return 1024 + dense_stages(K) * (size_t)(K + 1) * kTileBytes + 128 + 2 * sizeof(float) * kTileN * (K + 1); }
 
 // ---- the whole trajectory in one CTA: dense graphs of at most 128 spins ----------------
 // With n_pad = 128 a CTA holds everything a block of 128 replicas needs for all T steps:
@@ -807,6 +1051,15 @@ size_t dense_smem_bytes(int K) { return 1024 + dense_stages(K) * (size_t)(K + 1)
 template <int VARIANT, int KOBJ, bool NOISE, int CL>
 cudaError_t launch_step(const moq_dense* d, const CUtensorMap& tm_phi, const DenseStepArgs& a, dim3 grid, cudaStream_t st)
 {
+    if (CL == 1) {  // persistent, warp-specialised form
+        auto k = k_dense_step_ws<VARIANT, KOBJ, NOISE>;
+        const size_t smem = ws_smem_bytes(KOBJ);
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const int n_tiles = (int)(grid.x * grid.y);
+        k<<<std::min(n_tiles, d->sms), kWsThreads, smem, st>>>(d->tm_J, tm_phi, a, (int32_t)grid.x, n_tiles);
+        return cudaGetLastError();
+    }
     auto k = k_dense_step<VARIANT, KOBJ, NOISE, CL>;
     const size_t smem = dense_smem_bytes(KOBJ);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -949,6 +1202,12 @@ int moq_dense_create(const moq_instance* inst, int32_t max_replicas, moq_dense**
     // cluster to each other's pace; at n = 2000, R = 8192 single CTAs measured fastest
     // (204 us per step against 210 and 234), so clusters are opt-in (MOQ_DENSE_CLUSTER)
     d->cluster = 1;
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            sms > 0)
+            d->sms = sms;
+    }
     if (const char* env = getenv("MOQ_DENSE_CLUSTER")) {
         const int v = atoi(env);
         d->cluster = (v == 2 || v == 4) ? v : 1;
