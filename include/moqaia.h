@@ -153,7 +153,9 @@ int moq_batch_layout(const moq_batch* b, int64_t* replica_offsets, int64_t* word
  * slots_per_thread >= the largest n; *items_out (may be NULL) = work items. (0, 0) selects
  * per-instance mode: moq_sample_batch then launches the single-instance sampler once per
  * instance (largest first, replica counters from the instance's offset), whose blocks are
- * sized per instance; the samples are the same bits either way. Synchronous. */
+ * sized per instance, round-robin over internal streams (MOQ_BATCH_STREAMS, default 4,
+ * created by the first such call) that fork from and join back into the caller's stream;
+ * the samples are the same bits either way. Synchronous. */
 int moq_batch_set_tiles(moq_batch* b, int32_t block_threads, int32_t slots_per_thread, int32_t* items_out);
 /* Samples every replica of every instance (asynchronous; p's state arrays must be NULL). */
 int moq_sample_batch(moq_batch* b, const float* lambda_all, const moq_sample_params* p, uint64_t seed, uint64_t round,
@@ -300,6 +302,10 @@ int moq_mlp_forward(const moq_mlp* m, const float* X, int32_t B, float* Y, void*
 int moq_mlp_gradient(moq_mlp* m, const float* X, const float* T, int32_t B, float* grad_out, float* loss_out, void* stream);
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with the last gradient. */
 int moq_mlp_adam_step(moq_mlp* m, float lr, void* stream);
+/* moq_mlp_gradient followed by moq_mlp_adam_step in two launches instead of three (the
+ * gradient sum and the update share one pass): the same parameters bit for bit. loss_out
+ * (device, 1 float) may be NULL. Asynchronous; errors: MOQ_ERR_ARG. */
+int moq_mlp_train_step(moq_mlp* m, const float* X, const float* T, int32_t B, float lr, float* loss_out, void* stream);
 /* Training rows from M samples (device): X[m] = [lambda[m] (K), features (host, n_features)],
  * T[m][k] = (cuts[m][k] - offset[k]) / scale[k] (host offset, scale: K int64; the learned
  * proposal uses the reference point and sum |J^(k)|, so targets lie in [0, 1]). X: M x

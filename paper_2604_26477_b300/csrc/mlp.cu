@@ -60,8 +60,8 @@ struct MlpSmem {
     float* W3;  // kMaxOut x kLd
     float* b3;
     float* x;   // kRows x (kMaxIn + 1)
-    float* a1;  // kRows x kLd (pre-activation 1)
-    float* a2;  // kRows x kLd (pre-activation 2)
+    float* a1;  // kRows x kLd (activation 1, relu applied)
+    float* a2;  // kRows x kLd (activation 2, relu applied)
     float* d1;  // kRows x kLd
     float* d2;  // kRows x kLd
     float* dy;  // kRows x kMaxOut
@@ -91,19 +91,70 @@ __device__ MlpSmem carve_mlp(float* s)
     return m;
 }
 
+// BF16 weights -> FP32 shared memory, eight values per 16-byte load (every block of the
+// flat vector starts on a 16-byte boundary: its offsets are multiples of 128 elements),
+// all loads of a thread issued before the first store
+__device__ __forceinline__ void unpack8(const uint4& u, float (&v)[8])
+{
+    const uint32_t wd[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        v[2 * e] = __uint_as_float(wd[e] << 16);
+        v[2 * e + 1] = __uint_as_float(wd[e] & 0xFFFF0000u);
+    }
+}
+
 __device__ void load_weights(const __nv_bfloat16* __restrict__ w, const MlpShape& sh, MlpSmem& m)
 {
-    for (int q = threadIdx.x; q < kH * sh.din; q += blockDim.x) m.W1[(q / sh.din) * (kMaxIn + 1) + q % sh.din] = __bfloat162float(w[sh.oW1 + q]);
-    for (int q = threadIdx.x; q < kH * kH; q += blockDim.x) m.W2[(q / kH) * kLd + q % kH] = __bfloat162float(w[sh.oW2 + q]);
-    for (int q = threadIdx.x; q < sh.dout * kH; q += blockDim.x) m.W3[(q / kH) * kLd + q % kH] = __bfloat162float(w[sh.oW3 + q]);
-    for (int q = threadIdx.x; q < kH; q += blockDim.x) {
-        m.b1[q] = __bfloat162float(w[sh.ob1 + q]);
-        m.b2[q] = __bfloat162float(w[sh.ob2 + q]);
+    const uint4* w4 = reinterpret_cast<const uint4*>(w);
+    constexpr int kW2Vec = kH * kH / 8;
+    uint4 u2[kW2Vec / kThreads];
+#pragma unroll
+    for (int t = 0; t < kW2Vec / kThreads; ++t) u2[t] = __ldg(w4 + (sh.oW2 >> 3) + threadIdx.x + t * kThreads);
+    const int n1 = kH * sh.din / 8, n3 = sh.dout * kH / 8;  // <= 256, <= 128 vectors
+    uint4 u1 = make_uint4(0, 0, 0, 0), u3 = u1, ub = u1;
+    if ((int)threadIdx.x < n1) u1 = __ldg(w4 + (sh.oW1 >> 3) + threadIdx.x);
+    if ((int)threadIdx.x < n3) u3 = __ldg(w4 + (sh.oW3 >> 3) + threadIdx.x);
+    if (threadIdx.x < 32) ub = __ldg(w4 + ((threadIdx.x < 16 ? sh.ob1 : sh.ob2 - 128) >> 3) + threadIdx.x);
+#pragma unroll
+    for (int t = 0; t < kW2Vec / kThreads; ++t) {
+        const int q = (threadIdx.x + t * kThreads) * 8;
+        float v[8];
+        unpack8(u2[t], v);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) m.W2[(q >> 7) * kLd + (q & 127) + e] = v[e];
+    }
+    float v[8];
+    if ((int)threadIdx.x < n1) {
+        unpack8(u1, v);
+        for (int e = 0; e < 8; ++e) {
+            const int q = threadIdx.x * 8 + e;
+            m.W1[(q / sh.din) * (kMaxIn + 1) + q % sh.din] = v[e];
+        }
+    }
+    if ((int)threadIdx.x < n3) {
+        unpack8(u3, v);
+        for (int e = 0; e < 8; ++e) {
+            const int q = threadIdx.x * 8 + e;
+            m.W3[(q >> 7) * kLd + (q & 127)] = v[e];
+        }
+    }
+    if (threadIdx.x < 32) {
+        unpack8(ub, v);
+        float* dst = threadIdx.x < 16 ? m.b1 + threadIdx.x * 8 : m.b2 + (threadIdx.x - 16) * 8;
+        for (int e = 0; e < 8; ++e) dst[e] = v[e];
     }
     for (int q = threadIdx.x; q < sh.dout; q += blockDim.x) m.b3[q] = __bfloat162float(w[sh.ob3 + q]);
 }
 
-// forward pass of the rows [row0, row0 + nr) into m.a1, m.a2 (pre-activations) and y (registers -> out)
+// Thread tiles of the H-wide products: warp w, lane l own rows w + 8a and columns l + 32b
+// (a, b = 0..3), so every step of a dot product loads 4 + 4 values for 16 FMAs (the weight
+// loads run along a padded row: conflict-free; the activation loads are warp broadcasts).
+// Each output keeps its own FMA chain in index order, so the sums are those of the plain loops.
+constexpr int kTileRows = kRows / 8;
+constexpr int kTileCols = kH / 32;
+
+// forward pass of the rows [row0, row0 + nr) into m.a1, m.a2 (activations after relu) and y (out)
 __device__ void forward_tile(const MlpShape& sh, MlpSmem& m, const float* __restrict__ X, int64_t row0, int nr, float* Yout,
                              float* ysm)
 {
@@ -112,21 +163,52 @@ __device__ void forward_tile(const MlpShape& sh, MlpSmem& m, const float* __rest
         m.x[r * (kMaxIn + 1) + i] = r < nr ? X[(row0 + r) * sh.din + i] : 0.0f;
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < kRows * kH; q += blockDim.x) {  // layer 1
-        const int r = q / kH, j = q % kH;
-        float s = m.b1[j];
-        for (int i = 0; i < sh.din; ++i) s = fmaf(m.W1[j * (kMaxIn + 1) + i], m.x[r * (kMaxIn + 1) + i], s);
-        m.a1[r * kLd + j] = s;
+    const int w8 = threadIdx.x >> 5, l = threadIdx.x & 31;
+    {  // layer 1
+        float acc[kTileRows][kTileCols];
+#pragma unroll
+        for (int a = 0; a < kTileRows; ++a)
+#pragma unroll
+            for (int b = 0; b < kTileCols; ++b) acc[a][b] = m.b1[l + 32 * b];
+        for (int i = 0; i < sh.din; ++i) {
+            float wv[kTileCols], xv[kTileRows];
+#pragma unroll
+            for (int b = 0; b < kTileCols; ++b) wv[b] = m.W1[(l + 32 * b) * (kMaxIn + 1) + i];
+#pragma unroll
+            for (int a = 0; a < kTileRows; ++a) xv[a] = m.x[(w8 + 8 * a) * (kMaxIn + 1) + i];
+#pragma unroll
+            for (int a = 0; a < kTileRows; ++a)
+#pragma unroll
+                for (int b = 0; b < kTileCols; ++b) acc[a][b] = fmaf(wv[b], xv[a], acc[a][b]);
+        }
+#pragma unroll
+        for (int a = 0; a < kTileRows; ++a)
+#pragma unroll
+            for (int b = 0; b < kTileCols; ++b) m.a1[(w8 + 8 * a) * kLd + l + 32 * b] = fmaxf(acc[a][b], 0.0f);
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < kRows * kH; q += blockDim.x) {  // layer 2
-        const int r = q / kH, j = q % kH;
-        float s = m.b2[j];
-        const float* w = m.W2 + j * kLd;
-        const float* a = m.a1 + r * kLd;
-#pragma unroll 8
-        for (int i = 0; i < kH; ++i) s = fmaf(w[i], fmaxf(a[i], 0.0f), s);
-        m.a2[r * kLd + j] = s;
+    {  // layer 2
+        float acc[kTileRows][kTileCols];
+#pragma unroll
+        for (int a = 0; a < kTileRows; ++a)
+#pragma unroll
+            for (int b = 0; b < kTileCols; ++b) acc[a][b] = m.b2[l + 32 * b];
+#pragma unroll 4
+        for (int i = 0; i < kH; ++i) {
+            float wv[kTileCols], hv[kTileRows];
+#pragma unroll
+            for (int b = 0; b < kTileCols; ++b) wv[b] = m.W2[(l + 32 * b) * kLd + i];
+#pragma unroll
+            for (int a = 0; a < kTileRows; ++a) hv[a] = m.a1[(w8 + 8 * a) * kLd + i];
+#pragma unroll
+            for (int a = 0; a < kTileRows; ++a)
+#pragma unroll
+                for (int b = 0; b < kTileCols; ++b) acc[a][b] = fmaf(wv[b], hv[a], acc[a][b]);
+        }
+#pragma unroll
+        for (int a = 0; a < kTileRows; ++a)
+#pragma unroll
+            for (int b = 0; b < kTileCols; ++b) m.a2[(w8 + 8 * a) * kLd + l + 32 * b] = fmaxf(acc[a][b], 0.0f);
     }
     __syncthreads();
     for (int q = threadIdx.x; q < kRows * sh.dout; q += blockDim.x) {  // layer 3
@@ -134,7 +216,7 @@ __device__ void forward_tile(const MlpShape& sh, MlpSmem& m, const float* __rest
         float s = m.b3[k];
         const float* w = m.W3 + k * kLd;
         const float* a = m.a2 + r * kLd;
-        for (int i = 0; i < kH; ++i) s = fmaf(w[i], fmaxf(a[i], 0.0f), s);
+        for (int i = 0; i < kH; ++i) s = fmaf(w[i], a[i], s);
         if (ysm) ysm[r * kMaxOut + k] = s;
         if (Yout && r < nr) Yout[(row0 + r) * sh.dout + k] = s;
     }
@@ -184,6 +266,7 @@ __global__ void __launch_bounds__(kThreads) k_mlp_grad(const __nv_bfloat16* __re
         __syncthreads();
     }
     if (threadIdx.x == 0) loss_part[blockIdx.x] = red[0];
+    const int w8 = threadIdx.x >> 5, l = threadIdx.x & 31;
     // d2 = (W3^T dy) * [a2 > 0]
     for (int q = threadIdx.x; q < kRows * kH; q += blockDim.x) {
         const int r = q / kH, i = q % kH;
@@ -192,13 +275,31 @@ __global__ void __launch_bounds__(kThreads) k_mlp_grad(const __nv_bfloat16* __re
         m.d2[r * kLd + i] = m.a2[r * kLd + i] > 0.0f ? s : 0.0f;
     }
     __syncthreads();
-    // d1 = (W2^T d2) * [a1 > 0]
-    for (int q = threadIdx.x; q < kRows * kH; q += blockDim.x) {
-        const int r = q / kH, i = q % kH;
-        float s = 0.0f;
-#pragma unroll 8
-        for (int j = 0; j < kH; ++j) s = fmaf(m.W2[j * kLd + i], m.d2[r * kLd + j], s);
-        m.d1[r * kLd + i] = m.a1[r * kLd + i] > 0.0f ? s : 0.0f;
+    {  // d1 = (W2^T d2) * [a1 > 0], thread tiles as in the forward pass
+        float acc[kTileRows][kTileCols];
+#pragma unroll
+        for (int a = 0; a < kTileRows; ++a)
+#pragma unroll
+            for (int b = 0; b < kTileCols; ++b) acc[a][b] = 0.0f;
+#pragma unroll 4
+        for (int j = 0; j < kH; ++j) {
+            float wv[kTileCols], dv[kTileRows];
+#pragma unroll
+            for (int b = 0; b < kTileCols; ++b) wv[b] = m.W2[j * kLd + l + 32 * b];
+#pragma unroll
+            for (int a = 0; a < kTileRows; ++a) dv[a] = m.d2[(w8 + 8 * a) * kLd + j];
+#pragma unroll
+            for (int a = 0; a < kTileRows; ++a)
+#pragma unroll
+                for (int b = 0; b < kTileCols; ++b) acc[a][b] = fmaf(wv[b], dv[a], acc[a][b]);
+        }
+#pragma unroll
+        for (int a = 0; a < kTileRows; ++a)
+#pragma unroll
+            for (int b = 0; b < kTileCols; ++b) {
+                const int at = (w8 + 8 * a) * kLd + l + 32 * b;
+                m.d1[at] = m.a1[at] > 0.0f ? acc[a][b] : 0.0f;
+            }
     }
     __syncthreads();
     float* g = partial + (int64_t)blockIdx.x * sh.P;
@@ -206,7 +307,7 @@ __global__ void __launch_bounds__(kThreads) k_mlp_grad(const __nv_bfloat16* __re
     for (int q = threadIdx.x; q < dout * kH; q += blockDim.x) {
         const int k = q / kH, i = q % kH;
         float s = 0.0f;
-        for (int r = 0; r < kRows; ++r) s = fmaf(m.dy[r * kMaxOut + k], fmaxf(m.a2[r * kLd + i], 0.0f), s);
+        for (int r = 0; r < kRows; ++r) s = fmaf(m.dy[r * kMaxOut + k], m.a2[r * kLd + i], s);
         g[sh.oW3 + q] = s;
     }
     for (int k = threadIdx.x; k < dout; k += blockDim.x) {
@@ -214,12 +315,30 @@ __global__ void __launch_bounds__(kThreads) k_mlp_grad(const __nv_bfloat16* __re
         for (int r = 0; r < kRows; ++r) s += m.dy[r * kMaxOut + k];
         g[sh.ob3 + k] = s;
     }
-    // layer 2: dW2[j][i] = sum_r d2[r][j] h1[r][i]; db2
-    for (int q = threadIdx.x; q < kH * kH; q += blockDim.x) {
-        const int j = q / kH, i = q % kH;
-        float s = 0.0f;
-        for (int r = 0; r < kRows; ++r) s = fmaf(m.d2[r * kLd + j], fmaxf(m.a1[r * kLd + i], 0.0f), s);
-        g[sh.oW2 + q] = s;
+    // layer 2: dW2[j][i] = sum_r d2[r][j] h1[r][i] (thread tile: i = l + 32a, j = w + 8b); db2
+    {
+        constexpr int kJ = kH / 8;
+        float acc[kJ][kTileCols];
+#pragma unroll
+        for (int b = 0; b < kJ; ++b)
+#pragma unroll
+            for (int a = 0; a < kTileCols; ++a) acc[b][a] = 0.0f;
+#pragma unroll 2
+        for (int r = 0; r < kRows; ++r) {
+            float hv[kTileCols], dv[kJ];
+#pragma unroll
+            for (int a = 0; a < kTileCols; ++a) hv[a] = m.a1[r * kLd + l + 32 * a];
+#pragma unroll
+            for (int b = 0; b < kJ; ++b) dv[b] = m.d2[r * kLd + w8 + 8 * b];
+#pragma unroll
+            for (int b = 0; b < kJ; ++b)
+#pragma unroll
+                for (int a = 0; a < kTileCols; ++a) acc[b][a] = fmaf(dv[b], hv[a], acc[b][a]);
+        }
+#pragma unroll
+        for (int b = 0; b < kJ; ++b)
+#pragma unroll
+            for (int a = 0; a < kTileCols; ++a) g[sh.oW2 + (w8 + 8 * b) * kH + l + 32 * a] = acc[b][a];
     }
     for (int j = threadIdx.x; j < kH; j += blockDim.x) {
         float s2 = 0.0f, s1 = 0.0f;
@@ -245,7 +364,8 @@ __global__ void k_mlp_reduce(const float* __restrict__ partial, const float* __r
 {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < P; q += (int64_t)gridDim.x * blockDim.x) {
         float s = 0.0f;
-        for (int b = 0; b < nblocks; ++b) s += partial[(int64_t)b * P + q];
+#pragma unroll 8
+        for (int b = 0; b < nblocks; ++b) s += partial[(int64_t)b * P + q];  // loads in flight together, sum in block order
         grad[q] = s;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && loss) {
@@ -269,6 +389,31 @@ __global__ void k_mlp_adam(float* p, float* mo, float* ve, const float* __restri
         const float pq = p[q] - lr_t * mq / (sqrtf(vq) + eps);
         p[q] = pq;
         w[q] = __float2bfloat16_rn(pq);
+    }
+}
+
+// k_mlp_reduce and k_mlp_adam in one pass: the same gradient sums, then the same update.
+__global__ void k_mlp_reduce_adam(const float* __restrict__ partial, const float* __restrict__ loss_part, int nblocks, int64_t P,
+                                  float* grad, float* loss, float* p, float* mo, float* ve, float lr_t, float b1, float b2, float eps,
+                                  __nv_bfloat16* w)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < P; q += (int64_t)gridDim.x * blockDim.x) {
+        float gq = 0.0f;
+#pragma unroll 8
+        for (int b = 0; b < nblocks; ++b) gq += partial[(int64_t)b * P + q];
+        grad[q] = gq;
+        const float mq = b1 * mo[q] + (1.0f - b1) * gq;
+        const float vq = b2 * ve[q] + (1.0f - b2) * gq * gq;
+        mo[q] = mq;
+        ve[q] = vq;
+        const float pq = p[q] - lr_t * mq / (sqrtf(vq) + eps);
+        p[q] = pq;
+        w[q] = __float2bfloat16_rn(pq);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && loss) {
+        float sl = 0.0f;
+        for (int b = 0; b < nblocks; ++b) sl += loss_part[b];
+        *loss = sl;
     }
 }
 
@@ -326,9 +471,28 @@ __global__ void k_mlp_inputs(const float* __restrict__ lam, int K, int din, cons
 
 // gap(p) = min over front members f of max_k (p_k - fhat_k), fhat = (f - offset) * inv_scale:
 // how far the predicted point reaches beyond the nearest front member (> 0: undominated).
+// Block (x, y) takes 256 candidates and the front chunks y, y + gridDim.y, ... of 256
+// members; the minima meet in `key` through atomicMin on an order-preserving integer image of
+// the float (min is exact, so the result does not depend on the split).
+__device__ __forceinline__ uint32_t order_key(float v)
+{
+    const uint32_t u = __float_as_uint(v);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ float from_order_key(uint32_t k) { return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k); }
+
+constexpr uint32_t kKeyInf = 0xFF800000u;  // order_key(+inf)
+constexpr int kGapSplits = 64;
+
+__global__ void k_gap_init(uint32_t* key, int C)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) key[c] = kKeyInf;
+}
+
 __global__ void __launch_bounds__(256) k_front_gap(const float* __restrict__ pred, int C, int K, const int64_t* __restrict__ front,
                                                    const int64_t* __restrict__ d_count, const float* __restrict__ offset,
-                                                   const float* __restrict__ inv_scale, float* score)
+                                                   const float* __restrict__ inv_scale, uint32_t* key)
 {
     __shared__ float tile[256][kMaxOut];
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -336,7 +500,7 @@ __global__ void __launch_bounds__(256) k_front_gap(const float* __restrict__ pre
     for (int k = 0; k < kMaxOut; ++k) p[k] = (c < C && k < K) ? pred[(int64_t)c * K + k] : 0.0f;
     const int64_t F = *d_count;
     float gap = INFINITY;
-    for (int64_t base = 0; base < F; base += 256) {
+    for (int64_t base = (int64_t)blockIdx.y * 256; base < F; base += (int64_t)gridDim.y * 256) {
         const int cnt = (int)min((int64_t)256, F - base);
         __syncthreads();
         if (threadIdx.x < cnt)
@@ -348,21 +512,33 @@ __global__ void __launch_bounds__(256) k_front_gap(const float* __restrict__ pre
             gap = fminf(gap, mx);
         }
     }
-    if (c < C) score[c] = isnan(gap) ? -INFINITY : gap;
+    if (c < C && gap < INFINITY) atomicMin(key + c, order_key(gap));
 }
 
-// rank = number of candidates with a higher score (ties: lower index first); the R best go out in rank order
-__global__ void k_top_r(const float* __restrict__ score, const float* __restrict__ lam, int C, int K, int R, float* out)
+// score = the gap (NaN -> -inf); rank = number of candidates with a higher score (ties: lower
+// index first); the R best go out in rank order. Scores pass through shared memory in chunks.
+__global__ void __launch_bounds__(64) k_top_r(const uint32_t* __restrict__ key, const float* __restrict__ lam, int C, int K, int R,
+                                              float* out)
 {
+    __shared__ float sc[1024];
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
-    const float s = score[c];
+    auto score_of = [&](int q) {
+        const float g = from_order_key(key[q]);
+        return isnan(g) ? -INFINITY : g;
+    };
+    const float s = c < C ? score_of(c) : 0.0f;
     int rank = 0;
-    for (int q = 0; q < C; ++q) {
-        const float t = score[q];
-        rank += (t > s) || (t == s && q < c);
+    for (int base = 0; base < C; base += 1024) {
+        const int cnt = min(1024, C - base);
+        __syncthreads();
+        for (int q = threadIdx.x; q < cnt; q += blockDim.x) sc[q] = score_of(base + q);
+        __syncthreads();
+        for (int q = 0; q < cnt; ++q) {
+            const float t = sc[q];
+            rank += (t > s) || (t == s && base + q < c);
+        }
     }
-    if (rank < R)
+    if (c < C && rank < R)
         for (int k = 0; k < K; ++k) out[(int64_t)rank * K + k] = lam[(int64_t)c * K + k];
 }
 
@@ -519,6 +695,25 @@ int moq_mlp_adam_step(moq_mlp* m, float lr, void* stream)
     return MOQ_OK;
 }
 
+int moq_mlp_train_step(moq_mlp* m, const float* X, const float* T, int32_t B, float lr, float* loss_out, void* stream)
+{
+    using namespace moq;
+    if (!m || B < 1 || B > m->max_batch || !X || !T || !(lr > 0.0f))
+        return fail(MOQ_ERR_ARG, "moq_mlp_train_step: need 1 <= B <= max_batch, inputs and lr > 0");
+    cudaStream_t st = as_stream(stream);
+    const int nb = (int)ceil_div(B, kRows);
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    m->step += 1;
+    const double t = (double)m->step;
+    const float lr_t = (float)(lr * std::sqrt(1.0 - std::pow(b2, t)) / (1.0 - std::pow(b1, t)));
+    k_mlp_grad<<<nb, kThreads, mlp_smem_bytes(), st>>>(m->w16, m->din, m->dout, X, T, B, m->partial, m->loss_part);
+    k_mlp_reduce_adam<<<(unsigned)std::min<int64_t>(ceil_div(m->P, 256), 148), 256, 0, st>>>(
+        m->partial, m->loss_part, nb, m->P, m->grad, loss_out ? loss_out : m->loss_part + m->max_blocks, m->master, m->adam_m,
+        m->adam_v, lr_t, b1, b2, eps, m->w16);
+    MOQ_LAUNCH_CHECK("moq_mlp_train_step");
+    return MOQ_OK;
+}
+
 int moq_mlp_make_rows(int32_t K, int32_t n_features, const float* lambda, const int64_t* cuts, int64_t M, const float* features,
                       const int64_t* offset, const int64_t* scale, float* X, float* T, void* stream)
 {
@@ -568,8 +763,10 @@ int moq_lambda_propose(moq_mlp* m, const moq_archive* a, const float* features, 
     if (rc != MOQ_OK) return rc;
     const int64_t *fc = nullptr, *cnt = nullptr;
     moq_archive_device_view(a, &fc, nullptr, nullptr, &cnt);
-    k_front_gap<<<(unsigned)ceil_div(C, 256), 256, 0, st>>>(m->cand_pred, C, K, fc, cnt, m->consts + 16, m->consts + 24, m->cand_score);
-    k_top_r<<<(unsigned)ceil_div(C, 256), 256, 0, st>>>(m->cand_score, m->cand, C, K, R, lambda_out);
+    uint32_t* key = reinterpret_cast<uint32_t*>(m->cand_score);
+    k_gap_init<<<(unsigned)ceil_div(C, 256), 256, 0, st>>>(key, C);
+    k_front_gap<<<dim3((unsigned)ceil_div(C, 256), kGapSplits), 256, 0, st>>>(m->cand_pred, C, K, fc, cnt, m->consts + 16, m->consts + 24, key);
+    k_top_r<<<(unsigned)ceil_div(C, 64), 64, 0, st>>>(key, m->cand, C, K, R, lambda_out);
     MOQ_LAUNCH_CHECK("moq_lambda_propose select");
     return MOQ_OK;
 }

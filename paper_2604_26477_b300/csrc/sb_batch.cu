@@ -271,6 +271,11 @@ struct moq_batch {
     std::vector<moq::BatchInst> h_insts;
     std::vector<int64_t> h_E;
     std::vector<const moq_instance*> h_handles;  // for the per-instance mode (bd == 0)
+    // per-instance mode: launches fan out over these streams (one instance's tail overlaps
+    // the next one's start) and join back into the caller's stream
+    std::vector<cudaStream_t> lanes;
+    std::vector<cudaEvent_t> lane_done;
+    cudaEvent_t fork = nullptr;
     moq::BatchInst* d_insts = nullptr;
     moq::BatchItem* d_items = nullptr;
     int64_t items_cap = 0;
@@ -294,6 +299,9 @@ void free_batch(moq_batch* b)
     cudaFree(b->d_ej);
     cudaFree(b->d_w);
     cudaFree(b->d_E);
+    for (cudaStream_t s : b->lanes) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->lane_done) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
     delete b;
 }
 
@@ -465,6 +473,19 @@ int moq_batch_set_tiles(moq_batch* b, int32_t block_threads, int32_t slots_per_t
     using namespace moq;
     if (!b) return fail(MOQ_ERR_ARG, "moq_batch_set_tiles: NULL batch");
     if (block_threads == 0 && slots_per_thread == 0) {  // per-instance launches of the single-instance sampler
+        if (b->lanes.empty()) {
+            int nl = 4;
+            if (const char* env = getenv("MOQ_BATCH_STREAMS")) nl = std::max(1, std::min(16, atoi(env)));
+            MOQ_CUDA_TRY(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+            for (int l = 0; l < nl; ++l) {
+                cudaStream_t s = nullptr;
+                cudaEvent_t e = nullptr;
+                MOQ_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+                b->lanes.push_back(s);
+                MOQ_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+                b->lane_done.push_back(e);
+            }
+        }
         b->bd = 0;
         b->spt = 0;
         if (items_out) *items_out = b->count;
@@ -497,15 +518,24 @@ int moq_sample_batch(moq_batch* b, const float* lambda_all, const moq_sample_par
         std::vector<int> order(b->count);
         for (int i = 0; i < b->count; ++i) order[i] = i;
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->h_insts[x].n > b->h_insts[y].n; });
-        for (int i : order) {
+        const int nl = (int)b->lanes.size();
+        MOQ_CUDA_TRY(cudaEventRecord(b->fork, st));
+        for (int l = 0; l < nl; ++l) MOQ_CUDA_TRY(cudaStreamWaitEvent(b->lanes[l], b->fork, 0));
+        int rc = MOQ_OK;
+        for (int q = 0; q < b->count && rc == MOQ_OK; ++q) {
+            const int i = order[q];
             const BatchInst& in = b->h_insts[i];
             moq_sample_params pi = *p;
             pi.replica_offset = (uint32_t)in.rep_off;
-            const int rc = moq_sample(b->h_handles[i], lambda_all + in.rep_off * b->K, in.R, &pi, seed, round,
-                                      bits_all + in.bits_off, stream);
-            if (rc != MOQ_OK) return rc;
+            rc = moq_sample(b->h_handles[i], lambda_all + in.rep_off * b->K, in.R, &pi, seed, round, bits_all + in.bits_off,
+                            nl ? (void*)b->lanes[q % nl] : stream);
         }
-        return MOQ_OK;
+        // the caller's stream waits for every lane, also after a failed launch
+        for (int l = 0; l < nl; ++l) {
+            MOQ_CUDA_TRY(cudaEventRecord(b->lane_done[l], b->lanes[l]));
+            MOQ_CUDA_TRY(cudaStreamWaitEvent(st, b->lane_done[l], 0));
+        }
+        return rc;
     }
     MOQ_CUDA_TRY(cudaMemsetAsync(b->d_queue, 0, sizeof(int32_t), st));
     BatchArgs a{};

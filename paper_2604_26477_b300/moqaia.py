@@ -100,6 +100,7 @@ _sigs = {
     "moq_mlp_forward": (C.c_int, [_vp, _vp, _i32, _vp, _vp]),
     "moq_mlp_gradient": (C.c_int, [_vp, _vp, _vp, _i32, _vp, _vp, _vp]),
     "moq_mlp_adam_step": (C.c_int, [_vp, C.c_float, _vp]),
+    "moq_mlp_train_step": (C.c_int, [_vp, _vp, _vp, _i32, C.c_float, _vp, _vp]),
     "moq_lambda_propose": (C.c_int, [_vp, _vp, _vp, _i32, _vp, _vp, _i32, _u64, _u64, _vp, _i32, _vp]),
     "moq_mlp_make_rows": (C.c_int, [_i32, _i32, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "moq_strerror": (C.c_char_p, [C.c_int]),
@@ -391,6 +392,12 @@ def moq_mlp_gradient(h, X, T, B, grad=None, loss=None, stream=None):
 
 def moq_mlp_adam_step(h, lr, stream=None):
     _check(_lib.moq_mlp_adam_step(h, lr, _stream(stream)), "moq_mlp_adam_step")
+
+
+def moq_mlp_train_step(h, X, T, B, lr, loss=None, stream=None):
+    f32, _, _ = _torch_types()
+    _check(_lib.moq_mlp_train_step(h, _dptr(X, "X", f32), _dptr(T, "T", f32), B, lr, _dptr(loss, "loss", f32), _stream(stream)),
+           "moq_mlp_train_step")
 
 
 def moq_mlp_make_rows(K, features, lam, cuts, M, offset, scale, X, T, stream=None):

@@ -207,8 +207,7 @@ class LearnedProposer:
             while end <= 0:
                 end += filled
             start = max(0, end - self.batch)
-            M.moq_mlp_gradient(self.mlp, self.X[start:end], self.T[start:end], end - start, None, self.loss)
-            M.moq_mlp_adam_step(self.mlp, self.lr)
+            M.moq_mlp_train_step(self.mlp, self.X[start:end], self.T[start:end], end - start, self.lr, self.loss)
 
     def close(self):
         if getattr(self, "mlp", None):

@@ -94,6 +94,29 @@ def test_adam_training_fits_a_smooth_map(M):
         M.moq_mlp_destroy(h)
 
 
+def test_train_step_equals_gradient_then_adam(M):
+    # the fused entry point takes the same gradient sums and the same update: after a few
+    # steps both handles hold the same parameters bit for bit, and the losses agree
+    ha, hb = _mlp(M, seed=5), _mlp(M, seed=5)
+    try:
+        X, T = _data(3000, 11)
+        Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+        la, lb = torch.zeros(1, device="cuda"), torch.zeros(1, device="cuda")
+        for s in range(4):
+            B = 3000 - 700 * s
+            M.moq_mlp_gradient(ha, Xd, Td, B, None, la)
+            M.moq_mlp_adam_step(ha, 2e-3)
+            M.moq_mlp_train_step(hb, Xd, Td, B, 2e-3, lb)
+            assert torch.equal(la, lb)
+        assert np.array_equal(M.moq_mlp_get_params(ha), M.moq_mlp_get_params(hb))
+        assert np.array_equal(M.moq_mlp_get_params(ha, bf16_rounded=True), M.moq_mlp_get_params(hb, bf16_rounded=True))
+        with pytest.raises(Exception):
+            M.moq_mlp_train_step(hb, Xd, Td, 5000, 2e-3)  # beyond max_batch
+    finally:
+        M.moq_mlp_destroy(ha)
+        M.moq_mlp_destroy(hb)
+
+
 def test_graph_features(M):
     from paper_2604_26477_b300 import pipeline as P
     src = wl.app_e_correlated(60, 0.5, 4)
