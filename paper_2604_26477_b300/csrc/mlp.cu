@@ -29,7 +29,7 @@ constexpr int kMaxIn = 16;    // D_in <= 16
 constexpr int kMaxOut = 8;    // D_out <= 8
 constexpr int kRows = 32;     // rows per block
 constexpr int kThreads = 256;
-constexpr int kLd = kH + 1;   // padded row stride of H-wide smem matrices
+constexpr int kLd = kH + 4;   // padded row stride of H-wide smem matrices (16-byte rows, 4-bank skew)
 
 struct MlpShape {
     int din, dout;
@@ -193,17 +193,22 @@ __device__ void forward_tile(const MlpShape& sh, MlpSmem& m, const float* __rest
         for (int a = 0; a < kTileRows; ++a)
 #pragma unroll
             for (int b = 0; b < kTileCols; ++b) acc[a][b] = m.b2[l + 32 * b];
-#pragma unroll 4
-        for (int i = 0; i < kH; ++i) {
-            float wv[kTileCols], hv[kTileRows];
+#pragma unroll 2
+        for (int i = 0; i < kH; i += 4) {  // four steps per 16-byte load
+            float4 wv[kTileCols], hv[kTileRows];
 #pragma unroll
-            for (int b = 0; b < kTileCols; ++b) wv[b] = m.W2[(l + 32 * b) * kLd + i];
+            for (int b = 0; b < kTileCols; ++b) wv[b] = *reinterpret_cast<const float4*>(m.W2 + (l + 32 * b) * kLd + i);
 #pragma unroll
-            for (int a = 0; a < kTileRows; ++a) hv[a] = m.a1[(w8 + 8 * a) * kLd + i];
+            for (int a = 0; a < kTileRows; ++a) hv[a] = *reinterpret_cast<const float4*>(m.a1 + (w8 + 8 * a) * kLd + i);
 #pragma unroll
             for (int a = 0; a < kTileRows; ++a)
 #pragma unroll
-                for (int b = 0; b < kTileCols; ++b) acc[a][b] = fmaf(wv[b], hv[a], acc[a][b]);
+                for (int b = 0; b < kTileCols; ++b) {
+                    acc[a][b] = fmaf(wv[b].x, hv[a].x, acc[a][b]);
+                    acc[a][b] = fmaf(wv[b].y, hv[a].y, acc[a][b]);
+                    acc[a][b] = fmaf(wv[b].z, hv[a].z, acc[a][b]);
+                    acc[a][b] = fmaf(wv[b].w, hv[a].w, acc[a][b]);
+                }
         }
 #pragma unroll
         for (int a = 0; a < kTileRows; ++a)
@@ -275,31 +280,38 @@ __global__ void __launch_bounds__(kThreads) k_mlp_grad(const __nv_bfloat16* __re
         m.d2[r * kLd + i] = m.a2[r * kLd + i] > 0.0f ? s : 0.0f;
     }
     __syncthreads();
-    {  // d1 = (W2^T d2) * [a1 > 0], thread tiles as in the forward pass
-        float acc[kTileRows][kTileCols];
+    {  // d1 = (W2^T d2) * [a1 > 0]: rows w + 8a, columns 4l..4l+3 (one 16-byte load of a W2 row)
+        float acc[kTileRows][4];
 #pragma unroll
         for (int a = 0; a < kTileRows; ++a)
 #pragma unroll
-            for (int b = 0; b < kTileCols; ++b) acc[a][b] = 0.0f;
-#pragma unroll 4
-        for (int j = 0; j < kH; ++j) {
-            float wv[kTileCols], dv[kTileRows];
+            for (int c = 0; c < 4; ++c) acc[a][c] = 0.0f;
+#pragma unroll 2
+        for (int j = 0; j < kH; j += 4) {
+            float4 dv[kTileRows];
 #pragma unroll
-            for (int b = 0; b < kTileCols; ++b) wv[b] = m.W2[j * kLd + l + 32 * b];
+            for (int a = 0; a < kTileRows; ++a) dv[a] = *reinterpret_cast<const float4*>(m.d2 + (w8 + 8 * a) * kLd + j);
 #pragma unroll
-            for (int a = 0; a < kTileRows; ++a) dv[a] = m.d2[(w8 + 8 * a) * kLd + j];
+            for (int jj = 0; jj < 4; ++jj) {
+                const float4 wv = *reinterpret_cast<const float4*>(m.W2 + (j + jj) * kLd + 4 * l);
 #pragma unroll
-            for (int a = 0; a < kTileRows; ++a)
-#pragma unroll
-                for (int b = 0; b < kTileCols; ++b) acc[a][b] = fmaf(wv[b], dv[a], acc[a][b]);
+                for (int a = 0; a < kTileRows; ++a) {
+                    const float d = jj == 0 ? dv[a].x : (jj == 1 ? dv[a].y : (jj == 2 ? dv[a].z : dv[a].w));
+                    acc[a][0] = fmaf(wv.x, d, acc[a][0]);
+                    acc[a][1] = fmaf(wv.y, d, acc[a][1]);
+                    acc[a][2] = fmaf(wv.z, d, acc[a][2]);
+                    acc[a][3] = fmaf(wv.w, d, acc[a][3]);
+                }
+            }
         }
 #pragma unroll
-        for (int a = 0; a < kTileRows; ++a)
-#pragma unroll
-            for (int b = 0; b < kTileCols; ++b) {
-                const int at = (w8 + 8 * a) * kLd + l + 32 * b;
-                m.d1[at] = m.a1[at] > 0.0f ? acc[a][b] : 0.0f;
-            }
+        for (int a = 0; a < kTileRows; ++a) {
+            const int at = (w8 + 8 * a) * kLd + 4 * l;
+            const float4 h = *reinterpret_cast<const float4*>(m.a1 + at);
+            *reinterpret_cast<float4*>(m.d1 + at) =
+                make_float4(h.x > 0.0f ? acc[a][0] : 0.0f, h.y > 0.0f ? acc[a][1] : 0.0f, h.z > 0.0f ? acc[a][2] : 0.0f,
+                            h.w > 0.0f ? acc[a][3] : 0.0f);
+        }
     }
     __syncthreads();
     float* g = partial + (int64_t)blockIdx.x * sh.P;
@@ -315,30 +327,36 @@ __global__ void __launch_bounds__(kThreads) k_mlp_grad(const __nv_bfloat16* __re
         for (int r = 0; r < kRows; ++r) s += m.dy[r * kMaxOut + k];
         g[sh.ob3 + k] = s;
     }
-    // layer 2: dW2[j][i] = sum_r d2[r][j] h1[r][i] (thread tile: i = l + 32a, j = w + 8b); db2
+    // layer 2: dW2[j][i] = sum_r d2[r][j] h1[r][i] (thread tile: j = 16w + b, i = 4l + c: per row
+    // one 16-byte load of h1 and four broadcast 16-byte loads of d2); db2
     {
         constexpr int kJ = kH / 8;
-        float acc[kJ][kTileCols];
+        float acc[kJ][4];
 #pragma unroll
         for (int b = 0; b < kJ; ++b)
 #pragma unroll
-            for (int a = 0; a < kTileCols; ++a) acc[b][a] = 0.0f;
+            for (int c = 0; c < 4; ++c) acc[b][c] = 0.0f;
 #pragma unroll 2
         for (int r = 0; r < kRows; ++r) {
-            float hv[kTileCols], dv[kJ];
+            const float4 hv = *reinterpret_cast<const float4*>(m.a1 + r * kLd + 4 * l);
 #pragma unroll
-            for (int a = 0; a < kTileCols; ++a) hv[a] = m.a1[r * kLd + l + 32 * a];
+            for (int b4 = 0; b4 < kJ / 4; ++b4) {
+                const float4 dv = *reinterpret_cast<const float4*>(m.d2 + r * kLd + kJ * w8 + 4 * b4);
+                const float d[4] = {dv.x, dv.y, dv.z, dv.w};
 #pragma unroll
-            for (int b = 0; b < kJ; ++b) dv[b] = m.d2[r * kLd + w8 + 8 * b];
-#pragma unroll
-            for (int b = 0; b < kJ; ++b)
-#pragma unroll
-                for (int a = 0; a < kTileCols; ++a) acc[b][a] = fmaf(dv[b], hv[a], acc[b][a]);
+                for (int e = 0; e < 4; ++e) {
+                    float* ac = acc[4 * b4 + e];
+                    ac[0] = fmaf(d[e], hv.x, ac[0]);
+                    ac[1] = fmaf(d[e], hv.y, ac[1]);
+                    ac[2] = fmaf(d[e], hv.z, ac[2]);
+                    ac[3] = fmaf(d[e], hv.w, ac[3]);
+                }
+            }
         }
 #pragma unroll
         for (int b = 0; b < kJ; ++b)
 #pragma unroll
-            for (int a = 0; a < kTileCols; ++a) g[sh.oW2 + (w8 + 8 * b) * kH + l + 32 * a] = acc[b][a];
+            for (int c = 0; c < 4; ++c) g[sh.oW2 + (kJ * w8 + b) * kH + 4 * l + c] = acc[b][c];
     }
     for (int j = threadIdx.x; j < kH; j += blockDim.x) {
         float s2 = 0.0f, s1 = 0.0f;
@@ -399,8 +417,8 @@ __global__ void k_mlp_reduce_adam(const float* __restrict__ partial, const float
 {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < P; q += (int64_t)gridDim.x * blockDim.x) {
         float gq = 0.0f;
-#pragma unroll 8
-        for (int b = 0; b < nblocks; ++b) gq += partial[(int64_t)b * P + q];
+#pragma unroll 16
+        for (int b = 0; b < nblocks; ++b) gq += partial[(int64_t)b * P + q];  // loads in flight together, sum in block order
         grad[q] = gq;
         const float mq = b1 * mo[q] + (1.0f - b1) * gq;
         const float vq = b2 * ve[q] + (1.0f - b2) * gq * gq;
