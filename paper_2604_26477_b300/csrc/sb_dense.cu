@@ -263,149 +263,23 @@ __device__ __forceinline__ bool dense_products(const CUtensorMap* tmA, const CUt
     return ok;
 }
 
-template <int VARIANT, int KOBJ, bool NOISE, int CL>
-__global__ void __launch_bounds__(kThreads, 1)
-    k_dense_step(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmPhi, const DenseStepArgs a)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    // 1024-aligned operand stages: stage s holds KOBJ J tiles then the Phi tile. The offset
-    // of every buffer below is the same in all CTAs (same kernel, same dynamic size), which
-    // the multicast copies and commits rely on.
-    const uint32_t raw = smem_u32(smem_raw);
-    const uint32_t base = (raw + 1023u) & ~1023u;
-    unsigned char* gbase = smem_raw + (base - raw);
-    constexpr int kStageBytes = (KOBJ + 1) * kTileBytes;
-    constexpr int S = dense_stages(KOBJ);
-    float* lam_s = reinterpret_cast<float*>(gbase + S * kStageBytes);  // kTileN x KOBJ
-    float* c0_s = lam_s + kTileN * KOBJ;                                // kTileN
-    uint64_t* full = reinterpret_cast<uint64_t*>(c0_s + kTileN);        // S (8-aligned: offsets are multiples of 8)
-    uint64_t* empty = full + S;                                         // S
-    uint64_t* done = empty + S;                                         // 1
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int i0 = blockIdx.x * kTileM, r0 = blockIdx.y * kTileN;
-    const int np = a.n_pad;
-    uint32_t rank = 0;
-    if (CL > 1) asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
-
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)), "r"(512));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    if (tid == 0) {
-        for (int s = 0; s < S; ++s) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[s])), "r"(1));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[s])), "r"(CL));
-        }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(done)), "r"(1));
-        asm volatile("fence.mbarrier_init.release.cluster;");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmJ)) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmPhi)) : "memory");
-    }
-    for (int q = tid; q < kTileN; q += kThreads) {
-        const int r = r0 + q;
-        c0_s[q] = r < a.R ? a.c0[r] : 0.0f;
-#pragma unroll
-        for (int k = 0; k < KOBJ; ++k) lam_s[q * KOBJ + k] = r < a.R ? a.lambda[(int64_t)r * KOBJ + k] : 0.0f;
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    if (CL > 1) cluster_sync();  // every CTA's barriers are initialised before any copy targets them
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    const uint32_t tmem = *tmem_slot;
-
-    // ---- main loop: products of all objectives over the spin chunks ----
-    bool ok = dense_products<KOBJ, CL>(&tmJ, &tmPhi, base, full, empty, done, tmem, i0, r0, np / kChunkK, rank);
-    // warp w owns TMEM lanes 32*(w % 4).. (its spins) and columns 32*(w / 4).. (replicas);
-    // each lane's state for the first 16 columns is loaded while the last products finish
-    const int quarter = warp & 3, part = warp >> 2;
-    const int i = i0 + quarter * 32 + lane;
-    float xs[16], ys[16];
-    auto load_state = [&](int col0) {
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const int r = r0 + col0 + q;
-            const bool v = i < a.n && r < a.R;
-            xs[q] = v ? a.x[(int64_t)r * np + i] : 0.0f;
-            ys[q] = v ? a.y[(int64_t)r * np + i] : 0.0f;
-        }
-    };
-    load_state(part * 32);
-    // `done` covers every product the MMA thread issued (it commits even after a failed wait)
-    const bool products = mbar_wait(smem_u32(done), 0u);
-    ok = __syncthreads_and(ok && products);
-    asm volatile("tcgen05.fence::after_thread_sync;");
-
-    if (ok) {
-        // ---- epilogue: force, update, wall, next phi ----
-        const float cm = a.schedule ? (__ldg(a.schedule + a.m) - a.a0) : a.cm;
-#pragma unroll 1
-        for (int cc = 0; cc < 2; ++cc) {
-            const int col0 = part * 32 + cc * 16;
-            if (cc > 0) load_state(col0);  // all 32 loads in flight together
-            float g[KOBJ][16];
-#pragma unroll
-            for (int k = 0; k < KOBJ; ++k) tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + k * kTileN + col0, g[k]);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            float eta[16];
-#pragma unroll
-            for (int q8 = 0; q8 < 2; ++q8) {
-#pragma unroll
-                for (int t = 0; t < 8; ++t) eta[8 * q8 + t] = 0.0f;
-                if (NOISE) {
-                    const uint32_t octet = (uint32_t)((r0 + col0) >> 3) + q8;
-                    const uint4 o = Philox4x32::block(make_uint4((uint32_t)a.m, (uint32_t)i, 0x40000000u + octet, a.round32), a.key0, a.key1);
-#pragma unroll
-                    for (int w = 0; w < 4; ++w) {
-                        const float2 p = box_muller16(word_of(o, w));
-                        eta[8 * q8 + 2 * w] = p.x;
-                        eta[8 * q8 + 2 * w + 1] = p.y;
-                    }
-                }
-            }
-            if (i < a.n) {
-#pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const int rl = col0 + q, r = r0 + rl;
-                    if (r < a.R) {
-                        float f = 0.0f;
-#pragma unroll
-                        for (int k = 0; k < KOBJ; ++k) f = fmaf(lam_s[rl * KOBJ + k], g[k][q], f);
-                        f *= -c0_s[rl];  // the force acts on the negated coupling
-                        const int64_t at = (int64_t)r * np + i;
-                        float xv = xs[q], yv = ys[q];
-                        sb_update<NOISE>(f, cm, eta[q], a.dt, a.kappa, a.dta0, xv, yv);
-                        a.x[at] = xv;
-                        a.y[at] = yv;
-                        a.phi_out[at] = __float2bfloat16_rn(phi_of<VARIANT>(xv));
-                    }
-                }
-            }
-        }
-    } else if (tid == 0) {
-        atomicOr(a.status, 1);
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    if (CL > 1) cluster_sync();  // no CTA leaves while a peer may still write to it
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
-}
-
-// ---- one step, persistent and warp-specialised (single-CTA clusters) -----------------
-// One CTA per SM walks the tiles b, b + G, ...; warp 0 is the TMA producer, warp 1 issues
-// the MMAs, warps 2..17 run the epilogue. The epilogue reads the K accumulators of a tile,
-// combines them into the force (32 values per thread, in registers) and releases TMEM at
-// once, so the products of the next tile run on the tensor cores while the same warps
-// stream the state update (x, y in, x, y, phi out) through HBM. The force, update and noise
-// are those of k_dense_step, so both give the same bits.
+// ---- one SB step over all tiles: persistent and warp-specialised ---------------------
+// Tiles of 128 spins x 128 replicas. One CTA per SM walks its tiles b, b + G, ...; warp 0 is
+// the TMA producer, warp 1 issues the MMAs, warps 2..17 run the epilogue. The epilogue reads
+// the K accumulators of a tile, combines them into the force (32 values per thread, in
+// registers) and releases TMEM at once, so the products of the next tile run on the tensor
+// cores while the same warps stream the state update (x, y in, x, y, phi out) through HBM.
 constexpr int kWsEpiWarps = 16;
 constexpr int kWsThreads = 32 * (2 + kWsEpiWarps);
 
-template <int VARIANT, int KOBJ, bool NOISE>
+// With clusters of CL CTAs (CL = 2, 4), the CTAs of a cluster take the CL replica blocks of
+// one spin block together: each loads 128 / CL rows of every J tile and multicasts them to
+// all, so L2 delivers each J tile once per cluster; a stage is refilled once every CTA's
+// products have released it (the MMA commits arrive in every CTA of the cluster).
+template <int VARIANT, int KOBJ, bool NOISE, int CL>
 __global__ void __launch_bounds__(kWsThreads, 1)
     k_dense_step_ws(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmPhi, const DenseStepArgs a,
-                    int32_t n_ib, int32_t n_tiles)
+                    int32_t n_ib, int32_t n_groups)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -425,6 +299,16 @@ __global__ void __launch_bounds__(kWsThreads, 1)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int np = a.n_pad, nchunks = np / kChunkK;
+    constexpr int kSliceRows = kTileM / CL;
+    constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
+    uint32_t rank = 0;
+    if (CL > 1) asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    const int cid = blockIdx.x / CL, nclusters = gridDim.x / CL;
+    // tile group g = (spin block g % n_ib, replica blocks CL (g / n_ib) ..); this CTA's block: + rank
+    auto tile_of = [&](int g, int& i0, int& r0) {
+        i0 = (g % n_ib) * kTileM;
+        r0 = ((g / n_ib) * CL + (int)rank) * kTileN;
+    };
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)), "r"(512));
@@ -433,7 +317,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     if (tid == 32) {
         for (int st = 0; st < S; ++st) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[st])), "r"(1));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[st])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[st])), "r"(CL));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(tfull)), "r"(1));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(tempty)), "r"(kWsEpiWarps));
@@ -446,6 +330,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
+    if (CL > 1) cluster_sync();  // every CTA's barriers are initialised before any copy targets them
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
     bool ok = true;
@@ -453,8 +338,9 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     if (warp == 0) {
         if (lane == 0) {  // producer
             int gc = 0;
-            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-                const int i0 = (t % n_ib) * kTileM, r0 = (t / n_ib) * kTileN;
+            for (int g = cid; g < n_groups && ok; g += nclusters) {
+                int i0, r0;
+                tile_of(g, i0, r0);
                 for (int c = 0; c < nchunks; ++c, ++gc) {
                     const int st = gc % S;
                     if (gc >= S && !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((gc - S) / S) & 1))) {
@@ -465,21 +351,29 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                     mbar_expect_tx(fb, (uint32_t)kStageBytes);
                     const int j0 = c * kChunkK;
 #pragma unroll
-                    for (int k = 0; k < KOBJ; ++k) tma_load_3d(stage + k * kTileBytes, &tmJ, j0, i0, k, fb);
+                    for (int k = 0; k < KOBJ; ++k) {
+                        if (CL > 1)
+                            tma_load_3d_mc(stage + k * kTileBytes + rank * (kSliceRows * kChunkK * 2), &tmJ, j0, i0 + (int)rank * kSliceRows,
+                                           k, fb, kMask);
+                        else
+                            tma_load_3d(stage + k * kTileBytes, &tmJ, j0, i0, k, fb);
+                    }
                     tma_load_2d(stage + KOBJ * kTileBytes, &tmPhi, j0, r0, fb);
                 }
             }
-            // no copy of this CTA is still in flight when it leaves (gc chunks were issued)
+            // no copy into this CTA is still in flight when it leaves (gc chunks were issued), and
+            // with clusters every CTA's release of the last use of each stage has arrived
             for (int st = 0; st < S && st < gc; ++st) {
                 const int c_last = st + ((gc - 1 - st) / S) * S;
                 if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((c_last / S) & 1))) ok = false;
+                if (CL > 1 && !mbar_wait(smem_u32(&empty[st]), (uint32_t)((c_last / S) & 1))) ok = false;
             }
         }
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {  // MMA issuer
             int gc = 0, lt = 0;
-            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++lt) {
+            for (int g = cid; g < n_groups && ok; g += nclusters, ++lt) {
                 // the epilogue has read the previous tile's accumulators
                 if (lt > 0 && !mbar_wait(smem_u32(tempty), (uint32_t)((lt - 1) & 1))) {
                     ok = false;
@@ -500,9 +394,16 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                         for (int ks = 0; ks < kChunkK / 16; ++ks)
                             mma_bf16(tmem + k * kTileN, sw128_desc(stage + k * kTileBytes + ks * 32),
                                      sw128_desc(stage + KOBJ * kTileBytes + ks * 32), (c > 0 || ks > 0) ? 1u : 0u);
-                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                     smem_u32(&empty[st]))
-                                 : "memory");
+                    if (CL > 1)
+                        asm volatile(
+                            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                                smem_u32(&empty[st])),
+                            "h"(kMask)
+                            : "memory");
+                    else
+                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                         smem_u32(&empty[st]))
+                                     : "memory");
                 }
                 if (!ok) break;
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(tfull))
@@ -522,8 +423,9 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         // buffer reuse is ordered by the TMEM hand-off: a warp fills buffer b for tile lt + 2
         // only after the products of tile lt + 1, which wait for every warp to read tile lt
         const int e = tid - 64;
-        auto stage_lambda = [&](int t, int b) {
-            const int r0 = (t / n_ib) * kTileN;
+        auto stage_lambda = [&](int g, int b) {
+            int i0_unused, r0;
+            tile_of(g, i0_unused, r0);
             for (int q = e; q < kTileN * (KOBJ + 1); q += 32 * kWsEpiWarps) {
                 const int rl = q / (KOBJ + 1), k = q - rl * (KOBJ + 1), r = r0 + rl;
                 const float v = r < a.R ? (k < KOBJ ? a.lambda[(int64_t)r * KOBJ + k] : a.c0[r]) : 0.0f;
@@ -533,10 +435,11 @@ __global__ void __launch_bounds__(kWsThreads, 1)
             __syncwarp();
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&lready[b])) : "memory");
         };
-        stage_lambda(blockIdx.x, 0);
+        stage_lambda(cid, 0);
         int lt = 0;
-        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++lt) {
-            const int i0 = (t % n_ib) * kTileM, r0 = (t / n_ib) * kTileN;
+        for (int g = cid; g < n_groups; g += nclusters, ++lt) {
+            int i0, r0;
+            tile_of(g, i0, r0);
             const int i = i0 + quarter * 32 + lane;
             const int b = lt & 1;
             const bool got = __all_sync(0xffffffffu, mbar_wait(smem_u32(tfull), (uint32_t)(lt & 1)) &&
@@ -571,7 +474,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tempty)) : "memory");
-            if (t + (int)gridDim.x < n_tiles) stage_lambda(t + gridDim.x, b ^ 1);
+            if (g + nclusters < n_groups) stage_lambda(g + nclusters, b ^ 1);
             if (i < a.n) {
                 // one octet of columns per pass; the force of the next octet moves to f[0..7]
 #pragma unroll 1
@@ -618,6 +521,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     if (!ok) atomicOr(a.status, 1);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
+    if (CL > 1) cluster_sync();  // no CTA leaves while a peer may still write to it
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
@@ -1048,35 +952,37 @@ __global__ void k_dense_readout(int32_t n, int32_t np, int32_t R, int32_t W, con
 
 size_t dense_smem_bytes(int K) { return 1024 + dense_stages(K) * (size_t)(K + 1) * kTileBytes + (size_t)kTileN * (K + 1) * 4 + 64; }
 
+// grid: one CTA per SM (clusters of CL CTAs), at most one per tile group; `grid` carries the
+// spin-block and replica-block counts
 template <int VARIANT, int KOBJ, bool NOISE, int CL>
 cudaError_t launch_step(const moq_dense* d, const CUtensorMap& tm_phi, const DenseStepArgs& a, dim3 grid, cudaStream_t st)
 {
-    if (CL == 1) {  // persistent, warp-specialised form
-        auto k = k_dense_step_ws<VARIANT, KOBJ, NOISE>;
-        const size_t smem = ws_smem_bytes(KOBJ);
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        const int n_tiles = (int)(grid.x * grid.y);
-        k<<<std::min(n_tiles, d->sms), kWsThreads, smem, st>>>(d->tm_J, tm_phi, a, (int32_t)grid.x, n_tiles);
-        return cudaGetLastError();
-    }
-    auto k = k_dense_step<VARIANT, KOBJ, NOISE, CL>;
-    const size_t smem = dense_smem_bytes(KOBJ);
+    auto k = k_dense_step_ws<VARIANT, KOBJ, NOISE, CL>;
+    const size_t smem = ws_smem_bytes(KOBJ);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    const int n_groups = (int)(grid.x * (grid.y / CL));
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = dim3(kThreads);
+    cfg.blockDim = dim3(kWsThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 1;
-    attr[0].val.clusterDim.y = CL;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k, d->tm_J, tm_phi, a);
+    int clusters = d->sms / CL;
+    if (CL > 1) {
+        cfg.gridDim = dim3((unsigned)(clusters * CL));
+        int active = 0;
+        if (cudaOccupancyMaxActiveClusters(&active, k, &cfg) == cudaSuccess && active > 0) clusters = std::min(clusters, active);
+        (void)cudaGetLastError();
+    }
+    clusters = std::max(1, std::min(clusters, n_groups));
+    cfg.gridDim = dim3((unsigned)(clusters * CL));
+    return cudaLaunchKernelEx(&cfg, k, d->tm_J, tm_phi, a, (int32_t)grid.x, (int32_t)n_groups);
 }
 
 template <int VARIANT, bool NOISE, int CL>
@@ -1198,9 +1104,10 @@ int moq_dense_create(const moq_instance* inst, int32_t max_replicas, moq_dense**
     d->n_pad = (int)ceil_div(inst->n, kTileM) * kTileM;
     d->max_R = max_replicas;
     d->R_pad = (int)ceil_div(max_replicas, kTileN * kMaxCluster) * kTileN * kMaxCluster;
-    // J tiles multicast over clusters of 2 or 4 CTAs cut L2 reads but tie the CTAs of a
-    // cluster to each other's pace; at n = 2000, R = 8192 single CTAs measured fastest
-    // (204 us per step against 210 and 234), so clusters are opt-in (MOQ_DENSE_CLUSTER)
+    // J tiles multicast over clusters of 2 or 4 CTAs cut the L2 reads of J by 2 or 4 but tie
+    // the CTAs of a cluster to each other's pace; at n = 2000, R = 8192 (persistent kernel,
+    // same call) clusters of 1, 2, 4 measured 187-191, 188-189 and 198-200 us per step, so
+    // clusters are opt-in (MOQ_DENSE_CLUSTER)
     d->cluster = 1;
     {
         int dev = 0, sms = 0;
