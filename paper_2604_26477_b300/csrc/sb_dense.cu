@@ -665,7 +665,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool step_ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&bars[1]), (uint32_t)(m & 1)));
         asm volatile("tcgen05.fence::after_thread_sync;");
         const float cm = a.schedule ? (__ldg(a.schedule + m) - a.a0) : fmaf(a.a0inv, (float)m, -a.a0);
-        if (step_ok) {
+        if (step_ok && quarter * 32 < a.n) {  // warps of padding spins only (warp-uniform) have nothing to do
 #pragma unroll 1
             for (int cc = 0; cc < 2; ++cc) {
                 const int col0 = part * 32 + cc * 16;
