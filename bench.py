@@ -538,6 +538,7 @@ def paper_arm(args, rank, world):
             return trace, front, secs, ref
 
         res = {"weight_vectors": nw, "replicas_per_round": R}
+        run(alpha_paper, 1, seed=99)  # untimed: loads every kernel of the pipeline once
         tr_noise, front_noise, secs_noise, ref = run(alpha_paper, rounds)
         tr_plain, front_plain, _, _ = run(0.0, rounds)
         tr_rand, front_rand, _, _ = run(0.0, rounds, steps=0)  # uniform random configurations
@@ -567,7 +568,7 @@ def paper_arm(args, rank, world):
         res["reference_point"] = [int(v) for v in ref]
         out["instances"]["heavy_hex_like_n42_K%d" % K] = res
     return {"metric": METRIC, "value": total_units / total_s, "unit": METRIC, "n_gpus": world, "steps": rounds,
-            "warmup": 0, "ms_per_step": total_s / (2 * rounds) * 1e3, "higher_is_better": True, "scaling": "weak",
+            "warmup": 1, "ms_per_step": total_s / (2 * rounds) * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "paper protocol: heavy-hex-like n=42, K=3 (190 weights) and K=4 (220 weights) x "
                                    "3000 replicas, NI-dSB T=50 dt=1; value = spin updates of the noisy runs over "
