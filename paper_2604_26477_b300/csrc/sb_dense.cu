@@ -191,24 +191,19 @@ struct DenseStepArgs {
 };
 
 // The products G_k = A_k B^T of one 128 x 128 tile for every objective k, accumulated in
-// TMEM columns k * 128..: thread 0 is the TMA producer (A_k tiles shared by the CL CTAs of
-// a cluster, each loading 128 / CL rows and multicasting them; the B tile its own), thread
-// 32 issues the MMAs and releases each stage to every CTA of the cluster; `done` flips once
-// all products of this CTA are complete. Returns false on a timed-out wait (roles only).
-template <int KOBJ, int CL>
+// TMEM columns k * 128.. (the exact cut evaluation): thread 0 is the TMA producer, thread 32
+// issues the MMAs and releases each stage; `done` flips once all products are complete.
+// Returns false on a timed-out wait (role threads only).
+template <int KOBJ>
 __device__ __forceinline__ bool dense_products(const CUtensorMap* tmA, const CUtensorMap* tmB, uint32_t base, uint64_t* full,
-                                               uint64_t* empty, uint64_t* done, uint32_t tmem, int i0, int r0, int nchunks,
-                                               uint32_t rank)
+                                               uint64_t* empty, uint64_t* done, uint32_t tmem, int i0, int r0, int nchunks)
 {
     constexpr int kStageBytes = (KOBJ + 1) * kTileBytes;
     constexpr int S = dense_stages(KOBJ);
-    constexpr int kSliceRows = kTileM / CL;
-    constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
     const int tid = threadIdx.x;
     bool ok = true;
     if (tid == 0) {
-        // producer: chunk c goes to stage c % S once every CTA of the cluster has released
-        // the stage's previous contents (chunk c - S)
+        // producer: chunk c goes to stage c % S once the products of chunk c - S released it
         for (int c = 0; c < nchunks && ok; ++c) {
             const int st = c % S;
             if (c >= S && !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((c - S) / S) & 1))) {
@@ -219,14 +214,10 @@ __device__ __forceinline__ bool dense_products(const CUtensorMap* tmA, const CUt
             mbar_expect_tx(fb, (uint32_t)kStageBytes);
             const int j0 = c * kChunkK;
 #pragma unroll
-            for (int k = 0; k < KOBJ; ++k) {
-                const uint32_t dst = stage + k * kTileBytes + rank * (kSliceRows * kChunkK * 2);
-                if (CL > 1) tma_load_3d_mc(dst, tmA, j0, i0 + (int)rank * kSliceRows, k, fb, kMask);
-                else tma_load_3d(dst, tmA, j0, i0, k, fb);
-            }
+            for (int k = 0; k < KOBJ; ++k) tma_load_3d(stage + k * kTileBytes, tmA, j0, i0, k, fb);
             tma_load_2d(stage + KOBJ * kTileBytes, tmB, j0, r0, fb);
         }
-        // every peer's release of every stage has arrived before this CTA may leave
+        // the last release of every stage has arrived before this CTA may leave
         for (int st = 0; st < S && st < nchunks && ok; ++st) {
             const int c_last = st + ((nchunks - 1 - st) / S) * S;
             if (!mbar_wait(smem_u32(&empty[st]), (uint32_t)((c_last / S) & 1))) ok = false;
@@ -247,14 +238,8 @@ __device__ __forceinline__ bool dense_products(const CUtensorMap* tmA, const CUt
                 for (int ks = 0; ks < kChunkK / 16; ++ks)
                     mma_bf16(tmem + k * kTileN, sw128_desc(stage + k * kTileBytes + ks * 32),
                              sw128_desc(stage + KOBJ * kTileBytes + ks * 32), (c > 0 || ks > 0) ? 1u : 0u);
-            if (CL > 1)
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                                 smem_u32(&empty[st])),
-                             "h"(kMask)
-                             : "memory");
-            else
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&empty[st]))
-                             : "memory");
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&empty[st]))
+                         : "memory");
         }
         // the products of this CTA are complete once `done` flips
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(done)) : "memory");
@@ -799,7 +784,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
 
-    bool ok = dense_products<KOBJ, 1>(&tmA, &tmS, base, full, empty, done, tmem, i0, r0, np / kChunkK, 0u);
+    bool ok = dense_products<KOBJ>(&tmA, &tmS, base, full, empty, done, tmem, i0, r0, np / kChunkK);
     const bool products = mbar_wait(smem_u32(done), 0u);
     ok = __syncthreads_and(ok && products);
     asm volatile("tcgen05.fence::after_thread_sync;");
