@@ -276,7 +276,8 @@ def gpu_arm(args, rank, world):
     ops = ops_per_spin_update(2.0 * src.E / n)
     sample_avg = samp_s / args.steps
     achieved = ops * R * n * T / sample_avg / 1e12
-    roofline = {"bound": "alu", "kernel": "k_sb_sparse", "achieved": achieved, "peak": peak_alu_tops(),
+    roofline = {"bound": "alu", "kernel": "k_sb_sparse2 (two replicas per thread; k_sb_sparse where that keeps fewer in flight)",
+                "achieved": achieved, "peak": peak_alu_tops(),
                 "unit": "Tops/s", "frac": achieved / peak_alu_tops(),
                 "traffic": profile_traffic("sb_sparse.cu", "sb_sparse_precision_n42_K4.txt"),
                 "peak_source": "derived: 148 SMs x 128 FP32/INT32 lanes x 2032 MHz max SM clock",

@@ -269,6 +269,276 @@ cudaError_t launch_variant(const SbArgs& a, int dmax, bool noise, int pump, dim3
     }
 }
 
+
+// ---- two replicas per thread ------------------------------------------------------------
+// The same dynamics with each thread running spin i of two replicas (2q, 2q + 1) of its
+// block: the neighbour gathers fetch both replicas' phi in one 8-byte load (phi is stored
+// as a float2 per slot and pair), and the pump value, the barrier and the loop control are
+// shared by two updates. Each replica's arithmetic and noise counters are those of
+// k_sb_sparse, so both kernels give the same bits; the host takes this form when it keeps
+// more replicas in flight per SM (register and block limits, from the occupancy API).
+template <int VARIANT, int DMAX, bool NOISE>
+__device__ __forceinline__ void sb_step2(const float2* rd, float2* wr, int tid, const float (&jc0)[DMAX], const float (&jc1)[DMAX],
+                                         const int (&nb)[DMAX], float cm, float e0, float e1, float dt, float kappa, float dta0,
+                                         float& x0, float& y0, float& x1, float& y1)
+{
+    float f0 = 0.0f, f1 = 0.0f;
+#pragma unroll
+    for (int d = 0; d < DMAX; ++d) {
+        const float2 ph = rd[nb[d]];
+        f0 = fmaf(jc0[d], ph.x, f0);
+        f1 = fmaf(jc1[d], ph.y, f1);
+    }
+    sb_update<NOISE>(f0, cm, e0, dt, kappa, dta0, x0, y0);
+    sb_update<NOISE>(f1, cm, e1, dt, kappa, dta0, x1, y1);
+    wr[tid] = make_float2(phi_of<VARIANT>(x0), phi_of<VARIANT>(x1));
+    __syncthreads();
+}
+
+__host__ __device__ inline size_t sb_smem_bytes2(int Rb, int W, int pump_table_steps)
+{
+    return sizeof(float) * 4 * kPhiStride + align_up(sizeof(unsigned) * 2 * Rb, 16) +
+           align_up(sizeof(unsigned long long) * (size_t)Rb * W, 16) + sizeof(float) * (size_t)pump_table_steps;
+}
+
+template <int VARIANT, int DMAX, bool NOISE, int PUMP>
+__global__ void __launch_bounds__(1024) k_sb_sparse2(const SbArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = a.n, Rb = a.Rb, Rp = a.Rb >> 1;
+    float2* phiA = reinterpret_cast<float2*>(smem_raw);
+    float2* phiB = phiA + kPhiStride;
+    unsigned* red = reinterpret_cast<unsigned*>(phiB + kPhiStride);  // 2 * Rb
+    unsigned long long* wb = reinterpret_cast<unsigned long long*>(smem_raw + sizeof(float) * 4 * kPhiStride +
+                                                                   align_up(sizeof(unsigned) * 2 * Rb, 16));
+    float* pump_t = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(wb) +
+                                             align_up(sizeof(unsigned long long) * (size_t)Rb * a.W, 16));
+    const int tid = threadIdx.x;
+    const int slot = tid / Rp;
+    const int lp = tid - slot * Rp;
+    const int i = a.slot_spin[slot];
+    const int r0 = blockIdx.x * Rb + 2 * lp, r1 = r0 + 1;
+    const bool act0 = r0 < a.R, act1 = r1 < a.R;
+    const int rs0 = act0 ? r0 : 0, rs1 = act1 ? r1 : 0;
+    float lam0[kMaxK], lam1[kMaxK];
+#pragma unroll
+    for (int k = 0; k < kMaxK; ++k) {
+        lam0[k] = (k < a.K) ? a.lambda[(int64_t)rs0 * a.K + k] : 0.0f;
+        lam1[k] = (k < a.K) ? a.lambda[(int64_t)rs1 * a.K + k] : 0.0f;
+    }
+    const int p0 = a.rowptr[i];
+    const int deg = a.rowptr[i + 1] - p0;
+    float jc0[DMAX], jc1[DMAX];
+    int nb[DMAX];
+    float sabs0 = 0.0f, sabs1 = 0.0f;
+#pragma unroll
+    for (int d = 0; d < DMAX; ++d) {
+        float v0 = 0.0f, v1 = 0.0f;
+        int c = i;
+        if (d < deg) {
+            const int p = p0 + d;
+            c = a.col[p];
+#pragma unroll
+            for (int k = 0; k < kMaxK; ++k)
+                if (k < a.K) {
+                    const float w = (float)a.wn[(int64_t)k * a.nnz + p];
+                    v0 = fmaf(lam0[k], w, v0);
+                    v1 = fmaf(lam1[k], w, v1);
+                }
+        }
+        jc0[d] = v0;
+        jc1[d] = v1;
+        nb[d] = a.spin_slot[c] * Rp + lp;
+        sabs0 += fabsf(v0);
+        sabs1 += fabsf(v1);
+    }
+    float srow0 = 0.0f, srow1 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kMaxK; ++k)
+        if (k < a.K) {
+            const float w = (float)a.rowsum[(int64_t)i * a.K + k];
+            srow0 = fmaf(lam0[k], w, srow0);
+            srow1 = fmaf(lam1[k], w, srow1);
+        }
+    if (tid < 2 * Rb) red[tid] = 0u;
+    __syncthreads();
+    atomicMax(&red[2 * lp], __float_as_uint(fabsf(srow0)));
+    atomicMax(&red[2 * lp + 1], __float_as_uint(fabsf(srow1)));
+    atomicMax(&red[Rb + 2 * lp], __float_as_uint(sabs0));
+    atomicMax(&red[Rb + 2 * lp + 1], __float_as_uint(sabs1));
+    __syncthreads();
+    {
+        const float mx0 = __uint_as_float(red[2 * lp]), mxa0 = __uint_as_float(red[Rb + 2 * lp]);
+        const float mx1 = __uint_as_float(red[2 * lp + 1]), mxa1 = __uint_as_float(red[Rb + 2 * lp + 1]);
+        const float c00 = mx0 > 0.0f ? 1.0f / mx0 : (mxa0 > 0.0f ? 1.0f / mxa0 : 1.0f);
+        const float c01 = mx1 > 0.0f ? 1.0f / mx1 : (mxa1 > 0.0f ? 1.0f / mxa1 : 1.0f);
+#pragma unroll
+        for (int d = 0; d < DMAX; ++d) {
+            jc0[d] *= -c00;
+            jc1[d] *= -c01;
+        }
+    }
+    float x0, y0, x1, y1;
+    if (a.x_init) {
+        x0 = (act0 ? a.x_init[(int64_t)r0 * n + i] : 0.0f) + 0.0f;
+        y0 = (act0 && a.y_init) ? a.y_init[(int64_t)r0 * n + i] : 0.0f;
+        x1 = (act1 ? a.x_init[(int64_t)r1 * n + i] : 0.0f) + 0.0f;
+        y1 = (act1 && a.y_init) ? a.y_init[(int64_t)r1 * n + i] : 0.0f;
+    } else {
+        const uint4 o0 = Philox4x32::block(make_uint4(0xFFFFFFFFu, (uint32_t)i, a.rep_off + (uint32_t)r0, a.round32), a.key0, a.key1);
+        const uint4 o1 = Philox4x32::block(make_uint4(0xFFFFFFFFu, (uint32_t)i, a.rep_off + (uint32_t)r1, a.round32), a.key0, a.key1);
+        x0 = __fmul_rn(a.init_amp, signed_unit(o0.x)) + 0.0f;
+        y0 = __fmul_rn(a.init_amp, signed_unit(o0.y));
+        x1 = __fmul_rn(a.init_amp, signed_unit(o1.x)) + 0.0f;
+        y1 = __fmul_rn(a.init_amp, signed_unit(o1.y));
+    }
+    phiA[tid] = make_float2(phi_of<VARIANT>(x0), phi_of<VARIANT>(x1));
+    __syncthreads();
+    const float dt = a.dt, kappa = a.kappa, dta0 = a.dt * a.a0, a0 = a.a0, a0inv = a.a0inv;
+    const float* sched = a.schedule;
+    const int T = a.T;
+    if (PUMP == kPumpTable) {
+        for (int q = tid; q < T; q += blockDim.x) pump_t[q] = fmaf(a0inv, (float)q, -a0);
+        __syncthreads();
+    }
+    auto cm_at = [&](int m, float mf) -> float {
+        return PUMP == kPumpTable ? pump_t[m] : (PUMP == kPumpInline ? fmaf(a0inv, mf, -a0) : (__ldg(sched + m) - a0));
+    };
+    auto block8 = [&](int m, int r) -> uint4 {
+        return NOISE ? Philox4x32::block(make_uint4((uint32_t)(m >> 3), (uint32_t)i, a.rep_off + (uint32_t)r, a.round32), a.key0, a.key1)
+                     : make_uint4(0u, 0u, 0u, 0u);
+    };
+    auto noise4 = [&](uint32_t wa, uint32_t wbb, float (&e)[4]) {
+        if (NOISE) {
+            const float2 p = box_muller16(wa), q = box_muller16(wbb);
+            e[0] = p.x; e[1] = p.y; e[2] = q.x; e[3] = q.y;
+        }
+    };
+    auto step = [&](const float2* rd, float2* wr, float cm, float e0, float e1) {
+        sb_step2<VARIANT, DMAX, NOISE>(rd, wr, tid, jc0, jc1, nb, cm, e0, e1, dt, kappa, dta0, x0, y0, x1, y1);
+    };
+    auto four_steps = [&](int m, float mf, const float (&e)[4], const float (&g)[4]) {
+        step(phiA, phiB, cm_at(m, mf), e[0], g[0]);
+        step(phiB, phiA, cm_at(m + 1, mf + 1.0f), e[1], g[1]);
+        step(phiA, phiB, cm_at(m + 2, mf + 2.0f), e[2], g[2]);
+        step(phiB, phiA, cm_at(m + 3, mf + 3.0f), e[3], g[3]);
+    };
+    auto noise_at = [&](int m, float (&e)[4], float (&g)[4]) {
+        if (NOISE) {
+            const uint4 o = block8(m, r0), q = block8(m, r1);
+            noise4((m & 4) ? o.z : o.x, (m & 4) ? o.w : o.y, e);
+            noise4((m & 4) ? q.z : q.x, (m & 4) ? q.w : q.y, g);
+        }
+    };
+    int m = 0;
+    float mf = 0.0f;
+    if (NOISE) {
+        for (; m + 8 <= T; m += 8) {
+            const uint4 o = block8(m, r0), q = block8(m, r1);
+            float e[4], g[4];
+            noise4(o.x, o.y, e);
+            noise4(q.x, q.y, g);
+            four_steps(m, mf, e, g);
+            noise4(o.z, o.w, e);
+            noise4(q.z, q.w, g);
+            four_steps(m + 4, mf + 4.0f, e, g);
+            mf += 8.0f;
+        }
+    }
+    for (; m + 4 <= T; m += 4) {
+        float e[4] = {0.0f, 0.0f, 0.0f, 0.0f}, g[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        noise_at(m, e, g);
+        four_steps(m, mf, e, g);
+        mf += 4.0f;
+    }
+    if (m < T) {
+        float e[4] = {0.0f, 0.0f, 0.0f, 0.0f}, g[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        noise_at(m, e, g);
+        step(phiA, phiB, cm_at(m, mf), e[0], g[0]);
+        if (m + 1 < T) step(phiB, phiA, cm_at(m + 1, mf + 1.0f), e[1], g[1]);
+        if (m + 2 < T) step(phiA, phiB, cm_at(m + 2, mf + 2.0f), e[2], g[2]);
+    }
+    const int W = a.W;
+    for (int t = tid; t < Rb * W; t += blockDim.x) wb[t] = 0ull;
+    __syncthreads();
+    if (x0 < 0.0f) atomicOr(&wb[(2 * lp) * W + (i >> 6)], 1ull << (i & 63));
+    if (x1 < 0.0f) atomicOr(&wb[(2 * lp + 1) * W + (i >> 6)], 1ull << (i & 63));
+    __syncthreads();
+    for (int t = tid; t < Rb * W; t += blockDim.x) {
+        const int r2 = blockIdx.x * Rb + t / W;
+        if (r2 < a.R) a.bits[(int64_t)r2 * W + (t % W)] = wb[t];
+    }
+    if (act0) {
+        if (a.x_out) a.x_out[(int64_t)r0 * n + i] = x0;
+        if (a.y_out) a.y_out[(int64_t)r0 * n + i] = y0;
+    }
+    if (act1) {
+        if (a.x_out) a.x_out[(int64_t)r1 * n + i] = x1;
+        if (a.y_out) a.y_out[(int64_t)r1 * n + i] = y1;
+    }
+}
+
+template <int VARIANT, int DMAX, bool NOISE, int PUMP>
+cudaError_t launch_one2(const SbArgs& a, dim3 grid, dim3 block, size_t smem, cudaStream_t st)
+{
+    auto k = k_sb_sparse2<VARIANT, DMAX, NOISE, PUMP>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, block, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int VARIANT, int DMAX, bool NOISE>
+cudaError_t launch_pump2(const SbArgs& a, int pump, dim3 grid, dim3 block, size_t smem, cudaStream_t st)
+{
+    switch (pump) {
+    case kPumpTable: return launch_one2<VARIANT, DMAX, NOISE, kPumpTable>(a, grid, block, smem, st);
+    case kPumpInline: return launch_one2<VARIANT, DMAX, NOISE, kPumpInline>(a, grid, block, smem, st);
+    default: return launch_one2<VARIANT, DMAX, NOISE, kPumpSchedule>(a, grid, block, smem, st);
+    }
+}
+
+// pairs for degree bounds 3 and 4 only: from 8 up, two rows of J(c) no longer fit in registers
+template <int VARIANT>
+cudaError_t launch_variant2(const SbArgs& a, int dmax, bool noise, int pump, dim3 grid, dim3 block, size_t smem, cudaStream_t st)
+{
+    switch (dmax) {
+    case 3: return noise ? launch_pump2<VARIANT, 3, true>(a, pump, grid, block, smem, st) : launch_pump2<VARIANT, 3, false>(a, pump, grid, block, smem, st);
+    case 4: return noise ? launch_pump2<VARIANT, 4, true>(a, pump, grid, block, smem, st) : launch_pump2<VARIANT, 4, false>(a, pump, grid, block, smem, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// the kernel instance a launch would use (for the occupancy query)
+template <int VARIANT, int DMAX, bool NOISE>
+const void* kernel_of(bool pair, int pump)
+{
+    if (DMAX <= 4 && pair) {
+        switch (pump) {
+        case kPumpTable: return (const void*)k_sb_sparse2<VARIANT, (DMAX <= 4 ? DMAX : 4), NOISE, kPumpTable>;
+        case kPumpInline: return (const void*)k_sb_sparse2<VARIANT, (DMAX <= 4 ? DMAX : 4), NOISE, kPumpInline>;
+        default: return (const void*)k_sb_sparse2<VARIANT, (DMAX <= 4 ? DMAX : 4), NOISE, kPumpSchedule>;
+        }
+    }
+    switch (pump) {
+    case kPumpTable: return (const void*)k_sb_sparse<VARIANT, DMAX, NOISE, kPumpTable>;
+    case kPumpInline: return (const void*)k_sb_sparse<VARIANT, DMAX, NOISE, kPumpInline>;
+    default: return (const void*)k_sb_sparse<VARIANT, DMAX, NOISE, kPumpSchedule>;
+    }
+}
+
+template <int VARIANT>
+const void* kernel_of_variant(int dmax, bool noise, bool pair, int pump)
+{
+    switch (dmax) {
+    case 3: return noise ? kernel_of<VARIANT, 3, true>(pair, pump) : kernel_of<VARIANT, 3, false>(pair, pump);
+    case 4: return noise ? kernel_of<VARIANT, 4, true>(pair, pump) : kernel_of<VARIANT, 4, false>(pair, pump);
+    case 8: return noise ? kernel_of<VARIANT, 8, true>(pair, pump) : kernel_of<VARIANT, 8, false>(pair, pump);
+    default: return noise ? kernel_of<VARIANT, 16, true>(pair, pump) : kernel_of<VARIANT, 16, false>(pair, pump);
+    }
+}
+
+
 // Replicas per block: among blocks of up to about 256 threads, the one whose warps are
 // fullest (n * Rb close to a multiple of 32), the smaller block on ties -- small blocks hide
 // each other's step barriers (measured at n = 42: 126-thread blocks 1.76 ms, 252-thread
@@ -341,19 +611,66 @@ extern "C" int moq_sample(const moq_instance* inst, const float* lambda, int32_t
     a.round32 = (uint32_t)round;
     a.rep_off = p->replica_offset;
     a.bits = bits;
-    a.Rb = choose_rb(a.n, R);
     const int md = inst->max_degree;
     const int dmax = md <= 3 ? 3 : (md <= 4 ? 4 : (md <= 8 ? 8 : 16));
-    const dim3 block(a.n * a.Rb), grid((unsigned)ceil_div(R, a.Rb));
     const bool noise = p->alpha != 0.0f;
-    // the table trades a multiply-add for a shared-memory load: a gain for small blocks, a
+    // Block shape of either form: replicas per block, threads, pump source, shared memory.
+    // The table trades a multiply-add for a shared-memory load: a gain for small blocks, a
     // loss for blocks of more than 256 threads, whose gathers already keep the shared-memory
-    // pipe busy (measured: n = 42..150 3-5 % faster, n = 300..1024 2-5 % slower)
-    const bool small_block = a.n * a.Rb <= kPumpTableMaxThreads;
-    const int pump = p->schedule ? kPumpSchedule : (a.T <= kPumpTableMax && small_block ? kPumpTable : kPumpInline);
-    const size_t smem = sb_smem_bytes(a.Rb, a.W, pump == kPumpTable ? a.T : 0);
-    cudaError_t e = (p->variant == MOQ_DSB) ? launch_variant<MOQ_DSB>(a, dmax, noise, pump, grid, block, smem, as_stream(stream))
-                                            : launch_variant<MOQ_BSB>(a, dmax, noise, pump, grid, block, smem, as_stream(stream));
+    // pipe busy (measured: n = 42..150 3-5 % faster, n = 300..1024 2-5 % slower).
+    struct Shape {
+        int Rb, threads, pump;
+        size_t smem;
+    };
+    auto shape_of = [&](bool pair) {
+        Shape sh;
+        if (pair) {
+            const int Rp = choose_rb(a.n, (R + 1) / 2);
+            sh.Rb = 2 * Rp;
+            sh.threads = a.n * Rp;
+        } else {
+            sh.Rb = choose_rb(a.n, R);
+            sh.threads = a.n * sh.Rb;
+        }
+        sh.pump = p->schedule ? kPumpSchedule : (a.T <= kPumpTableMax && sh.threads <= kPumpTableMaxThreads ? kPumpTable : kPumpInline);
+        sh.smem = pair ? sb_smem_bytes2(sh.Rb, a.W, sh.pump == kPumpTable ? a.T : 0) : sb_smem_bytes(sh.Rb, a.W, sh.pump == kPumpTable ? a.T : 0);
+        return sh;
+    };
+    const Shape one = shape_of(false), two = shape_of(true);
+    // two replicas per thread (degree bound <= 4) when that keeps more replicas in flight per
+    // SM (n = 42: 8 blocks of 6 against 10 of 3; n = 1024: one block either way; n = 600: 2
+    // against 2, where the one-replica form hides latency with twice the warps);
+    // MOQ_SB_PAIR = 0 / 1 forces a form
+    bool pair = false;
+    {
+        auto resident = [&](bool pr, const Shape& sh) -> int {
+            const void* k = p->variant == MOQ_DSB ? kernel_of_variant<MOQ_DSB>(dmax, noise, pr, sh.pump)
+                                                  : kernel_of_variant<MOQ_BSB>(dmax, noise, pr, sh.pump);
+            int blocks = 0;
+            if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, sh.threads, sh.smem) != cudaSuccess) {
+                (void)cudaGetLastError();
+                return 0;
+            }
+            return blocks * sh.Rb;
+        };
+        pair = R > 1 && dmax <= 4 && resident(true, two) > resident(false, one);
+        if (const char* env = getenv("MOQ_SB_PAIR")) {
+            const int v = atoi(env);
+            if (v == 0) pair = false;
+            if (v == 1 && dmax <= 4) pair = true;
+        }
+    }
+    const Shape& sh = pair ? two : one;
+    a.Rb = sh.Rb;
+    const dim3 block(sh.threads), grid((unsigned)ceil_div(R, sh.Rb));
+    cudaError_t e;
+    if (pair)
+        e = (p->variant == MOQ_DSB) ? launch_variant2<MOQ_DSB>(a, dmax, noise, sh.pump, grid, block, sh.smem, as_stream(stream))
+                                    : launch_variant2<MOQ_BSB>(a, dmax, noise, sh.pump, grid, block, sh.smem, as_stream(stream));
+    else
+        e = (p->variant == MOQ_DSB) ? launch_variant<MOQ_DSB>(a, dmax, noise, sh.pump, grid, block, sh.smem, as_stream(stream))
+                                    : launch_variant<MOQ_BSB>(a, dmax, noise, sh.pump, grid, block, sh.smem, as_stream(stream));
     if (e != cudaSuccess) return cuda_fail(e, "moq_sample launch");
     return MOQ_OK;
 }

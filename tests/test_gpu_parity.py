@@ -464,6 +464,39 @@ def test_replica_shards_reproduce_one_call(M, P, world):
         assert torch.equal(part, whole[first:first + count])
 
 
+@pytest.mark.parametrize("name,R,T,variant,alpha,sched,state", [
+    ("heavyhex_K4", 1001, 203, "dsb", 0.1, False, False), ("heavyhex_K3", 77, 96, "bsb", 0.1, True, True),
+    ("heavyhex_K4", 2, 13, "dsb", 0.0, False, True), ("reg3_n1024_K3", 9, 64, "dsb", 0.15, False, False),
+    ("reg4_n300_K3", 31, 101, "bsb", 0.0, False, False), ("reg3_n150_K3", 5, 42, "dsb", 0.1, False, True)])
+def test_replica_pairs_match_single_replica_threads(M, P, monkeypatch, name, R, T, variant, alpha, sched, state):
+    # the sampler form with two replicas per thread (float2 gathers, shared pump and barrier)
+    # and the one-replica form give the same samples and final x, y bit for bit: odd and tiny
+    # R (a half-empty last pair), step counts with tails, both variants, with and without
+    # noise, an explicit pump, caller start states, degree bounds 3 and 4
+    src = wl.random_regular(300, 9, K=3, d=4) if name == "reg4_n300_K3" else INSTANCES[name]()
+    inst = P.Instance(src)
+    n = src.n
+    lam = _dev(wl.dirichlet_lambdas(R, src.K, 6), torch.float32)
+    schedule = torch.linspace(0.0, 1.0, T, device="cuda") ** 0.5 if sched else None
+    rng = np.random.default_rng(8)
+    x0 = _dev(rng.uniform(-0.2, 0.2, (R, n)), torch.float32) if state else None
+    y0 = _dev(rng.uniform(-0.1, 0.1, (R, n)), torch.float32) if state else None
+    out = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("MOQ_SB_PAIR", mode)
+        xo = torch.zeros((R, n), device="cuda")
+        yo = torch.zeros((R, n), device="cuda")
+        bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+        p = M.moq_default_params(variant=variant, steps=T, dt=0.5, alpha=alpha, schedule=schedule, x_init=x0, y_init=y0,
+                                 x_out=xo, y_out=yo, replica_offset=3)
+        M.moq_sample(inst.handle, lam, R, p, 21, 4, bits)
+        torch.cuda.synchronize()
+        out[mode] = (bits.cpu(), xo.cpu(), yo.cpu())
+    for a, b in zip(out["1"], out["0"]):
+        assert torch.equal(a, b)
+    assert R < 3 or len(torch.unique(out["1"][0], dim=0)) > 1
+
+
 @pytest.mark.parametrize("variant", ["dsb", "bsb"])
 def test_bipartite_reaches_max_cut(M, P, variant):
     rows, cols = 6, 7
