@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(1024) k_sb_sparse2(const SbArgs a)
             srow0 = fmaf(lam0[k], w, srow0);
             srow1 = fmaf(lam1[k], w, srow1);
         }
-    if (tid < 2 * Rb) red[tid] = 0u;
+    for (int q = tid; q < 2 * Rb; q += blockDim.x) red[q] = 0u;  // 2 Rb = 4 Rp may exceed n Rp threads (n < 4)
     __syncthreads();
     atomicMax(&red[2 * lp], __float_as_uint(fabsf(srow0)));
     atomicMax(&red[2 * lp + 1], __float_as_uint(fabsf(srow1)));

@@ -467,13 +467,20 @@ def test_replica_shards_reproduce_one_call(M, P, world):
 @pytest.mark.parametrize("name,R,T,variant,alpha,sched,state", [
     ("heavyhex_K4", 1001, 203, "dsb", 0.1, False, False), ("heavyhex_K3", 77, 96, "bsb", 0.1, True, True),
     ("heavyhex_K4", 2, 13, "dsb", 0.0, False, True), ("reg3_n1024_K3", 9, 64, "dsb", 0.15, False, False),
-    ("reg4_n300_K3", 31, 101, "bsb", 0.0, False, False), ("reg3_n150_K3", 5, 42, "dsb", 0.1, False, True)])
+    ("reg4_n300_K3", 31, 101, "bsb", 0.0, False, False), ("reg3_n150_K3", 5, 42, "dsb", 0.1, False, True),
+    ("triangle_K2", 301, 50, "dsb", 0.2, False, False)])
 def test_replica_pairs_match_single_replica_threads(M, P, monkeypatch, name, R, T, variant, alpha, sched, state):
     # the sampler form with two replicas per thread (float2 gathers, shared pump and barrier)
     # and the one-replica form give the same samples and final x, y bit for bit: odd and tiny
     # R (a half-empty last pair), step counts with tails, both variants, with and without
     # noise, an explicit pump, caller start states, degree bounds 3 and 4
-    src = wl.random_regular(300, 9, K=3, d=4) if name == "reg4_n300_K3" else INSTANCES[name]()
+    if name == "reg4_n300_K3":
+        src = wl.random_regular(300, 9, K=3, d=4)
+    elif name == "triangle_K2":  # n = 3: blocks of 3 Rp threads hold 4 Rp reduction slots
+        src = wl.Instance(3, np.array([0, 0, 1], np.int32), np.array([1, 2, 2], np.int32),
+                          np.array([[3, -2, 5], [1, 4, -2]], np.int32))
+    else:
+        src = INSTANCES[name]()
     inst = P.Instance(src)
     n = src.n
     lam = _dev(wl.dirichlet_lambdas(R, src.K, 6), torch.float32)
