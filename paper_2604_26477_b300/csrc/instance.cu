@@ -205,30 +205,31 @@ void graph_features(int n, int K, int64_t E, const long long* sums, const long l
 void free_instance(moq_instance* h)
 {
     if (!h) return;
-    cudaFree(h->ei);
-    cudaFree(h->ej);
-    cudaFree(h->w);
-    cudaFree(h->rowptr);
-    cudaFree(h->col);
-    cudaFree(h->wn);
-    cudaFree(h->rowsum);
-    cudaFree(h->slot_spin);
-    cudaFree(h->spin_slot);
+    slab_free(h->slab);
     delete h;
 }
 
-template <class T>
-int dalloc(T** p, int64_t count)
-{
-    *p = nullptr;
-    if (count <= 0) count = 1;
-    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (size_t)count);
-    if (e != cudaSuccess) {
-        *p = nullptr;
-        return cuda_fail(e, "cudaMalloc");
+// Offsets of the arrays of one slab, rounded to 256 bytes; place() fills the pointers once the
+// slab exists.
+struct SlabPlan {
+    std::vector<std::pair<void**, size_t>> parts;
+    template <class T>
+    void add(T** p, int64_t count) { parts.emplace_back((void**)p, sizeof(T) * (size_t)std::max<int64_t>(count, 1)); }
+    size_t bytes() const
+    {
+        size_t t = 0;
+        for (auto& pr : parts) t += slab_align(pr.second);
+        return t;
     }
-    return MOQ_OK;
-}
+    void place(void* slab) const
+    {
+        size_t off = 0;
+        for (auto& pr : parts) {
+            *pr.first = static_cast<char*>(slab) + off;
+            off += slab_align(pr.second);
+        }
+    }
+};
 
 }  // namespace
 }  // namespace moq
@@ -257,26 +258,50 @@ int moq_create_instance(int32_t n, int32_t K, int64_t E, const int32_t* ei, cons
 
     int32_t *deg = nullptr, *cursor = nullptr, *col_tmp = nullptr, *eid_tmp = nullptr, *eid = nullptr, *status = nullptr;
     unsigned long long* sums = nullptr;
+    void* tmp_slab = nullptr;
     int rc = MOQ_OK;
-    auto cleanup_tmp = [&]() {
-        cudaFree(deg); cudaFree(cursor); cudaFree(col_tmp); cudaFree(eid_tmp); cudaFree(eid); cudaFree(status); cudaFree(sums);
-    };
+    auto cleanup_tmp = [&]() { slab_free_async(tmp_slab, st); };
 #define MOQ_STEP(x) do { rc = (x); if (rc != MOQ_OK) { cleanup_tmp(); free_instance(h); return rc; } } while (0)
-    MOQ_STEP(dalloc(&h->ei, E));
-    MOQ_STEP(dalloc(&h->ej, E));
-    MOQ_STEP(dalloc(&h->w, K * E));
-    MOQ_STEP(dalloc(&h->rowptr, n + 1));
-    MOQ_STEP(dalloc(&h->col, h->nnz));
-    MOQ_STEP(dalloc(&h->wn, K * h->nnz));
-    MOQ_STEP(dalloc(&h->rowsum, (int64_t)n * K));
-    MOQ_STEP(dalloc(&deg, n + 1));
-    MOQ_STEP(dalloc(&cursor, n));
-    MOQ_STEP(dalloc(&col_tmp, h->nnz));
-    MOQ_STEP(dalloc(&eid_tmp, h->nnz));
-    MOQ_STEP(dalloc(&eid, h->nnz));
-    MOQ_STEP(dalloc(&status, 2));
+    // sampler slots in order of decreasing degree (stable), so that warps of the on-chip
+    // sampler hold spins of equal degree where the graph allows it (host side, from the
+    // edge list; validated on the device below)
+    std::vector<int32_t> order(n), inv(n);
+    {
+        std::vector<int32_t> dgr(n, 0);
+        for (int64_t e = 0; e < E; ++e) {
+            if (ei[e] >= 0 && ei[e] < n) ++dgr[ei[e]];
+            if (ej[e] >= 0 && ej[e] < n) ++dgr[ej[e]];
+        }
+        for (int32_t i = 0; i < n; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return dgr[a] > dgr[b]; });
+        for (int32_t q = 0; q < n; ++q) inv[order[q]] = q;
+    }
     const int nmom = 2 * K + K * (K - 1) / 2;  // weight moments after the 3K sums
-    MOQ_STEP(dalloc(&sums, 3 * K + nmom));
+    SlabPlan keep, tmp;
+    keep.add(&h->ei, E);
+    keep.add(&h->ej, E);
+    keep.add(&h->w, K * E);
+    keep.add(&h->rowptr, n + 1);
+    keep.add(&h->col, h->nnz);
+    keep.add(&h->wn, K * h->nnz);
+    keep.add(&h->rowsum, (int64_t)n * K);
+    keep.add(&h->slot_spin, n);
+    keep.add(&h->spin_slot, n);
+    tmp.add(&deg, n + 1);
+    tmp.add(&cursor, n);
+    tmp.add(&col_tmp, h->nnz);
+    tmp.add(&eid_tmp, h->nnz);
+    tmp.add(&eid, h->nnz);
+    tmp.add(&status, 2);
+    tmp.add(&sums, 3 * K + nmom);
+    {
+        cudaError_t e = slab_alloc(&h->slab, keep.bytes(), st);
+        if (e != cudaSuccess) MOQ_STEP(cuda_fail(e, "moq_create_instance"));
+        keep.place(h->slab);
+        e = slab_alloc(&tmp_slab, tmp.bytes(), st);
+        if (e != cudaSuccess) MOQ_STEP(cuda_fail(e, "moq_create_instance"));
+        tmp.place(tmp_slab);
+    }
 
     auto cu = [&](cudaError_t e, const char* what) { return e == cudaSuccess ? MOQ_OK : cuda_fail(e, what); };
     if (E > 0) {
@@ -284,6 +309,8 @@ int moq_create_instance(int32_t n, int32_t K, int64_t E, const int32_t* ei, cons
         MOQ_STEP(cu(cudaMemcpyAsync(h->ej, ej, sizeof(int32_t) * E, cudaMemcpyHostToDevice, st), "copy ej"));
         MOQ_STEP(cu(cudaMemcpyAsync(h->w, w, sizeof(int32_t) * K * E, cudaMemcpyHostToDevice, st), "copy w"));
     }
+    MOQ_STEP(cu(cudaMemcpyAsync(h->slot_spin, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st), "copy slot order"));
+    MOQ_STEP(cu(cudaMemcpyAsync(h->spin_slot, inv.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st), "copy slot order"));
     MOQ_STEP(cu(cudaMemsetAsync(deg, 0, sizeof(int32_t) * (n + 1), st), "memset"));
     MOQ_STEP(cu(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * n, st), "memset"));
     MOQ_STEP(cu(cudaMemsetAsync(status, 0, sizeof(int32_t) * 2, st), "memset"));
@@ -329,26 +356,6 @@ int moq_create_instance(int32_t n, int32_t K, int64_t E, const int32_t* ei, cons
         inf.ref_point[k] = hsums[2 * K + k];
     }
     graph_features(n, K, E, hsums, hsums + 3 * K, inf.features);
-    // sampler slots in order of decreasing degree (stable), so that warps of the on-chip
-    // sampler hold spins of equal degree where the graph allows it
-    {
-        std::vector<int32_t> dgr(n, 0), order(n), inv(n);
-        for (int64_t e = 0; e < E; ++e) {
-            ++dgr[ei[e]];
-            ++dgr[ej[e]];
-        }
-        for (int32_t i = 0; i < n; ++i) order[i] = i;
-        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return dgr[a] > dgr[b]; });
-        for (int32_t q = 0; q < n; ++q) inv[order[q]] = q;
-        cudaError_t e = cudaMalloc((void**)&h->slot_spin, sizeof(int32_t) * n);
-        if (e == cudaSuccess) e = cudaMalloc((void**)&h->spin_slot, sizeof(int32_t) * n);
-        if (e == cudaSuccess) e = cudaMemcpy(h->slot_spin, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(h->spin_slot, inv.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) {
-            free_instance(h);
-            return cuda_fail(e, "moq_create_instance slot order");
-        }
-    }
     *out = h;
     return MOQ_OK;
 }

@@ -30,6 +30,18 @@ int cuda_fail(cudaError_t err, const char* what);
 
 inline cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
+// ---- handle memory (pool.cu) ----------------------------------------------------------
+// One device slab per handle and lifetime class from a library-owned memory pool that keeps
+// freed memory; slab_alloc is ordered on `st`; slab_free waits for the device first,
+// slab_free_async frees in the order of `st` (a slab only `st` used). Pinned
+// 64-byte host slots for read-backs. Offsets inside a slab are rounded up with slab_align.
+size_t slab_align(size_t bytes);
+cudaError_t slab_alloc(void** p, size_t bytes, cudaStream_t st);
+void slab_free(void* p);
+void slab_free_async(void* p, cudaStream_t st);  // once everything queued on st before it is done
+cudaError_t pinned_slot_alloc(void** p);
+void pinned_slot_free(void* p);
+
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // Device status bits latched by kernels and read back by synchronising calls.
@@ -118,6 +130,7 @@ struct moq_instance {
     int64_t* rowsum = nullptr;  // n x K integer row sums sum_j J^(k)_ij
     int32_t* slot_spin = nullptr;  // sampler slot -> spin, by decreasing degree
     int32_t* spin_slot = nullptr;  // spin -> sampler slot
+    void* slab = nullptr;          // the one device allocation the arrays above live in
     moq_instance_info info{};
 };
 
@@ -144,5 +157,6 @@ struct moq_archive {
     int64_t large_min = 0;         // batches from this size take the dedup / survivor path
     int64_t n_blocksum = 0;
     void* hv_ws = nullptr;         // hypervolume workspace sized for cap
-    int64_t* h_pinned = nullptr;   // pinned host words for read-backs
+    int64_t* h_pinned = nullptr;   // pinned host words for read-backs (one 64-byte slot)
+    void* slab = nullptr;          // the one device allocation all arrays above live in
 };

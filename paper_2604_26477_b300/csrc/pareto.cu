@@ -25,6 +25,8 @@
 #include <algorithm>
 #include <stdlib.h>
 
+#include <vector>
+
 #include "moq_common.cuh"
 
 namespace moq {
@@ -591,24 +593,8 @@ int read_status(const moq_archive* a, cudaStream_t st, int64_t* size_out)
 void free_archive(moq_archive* a)
 {
     if (!a) return;
-    for (int b = 0; b < 2; ++b) {
-        cudaFree(a->cuts[b]);
-        cudaFree(a->bits[b]);
-        cudaFree(a->index[b]);
-    }
-    cudaFree(a->d_count);
-    cudaFree(a->d_status);
-    cudaFree(a->flag_arch);
-    cudaFree(a->flag_cand);
-    cudaFree(a->blocksum);
-    cudaFree(a->range);
-    cudaFree(a->table);
-    cudaFree(a->ccuts);
-    cudaFree(a->cidx);
-    cudaFree(a->cflag);
-    cudaFree(a->d_m);
-    cudaFree(a->hv_ws);
-    if (a->h_pinned) cudaFreeHost(a->h_pinned);
+    slab_free(a->slab);
+    pinned_slot_free(a->h_pinned);
     delete a;
 }
 
@@ -632,8 +618,9 @@ int moq_archive_create(int32_t n, int32_t K, int64_t capacity, int64_t max_batch
     a->max_batch = max_batch;
     cudaGetDevice(&a->device);
     a->n_blocksum = ceil_div(capacity, kScanBlock) + ceil_div(max_batch, kScanBlock) + 1;
-    cudaError_t e = cudaSuccess;
-    auto al = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
+    // every device array in one slab: the offsets first, then one allocation
+    std::vector<std::pair<void**, size_t>> parts;
+    auto al = [&](void** p, size_t bytes) { parts.emplace_back(p, bytes); };
     for (int b = 0; b < 2; ++b) {
         al((void**)&a->cuts[b], sizeof(int64_t) * capacity * K);
         al((void**)&a->bits[b], sizeof(uint64_t) * capacity * a->W);
@@ -658,10 +645,21 @@ int moq_archive_create(int32_t n, int32_t K, int64_t capacity, int64_t max_batch
         al((void**)&a->d_m, sizeof(int64_t));
     }
     al(&a->hv_ws, (size_t)moq_hypervolume_workspace_size(capacity, K));
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&a->h_pinned, 64);
-    if (e == cudaSuccess) e = cudaMemset(a->d_count, 0, sizeof(int64_t));
-    if (e == cudaSuccess) e = cudaMemset(a->d_status, 0, sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    size_t total = 0;
+    for (auto& pr : parts) total += slab_align(pr.second);
+    const cudaStream_t st = cudaStreamLegacy;
+    cudaError_t e = slab_alloc(&a->slab, total, st);
+    if (e == cudaSuccess) {
+        size_t off = 0;
+        for (auto& pr : parts) {
+            *pr.first = static_cast<char*>(a->slab) + off;
+            off += slab_align(pr.second);
+        }
+        e = pinned_slot_alloc((void**)&a->h_pinned);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(a->d_count, 0, sizeof(int64_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a->d_status, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         free_archive(a);
         return cuda_fail(e, "moq_archive_create");
