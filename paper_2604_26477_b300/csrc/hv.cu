@@ -652,10 +652,12 @@ int moq_hypervolume_points(const int64_t* pts, int64_t F, int32_t K, const int64
     }
     k_hv_final<<<1, kThreads, 0, st>>>(pts, F, K, r, nparts, ws);
     MOQ_LAUNCH_CHECK("moq_hypervolume launch");
-    struct {
+    struct Result {
         i128 v;
         int32_t flags;
-    } host;
+    } local;
+    Result* pin = static_cast<Result*>(pinned_scratch(sizeof(Result)));
+    Result& host = pin ? *pin : local;
     MOQ_CUDA_TRY(cudaMemcpyAsync(&host.v, ws.result, sizeof(i128), cudaMemcpyDeviceToHost, st));
     MOQ_CUDA_TRY(cudaMemcpyAsync(&host.flags, ws.flags, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     MOQ_CUDA_TRY(cudaStreamSynchronize(st));

@@ -333,9 +333,15 @@ int moq_create_instance(int32_t n, int32_t K, int64_t E, const int32_t* ei, cons
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) MOQ_STEP(cuda_fail(e, "instance build launch"));
     }
-    int32_t hstatus[2] = {0, 0};
-    long long hsums[3 * kMaxK + 2 * kMaxK + kMaxK * (kMaxK - 1) / 2];
-    MOQ_STEP(cu(cudaMemcpyAsync(hstatus, status, sizeof(hstatus), cudaMemcpyDeviceToHost, st), "read status"));
+    struct ReadBack {
+        long long sums[3 * kMaxK + 2 * kMaxK + kMaxK * (kMaxK - 1) / 2];
+        int32_t status[2];
+    } local;
+    ReadBack* pin = static_cast<ReadBack*>(pinned_scratch(sizeof(ReadBack)));
+    ReadBack& rb = pin ? *pin : local;
+    int32_t* hstatus = rb.status;
+    long long* hsums = rb.sums;
+    MOQ_STEP(cu(cudaMemcpyAsync(hstatus, status, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, st), "read status"));
     MOQ_STEP(cu(cudaMemcpyAsync(hsums, sums, sizeof(long long) * (3 * K + nmom), cudaMemcpyDeviceToHost, st), "read sums"));
     MOQ_STEP(cu(cudaStreamSynchronize(st), "instance build"));
     if (hstatus[0] & kStatusBadEdge) MOQ_STEP(fail(MOQ_ERR_ARG, "moq_create_instance: an edge has i >= j or an endpoint outside [0, n)"));

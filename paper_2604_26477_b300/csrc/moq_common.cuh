@@ -41,6 +41,7 @@ void slab_free(void* p);
 void slab_free_async(void* p, cudaStream_t st);  // once everything queued on st before it is done
 cudaError_t pinned_slot_alloc(void** p);
 void pinned_slot_free(void* p);
+void* pinned_scratch(size_t bytes);  // this host thread's pinned read-back buffer (NULL if pinning fails)
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 

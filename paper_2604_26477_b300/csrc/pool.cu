@@ -101,4 +101,21 @@ void pinned_slot_free(void* p)
     g_free_slots.push_back(p);
 }
 
+void* pinned_scratch(size_t bytes)
+{
+    // per host thread, grown on demand and kept (a copy into pageable memory is staged by
+    // the driver and costs more than the bytes)
+    thread_local void* buf = nullptr;
+    thread_local size_t cap = 0;
+    if (cap < bytes) {
+        void* p = nullptr;
+        const size_t want = bytes < 4096 ? 4096 : bytes;
+        if (cudaMallocHost(&p, want) != cudaSuccess) return nullptr;
+        if (buf) cudaFreeHost(buf);
+        buf = p;
+        cap = want;
+    }
+    return buf;
+}
+
 }  // namespace moq
