@@ -323,6 +323,14 @@ int moq_lambda_propose(moq_mlp* m, const moq_archive* a, const float* features, 
                        const int64_t* scale, int32_t n_candidates, uint64_t seed, uint64_t round, float* lambda_out, int32_t R,
                        void* stream);
 
+/* ---- handle memory --------------------------------------------------------------
+ * Instances and archives take their device arrays from a memory pool the library keeps
+ * per device: memory freed by moq_destroy_instance / moq_archive_destroy stays reserved
+ * for the next handle instead of going back to the driver. moq_release_cached_memory
+ * returns the unused part of the current device's pool to the driver (synchronises the
+ * device; handles that are alive keep their memory). Errors: MOQ_ERR_CUDA. */
+int moq_release_cached_memory(void);
+
 /* ---- errors -------------------------------------------------------------------- */
 const char* moq_strerror(int code);
 const char* moq_last_error_message(void);

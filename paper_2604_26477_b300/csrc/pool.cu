@@ -119,3 +119,20 @@ void* pinned_scratch(size_t bytes)
 }
 
 }  // namespace moq
+
+extern "C" int moq_release_cached_memory(void)
+{
+    using namespace moq;
+    int device = 0;
+    MOQ_CUDA_TRY(cudaGetDevice(&device));
+    if (device < 0 || device >= kMaxDevices) return MOQ_OK;
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mutex);
+        pool = g_pools[device];
+    }
+    if (!pool) return MOQ_OK;
+    MOQ_CUDA_TRY(cudaDeviceSynchronize());
+    MOQ_CUDA_TRY(cudaMemPoolTrimTo(pool, 0));
+    return MOQ_OK;
+}

@@ -103,6 +103,7 @@ _sigs = {
     "moq_mlp_train_step": (C.c_int, [_vp, _vp, _vp, _i32, C.c_float, _vp, _vp]),
     "moq_lambda_propose": (C.c_int, [_vp, _vp, _vp, _i32, _vp, _vp, _i32, _u64, _u64, _vp, _i32, _vp]),
     "moq_mlp_make_rows": (C.c_int, [_i32, _i32, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "moq_release_cached_memory": (C.c_int, []),
     "moq_strerror": (C.c_char_p, [C.c_int]),
     "moq_last_error_message": (C.c_char_p, []),
 }
@@ -392,6 +393,10 @@ def moq_mlp_gradient(h, X, T, B, grad=None, loss=None, stream=None):
 
 def moq_mlp_adam_step(h, lr, stream=None):
     _check(_lib.moq_mlp_adam_step(h, lr, _stream(stream)), "moq_mlp_adam_step")
+
+
+def moq_release_cached_memory():
+    _check(_lib.moq_release_cached_memory(), "moq_release_cached_memory")
 
 
 def moq_mlp_train_step(h, X, T, B, lr, loss=None, stream=None):

@@ -445,6 +445,28 @@ def test_sampler_invariants_and_determinism(M, P, variant):
     assert not torch.equal(b1, b3)
 
 
+def test_handles_reuse_pooled_memory(M, P):
+    # instances and archives take their arrays from the library's memory pool: handles of the
+    # same size come back after destruction, the cached memory can be returned to the driver,
+    # and handles made before and after give the same results
+    src = INSTANCES["heavyhex_K3"]()
+    R = 512
+    lam = _dev(wl.dirichlet_lambdas(R, 3, 2), torch.float32)
+    params = M.moq_default_params(variant="dsb", steps=64, dt=0.5, alpha=0.1)
+    hvs = []
+    for it in range(3):
+        inst = P.Instance(src)
+        arch = P.Archive(src.n, src.K, capacity=1 << 12, max_batch=R)
+        buf = P.RoundBuffers(R, src.n, src.K)
+        P.sample_round(inst, arch, buf, params, 5, 0, lam=lam)
+        hvs.append(arch.hypervolume(inst.ref))
+        arch.close()
+        inst.close()
+        if it == 1:
+            M.moq_release_cached_memory()
+    assert hvs[0] == hvs[1] == hvs[2] > 0
+
+
 @pytest.mark.parametrize("world", [2, 3])
 def test_replica_shards_reproduce_one_call(M, P, world):
     # the multi-GPU path: each rank samples a contiguous replica shard with the shard's first
