@@ -126,7 +126,10 @@ int moq_instance_get_info(const moq_instance* inst, moq_instance_info* out);
  * (o = p->replica_offset): word (m & 7) >> 1 gives two Gaussians by Box-Muller on its
  * 16-bit halves, u1 = (low + 1) 2^-16, u2 = high 2^-16 (cosine for even m, sine for odd m);
  * the start state from counter (0xFFFFFFFF, i, o + r, round). `seed` and `round` fully
- * determine the output on a given GPU build.
+ * determine the output on a given GPU build. The whole trajectory of a block of replicas
+ * runs on-chip in one launch; each thread runs one spin of one replica or, where that keeps
+ * more replicas in flight per SM (degree bound <= 4), of two (same results; the
+ * environment variable MOQ_SB_PAIR = 0 / 1 forces a form).
  * Errors: MOQ_ERR_ARG (R < 0, steps < 0, bad variant, NULL lambda/bits with R > 0),
  * MOQ_ERR_UNSUPPORTED (n > 1024 or max degree > 16), MOQ_ERR_CUDA. Asynchronous. */
 int moq_sample(const moq_instance* inst, const float* lambda, int32_t R, const moq_sample_params* p,
