@@ -639,11 +639,13 @@ extern "C" int moq_sample(const moq_instance* inst, const float* lambda, int32_t
     const Shape one = shape_of(false), two = shape_of(true);
     // two replicas per thread (degree bound <= 4) when that keeps more replicas in flight per
     // SM (n = 42: 8 blocks of 6 against 10 of 3; n = 1024: one block either way; n = 600: 2
-    // against 2, where the one-replica form hides latency with twice the warps);
-    // MOQ_SB_PAIR = 0 / 1 forces a form
+    // against 2, where the one-replica form hides latency with twice the warps) and its grid
+    // fills at least two waves: below that the per-block latency decides and the shorter
+    // one-replica blocks finish first (n = 42, R = 1024: 0.100 against 0.120 ms; n = 300,
+    // R = 1024: 0.48 against 0.55 ms); MOQ_SB_PAIR = 0 / 1 forces a form
     bool pair = false;
     {
-        auto resident = [&](bool pr, const Shape& sh) -> int {
+        auto blocks_per_sm = [&](bool pr, const Shape& sh) -> int {
             const void* k = p->variant == MOQ_DSB ? kernel_of_variant<MOQ_DSB>(dmax, noise, pr, sh.pump)
                                                   : kernel_of_variant<MOQ_BSB>(dmax, noise, pr, sh.pump);
             int blocks = 0;
@@ -652,9 +654,16 @@ extern "C" int moq_sample(const moq_instance* inst, const float* lambda, int32_t
                 (void)cudaGetLastError();
                 return 0;
             }
-            return blocks * sh.Rb;
+            return blocks;
         };
-        pair = R > 1 && dmax <= 4 && resident(true, two) > resident(false, one);
+        if (R > 1 && dmax <= 4) {
+            int dev = 0, sms = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+                sms = 148;
+            const int b1 = blocks_per_sm(false, one), b2 = blocks_per_sm(true, two);
+            const int64_t grid2 = ceil_div(R, two.Rb);
+            pair = (int64_t)b2 * two.Rb > (int64_t)b1 * one.Rb && grid2 >= 2 * (int64_t)sms * b2;
+        }
         if (const char* env = getenv("MOQ_SB_PAIR")) {
             const int v = atoi(env);
             if (v == 0) pair = false;
