@@ -192,6 +192,26 @@ int moq_sample_dense(moq_dense* d, const float* lambda, int32_t R, const moq_sam
                      uint64_t* bits, void* stream);
 int moq_dense_status(moq_dense* d, void* stream);
 
+/* ---- a3 dense, plain FP32 form on the CUDA cores (same dynamics as moq_sample_dense)
+ * The force c0 sum_k c_k (J^(k) Phi)_i of the SB equations with J^(k) and phi in FP32 and
+ * every product and sum in FP32: the full-precision comparison for the tensor-core form.
+ * moq_dense_fp32_create copies the couplings into K zero-padded n_pad x n_pad FP32 matrices
+ * (n_pad = n rounded up to 64; integers |J| < 2^24 are exact) and allocates x, y and two
+ * phi buffers (FP32, ceil(max_replicas/128)*128 x n_pad each). K <= 4, n <= 16384. The
+ * instance must outlive the handle. moq_sample_dense_fp32 takes the arguments of
+ * moq_sample_dense and draws the same start state and the same noise (the counters of
+ * moq_sample_dense), combines the force in the same order and applies the same update, so
+ * for dSB with integer couplings whose row sums of |J| stay below 2^24 (every per-objective
+ * product exact in both forms) and |J| <= 256 (exact in BF16) the two forms give identical
+ * results; otherwise they differ by the BF16 rounding of J (and of x for bSB) only.
+ * Asynchronous on `stream`; replica_offset must be 0. Errors: MOQ_ERR_ARG,
+ * MOQ_ERR_UNSUPPORTED, MOQ_ERR_OOM, MOQ_ERR_CUDA. */
+typedef struct moq_dense_fp32 moq_dense_fp32;
+int moq_dense_fp32_create(const moq_instance* inst, int32_t max_replicas, moq_dense_fp32** out);
+void moq_dense_fp32_destroy(moq_dense_fp32* d);
+int moq_sample_dense_fp32(moq_dense_fp32* d, const float* lambda, int32_t R, const moq_sample_params* p, uint64_t seed,
+                          uint64_t round, uint64_t* bits, void* stream);
+
 /* a6 for dense instances on the tensor cores, exact: C_k(s) (Eq. single_obj) of M packed
  * configurations bits (device, M x W words, bit set for s_i = -1; M <= max_replicas) into
  * cuts (device, M x K int64, row-major), the same values as moq_evaluate_cuts. Uses

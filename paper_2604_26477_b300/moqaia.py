@@ -92,6 +92,9 @@ _sigs = {
     "moq_sample_dense": (C.c_int, [_vp, _vp, _i32, C.POINTER(moq_sample_params), _u64, _u64, _vp, _vp]),
     "moq_dense_status": (C.c_int, [_vp, _vp]),
     "moq_dense_evaluate_cuts": (C.c_int, [_vp, _vp, _i32, _vp, _vp]),
+    "moq_dense_fp32_create": (C.c_int, [_vp, _i32, C.POINTER(_vp)]),
+    "moq_dense_fp32_destroy": (None, [_vp]),
+    "moq_sample_dense_fp32": (C.c_int, [_vp, _vp, _i32, C.POINTER(moq_sample_params), _u64, _u64, _vp, _vp]),
     "moq_mlp_create": (C.c_int, [_i32, _i32, _i32, _i32, _u64, C.POINTER(_vp)]),
     "moq_mlp_destroy": (None, [_vp]),
     "moq_mlp_param_count": (_i64, [_vp]),
@@ -353,6 +356,22 @@ def moq_dense_evaluate_cuts(h, bits, M, cuts, stream=None):
     _, i64, u64 = _torch_types()
     _check(_lib.moq_dense_evaluate_cuts(h, _dptr(bits, "bits", u64), M, _dptr(cuts, "cuts", i64), _stream(stream)),
            "moq_dense_evaluate_cuts")
+
+
+def moq_dense_fp32_create(inst, max_replicas) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(_lib.moq_dense_fp32_create(inst, max_replicas, C.byref(h)), "moq_dense_fp32_create")
+    return h
+
+
+def moq_dense_fp32_destroy(h):
+    _lib.moq_dense_fp32_destroy(h)
+
+
+def moq_sample_dense_fp32(h, lam, R, params, seed, round_, bits, stream=None):
+    f32, _, u64 = _torch_types()
+    _check(_lib.moq_sample_dense_fp32(h, _dptr(lam, "lambda", f32), R, C.byref(params), seed, round_,
+                                      _dptr(bits, "bits", u64), _stream(stream)), "moq_sample_dense_fp32")
 
 
 def moq_mlp_create(d_in, d_out, max_batch, max_candidates, seed) -> C.c_void_p:

@@ -273,3 +273,107 @@ def test_round_driver_on_the_dense_sampler(M, P):
     arch.close()
     out = P.time_to_target(src, target, params, 512, seed=7, max_rounds=4, dense=True)
     assert out["reached"] and out["rounds"] <= 4 and out["hv"] >= target
+
+
+# ---- the plain FP32 form on the CUDA cores -------------------------------------------
+
+def _force_fp32(M, P, src, variant, R, seed=1):
+    inst = P.Instance(src)
+    d = M.moq_dense_fp32_create(inst.handle, R)
+    try:
+        lam = wl.dirichlet_lambdas(R, src.K, seed)
+        rng = np.random.default_rng(seed)
+        x0 = rng.uniform(-0.5, 0.5, (R, src.n)).astype(np.float32)
+        dt = 2.0 ** -10
+        yo = torch.zeros((R, src.n), device="cuda")
+        p = M.moq_default_params(variant=variant, steps=1, dt=dt, alpha=0.0, schedule=torch.ones(1, device="cuda"),
+                                 x_init=_dev(x0), y_init=torch.zeros((R, src.n), device="cuda"), y_out=yo)
+        bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+        M.moq_sample_dense_fp32(d, _dev(lam), R, p, 0, 0, bits)
+        torch.cuda.synchronize()
+    finally:
+        M.moq_dense_fp32_destroy(d)
+    return lam, x0, yo.cpu().numpy().astype(np.float64) / dt
+
+
+@pytest.mark.parametrize("n,R,K,variant", [(300, 200, 3, "dsb"), (300, 200, 3, "bsb"), (130, 129, 4, "bsb"),
+                                           (64, 1, 2, "dsb"), (257, 70, 2, "bsb")])
+def test_dense_fp32_force_within_1e5(M, P, oracle, n, R, K, variant):
+    # the dense workload's weights (round(1000 N(0,1)), |J| up to about 5000, far from exact
+    # in BF16): with FP32 couplings and phi the force meets the 1e-5 normwise FP32 bound
+    # against the FP64 oracle for both variants (ragged spin and replica tiles)
+    src = wl.complete_graph(n, 70 + n, K=K)
+    lam, x0, f_gpu = _force_fp32(M, P, src, variant, R)
+    ref = oracle.sb(src, lam.astype(np.float64), variant=variant, steps=1, dt=2.0 ** -10, alpha=0.0, schedule=[1.0],
+                    x_init=x0.astype(np.float64), y_init=np.zeros((R, n)))
+    phi = np.where(x0 >= 0, 1.0, -1.0) if variant == "dsb" else x0.astype(np.float64)
+    scale = _abs_force_scale(src, lam, phi, ref["c0"])
+    err = np.abs(f_gpu - ref["y"] / 2.0 ** -10)
+    assert np.all(err <= 1e-5 * scale + 1e-30), float((err / np.maximum(scale, 1e-30)).max())
+
+
+def test_dense_fp32_bsb_short_trajectory(M, P, oracle):
+    # noise-free bSB is continuous in the state: a few FP32 steps stay on the FP64 trajectory
+    src = wl.complete_graph(200, 91, K=3)
+    inst = P.Instance(src)
+    R, T = 192, 8
+    d = M.moq_dense_fp32_create(inst.handle, R)
+    try:
+        lam = wl.dirichlet_lambdas(R, 3, 6)
+        xo = torch.zeros((R, src.n), device="cuda")
+        yo = torch.zeros((R, src.n), device="cuda")
+        p = M.moq_default_params(variant="bsb", steps=T, dt=0.5, x_out=xo, y_out=yo)
+        bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+        M.moq_sample_dense_fp32(d, _dev(lam), R, p, 4, 0, bits)
+        ref = oracle.sb(src, lam.astype(np.float64), variant="bsb", steps=T, dt=0.5, seed=4)
+        assert np.abs(xo.cpu().numpy() - ref["x"]).max() < 1e-4
+        assert np.abs(yo.cpu().numpy() - ref["y"]).max() < 1e-4
+    finally:
+        M.moq_dense_fp32_destroy(d)
+
+
+@pytest.mark.parametrize("n,R,K,alpha,sched", [(300, 300, 3, 0.1, False), (100, 130, 3, 0.15, False), (257, 64, 4, 0.1, True),
+                                                (129, 1, 2, 0.0, False)])
+def test_dense_fp32_matches_tensor_core_form_bitwise(M, P, n, R, K, alpha, sched):
+    # dSB with |J| <= 256: every per-objective product is an exact integer in both forms,
+    # and the start state, noise counters, force combination and update are the same, so
+    # the FP32 CUDA-core form and the BF16 tensor-core form (per-step or resident kernel)
+    # give the same bits, x and y over a noisy trajectory
+    src = wl.random_graph(n, 1.0, 7 + n + R, K=K, wmax=256)
+    inst = P.Instance(src)
+    T = 40
+    lam = _dev(wl.dirichlet_lambdas(R, K, 12))
+    schedule = torch.linspace(0.0, 1.0, T, device="cuda") ** 2 if sched else None
+    out = {}
+    for form in ("bf16", "fp32"):
+        d = (M.moq_dense_create if form == "bf16" else M.moq_dense_fp32_create)(inst.handle, R)
+        try:
+            xo = torch.zeros((R, n), device="cuda")
+            yo = torch.zeros((R, n), device="cuda")
+            bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+            p = M.moq_default_params(variant="dsb", steps=T, dt=0.5, alpha=alpha, schedule=schedule, x_out=xo, y_out=yo)
+            if form == "bf16":
+                M.moq_sample_dense(d, lam, R, p, 21, 3, bits)
+                M.moq_dense_status(d)
+            else:
+                M.moq_sample_dense_fp32(d, lam, R, p, 21, 3, bits)
+            out[form] = (bits.cpu(), xo.cpu(), yo.cpu())
+        finally:
+            (M.moq_dense_destroy if form == "bf16" else M.moq_dense_fp32_destroy)(d)
+    for a, b in zip(out["bf16"], out["fp32"]):
+        assert torch.equal(a, b)
+    assert R == 1 or len(torch.unique(out["fp32"][0], dim=0)) > 1
+
+
+def test_dense_fp32_rejects_bad_arguments(M, P):
+    src = wl.random_graph(40, 1.0, 3, K=2, wmax=10)
+    inst = P.Instance(src)
+    d = M.moq_dense_fp32_create(inst.handle, 16)
+    try:
+        p = M.moq_default_params(steps=3)
+        bits = torch.zeros((32, 1), dtype=torch.int64, device="cuda")
+        with pytest.raises(M.MoqError) as e:
+            M.moq_sample_dense_fp32(d, _dev(np.full((32, 2), 0.5)), 32, p, 0, 0, bits)
+        assert e.value.code == M.MOQ_ERR_ARG
+    finally:
+        M.moq_dense_fp32_destroy(d)
