@@ -470,7 +470,10 @@ def dense_arm(args, rank, world):
     peak = peaks.get("bf16_tflops_sustained", 1392.4)
     achieved = flops / samp_s / 1e12
     front = arch.size()
+    plain = dense_plain_fp32(args, M, inst, d, lam, src) if args.dense_fp32_steps > 0 else None
     M.moq_dense_destroy(d)
+    if plain is not None:
+        plain["chosen_speedup_per_sb_step"] = plain["ms_per_sb_step"] / (samp_s / args.steps / T * 1e3)
     return {"metric": METRIC, "value": units / step_s * world, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_s / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16 products, f32 state", "data": "synthetic",
@@ -485,8 +488,71 @@ def dense_arm(args, rank, world):
                          "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16, seconds-long loop)"},
             "sampling_only_value": units / samp_s * world, "sampler_ms": samp_s / args.steps * 1e3,
             "clocks": clk.summary(), "front_points_last_step": front, "hv_last_step": int(hv[0]),
+            "plain_fp32": plain,
             # c0, init, T steps, readout; cuts: signs, two products, finish; merge 12; HV 4
             "gpu_launches": (T + 3 + 4 + 12 + 4) * args.steps}
+
+
+def dense_plain_fp32(args, M, inst, d, lam, src):
+    """The plain FP32 form of the dense step on the CUDA cores beside the chosen tensor-core
+    form, on the same instance and weight vectors (outside the timed step): ms per SB step over
+    --dense-fp32-steps steps (CUDA events on the launching stream), its fraction of the derived
+    FP32 FMA peak, and the force error of the BF16 products against the FP32 form (which
+    meets the 1e-5 normwise bound against FP64) for one step from the same state."""
+    import torch
+
+    n, K, R = src.n, src.K, lam.shape[0]
+    dev = lam.device
+    T = args.dense_fp32_steps
+    d32 = M.moq_dense_fp32_create(inst.handle, R)
+    try:
+        bits = torch.zeros((R, inst.W), dtype=torch.int64, device=dev)
+        p = M.moq_default_params(variant="bsb", steps=2, dt=0.5, alpha=0.1)
+        M.moq_sample_dense_fp32(d32, lam, R, p, 1, 0, bits)  # warm-up (module load, attributes)
+        p = M.moq_default_params(variant="bsb", steps=T, dt=0.5, alpha=0.1)
+        stream = torch.cuda.current_stream()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(dev.index) as clk:
+            e0.record(stream)
+            M.moq_sample_dense_fp32(d32, lam, R, p, 1, 1, bits)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / T
+        # force of one step from the same state: y_out / dt with y = 0, a = a0, no noise
+        g = torch.Generator(device="cpu").manual_seed(17)
+        x0 = (torch.rand((R, n), generator=g) * 2 - 1).to(dev)
+        y0 = torch.zeros((R, n), device=dev)
+        dt = 2.0 ** -10
+        forces = []
+        for form in ("fp32", "bf16"):
+            yo = torch.zeros((R, n), device=dev)
+            q = M.moq_default_params(variant="bsb", steps=1, dt=dt, alpha=0.0, schedule=torch.ones(1, device=dev),
+                                     x_init=x0, y_init=y0, y_out=yo)
+            if form == "fp32":
+                M.moq_sample_dense_fp32(d32, lam, R, q, 0, 0, bits)
+            else:
+                M.moq_sample_dense(d, lam, R, q, 0, 0, bits)
+            torch.cuda.synchronize()
+            forces.append(yo.double() / dt)
+        f32, f16 = forces
+        diff = (f16 - f32).abs()
+        row_rel = diff.max(dim=1).values / f32.abs().max(dim=1).values.clamp_min(1e-300)
+    finally:
+        M.moq_dense_fp32_destroy(d32)
+    flops = 2.0 * K * n * n * R
+    peak = peak_alu_tops() * 2  # FP32 FMA lanes: 148 SMs x 128 x 2 flops x 2032 MHz
+    return {"form": "k_dense32_step: FP32 J and phi on the CUDA cores, FP32 accumulate (register-tiled FMA, cp.async stages)",
+            "sb_steps_timed": T, "ms_per_sb_step": ms,
+            "replica_spin_updates_per_s": n * R / (ms * 1e-3),
+            "achieved_tflops": flops / (ms * 1e-3) / 1e12, "peak_tflops": peak,
+            "frac": flops / (ms * 1e-3) / 1e12 / peak,
+            "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 flops x 2032 MHz max SM clock",
+            "clocks": clk.summary(),
+            "bf16_force_error_vs_fp32": {
+                "state": "bSB, x uniform in [-1, 1), one step, all replicas",
+                "relative_frobenius": float(diff.norm() / f32.norm()),
+                "row_max_relative_median": float(row_rel.median()), "row_max_relative_max": float(row_rel.max())}}
 
 
 def paper_arm(args, rank, world):
@@ -748,6 +814,8 @@ def main():
     ap.add_argument("--dense-n", type=int, default=2000)
     ap.add_argument("--dense-replicas", type=int, default=8192)
     ap.add_argument("--dense-steps", type=int, default=3000)
+    ap.add_argument("--dense-fp32-steps", type=int, default=100,
+                    help="SB steps of the plain FP32 CUDA-core comparison in the dense workload (0: skip it)")
     ap.add_argument("--batch-instances", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and not args.cpu_baseline_worker:
