@@ -471,6 +471,7 @@ def dense_arm(args, rank, world):
     achieved = flops / samp_s / 1e12
     front = arch.size()
     plain = dense_plain_fp32(args, M, inst, d, lam, src) if args.dense_fp32_steps > 0 else None
+    fp8 = dense_fp8_dsb(args, M, d, lam, src) if args.dense_fp8_steps > 0 else None
     M.moq_dense_destroy(d)
     if plain is not None:
         plain["chosen_speedup_per_sb_step"] = plain["ms_per_sb_step"] / (samp_s / args.steps / T * 1e3)
@@ -488,7 +489,7 @@ def dense_arm(args, rank, world):
                          "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16, seconds-long loop)"},
             "sampling_only_value": units / samp_s * world, "sampler_ms": samp_s / args.steps * 1e3,
             "clocks": clk.summary(), "front_points_last_step": front, "hv_last_step": int(hv[0]),
-            "plain_fp32": plain,
+            "plain_fp32": plain, "fp8_dsb": fp8,
             # c0, init, T steps, readout; cuts: signs, two products, finish; merge 12; HV 4
             "gpu_launches": (T + 3 + 4 + 12 + 4) * args.steps}
 
@@ -538,6 +539,23 @@ def dense_plain_fp32(args, M, inst, d, lam, src):
         f32, f16 = forces
         diff = (f16 - f32).abs()
         row_rel = diff.max(dim=1).values / f32.abs().max(dim=1).values.clamp_min(1e-300)
+        # dSB (phi = +-1): the BF16 and the E4M3 operand forms against FP32
+        dsb = {}
+        for form in ("fp32", "bf16", "fp8"):
+            yo = torch.zeros((R, n), device=dev)
+            q = M.moq_default_params(variant="dsb", steps=1, dt=dt, alpha=0.0, schedule=torch.ones(1, device=dev),
+                                     x_init=x0, y_init=y0, y_out=yo)
+            {"fp32": lambda: M.moq_sample_dense_fp32(d32, lam, R, q, 0, 0, bits),
+             "bf16": lambda: M.moq_sample_dense(d, lam, R, q, 0, 0, bits),
+             "fp8": lambda: M.moq_sample_dense_fp8(d, lam, R, q, 0, 0, bits)}[form]()
+            torch.cuda.synchronize()
+            dsb[form] = yo.double() / dt
+        dsb_err = {}
+        for form in ("bf16", "fp8"):
+            dd = (dsb[form] - dsb["fp32"]).abs()
+            rr = dd.max(dim=1).values / dsb["fp32"].abs().max(dim=1).values.clamp_min(1e-300)
+            dsb_err[form] = {"relative_frobenius": float(dd.norm() / dsb["fp32"].norm()),
+                             "row_max_relative_median": float(rr.median()), "row_max_relative_max": float(rr.max())}
     finally:
         M.moq_dense_fp32_destroy(d32)
     flops = 2.0 * K * n * n * R
@@ -552,7 +570,47 @@ def dense_plain_fp32(args, M, inst, d, lam, src):
             "bf16_force_error_vs_fp32": {
                 "state": "bSB, x uniform in [-1, 1), one step, all replicas",
                 "relative_frobenius": float(diff.norm() / f32.norm()),
-                "row_max_relative_median": float(row_rel.median()), "row_max_relative_max": float(row_rel.max())}}
+                "row_max_relative_median": float(row_rel.median()), "row_max_relative_max": float(row_rel.max())},
+            "dsb_force_error_vs_fp32": dict(state="dSB (phi = sgn x, x uniform in [-1, 1)), one step, all replicas",
+                                            **dsb_err)}
+
+
+def dense_fp8_dsb(args, M, d, lam, src):
+    """dSB on the dense workload with BF16 operands (moq_sample_dense) and with E4M3 operands
+    (moq_sample_dense_fp8: J rounded to E4M3 with power-of-two row scales, phi = +-1 exact),
+    --dense-fp8-steps SB steps each on the same handle, CUDA events on the launching stream,
+    the per-step time from the difference of two lengths (start-up and read-out cancel)."""
+    import torch
+
+    n, K, R = src.n, src.K, lam.shape[0]
+    T = args.dense_fp8_steps
+    bits = torch.zeros((R, (n + 63) // 64), dtype=torch.int64, device=lam.device)
+    stream = torch.cuda.current_stream()
+    out = {}
+    with ClockSampler(lam.device.index) as clk:
+        for form, fn in (("bf16", M.moq_sample_dense), ("fp8", M.moq_sample_dense_fp8)):
+            ms = {}
+            for steps in (10, 10 + T):
+                p = M.moq_default_params(variant="dsb", steps=steps, dt=0.5, alpha=0.1)
+                fn(d, lam, R, p, 1, 0, bits)  # warm-up of this length
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn(d, lam, R, p, 1, 1, bits)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms[steps] = e0.elapsed_time(e1)
+            out[form] = (ms[10 + T] - ms[10]) / T
+    M.moq_dense_status(d)
+    flops = 2.0 * K * n * n * R
+    peaks = measured_peaks()
+    peak = 2.0 * peaks.get("bf16_tflops_sustained", 1392.4)
+    ach = flops / (out["fp8"] * 1e-3) / 1e12
+    return {"kernel": "k_dense_step_ws<dSB, K, noise, 1, F8 = true> (tcgen05.mma kind::f8f6f4, E4M3 x E4M3 -> FP32)",
+            "sb_steps_timed": T, "ms_per_sb_step_fp8": out["fp8"], "ms_per_sb_step_bf16": out["bf16"],
+            "fp8_speedup": out["bf16"] / out["fp8"], "replica_spin_updates_per_s_fp8": n * R / (out["fp8"] * 1e-3),
+            "achieved_tflops": ach, "peak_tflops": peak, "frac": ach / peak,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained x 2 (nominal dense FP8/BF16 ratio)",
+            "clocks": clk.summary()}
 
 
 def paper_arm(args, rank, world):
@@ -816,6 +874,8 @@ def main():
     ap.add_argument("--dense-steps", type=int, default=3000)
     ap.add_argument("--dense-fp32-steps", type=int, default=100,
                     help="SB steps of the plain FP32 CUDA-core comparison in the dense workload (0: skip it)")
+    ap.add_argument("--dense-fp8-steps", type=int, default=300,
+                    help="SB steps of the dSB BF16 vs FP8 (E4M3) comparison in the dense workload (0: skip it)")
     ap.add_argument("--batch-instances", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and not args.cpu_baseline_worker:

@@ -170,8 +170,9 @@ int moq_evaluate_cuts_batch(const moq_batch* b, const uint64_t* bits_all, int64_
 /* ---- a3 dense: tensor-core sampler (same dynamics as moq_sample; the force
  * c0 sum_k c_k (J^(k) Phi)_i is a matrix product) -----------------------------------------
  * moq_dense_create copies the instance's couplings into K zero-padded n_pad x n_pad BF16
- * matrices (n_pad = n rounded up to 128; integers |J| <= 256 are exact) and allocates the
- * replica state for up to max_replicas (x, y FP32 and two BF16 phi buffers, each
+ * matrices (n_pad = n rounded up to 128; integers |J| <= 256 are exact) and E4M3 matrices
+ * with row scales (moq_sample_dense_fp8), and allocates the replica state for up to
+ * max_replicas (x, y FP32, two BF16 and two E4M3 phi buffers, each
  * ceil(max_replicas/128)*128 x n_pad). K <= 4, n <= 16384. The instance must outlive it.
  * moq_sample_dense runs T step kernels (tcgen05.mma BF16 -> FP32 products for every
  * objective, fused update/wall/phi epilogue) on `stream`, then writes the packed signs
@@ -191,6 +192,19 @@ void moq_dense_destroy(moq_dense* d);
 int moq_sample_dense(moq_dense* d, const float* lambda, int32_t R, const moq_sample_params* p, uint64_t seed, uint64_t round,
                      uint64_t* bits, void* stream);
 int moq_dense_status(moq_dense* d, void* stream);
+
+/* FP8 form of the dense dSB step (precision growth of the force contraction): the couplings
+ * as E4M3 with one power-of-two scale per row and objective (J^(k)_ij = 2^e J8_ij, e >= 0
+ * the smallest with max_j |J^(k)_ij| <= 448 2^e; integers |J| <= 16 are exact, larger ones
+ * round to 4 significant bits) and phi = sgn(x) as exact +-1 E4M3, multiplied by
+ * tcgen05.mma kind::f8f6f4 with FP32 accumulation; the row scale is applied to each
+ * accumulator in the epilogue. Same arguments, start state, noise and update as
+ * moq_sample_dense (with |J| <= 16 the two give identical results); the per-step kernel is
+ * used for every n. dSB only: p->variant = MOQ_BSB returns MOQ_ERR_UNSUPPORTED (x would
+ * round to 4 significant bits). Buffers are allocated by moq_dense_create. Errors as
+ * moq_sample_dense; a timed-out device wait shows in moq_dense_status. */
+int moq_sample_dense_fp8(moq_dense* d, const float* lambda, int32_t R, const moq_sample_params* p, uint64_t seed,
+                         uint64_t round, uint64_t* bits, void* stream);
 
 /* ---- a3 dense, plain FP32 form on the CUDA cores (same dynamics as moq_sample_dense)
  * The force c0 sum_k c_k (J^(k) Phi)_i of the SB equations with J^(k) and phi in FP32 and

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "sb_common.cuh"
 
@@ -53,8 +54,9 @@ __global__ void k_dense_c0(const int64_t* __restrict__ rowsum, const int32_t* __
 
 __device__ __forceinline__ void store_phi(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 __device__ __forceinline__ void store_phi(float* p, float v) { *p = v; }
+__device__ __forceinline__ void store_phi(__nv_fp8_e4m3* p, float v) { *p = __nv_fp8_e4m3(v); }
 
-// Start state (Philox or the caller's arrays) and its phi; PhiT = BF16 (tensor-core
+// Start state (Philox or the caller's arrays) and its phi; PhiT = BF16 or E4M3 (tensor-core
 // sampler) or float (CUDA-core FP32 sampler).
 template <int VARIANT, typename PhiT>
 __global__ void k_dense_init(int32_t n, int32_t np, int32_t R, int32_t R_pad, float init_amp, const float* __restrict__ x_init,

@@ -30,6 +30,7 @@
 // Start state: the same counter (0xFFFFFFFF, i, r, round) as the sparse sampler.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -59,6 +60,12 @@ struct moq_dense {
     int32_t sms = 148;                           // persistent step kernel: one CTA per SM
     int32_t* status = nullptr;                   // device error flags
     int32_t* h_status = nullptr;                 // pinned
+    // FP8 (e4m3) operands of the dSB step: J^(k)_ij = rowscale_k(i) * J8, phi = +-1 exact
+    __nv_fp8_e4m3* J8 = nullptr;                 // K x n_pad x n_pad
+    float* rowscale = nullptr;                   // K x n_pad, powers of two
+    __nv_fp8_e4m3* phi8[2] = {nullptr, nullptr}; // R_pad x n_pad
+    CUtensorMap tm_J8;                           // box 128 x (128 / CL) x 1 (128 bytes per row, as BF16)
+    CUtensorMap tm_phi8[2];                      // box 128 x 128
 };
 
 namespace moq {
@@ -87,6 +94,13 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr)
 // both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
 constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTileN >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
 
+// kind::f8f6f4 with A = B = E4M3 (format 0 in bits 7-9 and 10-12), D = F32, both K-major.
+constexpr uint32_t kIdescE4m3 = (1u << 4) | ((uint32_t)(kTileN >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
+// one K-chunk is 128 bytes of a row in either precision: 64 BF16 or 128 E4M3 elements, and one
+// MMA consumes 32 bytes of it (K = 16 BF16 or K = 32 E4M3)
+template <bool F8>
+__host__ __device__ constexpr int chunk_elems() { return F8 ? 128 : kChunkK; }
+
 __device__ __forceinline__ uint64_t global_ns()
 {
     uint64_t t;
@@ -113,6 +127,13 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t 
 {
     asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
                  "l"(da), "l"(db), "r"(kIdescBf16), "r"(accumulate)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate)
+{
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+                 "l"(da), "l"(db), "r"(kIdescE4m3), "r"(accumulate)
                  : "memory");
 }
 
@@ -178,6 +199,8 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
 
 struct DenseStepArgs {
     __nv_bfloat16* phi_out;
+    __nv_fp8_e4m3* phi8_out;   // FP8 form
+    const float* rowscale;     // FP8 form: K x n_pad scales of the J8 rows
     float* x;
     float* y;
     const float* lambda;  // R x K
@@ -261,7 +284,12 @@ constexpr int kWsThreads = 32 * (2 + kWsEpiWarps);
 // one spin block together: each loads 128 / CL rows of every J tile and multicasts them to
 // all, so L2 delivers each J tile once per cluster; a stage is refilled once every CTA's
 // products have released it (the MMA commits arrive in every CTA of the cluster).
-template <int VARIANT, int KOBJ, bool NOISE, int CL>
+//
+// F8: the operands are E4M3 (J8 rows with a power-of-two scale per row and objective, phi = +-1
+// exact for dSB) multiplied by kind::f8f6f4 MMAs; a K-chunk is then 128 spins (the same 128
+// bytes per row, so the stages, swizzle and descriptors are those of BF16), and the epilogue
+// applies the row scale to each accumulator before the force combination.
+template <int VARIANT, int KOBJ, bool NOISE, int CL, bool F8>
 __global__ void __launch_bounds__(kWsThreads, 1)
     k_dense_step_ws(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmPhi, const DenseStepArgs a,
                     int32_t n_ib, int32_t n_groups)
@@ -283,7 +311,8 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     float* c0_s = lam_s + 2 * kTileN * KOBJ;                                 // 2 x kTileN
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int np = a.n_pad, nchunks = np / kChunkK;
+    constexpr int kCk = chunk_elems<F8>();
+    const int np = a.n_pad, nchunks = np / kCk;
     constexpr int kSliceRows = kTileM / CL;
     constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
     uint32_t rank = 0;
@@ -334,11 +363,11 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                     }
                     const uint32_t stage = base + st * kStageBytes, fb = smem_u32(&full[st]);
                     mbar_expect_tx(fb, (uint32_t)kStageBytes);
-                    const int j0 = c * kChunkK;
+                    const int j0 = c * kCk;
 #pragma unroll
                     for (int k = 0; k < KOBJ; ++k) {
                         if (CL > 1)
-                            tma_load_3d_mc(stage + k * kTileBytes + rank * (kSliceRows * kChunkK * 2), &tmJ, j0, i0 + (int)rank * kSliceRows,
+                            tma_load_3d_mc(stage + k * kTileBytes + rank * (kSliceRows * 128), &tmJ, j0, i0 + (int)rank * kSliceRows,
                                            k, fb, kMask);
                         else
                             tma_load_3d(stage + k * kTileBytes, &tmJ, j0, i0, k, fb);
@@ -376,9 +405,14 @@ __global__ void __launch_bounds__(kWsThreads, 1)
 #pragma unroll
                     for (int k = 0; k < KOBJ; ++k)
 #pragma unroll
-                        for (int ks = 0; ks < kChunkK / 16; ++ks)
-                            mma_bf16(tmem + k * kTileN, sw128_desc(stage + k * kTileBytes + ks * 32),
-                                     sw128_desc(stage + KOBJ * kTileBytes + ks * 32), (c > 0 || ks > 0) ? 1u : 0u);
+                        for (int ks = 0; ks < 4; ++ks) {  // 4 x 32 bytes of the 128-byte chunk
+                            if (F8)
+                                mma_e4m3(tmem + k * kTileN, sw128_desc(stage + k * kTileBytes + ks * 32),
+                                         sw128_desc(stage + KOBJ * kTileBytes + ks * 32), (c > 0 || ks > 0) ? 1u : 0u);
+                            else
+                                mma_bf16(tmem + k * kTileN, sw128_desc(stage + k * kTileBytes + ks * 32),
+                                         sw128_desc(stage + KOBJ * kTileBytes + ks * 32), (c > 0 || ks > 0) ? 1u : 0u);
+                        }
                     if (CL > 1)
                         asm volatile(
                             "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
@@ -446,6 +480,14 @@ __global__ void __launch_bounds__(kWsThreads, 1)
 #pragma unroll
                 for (int k = 0; k < KOBJ; ++k) tmem_ld8(tmem + ((uint32_t)(quarter * 32) << 16) + k * kTileN + col0, g[k]);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (F8) {  // the scale of this spin's J8 row per objective
+#pragma unroll
+                    for (int k = 0; k < KOBJ; ++k) {
+                        const float sc = __ldg(a.rowscale + (int64_t)k * np + i);
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) g[k][q] *= sc;
+                    }
+                }
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const int rl = col0 + q;
@@ -494,7 +536,10 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                             sb_update<NOISE>(f[q], cm, eta[q], a.dt, a.kappa, a.dta0, xv, yv);
                             a.x[at] = xv;
                             a.y[at] = yv;
-                            a.phi_out[at] = __float2bfloat16_rn(phi_of<VARIANT>(xv));
+                            if (F8)
+                                a.phi8_out[at] = __nv_fp8_e4m3(phi_of<VARIANT>(xv));
+                            else
+                                a.phi_out[at] = __float2bfloat16_rn(phi_of<VARIANT>(xv));
                         }
                     }
 #pragma unroll
@@ -853,14 +898,41 @@ __global__ void k_dense_fill(const int32_t* __restrict__ rowptr, const int32_t* 
     if (mx > 0) atomicMax(maxabs, mx);
 }
 
+// FP8 operands of the dSB step: per row i and objective k the power-of-two scale 2^e
+// (smallest e >= 0 with max_j |J^(k)_ij| <= 448 2^e, 448 the largest E4M3 value) and
+// J8_ij = E4M3(J^(k)_ij / 2^e) (round to nearest even; integers |J| <= 16 are exact). One
+// block per row.
+__global__ void k_dense_fill8(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, const int32_t* __restrict__ wn,
+                              int64_t nnz, int32_t n, int32_t K, int32_t np, __nv_fp8_e4m3* J8, float* rowscale)
+{
+    __shared__ int32_t red;
+    for (int64_t i = blockIdx.x; i < n; i += gridDim.x)
+        for (int k = 0; k < K; ++k) {
+            if (threadIdx.x == 0) red = 0;
+            __syncthreads();
+            int32_t mx = 0;
+            for (int32_t p = rowptr[i] + threadIdx.x; p < rowptr[i + 1]; p += blockDim.x)
+                mx = max(mx, abs(wn[(int64_t)k * nnz + p]));
+            atomicMax(&red, mx);
+            __syncthreads();
+            int e = 0;
+            while ((double)red > 448.0 * (double)(1ll << e)) ++e;
+            const float inv = ldexpf(1.0f, -e);
+            for (int32_t p = rowptr[i] + threadIdx.x; p < rowptr[i + 1]; p += blockDim.x)
+                J8[((int64_t)k * np + i) * np + col[p]] = __nv_fp8_e4m3((float)wn[(int64_t)k * nnz + p] * inv);
+            if (threadIdx.x == 0) rowscale[(int64_t)k * np + i] = ldexpf(1.0f, e);
+            __syncthreads();
+        }
+}
+
 size_t dense_smem_bytes(int K) { return 1024 + dense_stages(K) * (size_t)(K + 1) * kTileBytes + (size_t)kTileN * (K + 1) * 4 + 64; }
 
 // grid: one CTA per SM (clusters of CL CTAs), at most one per tile group; `grid` carries the
 // spin-block and replica-block counts
-template <int VARIANT, int KOBJ, bool NOISE, int CL>
+template <int VARIANT, int KOBJ, bool NOISE, int CL, bool F8>
 cudaError_t launch_step(const moq_dense* d, const CUtensorMap& tm_phi, const DenseStepArgs& a, dim3 grid, cudaStream_t st)
 {
-    auto k = k_dense_step_ws<VARIANT, KOBJ, NOISE, CL>;
+    auto k = k_dense_step_ws<VARIANT, KOBJ, NOISE, CL, F8>;
     const size_t smem = ws_smem_bytes(KOBJ);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -885,26 +957,26 @@ cudaError_t launch_step(const moq_dense* d, const CUtensorMap& tm_phi, const Den
     }
     clusters = std::max(1, std::min(clusters, n_groups));
     cfg.gridDim = dim3((unsigned)(clusters * CL));
-    return cudaLaunchKernelEx(&cfg, k, d->tm_J, tm_phi, a, (int32_t)grid.x, (int32_t)n_groups);
+    return cudaLaunchKernelEx(&cfg, k, F8 ? d->tm_J8 : d->tm_J, tm_phi, a, (int32_t)grid.x, (int32_t)n_groups);
 }
 
-template <int VARIANT, bool NOISE, int CL>
+template <int VARIANT, bool NOISE, int CL, bool F8>
 cudaError_t launch_step_k(const moq_dense* d, const CUtensorMap& tm_phi, const DenseStepArgs& a, dim3 grid, cudaStream_t st)
 {
     switch (a.K) {
-    case 2: return launch_step<VARIANT, 2, NOISE, CL>(d, tm_phi, a, grid, st);
-    case 3: return launch_step<VARIANT, 3, NOISE, CL>(d, tm_phi, a, grid, st);
-    default: return launch_step<VARIANT, 4, NOISE, CL>(d, tm_phi, a, grid, st);
+    case 2: return launch_step<VARIANT, 2, NOISE, CL, F8>(d, tm_phi, a, grid, st);
+    case 3: return launch_step<VARIANT, 3, NOISE, CL, F8>(d, tm_phi, a, grid, st);
+    default: return launch_step<VARIANT, 4, NOISE, CL, F8>(d, tm_phi, a, grid, st);
     }
 }
 
-template <int VARIANT, bool NOISE>
+template <int VARIANT, bool NOISE, bool F8 = false>
 cudaError_t launch_step_cl(const moq_dense* d, const CUtensorMap& tm_phi, const DenseStepArgs& a, dim3 grid, cudaStream_t st)
 {
     switch (d->cluster) {
-    case 1: return launch_step_k<VARIANT, NOISE, 1>(d, tm_phi, a, grid, st);
-    case 2: return launch_step_k<VARIANT, NOISE, 2>(d, tm_phi, a, grid, st);
-    default: return launch_step_k<VARIANT, NOISE, 4>(d, tm_phi, a, grid, st);
+    case 1: return launch_step_k<VARIANT, NOISE, 1, F8>(d, tm_phi, a, grid, st);
+    case 2: return launch_step_k<VARIANT, NOISE, 2, F8>(d, tm_phi, a, grid, st);
+    default: return launch_step_k<VARIANT, NOISE, 4, F8>(d, tm_phi, a, grid, st);
     }
 }
 
@@ -966,6 +1038,23 @@ int encode_maps(moq_dense* d)
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(MOQ_ERR_CUDA, "cuTensorMapEncodeTiled(phi) failed: %d", (int)r);
     }
+    {  // FP8 operands: the same 128-byte rows, 128 E4M3 elements per chunk
+        const cuuint64_t dims[3] = {np, np, (cuuint64_t)d->K};
+        const cuuint64_t strides[2] = {np, np * np};
+        const cuuint32_t box[3] = {128u, (cuuint32_t)(kTileM / d->cluster), 1};
+        CUresult r = encode(&d->tm_J8, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, d->J8, dims, strides, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(MOQ_ERR_CUDA, "cuTensorMapEncodeTiled(J8) failed: %d", (int)r);
+    }
+    for (int b = 0; b < 2; ++b) {
+        const cuuint64_t dims[2] = {np, (cuuint64_t)d->R_pad};
+        const cuuint64_t strides[1] = {np};
+        const cuuint32_t box[2] = {128u, (cuuint32_t)kTileN};
+        CUresult r = encode(&d->tm_phi8[b], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, d->phi8[b], dims, strides, box, one,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(MOQ_ERR_CUDA, "cuTensorMapEncodeTiled(phi8) failed: %d", (int)r);
+    }
     return MOQ_OK;
 }
 
@@ -983,8 +1072,121 @@ void free_dense(moq_dense* d)
     cudaFree(d->phi[1]);
     cudaFree(d->c0);
     cudaFree(d->status);
+    cudaFree(d->J8);
+    cudaFree(d->rowscale);
+    cudaFree(d->phi8[0]);
+    cudaFree(d->phi8[1]);
     if (d->h_status) cudaFreeHost(d->h_status);
     delete d;
+}
+
+// moq_sample_dense (BF16 operands) and moq_sample_dense_fp8 (E4M3 operands, dSB)
+int sample_dense_impl(moq_dense* d, const float* lambda, int32_t R, const moq_sample_params* p, uint64_t seed, uint64_t round,
+                      uint64_t* bits, void* stream, bool f8)
+{
+    if (!d || !p) return fail(MOQ_ERR_ARG, "moq_sample_dense: NULL handle or params");
+    if (R < 0 || R > d->max_R) return fail(MOQ_ERR_ARG, "moq_sample_dense: R=%d outside [0, max_replicas=%d]", R, d->max_R);
+    if (p->steps < 0 || (p->variant != MOQ_DSB && p->variant != MOQ_BSB)) return fail(MOQ_ERR_ARG, "moq_sample_dense: bad steps or variant");
+    if (R == 0) return MOQ_OK;
+    if (!lambda || !bits) return fail(MOQ_ERR_ARG, "moq_sample_dense: NULL lambda or bits");
+    if (p->replica_offset != 0) return fail(MOQ_ERR_UNSUPPORTED, "moq_sample_dense: replica_offset must be 0");
+    if (f8 && p->variant != MOQ_DSB)
+        return fail(MOQ_ERR_UNSUPPORTED, "moq_sample_dense_fp8: E4M3 phi is exact for dSB only (bSB: use moq_sample_dense)");
+    cudaStream_t st = as_stream(stream);
+    const moq_instance* h = d->inst;
+    // replica tiles come in whole clusters (the padded replicas compute on zero weights and
+    // are never written)
+    const int np = d->n_pad, Rp = (int)ceil_div(R, kTileN * d->cluster) * kTileN * d->cluster;
+    const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32), rnd = (uint32_t)round;
+    k_dense_c0<<<R, 256, 0, st>>>(h->rowsum, h->rowptr, h->wn, h->nnz, d->n, d->K, lambda, R, d->c0);
+    const int gi = (int)std::min<int64_t>(ceil_div((int64_t)Rp * np, 256), 148 * 32);
+    if (f8) {
+        k_dense_init<MOQ_DSB, __nv_fp8_e4m3><<<gi, 256, 0, st>>>(d->n, np, R, Rp, p->init_amp, p->x_init, p->y_init, key0, key1, rnd, d->x,
+                                                                 d->y, d->phi8[0]);
+        MOQ_CUDA_TRY(cudaMemsetAsync(d->phi8[1], 0, (size_t)Rp * np, st));  // padded entries stay 0
+    } else {
+        if (p->variant == MOQ_DSB)
+            k_dense_init<MOQ_DSB, __nv_bfloat16><<<gi, 256, 0, st>>>(d->n, np, R, Rp, p->init_amp, p->x_init, p->y_init, key0, key1, rnd,
+                                                                     d->x, d->y, d->phi[0]);
+        else
+            k_dense_init<MOQ_BSB, __nv_bfloat16><<<gi, 256, 0, st>>>(d->n, np, R, Rp, p->init_amp, p->x_init, p->y_init, key0, key1, rnd,
+                                                                     d->x, d->y, d->phi[0]);
+        MOQ_CUDA_TRY(cudaMemsetAsync(d->phi[1], 0, sizeof(__nv_bfloat16) * (size_t)Rp * np, st));  // padded entries stay 0
+    }
+    MOQ_LAUNCH_CHECK("moq_sample_dense prologue");
+    DenseStepArgs a{};
+    a.x = d->x;
+    a.y = d->y;
+    a.lambda = lambda;
+    a.c0 = d->c0;
+    a.n = d->n;
+    a.n_pad = np;
+    a.R = R;
+    a.K = d->K;
+    a.schedule = p->schedule;
+    a.a0 = p->a0;
+    a.dt = p->dt;
+    a.kappa = (p->noise_sqrt_dt ? sqrtf(p->dt) : p->dt) * p->alpha;
+    a.dta0 = p->dt * p->a0;
+    a.key0 = key0;
+    a.key1 = key1;
+    a.round32 = rnd;
+    a.status = d->status;
+    a.rowscale = d->rowscale;
+    const float a0inv = p->steps > 1 ? p->a0 / (float)(p->steps - 1) : 0.0f;
+    const dim3 grid(np / kTileM, Rp / kTileN);
+    const bool noise = p->alpha != 0.0f;
+    if (d->resident && !f8 && p->steps > 0) {
+        // one launch runs every step (n_pad = 128, K <= 3): same arithmetic, same bits
+        ResidentArgs ra{};
+        ra.x = d->x;
+        ra.y = d->y;
+        ra.lambda = lambda;
+        ra.c0 = d->c0;
+        ra.n = d->n;
+        ra.n_pad = np;
+        ra.R = R;
+        ra.K = d->K;
+        ra.T = p->steps;
+        ra.schedule = p->schedule;
+        ra.a0 = a.a0;
+        ra.a0inv = a0inv;
+        ra.dt = a.dt;
+        ra.kappa = a.kappa;
+        ra.dta0 = a.dta0;
+        ra.key0 = key0;
+        ra.key1 = key1;
+        ra.round32 = rnd;
+        ra.status = d->status;
+        const int tiles = (int)ceil_div(R, kTileN);
+        cudaError_t e;
+        if (p->variant == MOQ_DSB)
+            e = noise ? launch_resident_k<MOQ_DSB, true>(d, ra, tiles, st) : launch_resident_k<MOQ_DSB, false>(d, ra, tiles, st);
+        else
+            e = noise ? launch_resident_k<MOQ_BSB, true>(d, ra, tiles, st) : launch_resident_k<MOQ_BSB, false>(d, ra, tiles, st);
+        if (e != cudaSuccess) return cuda_fail(e, "moq_sample_dense resident launch");
+        k_dense_readout<<<R, 128, 0, st>>>(d->n, np, R, h->words, d->x, d->y, bits, p->x_out, p->y_out);
+        MOQ_LAUNCH_CHECK("moq_sample_dense readout");
+        return MOQ_OK;
+    }
+    for (int m = 0; m < p->steps; ++m) {
+        a.m = m;
+        a.cm = fmaf(a0inv, (float)m, -p->a0);
+        const CUtensorMap& tm_in = f8 ? d->tm_phi8[m & 1] : d->tm_phi[m & 1];
+        a.phi_out = d->phi[(m + 1) & 1];
+        a.phi8_out = d->phi8[(m + 1) & 1];
+        cudaError_t e;
+        if (f8)
+            e = noise ? launch_step_cl<MOQ_DSB, true, true>(d, tm_in, a, grid, st) : launch_step_cl<MOQ_DSB, false, true>(d, tm_in, a, grid, st);
+        else if (p->variant == MOQ_DSB)
+            e = noise ? launch_step_cl<MOQ_DSB, true>(d, tm_in, a, grid, st) : launch_step_cl<MOQ_DSB, false>(d, tm_in, a, grid, st);
+        else
+            e = noise ? launch_step_cl<MOQ_BSB, true>(d, tm_in, a, grid, st) : launch_step_cl<MOQ_BSB, false>(d, tm_in, a, grid, st);
+        if (e != cudaSuccess) return cuda_fail(e, "moq_sample_dense step launch");
+    }
+    k_dense_readout<<<R, 128, 0, st>>>(d->n, np, R, h->words, d->x, d->y, bits, p->x_out, p->y_out);
+    MOQ_LAUNCH_CHECK("moq_sample_dense readout");
+    return MOQ_OK;
 }
 
 }  // namespace
@@ -1041,6 +1243,13 @@ int moq_dense_create(const moq_instance* inst, int32_t max_replicas, moq_dense**
     if (e == cudaSuccess) e = cudaMalloc((void**)&d->c0, sizeof(float) * d->R_pad);
     if (e == cudaSuccess) e = cudaMalloc((void**)&d->status, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&d->h_status, sizeof(int32_t));
+    const size_t j8bytes = (size_t)d->K * d->n_pad * d->n_pad;
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d->J8, j8bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d->rowscale, sizeof(float) * (size_t)d->K * d->n_pad);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d->phi8[0], cells);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d->phi8[1], cells);
+    if (e == cudaSuccess) e = cudaMemset(d->J8, 0, j8bytes);
+    if (e == cudaSuccess) e = cudaMemset(d->rowscale, 0, sizeof(float) * (size_t)d->K * d->n_pad);
     if (e == cudaSuccess) e = cudaMemset(d->J, 0, jbytes);
     if (e == cudaSuccess) e = cudaMemset(d->J_hi, 0, jbytes);
     if (e == cudaSuccess) e = cudaMemset(d->J_lo, 0, jbytes);
@@ -1049,6 +1258,11 @@ int moq_dense_create(const moq_instance* inst, int32_t max_replicas, moq_dense**
     if (e == cudaSuccess) {
         k_dense_fill<<<std::min(d->n, 148 * 8), 128>>>(inst->rowptr, inst->col, inst->wn, inst->nnz, d->n, d->K, d->n_pad, d->J,
                                                        d->J_hi, d->J_lo, d->maxabs);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        k_dense_fill8<<<std::min(d->n, 148 * 8), 128>>>(inst->rowptr, inst->col, inst->wn, inst->nnz, d->n, d->K, d->n_pad, d->J8,
+                                                        d->rowscale);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -1071,96 +1285,13 @@ void moq_dense_destroy(moq_dense* d) { moq::free_dense(d); }
 int moq_sample_dense(moq_dense* d, const float* lambda, int32_t R, const moq_sample_params* p, uint64_t seed, uint64_t round,
                      uint64_t* bits, void* stream)
 {
-    using namespace moq;
-    if (!d || !p) return fail(MOQ_ERR_ARG, "moq_sample_dense: NULL handle or params");
-    if (R < 0 || R > d->max_R) return fail(MOQ_ERR_ARG, "moq_sample_dense: R=%d outside [0, max_replicas=%d]", R, d->max_R);
-    if (p->steps < 0 || (p->variant != MOQ_DSB && p->variant != MOQ_BSB)) return fail(MOQ_ERR_ARG, "moq_sample_dense: bad steps or variant");
-    if (R == 0) return MOQ_OK;
-    if (!lambda || !bits) return fail(MOQ_ERR_ARG, "moq_sample_dense: NULL lambda or bits");
-    if (p->replica_offset != 0) return fail(MOQ_ERR_UNSUPPORTED, "moq_sample_dense: replica_offset must be 0");
-    cudaStream_t st = as_stream(stream);
-    const moq_instance* h = d->inst;
-    // replica tiles come in whole clusters (the padded replicas compute on zero weights and
-    // are never written)
-    const int np = d->n_pad, Rp = (int)ceil_div(R, kTileN * d->cluster) * kTileN * d->cluster;
-    const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32), rnd = (uint32_t)round;
-    k_dense_c0<<<R, 256, 0, st>>>(h->rowsum, h->rowptr, h->wn, h->nnz, d->n, d->K, lambda, R, d->c0);
-    const int gi = (int)std::min<int64_t>(ceil_div((int64_t)Rp * np, 256), 148 * 32);
-    if (p->variant == MOQ_DSB)
-        k_dense_init<MOQ_DSB, __nv_bfloat16><<<gi, 256, 0, st>>>(d->n, np, R, Rp, p->init_amp, p->x_init, p->y_init, key0, key1, rnd, d->x, d->y, d->phi[0]);
-    else
-        k_dense_init<MOQ_BSB, __nv_bfloat16><<<gi, 256, 0, st>>>(d->n, np, R, Rp, p->init_amp, p->x_init, p->y_init, key0, key1, rnd, d->x, d->y, d->phi[0]);
-    MOQ_CUDA_TRY(cudaMemsetAsync(d->phi[1], 0, sizeof(__nv_bfloat16) * (size_t)Rp * np, st));  // padded entries stay 0
-    MOQ_LAUNCH_CHECK("moq_sample_dense prologue");
-    DenseStepArgs a{};
-    a.x = d->x;
-    a.y = d->y;
-    a.lambda = lambda;
-    a.c0 = d->c0;
-    a.n = d->n;
-    a.n_pad = np;
-    a.R = R;
-    a.K = d->K;
-    a.schedule = p->schedule;
-    a.a0 = p->a0;
-    a.dt = p->dt;
-    a.kappa = (p->noise_sqrt_dt ? sqrtf(p->dt) : p->dt) * p->alpha;
-    a.dta0 = p->dt * p->a0;
-    a.key0 = key0;
-    a.key1 = key1;
-    a.round32 = rnd;
-    a.status = d->status;
-    const float a0inv = p->steps > 1 ? p->a0 / (float)(p->steps - 1) : 0.0f;
-    const dim3 grid(np / kTileM, Rp / kTileN);
-    const bool noise = p->alpha != 0.0f;
-    if (d->resident && p->steps > 0) {
-        // one launch runs every step (n_pad = 128, K <= 3): same arithmetic, same bits
-        ResidentArgs ra{};
-        ra.x = d->x;
-        ra.y = d->y;
-        ra.lambda = lambda;
-        ra.c0 = d->c0;
-        ra.n = d->n;
-        ra.n_pad = np;
-        ra.R = R;
-        ra.K = d->K;
-        ra.T = p->steps;
-        ra.schedule = p->schedule;
-        ra.a0 = a.a0;
-        ra.a0inv = a0inv;
-        ra.dt = a.dt;
-        ra.kappa = a.kappa;
-        ra.dta0 = a.dta0;
-        ra.key0 = key0;
-        ra.key1 = key1;
-        ra.round32 = rnd;
-        ra.status = d->status;
-        const int tiles = (int)ceil_div(R, kTileN);
-        cudaError_t e;
-        if (p->variant == MOQ_DSB)
-            e = noise ? launch_resident_k<MOQ_DSB, true>(d, ra, tiles, st) : launch_resident_k<MOQ_DSB, false>(d, ra, tiles, st);
-        else
-            e = noise ? launch_resident_k<MOQ_BSB, true>(d, ra, tiles, st) : launch_resident_k<MOQ_BSB, false>(d, ra, tiles, st);
-        if (e != cudaSuccess) return cuda_fail(e, "moq_sample_dense resident launch");
-        k_dense_readout<<<R, 128, 0, st>>>(d->n, np, R, h->words, d->x, d->y, bits, p->x_out, p->y_out);
-        MOQ_LAUNCH_CHECK("moq_sample_dense readout");
-        return MOQ_OK;
-    }
-    for (int m = 0; m < p->steps; ++m) {
-        a.m = m;
-        a.cm = fmaf(a0inv, (float)m, -p->a0);
-        const CUtensorMap& tm_in = d->tm_phi[m & 1];
-        a.phi_out = d->phi[(m + 1) & 1];
-        cudaError_t e;
-        if (p->variant == MOQ_DSB)
-            e = noise ? launch_step_cl<MOQ_DSB, true>(d, tm_in, a, grid, st) : launch_step_cl<MOQ_DSB, false>(d, tm_in, a, grid, st);
-        else
-            e = noise ? launch_step_cl<MOQ_BSB, true>(d, tm_in, a, grid, st) : launch_step_cl<MOQ_BSB, false>(d, tm_in, a, grid, st);
-        if (e != cudaSuccess) return cuda_fail(e, "moq_sample_dense step launch");
-    }
-    k_dense_readout<<<R, 128, 0, st>>>(d->n, np, R, h->words, d->x, d->y, bits, p->x_out, p->y_out);
-    MOQ_LAUNCH_CHECK("moq_sample_dense readout");
-    return MOQ_OK;
+    return moq::sample_dense_impl(d, lambda, R, p, seed, round, bits, stream, false);
+}
+
+int moq_sample_dense_fp8(moq_dense* d, const float* lambda, int32_t R, const moq_sample_params* p, uint64_t seed, uint64_t round,
+                         uint64_t* bits, void* stream)
+{
+    return moq::sample_dense_impl(d, lambda, R, p, seed, round, bits, stream, true);
 }
 
 int moq_dense_evaluate_cuts(moq_dense* d, const uint64_t* bits, int32_t M, int64_t* cuts, void* stream)

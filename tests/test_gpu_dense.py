@@ -377,3 +377,101 @@ def test_dense_fp32_rejects_bad_arguments(M, P):
         assert e.value.code == M.MOQ_ERR_ARG
     finally:
         M.moq_dense_fp32_destroy(d)
+
+
+# ---- the FP8 (E4M3) form of the dSB step ------------------------------------------------
+
+@pytest.mark.parametrize("n,R,K,alpha,sched", [(300, 300, 3, 0.1, False), (100, 130, 3, 0.15, False), (257, 64, 4, 0.1, True),
+                                                (129, 1, 2, 0.0, False)])
+def test_dense_fp8_matches_bf16_form_for_small_weights(M, P, n, R, K, alpha, sched):
+    # |J| <= 16 is exact in E4M3 (row scale 1) and phi = +-1 is exact, so every per-objective
+    # product is the same exact integer as with BF16 operands: the FP8 form gives the bits,
+    # x and y of moq_sample_dense (per-step or resident kernel) over a noisy trajectory
+    src = wl.random_graph(n, 1.0, 3 + n + R, K=K, wmax=16)
+    inst = P.Instance(src)
+    T = 40
+    lam = _dev(wl.dirichlet_lambdas(R, K, 14))
+    schedule = torch.linspace(0.0, 1.0, T, device="cuda") ** 2 if sched else None
+    d = M.moq_dense_create(inst.handle, R)
+    out = {}
+    try:
+        for form in ("bf16", "fp8"):
+            xo = torch.zeros((R, n), device="cuda")
+            yo = torch.zeros((R, n), device="cuda")
+            bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+            p = M.moq_default_params(variant="dsb", steps=T, dt=0.5, alpha=alpha, schedule=schedule, x_out=xo, y_out=yo)
+            (M.moq_sample_dense if form == "bf16" else M.moq_sample_dense_fp8)(d, lam, R, p, 23, 1, bits)
+            M.moq_dense_status(d)
+            out[form] = (bits.cpu(), xo.cpu(), yo.cpu())
+    finally:
+        M.moq_dense_destroy(d)
+    for a, b in zip(out["bf16"], out["fp8"]):
+        assert torch.equal(a, b)
+    assert R == 1 or len(torch.unique(out["fp8"][0], dim=0)) > 1
+
+
+@pytest.mark.parametrize("n,R,K", [(300, 200, 3), (130, 129, 4), (64, 1, 2)])
+def test_dense_fp8_force_within_e4m3_bound(M, P, oracle, n, R, K):
+    # the dense workload's weights (|J| up to about 5000): J rounds to E4M3 with a power-of-two
+    # row scale (relative error <= 2^-4 per weight, 2^-4 = half an E4M3 ulp), phi = +-1 exact,
+    # FP32 accumulation: |f - f64| <= 2^-4 c0 sum_j |J(c)_ij phi_j| against the FP64 oracle
+    src = wl.complete_graph(n, 80 + n, K=K)
+    inst = P.Instance(src)
+    d = M.moq_dense_create(inst.handle, R)
+    try:
+        lam = wl.dirichlet_lambdas(R, K, 2)
+        x0 = np.random.default_rng(3).uniform(-0.5, 0.5, (R, n)).astype(np.float32)
+        dt = 2.0 ** -10
+        yo = torch.zeros((R, n), device="cuda")
+        p = M.moq_default_params(variant="dsb", steps=1, dt=dt, alpha=0.0, schedule=torch.ones(1, device="cuda"),
+                                 x_init=_dev(x0), y_init=torch.zeros((R, n), device="cuda"), y_out=yo)
+        bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+        M.moq_sample_dense_fp8(d, _dev(lam), R, p, 0, 0, bits)
+        M.moq_dense_status(d)
+        f_gpu = yo.cpu().numpy().astype(np.float64) / dt
+    finally:
+        M.moq_dense_destroy(d)
+    ref = oracle.sb(src, lam.astype(np.float64), variant="dsb", steps=1, dt=dt, alpha=0.0, schedule=[1.0],
+                    x_init=x0.astype(np.float64), y_init=np.zeros((R, n)))
+    scale = _abs_force_scale(src, lam, np.where(x0 >= 0, 1.0, -1.0), ref["c0"])
+    rel = np.abs(f_gpu - ref["y"] / dt) / np.maximum(scale, 1e-30)
+    assert rel.max() <= 2.0 ** -4, float(rel.max())
+    assert rel.max() > 1e-5  # the weights really are rounded (not the exact path)
+
+
+@pytest.mark.parametrize("cl", ["2", "4"])
+def test_dense_fp8_cluster_sizes_agree_bitwise(M, P, cl, monkeypatch):
+    # E4M3 J tiles multicast over clusters of 2 or 4 CTAs give the bits of single CTAs
+    src = wl.complete_graph(300, 33, K=3)
+    inst = P.Instance(src)
+    R, T = 700, 7
+    lam = _dev(wl.dirichlet_lambdas(R, 3, 8))
+    out = {}
+    for c in ("1", cl):
+        monkeypatch.setenv("MOQ_DENSE_CLUSTER", c)
+        d = M.moq_dense_create(inst.handle, R)
+        try:
+            xo = torch.zeros((R, src.n), device="cuda")
+            bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+            p = M.moq_default_params(variant="dsb", steps=T, dt=0.5, alpha=0.1, x_out=xo)
+            M.moq_sample_dense_fp8(d, lam, R, p, 3, 1, bits)
+            M.moq_dense_status(d)
+            out[c] = (bits.cpu(), xo.cpu())
+        finally:
+            M.moq_dense_destroy(d)
+    for a, b in zip(out["1"], out[cl]):
+        assert torch.equal(a, b)
+
+
+def test_dense_fp8_rejects_bsb(M, P):
+    src = wl.random_graph(40, 1.0, 3, K=2, wmax=10)
+    inst = P.Instance(src)
+    d = M.moq_dense_create(inst.handle, 16)
+    try:
+        p = M.moq_default_params(variant="bsb", steps=3)
+        with pytest.raises(M.MoqError) as e:
+            M.moq_sample_dense_fp8(d, _dev(np.full((16, 2), 0.5)), 16, p, 0, 0,
+                                   torch.zeros((16, 1), dtype=torch.int64, device="cuda"))
+        assert e.value.code == M.MOQ_ERR_UNSUPPORTED
+    finally:
+        M.moq_dense_destroy(d)
