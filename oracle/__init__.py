@@ -74,6 +74,10 @@ def _load():
             lib.or_mlp_forward.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.c_int64, dp, dp]
             lib.or_mlp_loss_grad.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.c_int64, dp, dp, dp]
             lib.or_mlp_loss_grad.restype = C.c_double
+            lib.or_e4m3.argtypes = [C.c_double]
+            lib.or_e4m3.restype = C.c_double
+            lib.or_e4m3_couplings.argtypes = [C.c_int, C.c_int, C.c_int64, i32p, i32p, i32p, dp, dp, dp]
+            lib.or_force_e4m3.argtypes = [C.c_int, C.c_int, C.c_int64, i32p, i32p, dp, dp, C.c_int, dp, dp, dp, dp]
             _lib = lib
     return _lib
 
@@ -220,3 +224,32 @@ def mlp_loss_grad(params, X, T, din: int, h: int, dout: int):
     g = np.zeros(mlp_param_count(din, h, dout), np.float64)
     loss = _load().or_mlp_loss_grad(din, h, dout, np.ascontiguousarray(params, np.float64), X.shape[0], X, T, g)
     return loss, g
+
+
+def e4m3(values) -> np.ndarray:
+    """Nearest E4M3 value of each input (ties to an even mantissa, saturating at +-448)."""
+    v = np.asarray(values, np.float64)
+    lib = _load()
+    return np.array([lib.or_e4m3(float(a)) for a in v.ravel()]).reshape(v.shape)
+
+
+def e4m3_couplings(inst):
+    """Couplings of the FP8 force: (wq_i, wq_j, scale): the value of each edge's weight as
+    seen from row ei and from row ej (K x E each) and the power-of-two row scales (K x n)."""
+    ei, ej, w = _inst_arrays(inst)
+    K, E = w.shape
+    wq_i = np.zeros((K, E)); wq_j = np.zeros((K, E)); sc = np.zeros((K, inst.n))
+    _load().or_e4m3_couplings(inst.n, K, E, ei, ej, w, wq_i, wq_j, sc)
+    return wq_i, wq_j, sc
+
+
+def force_e4m3(inst, lam, phi, c0) -> np.ndarray:
+    """One-step SB force c0 sum_j (-J(c)_ij) phi_j with the FP8 couplings (R x n)."""
+    ei, ej, _ = _inst_arrays(inst)
+    wq_i, wq_j, _ = e4m3_couplings(inst)
+    lam = np.ascontiguousarray(np.asarray(lam, np.float64).reshape(-1, inst.K))
+    phi = np.ascontiguousarray(np.asarray(phi, np.float64))
+    c0 = np.ascontiguousarray(np.asarray(c0, np.float64))
+    f = np.zeros_like(phi)
+    _load().or_force_e4m3(inst.n, inst.K, wq_i.shape[1], ei, ej, wq_i, wq_j, lam.shape[0], lam, c0, phi, f)
+    return f

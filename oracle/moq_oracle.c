@@ -24,6 +24,10 @@
  *                     it goes through libm log/cos/sin).
  *   or_dirichlet      pinned: simplex sums, moments of Dirichlet(1,..,1).
  *   or_mlp_*          pinned: central finite differences of the loss.
+ *   or_e4m3           pinned: torch's float8_e4m3fn conversion (nearest even) on every
+ *                     midpoint and random values, hand values (ties, saturation).
+ *   or_force_e4m3     pinned: equals the one-step force of or_sb when every weight is
+ *                     exact in E4M3; the row scales by hand; error bound 2^-4.
  */
 #include <math.h>
 #include <stdint.h>
@@ -460,6 +464,89 @@ int or_sb(int n, int K, int64_t E, const int32_t* ei, const int32_t* ej, const i
     }
     free(rowsum);
     return status;
+}
+
+/* ------------------------------------------------------------------------------------
+ * FP8 operands of the dense dSB force (the precision growth of the force contraction;
+ * the paper itself runs float16). E4M3 (the OCP 8-bit floating-point format): a sign,
+ * 4 exponent bits with bias 7 and 3 mantissa bits; the normal values are
+ * (1 + m/8) 2^(e-7) for e = 1..15 except e = 15, m = 7 (NaN), the subnormal ones m 2^-9,
+ * so the largest finite value is 448. or_e4m3 returns the value of that set nearest to v,
+ * on a tie the one whose mantissa field m is even, saturating at +-448; it walks the 127
+ * non-negative values in increasing order, by the definition.
+ * ---------------------------------------------------------------------------------- */
+double or_e4m3(double v)
+{
+    double a = fabs(v), best = 0.0, bestd = a;
+    int bestm = 0;
+    for (int e = 0; e <= 15; ++e)
+        for (int m = 0; m <= 7; ++m) {
+            if (e == 15 && m == 7) continue;
+            double val = (e == 0) ? ldexp((double)m, -9) : ldexp(1.0 + m / 8.0, e - 7);
+            double d = fabs(a - val);
+            if (d < bestd || (d == bestd && (m & 1) == 0 && (bestm & 1) == 1)) {
+                best = val;
+                bestd = d;
+                bestm = m;
+            }
+        }
+    if (a > 448.0) best = 448.0;
+    return v < 0.0 ? -best : best;
+}
+
+/* The couplings the FP8 force uses (reading: one power-of-two scale per row and
+ * objective). For row i of objective k, s = 2^e with e >= 0 the smallest exponent such
+ * that max_j |J^(k)_ij| <= 448 s, and the coupling J^(k)_ij enters row i as
+ * s * E4M3(J^(k)_ij / s). An edge e = (ei, ej) thus has one value for row ei (wq_i) and
+ * one for row ej (wq_j), both K x E; scale is K x n. */
+void or_e4m3_couplings(int n, int K, int64_t E, const int32_t* ei, const int32_t* ej, const int32_t* w,
+                       double* wq_i, double* wq_j, double* scale)
+{
+    for (int k = 0; k < K; ++k) {
+        double* sc = scale + (int64_t)k * n;
+        double* mx = (double*)calloc((size_t)n, sizeof(double));
+        for (int64_t e = 0; e < E; ++e) {
+            double a = fabs((double)w[(int64_t)k * E + e]);
+            if (a > mx[ei[e]]) mx[ei[e]] = a;
+            if (a > mx[ej[e]]) mx[ej[e]] = a;
+        }
+        for (int i = 0; i < n; ++i) {
+            double s = 1.0;
+            while (mx[i] > 448.0 * s) s *= 2.0;
+            sc[i] = s;
+        }
+        for (int64_t e = 0; e < E; ++e) {
+            double v = (double)w[(int64_t)k * E + e];
+            wq_i[(int64_t)k * E + e] = sc[ei[e]] * or_e4m3(v / sc[ei[e]]);
+            wq_j[(int64_t)k * E + e] = sc[ej[e]] * or_e4m3(v / sc[ej[e]]);
+        }
+        free(mx);
+    }
+}
+
+/* The SB force c0 sum_j (-J(c)_ij) phi_j (SB equations, negated coupling) of R replicas
+ * with the couplings of or_e4m3_couplings: J(c)_ij = sum_k c_k wq^(k) of the edge as seen
+ * from row i. c0 (R) is given (the FP8 step keeps the c0 of the exact weights). phi and
+ * f are R x n. */
+void or_force_e4m3(int n, int K, int64_t E, const int32_t* ei, const int32_t* ej, const double* wq_i, const double* wq_j,
+                   int R, const double* lambda, const double* c0, const double* phi, double* f)
+{
+    for (int r = 0; r < R; ++r) {
+        const double* c = lambda + (int64_t)r * K;
+        const double* p = phi + (int64_t)r * n;
+        double* fr = f + (int64_t)r * n;
+        for (int i = 0; i < n; ++i) fr[i] = 0.0;
+        for (int64_t e = 0; e < E; ++e) {
+            double ji = 0.0, jj = 0.0;
+            for (int k = 0; k < K; ++k) {
+                ji += c[k] * wq_i[(int64_t)k * E + e];
+                jj += c[k] * wq_j[(int64_t)k * E + e];
+            }
+            fr[ei[e]] += -ji * p[ej[e]];
+            fr[ej[e]] += -jj * p[ei[e]];
+        }
+        for (int i = 0; i < n; ++i) fr[i] *= c0[r];
+    }
 }
 
 /* Reference point r_k = sum_E min(0, J^(k)_e): every cut value satisfies C_k(s) >= r_k
