@@ -272,6 +272,30 @@ def gpu_arm(args, rank, world):
     e2e = {"value": R * n * T * e2e_steps / e2e_s * world, "unit": METRIC,
            "h2d_bytes_per_step": R * K * 4, "d2h_bytes_per_step": 8 + 4 + 8 + 4 + 16 + 4}
 
+    # the configuration's second variant: NI-bSB (phi = x) on the same instance, weight
+    # vectors and step structure, timed the same way (L2 flushed before every step)
+    params_b = M.moq_default_params(variant="bsb", steps=T, dt=w["dt"], a0=w["a0"], alpha=w["alpha"],
+                                    init_amp=w["init_amp"], replica_offset=first)
+    nb = max(1, min(args.steps, 5))
+    evb = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+            torch.cuda.Event(enable_timing=True)) for _ in range(nb + 1)]
+    for s in range(nb + 1):  # the first is a warm-up
+        flush.zero_()
+        arch.reset()
+        evb[s][0].record(stream)
+        M.moq_sample(inst.handle, lam_all[s % nsteps], R, params_b, 2, s, buf.bits)
+        evb[s][1].record(stream)
+        M.moq_evaluate_cuts(inst.handle, buf.bits, R, buf.cuts)
+        arch.merge(buf.cuts, buf.bits, R, 0)
+        hv_b = arch.hypervolume(inst.ref)
+        evb[s][2].record(stream)
+    torch.cuda.synchronize()
+    b_step = shard.max_over_ranks([sum(evb[s][0].elapsed_time(evb[s][2]) for s in range(1, nb + 1)) / nb / 1e3])[0]
+    b_samp = shard.max_over_ranks([sum(evb[s][0].elapsed_time(evb[s][1]) for s in range(1, nb + 1)) / nb / 1e3])[0]
+    bsb = {"variant": "NI-bSB, same workload", "steps_timed": nb, "ms_per_step": b_step * 1e3, "sampler_ms": b_samp * 1e3,
+           "value": R * n * T * world / b_step, "sampling_only_value": R * n * T * world / b_samp,
+           "front_points": arch.size(), "hv": int(hv_b)}
+
     peaks = measured_peaks()
     ops = ops_per_spin_update(2.0 * src.E / n)
     sample_avg = samp_s / args.steps
@@ -285,7 +309,7 @@ def gpu_arm(args, rank, world):
                 "hbm_peak_measured_gbs": peaks.get("hbm_gbs")}
     return {"value": value, "ms_per_step": dev_s / args.steps * 1e3, "wall_s": t_wall, "e2e": e2e,
             "roofline": roofline, "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps,
-            "front_last": fronts[-1], "hv_last": int(hvs[-1]), "sampling_only_value": units / samp_s,
+            "front_last": fronts[-1], "hv_last": int(hvs[-1]), "sampling_only_value": units / samp_s, "bsb": bsb,
             "inst": inst, "src": src, "params": params}
 
 
@@ -938,7 +962,7 @@ def main():
                 "roofline": res["roofline"], "cpu_baseline": cpu_base, "e2e": res["e2e"], "clocks": res["clocks"],
                 "gpu_launches": res["gpu_launches"], "sampling_only_value": res["sampling_only_value"],
                 "front_points_last_step": res["front_last"], "hv_last_step": res["hv_last"],
-                "time_to_99pct_hv": ttt}
+                "bsb": res["bsb"], "time_to_99pct_hv": ttt}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -475,3 +475,32 @@ def test_dense_fp8_rejects_bsb(M, P):
         assert e.value.code == M.MOQ_ERR_UNSUPPORTED
     finally:
         M.moq_dense_destroy(d)
+
+
+@pytest.mark.parametrize("n,R,K", [(300, 200, 3), (130, 129, 4), (64, 1, 2), (257, 70, 3)])
+def test_dense_fp8_force_matches_oracle_e4m3_force(M, P, oracle, n, R, K):
+    # parity of the FP8 form proper: the oracle's force with the same E4M3 couplings (row
+    # scales, nearest-even rounding) in FP64; the E4M3 products are exact and only the FP32
+    # accumulation and combination differ, so the 1e-5 normwise FP32 bound applies
+    src = wl.complete_graph(n, 90 + n, K=K)
+    inst = P.Instance(src)
+    d = M.moq_dense_create(inst.handle, R)
+    try:
+        lam = wl.dirichlet_lambdas(R, K, 6)
+        x0 = np.random.default_rng(7).uniform(-0.5, 0.5, (R, n)).astype(np.float32)
+        dt = 2.0 ** -10
+        yo = torch.zeros((R, n), device="cuda")
+        p = M.moq_default_params(variant="dsb", steps=1, dt=dt, alpha=0.0, schedule=torch.ones(1, device="cuda"),
+                                 x_init=_dev(x0), y_init=torch.zeros((R, n), device="cuda"), y_out=yo)
+        bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+        M.moq_sample_dense_fp8(d, _dev(lam), R, p, 0, 0, bits)
+        M.moq_dense_status(d)
+        f_gpu = yo.cpu().numpy().astype(np.float64) / dt
+    finally:
+        M.moq_dense_destroy(d)
+    phi = np.where(x0 >= 0, 1.0, -1.0)
+    c0 = oracle.sb(src, lam.astype(np.float64), steps=0, x_init=np.zeros((R, n)))["c0"]
+    f_ref = oracle.force_e4m3(src, lam.astype(np.float64), phi, c0)
+    scale = _abs_force_scale(src, lam, phi, c0)
+    err = np.abs(f_gpu - f_ref)
+    assert np.all(err <= 1e-5 * scale + 1e-30), float((err / np.maximum(scale, 1e-30)).max())
