@@ -326,9 +326,13 @@ def time_to_target_block(args, src):
     inst = P.Instance(src)
     arch = P.Archive(src.n, src.K, capacity=1 << 18, max_batch=w["R"])
     buf = P.RoundBuffers(1024, src.n, src.K)
-    for rnd in range(args.ttt_rounds):
-        P.sample_round(inst, arch, buf, plain, seed=4242, round_=rnd)
-    hv_plain_final = arch.hypervolume(inst.ref)
+    finals = []
+    for seed in range(args.ttt_seeds):  # the plain sampler's final HV: lower median over the seeds
+        arch.reset()
+        for rnd in range(args.ttt_rounds):
+            P.sample_round(inst, arch, buf, plain, seed=4242 + seed, round_=rnd)
+        finals.append(arch.hypervolume(inst.ref))
+    hv_plain_final = statistics.median_low(finals)
     arch.close()
     inst.close()
     torch.cuda.synchronize()
@@ -340,8 +344,9 @@ def time_to_target_block(args, src):
             ("chosen_dsb_R16384_T200_alpha0.1", chosen, 16384, False),
             ("chosen+learned_R4096_T200_alpha0.1", chosen, 4096, True)]
     res = {"hv_plain_final": int(hv_plain_final), "plain_budget_rounds": args.ttt_rounds,
+           "hv_plain_final_range": [int(min(finals)), int(max(finals))],
            "clock": "instance build + rounds (weight vectors, sampling, cuts, Pareto merge, surrogate) + one HV check per round",
-           "seeds": 5}
+           "seeds": args.ttt_seeds}
     for frac_label, num in (("99%", 99), ("99.9%", 999)):
         den = 100 if num == 99 else 1000
         target = (hv_plain_final * num + den - 1) // den
@@ -349,10 +354,12 @@ def time_to_target_block(args, src):
         for label, params, R, learned in arms:
             P.time_to_target(src, target, params, R, seed=99, max_rounds=2, learned=learned)  # warm-up
             runs = [P.time_to_target(src, target, params, R, seed=s, max_rounds=4 * args.ttt_rounds, learned=learned)
-                    for s in range(5)]
-            block[label] = {"seconds_median": float(np.median([r["seconds"] for r in runs])),
+                    for s in range(args.ttt_seeds)]
+            secs = [r["seconds"] for r in runs]
+            block[label] = {"seconds_median": float(np.median(secs)),
+                            "seconds_p10_p90": [float(np.percentile(secs, 10)), float(np.percentile(secs, 90))],
                             "samples_median": int(np.median([r["samples"] for r in runs])),
-                            "reached": all(r["reached"] for r in runs)}
+                            "reached": sum(r["reached"] for r in runs), "of": len(runs)}
         res[frac_label] = block
     return res
 
@@ -886,6 +893,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ttt-rounds", type=int, default=64)
+    ap.add_argument("--ttt-seeds", type=int, default=32, help="seeds of the time-to-target medians")
     ap.add_argument("--no-ttt", action="store_true")
     ap.add_argument("--cpu-baseline-worker", action="store_true")
     ap.add_argument("--workload", default="precision", choices=["precision", "batching", "dense", "paper", "appendix_e"],
