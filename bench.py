@@ -502,7 +502,8 @@ def dense_arm(args, rank, world):
     achieved = flops / samp_s / 1e12
     front = arch.size()
     plain = dense_plain_fp32(args, M, inst, d, lam, src) if args.dense_fp32_steps > 0 else None
-    fp8 = dense_fp8_dsb(args, M, d, lam, src) if args.dense_fp8_steps > 0 else None
+    forms = dense_operand_forms(args, M, d, lam, src) if args.dense_fp8_steps > 0 else None
+    forms_hv = dense_forms_hv(args, M, P, inst, d, src) if args.dense_hv_rounds > 0 else None
     M.moq_dense_destroy(d)
     if plain is not None:
         plain["chosen_speedup_per_sb_step"] = plain["ms_per_sb_step"] / (samp_s / args.steps / T * 1e3)
@@ -520,7 +521,7 @@ def dense_arm(args, rank, world):
                          "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16, seconds-long loop)"},
             "sampling_only_value": units / samp_s * world, "sampler_ms": samp_s / args.steps * 1e3,
             "clocks": clk.summary(), "front_points_last_step": front, "hv_last_step": int(hv[0]),
-            "plain_fp32": plain, "fp8_dsb": fp8,
+            "plain_fp32": plain, "operand_forms": forms, "forms_hv": forms_hv,
             # c0, init, T steps, readout; cuts: signs, two products, finish; merge 12; HV 4
             "gpu_launches": (T + 3 + 4 + 12 + 4) * args.steps}
 
@@ -606,23 +607,89 @@ def dense_plain_fp32(args, M, inst, d, lam, src):
                                             **dsb_err)}
 
 
-def dense_fp8_dsb(args, M, d, lam, src):
-    """dSB on the dense workload with BF16 operands (moq_sample_dense) and with E4M3 operands
-    (moq_sample_dense_fp8: J rounded to E4M3 with power-of-two row scales, phi = +-1 exact),
-    --dense-fp8-steps SB steps each on the same handle, CUDA events on the launching stream,
-    the per-step time from the difference of two lengths (start-up and read-out cancel)."""
+def dense_forms_hv(args, M, P, inst, d, src):
+    """Sample quality per unit time of the three dense forms on the dense instance: rounds of
+    2048 NI-dSB replicas (T = 500, dt = 0.5, alpha = 0.1, the same uniform-simplex weight
+    vectors per round for every form) with FP32 operands on the CUDA cores, BF16, E4M3 and
+    split (BF16(J) + exact residual: the FP32 form's exact products) operands on the tensor cores; exact cuts (tensor cores), Pareto merge and HV after every
+    round. Reports the sampler time per round, the HV after each round and how long each
+    form needs to reach 99% / 99.9% of the FP32 form's final HV (sampler + cuts + merge + HV
+    time, CUDA events on the launching stream)."""
+    import torch
+
+    from paper_2604_26477_b300 import workloads as wl
+
+    n, K = src.n, src.K
+    R, T, rounds = 2048, 500, args.dense_hv_rounds
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    lams = [torch.from_numpy(wl.dirichlet_lambdas(R, K, 300 + rnd)).to(dev) for rnd in range(rounds)]
+    bits = torch.zeros((R, inst.W), dtype=torch.int64, device=dev)
+    cuts = torch.zeros((R, K), dtype=torch.int64, device=dev)
+    p = M.moq_default_params(variant="dsb", steps=T, dt=0.5, alpha=0.1)
+    d32 = M.moq_dense_fp32_create(inst.handle, R)
+    forms = {"fp32": lambda lam, rnd: M.moq_sample_dense_fp32(d32, lam, R, p, 5, rnd, bits),
+             "bf16": lambda lam, rnd: M.moq_sample_dense(d, lam, R, p, 5, rnd, bits),
+             "fp8": lambda lam, rnd: M.moq_sample_dense_fp8(d, lam, R, p, 5, rnd, bits),
+             "split": lambda lam, rnd: M.moq_sample_dense_split(d, lam, R, p, 5, rnd, bits)}
+    out = {}
+    try:
+        for form, run in forms.items():
+            run(lams[0], 99)  # warm-up
+            arch = P.Archive(n, K, capacity=1 << 16, max_batch=R)
+            t, traj, samp = 0.0, [], []
+            for rnd in range(rounds):
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                e0.record(stream)
+                run(lams[rnd], rnd)
+                e1.record(stream)
+                M.moq_dense_evaluate_cuts(d, bits, R, cuts)
+                arch.merge(cuts, bits, R, rnd * R)
+                hv = arch.hypervolume(inst.ref)
+                e2.record(stream)
+                torch.cuda.synchronize()
+                t += e0.elapsed_time(e2) / 1e3
+                samp.append(e0.elapsed_time(e1))
+                traj.append((t, hv))
+            out[form] = {"sampler_ms_per_round": float(np.median(samp)), "hv_per_round": [int(h) for _, h in traj],
+                         "seconds_per_round": [float(x) for x, _ in traj], "front_points": arch.size()}
+            arch.close()
+    finally:
+        M.moq_dense_fp32_destroy(d32)
+    M.moq_dense_status(d)
+    # the reference point r_k = sum_E min(0, J) lies far below the front, so 99% of the HV is
+    # reached by any form in one round; the forms differ in the last digits: report the relative
+    # gap to the FP32 form's final HV and the time to reach the FP32 form's first-round HV
+    final = out["fp32"]["hv_per_round"][-1]
+    first = out["fp32"]["hv_per_round"][0]
+    for form in out:
+        out[form]["rel_gap_to_fp32_final"] = [float((final - h) / final) for h in out[form]["hv_per_round"]]
+        hit = [x for x, h in zip(out[form]["seconds_per_round"], out[form]["hv_per_round"]) if h >= first]
+        out[form]["seconds_to_fp32_round1_hv"] = hit[0] if hit else None
+    return {"rounds": rounds, "R": R, "T": T, "variant": "NI-dSB alpha=0.1 dt=0.5", "fp32_final_hv": int(final), **out}
+
+
+def dense_operand_forms(args, M, d, lam, src):
+    """Per-SB-step time of the operand forms of the tensor-core step on the dense workload, on
+    the same handle: dSB with BF16, E4M3 (moq_sample_dense_fp8) and split (moq_sample_dense_split:
+    BF16(J) + exact residual, two passes) operands, bSB with BF16 and split (three passes)
+    operands; --dense-fp8-steps SB steps each, CUDA events on the launching stream, the per-step
+    time from the difference of two lengths (start-up and read-out cancel)."""
     import torch
 
     n, K, R = src.n, src.K, lam.shape[0]
     T = args.dense_fp8_steps
     bits = torch.zeros((R, (n + 63) // 64), dtype=torch.int64, device=lam.device)
     stream = torch.cuda.current_stream()
+    runs = (("dsb_bf16", "dsb", M.moq_sample_dense), ("dsb_fp8", "dsb", M.moq_sample_dense_fp8),
+            ("dsb_split", "dsb", M.moq_sample_dense_split), ("bsb_bf16", "bsb", M.moq_sample_dense),
+            ("bsb_split", "bsb", M.moq_sample_dense_split))
     out = {}
     with ClockSampler(lam.device.index) as clk:
-        for form, fn in (("bf16", M.moq_sample_dense), ("fp8", M.moq_sample_dense_fp8)):
+        for name, variant, fn in runs:
             ms = {}
             for steps in (10, 10 + T):
-                p = M.moq_default_params(variant="dsb", steps=steps, dt=0.5, alpha=0.1)
+                p = M.moq_default_params(variant=variant, steps=steps, dt=0.5, alpha=0.1)
                 fn(d, lam, R, p, 1, 0, bits)  # warm-up of this length
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
@@ -630,17 +697,20 @@ def dense_fp8_dsb(args, M, d, lam, src):
                 e1.record(stream)
                 torch.cuda.synchronize()
                 ms[steps] = e0.elapsed_time(e1)
-            out[form] = (ms[10 + T] - ms[10]) / T
+            out[name] = (ms[10 + T] - ms[10]) / T
     M.moq_dense_status(d)
     flops = 2.0 * K * n * n * R
     peaks = measured_peaks()
-    peak = 2.0 * peaks.get("bf16_tflops_sustained", 1392.4)
-    ach = flops / (out["fp8"] * 1e-3) / 1e12
-    return {"kernel": "k_dense_step_ws<dSB, K, noise, 1, F8 = true> (tcgen05.mma kind::f8f6f4, E4M3 x E4M3 -> FP32)",
-            "sb_steps_timed": T, "ms_per_sb_step_fp8": out["fp8"], "ms_per_sb_step_bf16": out["bf16"],
-            "fp8_speedup": out["bf16"] / out["fp8"], "replica_spin_updates_per_s_fp8": n * R / (out["fp8"] * 1e-3),
-            "achieved_tflops": ach, "peak_tflops": peak, "frac": ach / peak,
-            "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained x 2 (nominal dense FP8/BF16 ratio)",
+    bf16 = peaks.get("bf16_tflops_sustained", 1392.4)
+    ach = {k: flops / (v * 1e-3) / 1e12 for k, v in out.items()}
+    return {"sb_steps_timed": T, "ms_per_sb_step": out, "algorithmic_tflops": ach,
+            "fp8_dsb": {"kernel": "k_dense_step_ws<dSB, K, noise, 1, E4M3> (tcgen05.mma kind::f8f6f4, E4M3 x E4M3 -> FP32)",
+                        "speedup_vs_bf16": out["dsb_bf16"] / out["dsb_fp8"], "achieved_tflops": ach["dsb_fp8"],
+                        "peak_tflops": 2.0 * bf16, "frac": ach["dsb_fp8"] / (2.0 * bf16),
+                        "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained x 2 (nominal dense FP8/BF16 ratio)"},
+            "split": {"note": "executed products: 2x (dSB) or 3x (bSB) the algorithmic flops, on BF16 tensor cores",
+                      "dsb_executed_frac_of_bf16_sustained": 2.0 * ach["dsb_split"] / bf16,
+                      "bsb_executed_frac_of_bf16_sustained": 3.0 * ach["bsb_split"] / bf16},
             "clocks": clk.summary()}
 
 
@@ -906,8 +976,10 @@ def main():
     ap.add_argument("--dense-steps", type=int, default=3000)
     ap.add_argument("--dense-fp32-steps", type=int, default=100,
                     help="SB steps of the plain FP32 CUDA-core comparison in the dense workload (0: skip it)")
+    ap.add_argument("--dense-hv-rounds", type=int, default=4,
+                    help="rounds of the FP32 / BF16 / FP8 hypervolume comparison in the dense workload (0: skip it)")
     ap.add_argument("--dense-fp8-steps", type=int, default=300,
-                    help="SB steps of the dSB BF16 vs FP8 (E4M3) comparison in the dense workload (0: skip it)")
+                    help="SB steps per operand form (BF16, E4M3, split) in the dense workload's comparison (0: skip it)")
     ap.add_argument("--batch-instances", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and not args.cpu_baseline_worker:

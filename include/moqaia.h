@@ -170,10 +170,10 @@ int moq_evaluate_cuts_batch(const moq_batch* b, const uint64_t* bits_all, int64_
 /* ---- a3 dense: tensor-core sampler (same dynamics as moq_sample; the force
  * c0 sum_k c_k (J^(k) Phi)_i is a matrix product) -----------------------------------------
  * moq_dense_create copies the instance's couplings into K zero-padded n_pad x n_pad BF16
- * matrices (n_pad = n rounded up to 128; integers |J| <= 256 are exact) and E4M3 matrices
- * with row scales (moq_sample_dense_fp8), and allocates the replica state for up to
- * max_replicas (x, y FP32, two BF16 and two E4M3 phi buffers, each
- * ceil(max_replicas/128)*128 x n_pad). K <= 4, n <= 16384. The instance must outlive it.
+ * matrices (n_pad = n rounded up to 128; integers |J| <= 256 are exact), their residuals
+ * (moq_sample_dense_split) and E4M3 matrices with row scales (moq_sample_dense_fp8), and
+ * allocates the replica state for up to max_replicas (x, y FP32, four BF16 and two E4M3 phi
+ * buffers, each ceil(max_replicas/128)*128 x n_pad). K <= 4, n <= 16384. The instance must outlive it.
  * moq_sample_dense runs T step kernels (tcgen05.mma BF16 -> FP32 products for every
  * objective, fused update/wall/phi epilogue) on `stream`, then writes the packed signs
  * (and x_out/y_out if given); with n_pad = 128 and K <= 3 one launch runs all T steps with
@@ -205,6 +205,19 @@ int moq_dense_status(moq_dense* d, void* stream);
  * moq_sample_dense; a timed-out device wait shows in moq_dense_status. */
 int moq_sample_dense_fp8(moq_dense* d, const float* lambda, int32_t R, const moq_sample_params* p, uint64_t seed,
                          uint64_t round, uint64_t* bits, void* stream);
+
+/* Split-precision form of the dense step on the tensor cores: J = BF16(J) + J_res with the
+ * residual J - BF16(J) exact in BF16 (|J| <= 65408), and for bSB phi = phi_hi + phi_lo with
+ * phi_hi = BF16(x), phi_lo = BF16(x - phi_hi); each K-chunk is multiplied in passes into the
+ * same FP32 accumulator: (BF16(J) + J_res) phi for dSB -- the exact integer products, so the
+ * results equal those of moq_sample_dense_fp32 whenever every row sum of |J| stays below
+ * 2^24 -- and BF16(J) phi_hi + J_res phi_hi + BF16(J) phi_lo for bSB (relative error of the
+ * products about 2^-16, inside the FP32 force bound 1e-5). Two (dSB) or three (bSB) times
+ * the products of moq_sample_dense. Same arguments, start state, noise and update as
+ * moq_sample_dense; the per-step kernel is used for every n. Errors as moq_sample_dense,
+ * and MOQ_ERR_UNSUPPORTED when some |J| > 65408. */
+int moq_sample_dense_split(moq_dense* d, const float* lambda, int32_t R, const moq_sample_params* p, uint64_t seed,
+                           uint64_t round, uint64_t* bits, void* stream);
 
 /* ---- a3 dense, plain FP32 form on the CUDA cores (same dynamics as moq_sample_dense)
  * The force c0 sum_k c_k (J^(k) Phi)_i of the SB equations with J^(k) and phi in FP32 and

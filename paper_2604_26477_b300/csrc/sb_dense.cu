@@ -66,6 +66,12 @@ struct moq_dense {
     __nv_fp8_e4m3* phi8[2] = {nullptr, nullptr}; // R_pad x n_pad
     CUtensorMap tm_J8;                           // box 128 x (128 / CL) x 1 (128 bytes per row, as BF16)
     CUtensorMap tm_phi8[2];                      // box 128 x 128
+    // split-precision operands (moq_sample_dense_split): J = BF16(J) + J_res with the residual
+    // exact in BF16 (|J| <= kSplitMax), and for bSB phi = phi_hi + phi_lo (two BF16 parts)
+    __nv_bfloat16* J_res = nullptr;              // K x n_pad x n_pad
+    __nv_bfloat16* phi_lo[2] = {nullptr, nullptr};  // R_pad x n_pad
+    CUtensorMap tm_Jres;                         // box 64 x (128 / CL) x 1
+    CUtensorMap tm_philo[2];                     // box 64 x 128
 };
 
 namespace moq {
@@ -100,6 +106,13 @@ constexpr uint32_t kIdescE4m3 = (1u << 4) | ((uint32_t)(kTileN >> 3) << 17) | ((
 // MMA consumes 32 bytes of it (K = 16 BF16 or K = 32 E4M3)
 template <bool F8>
 __host__ __device__ constexpr int chunk_elems() { return F8 ? 128 : kChunkK; }
+// operand forms of the step kernel
+constexpr int kPrecBf16 = 0, kPrecE4m3 = 1, kPrecSplit = 2;
+// products per K-chunk: one, or for the split form (J_main + J_res) phi (dSB: phi = +-1 is
+// exact in BF16) and J_main phi_hi + J_res phi_hi + J_main phi_lo (bSB; J_res phi_lo is below
+// 2^-17 of the product and left out)
+template <int PREC, int VARIANT>
+__host__ __device__ constexpr int prec_passes() { return PREC == kPrecSplit ? (VARIANT == MOQ_DSB ? 2 : 3) : 1; }
 
 __device__ __forceinline__ uint64_t global_ns()
 {
@@ -200,6 +213,7 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
 struct DenseStepArgs {
     __nv_bfloat16* phi_out;
     __nv_fp8_e4m3* phi8_out;   // FP8 form
+    __nv_bfloat16* philo_out;  // split form, bSB: BF16(x - BF16(x))
     const float* rowscale;     // FP8 form: K x n_pad scales of the J8 rows
     float* x;
     float* y;
@@ -289,11 +303,18 @@ constexpr int kWsThreads = 32 * (2 + kWsEpiWarps);
 // exact for dSB) multiplied by kind::f8f6f4 MMAs; a K-chunk is then 128 spins (the same 128
 // bytes per row, so the stages, swizzle and descriptors are those of BF16), and the epilogue
 // applies the row scale to each accumulator before the force combination.
-template <int VARIANT, int KOBJ, bool NOISE, int CL, bool F8>
+//
+// Split (PREC = kPrecSplit): every K-chunk is multiplied in P passes into the same FP32
+// accumulator, each pass a full stage: (J_main, phi) and (J_res, phi) for dSB -- exact integer
+// products, the FP32 force -- and (J_main, phi_hi), (J_res, phi_hi), (J_main, phi_lo) for bSB.
+template <int VARIANT, int KOBJ, bool NOISE, int CL, int PREC>
 __global__ void __launch_bounds__(kWsThreads, 1)
-    k_dense_step_ws(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmPhi, const DenseStepArgs a,
+    k_dense_step_ws(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmPhi,
+                    const __grid_constant__ CUtensorMap tmJ2, const __grid_constant__ CUtensorMap tmPhi2, const DenseStepArgs a,
                     int32_t n_ib, int32_t n_groups)
 {
+    constexpr bool F8 = PREC == kPrecE4m3;
+    constexpr int P = prec_passes<PREC, VARIANT>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -341,6 +362,8 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         asm volatile("fence.mbarrier_init.release.cluster;");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmJ)) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmPhi)) : "memory");
+        if (P > 1) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmJ2)) : "memory");
+        if (P > 2) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmPhi2)) : "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -355,7 +378,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
             for (int g = cid; g < n_groups && ok; g += nclusters) {
                 int i0, r0;
                 tile_of(g, i0, r0);
-                for (int c = 0; c < nchunks; ++c, ++gc) {
+                for (int vc = 0; vc < nchunks * P; ++vc, ++gc) {  // chunk vc / P, pass vc % P
                     const int st = gc % S;
                     if (gc >= S && !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((gc - S) / S) & 1))) {
                         ok = false;
@@ -363,16 +386,18 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                     }
                     const uint32_t stage = base + st * kStageBytes, fb = smem_u32(&full[st]);
                     mbar_expect_tx(fb, (uint32_t)kStageBytes);
-                    const int j0 = c * kCk;
+                    const int j0 = (vc / P) * kCk, pass = vc % P;
+                    const CUtensorMap* tA = (P > 1 && pass == 1) ? &tmJ2 : &tmJ;
+                    const CUtensorMap* tB = (P > 2 && pass == 2) ? &tmPhi2 : &tmPhi;
 #pragma unroll
                     for (int k = 0; k < KOBJ; ++k) {
                         if (CL > 1)
-                            tma_load_3d_mc(stage + k * kTileBytes + rank * (kSliceRows * 128), &tmJ, j0, i0 + (int)rank * kSliceRows,
+                            tma_load_3d_mc(stage + k * kTileBytes + rank * (kSliceRows * 128), tA, j0, i0 + (int)rank * kSliceRows,
                                            k, fb, kMask);
                         else
-                            tma_load_3d(stage + k * kTileBytes, &tmJ, j0, i0, k, fb);
+                            tma_load_3d(stage + k * kTileBytes, tA, j0, i0, k, fb);
                     }
-                    tma_load_2d(stage + KOBJ * kTileBytes, &tmPhi, j0, r0, fb);
+                    tma_load_2d(stage + KOBJ * kTileBytes, tB, j0, r0, fb);
                 }
             }
             // no copy into this CTA is still in flight when it leaves (gc chunks were issued), and
@@ -394,7 +419,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                for (int c = 0; c < nchunks; ++c, ++gc) {
+                for (int vc = 0; vc < nchunks * P; ++vc, ++gc) {
                     const int st = gc % S;
                     if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((gc / S) & 1))) {
                         ok = false;
@@ -408,10 +433,10 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                         for (int ks = 0; ks < 4; ++ks) {  // 4 x 32 bytes of the 128-byte chunk
                             if (F8)
                                 mma_e4m3(tmem + k * kTileN, sw128_desc(stage + k * kTileBytes + ks * 32),
-                                         sw128_desc(stage + KOBJ * kTileBytes + ks * 32), (c > 0 || ks > 0) ? 1u : 0u);
+                                         sw128_desc(stage + KOBJ * kTileBytes + ks * 32), (vc > 0 || ks > 0) ? 1u : 0u);
                             else
                                 mma_bf16(tmem + k * kTileN, sw128_desc(stage + k * kTileBytes + ks * 32),
-                                         sw128_desc(stage + KOBJ * kTileBytes + ks * 32), (c > 0 || ks > 0) ? 1u : 0u);
+                                         sw128_desc(stage + KOBJ * kTileBytes + ks * 32), (vc > 0 || ks > 0) ? 1u : 0u);
                         }
                     if (CL > 1)
                         asm volatile(
@@ -536,10 +561,13 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                             sb_update<NOISE>(f[q], cm, eta[q], a.dt, a.kappa, a.dta0, xv, yv);
                             a.x[at] = xv;
                             a.y[at] = yv;
-                            if (F8)
+                            if (F8) {
                                 a.phi8_out[at] = __nv_fp8_e4m3(phi_of<VARIANT>(xv));
-                            else
-                                a.phi_out[at] = __float2bfloat16_rn(phi_of<VARIANT>(xv));
+                            } else {
+                                const __nv_bfloat16 hi = __float2bfloat16_rn(phi_of<VARIANT>(xv));
+                                a.phi_out[at] = hi;
+                                if (P > 2) a.philo_out[at] = __float2bfloat16_rn(phi_of<VARIANT>(xv) - __bfloat162float(hi));
+                            }
                         }
                     }
 #pragma unroll
@@ -879,7 +907,7 @@ __global__ void k_dense_cuts_finish(const unsigned long long* __restrict__ acc, 
 // J^(k) rows from the CSR, rounded to BF16, into the zero-padded dense matrices.
 __global__ void k_dense_fill(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, const int32_t* __restrict__ wn,
                              int64_t nnz, int32_t n, int32_t K, int32_t np, __nv_bfloat16* J, __nv_bfloat16* J_hi,
-                             __nv_bfloat16* J_lo, int32_t* maxabs)
+                             __nv_bfloat16* J_lo, __nv_bfloat16* J_res, int32_t* maxabs)
 {
     int32_t mx = 0;
     for (int64_t i = blockIdx.x; i < n; i += gridDim.x)
@@ -887,7 +915,11 @@ __global__ void k_dense_fill(const int32_t* __restrict__ rowptr, const int32_t* 
             for (int k = 0; k < K; ++k) {
                 const int32_t w = wn[(int64_t)k * nnz + p];
                 const int64_t at = ((int64_t)k * np + i) * np + col[p];
-                J[at] = __float2bfloat16_rn((float)w);
+                const __nv_bfloat16 jm = __float2bfloat16_rn((float)w);
+                J[at] = jm;
+                // J - BF16(J): at most half a BF16 ulp of |J|, an integer <= 128 (exact) when
+                // |J| <= kSplitMax
+                J_res[at] = __float2bfloat16_rn((float)w - __bfloat162float(jm));
                 // J = 256 hi + lo with lo in [-128, 127]: both are integers of magnitude <= 256
                 // (exact in BF16) whenever |J| <= kSplitMax
                 const int32_t hi = (int32_t)(((int64_t)w + 128) >> 8);  // floor((w + 128) / 256)
@@ -925,14 +957,26 @@ __global__ void k_dense_fill8(const int32_t* __restrict__ rowptr, const int32_t*
         }
 }
 
+// phi_lo = BF16(x - BF16(x)) of the start state (split form, bSB); 0 on the padding
+__global__ void k_dense_philo(int32_t n, int32_t np, int32_t R, int32_t R_pad, const float* __restrict__ x,
+                              const __nv_bfloat16* __restrict__ phi, __nv_bfloat16* phi_lo)
+{
+    const int64_t total = (int64_t)R_pad * np;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(q / np), i = (int)(q - (int64_t)r * np);
+        phi_lo[q] = __float2bfloat16_rn((r < R && i < n) ? x[q] - __bfloat162float(phi[q]) : 0.0f);
+    }
+}
+
 size_t dense_smem_bytes(int K) { return 1024 + dense_stages(K) * (size_t)(K + 1) * kTileBytes + (size_t)kTileN * (K + 1) * 4 + 64; }
 
 // grid: one CTA per SM (clusters of CL CTAs), at most one per tile group; `grid` carries the
 // spin-block and replica-block counts
-template <int VARIANT, int KOBJ, bool NOISE, int CL, bool F8>
-cudaError_t launch_step(const moq_dense* d, const CUtensorMap& tm_phi, const DenseStepArgs& a, dim3 grid, cudaStream_t st)
+template <int VARIANT, int KOBJ, bool NOISE, int CL, int PREC>
+cudaError_t launch_step(const moq_dense* d, const CUtensorMap& tm_phi, const CUtensorMap& tm_phi2, const DenseStepArgs& a, dim3 grid,
+                        cudaStream_t st)
 {
-    auto k = k_dense_step_ws<VARIANT, KOBJ, NOISE, CL, F8>;
+    auto k = k_dense_step_ws<VARIANT, KOBJ, NOISE, CL, PREC>;
     const size_t smem = ws_smem_bytes(KOBJ);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -957,26 +1001,45 @@ cudaError_t launch_step(const moq_dense* d, const CUtensorMap& tm_phi, const Den
     }
     clusters = std::max(1, std::min(clusters, n_groups));
     cfg.gridDim = dim3((unsigned)(clusters * CL));
-    return cudaLaunchKernelEx(&cfg, k, F8 ? d->tm_J8 : d->tm_J, tm_phi, a, (int32_t)grid.x, (int32_t)n_groups);
+    return cudaLaunchKernelEx(&cfg, k, PREC == kPrecE4m3 ? d->tm_J8 : d->tm_J, tm_phi, d->tm_Jres, tm_phi2, a, (int32_t)grid.x,
+                              (int32_t)n_groups);
 }
 
-template <int VARIANT, bool NOISE, int CL, bool F8>
-cudaError_t launch_step_k(const moq_dense* d, const CUtensorMap& tm_phi, const DenseStepArgs& a, dim3 grid, cudaStream_t st)
+template <int VARIANT, bool NOISE, int CL, int PREC>
+cudaError_t launch_step_k(const moq_dense* d, const CUtensorMap& tm_phi, const CUtensorMap& tm_phi2, const DenseStepArgs& a, dim3 grid,
+                          cudaStream_t st)
 {
     switch (a.K) {
-    case 2: return launch_step<VARIANT, 2, NOISE, CL, F8>(d, tm_phi, a, grid, st);
-    case 3: return launch_step<VARIANT, 3, NOISE, CL, F8>(d, tm_phi, a, grid, st);
-    default: return launch_step<VARIANT, 4, NOISE, CL, F8>(d, tm_phi, a, grid, st);
+    case 2: return launch_step<VARIANT, 2, NOISE, CL, PREC>(d, tm_phi, tm_phi2, a, grid, st);
+    case 3: return launch_step<VARIANT, 3, NOISE, CL, PREC>(d, tm_phi, tm_phi2, a, grid, st);
+    default: return launch_step<VARIANT, 4, NOISE, CL, PREC>(d, tm_phi, tm_phi2, a, grid, st);
     }
 }
 
-template <int VARIANT, bool NOISE, bool F8 = false>
-cudaError_t launch_step_cl(const moq_dense* d, const CUtensorMap& tm_phi, const DenseStepArgs& a, dim3 grid, cudaStream_t st)
+template <int VARIANT, bool NOISE, int PREC>
+cudaError_t launch_step_cl(const moq_dense* d, const CUtensorMap& tm_phi, const CUtensorMap& tm_phi2, const DenseStepArgs& a, dim3 grid,
+                           cudaStream_t st)
 {
     switch (d->cluster) {
-    case 1: return launch_step_k<VARIANT, NOISE, 1, F8>(d, tm_phi, a, grid, st);
-    case 2: return launch_step_k<VARIANT, NOISE, 2, F8>(d, tm_phi, a, grid, st);
-    default: return launch_step_k<VARIANT, NOISE, 4, F8>(d, tm_phi, a, grid, st);
+    case 1: return launch_step_k<VARIANT, NOISE, 1, PREC>(d, tm_phi, tm_phi2, a, grid, st);
+    case 2: return launch_step_k<VARIANT, NOISE, 2, PREC>(d, tm_phi, tm_phi2, a, grid, st);
+    default: return launch_step_k<VARIANT, NOISE, 4, PREC>(d, tm_phi, tm_phi2, a, grid, st);
+    }
+}
+
+// variant x noise dispatch of one step of the given operand form
+template <int PREC>
+cudaError_t launch_step_form(const moq_dense* d, int variant, bool noise, const CUtensorMap& tm_phi, const CUtensorMap& tm_phi2,
+                             const DenseStepArgs& a, dim3 grid, cudaStream_t st)
+{
+    if (variant == MOQ_DSB)
+        return noise ? launch_step_cl<MOQ_DSB, true, PREC>(d, tm_phi, tm_phi2, a, grid, st)
+                     : launch_step_cl<MOQ_DSB, false, PREC>(d, tm_phi, tm_phi2, a, grid, st);
+    if constexpr (PREC == kPrecE4m3) {
+        return cudaErrorInvalidValue;  // E4M3 phi serves dSB only (checked by the caller)
+    } else {
+        return noise ? launch_step_cl<MOQ_BSB, true, PREC>(d, tm_phi, tm_phi2, a, grid, st)
+                     : launch_step_cl<MOQ_BSB, false, PREC>(d, tm_phi, tm_phi2, a, grid, st);
     }
 }
 
@@ -1038,6 +1101,24 @@ int encode_maps(moq_dense* d)
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(MOQ_ERR_CUDA, "cuTensorMapEncodeTiled(phi) failed: %d", (int)r);
     }
+    {  // the residual of the split form: as J
+        const cuuint64_t dims[3] = {np, np, (cuuint64_t)d->K};
+        const cuuint64_t strides[2] = {np * 2, np * np * 2};
+        const cuuint32_t box[3] = {(cuuint32_t)kChunkK, (cuuint32_t)(kTileM / d->cluster), 1};
+        CUresult r = encode(&d->tm_Jres, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, d->J_res, dims, strides, box, one,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(MOQ_ERR_CUDA, "cuTensorMapEncodeTiled(J_res) failed: %d", (int)r);
+    }
+    for (int b = 0; b < 2; ++b) {
+        const cuuint64_t dims[2] = {np, (cuuint64_t)d->R_pad};
+        const cuuint64_t strides[1] = {np * 2};
+        const cuuint32_t box[2] = {(cuuint32_t)kChunkK, (cuuint32_t)kTileN};
+        CUresult r = encode(&d->tm_philo[b], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, d->phi_lo[b], dims, strides, box, one,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(MOQ_ERR_CUDA, "cuTensorMapEncodeTiled(phi_lo) failed: %d", (int)r);
+    }
     {  // FP8 operands: the same 128-byte rows, 128 E4M3 elements per chunk
         const cuuint64_t dims[3] = {np, np, (cuuint64_t)d->K};
         const cuuint64_t strides[2] = {np, np * np};
@@ -1076,14 +1157,18 @@ void free_dense(moq_dense* d)
     cudaFree(d->rowscale);
     cudaFree(d->phi8[0]);
     cudaFree(d->phi8[1]);
+    cudaFree(d->J_res);
+    cudaFree(d->phi_lo[0]);
+    cudaFree(d->phi_lo[1]);
     if (d->h_status) cudaFreeHost(d->h_status);
     delete d;
 }
 
 // moq_sample_dense (BF16 operands) and moq_sample_dense_fp8 (E4M3 operands, dSB)
 int sample_dense_impl(moq_dense* d, const float* lambda, int32_t R, const moq_sample_params* p, uint64_t seed, uint64_t round,
-                      uint64_t* bits, void* stream, bool f8)
+                      uint64_t* bits, void* stream, int prec)
 {
+    const bool f8 = prec == kPrecE4m3, split = prec == kPrecSplit;
     if (!d || !p) return fail(MOQ_ERR_ARG, "moq_sample_dense: NULL handle or params");
     if (R < 0 || R > d->max_R) return fail(MOQ_ERR_ARG, "moq_sample_dense: R=%d outside [0, max_replicas=%d]", R, d->max_R);
     if (p->steps < 0 || (p->variant != MOQ_DSB && p->variant != MOQ_BSB)) return fail(MOQ_ERR_ARG, "moq_sample_dense: bad steps or variant");
@@ -1092,6 +1177,9 @@ int sample_dense_impl(moq_dense* d, const float* lambda, int32_t R, const moq_sa
     if (p->replica_offset != 0) return fail(MOQ_ERR_UNSUPPORTED, "moq_sample_dense: replica_offset must be 0");
     if (f8 && p->variant != MOQ_DSB)
         return fail(MOQ_ERR_UNSUPPORTED, "moq_sample_dense_fp8: E4M3 phi is exact for dSB only (bSB: use moq_sample_dense)");
+    if (split && d->max_abs_weight > kSplitMax)
+        return fail(MOQ_ERR_UNSUPPORTED, "moq_sample_dense_split: |J| = %d > %d (the residual J - BF16(J) is not exact in BF16)",
+                    d->max_abs_weight, kSplitMax);
     cudaStream_t st = as_stream(stream);
     const moq_instance* h = d->inst;
     // replica tiles come in whole clusters (the padded replicas compute on zero weights and
@@ -1112,6 +1200,10 @@ int sample_dense_impl(moq_dense* d, const float* lambda, int32_t R, const moq_sa
             k_dense_init<MOQ_BSB, __nv_bfloat16><<<gi, 256, 0, st>>>(d->n, np, R, Rp, p->init_amp, p->x_init, p->y_init, key0, key1, rnd,
                                                                      d->x, d->y, d->phi[0]);
         MOQ_CUDA_TRY(cudaMemsetAsync(d->phi[1], 0, sizeof(__nv_bfloat16) * (size_t)Rp * np, st));  // padded entries stay 0
+        if (split && p->variant == MOQ_BSB) {
+            k_dense_philo<<<gi, 256, 0, st>>>(d->n, np, R, Rp, d->x, d->phi[0], d->phi_lo[0]);
+            MOQ_CUDA_TRY(cudaMemsetAsync(d->phi_lo[1], 0, sizeof(__nv_bfloat16) * (size_t)Rp * np, st));
+        }
     }
     MOQ_LAUNCH_CHECK("moq_sample_dense prologue");
     DenseStepArgs a{};
@@ -1136,7 +1228,7 @@ int sample_dense_impl(moq_dense* d, const float* lambda, int32_t R, const moq_sa
     const float a0inv = p->steps > 1 ? p->a0 / (float)(p->steps - 1) : 0.0f;
     const dim3 grid(np / kTileM, Rp / kTileN);
     const bool noise = p->alpha != 0.0f;
-    if (d->resident && !f8 && p->steps > 0) {
+    if (d->resident && prec == kPrecBf16 && p->steps > 0) {
         // one launch runs every step (n_pad = 128, K <= 3): same arithmetic, same bits
         ResidentArgs ra{};
         ra.x = d->x;
@@ -1173,15 +1265,17 @@ int sample_dense_impl(moq_dense* d, const float* lambda, int32_t R, const moq_sa
         a.m = m;
         a.cm = fmaf(a0inv, (float)m, -p->a0);
         const CUtensorMap& tm_in = f8 ? d->tm_phi8[m & 1] : d->tm_phi[m & 1];
+        const CUtensorMap& tm_in2 = d->tm_philo[m & 1];
         a.phi_out = d->phi[(m + 1) & 1];
         a.phi8_out = d->phi8[(m + 1) & 1];
+        a.philo_out = d->phi_lo[(m + 1) & 1];
         cudaError_t e;
         if (f8)
-            e = noise ? launch_step_cl<MOQ_DSB, true, true>(d, tm_in, a, grid, st) : launch_step_cl<MOQ_DSB, false, true>(d, tm_in, a, grid, st);
-        else if (p->variant == MOQ_DSB)
-            e = noise ? launch_step_cl<MOQ_DSB, true>(d, tm_in, a, grid, st) : launch_step_cl<MOQ_DSB, false>(d, tm_in, a, grid, st);
+            e = launch_step_form<kPrecE4m3>(d, p->variant, noise, tm_in, tm_in2, a, grid, st);
+        else if (split)
+            e = launch_step_form<kPrecSplit>(d, p->variant, noise, tm_in, tm_in2, a, grid, st);
         else
-            e = noise ? launch_step_cl<MOQ_BSB, true>(d, tm_in, a, grid, st) : launch_step_cl<MOQ_BSB, false>(d, tm_in, a, grid, st);
+            e = launch_step_form<kPrecBf16>(d, p->variant, noise, tm_in, tm_in2, a, grid, st);
         if (e != cudaSuccess) return cuda_fail(e, "moq_sample_dense step launch");
     }
     k_dense_readout<<<R, 128, 0, st>>>(d->n, np, R, h->words, d->x, d->y, bits, p->x_out, p->y_out);
@@ -1250,6 +1344,10 @@ int moq_dense_create(const moq_instance* inst, int32_t max_replicas, moq_dense**
     if (e == cudaSuccess) e = cudaMalloc((void**)&d->phi8[1], cells);
     if (e == cudaSuccess) e = cudaMemset(d->J8, 0, j8bytes);
     if (e == cudaSuccess) e = cudaMemset(d->rowscale, 0, sizeof(float) * (size_t)d->K * d->n_pad);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d->J_res, jbytes);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d->phi_lo[0], sizeof(__nv_bfloat16) * cells);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d->phi_lo[1], sizeof(__nv_bfloat16) * cells);
+    if (e == cudaSuccess) e = cudaMemset(d->J_res, 0, jbytes);
     if (e == cudaSuccess) e = cudaMemset(d->J, 0, jbytes);
     if (e == cudaSuccess) e = cudaMemset(d->J_hi, 0, jbytes);
     if (e == cudaSuccess) e = cudaMemset(d->J_lo, 0, jbytes);
@@ -1257,7 +1355,7 @@ int moq_dense_create(const moq_instance* inst, int32_t max_replicas, moq_dense**
     if (e == cudaSuccess) e = cudaMemset(d->status, 0, sizeof(int32_t));
     if (e == cudaSuccess) {
         k_dense_fill<<<std::min(d->n, 148 * 8), 128>>>(inst->rowptr, inst->col, inst->wn, inst->nnz, d->n, d->K, d->n_pad, d->J,
-                                                       d->J_hi, d->J_lo, d->maxabs);
+                                                       d->J_hi, d->J_lo, d->J_res, d->maxabs);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
@@ -1285,13 +1383,19 @@ void moq_dense_destroy(moq_dense* d) { moq::free_dense(d); }
 int moq_sample_dense(moq_dense* d, const float* lambda, int32_t R, const moq_sample_params* p, uint64_t seed, uint64_t round,
                      uint64_t* bits, void* stream)
 {
-    return moq::sample_dense_impl(d, lambda, R, p, seed, round, bits, stream, false);
+    return moq::sample_dense_impl(d, lambda, R, p, seed, round, bits, stream, moq::kPrecBf16);
 }
 
 int moq_sample_dense_fp8(moq_dense* d, const float* lambda, int32_t R, const moq_sample_params* p, uint64_t seed, uint64_t round,
                          uint64_t* bits, void* stream)
 {
-    return moq::sample_dense_impl(d, lambda, R, p, seed, round, bits, stream, true);
+    return moq::sample_dense_impl(d, lambda, R, p, seed, round, bits, stream, moq::kPrecE4m3);
+}
+
+int moq_sample_dense_split(moq_dense* d, const float* lambda, int32_t R, const moq_sample_params* p, uint64_t seed, uint64_t round,
+                           uint64_t* bits, void* stream)
+{
+    return moq::sample_dense_impl(d, lambda, R, p, seed, round, bits, stream, moq::kPrecSplit);
 }
 
 int moq_dense_evaluate_cuts(moq_dense* d, const uint64_t* bits, int32_t M, int64_t* cuts, void* stream)

@@ -93,6 +93,7 @@ _sigs = {
     "moq_dense_status": (C.c_int, [_vp, _vp]),
     "moq_dense_evaluate_cuts": (C.c_int, [_vp, _vp, _i32, _vp, _vp]),
     "moq_sample_dense_fp8": (C.c_int, [_vp, _vp, _i32, C.POINTER(moq_sample_params), _u64, _u64, _vp, _vp]),
+    "moq_sample_dense_split": (C.c_int, [_vp, _vp, _i32, C.POINTER(moq_sample_params), _u64, _u64, _vp, _vp]),
     "moq_dense_fp32_create": (C.c_int, [_vp, _i32, C.POINTER(_vp)]),
     "moq_dense_fp32_destroy": (None, [_vp]),
     "moq_sample_dense_fp32": (C.c_int, [_vp, _vp, _i32, C.POINTER(moq_sample_params), _u64, _u64, _vp, _vp]),
@@ -353,6 +354,12 @@ def moq_sample_dense_fp8(h, lam, R, params, seed, round_, bits, stream=None):
     f32, _, u64 = _torch_types()
     _check(_lib.moq_sample_dense_fp8(h, _dptr(lam, "lambda", f32), R, C.byref(params), seed, round_,
                                      _dptr(bits, "bits", u64), _stream(stream)), "moq_sample_dense_fp8")
+
+
+def moq_sample_dense_split(h, lam, R, params, seed, round_, bits, stream=None):
+    f32, _, u64 = _torch_types()
+    _check(_lib.moq_sample_dense_split(h, _dptr(lam, "lambda", f32), R, C.byref(params), seed, round_,
+                                       _dptr(bits, "bits", u64), _stream(stream)), "moq_sample_dense_split")
 
 
 def moq_dense_status(h, stream=None):

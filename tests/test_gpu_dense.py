@@ -504,3 +504,127 @@ def test_dense_fp8_force_matches_oracle_e4m3_force(M, P, oracle, n, R, K):
     scale = _abs_force_scale(src, lam, phi, c0)
     err = np.abs(f_gpu - f_ref)
     assert np.all(err <= 1e-5 * scale + 1e-30), float((err / np.maximum(scale, 1e-30)).max())
+
+
+# ---- the split-precision form (BF16(J) + exact residual; bSB: phi_hi + phi_lo) -------------
+
+@pytest.mark.parametrize("n,R,K,alpha,sched", [(300, 300, 3, 0.1, False), (100, 130, 3, 0.15, False), (257, 64, 4, 0.1, True),
+                                                (129, 1, 2, 0.0, False)])
+def test_dense_split_dsb_matches_fp32_form_bitwise(M, P, n, R, K, alpha, sched):
+    # the dense workload's weights (|J| up to about 5000, not exact in BF16): BF16(J) and the
+    # residual J - BF16(J) are both exact, so with phi = +-1 every per-objective product is the
+    # exact integer the FP32 CUDA-core form computes: same bits, x and y over a noisy trajectory
+    src = wl.complete_graph(n, 11 + n + R, K=K)
+    inst = P.Instance(src)
+    T = 40
+    lam = _dev(wl.dirichlet_lambdas(R, K, 15))
+    schedule = torch.linspace(0.0, 1.0, T, device="cuda") ** 2 if sched else None
+    out = {}
+    for form in ("split", "fp32"):
+        d = (M.moq_dense_create if form == "split" else M.moq_dense_fp32_create)(inst.handle, R)
+        try:
+            xo = torch.zeros((R, n), device="cuda")
+            yo = torch.zeros((R, n), device="cuda")
+            bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+            p = M.moq_default_params(variant="dsb", steps=T, dt=0.5, alpha=alpha, schedule=schedule, x_out=xo, y_out=yo)
+            if form == "split":
+                M.moq_sample_dense_split(d, lam, R, p, 29, 2, bits)
+                M.moq_dense_status(d)
+            else:
+                M.moq_sample_dense_fp32(d, lam, R, p, 29, 2, bits)
+            out[form] = (bits.cpu(), xo.cpu(), yo.cpu())
+        finally:
+            (M.moq_dense_destroy if form == "split" else M.moq_dense_fp32_destroy)(d)
+    for a, b in zip(out["split"], out["fp32"]):
+        assert torch.equal(a, b)
+    assert R == 1 or len(torch.unique(out["split"][0], dim=0)) > 1
+
+
+def _force_split(M, P, src, variant, R, seed=1):
+    inst = P.Instance(src)
+    d = M.moq_dense_create(inst.handle, R)
+    try:
+        lam = wl.dirichlet_lambdas(R, src.K, seed)
+        x0 = np.random.default_rng(seed).uniform(-0.5, 0.5, (R, src.n)).astype(np.float32)
+        dt = 2.0 ** -10
+        yo = torch.zeros((R, src.n), device="cuda")
+        p = M.moq_default_params(variant=variant, steps=1, dt=dt, alpha=0.0, schedule=torch.ones(1, device="cuda"),
+                                 x_init=_dev(x0), y_init=torch.zeros((R, src.n), device="cuda"), y_out=yo)
+        bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+        M.moq_sample_dense_split(d, _dev(lam), R, p, 0, 0, bits)
+        M.moq_dense_status(d)
+        torch.cuda.synchronize()
+    finally:
+        M.moq_dense_destroy(d)
+    return lam, x0, yo.cpu().numpy().astype(np.float64) / dt
+
+
+@pytest.mark.parametrize("n,R,K", [(300, 200, 3), (130, 129, 4), (64, 1, 2), (257, 70, 3)])
+def test_dense_split_bsb_force_within_1e5(M, P, oracle, n, R, K):
+    # bSB on the tensor cores with the FP32 force bound: BF16(J) x_hi + J_res x_hi + BF16(J) x_lo
+    # leaves out J_res x_lo (about 2^-18 of each product)
+    src = wl.complete_graph(n, 60 + n, K=K)
+    lam, x0, f_gpu = _force_split(M, P, src, "bsb", R)
+    ref = oracle.sb(src, lam.astype(np.float64), variant="bsb", steps=1, dt=2.0 ** -10, alpha=0.0, schedule=[1.0],
+                    x_init=x0.astype(np.float64), y_init=np.zeros((R, n)))
+    scale = _abs_force_scale(src, lam, x0.astype(np.float64), ref["c0"])
+    err = np.abs(f_gpu - ref["y"] / 2.0 ** -10)
+    assert np.all(err <= 1e-5 * scale + 1e-30), float((err / np.maximum(scale, 1e-30)).max())
+
+
+def test_dense_split_bsb_tracks_fp32_form(M, P):
+    # a short noise-free bSB trajectory stays on the FP32 CUDA-core form's
+    src = wl.complete_graph(200, 92, K=3)
+    inst = P.Instance(src)
+    R, T = 192, 8
+    lam = _dev(wl.dirichlet_lambdas(R, 3, 6))
+    res = {}
+    for form in ("split", "fp32"):
+        d = (M.moq_dense_create if form == "split" else M.moq_dense_fp32_create)(inst.handle, R)
+        try:
+            xo = torch.zeros((R, src.n), device="cuda")
+            p = M.moq_default_params(variant="bsb", steps=T, dt=0.5, x_out=xo)
+            bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+            (M.moq_sample_dense_split if form == "split" else M.moq_sample_dense_fp32)(d, lam, R, p, 4, 0, bits)
+            torch.cuda.synchronize()
+            res[form] = xo.cpu().numpy()
+        finally:
+            (M.moq_dense_destroy if form == "split" else M.moq_dense_fp32_destroy)(d)
+    assert np.abs(res["split"] - res["fp32"]).max() < 1e-5
+
+
+@pytest.mark.parametrize("cl", ["2", "4"])
+def test_dense_split_cluster_sizes_agree_bitwise(M, P, cl, monkeypatch):
+    src = wl.complete_graph(300, 34, K=3)
+    inst = P.Instance(src)
+    R, T = 700, 7
+    lam = _dev(wl.dirichlet_lambdas(R, 3, 9))
+    out = {}
+    for c in ("1", cl):
+        monkeypatch.setenv("MOQ_DENSE_CLUSTER", c)
+        d = M.moq_dense_create(inst.handle, R)
+        try:
+            xo = torch.zeros((R, src.n), device="cuda")
+            bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+            p = M.moq_default_params(variant="bsb", steps=T, dt=0.5, alpha=0.1, x_out=xo)
+            M.moq_sample_dense_split(d, lam, R, p, 3, 1, bits)
+            M.moq_dense_status(d)
+            out[c] = (bits.cpu(), xo.cpu())
+        finally:
+            M.moq_dense_destroy(d)
+    for a, b in zip(out["1"], out[cl]):
+        assert torch.equal(a, b)
+
+
+def test_dense_split_rejects_large_weights(M, P):
+    src = wl.random_graph(40, 1.0, 3, K=2, wmax=10)
+    src.w[0, 0] = 70000
+    inst = P.Instance(src)
+    d = M.moq_dense_create(inst.handle, 16)
+    try:
+        with pytest.raises(M.MoqError) as e:
+            M.moq_sample_dense_split(d, _dev(np.full((16, 2), 0.5)), 16, M.moq_default_params(steps=3), 0, 0,
+                                     torch.zeros((16, 1), dtype=torch.int64, device="cuda"))
+        assert e.value.code == M.MOQ_ERR_UNSUPPORTED
+    finally:
+        M.moq_dense_destroy(d)
