@@ -134,20 +134,25 @@ class RoundBuffers:
         self.lam = torch.zeros((R, K), dtype=torch.float32, device=device)
 
 
+DENSE_FORMS = {"bf16": "moq_sample_dense", "fp8": "moq_sample_dense_fp8", "split": "moq_sample_dense_split"}
+
+
 def sample_round(inst: Instance, archive: Archive, buf: RoundBuffers, params, seed: int, round_: int,
-                 lam=None, index_base=None, stream=None, dense=None):
+                 lam=None, index_base=None, stream=None, dense=None, dense_form: str = "bf16"):
     """One pass of the hot path: (lambda) -> sample -> cuts -> Pareto merge. Asynchronous.
 
     With ``lam=None`` the round draws its own uniform-simplex weight vectors on the GPU.
     With ``dense`` (a ``moq_dense_create`` handle for ``inst``) the round runs the
-    tensor-core sampler and the tensor-core cut evaluation.
+    tensor-core sampler with the operands ``dense_form`` names ("bf16", "fp8" for dSB with
+    E4M3 operands, "split" for the FP32 force from split BF16 operands) and the tensor-core
+    cut evaluation.
     """
     R = buf.R
     if lam is None:
         M.moq_lambda_dirichlet(inst.K, R, seed, round_, buf.lam, stream)
         lam = buf.lam
     if dense is not None:
-        M.moq_sample_dense(dense, lam, R, params, seed, round_, buf.bits, stream)
+        getattr(M, DENSE_FORMS[dense_form])(dense, lam, R, params, seed, round_, buf.bits, stream)
         M.moq_dense_evaluate_cuts(dense, buf.bits, R, buf.cuts, stream)
     else:
         M.moq_sample(inst.handle, lam, R, params, seed, round_, buf.bits, stream)
@@ -222,7 +227,8 @@ class LearnedProposer:
 
 
 def time_to_target(src, target_hv: int, params, R: int, seed: int = 0, max_rounds: int = 1000,
-                   capacity=1 << 18, learned: bool = False, proposer_kwargs=None, dense: bool = False):
+                   capacity=1 << 18, learned: bool = False, proposer_kwargs=None, dense: bool = False,
+                   dense_form: str = "bf16"):
     """Repeat sampling rounds until the archive's hypervolume reaches ``target_hv``.
 
     The clock covers instance construction, every round (weight vectors, sampling, cuts,
@@ -241,7 +247,7 @@ def time_to_target(src, target_hv: int, params, R: int, seed: int = 0, max_round
     hv, rounds, trace = 0, 0, []
     while rounds < max_rounds:
         lam = prop.lambdas(rounds, arch) if prop else None
-        sample_round(inst, arch, buf, params, seed, rounds, lam=lam, dense=dh)
+        sample_round(inst, arch, buf, params, seed, rounds, lam=lam, dense=dh, dense_form=dense_form)
         if prop:
             prop.observe(lam, buf.cuts, R)
         rounds += 1

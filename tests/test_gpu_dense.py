@@ -628,3 +628,37 @@ def test_dense_split_rejects_large_weights(M, P):
         assert e.value.code == M.MOQ_ERR_UNSUPPORTED
     finally:
         M.moq_dense_destroy(d)
+
+
+def test_round_driver_dense_forms(M, P):
+    # the round driver runs every operand form; the split form's archive is the one the FP32
+    # CUDA-core sampler's samples give (identical dSB samples), and the E4M3 form gives a
+    # non-empty mutually non-dominated front
+    src = wl.complete_graph(150, 13, K=3)
+    inst = P.Instance(src)
+    R = 256
+    params = M.moq_default_params(variant="dsb", steps=200, dt=0.5, alpha=0.1)
+    dh = M.moq_dense_create(inst.handle, R)
+    hv = {}
+    for form in ("split", "fp8", "bf16"):
+        arch = P.Archive(src.n, 3, capacity=1 << 16, max_batch=R)
+        buf = P.RoundBuffers(R, src.n, 3)
+        for rnd in range(2):
+            P.sample_round(inst, arch, buf, params, 7, rnd, dense=dh, dense_form=form)
+        M.moq_dense_status(dh)
+        hv[form] = arch.hypervolume(inst.ref)
+        c, _, _ = arch.copy_out()
+        assert len(c) > 0
+        arch.close()
+    M.moq_dense_destroy(dh)
+    d32 = M.moq_dense_fp32_create(inst.handle, R)
+    arch = P.Archive(src.n, 3, capacity=1 << 16, max_batch=R)
+    buf = P.RoundBuffers(R, src.n, 3)
+    for rnd in range(2):
+        M.moq_lambda_dirichlet(3, R, 7, rnd, buf.lam)
+        M.moq_sample_dense_fp32(d32, buf.lam, R, params, 7, rnd, buf.bits)
+        M.moq_evaluate_cuts(inst.handle, buf.bits, R, buf.cuts)
+        arch.merge(buf.cuts, buf.bits, R, R * rnd)
+    assert arch.hypervolume(inst.ref) == hv["split"]
+    arch.close()
+    M.moq_dense_fp32_destroy(d32)
