@@ -662,3 +662,38 @@ def test_round_driver_dense_forms(M, P):
     assert arch.hypervolume(inst.ref) == hv["split"]
     arch.close()
     M.moq_dense_fp32_destroy(d32)
+
+
+def test_dense_forms_edge_cases(M, P, oracle):
+    # T = 0 reads out the start state (the same Philox start in every form, the oracle's
+    # signs); R = 0 is a no-op; a handle rejects more replicas than it was made for
+    src = wl.complete_graph(70, 21, K=2)
+    inst = P.Instance(src)
+    R = 33
+    lam = _dev(wl.dirichlet_lambdas(R, 2, 3))
+    d = M.moq_dense_create(inst.handle, R)
+    d32 = M.moq_dense_fp32_create(inst.handle, R)
+    try:
+        want = np.array([[oracle.initial_state(8, 1, r, i)[0] < 0 for i in range(src.n)] for r in range(R)])
+        for fn, h in ((M.moq_sample_dense, d), (M.moq_sample_dense_fp8, d), (M.moq_sample_dense_split, d),
+                      (M.moq_sample_dense_fp32, d32)):
+            bits = torch.full((R, inst.W), -1, dtype=torch.int64, device="cuda")
+            fn(h, lam, R, M.moq_default_params(variant="dsb", steps=0), 8, 1, bits)
+            torch.cuda.synchronize()
+            s = wl.bits_to_signs(bits.cpu().numpy().view(np.uint64), src.n)
+            assert np.array_equal(s < 0, want)
+            untouched = torch.full((1, inst.W), -1, dtype=torch.int64, device="cuda")
+            fn(h, lam, 0, M.moq_default_params(steps=5), 8, 1, untouched)  # R = 0: nothing written
+            torch.cuda.synchronize()
+            assert int(untouched[0, 0]) == -1
+            with pytest.raises(M.MoqError) as e:
+                fn(h, _dev(np.full((R + 1, 2), 0.5)), R + 1, M.moq_default_params(steps=2), 0, 0,
+                   torch.zeros((R + 1, inst.W), dtype=torch.int64, device="cuda"))
+            assert e.value.code == M.MOQ_ERR_ARG
+        M.moq_dense_status(d)
+    finally:
+        M.moq_dense_destroy(d)
+        M.moq_dense_fp32_destroy(d32)
+    with pytest.raises(M.MoqError) as e:
+        M.moq_dense_fp32_create(inst.handle, 0)
+    assert e.value.code == M.MOQ_ERR_ARG
