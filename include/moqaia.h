@@ -382,8 +382,12 @@ int moq_lambda_propose(moq_mlp* m, const moq_archive* a, const float* features, 
 int moq_release_cached_memory(void);
 
 /* ---- errors -------------------------------------------------------------------- */
+/* moq_strerror: a fixed text for a status code. moq_last_error_message and moq_last_status:
+ * the message and the code of the last call on this thread that failed (a successful call
+ * leaves both unchanged; "" and MOQ_OK before any failure). */
 const char* moq_strerror(int code);
 const char* moq_last_error_message(void);
+int moq_last_status(void);
 
 #if defined(__GNUC__)
 #pragma GCC visibility pop

@@ -7,9 +7,11 @@
 namespace moq {
 
 static thread_local char g_last_msg[512] = "";
+static thread_local int g_last_code = MOQ_OK;
 
 int fail(int code, const char* fmt, ...)
 {
+    g_last_code = code;
     va_list ap;
     va_start(ap, fmt);
     vsnprintf(g_last_msg, sizeof(g_last_msg), fmt, ap);
@@ -46,6 +48,8 @@ const char* moq_strerror(int code)
 }
 
 const char* moq_last_error_message(void) { return moq::g_last_msg; }
+
+int moq_last_status(void) { return moq::g_last_code; }
 
 void moq_default_params(moq_sample_params* p)
 {

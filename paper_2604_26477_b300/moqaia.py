@@ -111,6 +111,7 @@ _sigs = {
     "moq_release_cached_memory": (C.c_int, []),
     "moq_strerror": (C.c_char_p, [C.c_int]),
     "moq_last_error_message": (C.c_char_p, []),
+    "moq_last_status": (C.c_int, []),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -118,6 +119,11 @@ for _name, (_res, _args) in _sigs.items():
     _f.argtypes = _args
 
 EXPORTED = tuple(_sigs)
+
+
+def moq_last_status() -> int:
+    """Code of the last failed call on this thread (MOQ_OK before any failure)."""
+    return int(_lib.moq_last_status())
 
 
 def _check(rc: int, where: str):

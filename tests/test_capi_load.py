@@ -38,3 +38,16 @@ def test_binding_wraps_every_symbol_and_strerror_works():
     assert M.moq_strerror(M.MOQ_ERR_CAPACITY) == "capacity exceeded"
     p = M.moq_default_params(variant="bsb", steps=7, dt=0.5)
     assert (p.variant, p.steps, p.dt, p.a0, p.init_amp) == (M.MOQ_BSB, 7, 0.5, 1.0, pytest.approx(0.1))
+
+
+def test_last_status_and_message_follow_a_rejected_call():
+    # argument checks run before any device work, so this needs no GPU
+    from paper_2604_26477_b300 import build
+    lib = ctypes.CDLL(build.build())
+    lib.moq_last_error_message.restype = ctypes.c_char_p
+    out = ctypes.c_void_p()
+    rc = lib.moq_create_instance(1, 3, 0, None, None, None, None, ctypes.byref(out))
+    assert rc == -1 and lib.moq_last_status() == -1
+    assert b"n" in lib.moq_last_error_message()
+    lib.moq_default_params(None)  # a call that cannot fail leaves the status as it was
+    assert lib.moq_last_status() == -1
