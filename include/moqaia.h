@@ -43,7 +43,7 @@ extern "C" {
 #define MOQ_ERR_TIMEOUT -4     /* a device-side wait ran out of its budget */
 #define MOQ_ERR_CAPACITY -5    /* the archive (or a buffer) is too small */
 #define MOQ_ERR_OVERFLOW -6    /* a result would leave the exact integer range */
-#define MOQ_ERR_UNSUPPORTED -7 /* valid request outside what this build implements */
+#define MOQ_ERR_UNSUPPORTED -7 /* valid request outside what the library implements */
 
 /* ---- SB variants ("Simulated Bifurcation with Gaussian noise") ----------------- */
 #define MOQ_DSB 0 /* discrete SB: phi(x) = sgn(x) */

@@ -42,7 +42,7 @@ const char* moq_strerror(int code)
     case MOQ_ERR_TIMEOUT: return "device wait timed out";
     case MOQ_ERR_CAPACITY: return "capacity exceeded";
     case MOQ_ERR_OVERFLOW: return "result outside the exact integer range";
-    case MOQ_ERR_UNSUPPORTED: return "not supported by this build";
+    case MOQ_ERR_UNSUPPORTED: return "not supported by the library";
     default: return "unknown status";
     }
 }
