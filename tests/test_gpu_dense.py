@@ -697,3 +697,56 @@ def test_dense_forms_edge_cases(M, P, oracle):
     with pytest.raises(M.MoqError) as e:
         M.moq_dense_fp32_create(inst.handle, 0)
     assert e.value.code == M.MOQ_ERR_ARG
+
+
+@pytest.mark.slow
+def test_dense_full_size_sampled_parity(M, P, oracle):
+    # the dense benchmark's configuration (complete graph n = 2000, K = 3, R = 8192, the
+    # persistent step kernel's launch): one step of every operand form from the same state,
+    # checked on sampled replicas against the FP64 oracle with each form's stated bound, and
+    # the exact tensor-core cuts of a short run on sampled rows against the oracle's cuts
+    n, K, R = 2000, 3, 8192
+    src = wl.complete_graph(n, 2000, K=K)
+    inst = P.Instance(src)
+    lam = wl.dirichlet_lambdas(R, K, 5)
+    x0 = np.random.default_rng(11).uniform(-1, 1, (R, n)).astype(np.float32)
+    sel = np.random.default_rng(12).choice(R, 12, replace=False)
+    sel.sort()
+    dt = 2.0 ** -10
+    d = M.moq_dense_create(inst.handle, R)
+    d32 = M.moq_dense_fp32_create(inst.handle, R)
+    ld, xd = _dev(lam), _dev(x0)
+    forces = {}
+    try:
+        for name, variant, fn, h in (("fp32_bsb", "bsb", M.moq_sample_dense_fp32, d32), ("split_bsb", "bsb", M.moq_sample_dense_split, d),
+                                     ("bf16_bsb", "bsb", M.moq_sample_dense, d), ("split_dsb", "dsb", M.moq_sample_dense_split, d),
+                                     ("fp8_dsb", "dsb", M.moq_sample_dense_fp8, d)):
+            yo = torch.zeros((R, n), device="cuda")
+            p = M.moq_default_params(variant=variant, steps=1, dt=dt, alpha=0.0, schedule=torch.ones(1, device="cuda"),
+                                     x_init=xd, y_init=torch.zeros((R, n), device="cuda"), y_out=yo)
+            fn(h, ld, R, p, 0, 0, torch.zeros((R, inst.W), dtype=torch.int64, device="cuda"))
+            forces[name] = yo[torch.from_numpy(sel).cuda()].cpu().numpy().astype(np.float64) / dt
+        bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+        M.moq_sample_dense(d, ld, R, M.moq_default_params(variant="bsb", steps=20, dt=0.5, alpha=0.1), 3, 0, bits)
+        cuts = torch.zeros((R, K), dtype=torch.int64, device="cuda")
+        M.moq_dense_evaluate_cuts(d, bits, R, cuts)
+        M.moq_dense_status(d)
+        rows = bits.cpu().numpy().view(np.uint64)[sel]
+        assert np.array_equal(cuts.cpu().numpy()[sel], oracle.cuts(src, rows))
+    finally:
+        M.moq_dense_destroy(d)
+        M.moq_dense_fp32_destroy(d32)
+    ls, xs = lam[sel].astype(np.float64), x0[sel].astype(np.float64)
+    for variant in ("bsb", "dsb"):
+        ref = oracle.sb(src, ls, variant=variant, steps=1, dt=dt, alpha=0.0, schedule=[1.0], x_init=xs, y_init=np.zeros_like(xs))
+        phi = xs if variant == "bsb" else np.where(xs >= 0, 1.0, -1.0)
+        scale = _abs_force_scale(src, ls, phi, ref["c0"])
+        f64 = ref["y"] / dt
+        bounds = {"bsb": {"fp32_bsb": 1e-5, "split_bsb": 1e-5, "bf16_bsb": 4e-3}, "dsb": {"split_dsb": 1e-5}}[variant]
+        for name, bound in bounds.items():
+            err = np.abs(forces[name] - f64)
+            assert np.all(err <= bound * scale + 1e-30), (name, float((err / scale).max()))
+        if variant == "dsb":
+            f8 = oracle.force_e4m3(src, ls, phi, ref["c0"])
+            err = np.abs(forces["fp8_dsb"] - f8)
+            assert np.all(err <= 1e-5 * scale + 1e-30), float((err / scale).max())
