@@ -132,8 +132,8 @@ def _check(rc: int, where: str):
 
 
 def _stream(stream):
-    if stream is not None:
-        return C.c_void_p(int(stream))
+    if stream is not None:  # a torch.cuda.Stream or a raw cudaStream_t value
+        return C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
     import torch
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
 

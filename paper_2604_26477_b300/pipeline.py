@@ -172,10 +172,16 @@ class LearnedProposer:
     Defaults (2048 candidates, 5 Adam steps per round) were picked on a held-out n = 300
     instance: 8192 candidates and 20 steps gave about as many samples to the target but
     twice the time per round.
+
+    With ``overlap`` the Adam steps on a round's rows run on a second stream while the next
+    round samples (the proposal for round t then uses the model trained through round t - 2;
+    the first model is trained before its first proposal). Proposal and training never run
+    at the same time: training starts after the proposal that precedes it, and the next
+    proposal waits for it.
     """
 
     def __init__(self, inst: Instance, R: int, rho=0.5, n_candidates=2048, max_rows=1 << 20, train_steps=5,
-                 batch=4096, lr=3e-3, seed=0, device="cuda"):
+                 batch=4096, lr=3e-3, seed=0, device="cuda", overlap=True):
         self.inst, self.R, self.K = inst, R, inst.K
         self.rho, self.n_candidates, self.train_steps, self.batch, self.lr, self.seed = \
             rho, n_candidates, train_steps, batch, lr, seed
@@ -190,14 +196,30 @@ class LearnedProposer:
         self.rows = 0
         self.lam = torch.zeros((R, self.K), dtype=torch.float32, device=device)
         self.loss = torch.zeros(1, dtype=torch.float32, device=device)
+        self.side = torch.cuda.Stream(device=device) if overlap else None
+        self.trained_steps = 0
+        self.pending = None     # (newest, filled) of rows waiting for their Adam steps
+        self.train_done = None  # event after the second stream's last Adam step
 
     def lambdas(self, round_, arch: Archive):
+        main = torch.cuda.current_stream()
+        if self.train_done is not None:  # the weights are final before the proposal reads them
+            main.wait_stream(self.side)
+            self.train_done = None
+        if self.pending is not None and self.trained_steps == 0:
+            self._train(*self.pending, stream=None)  # the first model is trained before it proposes
+            self.pending = None
         n_prop = int(self.rho * self.R) if self.rows > 0 else 0
         if n_prop > 0:
             M.moq_lambda_propose(self.mlp, arch.handle, self.features, self.offset, self.scale, self.n_candidates,
                                  self.seed + 7, round_, self.lam, n_prop)
         if n_prop < self.R:
             M.moq_lambda_dirichlet(self.K, self.R - n_prop, self.seed, round_, self.lam[n_prop:])
+        if self.pending is not None:  # train on the last round's rows while this round samples
+            self.side.wait_stream(main)
+            self._train(*self.pending, stream=self.side)
+            self.train_done = self.side.record_event()
+            self.pending = None
         return self.lam
 
     def observe(self, lam, cuts, m):
@@ -207,15 +229,24 @@ class LearnedProposer:
         self.rows += m
         filled = min(self.rows, self.max_rows)
         newest = (self.rows - 1) % self.max_rows
+        if self.side is not None:
+            self.pending = (newest, filled)
+        else:
+            self._train(newest, filled, stream=None)
+
+    def _train(self, newest, filled, stream):
         for s in range(self.train_steps):  # batches walk back from the newest rows
             end = newest + 1 - s * self.batch
             while end <= 0:
                 end += filled
             start = max(0, end - self.batch)
-            M.moq_mlp_train_step(self.mlp, self.X[start:end], self.T[start:end], end - start, self.lr, self.loss)
+            M.moq_mlp_train_step(self.mlp, self.X[start:end], self.T[start:end], end - start, self.lr, self.loss, stream)
+        self.trained_steps += self.train_steps
 
     def close(self):
         if getattr(self, "mlp", None):
+            if getattr(self, "side", None) is not None:
+                self.side.synchronize()
             M.moq_mlp_destroy(self.mlp)
             self.mlp = None
 
