@@ -82,3 +82,20 @@ def test_force_e4m3_within_its_bound(oracle):
     err = np.abs(f - f64)
     assert np.all(err <= 2.0 ** -4 * scale * 1.7)  # per-weight 2^-4 of sum_k c_k |J_k| <= 1.7 sum |J(c)| here
     assert err.max() > 0
+
+
+def test_split_residual_is_exact_in_bf16():
+    # the split-precision dense form rests on this: for every integer |J| <= 65408 (the
+    # bound the library enforces, shared with the exact cut evaluation), J = BF16(J) +
+    # (J - BF16(J)) with the residual an integer of magnitude <= 128, hence exact in BF16
+    J = np.arange(-65408, 65409, dtype=np.float64)
+    hi = torch.from_numpy(J).float().to(torch.bfloat16).double().numpy()
+    res = J - hi
+    assert np.all(np.abs(res) <= 128) and np.all(res == np.round(res))
+    assert np.array_equal(torch.from_numpy(res).float().to(torch.bfloat16).double().numpy(), res)
+    assert np.array_equal(hi + res, J)
+    # the bound is conservative for the residual: between 2^17 and 2^18 an odd residual above
+    # 256 needs 9 significant bits and is rounded
+    big = np.arange(2 ** 17, 2 ** 17 + 4096, dtype=np.float64)
+    r2 = big - torch.from_numpy(big).float().to(torch.bfloat16).double().numpy()
+    assert np.any(torch.from_numpy(r2).float().to(torch.bfloat16).double().numpy() != r2)
