@@ -34,8 +34,9 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)_
 // R = 8192 (bSB, same call): chunks of 16 took 4.57 ms per step, 32 4.29 ms; unrolling the
 // inner loop over j (254 registers) gained nothing at 32. The epilogue combines the force,
 // draws the noise and updates the state exactly as the tensor-core epilogue does, so for
-// dSB with integer couplings (sums of |J| below 2^24: every G_k exact in both forms) the
-// two forms give the same bits.
+// dSB with integer couplings whose row sums of |J| stay below 2^24 this form gives the bits
+// of the split-precision tensor-core form (|J| <= 65408) and of the BF16 form (|J| <= 256):
+// every G_k is then the same exact integer.
 constexpr int kF32M = 64, kF32N = 128, kF32K = 32, kF32Threads = 256, kF32Stages = 3;
 constexpr int kF32Row = kF32K + 4;  // staged operand row (floats)
 
