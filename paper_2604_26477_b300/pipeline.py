@@ -173,11 +173,13 @@ class LearnedProposer:
     instance: 8192 candidates and 20 steps gave about as many samples to the target but
     twice the time per round.
 
-    With ``overlap`` the Adam steps on a round's rows run on a second stream while the next
-    round samples (the proposal for round t then uses the model trained through round t - 2;
-    the first model is trained before its first proposal). Proposal and training never run
-    at the same time: training starts after the proposal that precedes it, and the next
-    proposal waits for it.
+    With ``overlap`` the surrogate works on a second stream, off the rounds' critical path:
+    once a round is merged (``observe`` with the archive), the next round's weight vectors are
+    proposed there while the main stream computes the round's hypervolume, and the Adam steps
+    on the round's rows follow while the next round samples. The proposal for round t + 1 thus
+    sees the archive after round t and the model trained through round t - 1 (the first model
+    is trained before its first proposal). Proposal and training are ordered on that stream, so
+    they never run at the same time, and a round starts sampling only once its proposal is done.
     """
 
     def __init__(self, inst: Instance, R: int, rho=0.5, n_candidates=2048, max_rows=1 << 20, train_steps=5,
@@ -198,41 +200,45 @@ class LearnedProposer:
         self.loss = torch.zeros(1, dtype=torch.float32, device=device)
         self.side = torch.cuda.Stream(device=device) if overlap else None
         self.trained_steps = 0
-        self.pending = None     # (newest, filled) of rows waiting for their Adam steps
-        self.train_done = None  # event after the second stream's last Adam step
+        self.ready = None  # event: the next round's vectors are proposed (second stream)
 
     def lambdas(self, round_, arch: Archive):
-        main = torch.cuda.current_stream()
-        if self.train_done is not None:  # the weights are final before the proposal reads them
-            main.wait_stream(self.side)
-            self.train_done = None
-        if self.pending is not None and self.trained_steps == 0:
-            self._train(*self.pending, stream=None)  # the first model is trained before it proposes
-            self.pending = None
+        if self.ready is not None:  # proposed on the second stream after the last round's merge
+            torch.cuda.current_stream().wait_event(self.ready)
+            self.ready = None
+            return self.lam
+        self._propose(round_, arch, stream=None)
+        return self.lam
+
+    def _propose(self, round_, arch, stream):
         n_prop = int(self.rho * self.R) if self.rows > 0 else 0
         if n_prop > 0:
             M.moq_lambda_propose(self.mlp, arch.handle, self.features, self.offset, self.scale, self.n_candidates,
-                                 self.seed + 7, round_, self.lam, n_prop)
+                                 self.seed + 7, round_, self.lam, n_prop, stream)
         if n_prop < self.R:
-            M.moq_lambda_dirichlet(self.K, self.R - n_prop, self.seed, round_, self.lam[n_prop:])
-        if self.pending is not None:  # train on the last round's rows while this round samples
-            self.side.wait_stream(main)
-            self._train(*self.pending, stream=self.side)
-            self.train_done = self.side.record_event()
-            self.pending = None
-        return self.lam
+            M.moq_lambda_dirichlet(self.K, self.R - n_prop, self.seed, round_, self.lam[n_prop:], stream)
 
-    def observe(self, lam, cuts, m):
+    def observe(self, lam, cuts, m, arch: Archive = None, round_: int = None):
+        """Adds the round's (lambda, cut) rows; with ``overlap`` and the merged ``arch`` of round
+        ``round_``, also queues the next round's proposal and the Adam steps on the second stream."""
         at = self.rows % self.max_rows
         m = min(m, self.max_rows - at)
         M.moq_mlp_make_rows(self.K, self.features, lam, cuts, m, self.offset, self.scale, self.X[at:], self.T[at:])
         self.rows += m
         filled = min(self.rows, self.max_rows)
         newest = (self.rows - 1) % self.max_rows
-        if self.side is not None:
-            self.pending = (newest, filled)
-        else:
+        if self.side is None or arch is None:
             self._train(newest, filled, stream=None)
+            return
+        self.side.wait_stream(torch.cuda.current_stream())  # rows, merge and lambda reads are done
+        if self.trained_steps == 0:
+            self._train(newest, filled, stream=self.side)  # the first model before its first proposal
+            self._propose(round_ + 1, arch, stream=self.side)
+            self.ready = self.side.record_event()
+            return
+        self._propose(round_ + 1, arch, stream=self.side)
+        self.ready = self.side.record_event()
+        self._train(newest, filled, stream=self.side)  # runs while the next round samples
 
     def _train(self, newest, filled, stream):
         for s in range(self.train_steps):  # batches walk back from the newest rows
@@ -280,7 +286,7 @@ def time_to_target(src, target_hv: int, params, R: int, seed: int = 0, max_round
         lam = prop.lambdas(rounds, arch) if prop else None
         sample_round(inst, arch, buf, params, seed, rounds, lam=lam, dense=dh, dense_form=dense_form)
         if prop:
-            prop.observe(lam, buf.cuts, R)
+            prop.observe(lam, buf.cuts, R, arch, rounds)
         rounds += 1
         hv = arch.hypervolume(inst.ref)
         trace.append((rounds * R, hv))
