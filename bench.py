@@ -922,7 +922,7 @@ def appendix_e_arm(args, rank, world):
 def learned_ttt_block(args):
     """Where the learned proposal pays: a held-out random 3-regular instance (n = 300, K = 3,
     weights {-100..100}\\{0}, seed 2000), rounds of 1024 NI-dSB replicas (T = 1000, dt = 0.5,
-    alpha = 0.1) with uniform weight vectors or with the surrogate proposing half of each
+    alpha = 0.1) with uniform weight vectors or with the surrogate proposing a quarter of each
     round's vectors, until the archive holds 99.9% of the hypervolume the plain sampler
     (alpha = 0, uniform) reaches in 32 rounds; median of 3 seeds."""
     import torch

@@ -169,9 +169,10 @@ class LearnedProposer:
     rows. The next round's batch is a fraction ``rho`` of proposed weight vectors -- the
     candidates whose predicted cuts reach furthest beyond the current front -- and the rest
     uniform on the simplex (exploration, and the fallback before any data exists).
-    Defaults (2048 candidates, 5 Adam steps per round) were picked on a held-out n = 300
-    instance: 8192 candidates and 20 steps gave about as many samples to the target but
-    twice the time per round.
+    Defaults (2048 candidates, 5 Adam steps per round, a quarter of each round proposed) were
+    picked on held-out n = 300 instances: 8192 candidates and 20 steps gave about as many
+    samples to the target but twice the time per round, and proposing half or three quarters
+    of each round needed more samples than a quarter.
 
     With ``overlap`` the surrogate works on a second stream, off the rounds' critical path:
     once a round is merged (``observe`` with the archive), the next round's weight vectors are
@@ -182,7 +183,7 @@ class LearnedProposer:
     they never run at the same time, and a round starts sampling only once its proposal is done.
     """
 
-    def __init__(self, inst: Instance, R: int, rho=0.5, n_candidates=2048, max_rows=1 << 20, train_steps=5,
+    def __init__(self, inst: Instance, R: int, rho=0.25, n_candidates=2048, max_rows=1 << 20, train_steps=5,
                  batch=4096, lr=3e-3, seed=0, device="cuda", overlap=True):
         self.inst, self.R, self.K = inst, R, inst.K
         self.rho, self.n_candidates, self.train_steps, self.batch, self.lr, self.seed = \

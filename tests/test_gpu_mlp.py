@@ -181,7 +181,7 @@ def test_learned_proposal_saves_samples_on_held_out_instances(M):
     # (T = 1000, dt = 0.5, alpha = 0.1), samples until the archive holds 99.9% of the
     # hypervolume the plain sampler (alpha = 0, uniform weights) reaches in 32 rounds;
     # median over three seeds. The surrogate trains on each round's (lambda, cut) pairs
-    # and proposes half of the next round's weight vectors.
+    # and proposes a quarter of the next round's weight vectors.
     from paper_2604_26477_b300 import pipeline as P
     params = M.moq_default_params(variant="dsb", steps=1000, dt=0.5, alpha=0.1)
     for seed in (2000, 2001):
