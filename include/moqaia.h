@@ -276,6 +276,15 @@ int moq_archive_reset(moq_archive* a, void* stream);
  * Errors: MOQ_ERR_ARG (M < 0 or M > max_batch, NULL), MOQ_ERR_CAPACITY, MOQ_ERR_CUDA. */
 int moq_pareto_front(moq_archive* a, const int64_t* cuts, const uint64_t* bits, int64_t M, int64_t index_base,
                      int64_t* front_size_out, void* stream);
+/* The front of the union of two sample sets ("Pareto filtering": the non-dominated set of a
+ * pool does not depend on how the pool was split): merges every member of src (its cut
+ * vector, configuration and global sample index) into dst, in batches of dst's max_batch.
+ * On a cut vector present in both, dst's member is kept. The exchange step of a run split
+ * over several devices or processes (gather the parts' fronts, merge them). Synchronises
+ * once to read src's size; the merge itself is stream-ordered and src must not change
+ * meanwhile. Errors: MOQ_ERR_ARG (NULL, dst == src, different n or K), MOQ_ERR_CAPACITY
+ * (pending in src, or reported by the next synchronising call on dst), MOQ_ERR_CUDA. */
+int moq_archive_merge(moq_archive* dst, const moq_archive* src, void* stream);
 /* Archive size (synchronises). Returns a pending capacity error, if any. */
 int moq_archive_size(const moq_archive* a, int64_t* size_out, void* stream);
 /* Copies up to cap members to host arrays (cuts_host cap x K, bits_host cap x W,

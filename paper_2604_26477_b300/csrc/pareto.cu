@@ -475,6 +475,7 @@ struct ScatterArgs {
     const int64_t* old_index;
     const int64_t* cand_cuts;
     const uint64_t* cand_bits;
+    const int64_t* cand_index;  // NULL: candidate c has index index_base + c
     int64_t* new_cuts;
     uint64_t* new_bits;
     int64_t* new_index;
@@ -525,7 +526,7 @@ __global__ void __launch_bounds__(kScanBlock) k_scatter(const ScatterArgs s)
             }
             s.new_bits[pos * s.W + w] = word;
         }
-        s.new_index[pos] = s.index_base + c;
+        s.new_index[pos] = s.cand_index ? s.cand_index[c] : s.index_base + c;
     }
 }
 
@@ -679,8 +680,8 @@ int moq_archive_reset(moq_archive* a, void* stream)
     return MOQ_OK;
 }
 
-int moq_pareto_front(moq_archive* a, const int64_t* cuts, const uint64_t* bits, int64_t M, int64_t index_base,
-                     int64_t* front_size_out, void* stream)
+static int pareto_merge(moq_archive* a, const int64_t* cuts, const uint64_t* bits, int64_t M, int64_t index_base,
+                        const int64_t* cand_index, int64_t* front_size_out, void* stream)
 {
     using namespace moq;
     if (!a) return fail(MOQ_ERR_ARG, "moq_pareto_front: NULL archive");
@@ -709,6 +710,7 @@ int moq_pareto_front(moq_archive* a, const int64_t* cuts, const uint64_t* bits, 
     s.nbA = nbA;
     s.M = M;
     s.index_base = index_base;
+    s.cand_index = cand_index;
     s.d_count = a->d_count;
     s.flag_arch = a->flag_arch;
     s.flag_cand = a->flag_cand;
@@ -728,6 +730,32 @@ int moq_pareto_front(moq_archive* a, const int64_t* cuts, const uint64_t* bits, 
     MOQ_LAUNCH_CHECK("moq_pareto_front launch");
     a->cur = 1 - a->cur;
     if (front_size_out) return read_status(a, st, front_size_out);
+    return MOQ_OK;
+}
+
+int moq_pareto_front(moq_archive* a, const int64_t* cuts, const uint64_t* bits, int64_t M, int64_t index_base,
+                     int64_t* front_size_out, void* stream)
+{
+    return pareto_merge(a, cuts, bits, M, index_base, nullptr, front_size_out, stream);
+}
+
+int moq_archive_merge(moq_archive* dst, const moq_archive* src, void* stream)
+{
+    using namespace moq;
+    if (!dst || !src || dst == src) return fail(MOQ_ERR_ARG, "moq_archive_merge: NULL archive or dst == src");
+    if (dst->K != src->K || dst->n != src->n)
+        return fail(MOQ_ERR_ARG, "moq_archive_merge: archives of different n or K (%d, %d vs %d, %d)", dst->n, dst->K, src->n, src->K);
+    cudaStream_t st = as_stream(stream);
+    int64_t F = 0;
+    int rc = read_status(src, st, &F);
+    if (rc != MOQ_OK) return rc;
+    // src's members are distinct and mutually non-dominated, so they can enter in batches
+    for (int64_t off = 0; off < F; off += dst->max_batch) {
+        const int64_t m = std::min<int64_t>(dst->max_batch, F - off);
+        rc = pareto_merge(dst, src->cuts[src->cur] + off * src->K, src->bits[src->cur] + off * src->W, m, 0, src->index[src->cur] + off,
+                          nullptr, stream);
+        if (rc != MOQ_OK) return rc;
+    }
     return MOQ_OK;
 }
 

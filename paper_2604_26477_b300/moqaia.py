@@ -71,6 +71,7 @@ _sigs = {
     "moq_archive_destroy": (None, [_vp]),
     "moq_archive_reset": (C.c_int, [_vp, _vp]),
     "moq_pareto_front": (C.c_int, [_vp, _vp, _vp, _i64, _i64, C.POINTER(_i64), _vp]),
+    "moq_archive_merge": (C.c_int, [_vp, _vp, _vp]),
     "moq_archive_size": (C.c_int, [_vp, C.POINTER(_i64), _vp]),
     "moq_archive_copy_out": (C.c_int, [_vp, _vp, _vp, _vp, _i64, C.POINTER(_i64), _vp]),
     "moq_archive_device_view": (C.c_int, [_vp, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp)]),
@@ -254,6 +255,10 @@ def moq_pareto_front(a, cuts, bits, M, index_base, want_size=False, stream=None)
     _check(_lib.moq_pareto_front(a, _dptr(cuts, "cuts", i64), _dptr(bits, "bits", u64), M, index_base,
                                  C.byref(size) if want_size else None, _stream(stream)), "moq_pareto_front")
     return int(size.value) if want_size else None
+
+
+def moq_archive_merge(dst, src, stream=None):
+    _check(_lib.moq_archive_merge(dst, src, _stream(stream)), "moq_archive_merge")
 
 
 def moq_archive_size(a, stream=None) -> int:

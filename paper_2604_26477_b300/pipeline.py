@@ -60,6 +60,10 @@ class Archive:
     def reset(self, stream=None):
         M.moq_archive_reset(self.handle, stream)
 
+    def merge_from(self, other: "Archive", stream=None):
+        """Merges another archive's front into this one (``moq_archive_merge``)."""
+        M.moq_archive_merge(self.handle, other.handle, stream)
+
     def close(self):
         if getattr(self, "handle", None):
             M.moq_archive_destroy(self.handle)

@@ -660,3 +660,47 @@ def test_full_round_matches_oracle(M, P, oracle):
     assert np.array_equal(gb, _canonical(bits[keep], src.n))
     assert len(keep) > 1000  # a front of the benchmark's size (about 2300 points)
     assert arch.hypervolume(inst.ref) == oracle.hypervolume(cuts[keep], inst.ref)
+
+
+@pytest.mark.parametrize("K,max_batch", [(3, 4096), (4, 700)])
+def test_archive_merge_is_the_front_of_the_union(M, P, oracle, K, max_batch):
+    # two archives fed disjoint rounds, merged, hold exactly the front one archive fed every
+    # round holds -- the oracle's filter of the whole pool, each vector with its lowest global
+    # index -- also when the source front enters in several batches (max_batch < its size)
+    src = wl.heavy_hex_like(1003, K=K)
+    inst = P.Instance(src)
+    R = 2048
+    params = M.moq_default_params(steps=300, dt=0.5, alpha=0.1)
+    a = P.Archive(src.n, K, capacity=1 << 16, max_batch=max_batch)
+    b = P.Archive(src.n, K, capacity=1 << 16, max_batch=R)
+    whole = P.Archive(src.n, K, capacity=1 << 16, max_batch=R)
+    buf = P.RoundBuffers(R, src.n, K)
+    pool_cuts, pool_bits = [], []
+    for rnd in range(4):
+        M.moq_lambda_dirichlet(K, R, 5, rnd, buf.lam)
+        M.moq_sample(inst.handle, buf.lam, R, params, 5, rnd, buf.bits)
+        M.moq_evaluate_cuts(inst.handle, buf.bits, R, buf.cuts)
+        if rnd < 2:
+            for o in range(0, R, max_batch):
+                m = min(max_batch, R - o)
+                a.merge(buf.cuts[o:o + m], buf.bits[o:o + m], m, rnd * R + o)
+        else:
+            b.merge(buf.cuts, buf.bits, R, rnd * R)
+        whole.merge(buf.cuts, buf.bits, R, rnd * R)
+        pool_cuts.append(buf.cuts.cpu().numpy())
+        pool_bits.append(_bits_host(buf.bits).copy())
+    a.merge_from(b)
+    ca, ba, ia = a.copy_out()
+    cw, bw, iw = whole.copy_out()
+    oa, ow = np.argsort(ia), np.argsort(iw)
+    assert np.array_equal(ia[oa], iw[ow]) and np.array_equal(ca[oa], cw[ow]) and np.array_equal(ba[oa], bw[ow])
+    cuts = np.concatenate(pool_cuts)
+    keep = oracle.pareto_filter(cuts)
+    assert np.array_equal(np.sort(ia), keep) and np.array_equal(ca[oa], cuts[keep])
+    assert np.array_equal(ba[oa], _canonical(np.concatenate(pool_bits)[keep], src.n))
+    assert len(keep) > max_batch or K == 3
+    with pytest.raises(M.MoqError) as e:
+        a.merge_from(a)
+    assert e.value.code == M.MOQ_ERR_ARG
+    for x in (a, b, whole):
+        x.close()
