@@ -2,7 +2,9 @@
 
 One step = one pass of the whole path over one batch: NI-dSB sampling of R replicas
 (each on its own weight vector), exact K-objective cuts of every sample, the Pareto
-filter into a fresh device archive, and the exact hypervolume of the front.
+filter into a fresh device archive, and the exact hypervolume of the front (read back on
+the host). The K timed steps run as a two-stage pipeline: step s + 1 samples while step
+s's cuts, merge and hypervolume finish.
 
 Workload (default): heavy-hex-like graph n=42 / E=50, K=4 integer objectives in
 {-10..10}\\{0}, R=16384 replicas with uniform-simplex weight vectors, dSB, T=2000
@@ -238,17 +240,48 @@ def gpu_arm(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    # Timed region: the K steps as a pipeline over two sample buffers -- the sampling of step
+    # s + 1 runs on a second stream while step s's cuts, Pareto merge and hypervolume (this
+    # stream, the result read back on the host) finish. Every step does its whole path; the
+    # L2 flush (256 MB) precedes every sampling launch inside the timed region.
+    bufs = [buf, P.RoundBuffers(R, n, K)]
+    s_a = torch.cuda.Stream(device=dev)
+    s_b = torch.cuda.Stream(device=dev, priority=-1)  # its blocks go first as the sampler's retire
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    samp_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+    sampled = [None] * nsteps
+
+    def launch_sample(s):
+        with torch.cuda.stream(s_a):
+            flush.zero_()
+            samp_ev[s][0].record(s_a)
+            M.moq_sample(inst.handle, lam_all[s], R, params, 1, s, bufs[s % 2].bits, s_a)
+            samp_ev[s][1].record(s_a)
+            sampled[s] = s_a.record_event()
+
     with ClockSampler(dev.index) as clk:
         t_wall = time.perf_counter()
+        t_start.record(stream)
+        s_a.wait_stream(stream)
+        s_b.wait_stream(stream)
+        launch_sample(args.warmup)
         for s in range(args.warmup, nsteps):
-            flush.zero_()
-            step(s)
+            if s + 1 < nsteps:
+                launch_sample(s + 1)  # its buffer was last read by step s - 1, finished below
+            b = bufs[s % 2]
+            s_b.wait_event(sampled[s])
+            arch.reset(s_b)
+            M.moq_evaluate_cuts(inst.handle, b.bits, R, b.cuts, s_b)
+            arch.merge(b.cuts, b.bits, R, 0, stream=s_b)
+            hvs.append(arch.hypervolume(inst.ref, s_b))  # synchronises: the step's result on the host
+        stream.wait_stream(s_a)
+        stream.wait_stream(s_b)
+        t_end.record(stream)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
     fronts.append(arch.size())
-    step_ms = [ev[s][0].elapsed_time(ev[s][2]) for s in range(args.warmup, nsteps)]
-    sample_ms = [ev[s][0].elapsed_time(ev[s][1]) for s in range(args.warmup, nsteps)]
-    dev_s = sum(step_ms) / 1e3
+    sample_ms = [samp_ev[s][0].elapsed_time(samp_ev[s][1]) for s in range(args.warmup, nsteps)]
+    dev_s = t_start.elapsed_time(t_end) / 1e3
     dev_s, t_wall, samp_s = shard.max_over_ranks([dev_s, t_wall, sum(sample_ms) / 1e3])
     units = R * n * T * args.steps * world
     value = units / dev_s
@@ -997,6 +1030,8 @@ def main():
                           f"alpha={w['alpha']}, cuts + Pareto + hypervolume per step",
               "n": w["n"], "K": w["K"], "R": w["R"], "T": w["T"], "variant": w["variant"], "dt": w["dt"],
               "alpha": w["alpha"], "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas x{world}",
+              "timing": "K steps timed as one region (CUDA events): step s+1 samples on a second stream while step s's "
+                        "cuts, merge and hypervolume finish; the hypervolume of every step is read back on the host",
               "prewarm_s": args.prewarm}
 
     if args.impl == "reference":
