@@ -288,18 +288,30 @@ def gpu_arm(args, rank, world):
 
     # e2e through the C ABI with host buffers: weight vectors copied in from pinned host
     # memory every step, hypervolume and front size read back every step
+    # (the same two-stage pipeline: the copy-in and sampling of step s + 1 overlap step s's tail)
     lam_host = torch.from_numpy(wl.dirichlet_lambdas(R, K, 777 + rank)).pin_memory()
-    lam_dev = torch.empty_like(lam_host, device=dev)
+    lam_devs = [torch.empty_like(lam_host, device=dev) for _ in range(2)]
     torch.cuda.synchronize()
-    e2e_steps = max(1, min(args.steps, 5))
+    e2e_steps = max(1, min(args.steps, 10))
+    e2e_sampled = [None] * e2e_steps
+
+    def launch_e2e(s):
+        with torch.cuda.stream(s_a):
+            lam_devs[s % 2].copy_(lam_host, non_blocking=True)
+            M.moq_sample(inst.handle, lam_devs[s % 2], R, params, 99, s, bufs[s % 2].bits, s_a)
+            e2e_sampled[s] = s_a.record_event()
+
     t0 = time.perf_counter()
+    launch_e2e(0)
     for s in range(e2e_steps):
-        lam_dev.copy_(lam_host, non_blocking=True)
-        arch.reset()
-        M.moq_sample(inst.handle, lam_dev, R, params, 99, s, buf.bits)
-        M.moq_evaluate_cuts(inst.handle, buf.bits, R, buf.cuts)
-        arch.merge(buf.cuts, buf.bits, R, 0)
-        arch.hypervolume(inst.ref)
+        if s + 1 < e2e_steps:
+            launch_e2e(s + 1)
+        b = bufs[s % 2]
+        s_b.wait_event(e2e_sampled[s])
+        arch.reset(s_b)
+        M.moq_evaluate_cuts(inst.handle, b.bits, R, b.cuts, s_b)
+        arch.merge(b.cuts, b.bits, R, 0, stream=s_b)
+        arch.hypervolume(inst.ref, s_b)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e = {"value": R * n * T * e2e_steps / e2e_s * world, "unit": METRIC,
