@@ -1033,6 +1033,10 @@ def main():
     if args.cpu_baseline_worker:
         cpu_baseline_worker(args)
         return
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # one process per GPU: this same command again under torch.distributed.run, N ranks
+        from paper_2604_26477_b300 import shard
+        sys.exit(shard.launch_ranks(args.gpus, [os.path.abspath(__file__)] + sys.argv[1:]))
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -315,10 +315,13 @@ int moq_hypervolume_points(const int64_t* pts, int64_t F, int32_t K, const int64
  * library's own device memory, sized for moq_hypervolume_noalloc_max_points() points
  * (16384) of up to 4 objectives, about 1.4 MB on every GPU that loads the library,
  * held until the process exits. The call allocates nothing; the caller still owns pts,
- * ref and out. The first call on a device looks up that device's address of the array
- * (make it before any stream capture). Every call shares the one array and leaves its
- * contents behind, so calls that overlap on the GPU (e.g. from two streams at once)
- * race; calls in sequence are safe (the call synchronises its stream).
+ * ref and out, and the 20 result bytes are read back into the call's own stack frame (no
+ * pinned host buffer either). The first call on a device looks up that device's address
+ * of the array (make it before any stream capture); the address stays valid for the life
+ * of the device's context, so do not call this across a cudaDeviceReset. Every call
+ * shares the one array and leaves its contents behind, so calls that overlap on the GPU
+ * (e.g. from two streams at once) race; calls in sequence are safe (the call
+ * synchronises its stream).
  * Errors: MOQ_ERR_CAPACITY (F above the limit), otherwise as moq_hypervolume_points. */
 int64_t moq_hypervolume_noalloc_max_points(void);
 int moq_hypervolume_points_noalloc(const int64_t* pts, int64_t F, int32_t K, const int64_t* ref, moq_hv* out,

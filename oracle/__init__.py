@@ -51,6 +51,7 @@ def _load():
                                              np.ctypeslib.ndpointer(np.uint32)]
             lib.or_normal.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64]
             lib.or_normal.restype = C.c_double
+            lib.or_normal_fill.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64, C.c_int64, dp]
             lib.or_initial_state.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_float,
                                              C.POINTER(C.c_double), C.POINTER(C.c_double)]
             lib.or_cuts.argtypes = [C.c_int, C.c_int, C.c_int64, i32p, i32p, i32p, C.c_int64, u64p, i64p]
@@ -95,6 +96,13 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 
 def normal(seed: int, round_: int, r: int, i: int, m: int) -> float:
     return _load().or_normal(seed, round_, r, i, m)
+
+
+def normals(seed: int, round_: int, r: int, i: int, m0: int, count: int) -> np.ndarray:
+    """The noise draws of steps m0 .. m0 + count - 1 of one spin and replica."""
+    out = np.zeros(count, np.float64)
+    _load().or_normal_fill(seed, round_, r, i, m0, count, out)
+    return out
 
 
 def initial_state(seed: int, round_: int, r: int, i: int, amp: float = 0.1):

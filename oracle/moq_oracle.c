@@ -20,8 +20,9 @@
  *   or_sb             pinned: hand-computed steps, J=0 closed form, symmetry, max-cut
  *                     on bipartite graphs; trajectories are chaotic, so beyond a few
  *                     steps parity is statistical only.
- *   or_normal         pinned: moments and a KS test (the Gaussian is not pinned bitwise:
- *                     it goes through libm log/cos/sin).
+ *   or_normal         pinned: moments, KS tests, the tail mass beyond 3 and 4.71 standard
+ *                     deviations, no repeated values in 10^6 draws (53-bit uniforms); not
+ *                     pinned bitwise (it goes through libm log/cos).
  *   or_dirichlet      pinned: simplex sums, moments of Dirichlet(1,..,1).
  *   or_mlp_*          pinned: central finite differences of the loss.
  *   or_e4m3           pinned: torch's float8_e4m3fn conversion (nearest even) on every
@@ -70,11 +71,12 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* Counter layout shared (by definition, not by code) with the CUDA sampler:
- *   noise of spin i, replica r, step m:  ctr = (m >> 3, i, r, round), key = seed
+/* Counter layout:
  *   initial state of spin i, replica r:  ctr = (0xFFFFFFFF, i, r, round), key = seed
- * Each of the four words of a block gives two normals by Box-Muller on its two 16-bit
- * halves; step m uses word (m & 7) >> 1, the cosine for even m and the sine for odd m. */
+ *     (the same definition as the CUDA sampler's, so both start from the same state);
+ *   noise of spin i, replica r, step m:  ctr = (m, i, r, round), key = seed, one block
+ *     per draw (the oracle's own stream: trajectories with noise are compared with the
+ *     CUDA sampler's by distribution only). */
 static void philox_at(uint64_t seed, uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3, uint32_t out[4])
 {
     uint32_t ctr[4] = {w0, w1, w2, w3};
@@ -82,19 +84,29 @@ static void philox_at(uint64_t seed, uint32_t w0, uint32_t w1, uint32_t w2, uint
     or_philox4x32_10(ctr, key, out);
 }
 
-/* Gaussian eta_{i,m} of Eq. (NI-SB): Box-Muller on two 16-bit uniforms of one word,
- * u1 = (low half + 1) 2^-16 in (0, 1], u2 = (high half) 2^-16 in [0, 1):
- * rho = sqrt(-2 ln u1), theta = 2 pi u2, eta = rho cos theta or rho sin theta. */
+/* Gaussian eta_{i,m} of Eq. (NI-SB), a standard normal draw: Box-Muller (Box and Muller,
+ * 1958) on two uniforms of full double resolution from the block at (m, i, r, round),
+ *   u1 = (a + 1) 2^-53 in (0, 1],  a = the top 53 bits of words 0, 1 (o0 * 2^21 + o1 >> 11),
+ *   u2 = b 2^-53 in [0, 1),        b = the same of words 2, 3,
+ *   eta = sqrt(-2 ln u1) cos(2 pi u2).
+ * The smallest u1 is 2^-53, so |eta| reaches 8.57: the tails are those of a Gaussian
+ * to well below the probabilities any test here can see. */
 double or_normal(uint64_t seed, uint64_t round, uint32_t r, uint32_t i, uint64_t m)
 {
     uint32_t o[4];
-    philox_at(seed, (uint32_t)(m >> 3), i, r, (uint32_t)round, o);
-    uint32_t word = o[(m & 7) >> 1];
-    double u1 = ((double)(word & 0xFFFFu) + 1.0) * 0x1p-16;
-    double u2 = (double)(word >> 16) * 0x1p-16;
+    philox_at(seed, (uint32_t)m, i, r, (uint32_t)round, o);
+    uint64_t a = ((uint64_t)o[0] << 21) | (o[1] >> 11);
+    uint64_t b = ((uint64_t)o[2] << 21) | (o[3] >> 11);
+    double u1 = ((double)a + 1.0) * 0x1p-53;
+    double u2 = (double)b * 0x1p-53;
     double rho = sqrt(-2.0 * log(u1));
-    double theta = 2.0 * M_PI * u2;
-    return (m & 1) ? rho * sin(theta) : rho * cos(theta);
+    return rho * cos(2.0 * M_PI * u2);
+}
+
+/* count consecutive steps m0, m0 + 1, .. of spin i, replica r (bulk draws for the tests) */
+void or_normal_fill(uint64_t seed, uint64_t round, uint32_t r, uint32_t i, uint64_t m0, int64_t count, double* out)
+{
+    for (int64_t t = 0; t < count; ++t) out[t] = or_normal(seed, round, r, i, m0 + (uint64_t)t);
 }
 
 /* Uniform initial value in [-amp, amp): v = (w >> 8 - 2^23) * 2^-23 is exact in

@@ -84,7 +84,8 @@ cudaError_t launch_cuts(const moq_instance* h, const uint64_t* bits, int64_t M, 
         const int bd = 128;
         const size_t smem = sizeof(uint64_t) * (size_t)W * bd;
         auto k = k_cuts<KT, kSmemWords>;
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
         k<<<(unsigned)ceil_div(M, bd), bd, smem, st>>>(W, h->E, h->ei, h->ej, h->w, M, bits, cuts);
     } else {
         const int bd = 128;
@@ -114,6 +115,6 @@ extern "C" int moq_evaluate_cuts(const moq_instance* inst, const uint64_t* bits,
     case 7: e = launch_cuts<7>(inst, bits, M, cuts, st); break;
     default: e = launch_cuts<8>(inst, bits, M, cuts, st); break;
     }
-    if (e != cudaSuccess) return cuda_fail(e, "moq_evaluate_cuts launch");
+    if (e != cudaSuccess) return cuda_fail(e, "moq_evaluate_cuts launch (or its shared-memory attribute)");
     return MOQ_OK;
 }

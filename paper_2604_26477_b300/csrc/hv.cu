@@ -601,10 +601,16 @@ int64_t moq_hypervolume_workspace_size(int64_t F, int32_t K)
     return (int64_t)(al256(sizeof(int32_t) * (size_t)K * F) * 2 + al256(16 * (size_t)F) + al256(40 * (size_t)F) + 256);
 }
 
-int moq_hypervolume_points(const int64_t* pts, int64_t F, int32_t K, const int64_t* ref, void* workspace, moq_hv* out,
-                           void* stream)
+}  // extern "C"
+
+namespace moq {
+// The hypervolume of F points in the caller's workspace. With pinned_readback the result
+// words come back through this host thread's kept pinned buffer (allocated on the thread's
+// first call); without it they land in this stack frame, so the call allocates nothing on
+// the host or the device.
+int hv_points_impl(const int64_t* pts, int64_t F, int32_t K, const int64_t* ref, void* workspace, moq_hv* out, void* stream,
+                   bool pinned_readback)
 {
-    using namespace moq;
     if (!ref || !out || !workspace) return fail(MOQ_ERR_ARG, "moq_hypervolume_points: NULL argument");
     if (F < 0 || F >= ((int64_t)1 << 31)) return fail(MOQ_ERR_ARG, "moq_hypervolume_points: F out of range");
     if (K < 2) return fail(MOQ_ERR_ARG, "moq_hypervolume_points: K=%d < 2", K);
@@ -656,7 +662,7 @@ int moq_hypervolume_points(const int64_t* pts, int64_t F, int32_t K, const int64
         i128 v;
         int32_t flags;
     } local;
-    Result* pin = static_cast<Result*>(pinned_scratch(sizeof(Result)));
+    Result* pin = pinned_readback ? static_cast<Result*>(pinned_scratch(sizeof(Result))) : nullptr;
     Result& host = pin ? *pin : local;
     MOQ_CUDA_TRY(cudaMemcpyAsync(&host.v, ws.result, sizeof(i128), cudaMemcpyDeviceToHost, st));
     MOQ_CUDA_TRY(cudaMemcpyAsync(&host.flags, ws.flags, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -666,6 +672,15 @@ int moq_hypervolume_points(const int64_t* pts, int64_t F, int32_t K, const int64
     out->hi = (int64_t)(host.v >> 64);
     out->approx = (double)host.v;
     return MOQ_OK;
+}
+}  // namespace moq
+
+extern "C" {
+
+int moq_hypervolume_points(const int64_t* pts, int64_t F, int32_t K, const int64_t* ref, void* workspace, moq_hv* out,
+                           void* stream)
+{
+    return moq::hv_points_impl(pts, F, K, ref, workspace, out, stream, true);
 }
 
 int moq_hypervolume(const moq_archive* a, const int64_t* ref, moq_hv* out, void* stream)
@@ -705,7 +720,9 @@ void* g_noalloc_ptr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device. The symbol's host-side
 // name is only a stand-in, so the address is looked up once per device (with that
-// device current) and cached.
+// device current) and cached. A cudaDeviceReset (or any teardown of the device's primary
+// context) reloads the module and can move the array, so the cached address is only valid
+// for the life of the context it was taken in.
 int noalloc_scratch(void** out)
 {
     int dev = 0;
@@ -739,9 +756,11 @@ int moq_hypervolume_points_noalloc(const int64_t* pts, int64_t F, int32_t K, con
     void* scratch = nullptr;
     int rc = noalloc_scratch(&scratch);
     if (rc != MOQ_OK) return rc;
-    // the allocating entry point, handed the fixed array as its workspace; it clears the
-    // counter and the rank array that must start at zero and overwrites the rest before reading it
-    return moq_hypervolume_points(pts, F, K, ref, scratch, out, stream);
+    // the path of the allocating entry point, handed the fixed array as its workspace (it
+    // clears the counter and the rank array that must start at zero and overwrites the rest
+    // before reading it), with the 20 result bytes read back into this call's stack frame
+    // instead of a pinned host buffer
+    return hv_points_impl(pts, F, K, ref, scratch, out, stream, false);
 }
 
 }  // extern "C"

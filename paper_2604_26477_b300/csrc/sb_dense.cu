@@ -4,18 +4,15 @@
 // step computes G_k = J^(k) Phi for all K objectives with tcgen05.mma and applies the
 // symplectic update, the wall and the next phi in the epilogue.
 //
-// Step kernel, one CTA per tile of 128 spins (M) x 128 replicas (N), launched in clusters
-// of CL CTAs that share the spin tile (consecutive replica tiles):
+// Step kernel, tiles of 128 spins (M) x 128 replicas (N), one persistent CTA per SM:
 //  - the K-dimension (spins j) is walked in chunks of 64. A producer thread loads the
 //    chunk's operands with TMA into the 128-byte-swizzled K-major layout the tensor core
-//    reads: J^(k)[i0:+128, j0:+64] of every objective is shared by the cluster, so each CTA
-//    loads 128/CL of its rows and multicasts them to all CL CTAs (one L2 read feeds CL
-//    SMs); Phi[r0:+128, j0:+64] is the CTA's own. Three stages for K <= 3, two for K = 4;
-//  - an MMA thread waits for a stage's "full" barrier (own and peers' bytes landed),
-//    issues tcgen05.mma (BF16 x BF16 -> FP32, M=128, N=128, K=16) into one TMEM
-//    accumulator per objective (K x 128 of the 512 columns), and tcgen05.commit arrives on
-//    the stage's "empty" barrier of every CTA in the cluster; a producer refills a stage
-//    only when all CL CTAs have released it;
+//    reads: J^(k)[i0:+128, j0:+64] of every objective and Phi[r0:+128, j0:+64]. Three
+//    stages for K <= 3, two for K = 4;
+//  - an MMA thread waits for a stage's "full" barrier (its bytes landed), issues
+//    tcgen05.mma (BF16 x BF16 -> FP32, M=128, N=128, K=16) into one TMEM accumulator per
+//    objective (K x 128 of the 512 columns), and tcgen05.commit arrives on the stage's
+//    "empty" barrier, after which the producer refills it;
 //  - the epilogue (16 warps; warp w reads TMEM lanes 32*(w%4).. of columns 32*(w/4)..) forms
 //    f = -c0_r sum_k c_rk G_k[i, r], updates x, y (FP32, in HBM), applies the wall and
 //    writes phi(x) as BF16 for the next step.
@@ -51,12 +48,10 @@ struct moq_dense {
     unsigned long long* acc = nullptr;           // R_pad x K: s^T J_k s of the configurations being evaluated
     int32_t* maxabs = nullptr;                   // max |J| (device), read back at create
     int32_t max_abs_weight = 0;
-    CUtensorMap tm_J;                            // K x n_pad x n_pad, box 64 x (128 / CL) x 1
+    CUtensorMap tm_J;                            // K x n_pad x n_pad, box 64 x 128 x 1
     CUtensorMap tm_Jhi, tm_Jlo;                  // the two halves, box 64 x 128 x 1
-    CUtensorMap tm_J128;                         // J with box 64 x 128 x 1 (the resident kernel)
     bool resident = false;                       // all steps in one launch (n_pad = 128, K <= 3)
     CUtensorMap tm_phi[2];                       // R_pad x n_pad, box 64 x 128
-    int32_t cluster = 1;                         // CTAs per cluster sharing J tiles
     int32_t sms = 148;                           // persistent step kernel: one CTA per SM
     int32_t* status = nullptr;                   // device error flags
     int32_t* h_status = nullptr;                 // pinned
@@ -64,13 +59,13 @@ struct moq_dense {
     __nv_fp8_e4m3* J8 = nullptr;                 // K x n_pad x n_pad
     float* rowscale = nullptr;                   // K x n_pad, powers of two
     __nv_fp8_e4m3* phi8[2] = {nullptr, nullptr}; // R_pad x n_pad
-    CUtensorMap tm_J8;                           // box 128 x (128 / CL) x 1 (128 bytes per row, as BF16)
+    CUtensorMap tm_J8;                           // box 128 x 128 x 1 (128 bytes per row, as BF16)
     CUtensorMap tm_phi8[2];                      // box 128 x 128
     // split-precision operands (moq_sample_dense_split): J = BF16(J) + J_res with the residual
     // exact in BF16 (|J| <= kSplitMax), and for bSB phi = phi_hi + phi_lo (two BF16 parts)
     __nv_bfloat16* J_res = nullptr;              // K x n_pad x n_pad
     __nv_bfloat16* phi_lo[2] = {nullptr, nullptr};  // R_pad x n_pad
-    CUtensorMap tm_Jres;                         // box 64 x (128 / CL) x 1
+    CUtensorMap tm_Jres;                         // box 64 x 128 x 1
     CUtensorMap tm_philo[2];                     // box 64 x 128
 };
 
@@ -83,7 +78,6 @@ constexpr int kThreads = 512;
 // three operand stages (prefetch distance 2) when they fit in shared memory, else two
 __host__ __device__ constexpr int dense_stages(int K) { return K <= 3 ? 3 : 2; }
 constexpr uint64_t kWaitNs = 2000000000ull;        // bound of every mbarrier wait (2 s)
-constexpr int kMaxCluster = 4;                     // replica tiles sharing one J tile
 constexpr int32_t kSplitMax = 65408;               // |J| bound of the exact two-part split (256 * 255 + 128)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -150,18 +144,7 @@ __device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, uint64_t da, uint64_t 
                  : "memory");
 }
 
-// TMA tiled loads into shared memory, completing bytes on an mbarrier; the multicast form
-// writes the same box (and signals the barrier at the same offset) in every CTA of mask.
-__device__ __forceinline__ void tma_load_3d_mc(uint32_t dst, const CUtensorMap* tm, int c0, int c1, int c2, uint32_t mbar,
-                                               uint16_t mask)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%2, %3, %4}], "
-        "[%5], %6;" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(mbar), "h"(mask)
-        : "memory");
-}
-
+// TMA tiled loads into this CTA's shared memory, completing bytes on an mbarrier.
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, int c2, uint32_t mbar)
 {
     asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
@@ -179,11 +162,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm,
 __device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void cluster_sync()
-{
-    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
@@ -294,11 +272,6 @@ __device__ __forceinline__ bool dense_products(const CUtensorMap* tmA, const CUt
 constexpr int kWsEpiWarps = 16;
 constexpr int kWsThreads = 32 * (2 + kWsEpiWarps);
 
-// With clusters of CL CTAs (CL = 2, 4), the CTAs of a cluster take the CL replica blocks of
-// one spin block together: each loads 128 / CL rows of every J tile and multicasts them to
-// all, so L2 delivers each J tile once per cluster; a stage is refilled once every CTA's
-// products have released it (the MMA commits arrive in every CTA of the cluster).
-//
 // F8: the operands are E4M3 (J8 rows with a power-of-two scale per row and objective, phi = +-1
 // exact for dSB) multiplied by kind::f8f6f4 MMAs; a K-chunk is then 128 spins (the same 128
 // bytes per row, so the stages, swizzle and descriptors are those of BF16), and the epilogue
@@ -307,7 +280,7 @@ constexpr int kWsThreads = 32 * (2 + kWsEpiWarps);
 // Split (PREC = kPrecSplit): every K-chunk is multiplied in P passes into the same FP32
 // accumulator, each pass a full stage: (J_main, phi) and (J_res, phi) for dSB -- exact integer
 // products, the FP32 force -- and (J_main, phi_hi), (J_res, phi_hi), (J_main, phi_lo) for bSB.
-template <int VARIANT, int KOBJ, bool NOISE, int CL, int PREC>
+template <int VARIANT, int KOBJ, bool NOISE, int PREC>
 __global__ void __launch_bounds__(kWsThreads, 1)
     k_dense_step_ws(const __grid_constant__ CUtensorMap tmJ, const __grid_constant__ CUtensorMap tmPhi,
                     const __grid_constant__ CUtensorMap tmJ2, const __grid_constant__ CUtensorMap tmPhi2, const DenseStepArgs a,
@@ -334,15 +307,11 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr int kCk = chunk_elems<F8>();
     const int np = a.n_pad, nchunks = np / kCk;
-    constexpr int kSliceRows = kTileM / CL;
-    constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
-    uint32_t rank = 0;
-    if (CL > 1) asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
-    const int cid = blockIdx.x / CL, nclusters = gridDim.x / CL;
-    // tile group g = (spin block g % n_ib, replica blocks CL (g / n_ib) ..); this CTA's block: + rank
+    const int cid = blockIdx.x, nctas = gridDim.x;
+    // tile g = (spin block g % n_ib, replica block g / n_ib)
     auto tile_of = [&](int g, int& i0, int& r0) {
         i0 = (g % n_ib) * kTileM;
-        r0 = ((g / n_ib) * CL + (int)rank) * kTileN;
+        r0 = (g / n_ib) * kTileN;
     };
 
     if (warp == 0) {
@@ -352,7 +321,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     if (tid == 32) {
         for (int st = 0; st < S; ++st) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[st])), "r"(1));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[st])), "r"(CL));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[st])), "r"(1));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(tfull)), "r"(1));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(tempty)), "r"(kWsEpiWarps));
@@ -367,7 +336,6 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (CL > 1) cluster_sync();  // every CTA's barriers are initialised before any copy targets them
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
     bool ok = true;
@@ -375,7 +343,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     if (warp == 0) {
         if (lane == 0) {  // producer
             int gc = 0;
-            for (int g = cid; g < n_groups && ok; g += nclusters) {
+            for (int g = cid; g < n_groups && ok; g += nctas) {
                 int i0, r0;
                 tile_of(g, i0, r0);
                 for (int vc = 0; vc < nchunks * P; ++vc, ++gc) {  // chunk vc / P, pass vc % P
@@ -390,29 +358,21 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                     const CUtensorMap* tA = (P > 1 && pass == 1) ? &tmJ2 : &tmJ;
                     const CUtensorMap* tB = (P > 2 && pass == 2) ? &tmPhi2 : &tmPhi;
 #pragma unroll
-                    for (int k = 0; k < KOBJ; ++k) {
-                        if (CL > 1)
-                            tma_load_3d_mc(stage + k * kTileBytes + rank * (kSliceRows * 128), tA, j0, i0 + (int)rank * kSliceRows,
-                                           k, fb, kMask);
-                        else
-                            tma_load_3d(stage + k * kTileBytes, tA, j0, i0, k, fb);
-                    }
+                    for (int k = 0; k < KOBJ; ++k) tma_load_3d(stage + k * kTileBytes, tA, j0, i0, k, fb);
                     tma_load_2d(stage + KOBJ * kTileBytes, tB, j0, r0, fb);
                 }
             }
-            // no copy into this CTA is still in flight when it leaves (gc chunks were issued), and
-            // with clusters every CTA's release of the last use of each stage has arrived
+            // no copy into this CTA is still in flight when it leaves (gc chunks were issued)
             for (int st = 0; st < S && st < gc; ++st) {
                 const int c_last = st + ((gc - 1 - st) / S) * S;
                 if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((c_last / S) & 1))) ok = false;
-                if (CL > 1 && !mbar_wait(smem_u32(&empty[st]), (uint32_t)((c_last / S) & 1))) ok = false;
             }
         }
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {  // MMA issuer
             int gc = 0, lt = 0;
-            for (int g = cid; g < n_groups && ok; g += nclusters, ++lt) {
+            for (int g = cid; g < n_groups && ok; g += nctas, ++lt) {
                 // the epilogue has read the previous tile's accumulators
                 if (lt > 0 && !mbar_wait(smem_u32(tempty), (uint32_t)((lt - 1) & 1))) {
                     ok = false;
@@ -438,16 +398,9 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                                 mma_bf16(tmem + k * kTileN, sw128_desc(stage + k * kTileBytes + ks * 32),
                                          sw128_desc(stage + KOBJ * kTileBytes + ks * 32), (vc > 0 || ks > 0) ? 1u : 0u);
                         }
-                    if (CL > 1)
-                        asm volatile(
-                            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                                smem_u32(&empty[st])),
-                            "h"(kMask)
-                            : "memory");
-                    else
-                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                         smem_u32(&empty[st]))
-                                     : "memory");
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     smem_u32(&empty[st]))
+                                 : "memory");
                 }
                 if (!ok) break;
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(tfull))
@@ -481,7 +434,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         };
         stage_lambda(cid, 0);
         int lt = 0;
-        for (int g = cid; g < n_groups; g += nclusters, ++lt) {
+        for (int g = cid; g < n_groups; g += nctas, ++lt) {
             int i0, r0;
             tile_of(g, i0, r0);
             const int i = i0 + quarter * 32 + lane;
@@ -526,7 +479,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tempty)) : "memory");
-            if (g + nclusters < n_groups) stage_lambda(g + nclusters, b ^ 1);
+            if (g + nctas < n_groups) stage_lambda(g + nctas, b ^ 1);
             if (i < a.n) {
                 // one octet of columns per pass; the force of the next octet moves to f[0..7]
 #pragma unroll 1
@@ -579,7 +532,6 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     if (!ok) atomicOr(a.status, 1);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (CL > 1) cluster_sync();  // no CTA leaves while a peer may still write to it
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
@@ -970,60 +922,31 @@ __global__ void k_dense_philo(int32_t n, int32_t np, int32_t R, int32_t R_pad, c
 
 size_t dense_smem_bytes(int K) { return 1024 + dense_stages(K) * (size_t)(K + 1) * kTileBytes + (size_t)kTileN * (K + 1) * 4 + 64; }
 
-// grid: one CTA per SM (clusters of CL CTAs), at most one per tile group; `grid` carries the
-// spin-block and replica-block counts
-template <int VARIANT, int KOBJ, bool NOISE, int CL, int PREC>
+// grid: one CTA per SM, at most one per tile; `grid` carries the spin-block and
+// replica-block counts
+template <int VARIANT, int KOBJ, bool NOISE, int PREC>
 cudaError_t launch_step(const moq_dense* d, const CUtensorMap& tm_phi, const CUtensorMap& tm_phi2, const DenseStepArgs& a, dim3 grid,
                         cudaStream_t st)
 {
-    auto k = k_dense_step_ws<VARIANT, KOBJ, NOISE, CL, PREC>;
+    auto k = k_dense_step_ws<VARIANT, KOBJ, NOISE, PREC>;
     const size_t smem = ws_smem_bytes(KOBJ);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int n_groups = (int)(grid.x * (grid.y / CL));
-    cudaLaunchConfig_t cfg = {};
-    cfg.blockDim = dim3(kWsThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int clusters = d->sms / CL;
-    if (CL > 1) {
-        cfg.gridDim = dim3((unsigned)(clusters * CL));
-        int active = 0;
-        if (cudaOccupancyMaxActiveClusters(&active, k, &cfg) == cudaSuccess && active > 0) clusters = std::min(clusters, active);
-        (void)cudaGetLastError();
-    }
-    clusters = std::max(1, std::min(clusters, n_groups));
-    cfg.gridDim = dim3((unsigned)(clusters * CL));
-    return cudaLaunchKernelEx(&cfg, k, PREC == kPrecE4m3 ? d->tm_J8 : d->tm_J, tm_phi, d->tm_Jres, tm_phi2, a, (int32_t)grid.x,
-                              (int32_t)n_groups);
+    const int n_tiles = (int)(grid.x * grid.y);
+    const int ctas = std::max(1, std::min(d->sms, n_tiles));
+    k<<<ctas, kWsThreads, smem, st>>>(PREC == kPrecE4m3 ? d->tm_J8 : d->tm_J, tm_phi, d->tm_Jres, tm_phi2, a, (int32_t)grid.x,
+                                      (int32_t)n_tiles);
+    return cudaGetLastError();
 }
 
-template <int VARIANT, bool NOISE, int CL, int PREC>
+template <int VARIANT, bool NOISE, int PREC>
 cudaError_t launch_step_k(const moq_dense* d, const CUtensorMap& tm_phi, const CUtensorMap& tm_phi2, const DenseStepArgs& a, dim3 grid,
                           cudaStream_t st)
 {
     switch (a.K) {
-    case 2: return launch_step<VARIANT, 2, NOISE, CL, PREC>(d, tm_phi, tm_phi2, a, grid, st);
-    case 3: return launch_step<VARIANT, 3, NOISE, CL, PREC>(d, tm_phi, tm_phi2, a, grid, st);
-    default: return launch_step<VARIANT, 4, NOISE, CL, PREC>(d, tm_phi, tm_phi2, a, grid, st);
-    }
-}
-
-template <int VARIANT, bool NOISE, int PREC>
-cudaError_t launch_step_cl(const moq_dense* d, const CUtensorMap& tm_phi, const CUtensorMap& tm_phi2, const DenseStepArgs& a, dim3 grid,
-                           cudaStream_t st)
-{
-    switch (d->cluster) {
-    case 1: return launch_step_k<VARIANT, NOISE, 1, PREC>(d, tm_phi, tm_phi2, a, grid, st);
-    case 2: return launch_step_k<VARIANT, NOISE, 2, PREC>(d, tm_phi, tm_phi2, a, grid, st);
-    default: return launch_step_k<VARIANT, NOISE, 4, PREC>(d, tm_phi, tm_phi2, a, grid, st);
+    case 2: return launch_step<VARIANT, 2, NOISE, PREC>(d, tm_phi, tm_phi2, a, grid, st);
+    case 3: return launch_step<VARIANT, 3, NOISE, PREC>(d, tm_phi, tm_phi2, a, grid, st);
+    default: return launch_step<VARIANT, 4, NOISE, PREC>(d, tm_phi, tm_phi2, a, grid, st);
     }
 }
 
@@ -1033,13 +956,13 @@ cudaError_t launch_step_form(const moq_dense* d, int variant, bool noise, const 
                              const DenseStepArgs& a, dim3 grid, cudaStream_t st)
 {
     if (variant == MOQ_DSB)
-        return noise ? launch_step_cl<MOQ_DSB, true, PREC>(d, tm_phi, tm_phi2, a, grid, st)
-                     : launch_step_cl<MOQ_DSB, false, PREC>(d, tm_phi, tm_phi2, a, grid, st);
+        return noise ? launch_step_k<MOQ_DSB, true, PREC>(d, tm_phi, tm_phi2, a, grid, st)
+                     : launch_step_k<MOQ_DSB, false, PREC>(d, tm_phi, tm_phi2, a, grid, st);
     if constexpr (PREC == kPrecE4m3) {
         return cudaErrorInvalidValue;  // E4M3 phi serves dSB only (checked by the caller)
     } else {
-        return noise ? launch_step_cl<MOQ_BSB, true, PREC>(d, tm_phi, tm_phi2, a, grid, st)
-                     : launch_step_cl<MOQ_BSB, false, PREC>(d, tm_phi, tm_phi2, a, grid, st);
+        return noise ? launch_step_k<MOQ_BSB, true, PREC>(d, tm_phi, tm_phi2, a, grid, st)
+                     : launch_step_k<MOQ_BSB, false, PREC>(d, tm_phi, tm_phi2, a, grid, st);
     }
 }
 
@@ -1050,7 +973,7 @@ cudaError_t launch_resident(const moq_dense* d, const ResidentArgs& a, int tiles
     const size_t smem = resident_smem_bytes(KOBJ);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<tiles, kThreads, smem, st>>>(d->tm_J128, d->tm_phi[0], a);
+    k<<<tiles, kThreads, smem, st>>>(d->tm_J, d->tm_phi[0], a);
     return cudaGetLastError();
 }
 
@@ -1074,14 +997,10 @@ int encode_maps(moq_dense* d)
     {
         const cuuint64_t dims[3] = {np, np, (cuuint64_t)d->K};
         const cuuint64_t strides[2] = {np * 2, np * np * 2};
-        const cuuint32_t box[3] = {(cuuint32_t)kChunkK, (cuuint32_t)(kTileM / d->cluster), 1};
+        const cuuint32_t box[3] = {(cuuint32_t)kChunkK, (cuuint32_t)kTileM, 1};
         CUresult r = encode(&d->tm_J, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, d->J, dims, strides, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
                             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(MOQ_ERR_CUDA, "cuTensorMapEncodeTiled(J) failed: %d", (int)r);
-        const cuuint32_t box128[3] = {(cuuint32_t)kChunkK, (cuuint32_t)kTileM, 1};
-        r = encode(&d->tm_J128, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, d->J, dims, strides, box128, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return fail(MOQ_ERR_CUDA, "cuTensorMapEncodeTiled(J full tile) failed: %d", (int)r);
     }
     for (int h = 0; h < 2; ++h) {
         const cuuint64_t dims[3] = {np, np, (cuuint64_t)d->K};
@@ -1104,7 +1023,7 @@ int encode_maps(moq_dense* d)
     {  // the residual of the split form: as J
         const cuuint64_t dims[3] = {np, np, (cuuint64_t)d->K};
         const cuuint64_t strides[2] = {np * 2, np * np * 2};
-        const cuuint32_t box[3] = {(cuuint32_t)kChunkK, (cuuint32_t)(kTileM / d->cluster), 1};
+        const cuuint32_t box[3] = {(cuuint32_t)kChunkK, (cuuint32_t)kTileM, 1};
         CUresult r = encode(&d->tm_Jres, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, d->J_res, dims, strides, box, one,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -1122,7 +1041,7 @@ int encode_maps(moq_dense* d)
     {  // FP8 operands: the same 128-byte rows, 128 E4M3 elements per chunk
         const cuuint64_t dims[3] = {np, np, (cuuint64_t)d->K};
         const cuuint64_t strides[2] = {np, np * np};
-        const cuuint32_t box[3] = {128u, (cuuint32_t)(kTileM / d->cluster), 1};
+        const cuuint32_t box[3] = {128u, (cuuint32_t)kTileM, 1};
         CUresult r = encode(&d->tm_J8, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, d->J8, dims, strides, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
                             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(MOQ_ERR_CUDA, "cuTensorMapEncodeTiled(J8) failed: %d", (int)r);
@@ -1182,9 +1101,9 @@ int sample_dense_impl(moq_dense* d, const float* lambda, int32_t R, const moq_sa
                     d->max_abs_weight, kSplitMax);
     cudaStream_t st = as_stream(stream);
     const moq_instance* h = d->inst;
-    // replica tiles come in whole clusters (the padded replicas compute on zero weights and
-    // are never written)
-    const int np = d->n_pad, Rp = (int)ceil_div(R, kTileN * d->cluster) * kTileN * d->cluster;
+    // replicas come in whole tiles (the padded replicas compute on zero weights and are never
+    // written)
+    const int np = d->n_pad, Rp = (int)ceil_div(R, kTileN) * kTileN;
     const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32), rnd = (uint32_t)round;
     k_dense_c0<<<R, 256, 0, st>>>(h->rowsum, h->rowptr, h->wn, h->nnz, d->n, d->K, lambda, R, d->c0);
     const int gi = (int)std::min<int64_t>(ceil_div((int64_t)Rp * np, 256), 148 * 32);
@@ -1302,21 +1221,12 @@ int moq_dense_create(const moq_instance* inst, int32_t max_replicas, moq_dense**
     d->inst = inst;
     d->n_pad = (int)ceil_div(inst->n, kTileM) * kTileM;
     d->max_R = max_replicas;
-    d->R_pad = (int)ceil_div(max_replicas, kTileN * kMaxCluster) * kTileN * kMaxCluster;
-    // J tiles multicast over clusters of 2 or 4 CTAs cut the L2 reads of J by 2 or 4 but tie
-    // the CTAs of a cluster to each other's pace; at n = 2000, R = 8192 (persistent kernel,
-    // same call) clusters of 1, 2, 4 measured 187-191, 188-189 and 198-200 us per step, so
-    // clusters are opt-in (MOQ_DENSE_CLUSTER)
-    d->cluster = 1;
+    d->R_pad = (int)ceil_div(max_replicas, kTileN) * kTileN;
     {
         int dev = 0, sms = 0;
         if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
             sms > 0)
             d->sms = sms;
-    }
-    if (const char* env = getenv("MOQ_DENSE_CLUSTER")) {
-        const int v = atoi(env);
-        d->cluster = (v == 2 || v == 4) ? v : 1;
     }
     // graphs of at most 128 spins with K <= 3 run all steps in one launch from shared
     // memory and TMEM (MOQ_DENSE_RESIDENT=0 keeps the per-step kernel)

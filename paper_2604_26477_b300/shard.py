@@ -15,9 +15,32 @@ here does arithmetic of the method.
 """
 from __future__ import annotations
 
+import socket
+import subprocess
+import sys
+
 import numpy as np
 import torch
 import torch.distributed as dist
+
+
+def free_port() -> int:
+    """A TCP port on 127.0.0.1 that is free right now (for the rendezvous of a local launch)."""
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def launch_ranks(n: int, script_argv: list[str], master_port: int | None = None) -> int:
+    """Runs ``python <script_argv>`` as n processes on this node (one per GPU) through
+    torch.distributed.run, with the rendezvous on 127.0.0.1; each process reads RANK,
+    LOCAL_RANK and WORLD_SIZE from its environment. Returns the launcher's exit code."""
+    if n < 1:
+        raise ValueError("need n >= 1")
+    port = master_port or free_port()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", f"--master-port={port}"] + list(script_argv)
+    return subprocess.call(cmd)
 
 
 def replica_shard(R_total: int, rank: int, world: int) -> tuple[int, int]:

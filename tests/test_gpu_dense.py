@@ -151,35 +151,6 @@ def test_dense_final_hv_distribution(M, P, oracle):
     assert abs(np.median(hv_g) / np.median(hv_c) - 1) < 0.03
 
 
-@pytest.mark.parametrize("variant", ["dsb", "bsb"])
-def test_dense_cluster_sizes_agree_bitwise(M, P, variant, monkeypatch):
-    # J tiles are shared by clusters of 1, 2 or 4 CTAs (each loads a slice and multicasts
-    # it); who loads a row does not change any product, so all cluster sizes give the
-    # same bits, x and y
-    src = wl.random_graph(300, 1.0, 31, K=3, wmax=300)
-    inst = P.Instance(src)
-    R, T = 700, 7  # ragged replica tiles, padded to whole clusters
-    lam = _dev(wl.dirichlet_lambdas(R, 3, 8))
-    out = {}
-    for cl in ("1", "2", "4"):
-        monkeypatch.setenv("MOQ_DENSE_CLUSTER", cl)
-        d = M.moq_dense_create(inst.handle, R)
-        try:
-            xo = torch.zeros((R, src.n), device="cuda")
-            yo = torch.zeros((R, src.n), device="cuda")
-            bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
-            p = M.moq_default_params(variant=variant, steps=T, dt=0.5, alpha=0.1, x_out=xo, y_out=yo)
-            M.moq_sample_dense(d, lam, R, p, 3, 1, bits)
-            M.moq_dense_status(d)
-            out[cl] = (bits.cpu(), xo.cpu(), yo.cpu())
-        finally:
-            M.moq_dense_destroy(d)
-    for cl in ("2", "4"):
-        for a, b in zip(out["1"], out[cl]):
-            assert torch.equal(a, b)
-
-
-
 @pytest.mark.parametrize("n,R,K,variant,alpha,sched", [(25, 300, 3, "dsb", 0.1, False), (128, 129, 2, "bsb", 0.1, False),
                                                       (100, 1, 3, "bsb", 0.0, True), (70, 640, 2, "dsb", 0.0, False),
                                                       (128, 256, 3, "dsb", 0.2, True)])
@@ -439,30 +410,6 @@ def test_dense_fp8_force_within_e4m3_bound(M, P, oracle, n, R, K):
     assert rel.max() > 1e-5  # the weights really are rounded (not the exact path)
 
 
-@pytest.mark.parametrize("cl", ["2", "4"])
-def test_dense_fp8_cluster_sizes_agree_bitwise(M, P, cl, monkeypatch):
-    # E4M3 J tiles multicast over clusters of 2 or 4 CTAs give the bits of single CTAs
-    src = wl.complete_graph(300, 33, K=3)
-    inst = P.Instance(src)
-    R, T = 700, 7
-    lam = _dev(wl.dirichlet_lambdas(R, 3, 8))
-    out = {}
-    for c in ("1", cl):
-        monkeypatch.setenv("MOQ_DENSE_CLUSTER", c)
-        d = M.moq_dense_create(inst.handle, R)
-        try:
-            xo = torch.zeros((R, src.n), device="cuda")
-            bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
-            p = M.moq_default_params(variant="dsb", steps=T, dt=0.5, alpha=0.1, x_out=xo)
-            M.moq_sample_dense_fp8(d, lam, R, p, 3, 1, bits)
-            M.moq_dense_status(d)
-            out[c] = (bits.cpu(), xo.cpu())
-        finally:
-            M.moq_dense_destroy(d)
-    for a, b in zip(out["1"], out[cl]):
-        assert torch.equal(a, b)
-
-
 def test_dense_fp8_rejects_bsb(M, P):
     src = wl.random_graph(40, 1.0, 3, K=2, wmax=10)
     inst = P.Instance(src)
@@ -591,29 +538,6 @@ def test_dense_split_bsb_tracks_fp32_form(M, P):
         finally:
             (M.moq_dense_destroy if form == "split" else M.moq_dense_fp32_destroy)(d)
     assert np.abs(res["split"] - res["fp32"]).max() < 1e-5
-
-
-@pytest.mark.parametrize("cl", ["2", "4"])
-def test_dense_split_cluster_sizes_agree_bitwise(M, P, cl, monkeypatch):
-    src = wl.complete_graph(300, 34, K=3)
-    inst = P.Instance(src)
-    R, T = 700, 7
-    lam = _dev(wl.dirichlet_lambdas(R, 3, 9))
-    out = {}
-    for c in ("1", cl):
-        monkeypatch.setenv("MOQ_DENSE_CLUSTER", c)
-        d = M.moq_dense_create(inst.handle, R)
-        try:
-            xo = torch.zeros((R, src.n), device="cuda")
-            bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
-            p = M.moq_default_params(variant="bsb", steps=T, dt=0.5, alpha=0.1, x_out=xo)
-            M.moq_sample_dense_split(d, lam, R, p, 3, 1, bits)
-            M.moq_dense_status(d)
-            out[c] = (bits.cpu(), xo.cpu())
-        finally:
-            M.moq_dense_destroy(d)
-    for a, b in zip(out["1"], out[cl]):
-        assert torch.equal(a, b)
 
 
 def test_dense_split_rejects_large_weights(M, P):

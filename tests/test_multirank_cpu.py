@@ -81,3 +81,20 @@ def test_single_process_is_the_identity():
     out = shard.gather_fronts(cuts, bits, np.arange(50))
     assert np.array_equal(out[0], cuts) and np.array_equal(out[1], bits) and np.array_equal(out[2], np.arange(50))
     assert shard.max_over_ranks([1.0, 2.0]) == [1.0, 2.0]
+
+
+def test_bench_launches_its_own_ranks():
+    # bench.py --gpus 2 without a launcher around it starts two ranks itself (torch.distributed.run,
+    # rendezvous on 127.0.0.1); the reference arm runs on rank 0 alone and prints one line
+    import json
+    import subprocess
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "3", "--cpu-seconds", "1"],
+                       capture_output=True, text=True, timeout=900, env=env, cwd=ROOT)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [ln for ln in p.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, p.stdout[-2000:]
+    line = json.loads(lines[0])
+    assert line["n_gpus"] == 2 and line["impl"] == "reference" and line["value"] > 0

@@ -28,21 +28,39 @@ def test_philox_known_answers(oracle):
 
 
 def test_normal_moments_and_ks(oracle):
+    # Eq. NI-SB asks for standard Gaussian noise: moments, KS, kurtosis
     z = np.array([oracle.normal(7, 3, r, i, m) for r in range(4) for i in range(50) for m in range(100)])
     assert abs(z.mean()) < 0.03 and abs(z.var() - 1.0) < 0.04
     assert stats.kstest(z, "norm").pvalue > 1e-3
     assert abs(stats.kurtosis(z, fisher=False) - 3.0) < 0.2
-    # the eight normals of one Philox block are distinct draws (cos/sin of four pairs)
-    blk = [oracle.normal(1, 0, 0, 0, m) for m in range(8)]
-    assert len(set(blk)) == 8
-    # 16-bit uniforms: u1 >= 2^-16 bounds every pair's radius by sqrt(32 ln 2); the pair's
-    # angle is uniform on the circle
-    pairs = z.reshape(-1, 2)
-    rad2 = (pairs ** 2).sum(axis=1)
-    assert rad2.max() <= 32 * np.log(2) + 1e-9
-    assert stats.kstest(1 - np.exp(-rad2 / 2), "uniform").pvalue > 1e-3  # rho^2 / 2 ~ Exp(1)
-    ang = (np.arctan2(pairs[:, 1], pairs[:, 0]) + np.pi) / (2 * np.pi)
-    assert stats.kstest(ang, "uniform").pvalue > 1e-3
+    # the bulk helper returns the same draws as single calls
+    assert np.array_equal(oracle.normals(7, 3, 1, 2, 0, 100), z[(1 * 50 + 2) * 100:(1 * 50 + 3) * 100])
+    # steps, spins, replicas, rounds and seeds are distinct draws
+    base = oracle.normal(1, 0, 0, 0, 0)
+    assert len({base, oracle.normal(1, 0, 0, 0, 1), oracle.normal(1, 0, 0, 1, 0), oracle.normal(1, 0, 1, 0, 0),
+                oracle.normal(1, 1, 0, 0, 0), oracle.normal(2, 0, 0, 0, 0)}) == 6
+
+
+def test_normal_tails_and_resolution(oracle):
+    # a standard Gaussian's tail mass: P(|Z| > 3) = 2.700e-3, P(|Z| > 4.71) = 2.48e-6. A draw
+    # from 16-bit uniforms is bounded by sqrt(32 ln 2) = 4.71 and fails the second check.
+    z = np.concatenate([oracle.normals(11, 0, r, i, 0, 1_000_000) for r in range(4) for i in range(5)])
+    N = z.size
+    a = np.abs(z)
+    p3 = 2 * stats.norm.sf(3.0)
+    n3 = int((a > 3.0).sum())
+    assert abs(n3 - N * p3) < 5 * np.sqrt(N * p3), n3
+    bound = np.sqrt(32 * np.log(2))
+    p4 = 2 * stats.norm.sf(bound)
+    n4 = int((a > bound).sum())
+    assert stats.poisson.cdf(n4, N * p4) > 1e-4 and stats.poisson.sf(n4 - 1, N * p4) > 1e-4, (n4, N * p4)
+    assert n4 > 0
+    # 53-bit uniforms: no two of a million draws coincide (16-bit pairs would collide ~100 times)
+    assert np.unique(z[:1_000_000]).size == 1_000_000
+    # the radius of Box-Muller: rho^2 / 2 = -ln u1 ~ Exp(1), checked on |eta| through the
+    # half-normal law, and the sign is a fair coin
+    assert stats.kstest(a[:200_000], stats.halfnorm.cdf).pvalue > 1e-3
+    assert abs((z[:200_000] > 0).mean() - 0.5) < 0.005
 
 
 def test_initial_state_uniform(oracle):

@@ -45,6 +45,29 @@ def test_noalloc_matches_allocating_entry_point_on_consecutive_calls(M):
                                             np.zeros(3, np.int64)) == 0
 
 
+def test_noalloc_from_a_fresh_host_thread(M):
+    # a host thread that never called the library before: the result comes back into the
+    # call's own stack frame, not a per-thread pinned buffer created on first use
+    import threading
+    pts = _points(5, 900, 3, 700)
+    ref = np.zeros(3, np.int64)
+    dev = torch.from_numpy(pts).cuda()
+    want = _with_workspace(M, dev, 900, 3, ref)
+    got = {}
+
+    def run():
+        try:
+            got["hv"] = [M.moq_hypervolume_points_noalloc(dev, 900, 3, ref) for _ in range(2)]
+        except Exception as e:  # surfaced by the assertion below
+            got["err"] = e
+
+    t = threading.Thread(target=run)
+    t.start()
+    t.join(120)
+    assert "err" not in got, got.get("err")
+    assert got["hv"] == [want, want]
+
+
 def test_noalloc_rejects_sizes_beyond_its_fixed_scratch(M):
     limit = M.moq_hypervolume_noalloc_max_points()
     assert limit == 16384
