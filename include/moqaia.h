@@ -48,6 +48,8 @@ extern "C" {
 /* ---- SB variants ("Simulated Bifurcation with Gaussian noise") ----------------- */
 #define MOQ_DSB 0 /* discrete SB: phi(x) = sgn(x) */
 #define MOQ_BSB 1 /* ballistic SB: phi(x) = x */
+#define MOQ_PREC_FP32 0 /* state and step arithmetic in FP32 */
+#define MOQ_PREC_FP16 1 /* state and step arithmetic in FP16, the paper's float16 (moq_sample) */
 
 typedef struct moq_instance moq_instance;
 typedef struct moq_archive moq_archive;
@@ -82,6 +84,7 @@ typedef struct moq_sample_params {
     float* x_out;          /* device R x n final positions, or NULL */
     float* y_out;          /* device R x n final momenta, or NULL */
     uint32_t replica_offset; /* added to r in the Philox replica counter (batches: the instance's offset) */
+    int32_t precision;     /* MOQ_PREC_FP32 (default) or MOQ_PREC_FP16 (moq_sample and per-instance batches only) */
 } moq_sample_params;
 
 /* Result of moq_hypervolume: value = hi * 2^64 + (uint64)lo (a signed 128-bit int). */
@@ -130,8 +133,14 @@ int moq_instance_get_info(const moq_instance* inst, moq_instance_info* out);
  * runs on-chip in one launch; each thread runs one spin of one replica or, where that keeps
  * more replicas in flight per SM (degree bound <= 4), of two (same results; the
  * environment variable MOQ_SB_PAIR = 0 / 1 forces a form).
- * Errors: MOQ_ERR_ARG (R < 0, steps < 0, bad variant, NULL lambda/bits with R > 0),
- * MOQ_ERR_UNSUPPORTED (n > 1024 or max degree > 16), MOQ_ERR_CUDA. Asynchronous. */
+ * p->precision = MOQ_PREC_FP16 runs the paper's float16 ("Results and discussion": SB in
+ * float16): x, y, the couplings -c0 J(c), phi and every multiply-add of a step in FP16
+ * (two replicas per thread as packed half2; c0 and J(c) formed in FP32, then rounded once);
+ * the start state, the pump value and eta are the FP32 form's, rounded to FP16. Degree
+ * bound 8. Per-step force error against FP64: at most (deg + 2) 2^-11 c0 sum_j |J(c)_ij phi_j|.
+ * Errors: MOQ_ERR_ARG (R < 0, steps < 0, bad variant or precision, NULL lambda/bits with
+ * R > 0), MOQ_ERR_UNSUPPORTED (n > 1024, max degree > 16, or > 8 with FP16), MOQ_ERR_CUDA.
+ * Asynchronous. */
 int moq_sample(const moq_instance* inst, const float* lambda, int32_t R, const moq_sample_params* p,
                uint64_t seed, uint64_t round, uint64_t* bits, void* stream);
 

@@ -67,6 +67,7 @@ void moq_default_params(moq_sample_params* p)
     p->x_out = nullptr;
     p->y_out = nullptr;
     p->replica_offset = 0;
+    p->precision = MOQ_PREC_FP32;
 }
 
 }  // extern "C"

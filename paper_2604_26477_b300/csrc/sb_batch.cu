@@ -537,6 +537,8 @@ int moq_sample_batch(moq_batch* b, const float* lambda_all, const moq_sample_par
         }
         return rc;
     }
+    if (p->precision != MOQ_PREC_FP32)
+        return fail(MOQ_ERR_UNSUPPORTED, "moq_sample_batch: the persistent kernel runs FP32 (per-instance mode runs FP16)");
     MOQ_CUDA_TRY(cudaMemsetAsync(b->d_queue, 0, sizeof(int32_t), st));
     BatchArgs a{};
     a.insts = b->d_insts;

@@ -29,4 +29,24 @@ __device__ __forceinline__ void sb_update(float f, float cm, float eta, float dt
     }
 }
 
+// The same update for the two replicas of a pair at once: every multiply-add is one
+// packed two-lane FP32 instruction (each lane rounds as the scalar fmaf does, so both forms
+// give the same bits); the wall is applied per lane.
+template <bool NOISE>
+__device__ __forceinline__ void sb_update2(float2 f, float2 cm, float2 eta, float2 dt, float2 kappa, float2 dta0, float2& x, float2& y)
+{
+    const float2 drift = __ffma2_rn(cm, x, f);
+    y = __ffma2_rn(dt, drift, y);
+    if (NOISE) y = __ffma2_rn(kappa, eta, y);
+    x = __ffma2_rn(dta0, y, x);
+    if (fabsf(x.x) > 1.0f) {
+        x.x = copysignf(1.0f, x.x);
+        y.x = 0.0f;
+    }
+    if (fabsf(x.y) > 1.0f) {
+        x.y = copysignf(1.0f, x.y);
+        y.y = 0.0f;
+    }
+}
+
 }  // namespace moq

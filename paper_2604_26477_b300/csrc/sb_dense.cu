@@ -1094,6 +1094,9 @@ int sample_dense_impl(moq_dense* d, const float* lambda, int32_t R, const moq_sa
     if (R == 0) return MOQ_OK;
     if (!lambda || !bits) return fail(MOQ_ERR_ARG, "moq_sample_dense: NULL lambda or bits");
     if (p->replica_offset != 0) return fail(MOQ_ERR_UNSUPPORTED, "moq_sample_dense: replica_offset must be 0");
+    if (p->precision != MOQ_PREC_FP32)
+        return fail(MOQ_ERR_UNSUPPORTED, "moq_sample_dense: the dense forms take their operand precision from the entry point "
+                                         "(state in FP32); p->precision must be MOQ_PREC_FP32");
     if (f8 && p->variant != MOQ_DSB)
         return fail(MOQ_ERR_UNSUPPORTED, "moq_sample_dense_fp8: E4M3 phi is exact for dSB only (bSB: use moq_sample_dense)");
     if (split && d->max_abs_weight > kSplitMax)

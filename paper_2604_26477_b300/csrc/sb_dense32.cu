@@ -278,6 +278,7 @@ int moq_sample_dense_fp32(moq_dense_fp32* d, const float* lambda, int32_t R, con
     if (R == 0) return MOQ_OK;
     if (!lambda || !bits) return fail(MOQ_ERR_ARG, "moq_sample_dense_fp32: NULL lambda or bits");
     if (p->replica_offset != 0) return fail(MOQ_ERR_UNSUPPORTED, "moq_sample_dense_fp32: replica_offset must be 0");
+    if (p->precision != MOQ_PREC_FP32) return fail(MOQ_ERR_UNSUPPORTED, "moq_sample_dense_fp32: p->precision must be MOQ_PREC_FP32");
     cudaStream_t st = as_stream(stream);
     const moq_instance* h = d->inst;
     const int np = d->n_pad, Rp = (int)ceil_div(R, kF32N) * kF32N;

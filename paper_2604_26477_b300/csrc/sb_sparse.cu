@@ -14,6 +14,8 @@
 #include <algorithm>
 #include <stdlib.h>
 
+#include <cuda_fp16.h>
+
 #include "sb_common.cuh"
 
 namespace moq {
@@ -277,21 +279,20 @@ cudaError_t launch_variant(const SbArgs& a, int dmax, bool noise, int pump, dim3
 // shared by two updates. Each replica's arithmetic and noise counters are those of
 // k_sb_sparse, so both kernels give the same bits; the host takes this form when it keeps
 // more replicas in flight per SM (register and block limits, from the occupancy API).
+// Both replicas' arithmetic runs in packed two-lane FP32 instructions (jc[d] holds the
+// pair's couplings of neighbour d, x and y the pair's states), lane by lane the scalar
+// arithmetic of k_sb_sparse. (Measured at n = 42, R = 16384, T = 2000: 1.55 against 1.63 ms
+// per launch for the scalar pair; packing the Box-Muller pairs as well, with the pump value
+// stored twice, measured 1.58 ms.)
 template <int VARIANT, int DMAX, bool NOISE>
-__device__ __forceinline__ void sb_step2(const float2* rd, float2* wr, int tid, const float (&jc0)[DMAX], const float (&jc1)[DMAX],
-                                         const int (&nb)[DMAX], float cm, float e0, float e1, float dt, float kappa, float dta0,
-                                         float& x0, float& y0, float& x1, float& y1)
+__device__ __forceinline__ void sb_step2(const float2* rd, float2* wr, int tid, const float2 (&jc)[DMAX], const int (&nb)[DMAX],
+                                         float cm, float e0, float e1, float2 dt, float2 kappa, float2 dta0, float2& x, float2& y)
 {
-    float f0 = 0.0f, f1 = 0.0f;
+    float2 f = make_float2(0.0f, 0.0f);
 #pragma unroll
-    for (int d = 0; d < DMAX; ++d) {
-        const float2 ph = rd[nb[d]];
-        f0 = fmaf(jc0[d], ph.x, f0);
-        f1 = fmaf(jc1[d], ph.y, f1);
-    }
-    sb_update<NOISE>(f0, cm, e0, dt, kappa, dta0, x0, y0);
-    sb_update<NOISE>(f1, cm, e1, dt, kappa, dta0, x1, y1);
-    wr[tid] = make_float2(phi_of<VARIANT>(x0), phi_of<VARIANT>(x1));
+    for (int d = 0; d < DMAX; ++d) f = __ffma2_rn(jc[d], rd[nb[d]], f);
+    sb_update2<NOISE>(f, make_float2(cm, cm), make_float2(e0, e1), dt, kappa, dta0, x, y);
+    wr[tid] = make_float2(phi_of<VARIANT>(x.x), phi_of<VARIANT>(x.y));
     __syncthreads();
 }
 
@@ -301,23 +302,15 @@ __host__ __device__ inline size_t sb_smem_bytes2(int Rb, int W, int pump_table_s
            align_up(sizeof(unsigned long long) * (size_t)Rb * W, 16) + sizeof(float) * (size_t)pump_table_steps;
 }
 
-template <int VARIANT, int DMAX, bool NOISE, int PUMP>
-__global__ void __launch_bounds__(1024) k_sb_sparse2(const SbArgs a)
+// Set-up of the replica pair (r0, r0 + 1) on spin i, shared by the FP32 and FP16 pair
+// kernels: both rows of -c0 J(c) in FP32 (c0 reduced over the block's replicas in red[]:
+// 4 * Rp words), the neighbours' phi indices and the start state. Contains two block barriers.
+template <int DMAX>
+__device__ __forceinline__ void pair_setup(const SbArgs& a, int tid, int i, int lp, int Rp, int r0, unsigned* red,
+                                           float (&jc0)[DMAX], float (&jc1)[DMAX], int (&nb)[DMAX], float& x0, float& y0,
+                                           float& x1, float& y1)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int n = a.n, Rb = a.Rb, Rp = a.Rb >> 1;
-    float2* phiA = reinterpret_cast<float2*>(smem_raw);
-    float2* phiB = phiA + kPhiStride;
-    unsigned* red = reinterpret_cast<unsigned*>(phiB + kPhiStride);  // 2 * Rb
-    unsigned long long* wb = reinterpret_cast<unsigned long long*>(smem_raw + sizeof(float) * 4 * kPhiStride +
-                                                                   align_up(sizeof(unsigned) * 2 * Rb, 16));
-    float* pump_t = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(wb) +
-                                             align_up(sizeof(unsigned long long) * (size_t)Rb * a.W, 16));
-    const int tid = threadIdx.x;
-    const int slot = tid / Rp;
-    const int lp = tid - slot * Rp;
-    const int i = a.slot_spin[slot];
-    const int r0 = blockIdx.x * Rb + 2 * lp, r1 = r0 + 1;
+    const int n = a.n, Rb = 2 * Rp, r1 = r0 + 1;
     const bool act0 = r0 < a.R, act1 = r1 < a.R;
     const int rs0 = act0 ? r0 : 0, rs1 = act1 ? r1 : 0;
     float lam0[kMaxK], lam1[kMaxK];
@@ -328,8 +321,6 @@ __global__ void __launch_bounds__(1024) k_sb_sparse2(const SbArgs a)
     }
     const int p0 = a.rowptr[i];
     const int deg = a.rowptr[i + 1] - p0;
-    float jc0[DMAX], jc1[DMAX];
-    int nb[DMAX];
     float sabs0 = 0.0f, sabs1 = 0.0f;
 #pragma unroll
     for (int d = 0; d < DMAX; ++d) {
@@ -378,7 +369,6 @@ __global__ void __launch_bounds__(1024) k_sb_sparse2(const SbArgs a)
             jc1[d] *= -c01;
         }
     }
-    float x0, y0, x1, y1;
     if (a.x_init) {
         x0 = (act0 ? a.x_init[(int64_t)r0 * n + i] : 0.0f) + 0.0f;
         y0 = (act0 && a.y_init) ? a.y_init[(int64_t)r0 * n + i] : 0.0f;
@@ -392,9 +382,39 @@ __global__ void __launch_bounds__(1024) k_sb_sparse2(const SbArgs a)
         x1 = __fmul_rn(a.init_amp, signed_unit(o1.x)) + 0.0f;
         y1 = __fmul_rn(a.init_amp, signed_unit(o1.y));
     }
+}
+
+template <int VARIANT, int DMAX, bool NOISE, int PUMP>
+__global__ void __launch_bounds__(1024) k_sb_sparse2(const SbArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = a.n, Rb = a.Rb, Rp = a.Rb >> 1;
+    float2* phiA = reinterpret_cast<float2*>(smem_raw);
+    float2* phiB = phiA + kPhiStride;
+    unsigned* red = reinterpret_cast<unsigned*>(phiB + kPhiStride);  // 2 * Rb
+    unsigned long long* wb = reinterpret_cast<unsigned long long*>(smem_raw + sizeof(float) * 4 * kPhiStride +
+                                                                   align_up(sizeof(unsigned) * 2 * Rb, 16));
+    float* pump_t = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(wb) +
+                                             align_up(sizeof(unsigned long long) * (size_t)Rb * a.W, 16));
+    const int tid = threadIdx.x;
+    const int slot = tid / Rp;
+    const int lp = tid - slot * Rp;
+    const int i = a.slot_spin[slot];
+    const int r0 = blockIdx.x * Rb + 2 * lp, r1 = r0 + 1;
+    const bool act0 = r0 < a.R, act1 = r1 < a.R;
+    float jc0[DMAX], jc1[DMAX];
+    int nb[DMAX];
+    float x0, y0, x1, y1;
+    pair_setup<DMAX>(a, tid, i, lp, Rp, r0, red, jc0, jc1, nb, x0, y0, x1, y1);
+    float2 jc[DMAX];
+#pragma unroll
+    for (int d = 0; d < DMAX; ++d) jc[d] = make_float2(jc0[d], jc1[d]);
     phiA[tid] = make_float2(phi_of<VARIANT>(x0), phi_of<VARIANT>(x1));
     __syncthreads();
-    const float dt = a.dt, kappa = a.kappa, dta0 = a.dt * a.a0, a0 = a.a0, a0inv = a.a0inv;
+    float2 xs = make_float2(x0, x1), ys = make_float2(y0, y1);
+    const float2 dt2 = make_float2(a.dt, a.dt), kappa2 = make_float2(a.kappa, a.kappa);
+    const float2 dta02 = make_float2(a.dt * a.a0, a.dt * a.a0);
+    const float a0 = a.a0, a0inv = a.a0inv;
     const float* sched = a.schedule;
     const int T = a.T;
     if (PUMP == kPumpTable) {
@@ -415,7 +435,7 @@ __global__ void __launch_bounds__(1024) k_sb_sparse2(const SbArgs a)
         }
     };
     auto step = [&](const float2* rd, float2* wr, float cm, float e0, float e1) {
-        sb_step2<VARIANT, DMAX, NOISE>(rd, wr, tid, jc0, jc1, nb, cm, e0, e1, dt, kappa, dta0, x0, y0, x1, y1);
+        sb_step2<VARIANT, DMAX, NOISE>(rd, wr, tid, jc, nb, cm, e0, e1, dt2, kappa2, dta02, xs, ys);
     };
     auto four_steps = [&](int m, float mf, const float (&e)[4], const float (&g)[4]) {
         step(phiA, phiB, cm_at(m, mf), e[0], g[0]);
@@ -458,6 +478,10 @@ __global__ void __launch_bounds__(1024) k_sb_sparse2(const SbArgs a)
         if (m + 1 < T) step(phiB, phiA, cm_at(m + 1, mf + 1.0f), e[1], g[1]);
         if (m + 2 < T) step(phiA, phiB, cm_at(m + 2, mf + 2.0f), e[2], g[2]);
     }
+    x0 = xs.x;
+    x1 = xs.y;
+    y0 = ys.x;
+    y1 = ys.y;
     const int W = a.W;
     for (int t = tid; t < Rb * W; t += blockDim.x) wb[t] = 0ull;
     __syncthreads();
@@ -495,6 +519,193 @@ cudaError_t launch_pump2(const SbArgs& a, int pump, dim3 grid, dim3 block, size_
     case kPumpTable: return launch_one2<VARIANT, DMAX, NOISE, kPumpTable>(a, grid, block, smem, st);
     case kPumpInline: return launch_one2<VARIANT, DMAX, NOISE, kPumpInline>(a, grid, block, smem, st);
     default: return launch_one2<VARIANT, DMAX, NOISE, kPumpSchedule>(a, grid, block, smem, st);
+    }
+}
+
+// ---- float16 state: the paper's precision ---------------------------------------------
+// The paper runs SB in float16. This form keeps the state and does the step's arithmetic in
+// FP16: each thread runs spin i of two replicas with x, y, its two rows of -c0 J(c) and phi
+// as packed half2 (lane 0: replica r0, lane 1: r0 + 1), the force sum and the Euler update
+// as two-lane FP16 multiply-adds (one rounding each), the wall and dSB's sign on the bit
+// patterns. c0 and the couplings are formed in FP32 (as the FP32 form does) and rounded once
+// to FP16, the start state is the FP32 form's rounded to FP16, and eta is the FP32 form's
+// Gaussian (same Philox counters) rounded to FP16; the pump value a_m - a0 is rounded to FP16.
+// phi takes 4 bytes per pair of replicas in shared memory (half the FP32 pair form's).
+__device__ __forceinline__ uint32_t h2_bits(__half2 v) { return *reinterpret_cast<uint32_t*>(&v); }
+__device__ __forceinline__ __half2 bits_h2(uint32_t u) { return *reinterpret_cast<__half2*>(&u); }
+
+__host__ __device__ inline size_t sb_smem_bytes_h(int Rb, int W, int pump_table_steps)
+{
+    return sizeof(__half2) * 2 * kPhiStride + align_up(sizeof(unsigned) * 2 * Rb, 16) +
+           align_up(sizeof(unsigned long long) * (size_t)Rb * W, 16) + sizeof(__half2) * (size_t)pump_table_steps;
+}
+
+template <int VARIANT, int DMAX, bool NOISE>
+__device__ __forceinline__ void sb_step_h(const __half2* rd, __half2* wr, int tid, const __half2 (&jc)[DMAX], const int (&nb)[DMAX],
+                                          __half2 cm, __half2 eta, __half2 dt, __half2 kappa, __half2 dta0, __half2& x, __half2& y)
+{
+    __half2 f = __float2half2_rn(0.0f);
+#pragma unroll
+    for (int d = 0; d < DMAX; ++d) f = __hfma2(jc[d], rd[nb[d]], f);
+    y = __hfma2(dt, __hfma2(cm, x, f), y);
+    if (NOISE) y = __hfma2(kappa, eta, y);
+    x = __hfma2(dta0, y, x);
+    // wall: lanes with |x| > 1 take x = sgn(x) (the dSB phi of x) and y = 0
+    const uint32_t xb = h2_bits(x);
+    const uint32_t sg = (xb & 0x80008000u) | 0x3C003C00u;
+    const uint32_t over = __hgt2_mask(__habs2(x), __float2half2_rn(1.0f));
+    x = bits_h2((over & sg) | (~over & xb));
+    y = bits_h2(~over & h2_bits(y));
+    wr[tid] = VARIANT == MOQ_DSB ? bits_h2(sg) : x;
+    __syncthreads();
+}
+
+template <int VARIANT, int DMAX, bool NOISE, int PUMP>
+__global__ void __launch_bounds__(1024) k_sb_sparse_h(const SbArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = a.n, Rb = a.Rb, Rp = a.Rb >> 1;
+    __half2* phiA = reinterpret_cast<__half2*>(smem_raw);
+    __half2* phiB = phiA + kPhiStride;
+    unsigned* red = reinterpret_cast<unsigned*>(phiB + kPhiStride);  // 2 * Rb
+    unsigned long long* wb = reinterpret_cast<unsigned long long*>(smem_raw + sizeof(__half2) * 2 * kPhiStride +
+                                                                   align_up(sizeof(unsigned) * 2 * Rb, 16));
+    __half2* pump_t = reinterpret_cast<__half2*>(reinterpret_cast<unsigned char*>(wb) +
+                                                 align_up(sizeof(unsigned long long) * (size_t)Rb * a.W, 16));
+    const int tid = threadIdx.x;
+    const int slot = tid / Rp;
+    const int lp = tid - slot * Rp;
+    const int i = a.slot_spin[slot];
+    const int r0 = blockIdx.x * Rb + 2 * lp, r1 = r0 + 1;
+    const bool act0 = r0 < a.R, act1 = r1 < a.R;
+    float jc0[DMAX], jc1[DMAX];
+    int nb[DMAX];
+    float x0, y0, x1, y1;
+    pair_setup<DMAX>(a, tid, i, lp, Rp, r0, red, jc0, jc1, nb, x0, y0, x1, y1);
+    __half2 jc[DMAX];
+#pragma unroll
+    for (int d = 0; d < DMAX; ++d) jc[d] = __floats2half2_rn(jc0[d], jc1[d]);
+    __half2 xs = __floats2half2_rn(x0, x1), ys = __floats2half2_rn(y0, y1);
+    phiA[tid] = VARIANT == MOQ_DSB ? bits_h2((h2_bits(xs) & 0x80008000u) | 0x3C003C00u) : xs;
+    __syncthreads();
+    const __half2 dt2 = __float2half2_rn(a.dt), kappa2 = __float2half2_rn(a.kappa), dta02 = __float2half2_rn(a.dt * a.a0);
+    const float a0 = a.a0, a0inv = a.a0inv;
+    const float* sched = a.schedule;
+    const int T = a.T;
+    if (PUMP == kPumpTable) {
+        for (int q = tid; q < T; q += blockDim.x) pump_t[q] = __float2half2_rn(fmaf(a0inv, (float)q, -a0));
+        __syncthreads();
+    }
+    auto cm_at = [&](int m, float mf) -> __half2 {
+        if (PUMP == kPumpTable) return pump_t[m];
+        return __float2half2_rn(PUMP == kPumpInline ? fmaf(a0inv, mf, -a0) : (__ldg(sched + m) - a0));
+    };
+    auto block8 = [&](int m, int r) -> uint4 {
+        return NOISE ? Philox4x32::block(make_uint4((uint32_t)(m >> 3), (uint32_t)i, a.rep_off + (uint32_t)r, a.round32), a.key0, a.key1)
+                     : make_uint4(0u, 0u, 0u, 0u);
+    };
+    // the Gaussians of four steps of both replicas, rounded to FP16 (lane 0: r0, lane 1: r1)
+    auto noise4 = [&](uint32_t wa, uint32_t wbb, uint32_t va, uint32_t vb, __half2 (&eg)[4]) {
+        if (NOISE) {
+            const float2 p = box_muller16(wa), q = box_muller16(wbb), u = box_muller16(va), v = box_muller16(vb);
+            eg[0] = __floats2half2_rn(p.x, u.x);
+            eg[1] = __floats2half2_rn(p.y, u.y);
+            eg[2] = __floats2half2_rn(q.x, v.x);
+            eg[3] = __floats2half2_rn(q.y, v.y);
+        }
+    };
+    auto step = [&](const __half2* rd, __half2* wr, __half2 cm, __half2 eta) {
+        sb_step_h<VARIANT, DMAX, NOISE>(rd, wr, tid, jc, nb, cm, eta, dt2, kappa2, dta02, xs, ys);
+    };
+    auto four_steps = [&](int m, float mf, const __half2 (&eg)[4]) {
+        step(phiA, phiB, cm_at(m, mf), eg[0]);
+        step(phiB, phiA, cm_at(m + 1, mf + 1.0f), eg[1]);
+        step(phiA, phiB, cm_at(m + 2, mf + 2.0f), eg[2]);
+        step(phiB, phiA, cm_at(m + 3, mf + 3.0f), eg[3]);
+    };
+    auto noise_at = [&](int m, __half2 (&eg)[4]) {
+        if (NOISE) {
+            const uint4 o = block8(m, r0), q = block8(m, r1);
+            noise4((m & 4) ? o.z : o.x, (m & 4) ? o.w : o.y, (m & 4) ? q.z : q.x, (m & 4) ? q.w : q.y, eg);
+        }
+    };
+    const __half2 zero2 = __float2half2_rn(0.0f);
+    int m = 0;
+    float mf = 0.0f;
+    if (NOISE) {
+        for (; m + 8 <= T; m += 8) {
+            const uint4 o = block8(m, r0), q = block8(m, r1);
+            __half2 eg[4];
+            noise4(o.x, o.y, q.x, q.y, eg);
+            four_steps(m, mf, eg);
+            noise4(o.z, o.w, q.z, q.w, eg);
+            four_steps(m + 4, mf + 4.0f, eg);
+            mf += 8.0f;
+        }
+    }
+    for (; m + 4 <= T; m += 4) {
+        __half2 eg[4] = {zero2, zero2, zero2, zero2};
+        noise_at(m, eg);
+        four_steps(m, mf, eg);
+        mf += 4.0f;
+    }
+    if (m < T) {
+        __half2 eg[4] = {zero2, zero2, zero2, zero2};
+        noise_at(m, eg);
+        step(phiA, phiB, cm_at(m, mf), eg[0]);
+        if (m + 1 < T) step(phiB, phiA, cm_at(m + 1, mf + 1.0f), eg[1]);
+        if (m + 2 < T) step(phiA, phiB, cm_at(m + 2, mf + 2.0f), eg[2]);
+    }
+    const float2 xf = __half22float2(xs), yf = __half22float2(ys);
+    const int W = a.W;
+    for (int t = tid; t < Rb * W; t += blockDim.x) wb[t] = 0ull;
+    __syncthreads();
+    if (xf.x < 0.0f) atomicOr(&wb[(2 * lp) * W + (i >> 6)], 1ull << (i & 63));
+    if (xf.y < 0.0f) atomicOr(&wb[(2 * lp + 1) * W + (i >> 6)], 1ull << (i & 63));
+    __syncthreads();
+    for (int t = tid; t < Rb * W; t += blockDim.x) {
+        const int r2 = blockIdx.x * Rb + t / W;
+        if (r2 < a.R) a.bits[(int64_t)r2 * W + (t % W)] = wb[t];
+    }
+    if (act0) {
+        if (a.x_out) a.x_out[(int64_t)r0 * n + i] = xf.x;
+        if (a.y_out) a.y_out[(int64_t)r0 * n + i] = yf.x;
+    }
+    if (act1) {
+        if (a.x_out) a.x_out[(int64_t)r1 * n + i] = xf.y;
+        if (a.y_out) a.y_out[(int64_t)r1 * n + i] = yf.y;
+    }
+}
+
+template <int VARIANT, int DMAX, bool NOISE, int PUMP>
+cudaError_t launch_one_h(const SbArgs& a, dim3 grid, dim3 block, size_t smem, cudaStream_t st)
+{
+    auto k = k_sb_sparse_h<VARIANT, DMAX, NOISE, PUMP>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, block, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int VARIANT, int DMAX, bool NOISE>
+cudaError_t launch_pump_h(const SbArgs& a, int pump, dim3 grid, dim3 block, size_t smem, cudaStream_t st)
+{
+    switch (pump) {
+    case kPumpTable: return launch_one_h<VARIANT, DMAX, NOISE, kPumpTable>(a, grid, block, smem, st);
+    case kPumpInline: return launch_one_h<VARIANT, DMAX, NOISE, kPumpInline>(a, grid, block, smem, st);
+    default: return launch_one_h<VARIANT, DMAX, NOISE, kPumpSchedule>(a, grid, block, smem, st);
+    }
+}
+
+// the FP16 form for degree bounds 3, 4 and 8 (two rows of half2 couplings fit in registers)
+template <int VARIANT>
+cudaError_t launch_variant_h(const SbArgs& a, int dmax, bool noise, int pump, dim3 grid, dim3 block, size_t smem, cudaStream_t st)
+{
+    switch (dmax) {
+    case 3: return noise ? launch_pump_h<VARIANT, 3, true>(a, pump, grid, block, smem, st) : launch_pump_h<VARIANT, 3, false>(a, pump, grid, block, smem, st);
+    case 4: return noise ? launch_pump_h<VARIANT, 4, true>(a, pump, grid, block, smem, st) : launch_pump_h<VARIANT, 4, false>(a, pump, grid, block, smem, st);
+    case 8: return noise ? launch_pump_h<VARIANT, 8, true>(a, pump, grid, block, smem, st) : launch_pump_h<VARIANT, 8, false>(a, pump, grid, block, smem, st);
+    default: return cudaErrorInvalidValue;
     }
 }
 
@@ -581,6 +792,10 @@ extern "C" int moq_sample(const moq_instance* inst, const float* lambda, int32_t
     if (!lambda || !bits) return fail(MOQ_ERR_ARG, "moq_sample: NULL lambda or bits");
     if (inst->n > 1024) return fail(MOQ_ERR_UNSUPPORTED, "moq_sample: n=%d > 1024 is not supported by the on-chip sampler", inst->n);
     if (inst->max_degree > 16) return fail(MOQ_ERR_UNSUPPORTED, "moq_sample: max degree %d > 16", inst->max_degree);
+    if (p->precision != MOQ_PREC_FP32 && p->precision != MOQ_PREC_FP16)
+        return fail(MOQ_ERR_ARG, "moq_sample: unknown precision %d", p->precision);
+    if (p->precision == MOQ_PREC_FP16 && inst->max_degree > 8)
+        return fail(MOQ_ERR_UNSUPPORTED, "moq_sample: the FP16 form runs degree bounds up to 8 (max degree %d)", inst->max_degree);
 
     SbArgs a{};
     a.n = inst->n;
@@ -614,6 +829,19 @@ extern "C" int moq_sample(const moq_instance* inst, const float* lambda, int32_t
     const int md = inst->max_degree;
     const int dmax = md <= 3 ? 3 : (md <= 4 ? 4 : (md <= 8 ? 8 : 16));
     const bool noise = p->alpha != 0.0f;
+    if (p->precision == MOQ_PREC_FP16) {
+        // pairs of replicas per thread, replicas per block as for the FP32 pair form
+        const int Rp = choose_rb(a.n, (R + 1) / 2);
+        a.Rb = 2 * Rp;
+        const int threads = a.n * Rp;
+        const int pump = p->schedule ? kPumpSchedule : (a.T <= kPumpTableMax && threads <= kPumpTableMaxThreads ? kPumpTable : kPumpInline);
+        const size_t smem = sb_smem_bytes_h(a.Rb, a.W, pump == kPumpTable ? a.T : 0);
+        const dim3 block(threads), grid((unsigned)ceil_div(R, a.Rb));
+        const cudaError_t e = (p->variant == MOQ_DSB) ? launch_variant_h<MOQ_DSB>(a, dmax, noise, pump, grid, block, smem, as_stream(stream))
+                                                      : launch_variant_h<MOQ_BSB>(a, dmax, noise, pump, grid, block, smem, as_stream(stream));
+        if (e != cudaSuccess) return cuda_fail(e, "moq_sample launch (FP16)");
+        return MOQ_OK;
+    }
     // Block shape of either form: replicas per block, threads, pump source, shared memory.
     // The table trades a multiply-add for a shared-memory load: a gain for small blocks, a
     // loss for blocks of more than 256 threads, whose gathers already keep the shared-memory

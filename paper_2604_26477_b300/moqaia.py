@@ -26,6 +26,8 @@ MOQ_ERR_OVERFLOW = -6
 MOQ_ERR_UNSUPPORTED = -7
 MOQ_DSB = 0
 MOQ_BSB = 1
+MOQ_PREC_FP32 = 0
+MOQ_PREC_FP16 = 1
 
 
 class MoqError(RuntimeError):
@@ -44,7 +46,7 @@ class moq_sample_params(C.Structure):
     _fields_ = [("variant", C.c_int32), ("steps", C.c_int32), ("dt", C.c_float), ("a0", C.c_float),
                 ("alpha", C.c_float), ("init_amp", C.c_float), ("noise_sqrt_dt", C.c_int32),
                 ("schedule", C.c_void_p), ("x_init", C.c_void_p), ("y_init", C.c_void_p),
-                ("x_out", C.c_void_p), ("y_out", C.c_void_p), ("replica_offset", C.c_uint32)]
+                ("x_out", C.c_void_p), ("y_out", C.c_void_p), ("replica_offset", C.c_uint32), ("precision", C.c_int32)]
 
 
 class moq_hv(C.Structure):
@@ -183,6 +185,8 @@ def moq_default_params(**overrides) -> moq_sample_params:
     for k, v in overrides.items():
         if k == "variant" and isinstance(v, str):
             v = {"dsb": MOQ_DSB, "bsb": MOQ_BSB}[v.lower()]
+        if k == "precision" and isinstance(v, str):
+            v = {"fp32": MOQ_PREC_FP32, "fp16": MOQ_PREC_FP16}[v.lower()]
         if k in ("schedule", "x_init", "y_init", "x_out", "y_out"):
             p._tensors[k] = v
             v = None if v is None else _dptr(v, k, _torch_types()[0])
