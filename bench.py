@@ -286,18 +286,21 @@ def gpu_arm(args, rank, world):
     units = R * n * T * args.steps * world
     value = units / dev_s
 
-    # e2e through the C ABI with host buffers: weight vectors copied in from pinned host
-    # memory every step, hypervolume and front size read back every step
+    # e2e through the C ABI with host buffers: each step's own weight vectors copied in from
+    # pinned host memory, and the step's result -- the hypervolume and the front itself (cut
+    # vectors, configurations, sample indices) -- read back to the host every step
     # (the same two-stage pipeline: the copy-in and sampling of step s + 1 overlap step s's tail)
-    lam_host = torch.from_numpy(wl.dirichlet_lambdas(R, K, 777 + rank)).pin_memory()
-    lam_devs = [torch.empty_like(lam_host, device=dev) for _ in range(2)]
-    torch.cuda.synchronize()
     e2e_steps = max(1, min(args.steps, 10))
+    lam_host = torch.from_numpy(np.stack([wl.dirichlet_lambdas(R * world, K, 777 + s)[first:first + R]
+                                          for s in range(e2e_steps)])).pin_memory()
+    lam_devs = [torch.empty_like(lam_host[0], device=dev) for _ in range(2)]
+    torch.cuda.synchronize()
     e2e_sampled = [None] * e2e_steps
+    d2h = []
 
     def launch_e2e(s):
         with torch.cuda.stream(s_a):
-            lam_devs[s % 2].copy_(lam_host, non_blocking=True)
+            lam_devs[s % 2].copy_(lam_host[s], non_blocking=True)
             M.moq_sample(inst.handle, lam_devs[s % 2], R, params, 99, s, bufs[s % 2].bits, s_a)
             e2e_sampled[s] = s_a.record_event()
 
@@ -312,10 +315,13 @@ def gpu_arm(args, rank, world):
         M.moq_evaluate_cuts(inst.handle, b.bits, R, b.cuts, s_b)
         arch.merge(b.cuts, b.bits, R, 0, stream=s_b)
         arch.hypervolume(inst.ref, s_b)
+        fc, fb, fi = arch.copy_out(s_b)  # the front on the host
+        d2h.append(16 + 4 + 8 + fc.nbytes + fb.nbytes + fi.nbytes)  # HV + status, size, front
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e = {"value": R * n * T * e2e_steps / e2e_s * world, "unit": METRIC,
-           "h2d_bytes_per_step": R * K * 4, "d2h_bytes_per_step": 8 + 4 + 8 + 4 + 16 + 4}
+           "h2d_bytes_per_step": R * K * 4, "d2h_bytes_per_step": int(np.mean(d2h)),
+           "steps": e2e_steps, "result_read_back": "hypervolume and the whole front (cuts, configurations, indices)"}
 
     # the configuration's second variant: NI-bSB (phi = x) on the same instance, weight
     # vectors and step structure, timed the same way (L2 flushed before every step)
@@ -998,6 +1004,244 @@ def learned_ttt_block(args):
     return out
 
 
+def _timed_steps(step, warmup, steps, flush):
+    """Runs `step(s, events)` warmup + steps times (L2 flushed before each); returns the timed
+    steps' (whole-step seconds, sampler seconds) sums from CUDA events on the current stream."""
+    import torch
+
+    mk = lambda: [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for s in range(warmup):
+        flush.zero_()
+        step(s, mk())
+    torch.cuda.synchronize()
+    ev = [mk() for _ in range(steps)]
+    for s in range(steps):
+        flush.zero_()
+        step(warmup + s, ev[s])
+    torch.cuda.synchronize()
+    return sum(e[0].elapsed_time(e[2]) for e in ev) / 1e3, sum(e[0].elapsed_time(e[1]) for e in ev) / 1e3
+
+
+def plain_config_block(args):
+    """The plain configuration (n=42 heavy-hex-like, E=50, K=3, weights {-10..10}\\{0}, seed
+    1000; 1024 uniform-simplex replicas; FP32 dSB T=1000, dt=0.5) at the paper's alpha for K=3
+    (0.15) and at alpha=0; one step = sampling + exact cuts + Pareto merge into a fresh
+    archive + hypervolume read back, L2 flushed before every step, CUDA events."""
+    import torch
+
+    from paper_2604_26477_b300 import moqaia as M
+    from paper_2604_26477_b300 import pipeline as P
+    from paper_2604_26477_b300 import workloads as wl
+
+    src = wl.heavy_hex_like(1000, K=3)
+    R, T = 1024, 1000
+    inst = P.Instance(src)
+    arch = P.Archive(src.n, src.K, capacity=1 << 16, max_batch=R)
+    buf = P.RoundBuffers(R, src.n, src.K)
+    nst = args.warmup + args.steps
+    lam_all = torch.from_numpy(np.stack([wl.dirichlet_lambdas(R, 3, 500 + s) for s in range(nst)])).cuda()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = {"workload": "plain: heavy-hex-like n=42 E=50 K=3 weights {-10..10}\\{0}, R=1024 uniform-simplex lambda, "
+                       "FP32 dSB T=1000 dt=0.5; step = sampling + cuts + Pareto + hypervolume (read back)",
+           "steps": args.steps, "warmup": args.warmup, "l2": "flushed (256 MB write) before every step"}
+    hv = [0]
+    for alpha in (0.15, 0.0):
+        params = M.moq_default_params(variant="dsb", steps=T, dt=0.5, alpha=alpha)
+
+        def step(s, evs):
+            arch.reset()
+            evs[0].record(stream)
+            M.moq_sample(inst.handle, lam_all[s], R, params, 3, s, buf.bits)
+            evs[1].record(stream)
+            M.moq_evaluate_cuts(inst.handle, buf.bits, R, buf.cuts)
+            arch.merge(buf.cuts, buf.bits, R, 0)
+            hv[0] = arch.hypervolume(inst.ref)
+            evs[2].record(stream)
+
+        step_s, samp_s = _timed_steps(step, args.warmup, args.steps, flush)
+        units = R * src.n * T * args.steps
+        ops = ops_per_spin_update(2.0 * src.E / src.n) - (0 if alpha else 17)  # no Philox / Box-Muller without noise
+        out[f"alpha_{alpha}"] = {"value": units / step_s, "unit": METRIC, "ms_per_step": step_s / args.steps * 1e3,
+                                 "sampling_only_value": units / samp_s, "sampler_ms": samp_s / args.steps * 1e3,
+                                 "roofline": {"bound": "alu", "kernel": "k_sb_sparse / k_sb_sparse2 (host's choice)",
+                                              "achieved": ops * units / samp_s / 1e12, "peak": peak_alu_tops(),
+                                              "unit": "Tops/s", "frac": ops * units / samp_s / 1e12 / peak_alu_tops(),
+                                              "ops_per_spin_update": ops,
+                                              "note": "1024 replicas fill 171 blocks (of 1184 resident slots): "
+                                                      "latency-bound by design, hence the low fraction"},
+                                 "front_points": arch.size(), "hv": int(hv[0])}
+    arch.close()
+    inst.close()
+    return out
+
+
+def fp16_block(args):
+    """The paper's float16 form (p->precision = MOQ_PREC_FP16) on the benchmark workload
+    (precision: n=42, K=4, R=16384, NI-dSB T=2000, alpha=0.1) beside the FP32 form, timed the
+    same way in one process: sampler launches alone and whole steps (sampling + cuts + Pareto
+    + hypervolume), L2 flushed before every step, CUDA events."""
+    import torch
+
+    from paper_2604_26477_b300 import moqaia as M
+    from paper_2604_26477_b300 import pipeline as P
+    from paper_2604_26477_b300 import workloads as wl
+
+    w = WORKLOAD
+    src = wl.heavy_hex_like(w["instance_seed"], K=w["K"], wmax=w["wmax"])
+    R, T = w["R"], w["T"]
+    inst = P.Instance(src)
+    arch = P.Archive(src.n, src.K, capacity=1 << 18, max_batch=R)
+    buf = P.RoundBuffers(R, src.n, src.K)
+    nst = args.warmup + max(1, min(args.steps, 10))
+    lam_all = torch.from_numpy(np.stack([wl.dirichlet_lambdas(R, w["K"], 10_000 + s) for s in range(nst)])).cuda()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = {"workload": "precision (n=42, K=4, R=16384, NI-dSB T=2000 dt=0.5 alpha=0.1), both forms in one process",
+           "steps": nst - args.warmup}
+    hv = [0]
+    for prec in ("fp32", "fp16"):
+        params = M.moq_default_params(variant="dsb", steps=T, dt=w["dt"], a0=w["a0"], alpha=w["alpha"], precision=prec)
+
+        def step(s, evs):
+            arch.reset()
+            evs[0].record(stream)
+            M.moq_sample(inst.handle, lam_all[s], R, params, 1, s, buf.bits)
+            evs[1].record(stream)
+            M.moq_evaluate_cuts(inst.handle, buf.bits, R, buf.cuts)
+            arch.merge(buf.cuts, buf.bits, R, 0)
+            hv[0] = arch.hypervolume(inst.ref)
+            evs[2].record(stream)
+
+        step_s, samp_s = _timed_steps(step, args.warmup, nst - args.warmup, flush)
+        units = R * src.n * T * (nst - args.warmup)
+        out[prec] = {"value": units / step_s, "ms_per_step": step_s / (nst - args.warmup) * 1e3,
+                     "sampling_only_value": units / samp_s, "sampler_ms": samp_s / (nst - args.warmup) * 1e3,
+                     "front_points": arch.size(), "hv": int(hv[0])}
+    out["sampler_speedup"] = out["fp32"]["sampler_ms"] / out["fp16"]["sampler_ms"]
+    arch.close()
+    inst.close()
+    return out
+
+
+def chosen_batch_block(args):
+    """The chosen form on a clock the plain sampler needs many rounds for (time to a fraction
+    of the plain sampler's final hypervolume, "Sampling time advantage" / "Sample quality and
+    end-to-end solution time"): 16 held-out random 3-regular instances (n ~ U[42,1024] even,
+    K=3, weights {-100..100}\\{0}, seed 2026), 1024 replicas per instance and round. Per
+    instance, the target is 99% (99.9%) of the hypervolume the plain sampler (FP32 dSB,
+    uniform lambda, T=1000, dt=0.5, alpha=0) reaches after 64 rounds, lower median over 8
+    seeds; the job is done when every instance is at its target. Arms: plain (one round per
+    instance in turn), and batched rounds over the instances still short of their target of
+    the paper's float16 NI-dSB (T=2000, alpha=0.1) with and without the batch surrogate,
+    and plain dynamics batched in FP32. End to end (instance builds, rounds, one hypervolume
+    check per active instance and round); median, p10/p90 over the seeds."""
+    import torch
+
+    from paper_2604_26477_b300 import moqaia as M
+    from paper_2604_26477_b300 import pipeline as P
+    from paper_2604_26477_b300 import workloads as wl
+
+    R = 1024
+    srcs = wl.uneven_regular_batch(16, 2026)
+    plain = M.moq_default_params(variant="dsb", steps=1000, dt=0.5, alpha=0.0)
+    chosen = M.moq_default_params(variant="dsb", steps=2000, dt=0.5, alpha=0.1, precision="fp16")
+    finals = []
+    for src in srcs:
+        inst = P.Instance(src)
+        arch = P.Archive(src.n, src.K, capacity=1 << 18, max_batch=R)
+        buf = P.RoundBuffers(R, src.n, src.K)
+        hv = []
+        for seed in range(8):
+            arch.reset()
+            for rnd in range(64):
+                P.sample_round(inst, arch, buf, plain, seed=4242 + seed, round_=rnd)
+            hv.append(int(arch.hypervolume(inst.ref)))
+        finals.append(sorted(hv)[3])  # lower median of 8
+        arch.close()
+        inst.close()
+    arms = [("plain_fp32_T1000_alpha0_per_instance", plain, False, False, (0.99, 0.999)),
+            ("chosen_fp16_T2000_alpha0.1_batched_learned", chosen, True, True, (0.99, 0.999)),
+            ("fp16_T2000_alpha0.1_batched_uniform", chosen, True, False, (0.99, 0.999)),
+            ("fp32_T1000_alpha0_batched_uniform", plain, True, False, (0.99,))]
+    out = {"instances": "16 random 3-regular, n~U[42,1024] even, K=3, weights {-100..100}\\{0} (held out, seed 2026)",
+           "n": [s.n for s in srcs], "replicas_per_round": R, "plain_final_hv": [int(f) for f in finals],
+           "plain_final": "plain sampler after 64 rounds, lower median of 8 seeds", "seeds": args.ttt_seeds,
+           "clock": "instance builds + rounds (weights, sampling, cuts, Pareto merges, surrogate) + one HV check per "
+                    "active instance and round; done when every instance is at its target"}
+    for frac in (0.99, 0.999):
+        targets = [int(-(-f * round(frac * 1000) // 1000)) for f in finals]
+        block = {}
+        for label, params, batched, learned, fracs in arms:
+            if frac not in fracs:
+                continue
+            P.time_to_target_batch(srcs[:2], targets[:2], params, R, seed=99, max_rounds=2, batched=batched, learned=learned)
+            runs = [P.time_to_target_batch(srcs, targets, params, R, seed=s, max_rounds=256, batched=batched, learned=learned)
+                    for s in range(args.ttt_seeds)]
+            secs = [r["seconds"] for r in runs]
+            block[label] = {"seconds_median": float(np.median(secs)),
+                            "seconds_p10_p90": [float(np.percentile(secs, 10)), float(np.percentile(secs, 90))],
+                            "rounds_median": float(np.median([r["rounds"] for r in runs])),
+                            "rounds_p10_p90": [float(np.percentile([r["rounds"] for r in runs], 10)),
+                                               float(np.percentile([r["rounds"] for r in runs], 90))],
+                            "samples_median": int(np.median([r["samples"] for r in runs])),
+                            "reached": sum(r["reached"] for r in runs), "of": len(runs)}
+        base = block["plain_fp32_T1000_alpha0_per_instance"]["seconds_median"]
+        block["chosen_speedup_vs_plain"] = base / block["chosen_fp16_T2000_alpha0.1_batched_learned"]["seconds_median"]
+        out[f"{frac * 100:g}%"] = block
+    # sampling throughput of one batched FP16 round of every instance against the FP32 round
+    insts = [P.Instance(s) for s in srcs]
+    batch = P.Batch(insts, [R] * len(insts))
+    batch.set_tiles(0, 0)
+    M.moq_lambda_dirichlet(3, batch.total_R, 1, 0, batch.lam)
+    units = float(sum(s.n for s in srcs)) * R
+    thr = {}
+    for label, params in (("fp16_T2000_alpha0.1", chosen), ("fp32_T2000_alpha0.1",
+                          M.moq_default_params(variant="dsb", steps=2000, dt=0.5, alpha=0.1))):
+        batch.sample(params, 1, 0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(3):
+            batch.sample(params, 1, 1 + k)
+        e1.record()
+        torch.cuda.synchronize()
+        thr[label] = {"ms_per_round": e0.elapsed_time(e1) / 3, "value": units * 2000 * 3 / (e0.elapsed_time(e1) / 1e3),
+                      "unit": METRIC}
+    out["batched_round_sampling"] = thr
+    batch.close()
+    for h in insts:
+        h.close()
+    torch.cuda.synchronize()
+    return out
+
+
+def growth_blocks(args):
+    """Compact runs of the batching and dense configurations for the default line (their own
+    --workload lines carry the full protocol): batching 2 timed steps after 1 warm-up, dense 1
+    after 1 with shorter comparison legs."""
+    import copy
+
+    a = copy.copy(args)
+    a.steps, a.warmup = 2, 1
+    b = batching_arm(a, 0, 1)
+    d_args = copy.copy(args)
+    d_args.steps, d_args.warmup = 1, 1
+    d_args.dense_fp32_steps, d_args.dense_fp8_steps, d_args.dense_hv_rounds = 50, 100, 2
+    d = dense_arm(d_args, 0, 1)
+    keep = ("value", "unit", "ms_per_step", "steps", "warmup", "roofline", "clocks", "sampling_only_value", "sampler_ms",
+            "plain_fp32", "operand_forms", "forms_hv", "front_points_mean", "front_points_last_step")
+    out = {}
+    for name, line in (("batching", b), ("dense", d)):
+        blk = {k: line[k] for k in keep if k in line}
+        blk["workload"] = line["config"]["workload"]
+        if "tile" in line["config"]:
+            blk["tile"] = line["config"]["tile"]
+            blk["tile_timings_ms"] = line["config"]["tile_timings_ms"]
+        out[name] = blk
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1010,6 +1254,8 @@ def main():
     ap.add_argument("--ttt-rounds", type=int, default=64)
     ap.add_argument("--ttt-seeds", type=int, default=32, help="seeds of the time-to-target medians")
     ap.add_argument("--no-ttt", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the plain-config, float16, chosen-form-batch, batching and dense blocks of the default line")
     ap.add_argument("--cpu-baseline-worker", action="store_true")
     ap.add_argument("--workload", default="precision", choices=["precision", "batching", "dense", "paper", "appendix_e"],
                     help="precision (the default line), the batching or dense configuration, or the paper's protocol")
@@ -1082,10 +1328,15 @@ def main():
         return
 
     res = gpu_arm(args, rank, world)
-    ttt = None
+    ttt = extra = None
     if rank == 0 and not args.no_ttt:
         ttt = time_to_target_block(args, res["src"])
         ttt["learned_held_out"] = learned_ttt_block(args)
+    if rank == 0 and not args.no_extra:
+        extra = {"plain_config": plain_config_block(args), "fp16_paper_precision": fp16_block(args)}
+        if not args.no_ttt:
+            extra["chosen_form_batch_time_to_target"] = chosen_batch_block(args)
+        extra.update(growth_blocks(args))
     if rank == 0:
         line = {"metric": METRIC, "value": res["value"], "unit": METRIC, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
@@ -1094,6 +1345,8 @@ def main():
                 "gpu_launches": res["gpu_launches"], "sampling_only_value": res["sampling_only_value"],
                 "front_points_last_step": res["front_last"], "hv_last_step": res["hv_last"],
                 "bsb": res["bsb"], "time_to_99pct_hv": ttt}
+        if extra:
+            line.update(extra)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -169,7 +169,14 @@ int moq_batch_layout(const moq_batch* b, int64_t* replica_offsets, int64_t* word
  * created by the first such call) that fork from and join back into the caller's stream;
  * the samples are the same bits either way. Synchronous. */
 int moq_batch_set_tiles(moq_batch* b, int32_t block_threads, int32_t slots_per_thread, int32_t* items_out);
-/* Samples every replica of every instance (asynchronous; p's state arrays must be NULL). */
+/* Active replicas per instance (host array of count entries): instance b then samples, and
+ * moq_evaluate_cuts_batch evaluates, its first replicas[b] replicas only (0 skips it), with
+ * the layout and the noise counters of the batch unchanged, so a driver can drop the
+ * instances that have reached their target. 0 <= replicas[b] <= the count given at
+ * creation, else MOQ_ERR_ARG. Synchronous (the persistent kernel's work list is rebuilt). */
+int moq_batch_set_replicas(moq_batch* b, const int32_t* replicas);
+/* Samples every active replica of every instance (asynchronous; p's state arrays must be
+ * NULL; p->precision = MOQ_PREC_FP16 runs in the per-instance mode only). */
 int moq_sample_batch(moq_batch* b, const float* lambda_all, const moq_sample_params* p, uint64_t seed, uint64_t round,
                      uint64_t* bits_all, void* stream);
 /* Exact cut values (Eq. single_obj) of every sample: cuts_all row replica_offsets[b] + m

@@ -269,6 +269,7 @@ struct moq_batch {
     int32_t bd = 1024, spt = 1;
     int32_t nitems = 0;
     std::vector<moq::BatchInst> h_insts;
+    std::vector<int32_t> h_created_R;            // replicas per instance at creation (the layout)
     std::vector<int64_t> h_E;
     std::vector<const moq_instance*> h_handles;  // for the per-instance mode (bd == 0)
     // per-instance mode: launches fan out over these streams (one instance's tail overlaps
@@ -408,6 +409,7 @@ int moq_batch_create(const moq_instance* const* insts, int32_t count, const int3
         words += (int64_t)in.R * in.W;
         items_cap += in.R;  // at most one item per replica
         b->h_insts.push_back(in);
+        b->h_created_R.push_back(in.R);
         b->h_E.push_back(h->E);
         b->h_handles.push_back(h);
         b->max_degree = std::max(b->max_degree, h->max_degree);
@@ -502,6 +504,20 @@ int moq_batch_set_tiles(moq_batch* b, int32_t block_threads, int32_t slots_per_t
     int rc = build_items(b);
     if (items_out) *items_out = b->nitems;
     return rc;
+}
+
+int moq_batch_set_replicas(moq_batch* b, const int32_t* replicas)
+{
+    using namespace moq;
+    if (!b || !replicas) return fail(MOQ_ERR_ARG, "moq_batch_set_replicas: NULL argument");
+    for (int i = 0; i < b->count; ++i)
+        if (replicas[i] < 0 || replicas[i] > b->h_created_R[i])
+            return fail(MOQ_ERR_ARG, "moq_batch_set_replicas: instance %d: %d replicas outside [0, %d]", i, replicas[i],
+                        b->h_created_R[i]);
+    for (int i = 0; i < b->count; ++i) b->h_insts[i].R = replicas[i];
+    MOQ_CUDA_TRY(cudaMemcpy(b->d_insts, b->h_insts.data(), sizeof(BatchInst) * b->count, cudaMemcpyHostToDevice));
+    if (b->bd == 0) return MOQ_OK;  // per-instance launches read the counts on the host
+    return build_items(b);
 }
 
 int moq_sample_batch(moq_batch* b, const float* lambda_all, const moq_sample_params* p, uint64_t seed, uint64_t round,

@@ -88,6 +88,7 @@ _sigs = {
     "moq_batch_destroy": (None, [_vp]),
     "moq_batch_layout": (C.c_int, [_vp, _vp, _vp]),
     "moq_batch_set_tiles": (C.c_int, [_vp, _i32, _i32, C.POINTER(_i32)]),
+    "moq_batch_set_replicas": (C.c_int, [_vp, _vp]),
     "moq_sample_batch": (C.c_int, [_vp, _vp, C.POINTER(moq_sample_params), _u64, _u64, _vp, _vp]),
     "moq_evaluate_cuts_batch": (C.c_int, [_vp, _vp, _vp, _vp]),
     "moq_dense_create": (C.c_int, [_vp, _i32, C.POINTER(_vp)]),
@@ -335,6 +336,11 @@ def moq_batch_set_tiles(h, block_threads, slots_per_thread) -> int:
     items = C.c_int32()
     _check(_lib.moq_batch_set_tiles(h, block_threads, slots_per_thread, C.byref(items)), "moq_batch_set_tiles")
     return int(items.value)
+
+
+def moq_batch_set_replicas(h, replicas):
+    reps, preps = _hptr(replicas, np.int32)
+    _check(_lib.moq_batch_set_replicas(h, preps), "moq_batch_set_replicas")
 
 
 def moq_sample_batch(h, lam_all, params, seed, round_, bits_all, stream=None):

@@ -309,3 +309,169 @@ def time_to_target(src, target_hv: int, params, R: int, seed: int = 0, max_round
     inst.close()
     return {"seconds": secs, "rounds": rounds, "samples": rounds * R, "hv": hv, "front": front,
             "reached": hv >= target_hv, "trace": trace}
+
+
+class BatchLearnedProposer:
+    """One surrogate for every instance of a batch (the learned proposal; not in the paper).
+
+    The MLP's inputs carry each instance's eight graph statistics, so one network serves the
+    whole batch: every round's (lambda, cut vector) rows of each active instance are added
+    (cuts normalised by that instance's reference point and sum |J^(k)|), the network takes
+    ``train_steps`` Adam steps on the newest rows, and for each active instance a fraction
+    ``rho`` of its next weight vectors are the candidates predicted to reach furthest beyond
+    that instance's front; the rest stay uniform on the simplex. As in LearnedProposer, the
+    proposal for round t + 1 (after round t's merges) and the training run on a second stream
+    while the main stream checks hypervolumes and samples.
+    """
+
+    def __init__(self, instances, R, rho=0.25, n_candidates=2048, max_rows=1 << 20, train_steps=5, batch=4096,
+                 lr=3e-3, seed=0, device="cuda"):
+        self.K, self.R = instances[0].K, R
+        self.rho, self.n_candidates, self.train_steps, self.batch, self.lr, self.seed = \
+            rho, n_candidates, train_steps, batch, lr, seed
+        self.n_prop = int(rho * R)
+        self.feats = [np.asarray(h.info["features"], np.float32) for h in instances]
+        self.offs = [np.asarray(h.info["ref_point"], np.int64) for h in instances]
+        self.scales = [np.maximum(np.asarray(h.info["abs_sum"], np.int64), 1) for h in instances]
+        self.din = self.K + self.feats[0].size
+        self.mlp = M.moq_mlp_create(self.din, self.K, batch, n_candidates, seed + 1)
+        self.max_rows = max_rows
+        self.X = torch.zeros((max_rows, self.din), dtype=torch.float32, device=device)
+        self.T = torch.zeros((max_rows, self.K), dtype=torch.float32, device=device)
+        self.prop = torch.zeros((len(instances), max(self.n_prop, 1), self.K), dtype=torch.float32, device=device)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=device)
+        self.rows = 0
+        self.side = torch.cuda.Stream(device=device)
+        self.ready = None
+        self.proposed = []
+        self.trained = False
+
+    def apply(self, lam_all, rep_off):
+        """Overwrites the first rho * R weight vectors of every instance proposed for this round
+        (main stream, after the round's uniform vectors were drawn)."""
+        if self.ready is None:
+            return
+        torch.cuda.current_stream().wait_event(self.ready)
+        for b in self.proposed:
+            r0 = int(rep_off[b])
+            lam_all[r0:r0 + self.n_prop].copy_(self.prop[b, :self.n_prop])
+        self.ready = None
+
+    def observe(self, lam_all, cuts_all, rep_off, active, archives, round_):
+        """Adds the round's rows of the active instances, then queues on the second stream the
+        next round's proposals for them and the Adam steps."""
+        for b in active:
+            r0 = int(rep_off[b])
+            at = self.rows % self.max_rows
+            m = min(self.R, self.max_rows - at)
+            M.moq_mlp_make_rows(self.K, self.feats[b], lam_all[r0:r0 + m], cuts_all[r0:r0 + m], m, self.offs[b],
+                                self.scales[b], self.X[at:], self.T[at:])
+            self.rows += m
+        filled = min(self.rows, self.max_rows)
+        newest = (self.rows - 1) % self.max_rows
+        self.side.wait_stream(torch.cuda.current_stream())
+        first = not self.trained
+        if first:
+            self._train(newest, filled)  # the first model before its first proposal
+            self.trained = True
+        if self.n_prop > 0:
+            for b in active:
+                M.moq_lambda_propose(self.mlp, archives[b].handle, self.feats[b], self.offs[b], self.scales[b],
+                                     self.n_candidates, self.seed + 7 + b, round_ + 1, self.prop[b], self.n_prop, self.side)
+        self.proposed = list(active)
+        self.ready = self.side.record_event()
+        if not first:
+            self._train(newest, filled)  # runs while the next round samples
+
+    def _train(self, newest, filled):
+        for s in range(self.train_steps):
+            end = newest + 1 - s * self.batch
+            while end <= 0:
+                end += filled
+            start = max(0, end - self.batch)
+            M.moq_mlp_train_step(self.mlp, self.X[start:end], self.T[start:end], end - start, self.lr, self.loss, self.side)
+
+    def close(self):
+        if getattr(self, "mlp", None):
+            self.side.synchronize()
+            M.moq_mlp_destroy(self.mlp)
+            self.mlp = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def time_to_target_batch(srcs, targets, params, R: int, seed: int = 0, max_rounds: int = 256, batched: bool = True,
+                         learned: bool = False, tiles=(0, 0), capacity=1 << 18, proposer_kwargs=None):
+    """Rounds over a set of instances until every instance's archive reaches its target
+    hypervolume (the job is done when the whole set is).
+
+    ``batched``: each round is one ``moq_sample_batch`` call and one batched cut evaluation
+    over the instances still short of their target (``moq_batch_set_replicas`` drops the
+    others), tile shape ``tiles`` ((0, 0): per-instance launches over internal streams);
+    else one ``sample_round`` per such instance in turn. Every instance has its own archive,
+    and after each round every active instance's hypervolume is checked (one synchronisation
+    each). ``learned`` adds the batch surrogate (``BatchLearnedProposer``). The clock covers
+    instance construction, every round and the checks.
+    Returns dict(seconds, rounds, samples, reached, rounds_per_instance).
+    """
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    B = len(srcs)
+    insts = [Instance(s) for s in srcs]
+    archs = [Archive(s.n, s.K, capacity=capacity, max_batch=R) for s in srcs]
+    K = insts[0].K
+    active = list(range(B))
+    done_at = [0] * B
+    rounds, samples = 0, 0
+    batch = prop = None
+    if batched:
+        batch = Batch(insts, [R] * B)
+        batch.set_tiles(*tiles)
+        prop = BatchLearnedProposer(insts, R, seed=seed, **(proposer_kwargs or {})) if learned else None
+    else:
+        bufs = {}
+    while active and rounds < max_rounds:
+        if batched:
+            M.moq_lambda_dirichlet(K, batch.total_R, seed, rounds, batch.lam)
+            if prop:
+                prop.apply(batch.lam, batch.rep_off)
+            batch.sample(params, seed, rounds)
+            batch.evaluate_cuts()
+            for b in active:
+                archs[b].merge(batch.cuts_of(b), batch.bits_of(b), R, R * rounds)
+            if prop:
+                prop.observe(batch.lam, batch.cuts, batch.rep_off, active, archs, rounds)
+        else:
+            for b in active:
+                if srcs[b].n not in bufs:
+                    bufs[srcs[b].n] = RoundBuffers(R, srcs[b].n, K)
+                sample_round(insts[b], archs[b], bufs[srcs[b].n], params, seed, rounds)
+        samples += R * len(active)
+        rounds += 1
+        still = []
+        for b in active:
+            if archs[b].hypervolume(insts[b].ref) >= targets[b]:
+                done_at[b] = rounds
+            else:
+                still.append(b)
+        if batched and len(still) < len(active) and still:
+            reps = np.zeros(B, np.int32)
+            reps[still] = R
+            M.moq_batch_set_replicas(batch.handle, reps)
+        active = still
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    if prop:
+        prop.close()
+    if batch is not None:
+        batch.close()
+    for a in archs:
+        a.close()
+    for h in insts:
+        h.close()
+    return {"seconds": secs, "rounds": rounds, "samples": samples, "reached": not active,
+            "rounds_per_instance": done_at}
