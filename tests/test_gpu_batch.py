@@ -102,3 +102,58 @@ def test_batch_round_in_cuda_graph(M, P, batch, tile):
     g.replay()
     torch.cuda.synchronize()
     assert torch.equal(b.bits, want_bits) and torch.equal(b.cuts, want_cuts)
+
+
+@pytest.mark.parametrize("tile", [(1024, 1), (0, 0)])
+def test_batch_active_replicas(M, P, tile):
+    # moq_batch_set_replicas: instance b samples (and gets cuts for) its first replicas[b]
+    # replicas only, 0 skipping it, with the layout and noise counters unchanged
+    srcs = _srcs()
+    insts = [P.Instance(s) for s in srcs]
+    reps = [300, 77, 5, 40, 1, 33]
+    b = P.Batch(insts, reps)
+    b.lam.copy_(torch.from_numpy(wl.dirichlet_lambdas(b.total_R, 3, 18)))
+    b.set_tiles(*tile)
+    params = M.moq_default_params(steps=120, dt=0.5, alpha=0.1)
+    b.sample(params, seed=4, round_=1)
+    b.evaluate_cuts()
+    full_bits, full_cuts = b.bits.clone(), b.cuts.clone()
+    active = [0, 77, 5, 0, 1, 20]
+    M.moq_batch_set_replicas(b.handle, np.array(active, np.int32))
+    b.bits.fill_(-1)
+    b.cuts.fill_(-1)
+    b.sample(params, seed=4, round_=1)
+    b.evaluate_cuts()
+    torch.cuda.synchronize()
+    for k, inst in enumerate(insts):
+        bits_k, cuts_k = b.bits_of(k), b.cuts_of(k)
+        a = active[k]
+        want_b = full_bits[int(b.word_off[k]):int(b.word_off[k + 1])].view(reps[k], inst.W)
+        assert torch.equal(bits_k[:a], want_b[:a])
+        assert torch.equal(cuts_k[:a], full_cuts[int(b.rep_off[k]):int(b.rep_off[k]) + a])
+        assert bool((bits_k[a:] == -1).all()) and bool((cuts_k[a:] == -1).all())  # untouched
+    with pytest.raises(M.MoqError) as e:
+        M.moq_batch_set_replicas(b.handle, np.array([301, 0, 0, 0, 0, 0], np.int32))
+    assert e.value.code == M.MOQ_ERR_ARG
+
+
+@pytest.mark.parametrize("batched,learned,prec", [(False, False, "fp32"), (True, False, "fp16"), (True, True, "fp16")])
+def test_batch_time_to_target_reaches_every_instance(M, P, oracle, batched, learned, prec):
+    # the batch driver stops each instance at its own target; the targets here are the
+    # 99% of the hypervolume of the oracle's filter of one plain round, so every arm gets there
+    srcs = [wl.random_regular(n, 60 + n, K=3) for n in (42, 130, 300)]
+    R = 256
+    targets = []
+    for src in srcs:
+        inst = P.Instance(src)
+        buf = P.RoundBuffers(R, src.n, 3)
+        arch = P.Archive(src.n, 3, capacity=1 << 14, max_batch=R)
+        P.sample_round(inst, arch, buf, M.moq_default_params(steps=300, dt=0.5), seed=0, round_=0)
+        c = oracle.cuts(src, buf.bits.cpu().numpy().view(np.uint64))
+        targets.append(int(oracle.hypervolume(c[oracle.pareto_filter(c)], inst.ref)) * 99 // 100)
+        arch.close()
+        inst.close()
+    params = M.moq_default_params(steps=400, dt=0.5, alpha=0.1, precision=prec)
+    res = P.time_to_target_batch(srcs, targets, params, R, seed=1, max_rounds=64, batched=batched, learned=learned)
+    assert res["reached"] and all(1 <= r <= res["rounds"] for r in res["rounds_per_instance"])
+    assert res["samples"] <= R * len(srcs) * res["rounds"]
