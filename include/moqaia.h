@@ -384,6 +384,24 @@ int moq_mlp_adam_step(moq_mlp* m, float lr, void* stream);
  * gradient sum and the update share one pass): the same parameters bit for bit. loss_out
  * (device, 1 float) may be NULL. Asynchronous; errors: MOQ_ERR_ARG. */
 int moq_mlp_train_step(moq_mlp* m, const float* X, const float* T, int32_t B, float lr, float* loss_out, void* stream);
+/* Which kernels run the products of moq_mlp_forward, moq_mlp_gradient, moq_mlp_train_step and
+ * the proposal's predictions (set per handle; default MOQ_MLP_CUDA_CORES):
+ *  MOQ_MLP_CUDA_CORES   FP32 activations, FP32 multiply-adds on the CUDA cores;
+ *  MOQ_MLP_TENSOR_CORES every matrix product (forward, the backward products and the weight
+ *                       gradients) a tcgen05 MMA with BF16 operands and FP32 accumulation in
+ *                       TMEM, one CTA per 128-row tile: inputs, activations and the
+ *                       backpropagated deltas are rounded to BF16 where they enter a product;
+ *                       sums, relu masks, the loss and the bias gradients stay FP32. Its
+ *                       gradient is that of the FP64 network with those roundings (within FP32
+ *                       summation error), and within a few BF16 units (2^-8) of the exact
+ *                       network's. Deterministic (fixed reduction order).
+ * Errors: MOQ_ERR_ARG. */
+#define MOQ_MLP_CUDA_CORES 0
+#define MOQ_MLP_TENSOR_CORES 1
+int moq_mlp_set_engine(moq_mlp* m, int32_t engine);
+/* Synchronises `stream`; MOQ_ERR_TIMEOUT if a tensor-core wait of an earlier call ran out of
+ * its 2 s budget (the call then left its outputs unwritten), which also clears the flag. */
+int moq_mlp_status(moq_mlp* m, void* stream);
 /* Training rows from M samples (device): X[m] = [lambda[m] (K), features (host, n_features)],
  * T[m][k] = (cuts[m][k] - offset[k]) / scale[k] (host offset, scale: K int64; the learned
  * proposal uses the reference point and sum |J^(k)|, so targets lie in [0, 1]). X: M x

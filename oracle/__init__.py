@@ -75,6 +75,11 @@ def _load():
             lib.or_mlp_forward.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.c_int64, dp, dp]
             lib.or_mlp_loss_grad.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.c_int64, dp, dp, dp]
             lib.or_mlp_loss_grad.restype = C.c_double
+            lib.or_bf16.argtypes = [C.c_double]
+            lib.or_bf16.restype = C.c_double
+            lib.or_mlp_forward_bf16.argtypes = lib.or_mlp_forward.argtypes
+            lib.or_mlp_loss_grad_bf16.argtypes = lib.or_mlp_loss_grad.argtypes
+            lib.or_mlp_loss_grad_bf16.restype = C.c_double
             lib.or_e4m3.argtypes = [C.c_double]
             lib.or_e4m3.restype = C.c_double
             lib.or_e4m3_couplings.argtypes = [C.c_int, C.c_int, C.c_int64, i32p, i32p, i32p, dp, dp, dp]
@@ -231,6 +236,28 @@ def mlp_loss_grad(params, X, T, din: int, h: int, dout: int):
     T = np.ascontiguousarray(np.asarray(T, np.float64).reshape(-1, dout))
     g = np.zeros(mlp_param_count(din, h, dout), np.float64)
     loss = _load().or_mlp_loss_grad(din, h, dout, np.ascontiguousarray(params, np.float64), X.shape[0], X, T, g)
+    return loss, g
+
+
+def bf16(v: float) -> float:
+    """v rounded to the nearest BF16 value (ties to an even significand)."""
+    return float(_load().or_bf16(float(v)))
+
+
+def mlp_forward_bf16(params, X, din: int, h: int, dout: int) -> np.ndarray:
+    """The network with every matrix-product operand rounded to BF16 (exact sums)."""
+    X = np.ascontiguousarray(np.asarray(X, np.float64).reshape(-1, din))
+    Y = np.zeros((X.shape[0], dout), np.float64)
+    _load().or_mlp_forward_bf16(din, h, dout, np.ascontiguousarray(params, np.float64), X.shape[0], X, Y)
+    return Y
+
+
+def mlp_loss_grad_bf16(params, X, T, din: int, h: int, dout: int):
+    """Loss and gradient with BF16 matrix-product operands (exact sums, exact bias gradients)."""
+    X = np.ascontiguousarray(np.asarray(X, np.float64).reshape(-1, din))
+    T = np.ascontiguousarray(np.asarray(T, np.float64).reshape(-1, dout))
+    g = np.zeros(mlp_param_count(din, h, dout), np.float64)
+    loss = _load().or_mlp_loss_grad_bf16(din, h, dout, np.ascontiguousarray(params, np.float64), X.shape[0], X, T, g)
     return loss, g
 
 

@@ -684,3 +684,108 @@ double or_mlp_loss_grad(int din, int h, int dout, const double* p, int64_t B, co
     free(a1);
     return loss;
 }
+
+/* ------------------------------------------------------------------------------------
+ * The same network with BF16 operands (the tensor-core surrogate's arithmetic; not in the
+ * paper). rho(v) rounds v to the nearest BF16 value (8 significant bits, the FP32
+ * exponent range, ties to an even significand; below 2^-126 multiples of 2^-133). Every
+ * matrix-product operand is rounded, every sum and every bias gradient is exact:
+ *   x~ = rho(x); a1 = W1 x~ + b1; h1~ = rho(relu(a1)); a2 = W2 h1~ + b2;
+ *   h2~ = rho(relu(a2)); y = W3 h2~ + b3; dy = 2 (y - t) / (B D_out); dy~ = rho(dy);
+ *   d2 = (W3^T dy~) [a2 > 0]; d2~ = rho(d2); d1 = (W2^T d2~) [a1 > 0]; d1~ = rho(d1);
+ *   dW3 = sum dy~ h2~^T, db3 = sum dy; dW2 = sum d2~ h1~^T, db2 = sum d2;
+ *   dW1 = sum d1~ x~^T, db1 = sum d1.
+ * The weights are taken as given (the caller passes BF16 values).
+ * ---------------------------------------------------------------------------------- */
+double or_bf16(double v)
+{
+    if (v == 0.0 || isnan(v) || isinf(v)) return v;
+    const double a = fabs(v);
+    if (a < 0x1p-126) return nearbyint(v * 0x1p133) * 0x1p-133; /* subnormal BF16 spacing */
+    int e;
+    const double f = frexp(v, &e); /* v = f 2^e, 0.5 <= |f| < 1 */
+    const double r = nearbyint(f * 256.0) * 0x1p-8; /* 8 significant bits, ties to even */
+    const double out = ldexp(r, e);
+    return fabs(out) > 0x1.FEp127 ? copysign(INFINITY, v) : out;
+}
+
+static void mlp_forward_row_bf16(int din, int h, int dout, const double* p, const double* x, double* xr, double* a1,
+                                 double* h1, double* a2, double* h2, double* y)
+{
+    int64_t off[6];
+    mlp_layer_offsets(din, h, dout, off);
+    for (int i = 0; i < din; ++i) xr[i] = or_bf16(x[i]);
+    for (int j = 0; j < h; ++j) {
+        double s = p[off[1] + j];
+        for (int i = 0; i < din; ++i) s += p[off[0] + (int64_t)j * din + i] * xr[i];
+        a1[j] = s;
+        h1[j] = or_bf16(s > 0.0 ? s : 0.0);
+    }
+    for (int j = 0; j < h; ++j) {
+        double s = p[off[3] + j];
+        for (int i = 0; i < h; ++i) s += p[off[2] + (int64_t)j * h + i] * h1[i];
+        a2[j] = s;
+        h2[j] = or_bf16(s > 0.0 ? s : 0.0);
+    }
+    for (int k = 0; k < dout; ++k) {
+        double s = p[off[5] + k];
+        for (int i = 0; i < h; ++i) s += p[off[4] + (int64_t)k * h + i] * h2[i];
+        y[k] = s;
+    }
+}
+
+void or_mlp_forward_bf16(int din, int h, int dout, const double* p, int64_t B, const double* X, double* Y)
+{
+    double* buf = (double*)malloc(sizeof(double) * (4 * h + din));
+    for (int64_t b = 0; b < B; ++b)
+        mlp_forward_row_bf16(din, h, dout, p, X + b * din, buf + 4 * h, buf, buf + h, buf + 2 * h, buf + 3 * h, Y + b * dout);
+    free(buf);
+}
+
+double or_mlp_loss_grad_bf16(int din, int h, int dout, const double* p, int64_t B, const double* X, const double* T, double* grad)
+{
+    int64_t off[6];
+    mlp_layer_offsets(din, h, dout, off);
+    const int64_t P = off[5] + dout;
+    for (int64_t q = 0; q < P; ++q) grad[q] = 0.0;
+    double* a1 = (double*)malloc(sizeof(double) * (8 * h + 3 * dout + din));
+    double *h1 = a1 + h, *a2 = h1 + h, *h2 = a2 + h, *d2 = h2 + h, *d1 = d2 + h, *d2r = d1 + h, *d1r = d2r + h;
+    double *y = d1r + h, *dy = y + dout, *dyr = dy + dout, *xr = dyr + dout;
+    double loss = 0.0;
+    const double scale = 1.0 / ((double)B * dout);
+    for (int64_t b = 0; b < B; ++b) {
+        mlp_forward_row_bf16(din, h, dout, p, X + b * din, xr, a1, h1, a2, h2, y);
+        for (int k = 0; k < dout; ++k) {
+            const double e = y[k] - T[b * dout + k];
+            loss += e * e * scale;
+            dy[k] = 2.0 * e * scale;
+            dyr[k] = or_bf16(dy[k]);
+        }
+        for (int k = 0; k < dout; ++k) {
+            grad[off[5] + k] += dy[k];
+            for (int i = 0; i < h; ++i) grad[off[4] + (int64_t)k * h + i] += dyr[k] * h2[i];
+        }
+        for (int i = 0; i < h; ++i) {
+            double s = 0.0;
+            for (int k = 0; k < dout; ++k) s += p[off[4] + (int64_t)k * h + i] * dyr[k];
+            d2[i] = a2[i] > 0.0 ? s : 0.0;
+            d2r[i] = or_bf16(d2[i]);
+        }
+        for (int j = 0; j < h; ++j) {
+            grad[off[3] + j] += d2[j];
+            for (int i = 0; i < h; ++i) grad[off[2] + (int64_t)j * h + i] += d2r[j] * h1[i];
+        }
+        for (int i = 0; i < h; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < h; ++j) s += p[off[2] + (int64_t)j * h + i] * d2r[j];
+            d1[i] = a1[i] > 0.0 ? s : 0.0;
+            d1r[i] = or_bf16(d1[i]);
+        }
+        for (int j = 0; j < h; ++j) {
+            grad[off[1] + j] += d1[j];
+            for (int i = 0; i < din; ++i) grad[off[0] + (int64_t)j * din + i] += d1r[j] * xr[i];
+        }
+    }
+    free(a1);
+    return loss;
+}

@@ -19,6 +19,7 @@
 #include <stdlib.h>
 #include <vector>
 
+#include "mlp_tc.cuh"
 #include "moq_common.cuh"
 
 namespace moq {
@@ -565,6 +566,8 @@ __global__ void __launch_bounds__(64) k_top_r(const uint32_t* __restrict__ key, 
 
 struct moq_mlp {
     int din = 0, dout = 0, max_batch = 0, max_cand = 0, max_blocks = 0;
+    int engine = MOQ_MLP_CUDA_CORES;    // which kernels run the products
+    int32_t* status = nullptr;          // tensor-core engine: latched wait time-outs
     int64_t P = 0, step = 0;
     float* master = nullptr;
     __nv_bfloat16* w16 = nullptr;
@@ -587,12 +590,37 @@ void free_mlp(moq_mlp* m)
 {
     if (!m) return;
     for (void* p : {(void*)m->master, (void*)m->w16, (void*)m->grad, (void*)m->adam_m, (void*)m->adam_v, (void*)m->partial,
-                    (void*)m->loss_part, (void*)m->cand, (void*)m->cand_in, (void*)m->cand_pred, (void*)m->cand_score, (void*)m->consts})
+                    (void*)m->loss_part, (void*)m->cand, (void*)m->cand_in, (void*)m->cand_pred, (void*)m->cand_score, (void*)m->consts,
+                    (void*)m->status})
         cudaFree(p);
     delete m;
 }
 
 size_t mlp_smem_bytes() { return sizeof(float) * mlp_smem_floats(); }
+
+MlpTcArgs tc_args(const moq_mlp* m, const float* X, const float* T, int64_t B, float* Y)
+{
+    const MlpShape sh = mlp_shape(m->din, m->dout);
+    MlpTcArgs a{};
+    a.w = m->w16;
+    a.din = m->din;
+    a.dout = m->dout;
+    a.oW1 = sh.oW1;
+    a.ob1 = sh.ob1;
+    a.oW2 = sh.oW2;
+    a.ob2 = sh.ob2;
+    a.oW3 = sh.oW3;
+    a.ob3 = sh.ob3;
+    a.P = sh.P;
+    a.X = X;
+    a.T = T;
+    a.B = B;
+    a.Y = Y;
+    a.partial = m->partial;
+    a.loss_part = m->loss_part;
+    a.status = m->status;
+    return a;
+}
 
 }  // namespace
 }  // namespace moq
@@ -627,6 +655,8 @@ int moq_mlp_create(int32_t d_in, int32_t d_out, int32_t max_batch, int32_t max_c
     al((void**)&m->cand_pred, sizeof(float) * max_candidates * d_out);
     al((void**)&m->cand_score, sizeof(float) * max_candidates);
     al((void**)&m->consts, sizeof(float) * 64);
+    al((void**)&m->status, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(m->status, 0, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(m->adam_m, 0, sizeof(float) * m->P);
     if (e == cudaSuccess) e = cudaMemset(m->adam_v, 0, sizeof(float) * m->P);
     if (e == cudaSuccess) e = cudaMemset(m->grad, 0, sizeof(float) * m->P);
@@ -679,6 +709,11 @@ int moq_mlp_forward(const moq_mlp* m, const float* X, int32_t B, float* Y, void*
     using namespace moq;
     if (!m || B < 0 || (B > 0 && (!X || !Y))) return fail(MOQ_ERR_ARG, "moq_mlp_forward: bad argument");
     if (B == 0) return MOQ_OK;
+    if (m->engine == MOQ_MLP_TENSOR_CORES) {
+        const cudaError_t e = launch_mlp_tc(tc_args(m, X, nullptr, B, Y), false, as_stream(stream));
+        if (e != cudaSuccess) return cuda_fail(e, "moq_mlp_forward (tensor cores)");
+        return MOQ_OK;
+    }
     const int grid = (int)std::min<int64_t>(ceil_div(B, kRows), 148 * 2);
     k_mlp_forward<<<grid, kThreads, mlp_smem_bytes(), as_stream(stream)>>>(m->w16, m->din, m->dout, X, B, Y);
     MOQ_LAUNCH_CHECK("moq_mlp_forward");
@@ -690,8 +725,15 @@ int moq_mlp_gradient(moq_mlp* m, const float* X, const float* T, int32_t B, floa
     using namespace moq;
     if (!m || B < 1 || B > m->max_batch || !X || !T) return fail(MOQ_ERR_ARG, "moq_mlp_gradient: need 1 <= B <= max_batch and inputs");
     cudaStream_t st = as_stream(stream);
-    const int nb = (int)ceil_div(B, kRows);
-    k_mlp_grad<<<nb, kThreads, mlp_smem_bytes(), st>>>(m->w16, m->din, m->dout, X, T, B, m->partial, m->loss_part);
+    int nb;
+    if (m->engine == MOQ_MLP_TENSOR_CORES) {
+        nb = (int)ceil_div(B, kMlpTcRows);
+        const cudaError_t e = launch_mlp_tc(tc_args(m, X, T, B, nullptr), true, st);
+        if (e != cudaSuccess) return cuda_fail(e, "moq_mlp_gradient (tensor cores)");
+    } else {
+        nb = (int)ceil_div(B, kRows);
+        k_mlp_grad<<<nb, kThreads, mlp_smem_bytes(), st>>>(m->w16, m->din, m->dout, X, T, B, m->partial, m->loss_part);
+    }
     k_mlp_reduce<<<(unsigned)std::min<int64_t>(ceil_div(m->P, 256), 148), 256, 0, st>>>(m->partial, m->loss_part, nb, m->P, m->grad,
                                                                                        loss_out ? loss_out : m->loss_part + m->max_blocks);
     MOQ_LAUNCH_CHECK("moq_mlp_gradient");
@@ -719,16 +761,46 @@ int moq_mlp_train_step(moq_mlp* m, const float* X, const float* T, int32_t B, fl
     if (!m || B < 1 || B > m->max_batch || !X || !T || !(lr > 0.0f))
         return fail(MOQ_ERR_ARG, "moq_mlp_train_step: need 1 <= B <= max_batch, inputs and lr > 0");
     cudaStream_t st = as_stream(stream);
-    const int nb = (int)ceil_div(B, kRows);
+    int nb;
+    if (m->engine == MOQ_MLP_TENSOR_CORES) {
+        nb = (int)ceil_div(B, kMlpTcRows);
+        const cudaError_t e = launch_mlp_tc(tc_args(m, X, T, B, nullptr), true, st);
+        if (e != cudaSuccess) return cuda_fail(e, "moq_mlp_train_step (tensor cores)");
+    } else {
+        nb = (int)ceil_div(B, kRows);
+        k_mlp_grad<<<nb, kThreads, mlp_smem_bytes(), st>>>(m->w16, m->din, m->dout, X, T, B, m->partial, m->loss_part);
+    }
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     m->step += 1;
     const double t = (double)m->step;
     const float lr_t = (float)(lr * std::sqrt(1.0 - std::pow(b2, t)) / (1.0 - std::pow(b1, t)));
-    k_mlp_grad<<<nb, kThreads, mlp_smem_bytes(), st>>>(m->w16, m->din, m->dout, X, T, B, m->partial, m->loss_part);
     k_mlp_reduce_adam<<<(unsigned)std::min<int64_t>(ceil_div(m->P, 256), 148), 256, 0, st>>>(
         m->partial, m->loss_part, nb, m->P, m->grad, loss_out ? loss_out : m->loss_part + m->max_blocks, m->master, m->adam_m,
         m->adam_v, lr_t, b1, b2, eps, m->w16);
     MOQ_LAUNCH_CHECK("moq_mlp_train_step");
+    return MOQ_OK;
+}
+
+int moq_mlp_set_engine(moq_mlp* m, int32_t engine)
+{
+    using namespace moq;
+    if (!m || (engine != MOQ_MLP_CUDA_CORES && engine != MOQ_MLP_TENSOR_CORES)) return fail(MOQ_ERR_ARG, "moq_mlp_set_engine: bad argument");
+    m->engine = engine;
+    return MOQ_OK;
+}
+
+int moq_mlp_status(moq_mlp* m, void* stream)
+{
+    using namespace moq;
+    if (!m) return fail(MOQ_ERR_ARG, "moq_mlp_status: NULL handle");
+    cudaStream_t st = as_stream(stream);
+    int32_t h = 0;
+    MOQ_CUDA_TRY(cudaMemcpyAsync(&h, m->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MOQ_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h) {
+        MOQ_CUDA_TRY(cudaMemsetAsync(m->status, 0, sizeof(int32_t), st));
+        return fail(MOQ_ERR_TIMEOUT, "moq_mlp: a tensor-core wait ran out of its budget");
+    }
     return MOQ_OK;
 }
 

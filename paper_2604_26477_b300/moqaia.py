@@ -28,6 +28,8 @@ MOQ_DSB = 0
 MOQ_BSB = 1
 MOQ_PREC_FP32 = 0
 MOQ_PREC_FP16 = 1
+MOQ_MLP_CUDA_CORES = 0
+MOQ_MLP_TENSOR_CORES = 1
 
 
 class MoqError(RuntimeError):
@@ -110,6 +112,8 @@ _sigs = {
     "moq_mlp_gradient": (C.c_int, [_vp, _vp, _vp, _i32, _vp, _vp, _vp]),
     "moq_mlp_adam_step": (C.c_int, [_vp, C.c_float, _vp]),
     "moq_mlp_train_step": (C.c_int, [_vp, _vp, _vp, _i32, C.c_float, _vp, _vp]),
+    "moq_mlp_set_engine": (C.c_int, [_vp, _i32]),
+    "moq_mlp_status": (C.c_int, [_vp, _vp]),
     "moq_lambda_propose": (C.c_int, [_vp, _vp, _vp, _i32, _vp, _vp, _i32, _u64, _u64, _vp, _i32, _vp]),
     "moq_mlp_make_rows": (C.c_int, [_i32, _i32, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "moq_release_cached_memory": (C.c_int, []),
@@ -457,6 +461,16 @@ def moq_mlp_train_step(h, X, T, B, lr, loss=None, stream=None):
     f32, _, _ = _torch_types()
     _check(_lib.moq_mlp_train_step(h, _dptr(X, "X", f32), _dptr(T, "T", f32), B, lr, _dptr(loss, "loss", f32), _stream(stream)),
            "moq_mlp_train_step")
+
+
+def moq_mlp_set_engine(h, engine):
+    if isinstance(engine, str):
+        engine = {"cuda_cores": MOQ_MLP_CUDA_CORES, "tensor_cores": MOQ_MLP_TENSOR_CORES}[engine]
+    _check(_lib.moq_mlp_set_engine(h, engine), "moq_mlp_set_engine")
+
+
+def moq_mlp_status(h, stream=None):
+    _check(_lib.moq_mlp_status(h, _stream(stream)), "moq_mlp_status")
 
 
 def moq_mlp_make_rows(K, features, lam, cuts, M, offset, scale, X, T, stream=None):

@@ -173,8 +173,9 @@ class LearnedProposer:
     rows. The next round's batch is a fraction ``rho`` of proposed weight vectors -- the
     candidates whose predicted cuts reach furthest beyond the current front -- and the rest
     uniform on the simplex (exploration, and the fallback before any data exists).
-    Defaults (2048 candidates, 5 Adam steps per round, a quarter of each round proposed) were
-    picked on held-out n = 300 instances: 8192 candidates and 20 steps gave about as many
+    The network trains and predicts on the tensor cores (``engine``; BF16 operands, FP32
+    accumulation). Defaults (2048 candidates, 5 Adam steps per round, a quarter of each round
+    proposed) were picked on held-out n = 300 instances: 8192 candidates and 20 steps gave about as many
     samples to the target but twice the time per round, and proposing half or three quarters
     of each round needed more samples than a quarter.
 
@@ -188,7 +189,7 @@ class LearnedProposer:
     """
 
     def __init__(self, inst: Instance, R: int, rho=0.25, n_candidates=2048, max_rows=1 << 20, train_steps=5,
-                 batch=4096, lr=3e-3, seed=0, device="cuda", overlap=True):
+                 batch=4096, lr=3e-3, seed=0, device="cuda", overlap=True, engine="tensor_cores"):
         self.inst, self.R, self.K = inst, R, inst.K
         self.rho, self.n_candidates, self.train_steps, self.batch, self.lr, self.seed = \
             rho, n_candidates, train_steps, batch, lr, seed
@@ -197,6 +198,7 @@ class LearnedProposer:
         self.offset = np.asarray(inst.info["ref_point"], np.int64)
         self.scale = np.maximum(np.asarray(inst.info["abs_sum"], np.int64), 1)
         self.mlp = M.moq_mlp_create(self.din, self.K, batch, n_candidates, seed + 1)
+        M.moq_mlp_set_engine(self.mlp, engine)
         self.max_rows = max_rows
         self.X = torch.zeros((max_rows, self.din), dtype=torch.float32, device=device)
         self.T = torch.zeros((max_rows, self.K), dtype=torch.float32, device=device)
@@ -325,7 +327,7 @@ class BatchLearnedProposer:
     """
 
     def __init__(self, instances, R, rho=0.25, n_candidates=2048, max_rows=1 << 20, train_steps=5, batch=4096,
-                 lr=3e-3, seed=0, device="cuda"):
+                 lr=3e-3, seed=0, device="cuda", engine="tensor_cores"):
         self.K, self.R = instances[0].K, R
         self.rho, self.n_candidates, self.train_steps, self.batch, self.lr, self.seed = \
             rho, n_candidates, train_steps, batch, lr, seed
@@ -335,6 +337,7 @@ class BatchLearnedProposer:
         self.scales = [np.maximum(np.asarray(h.info["abs_sum"], np.int64), 1) for h in instances]
         self.din = self.K + self.feats[0].size
         self.mlp = M.moq_mlp_create(self.din, self.K, batch, n_candidates, seed + 1)
+        M.moq_mlp_set_engine(self.mlp, engine)
         self.max_rows = max_rows
         self.X = torch.zeros((max_rows, self.din), dtype=torch.float32, device=device)
         self.T = torch.zeros((max_rows, self.K), dtype=torch.float32, device=device)

@@ -66,3 +66,57 @@ def test_gradient_central_differences(oracle):
         pm[q] -= hstep
         fd = (oracle.mlp_loss_grad(pp, X, T, DIN, H, DOUT)[0] - oracle.mlp_loss_grad(pm, X, T, DIN, H, DOUT)[0]) / (2 * hstep)
         assert abs(fd - g[q]) <= 1e-6 * max(1.0, abs(g[q])), (q, fd, g[q])
+
+
+# ------------------------------------------------ the BF16-operand variant (tensor-core surrogate)
+def test_bf16_rounding_matches_torch(oracle):
+    # rho is round to nearest even at 8 significant bits: torch's float32 -> bfloat16 cast on
+    # random floats, every midpoint between neighbouring BF16 values of a range, subnormals
+    import torch
+    rng = np.random.default_rng(3)
+    vals = np.concatenate([rng.normal(0, 1, 3000), rng.normal(0, 1e-3, 1000) * 10.0 ** rng.integers(-30, 30, 1000),
+                           np.array([0.0, -0.0, 1.0, -1.0, 3.0e-39, -7.1e-40, 2.0 ** -133, 3 * 2.0 ** -134])]).astype(np.float32)
+    b = torch.from_numpy(np.arange(0x3F80, 0x4080, dtype=np.int32)).to(torch.int16).view(torch.bfloat16).float().numpy()
+    mids = ((b[:-1].astype(np.float64) + b[1:]) / 2).astype(np.float32)  # exact in float32
+    vals = np.concatenate([vals, mids, -mids])
+    want = torch.from_numpy(vals).to(torch.bfloat16).float().numpy().astype(np.float64)
+    got = np.array([oracle.bf16(float(v)) for v in vals])
+    assert np.array_equal(got, want)
+
+
+def _exact_case(seed, din=4, h=8, dout=2, B=4):
+    """Weights in {0, +-1/8}, inputs in {-1, 0, 1}, targets y + {0, +-1/8}: with these every
+    product operand of the network has at most a few significant bits, so rounding to BF16
+    changes nothing."""
+    rng = np.random.default_rng(seed)
+    P = din * h + h + h * h + h + dout * h + dout
+    p = rng.choice([-0.125, 0.0, 0.125], P)
+    X = rng.choice([-1.0, 0.0, 1.0], (B, din))
+    return p, X
+
+
+def test_bf16_variant_equals_exact_network_on_exactly_representable_operands(oracle):
+    for seed in range(5):
+        p, X = _exact_case(seed)
+        Y = oracle.mlp_forward(p, X, 4, 8, 2)
+        assert np.array_equal(oracle.mlp_forward_bf16(p, X, 4, 8, 2), Y)
+        T = Y + np.random.default_rng(seed).choice([-0.125, 0.0, 0.125], Y.shape)
+        L, g = oracle.mlp_loss_grad(p, X, T, 4, 8, 2)
+        Lb, gb = oracle.mlp_loss_grad_bf16(p, X, T, 4, 8, 2)
+        assert Lb == L and np.array_equal(gb, g)
+        assert np.abs(g).max() > 0
+
+
+def test_bf16_variant_rounds_within_its_bound(oracle):
+    # on generic values the rounding is active, and the gradient stays within a few BF16
+    # units (2^-8) of the exact network's, normwise
+    rng = np.random.default_rng(4)
+    P = oracle.mlp_param_count(DIN, H, DOUT)
+    p = np.array([oracle.bf16(v) for v in rng.normal(0, 0.3, P)])
+    X = rng.normal(0, 1, (64, DIN))
+    T = rng.normal(0, 1, (64, DOUT))
+    L, g = oracle.mlp_loss_grad(p, X, T, DIN, H, DOUT)
+    Lb, gb = oracle.mlp_loss_grad_bf16(p, X, T, DIN, H, DOUT)
+    rel = np.linalg.norm(gb - g) / np.linalg.norm(g)
+    assert 1e-5 < rel < 8 * 2.0 ** -8
+    assert 0 < abs(Lb - L) / L < 8 * 2.0 ** -8
