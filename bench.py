@@ -876,9 +876,9 @@ def appendix_e_arm(args, rank, world):
     lam_dd = torch.zeros((4096, K), dtype=torch.float32, device=dev)
     nw = M.moq_lambda_das_dennis(K, 21, 1, lam_dd, 4096)
     lam = lam_dd[:nw].repeat_interleave(batch, dim=0).contiguous()
-    # the instances carry J2 = A - 25 B (integers, 5x the paper's 0.2 A - 5 B); the weight on
+    # the instances carry J2 = A - 25 B (integers, 5x the paper's 0.2 A - 5 B): the weight on
     # objective 2 is divided by 5 so that J(c) is the paper's scalarisation
-    lam[:, 1] *= 0.2
+    P.source_scalarisation(lam, wl.app_e_correlated(25, 0.5, 0).objective_scale)
     R = lam.shape[0]
     results, units, busy = {}, 0.0, 0.0
     for n, d in ((25, 0.5), (25, 1.0), (100, 0.5), (100, 1.0), (200, 0.5), (200, 1.0)):
@@ -926,14 +926,8 @@ def appendix_e_arm(args, rank, world):
                 busy += secs
             arch.close()
         if n == 25:  # exhaustive front: every configuration with s_0 = +1
-            ref_arch = P.Archive(n, K, capacity=1 << 19, max_batch=1 << 20)
-            chunk = torch.zeros((1 << 20, 1), dtype=torch.int64, device=dev)
-            ccut = torch.zeros((1 << 20, K), dtype=torch.int64, device=dev)
-            for c in range(1 << 4):
-                chunk[:, 0] = (torch.arange(1 << 20, device=dev, dtype=torch.int64) + (c << 20)) << 1
-                M.moq_evaluate_cuts(inst.handle, chunk, 1 << 20, ccut)
-                torch.minimum(lo, ccut.min(dim=0).values, out=lo)
-                ref_arch.merge(ccut, chunk, 1 << 20, c << 20)
+            ref_arch, lo_all = P.exhaustive_front(inst)
+            torch.minimum(lo, lo_all, out=lo)
             ref_type = "exhaustive (2^24 configurations)"
         else:  # composite front of the arms
             ref_arch = P.Archive(n, K, capacity=1 << 19, max_batch=1 << 19)

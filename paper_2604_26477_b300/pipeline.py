@@ -15,6 +15,43 @@ import torch
 from . import moqaia as M
 
 
+def source_scalarisation(lam, objective_scale):
+    """Weight vectors for an instance whose stored integer weights are objective_scale[k] times
+    the source's (an objective scaled to make its weights integers leaves the Pareto set
+    unchanged, but the weighted sum J(c) = sum_k c_k J^(k) would over-weight it): column k of
+    ``lam`` (torch, R x K) is divided by objective_scale[k] in place, so that the sampler's
+    J(c) on the stored weights equals the source's scalarisation. Returns ``lam``."""
+    if objective_scale is None:
+        return lam
+    for k, s in enumerate(np.asarray(objective_scale).tolist()):
+        if s != 1:
+            lam[:, k] /= float(s)
+    return lam
+
+
+def exhaustive_front(inst: "Instance", chunk_log2: int = 20, stream=None):
+    """The exact front of a small instance (n <= 32) by enumeration: every configuration
+    with s_0 = +1 (C(s) = C(-s)) in chunks of 2^chunk_log2, evaluated by
+    ``moq_evaluate_cuts`` and merged into one archive (``moq_pareto_front``; sample index =
+    configuration number). Returns (archive, per-objective minimum cut as a torch tensor)."""
+    n, K = inst.n, inst.K
+    if n > 32:
+        raise ValueError("exhaustive_front enumerates 2^(n-1) configurations: n <= 32")
+    total = 1 << (n - 1)
+    chunk = min(total, 1 << chunk_log2)
+    arch = Archive(n, K, capacity=1 << 19, max_batch=chunk)
+    bits = torch.zeros((chunk, inst.W), dtype=torch.int64, device="cuda")
+    cuts = torch.zeros((chunk, K), dtype=torch.int64, device="cuda")
+    lo = torch.full((K,), 2 ** 62, dtype=torch.int64, device="cuda")
+    for c in range(total // chunk):
+        # configuration number q sets spins 1..n-1 from its bits (spin 0 stays +1)
+        bits[:, 0] = (torch.arange(chunk, device="cuda", dtype=torch.int64) + c * chunk) << 1
+        M.moq_evaluate_cuts(inst.handle, bits, chunk, cuts, stream)
+        torch.minimum(lo, cuts.min(dim=0).values, out=lo)
+        arch.merge(cuts, bits, chunk, c * chunk, stream=stream)
+    return arch, lo
+
+
 class Instance:
     """Device copy of an MO-MaxCut instance (``moq_create_instance``)."""
 

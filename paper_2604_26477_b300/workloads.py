@@ -34,6 +34,9 @@ class Instance:
     ej: np.ndarray  # (E,) int32
     w: np.ndarray  # (K, E) int32, row k = objective k
     name: str = ""
+    # per objective, the factor by which the stored integer weights exceed the source's
+    # (None: all 1); a weighted sum over the source's weights takes lambda_k / scale_k
+    objective_scale: np.ndarray | None = None
 
     @property
     def K(self) -> int:
@@ -156,7 +159,8 @@ def app_e_correlated(n: int, density: float, seed: int) -> Instance:
     C = rng.integers(-25, 26, size=iu.size)
     keep = rng.random(iu.size) < density
     w = np.stack([A + B, A - 25 * B, C])[:, keep].astype(np.int32)
-    return Instance(n, iu[keep].astype(np.int32), ju[keep].astype(np.int32), w, name=f"appE_n{n}_d{density}_s{seed}")
+    return Instance(n, iu[keep].astype(np.int32), ju[keep].astype(np.int32), w, name=f"appE_n{n}_d{density}_s{seed}",
+                    objective_scale=np.array([1, 5, 1], np.int64))
 
 
 def dirichlet_lambdas(R: int, K: int, seed: int) -> np.ndarray:

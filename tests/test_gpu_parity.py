@@ -138,6 +138,21 @@ def test_cuts_bit_exact(M, P, oracle, name):
     M.moq_evaluate_cuts(inst.handle, _bits_dev(bits), 0, cuts)  # M = 0 is a no-op
 
 
+@pytest.mark.parametrize("form", ["thread", "warp"])
+@pytest.mark.parametrize("name,M_", [("gnp_n300_dense", 37), ("gnp_n300_dense", 1000), ("reg3_n1024_K3", 300),
+                                     ("heavyhex_K4", 1), ("gnp_n70_K8", 517)])
+def test_cuts_both_forms_bit_exact(M, P, oracle, monkeypatch, form, name, M_):
+    # one thread per sample and one warp per sample (lanes split the edges, shuffle reduction)
+    # give the oracle's exact cuts, K = 2..8, one or many words per sample, ragged blocks
+    monkeypatch.setenv("MOQ_CUTS_FORM", form)
+    src = wl.random_graph(300, 0.3, 5, K=3, wmax=1000) if name == "gnp_n300_dense" else INSTANCES[name]()
+    inst = P.Instance(src)
+    bits = wl.random_sign_bits(M_, src.n, 17)
+    cuts = torch.zeros((M_, src.K), dtype=torch.int64, device="cuda")
+    M.moq_evaluate_cuts(inst.handle, _bits_dev(bits), M_, cuts)
+    assert np.array_equal(cuts.cpu().numpy(), oracle.cuts(src, bits))
+
+
 def test_cuts_every_configuration(M, P, oracle):
     src = wl.random_graph(14, 0.4, 9, K=3)
     inst = P.Instance(src)
@@ -730,3 +745,21 @@ def test_archive_merge_is_the_front_of_the_union(M, P, oracle, K, max_batch):
     assert e.value.code == M.MOQ_ERR_ARG
     for x in (a, b, whole):
         x.close()
+
+
+def test_exhaustive_front_matches_brute_force(M, P, oracle):
+    # the enumeration behind the Appendix E reference fronts (pipeline.exhaustive_front, GPU
+    # cuts and merges in chunks of 2^20) against the oracle's brute force and filter: the same
+    # front, the same hypervolume, the same per-objective minima (n = 22: two chunks)
+    src = wl.app_e_correlated(22, 1.0, 9)
+    inst = P.Instance(src)
+    arch, lo = P.exhaustive_front(inst)
+    gc, gb, gi = arch.copy_out()
+    bits, cuts = oracle.brute_force(src)
+    keep = oracle.pareto_filter(cuts)
+    assert {tuple(v) for v in gc.tolist()} == {tuple(v) for v in cuts[keep].tolist()}
+    assert np.array_equal(lo.cpu().numpy(), cuts.min(axis=0))
+    ref = cuts.min(axis=0) - 1
+    assert arch.hypervolume(ref) == oracle.hypervolume(cuts[keep], ref)
+    assert np.array_equal(oracle.cuts(src, gb), gc)  # each representative has its cut vector
+    arch.close()
