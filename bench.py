@@ -47,6 +47,13 @@ def ops_per_spin_update(mean_degree):
     return mean_degree + 9 + 10 + 7
 
 
+# The paper's float16 form (two replicas per half2 instruction) per pair and step: force d
+# two-lane multiply-adds, Euler update 4, wall and sign 4, eta packed to half2 1, and per
+# replica one Gaussian (Philox 10 + Box-Muller 7, in FP32); per replica update half of that.
+def ops_per_spin_update_fp16(mean_degree):
+    return (mean_degree + 4 + 4 + 1 + 2 * (10 + 7)) / 2
+
+
 def peak_alu_tops():
     """FP32/INT32 lane-op peak: 148 SMs x 128 lanes x 2032 MHz (the maximum SM clock)."""
     return 148 * 128 * 2.032e9 / 1e12
@@ -203,7 +210,7 @@ def gpu_arm(args, rank, world):
     # the replica offset keys the noise so the shards equal one call over the whole range
     first, _ = shard.replica_shard(R * world, rank, world)
     params = M.moq_default_params(variant=w["variant"], steps=T, dt=w["dt"], a0=w["a0"], alpha=w["alpha"],
-                                  init_amp=w["init_amp"], replica_offset=first)
+                                  init_amp=w["init_amp"], replica_offset=first, precision=args.precision)
     nsteps = args.warmup + args.steps
     # inputs resident in HBM before the timed region: one weight-vector batch per step
     lam_all = torch.from_numpy(np.stack([wl.dirichlet_lambdas(R * world, K, 10_000 + s)[first:first + R]
@@ -348,13 +355,16 @@ def gpu_arm(args, rank, world):
            "front_points": arch.size(), "hv": int(hv_b)}
 
     peaks = measured_peaks()
-    ops = ops_per_spin_update(2.0 * src.E / n)
+    fp16 = args.precision == "fp16"
+    ops = (ops_per_spin_update_fp16 if fp16 else ops_per_spin_update)(2.0 * src.E / n)
     sample_avg = samp_s / args.steps
     achieved = ops * R * n * T / sample_avg / 1e12
-    roofline = {"bound": "alu", "kernel": "k_sb_sparse2 (two replicas per thread; k_sb_sparse where that keeps fewer in flight)",
+    roofline = {"bound": "alu", "kernel": "k_sb_sparse_h (FP16, two replicas per half2 lane)" if fp16 else
+                "k_sb_sparse2 (two replicas per thread; k_sb_sparse where that keeps fewer in flight)",
                 "achieved": achieved, "peak": peak_alu_tops(),
                 "unit": "Tops/s", "frac": achieved / peak_alu_tops(),
-                "traffic": profile_traffic("sb_sparse.cu", "sb_sparse_precision_n42_K4.txt"),
+                "traffic": profile_traffic("sb_sparse.cu", "sb_sparse_fp16_precision_n42_K4.txt" if fp16
+                                           else "sb_sparse_precision_n42_K4.txt"),
                 "peak_source": "derived: 148 SMs x 128 FP32/INT32 lanes x 2032 MHz max SM clock",
                 "ops_per_spin_update": ops, "kernel_ms": sample_avg * 1e3,
                 "hbm_peak_measured_gbs": peaks.get("hbm_gbs")}
@@ -1109,8 +1119,12 @@ def fp16_block(args):
 
         step_s, samp_s = _timed_steps(step, args.warmup, nst - args.warmup, flush)
         units = R * src.n * T * (nst - args.warmup)
+        ops = (ops_per_spin_update_fp16 if prec == "fp16" else ops_per_spin_update)(2.0 * src.E / src.n)
         out[prec] = {"value": units / step_s, "ms_per_step": step_s / (nst - args.warmup) * 1e3,
                      "sampling_only_value": units / samp_s, "sampler_ms": samp_s / (nst - args.warmup) * 1e3,
+                     "roofline": {"bound": "alu", "ops_per_spin_update": ops, "achieved": ops * units / samp_s / 1e12,
+                                  "peak": peak_alu_tops(), "unit": "Tops/s",
+                                  "frac": ops * units / samp_s / 1e12 / peak_alu_tops()},
                      "front_points": arch.size(), "hv": int(hv[0])}
     out["sampler_speedup"] = out["fp32"]["sampler_ms"] / out["fp16"]["sampler_ms"]
     arch.close()
@@ -1248,6 +1262,8 @@ def main():
     ap.add_argument("--ttt-rounds", type=int, default=64)
     ap.add_argument("--ttt-seeds", type=int, default=32, help="seeds of the time-to-target medians")
     ap.add_argument("--no-ttt", action="store_true")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"],
+                    help="state and step arithmetic of the precision workload's sampler (fp16: the paper's float16)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the plain-config, float16, chosen-form-batch, batching and dense blocks of the default line")
     ap.add_argument("--cpu-baseline-worker", action="store_true")
@@ -1285,7 +1301,8 @@ def main():
                           f"R={w['R']} uniform-simplex lambda, {w['variant']} T={w['T']} dt={w['dt']} "
                           f"alpha={w['alpha']}, cuts + Pareto + hypervolume per step",
               "n": w["n"], "K": w["K"], "R": w["R"], "T": w["T"], "variant": w["variant"], "dt": w["dt"],
-              "alpha": w["alpha"], "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas x{world}",
+              "alpha": w["alpha"], "precision": args.precision,
+              "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas x{world}",
               "timing": "K steps timed as one region (CUDA events): step s+1 samples on a second stream while step s's "
                         "cuts, merge and hypervolume finish; the hypervolume of every step is read back on the host",
               "prewarm_s": args.prewarm}
@@ -1334,7 +1351,8 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": res["value"], "unit": METRIC, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f16" if args.precision == "fp16" else "f32",
+                "data": "synthetic", "config": config,
                 "roofline": res["roofline"], "cpu_baseline": cpu_base, "e2e": res["e2e"], "clocks": res["clocks"],
                 "gpu_launches": res["gpu_launches"], "sampling_only_value": res["sampling_only_value"],
                 "front_points_last_step": res["front_last"], "hv_last_step": res["hv_last"],

@@ -22,7 +22,7 @@ import torch
 from . import moqaia as M
 
 # (0, 0): one launch of the single-instance sampler per instance (blocks sized per instance)
-CANDIDATES = [(1024, 1), (512, 2), (512, 1), (256, 2), (256, 1), (0, 0)]
+CANDIDATES = [(1024, 1), (512, 2), (512, 1), (256, 2), (256, 1), (512, 4), (256, 4), (0, 0)]
 _CACHE_PATH = os.environ.get("MOQ_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "moqaia_tiles.json"))
 _lock = threading.Lock()
 
@@ -50,7 +50,7 @@ def _store(cache):
 
 def legal(max_n):
     return [(bd, spt) for bd, spt in CANDIDATES
-            if (bd, spt) == (0, 0) or (bd * spt >= max_n and not (spt == 2 and bd > 512))]
+            if (bd, spt) == (0, 0) or (bd * spt >= max_n and not (spt >= 2 and bd > 512))]
 
 
 def tune_batch(batch_handle, ns, reps, K, lam_all, bits_all, params, probe_steps=64, use_cache=True):

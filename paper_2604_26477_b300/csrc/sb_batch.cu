@@ -58,7 +58,7 @@ struct BatchArgs {
 size_t batch_smem_bytes() { return sizeof(float) * 2 * kSlots + sizeof(unsigned) * 2 * kMaxRb + sizeof(unsigned long long) * kWbWords; }
 
 template <int VARIANT, int DMAX, bool NOISE, bool LINEAR, int SPT>
-__global__ void __launch_bounds__(SPT == 2 ? 512 : 1024) k_sb_batch(const BatchArgs a)
+__global__ void __launch_bounds__(SPT >= 2 ? 512 : 1024) k_sb_batch(const BatchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* phiA = reinterpret_cast<float*>(smem_raw);
@@ -344,7 +344,11 @@ cudaError_t launch_batch(const BatchArgs& a, int bd, cudaStream_t st)
 template <int VARIANT, int DMAX, bool NOISE, bool LINEAR>
 cudaError_t launch_spt(const BatchArgs& a, int bd, int spt, cudaStream_t st)
 {
-    return spt == 2 ? launch_batch<VARIANT, DMAX, NOISE, LINEAR, 2>(a, bd, st) : launch_batch<VARIANT, DMAX, NOISE, LINEAR, 1>(a, bd, st);
+    switch (spt) {
+    case 4: return launch_batch<VARIANT, DMAX, NOISE, LINEAR, 4>(a, bd, st);
+    case 2: return launch_batch<VARIANT, DMAX, NOISE, LINEAR, 2>(a, bd, st);
+    default: return launch_batch<VARIANT, DMAX, NOISE, LINEAR, 1>(a, bd, st);
+    }
 }
 
 template <int VARIANT, int DMAX>
@@ -493,10 +497,11 @@ int moq_batch_set_tiles(moq_batch* b, int32_t block_threads, int32_t slots_per_t
         if (items_out) *items_out = b->count;
         return MOQ_OK;
     }
-    if ((block_threads != 256 && block_threads != 512 && block_threads != 1024) || (slots_per_thread != 1 && slots_per_thread != 2))
-        return fail(MOQ_ERR_ARG, "moq_batch_set_tiles: block_threads in {256, 512, 1024}, slots_per_thread in {1, 2} (or 0, 0)");
-    if (slots_per_thread == 2 && block_threads > 512)
-        return fail(MOQ_ERR_ARG, "moq_batch_set_tiles: two slots per thread need block_threads <= 512");
+    if ((block_threads != 256 && block_threads != 512 && block_threads != 1024) ||
+        (slots_per_thread != 1 && slots_per_thread != 2 && slots_per_thread != 4))
+        return fail(MOQ_ERR_ARG, "moq_batch_set_tiles: block_threads in {256, 512, 1024}, slots_per_thread in {1, 2, 4} (or 0, 0)");
+    if (slots_per_thread >= 2 && block_threads > 512)
+        return fail(MOQ_ERR_ARG, "moq_batch_set_tiles: two or four slots per thread need block_threads <= 512");
     if (block_threads * slots_per_thread < b->max_n)
         return fail(MOQ_ERR_ARG, "moq_batch_set_tiles: %d x %d slots cannot hold n=%d", block_threads, slots_per_thread, b->max_n);
     b->bd = block_threads;

@@ -41,7 +41,7 @@ def batch(P):
 
 
 @pytest.mark.parametrize("variant,alpha", [("dsb", 0.15), ("bsb", 0.0)])
-@pytest.mark.parametrize("tile", [(1024, 1), (512, 2), (0, 0)])
+@pytest.mark.parametrize("tile", [(1024, 1), (512, 2), (512, 4), (256, 4), (0, 0)])
 def test_batch_matches_single_instance(M, P, batch, variant, alpha, tile):
     srcs, insts, b = batch
     b.set_tiles(*tile)
@@ -72,11 +72,15 @@ def test_batch_tiles_and_tuner(M, P, batch, tmp_path, monkeypatch):
         b.set_tiles(256, 1)  # 256 slots cannot hold n = 1024
     with pytest.raises(M.MoqError):
         b.set_tiles(1024, 2)
+    with pytest.raises(M.MoqError):
+        b.set_tiles(1024, 4)
     monkeypatch.setenv("MOQ_TUNE_CACHE", str(tmp_path / "tiles.json"))
     from paper_2604_26477_b300 import autotune
     monkeypatch.setattr(autotune, "_CACHE_PATH", str(tmp_path / "tiles.json"))
     tile, timings = b.tune(M.moq_default_params(steps=200, dt=0.5, alpha=0.1), probe_steps=32)
-    assert tile in [(1024, 1), (512, 2), (0, 0)] and set(timings) == {"1024x1", "512x2", "0x0"}
+    legal = autotune.legal(max(s.n for s in srcs))
+    assert tile in legal and set(timings) == {f"{bd}x{spt}" for bd, spt in legal}
+    assert {"1024x1", "512x2", "512x4", "256x4", "0x0"} <= set(timings)
     assert timings[f"{tile[0]}x{tile[1]}"] == min(timings.values())
     tile2, _ = b.tune(M.moq_default_params(steps=200, dt=0.5, alpha=0.1))  # from the cache
     assert tile2 == tile
