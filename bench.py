@@ -805,13 +805,13 @@ def paper_arm(args, rank, world):
         lam = lam_dd[:nw].repeat_interleave(batch, dim=0).contiguous()  # weight vector w for replicas w*3000..
         R = lam.shape[0]
 
-        def run(alpha, n_rounds, steps=T, seed=7):
+        def run(alpha, n_rounds, steps=T, seed=7, precision="fp32"):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             inst = P.Instance(src)
             arch = P.Archive(src.n, K, capacity=1 << 18, max_batch=R)
             buf = P.RoundBuffers(R, src.n, K)
-            params = M.moq_default_params(variant="dsb", steps=steps, dt=dt, alpha=alpha)
+            params = M.moq_default_params(variant="dsb", steps=steps, dt=dt, alpha=alpha, precision=precision)
             trace = []
             for rnd in range(n_rounds):
                 P.sample_round(inst, arch, buf, params, seed, rnd, lam=lam)
@@ -827,11 +827,13 @@ def paper_arm(args, rank, world):
         res = {"weight_vectors": nw, "replicas_per_round": R}
         run(alpha_paper, 1, seed=99)  # untimed: loads every kernel of the pipeline once
         tr_noise, front_noise, secs_noise, ref = run(alpha_paper, rounds)
+        # the same rounds in the paper's float16 (state and step arithmetic in FP16)
+        tr_h, front_h, secs_h, _ = run(alpha_paper, rounds, precision="fp16")
         tr_plain, front_plain, _, _ = run(0.0, rounds)
         tr_rand, front_rand, _, _ = run(0.0, rounds, steps=0)  # uniform random configurations
         total_units += float(R) * src.n * T * rounds
         total_s += secs_noise
-        hv_best = max(tr_noise[-1][2], tr_plain[-1][2], tr_rand[-1][2])
+        hv_best = max(tr_noise[-1][2], tr_h[-1][2], tr_plain[-1][2], tr_rand[-1][2])
 
         def reach(trace, frac_num, frac_den):
             target = (hv_best * frac_num + frac_den - 1) // frac_den
@@ -840,7 +842,8 @@ def paper_arm(args, rank, world):
                     return {"seconds": round(t, 5), "samples": smp}
             return None
 
-        for label, tr, fr in (("ni_dsb_alpha%.2f" % alpha_paper, tr_noise, front_noise), ("dsb_alpha0", tr_plain, front_plain),
+        for label, tr, fr in (("ni_dsb_alpha%.2f" % alpha_paper, tr_noise, front_noise),
+                              ("ni_dsb_alpha%.2f_float16" % alpha_paper, tr_h, front_h), ("dsb_alpha0", tr_plain, front_plain),
                               ("random_sampling", tr_rand, front_rand)):
             res[label] = {"hv_final": int(tr[-1][2]), "hv_ratio": tr[-1][2] / hv_best, "front_points": int(fr),
                           "samples_per_front_point": tr[-1][1] / max(fr, 1),
@@ -852,6 +855,8 @@ def paper_arm(args, rank, world):
             tr, fr, _, _ = run(a, 3)
             sweep["%.2f" % a] = {"hv_ratio": tr[-1][2] / hv_best, "front_points": int(fr)}
         res["alpha_sweep_3_rounds"] = sweep
+        res["float16_end_to_end_s"] = round(secs_h, 5)
+        res["float32_end_to_end_s"] = round(secs_noise, 5)
         res["reference_point"] = [int(v) for v in ref]
         out["instances"]["heavy_hex_like_n42_K%d" % K] = res
     return {"metric": METRIC, "value": total_units / total_s, "unit": METRIC, "n_gpus": world, "steps": rounds,
@@ -1214,8 +1219,12 @@ def chosen_batch_block(args):
             batch.sample(params, 1, 1 + k)
         e1.record()
         torch.cuda.synchronize()
-        thr[label] = {"ms_per_round": e0.elapsed_time(e1) / 3, "value": units * 2000 * 3 / (e0.elapsed_time(e1) / 1e3),
-                      "unit": METRIC}
+        val = units * 2000 * 3 / (e0.elapsed_time(e1) / 1e3)
+        mean_deg = float(np.mean([2.0 * s.E / s.n for s in srcs]))
+        ops = (ops_per_spin_update_fp16 if label.startswith("fp16") else ops_per_spin_update)(mean_deg)
+        thr[label] = {"ms_per_round": e0.elapsed_time(e1) / 3, "value": val, "unit": METRIC,
+                      "roofline": {"bound": "alu", "ops_per_spin_update": ops, "achieved": ops * val / 1e12,
+                                   "peak": peak_alu_tops(), "unit": "Tops/s", "frac": ops * val / 1e12 / peak_alu_tops()}}
     out["batched_round_sampling"] = thr
     batch.close()
     for h in insts:
