@@ -51,6 +51,15 @@ __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a -
 // read from a per-block table of the T values (one shared-memory load per step instead of
 // a multiply-add and a counter update; the same single-rounding formula fills it)
 constexpr int kPumpSchedule = 0, kPumpInline = 1, kPumpTable = 2;
+// The pair and FP16 kernels also come register-capped for two resident blocks of up to 640
+// threads (a pump code + 3; the table pump only serves blocks of up to 256 threads): where the
+// 60-register build fits one such block per SM, the capped build fits two, which hides the
+// per-step barrier (FP16, n = 600: 4.16 against 4.70 ms per launch); the host takes it only where
+// the occupancy API says it keeps more threads resident (n = 450 fits two blocks either way, and
+// the capped build's spills then cost 4 %).
+constexpr int kPumpScheduleCap = 3, kPumpInlineCap = 4;
+__host__ __device__ constexpr int pump_base(int p) { return p >= 3 ? p - 3 : p; }
+constexpr int kCapThreads = 640;
 constexpr int kPumpTableMax = 8192;
 constexpr int kPumpTableMaxThreads = 256;
 
@@ -385,7 +394,7 @@ __device__ __forceinline__ void pair_setup(const SbArgs& a, int tid, int i, int 
 }
 
 template <int VARIANT, int DMAX, bool NOISE, int PUMP>
-__global__ void __launch_bounds__(1024) k_sb_sparse2(const SbArgs a)
+__global__ void __launch_bounds__(PUMP >= 3 ? kCapThreads : 1024, PUMP >= 3 ? 2 : 1) k_sb_sparse2(const SbArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = a.n, Rb = a.Rb, Rp = a.Rb >> 1;
@@ -417,12 +426,12 @@ __global__ void __launch_bounds__(1024) k_sb_sparse2(const SbArgs a)
     const float a0 = a.a0, a0inv = a.a0inv;
     const float* sched = a.schedule;
     const int T = a.T;
-    if (PUMP == kPumpTable) {
+    if (pump_base(PUMP) == kPumpTable) {
         for (int q = tid; q < T; q += blockDim.x) pump_t[q] = fmaf(a0inv, (float)q, -a0);
         __syncthreads();
     }
     auto cm_at = [&](int m, float mf) -> float {
-        return PUMP == kPumpTable ? pump_t[m] : (PUMP == kPumpInline ? fmaf(a0inv, mf, -a0) : (__ldg(sched + m) - a0));
+        return pump_base(PUMP) == kPumpTable ? pump_t[m] : (pump_base(PUMP) == kPumpInline ? fmaf(a0inv, mf, -a0) : (__ldg(sched + m) - a0));
     };
     auto block8 = [&](int m, int r) -> uint4 {
         return NOISE ? Philox4x32::block(make_uint4((uint32_t)(m >> 3), (uint32_t)i, a.rep_off + (uint32_t)r, a.round32), a.key0, a.key1)
@@ -518,6 +527,8 @@ cudaError_t launch_pump2(const SbArgs& a, int pump, dim3 grid, dim3 block, size_
     switch (pump) {
     case kPumpTable: return launch_one2<VARIANT, DMAX, NOISE, kPumpTable>(a, grid, block, smem, st);
     case kPumpInline: return launch_one2<VARIANT, DMAX, NOISE, kPumpInline>(a, grid, block, smem, st);
+    case kPumpInlineCap: return launch_one2<VARIANT, DMAX, NOISE, kPumpInlineCap>(a, grid, block, smem, st);
+    case kPumpScheduleCap: return launch_one2<VARIANT, DMAX, NOISE, kPumpScheduleCap>(a, grid, block, smem, st);
     default: return launch_one2<VARIANT, DMAX, NOISE, kPumpSchedule>(a, grid, block, smem, st);
     }
 }
@@ -561,7 +572,7 @@ __device__ __forceinline__ void sb_step_h(const __half2* rd, __half2* wr, int ti
 }
 
 template <int VARIANT, int DMAX, bool NOISE, int PUMP>
-__global__ void __launch_bounds__(1024) k_sb_sparse_h(const SbArgs a)
+__global__ void __launch_bounds__(PUMP >= 3 ? kCapThreads : 1024, PUMP >= 3 ? 2 : 1) k_sb_sparse_h(const SbArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = a.n, Rb = a.Rb, Rp = a.Rb >> 1;
@@ -592,13 +603,13 @@ __global__ void __launch_bounds__(1024) k_sb_sparse_h(const SbArgs a)
     const float a0 = a.a0, a0inv = a.a0inv;
     const float* sched = a.schedule;
     const int T = a.T;
-    if (PUMP == kPumpTable) {
+    if (pump_base(PUMP) == kPumpTable) {
         for (int q = tid; q < T; q += blockDim.x) pump_t[q] = __float2half2_rn(fmaf(a0inv, (float)q, -a0));
         __syncthreads();
     }
     auto cm_at = [&](int m, float mf) -> __half2 {
-        if (PUMP == kPumpTable) return pump_t[m];
-        return __float2half2_rn(PUMP == kPumpInline ? fmaf(a0inv, mf, -a0) : (__ldg(sched + m) - a0));
+        if (pump_base(PUMP) == kPumpTable) return pump_t[m];
+        return __float2half2_rn(pump_base(PUMP) == kPumpInline ? fmaf(a0inv, mf, -a0) : (__ldg(sched + m) - a0));
     };
     auto block8 = [&](int m, int r) -> uint4 {
         return NOISE ? Philox4x32::block(make_uint4((uint32_t)(m >> 3), (uint32_t)i, a.rep_off + (uint32_t)r, a.round32), a.key0, a.key1)
@@ -693,6 +704,8 @@ cudaError_t launch_pump_h(const SbArgs& a, int pump, dim3 grid, dim3 block, size
     switch (pump) {
     case kPumpTable: return launch_one_h<VARIANT, DMAX, NOISE, kPumpTable>(a, grid, block, smem, st);
     case kPumpInline: return launch_one_h<VARIANT, DMAX, NOISE, kPumpInline>(a, grid, block, smem, st);
+    case kPumpInlineCap: return launch_one_h<VARIANT, DMAX, NOISE, kPumpInlineCap>(a, grid, block, smem, st);
+    case kPumpScheduleCap: return launch_one_h<VARIANT, DMAX, NOISE, kPumpScheduleCap>(a, grid, block, smem, st);
     default: return launch_one_h<VARIANT, DMAX, NOISE, kPumpSchedule>(a, grid, block, smem, st);
     }
 }
@@ -728,6 +741,8 @@ const void* kernel_of(bool pair, int pump)
         switch (pump) {
         case kPumpTable: return (const void*)k_sb_sparse2<VARIANT, (DMAX <= 4 ? DMAX : 4), NOISE, kPumpTable>;
         case kPumpInline: return (const void*)k_sb_sparse2<VARIANT, (DMAX <= 4 ? DMAX : 4), NOISE, kPumpInline>;
+        case kPumpInlineCap: return (const void*)k_sb_sparse2<VARIANT, (DMAX <= 4 ? DMAX : 4), NOISE, kPumpInlineCap>;
+        case kPumpScheduleCap: return (const void*)k_sb_sparse2<VARIANT, (DMAX <= 4 ? DMAX : 4), NOISE, kPumpScheduleCap>;
         default: return (const void*)k_sb_sparse2<VARIANT, (DMAX <= 4 ? DMAX : 4), NOISE, kPumpSchedule>;
         }
     }
@@ -736,6 +751,48 @@ const void* kernel_of(bool pair, int pump)
     case kPumpInline: return (const void*)k_sb_sparse<VARIANT, DMAX, NOISE, kPumpInline>;
     default: return (const void*)k_sb_sparse<VARIANT, DMAX, NOISE, kPumpSchedule>;
     }
+}
+
+template <int VARIANT, int DMAX, bool NOISE>
+const void* kernel_of_h(int pump)
+{
+    switch (pump) {
+    case kPumpTable: return (const void*)k_sb_sparse_h<VARIANT, DMAX, NOISE, kPumpTable>;
+    case kPumpInline: return (const void*)k_sb_sparse_h<VARIANT, DMAX, NOISE, kPumpInline>;
+    case kPumpInlineCap: return (const void*)k_sb_sparse_h<VARIANT, DMAX, NOISE, kPumpInlineCap>;
+    case kPumpScheduleCap: return (const void*)k_sb_sparse_h<VARIANT, DMAX, NOISE, kPumpScheduleCap>;
+    default: return (const void*)k_sb_sparse_h<VARIANT, DMAX, NOISE, kPumpSchedule>;
+    }
+}
+
+template <int VARIANT>
+const void* kernel_of_variant_h(int dmax, bool noise, int pump)
+{
+    switch (dmax) {
+    case 3: return noise ? kernel_of_h<VARIANT, 3, true>(pump) : kernel_of_h<VARIANT, 3, false>(pump);
+    case 4: return noise ? kernel_of_h<VARIANT, 4, true>(pump) : kernel_of_h<VARIANT, 4, false>(pump);
+    default: return noise ? kernel_of_h<VARIANT, 8, true>(pump) : kernel_of_h<VARIANT, 8, false>(pump);
+    }
+}
+
+// the register-capped build where it keeps more blocks resident; MOQ_SB_CAP = 0 / 1 forces the
+// choice (for blocks of at most 640 threads without the pump table)
+bool cap_choice(bool more_resident)
+{
+    if (const char* env = getenv("MOQ_SB_CAP")) return atoi(env) != 0;
+    return more_resident;
+}
+
+// resident blocks per SM of a kernel instance at the given block shape (0 if the query fails)
+int resident_blocks(const void* k, int threads, size_t smem)
+{
+    int blocks = 0;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, threads, smem) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return blocks;
 }
 
 template <int VARIANT>
@@ -834,8 +891,14 @@ extern "C" int moq_sample(const moq_instance* inst, const float* lambda, int32_t
         const int Rp = choose_rb(a.n, (R + 1) / 2);
         a.Rb = 2 * Rp;
         const int threads = a.n * Rp;
-        const int pump = p->schedule ? kPumpSchedule : (a.T <= kPumpTableMax && threads <= kPumpTableMaxThreads ? kPumpTable : kPumpInline);
+        int pump = p->schedule ? kPumpSchedule : (a.T <= kPumpTableMax && threads <= kPumpTableMaxThreads ? kPumpTable : kPumpInline);
         const size_t smem = sb_smem_bytes_h(a.Rb, a.W, pump == kPumpTable ? a.T : 0);
+        if (pump != kPumpTable && threads <= kCapThreads) {
+            auto kof = [&](int pu) {
+                return p->variant == MOQ_DSB ? kernel_of_variant_h<MOQ_DSB>(dmax, noise, pu) : kernel_of_variant_h<MOQ_BSB>(dmax, noise, pu);
+            };
+            if (cap_choice(resident_blocks(kof(pump + 3), threads, smem) > resident_blocks(kof(pump), threads, smem))) pump += 3;
+        }
         const dim3 block(threads), grid((unsigned)ceil_div(R, a.Rb));
         const cudaError_t e = (p->variant == MOQ_DSB) ? launch_variant_h<MOQ_DSB>(a, dmax, noise, pump, grid, block, smem, as_stream(stream))
                                                       : launch_variant_h<MOQ_BSB>(a, dmax, noise, pump, grid, block, smem, as_stream(stream));
@@ -864,7 +927,15 @@ extern "C" int moq_sample(const moq_instance* inst, const float* lambda, int32_t
         sh.smem = pair ? sb_smem_bytes2(sh.Rb, a.W, sh.pump == kPumpTable ? a.T : 0) : sb_smem_bytes(sh.Rb, a.W, sh.pump == kPumpTable ? a.T : 0);
         return sh;
     };
-    const Shape one = shape_of(false), two = shape_of(true);
+    const Shape one = shape_of(false);
+    Shape two = shape_of(true);
+    if (dmax <= 4 && two.pump != kPumpTable && two.threads <= kCapThreads) {
+        auto kof = [&](int pu) {
+            return p->variant == MOQ_DSB ? kernel_of_variant<MOQ_DSB>(dmax, noise, true, pu) : kernel_of_variant<MOQ_BSB>(dmax, noise, true, pu);
+        };
+        if (cap_choice(resident_blocks(kof(two.pump + 3), two.threads, two.smem) > resident_blocks(kof(two.pump), two.threads, two.smem)))
+            two.pump += 3;
+    }
     // two replicas per thread (degree bound <= 4) when that keeps more replicas in flight per
     // SM (n = 42: 8 blocks of 6 against 10 of 3; n = 1024: one block either way; n = 600: 2
     // against 2, where the one-replica form hides latency with twice the warps) and its grid

@@ -180,3 +180,23 @@ def test_fp16_rejects_what_it_does_not_run(M, P):
     with pytest.raises(M.MoqError) as e:
         M.moq_sample(inst.handle, lam, 8, M.moq_default_params(precision=7), 0, 0, bits)
     assert e.value.code == M.MOQ_ERR_ARG
+
+
+@pytest.mark.parametrize("prec", ["fp16", "fp32"])
+@pytest.mark.parametrize("n,R", [(600, 4096), (520, 301), (300, 2000)])
+def test_register_capped_build_gives_the_same_bits(M, P, monkeypatch, prec, n, R):
+    # blocks of up to 640 threads may run a register-capped build of the pair / FP16 kernels (two
+    # resident blocks per SM): the same arithmetic, so the same samples and final state
+    src = wl.random_regular(n, 41, K=3)
+    inst = P.Instance(src)
+    lam = _dev(wl.dirichlet_lambdas(R, 3, 4))
+    out = {}
+    for cap in ("0", "1"):
+        monkeypatch.setenv("MOQ_SB_CAP", cap)
+        monkeypatch.setenv("MOQ_SB_PAIR", "1")
+        xo = torch.zeros((R, n), device="cuda")
+        bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+        p = M.moq_default_params(steps=203, dt=0.5, alpha=0.1, precision=prec, x_out=xo)
+        M.moq_sample(inst.handle, lam, R, p, 6, 1, bits)
+        out[cap] = (bits.cpu(), xo.cpu())
+    assert torch.equal(out["0"][0], out["1"][0]) and torch.equal(out["0"][1], out["1"][1])
