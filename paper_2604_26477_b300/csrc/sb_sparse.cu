@@ -551,6 +551,23 @@ __host__ __device__ inline size_t sb_smem_bytes_h(int Rb, int W, int pump_table_
            align_up(sizeof(unsigned long long) * (size_t)Rb * W, 16) + sizeof(__half2) * (size_t)pump_table_steps;
 }
 
+// The FP16 Euler step of a replica pair on its force f, lane by lane: update, then the wall
+// (lanes with |x| > 1 take x = sgn(x), the dSB phi of x, and y = 0). Returns sgn(x) as +-1 halves.
+template <bool NOISE>
+__device__ __forceinline__ uint32_t h2_update(__half2 f, __half2 cm, __half2 eta, __half2 dt, __half2 kappa, __half2 dta0, __half2& x,
+                                              __half2& y)
+{
+    y = __hfma2(dt, __hfma2(cm, x, f), y);
+    if (NOISE) y = __hfma2(kappa, eta, y);
+    x = __hfma2(dta0, y, x);
+    const uint32_t xb = h2_bits(x);
+    const uint32_t sg = (xb & 0x80008000u) | 0x3C003C00u;
+    const uint32_t over = __hgt2_mask(__habs2(x), __float2half2_rn(1.0f));
+    x = bits_h2((over & sg) | (~over & xb));
+    y = bits_h2(~over & h2_bits(y));
+    return sg;
+}
+
 template <int VARIANT, int DMAX, bool NOISE>
 __device__ __forceinline__ void sb_step_h(const __half2* rd, __half2* wr, int tid, const __half2 (&jc)[DMAX], const int (&nb)[DMAX],
                                           __half2 cm, __half2 eta, __half2 dt, __half2 kappa, __half2 dta0, __half2& x, __half2& y)
@@ -558,15 +575,7 @@ __device__ __forceinline__ void sb_step_h(const __half2* rd, __half2* wr, int ti
     __half2 f = __float2half2_rn(0.0f);
 #pragma unroll
     for (int d = 0; d < DMAX; ++d) f = __hfma2(jc[d], rd[nb[d]], f);
-    y = __hfma2(dt, __hfma2(cm, x, f), y);
-    if (NOISE) y = __hfma2(kappa, eta, y);
-    x = __hfma2(dta0, y, x);
-    // wall: lanes with |x| > 1 take x = sgn(x) (the dSB phi of x) and y = 0
-    const uint32_t xb = h2_bits(x);
-    const uint32_t sg = (xb & 0x80008000u) | 0x3C003C00u;
-    const uint32_t over = __hgt2_mask(__habs2(x), __float2half2_rn(1.0f));
-    x = bits_h2((over & sg) | (~over & xb));
-    y = bits_h2(~over & h2_bits(y));
+    const uint32_t sg = h2_update<NOISE>(f, cm, eta, dt, kappa, dta0, x, y);
     wr[tid] = VARIANT == MOQ_DSB ? bits_h2(sg) : x;
     __syncthreads();
 }
@@ -685,6 +694,194 @@ __global__ void __launch_bounds__(PUMP >= 3 ? kCapThreads : 1024, PUMP >= 3 ? 2 
     if (act1) {
         if (a.x_out) a.x_out[(int64_t)r1 * n + i] = xf.y;
         if (a.y_out) a.y_out[(int64_t)r1 * n + i] = yf.y;
+    }
+}
+
+// Four replicas per thread (two half2 pairs, A = (r0, r0 + 1), B = (r0 + 2, r0 + 3)) for large
+// graphs, where one block of n threads fills an SM: one 8-byte gather brings a neighbour's phi of
+// all four replicas, and the barrier, pump value and loop control serve four updates. Each
+// replica's arithmetic and counters are those of k_sb_sparse_h, so both give the same bits.
+__host__ __device__ inline size_t sb_smem_bytes_h4(int Rb, int W, int pump_table_steps)
+{
+    return sizeof(uint2) * 2 * kPhiStride + align_up(sizeof(unsigned) * 2 * Rb, 16) +
+           align_up(sizeof(unsigned long long) * (size_t)Rb * W, 16) + sizeof(__half2) * (size_t)pump_table_steps;
+}
+
+template <int VARIANT, int DMAX, bool NOISE>
+__device__ __forceinline__ void sb_step_h4(const uint2* rd, uint2* wr, int tid, const __half2 (&ja)[DMAX], const __half2 (&jb)[DMAX],
+                                           const int (&nb)[DMAX], __half2 cm, __half2 ea, __half2 eb, __half2 dt, __half2 kappa,
+                                           __half2 dta0, __half2& xa, __half2& ya, __half2& xb, __half2& yb)
+{
+    __half2 fa = __float2half2_rn(0.0f), fb = fa;
+#pragma unroll
+    for (int d = 0; d < DMAX; ++d) {
+        const uint2 ph = rd[nb[d]];
+        fa = __hfma2(ja[d], bits_h2(ph.x), fa);
+        fb = __hfma2(jb[d], bits_h2(ph.y), fb);
+    }
+    const uint32_t sa = h2_update<NOISE>(fa, cm, ea, dt, kappa, dta0, xa, ya);
+    const uint32_t sg = h2_update<NOISE>(fb, cm, eb, dt, kappa, dta0, xb, yb);
+    wr[tid] = VARIANT == MOQ_DSB ? make_uint2(sa, sg) : make_uint2(h2_bits(xa), h2_bits(xb));
+    __syncthreads();
+}
+
+template <int VARIANT, int DMAX, bool NOISE, int PUMP>
+__global__ void __launch_bounds__(1024) k_sb_sparse_h4(const SbArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = a.n, Rb = a.Rb, Rq = a.Rb >> 2;
+    uint2* phiA = reinterpret_cast<uint2*>(smem_raw);
+    uint2* phiB = phiA + kPhiStride;
+    unsigned* red = reinterpret_cast<unsigned*>(phiB + kPhiStride);  // 2 * Rb
+    unsigned long long* wb = reinterpret_cast<unsigned long long*>(smem_raw + sizeof(uint2) * 2 * kPhiStride +
+                                                                   align_up(sizeof(unsigned) * 2 * Rb, 16));
+    __half2* pump_t = reinterpret_cast<__half2*>(reinterpret_cast<unsigned char*>(wb) +
+                                                 align_up(sizeof(unsigned long long) * (size_t)Rb * a.W, 16));
+    const int tid = threadIdx.x;
+    const int slot = tid / Rq;
+    const int lq = tid - slot * Rq;
+    const int i = a.slot_spin[slot];
+    const int r0 = blockIdx.x * Rb + 4 * lq;
+    // both pairs set up as pairs 2 lq and 2 lq + 1 of a block of 2 Rq pairs
+    float j0[DMAX], j1[DMAX];
+    int nb[DMAX];
+    float x0, y0, x1, y1;
+    __half2 ja[DMAX], jb[DMAX];
+    pair_setup<DMAX>(a, tid, i, 2 * lq, 2 * Rq, r0, red, j0, j1, nb, x0, y0, x1, y1);
+#pragma unroll
+    for (int d = 0; d < DMAX; ++d) ja[d] = __floats2half2_rn(j0[d], j1[d]);
+    __half2 xa = __floats2half2_rn(x0, x1), ya = __floats2half2_rn(y0, y1);
+    __syncthreads();  // the reduction words are reused by the second pair
+    pair_setup<DMAX>(a, tid, i, 2 * lq + 1, 2 * Rq, r0 + 2, red, j0, j1, nb, x0, y0, x1, y1);
+#pragma unroll
+    for (int d = 0; d < DMAX; ++d) {
+        jb[d] = __floats2half2_rn(j0[d], j1[d]);
+        nb[d] >>= 1;  // pair index 2 (slot Rq + lq) + 1 -> quad index slot Rq + lq
+    }
+    __half2 xb = __floats2half2_rn(x0, x1), yb = __floats2half2_rn(y0, y1);
+    phiA[tid] = VARIANT == MOQ_DSB ? make_uint2((h2_bits(xa) & 0x80008000u) | 0x3C003C00u, (h2_bits(xb) & 0x80008000u) | 0x3C003C00u)
+                                   : make_uint2(h2_bits(xa), h2_bits(xb));
+    __syncthreads();
+    const __half2 dt2 = __float2half2_rn(a.dt), kappa2 = __float2half2_rn(a.kappa), dta02 = __float2half2_rn(a.dt * a.a0);
+    const float a0 = a.a0, a0inv = a.a0inv;
+    const float* sched = a.schedule;
+    const int T = a.T;
+    if (pump_base(PUMP) == kPumpTable) {
+        for (int q = tid; q < T; q += blockDim.x) pump_t[q] = __float2half2_rn(fmaf(a0inv, (float)q, -a0));
+        __syncthreads();
+    }
+    auto cm_at = [&](int m, float mf) -> __half2 {
+        if (pump_base(PUMP) == kPumpTable) return pump_t[m];
+        return __float2half2_rn(pump_base(PUMP) == kPumpInline ? fmaf(a0inv, mf, -a0) : (__ldg(sched + m) - a0));
+    };
+    auto block8 = [&](int m, int r) -> uint4 {
+        return NOISE ? Philox4x32::block(make_uint4((uint32_t)(m >> 3), (uint32_t)i, a.rep_off + (uint32_t)r, a.round32), a.key0, a.key1)
+                     : make_uint4(0u, 0u, 0u, 0u);
+    };
+    auto noise4 = [&](uint32_t wa, uint32_t wbb, uint32_t va, uint32_t vb, __half2 (&eg)[4]) {
+        if (NOISE) {
+            const float2 p = box_muller16(wa), q = box_muller16(wbb), u = box_muller16(va), v = box_muller16(vb);
+            eg[0] = __floats2half2_rn(p.x, u.x);
+            eg[1] = __floats2half2_rn(p.y, u.y);
+            eg[2] = __floats2half2_rn(q.x, v.x);
+            eg[3] = __floats2half2_rn(q.y, v.y);
+        }
+    };
+    auto step = [&](const uint2* rd, uint2* wr, __half2 cm, __half2 ea, __half2 eb) {
+        sb_step_h4<VARIANT, DMAX, NOISE>(rd, wr, tid, ja, jb, nb, cm, ea, eb, dt2, kappa2, dta02, xa, ya, xb, yb);
+    };
+    auto four_steps = [&](int m, float mf, const __half2 (&ga)[4], const __half2 (&gb)[4]) {
+        step(phiA, phiB, cm_at(m, mf), ga[0], gb[0]);
+        step(phiB, phiA, cm_at(m + 1, mf + 1.0f), ga[1], gb[1]);
+        step(phiA, phiB, cm_at(m + 2, mf + 2.0f), ga[2], gb[2]);
+        step(phiB, phiA, cm_at(m + 3, mf + 3.0f), ga[3], gb[3]);
+    };
+    auto noise_at = [&](int m, __half2 (&ga)[4], __half2 (&gb)[4]) {
+        if (NOISE) {
+            const uint4 o0 = block8(m, r0), o1 = block8(m, r0 + 1), o2 = block8(m, r0 + 2), o3 = block8(m, r0 + 3);
+            const bool hi = (m & 4) != 0;
+            noise4(hi ? o0.z : o0.x, hi ? o0.w : o0.y, hi ? o1.z : o1.x, hi ? o1.w : o1.y, ga);
+            noise4(hi ? o2.z : o2.x, hi ? o2.w : o2.y, hi ? o3.z : o3.x, hi ? o3.w : o3.y, gb);
+        }
+    };
+    const __half2 zero2 = __float2half2_rn(0.0f);
+    int m = 0;
+    float mf = 0.0f;
+    if (NOISE) {
+        for (; m + 8 <= T; m += 8) {
+            const uint4 o0 = block8(m, r0), o1 = block8(m, r0 + 1), o2 = block8(m, r0 + 2), o3 = block8(m, r0 + 3);
+            __half2 ga[4], gb[4];
+            noise4(o0.x, o0.y, o1.x, o1.y, ga);
+            noise4(o2.x, o2.y, o3.x, o3.y, gb);
+            four_steps(m, mf, ga, gb);
+            noise4(o0.z, o0.w, o1.z, o1.w, ga);
+            noise4(o2.z, o2.w, o3.z, o3.w, gb);
+            four_steps(m + 4, mf + 4.0f, ga, gb);
+            mf += 8.0f;
+        }
+    }
+    for (; m + 4 <= T; m += 4) {
+        __half2 ga[4] = {zero2, zero2, zero2, zero2}, gb[4] = {zero2, zero2, zero2, zero2};
+        noise_at(m, ga, gb);
+        four_steps(m, mf, ga, gb);
+        mf += 4.0f;
+    }
+    if (m < T) {
+        __half2 ga[4] = {zero2, zero2, zero2, zero2}, gb[4] = {zero2, zero2, zero2, zero2};
+        noise_at(m, ga, gb);
+        step(phiA, phiB, cm_at(m, mf), ga[0], gb[0]);
+        if (m + 1 < T) step(phiB, phiA, cm_at(m + 1, mf + 1.0f), ga[1], gb[1]);
+        if (m + 2 < T) step(phiA, phiB, cm_at(m + 2, mf + 2.0f), ga[2], gb[2]);
+    }
+    const float2 xfa = __half22float2(xa), yfa = __half22float2(ya), xfb = __half22float2(xb), yfb = __half22float2(yb);
+    const float xf[4] = {xfa.x, xfa.y, xfb.x, xfb.y}, yf[4] = {yfa.x, yfa.y, yfb.x, yfb.y};
+    const int W = a.W;
+    for (int t = tid; t < Rb * W; t += blockDim.x) wb[t] = 0ull;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (xf[q] < 0.0f) atomicOr(&wb[(4 * lq + q) * W + (i >> 6)], 1ull << (i & 63));
+    __syncthreads();
+    for (int t = tid; t < Rb * W; t += blockDim.x) {
+        const int r2 = blockIdx.x * Rb + t / W;
+        if (r2 < a.R) a.bits[(int64_t)r2 * W + (t % W)] = wb[t];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (r0 + q < a.R) {
+            if (a.x_out) a.x_out[(int64_t)(r0 + q) * n + i] = xf[q];
+            if (a.y_out) a.y_out[(int64_t)(r0 + q) * n + i] = yf[q];
+        }
+}
+
+template <int VARIANT, int DMAX, bool NOISE, int PUMP>
+cudaError_t launch_one_h4(const SbArgs& a, dim3 grid, dim3 block, size_t smem, cudaStream_t st)
+{
+    auto k = k_sb_sparse_h4<VARIANT, DMAX, NOISE, PUMP>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, block, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int VARIANT, int DMAX, bool NOISE>
+cudaError_t launch_pump_h4(const SbArgs& a, int pump, dim3 grid, dim3 block, size_t smem, cudaStream_t st)
+{
+    switch (pump) {
+    case kPumpTable: return launch_one_h4<VARIANT, DMAX, NOISE, kPumpTable>(a, grid, block, smem, st);
+    case kPumpInline: return launch_one_h4<VARIANT, DMAX, NOISE, kPumpInline>(a, grid, block, smem, st);
+    default: return launch_one_h4<VARIANT, DMAX, NOISE, kPumpSchedule>(a, grid, block, smem, st);
+    }
+}
+
+// quads for degree bounds 3 and 4
+template <int VARIANT>
+cudaError_t launch_variant_h4(const SbArgs& a, int dmax, bool noise, int pump, dim3 grid, dim3 block, size_t smem, cudaStream_t st)
+{
+    switch (dmax) {
+    case 3: return noise ? launch_pump_h4<VARIANT, 3, true>(a, pump, grid, block, smem, st) : launch_pump_h4<VARIANT, 3, false>(a, pump, grid, block, smem, st);
+    case 4: return noise ? launch_pump_h4<VARIANT, 4, true>(a, pump, grid, block, smem, st) : launch_pump_h4<VARIANT, 4, false>(a, pump, grid, block, smem, st);
+    default: return cudaErrorInvalidValue;
     }
 }
 
@@ -887,6 +1084,24 @@ extern "C" int moq_sample(const moq_instance* inst, const float* lambda, int32_t
     const int dmax = md <= 3 ? 3 : (md <= 4 ? 4 : (md <= 8 ? 8 : 16));
     const bool noise = p->alpha != 0.0f;
     if (p->precision == MOQ_PREC_FP16) {
+        // large graphs (one block of more than 640 threads per SM): four replicas per thread when
+        // the grid still covers the GPU (MOQ_SB_QUAD = 0 / 1 forces the choice)
+        {
+            const int Rq = choose_rb(a.n, (R + 3) / 4);
+            bool quad = dmax <= 4 && a.n * choose_rb(a.n, (R + 1) / 2) > kCapThreads && ceil_div(R, 4 * Rq) >= 148;
+            if (const char* env = getenv("MOQ_SB_QUAD")) quad = atoi(env) != 0 && dmax <= 4;
+            if (quad) {
+                a.Rb = 4 * Rq;
+                const int threads = a.n * Rq;
+                const int pump = p->schedule ? kPumpSchedule : (a.T <= kPumpTableMax && threads <= kPumpTableMaxThreads ? kPumpTable : kPumpInline);
+                const size_t smem = sb_smem_bytes_h4(a.Rb, a.W, pump == kPumpTable ? a.T : 0);
+                const dim3 block(threads), grid((unsigned)ceil_div(R, a.Rb));
+                const cudaError_t e = (p->variant == MOQ_DSB) ? launch_variant_h4<MOQ_DSB>(a, dmax, noise, pump, grid, block, smem, as_stream(stream))
+                                                              : launch_variant_h4<MOQ_BSB>(a, dmax, noise, pump, grid, block, smem, as_stream(stream));
+                if (e != cudaSuccess) return cuda_fail(e, "moq_sample launch (FP16, four replicas per thread)");
+                return MOQ_OK;
+            }
+        }
         // pairs of replicas per thread, replicas per block as for the FP32 pair form
         const int Rp = choose_rb(a.n, (R + 1) / 2);
         a.Rb = 2 * Rp;

@@ -200,3 +200,45 @@ def test_register_capped_build_gives_the_same_bits(M, P, monkeypatch, prec, n, R
         M.moq_sample(inst.handle, lam, R, p, 6, 1, bits)
         out[cap] = (bits.cpu(), xo.cpu())
     assert torch.equal(out["0"][0], out["1"][0]) and torch.equal(out["0"][1], out["1"][1])
+
+
+@pytest.mark.parametrize("variant,alpha", [("dsb", 0.1), ("bsb", 0.0), ("bsb", 0.2)])
+@pytest.mark.parametrize("n,d,R", [(700, 3, 1021), (1024, 3, 600), (300, 4, 999), (42, 3, 517)])
+def test_fp16_quads_give_the_same_bits_as_pairs(M, P, monkeypatch, variant, alpha, n, d, R):
+    # four replicas per thread (two FP16 pairs, taken by default for large graphs; MOQ_SB_QUAD
+    # forces either form) run each replica's arithmetic and noise counters of the pair form:
+    # same samples and final state, ragged replica counts and step counts included
+    src = wl.heavy_hex_like(1000, K=3) if n == 42 else wl.random_regular(n, 43, K=3, d=d)
+    inst = P.Instance(src)
+    lam = _dev(wl.dirichlet_lambdas(R, 3, 5))
+    out = {}
+    for quad in ("0", "1"):
+        monkeypatch.setenv("MOQ_SB_QUAD", quad)
+        xo = torch.zeros((R, n), device="cuda")
+        yo = torch.zeros((R, n), device="cuda")
+        bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+        p = M.moq_default_params(variant=variant, steps=203, dt=0.5, alpha=alpha, precision="fp16", x_out=xo, y_out=yo)
+        M.moq_sample(inst.handle, lam, R, p, 7, 2, bits)
+        out[quad] = (bits.cpu(), xo.cpu(), yo.cpu())
+    for a, b in zip(out["0"], out["1"]):
+        assert torch.equal(a, b)
+
+
+def test_fp16_quads_from_a_given_state(M, P, monkeypatch):
+    # a given initial (x, y) reaches the same place in both forms
+    n, R = 800, 403
+    src = wl.random_regular(n, 44, K=3)
+    inst = P.Instance(src)
+    lam = _dev(wl.dirichlet_lambdas(R, 3, 6))
+    g = torch.Generator().manual_seed(3)
+    x0 = (torch.rand((R, n), generator=g) - 0.5).cuda()
+    y0 = (0.2 * torch.randn((R, n), generator=g)).cuda()
+    out = {}
+    for quad in ("0", "1"):
+        monkeypatch.setenv("MOQ_SB_QUAD", quad)
+        xo = torch.zeros((R, n), device="cuda")
+        bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+        p = M.moq_default_params(steps=150, dt=0.5, alpha=0.1, precision="fp16", x_init=x0, y_init=y0, x_out=xo)
+        M.moq_sample(inst.handle, lam, R, p, 8, 0, bits)
+        out[quad] = (bits.cpu(), xo.cpu())
+    assert torch.equal(out["0"][0], out["1"][0]) and torch.equal(out["0"][1], out["1"][1])
