@@ -114,6 +114,21 @@ int moq_create_instance(int32_t n, int32_t K, int64_t E, const int32_t* ei, cons
  * rest is moq_create_instance. Errors: MOQ_ERR_ARG (n outside [2, 65536], K outside
  * [2, 8], NULL), then those of moq_create_instance. Synchronises `stream`. */
 int moq_create_instance_dense(int32_t n, int32_t K, const int32_t* J_upper, void* stream, moq_instance** out);
+/* The sparse samplers' memory layout as moq_create_instance chooses it for graphs of n <= 1024
+ * with degrees <= 8 (an implementation detail with no counterpart in the paper): the slot of
+ * each spin in the samplers' shared-memory state and the order in which each spin gathers its
+ * neighbours, chosen by a seeded local search against shared-memory bank conflicts (a warp's
+ * 4-byte reads conflict-free when their words differ modulo 32, 8-byte reads when each
+ * half-warp's differ modulo 16). Gather order changes only the order of the FP32 force sums.
+ * Host only (no GPU, no allocation visible to the caller). Out: slot_spin[n] (slot -> spin);
+ * gather[2E] (rows in spin order, row i holding spin i's neighbours in gather order, row
+ * lengths the degrees); passes[4] or NULL: 8-byte and 4-byte shared-memory passes of one
+ * gather step over all warps for the column layout, then for the chosen one. Setting
+ * MOQ_SB_LAYOUT=0 in the environment makes moq_create_instance keep slots by decreasing
+ * degree and rows by column. Errors: MOQ_ERR_ARG (NULL outputs), MOQ_ERR_UNSUPPORTED (n
+ * outside [2, 1024], a degree above 8, an invalid or repeated edge, E = 0). */
+int moq_plan_gather_layout(int32_t n, int64_t E, const int32_t* ei, const int32_t* ej, int32_t* slot_spin, int32_t* gather,
+                           int64_t* passes);
 void moq_destroy_instance(moq_instance* inst);
 int moq_instance_get_info(const moq_instance* inst, moq_instance_info* out);
 

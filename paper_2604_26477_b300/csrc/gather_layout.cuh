@@ -1,0 +1,376 @@
+// Host-side choice of the on-chip samplers' slot order and of each spin's neighbour order, made
+// against shared-memory bank conflicts in the neighbour gathers of the force (the coupling sums
+// of Eq. 4 and 6).
+//
+// In the sparse samplers, thread t of a block of n * Rb threads holds spin slot_spin[t / Rb] for
+// replica lane t % Rb and, in gather round d, reads the phi word spin_slot[c] * Rb + t % Rb of its
+// d-th neighbour c in CSR order (its own word past its degree). Shared memory serves a warp's
+// 4-byte reads in one pass when their words are distinct modulo 32 (the banks), and a warp's
+// 8-byte reads in one pass per half-warp when each half's words are distinct modulo 16; a word
+// read by several lanes is broadcast, and each further distinct word in one bank costs a pass.
+// On random 3-regular graphs of n = 1024 the column order costs 18.4 passes per warp for the
+// three 8-byte gathers of a step against 6 without conflicts, which left the FP32 pair sampler
+// bound by shared memory (a conflict-free circulant graph of the same size ran 18 % faster).
+//
+// Two local searches, both from the degree-sorted slot order with neighbours by column, with a
+// fixed-seed generator so that the layout is a pure function of the graph:
+//  1. slots: exchanges of two spins' slots, judged by the bank loads of every half-warp (8-byte
+//     words modulo 16) and warp (4-byte words modulo 32) summed over the rounds. Their sum of
+//     squares is least when every bank takes one read per round, the condition under which the
+//     rounds can be ordered without a conflict (a D-regular bipartite multigraph of threads and
+//     banks splits into D perfect matchings, König). Annealed to zero temperature.
+//  2. orders: each visited spin takes the order of its reads (among all orders when the degree
+//     is at most 4) that gives the fewest passes, 8-byte passes weighted 4 to 1 over 4-byte ones
+//     (the FP32 pair and float16 four-replica forms gather 8 bytes, the single-replica and
+//     float16 pair forms 4); slot exchanges judged by the same count follow.
+// Neighbour order changes only the order of the force's FP32 sums; slot order changes nothing.
+#pragma once
+
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+namespace moq {
+
+// Replicas per block whose warps are fullest among blocks of up to about 256 threads (the
+// smaller on ties): the samplers' choice when the replica count does not limit it.
+inline int fullest_warp_rb(int n)
+{
+    const int hi = std::max(1, std::min(32, 256 / n));
+    int rb = 1;
+    double best = -1.0;
+    for (int c = 1; c <= hi; ++c) {
+        const int threads = n * c;
+        const double util = (double)threads / (32.0 * (double)((threads + 31) / 32));
+        if (util > best + 0.01) {
+            best = util;
+            rb = c;
+        }
+    }
+    return rb;
+}
+
+class GatherLayout {
+public:
+    static constexpr int kMaxDeg = 8;
+
+    // nbr: n rows of kMaxDeg entries, the first deg[i] of row i its neighbours (ascending)
+    GatherLayout(int n, int rb, std::vector<int32_t> nbr, std::vector<int32_t> deg)
+        : n_(n), rb_(rb), nbr_(std::move(nbr)), deg_(std::move(deg))
+    {
+        T_ = n_ * rb_;
+        D_ = 0;
+        for (int i = 0; i < n_; ++i) D_ = std::max(D_, (int)deg_[i]);
+        spin_at_.resize(n_);
+        for (int i = 0; i < n_; ++i) spin_at_[i] = i;
+        std::stable_sort(spin_at_.begin(), spin_at_.end(), [&](int32_t a, int32_t b) { return deg_[a] > deg_[b]; });
+        slot_of_.resize(n_);
+        for (int s = 0; s < n_; ++s) slot_of_[spin_at_[s]] = s;
+        H_ = (T_ + 15) / 16;
+        W_ = (T_ + 31) / 32;
+        c8_.assign((size_t)H_ * std::max(D_, 1), 0);
+        c4_.assign((size_t)W_ * std::max(D_, 1), 0);
+        stamp_.assign(std::max(T_, 1), 0u);
+        refresh();
+    }
+
+    int64_t passes8() const { return sum(c8_); }
+    int64_t passes4() const { return sum(c4_); }
+    int64_t ideal8() const { return (int64_t)H_ * D_; }
+    int64_t ideal4() const { return (int64_t)W_ * D_; }
+    const std::vector<int32_t>& slot_spin() const { return spin_at_; }
+    const std::vector<int32_t>& neighbours() const { return nbr_; }  // gather order, rows of kMaxDeg
+
+    void balance_slots(int64_t moves, uint64_t seed, double temp)
+    {
+        if (n_ < 2 || D_ == 0) return;
+        l8_.assign((size_t)H_ * 16, 0);
+        l4_.assign((size_t)W_ * 32, 0);
+        for (int i = 0; i < n_; ++i)
+            for (int d = 0; d < D_; ++d) load(i, d, +1);
+        uint64_t s = seed;
+        std::vector<int32_t> reads;
+        for (int64_t m = 0; m < moves; ++m) {
+            const uint64_t r = next(s);
+            const int u = (int)((r >> 8) % (uint64_t)n_);
+            int v = (int)((r >> 36) % (uint64_t)(n_ - 1));
+            if (v >= u) ++v;
+            reads.clear();
+            moving_reads(u, reads);
+            moving_reads(v, reads);
+            std::sort(reads.begin(), reads.end());
+            reads.erase(std::unique(reads.begin(), reads.end()), reads.end());
+            int64_t delta = 0;
+            for (int32_t q : reads) delta += load(q >> 4, q & 15, -1);
+            swap_slots(u, v);
+            for (int32_t q : reads) delta += load(q >> 4, q & 15, +1);
+            bool keep = delta <= 0;
+            const double t = temp * (1.0 - (double)m / (double)moves);
+            if (!keep && t > 0.0) keep = (double)(next(s) >> 11) * 0x1.0p-53 < std::exp(-(double)delta / t);
+            if (!keep) {
+                for (int32_t q : reads) load(q >> 4, q & 15, -1);
+                swap_slots(u, v);
+                for (int32_t q : reads) load(q >> 4, q & 15, +1);
+            }
+        }
+        refresh();
+    }
+
+    // `sweeps` passes over all spins choosing each one's best read order, then `slot_moves`
+    // exchanges of two slots, both by the weighted pass count
+    void order_reads(int sweeps, int64_t slot_moves, uint64_t seed)
+    {
+        if (D_ < 1) return;
+        std::vector<int> hs, ws;
+        uint64_t rs = seed ^ 0x5851F42D4C957F2Dull;
+        for (int sw = 0; sw < sweeps; ++sw) {
+            for (int u = 0; u < n_; ++u) {
+                const int dg = deg_[u];
+                if (dg < 2) continue;
+                hs.clear();
+                ws.clear();
+                threads_of(u, hs, ws);
+                int32_t* row = &nbr_[(size_t)u * kMaxDeg];
+                int32_t best[kMaxDeg], cur[kMaxDeg];
+                std::copy(row, row + dg, best);
+                int64_t best_cost = weighted(hs, ws, dg);
+                if (dg <= 4) {
+                    // the best order, a uniform choice among equal ones (walks plateaus)
+                    std::copy(row, row + dg, cur);
+                    std::sort(cur, cur + dg);
+                    int ties = 0;
+                    best_cost = INT64_MAX;
+                    do {
+                        std::copy(cur, cur + dg, row);
+                        const int64_t c = recompute(hs, ws, dg);
+                        if (c < best_cost) {
+                            best_cost = c;
+                            ties = 1;
+                            std::copy(cur, cur + dg, best);
+                        } else if (c == best_cost && next(rs) % (uint64_t)(++ties) == 0) {
+                            std::copy(cur, cur + dg, best);
+                        }
+                    } while (std::next_permutation(cur, cur + dg));
+                } else {
+                    uint64_t s = seed ^ ((uint64_t)u * 0x9E3779B97F4A7C15ull) ^ (uint64_t)sw;
+                    for (int k = 0; k < 24; ++k) {
+                        const uint64_t r = next(s);
+                        const int a = (int)(r % (uint64_t)dg), b = (int)((r >> 20) % (uint64_t)dg);
+                        std::copy(best, best + dg, row);
+                        std::swap(row[a], row[b]);
+                        const int64_t c = recompute(hs, ws, dg);
+                        if (c <= best_cost) {
+                            best_cost = c;
+                            std::copy(row, row + dg, best);
+                        }
+                    }
+                }
+                std::copy(best, best + dg, row);
+                recompute(hs, ws, dg);
+            }
+        }
+        uint64_t s = seed;
+        for (int64_t m = 0; m < slot_moves && n_ > 1; ++m) {
+            const uint64_t r = next(s);
+            const int u = (int)((r >> 8) % (uint64_t)n_);
+            int v = (int)((r >> 36) % (uint64_t)(n_ - 1));
+            if (v >= u) ++v;
+            hs.clear();
+            ws.clear();
+            threads_of(u, hs, ws);
+            threads_of(v, hs, ws);
+            for (int q = 0; q < deg_[u]; ++q) threads_of(nbr_[(size_t)u * kMaxDeg + q], hs, ws);
+            for (int q = 0; q < deg_[v]; ++q) threads_of(nbr_[(size_t)v * kMaxDeg + q], hs, ws);
+            dedup(hs);
+            dedup(ws);
+            const int64_t before = weighted(hs, ws, D_);
+            swap_slots(u, v);
+            if (recompute(hs, ws, D_) > before) {
+                swap_slots(u, v);
+                recompute(hs, ws, D_);
+            }
+        }
+    }
+
+private:
+    static int64_t sum(const std::vector<int>& v)
+    {
+        int64_t c = 0;
+        for (int x : v) c += x;
+        return c;
+    }
+
+    static uint64_t next(uint64_t& s)
+    {
+        uint64_t z = (s += 0x9E3779B97F4A7C15ull);  // splitmix64
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+
+    static void dedup(std::vector<int>& v)
+    {
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+    }
+
+    void refresh()
+    {
+        for (int h = 0; h < H_; ++h)
+            for (int d = 0; d < D_; ++d) c8_[h * D_ + d] = passes(16 * h, 16, d, 16);
+        for (int w = 0; w < W_; ++w)
+            for (int d = 0; d < D_; ++d) c4_[w * D_ + d] = passes(32 * w, 32, d, 32);
+    }
+
+    void swap_slots(int u, int v)
+    {
+        std::swap(slot_of_[u], slot_of_[v]);
+        spin_at_[slot_of_[u]] = u;
+        spin_at_[slot_of_[v]] = v;
+    }
+
+    // the half-warps and warps holding spin x's threads (appended)
+    void threads_of(int x, std::vector<int>& hs, std::vector<int>& ws) const
+    {
+        const int t0 = slot_of_[x] * rb_, t1 = t0 + rb_ - 1;
+        for (int h = t0 / 16; h <= t1 / 16; ++h) hs.push_back(h);
+        for (int w = t0 / 32; w <= t1 / 32; ++w) ws.push_back(w);
+    }
+
+    // passes of the `len` threads from t0 in round d, words distinct modulo `banks`
+    int passes(int t0, int len, int d, int banks)
+    {
+        int cnt[32] = {0};
+        if (++epoch_ == 0) {
+            std::fill(stamp_.begin(), stamp_.end(), 0u);
+            epoch_ = 1;
+        }
+        int mx = 0;
+        const int t1 = std::min(t0 + len, T_);
+        for (int t = t0; t < t1; ++t) {
+            const int sl = t / rb_, lp = t - sl * rb_;
+            const int i = spin_at_[sl];
+            const int c = d < deg_[i] ? nbr_[(size_t)i * kMaxDeg + d] : i;
+            const int word = slot_of_[c] * rb_ + lp;
+            if (stamp_[word] == epoch_) continue;
+            stamp_[word] = epoch_;
+            mx = std::max(mx, ++cnt[word % banks]);
+        }
+        return mx;
+    }
+
+    // weighted passes of rounds < dn in the given cells, from the cache
+    int64_t weighted(const std::vector<int>& hs, const std::vector<int>& ws, int dn) const
+    {
+        int64_t c = 0;
+        for (int d = 0; d < dn; ++d) {
+            for (int h : hs) c += 4 * c8_[h * D_ + d];
+            for (int w : ws) c += c4_[w * D_ + d];
+        }
+        return c;
+    }
+
+    // the same, recomputed into the cache
+    int64_t recompute(const std::vector<int>& hs, const std::vector<int>& ws, int dn)
+    {
+        int64_t c = 0;
+        for (int d = 0; d < dn; ++d) {
+            for (int h : hs) c += 4 * (c8_[h * D_ + d] = passes(16 * h, 16, d, 16));
+            for (int w : ws) c += (c4_[w * D_ + d] = passes(32 * w, 32, d, 32));
+        }
+        return c;
+    }
+
+    // read (i, d), spin i's round-d read (its d-th neighbour, or itself past its degree):
+    // adds `sign` to its bank loads, returns the change of the weighted sum of squared loads
+    int64_t load(int i, int d, int sign)
+    {
+        const int c = d < deg_[i] ? nbr_[(size_t)i * kMaxDeg + d] : i;
+        int64_t delta = 0;
+        for (int lp = 0; lp < rb_; ++lp) {
+            const int t = slot_of_[i] * rb_ + lp, word = slot_of_[c] * rb_ + lp;
+            int& a = l8_[(t >> 4) * 16 + (word & 15)];
+            int& b = l4_[(t >> 5) * 32 + (word & 31)];
+            delta += 4 * (sign > 0 ? 2 * a + 1 : 1 - 2 * a) + (sign > 0 ? 2 * b + 1 : 1 - 2 * b);
+            a += sign;
+            b += sign;
+        }
+        return delta;
+    }
+
+    // the reads whose thread or word moves with spin x: its own and its neighbours' reads of it
+    void moving_reads(int x, std::vector<int32_t>& out) const
+    {
+        for (int d = 0; d < D_; ++d) out.push_back(x << 4 | d);
+        for (int q = 0; q < deg_[x]; ++q) {
+            const int c = nbr_[(size_t)x * kMaxDeg + q];
+            for (int d = 0; d < deg_[c]; ++d)
+                if (nbr_[(size_t)c * kMaxDeg + d] == x) out.push_back(c << 4 | d);
+        }
+    }
+
+    int n_, rb_, T_ = 0, D_ = 0, H_ = 0, W_ = 0;
+    std::vector<int32_t> nbr_, deg_, spin_at_, slot_of_;
+    std::vector<int> c8_, c4_, l8_, l4_;
+    std::vector<uint32_t> stamp_;
+    uint32_t epoch_ = 0;
+};
+
+}  // namespace moq
+
+namespace moq {
+
+// The layout for the graph (ei, ej) of n spins, E edges: slot_spin (n, slot -> spin) and remap
+// (2E entries): row i's neighbour of rank r by column goes to position remap[rowptr_i + r] of
+// the row, rows in spin order with rowptr from the degrees. Returns false, leaving both
+// untouched, when the graph is outside the samplers' range (n > 1024, a degree above 8) or
+// holds an invalid or repeated edge (the device checks report those). `passes`, if given,
+// receives the 8-byte and 4-byte passes of the column layout and of the chosen one.
+inline bool plan_gather_layout(int n, int64_t E, const int32_t* ei, const int32_t* ej, std::vector<int32_t>& slot_spin,
+                               std::vector<int32_t>& remap, int64_t* passes = nullptr)
+{
+    constexpr int kD = GatherLayout::kMaxDeg;
+    if (n < 2 || n > 1024 || E <= 0) return false;
+    std::vector<int32_t> deg(n, 0), nbr((size_t)n * kD, 0);
+    for (int64_t e = 0; e < E; ++e) {
+        const int a = ei[e], b = ej[e];
+        if (a < 0 || b < 0 || a >= n || b >= n || a == b) return false;
+        if (deg[a] >= kD || deg[b] >= kD) return false;
+        nbr[(size_t)a * kD + deg[a]++] = b;
+        nbr[(size_t)b * kD + deg[b]++] = a;
+    }
+    for (int i = 0; i < n; ++i) {
+        int32_t* row = &nbr[(size_t)i * kD];
+        std::sort(row, row + deg[i]);
+        for (int d = 1; d < deg[i]; ++d)
+            if (row[d] == row[d - 1]) return false;
+    }
+    const uint64_t seed = 0x243F6A8885A308D3ull ^ ((uint64_t)n << 32) ^ (uint64_t)E;
+    GatherLayout col(n, fullest_warp_rb(n), nbr, deg);
+    GatherLayout lay = col;
+    lay.balance_slots(10LL * n, seed, 0.0);
+    lay.order_reads(10, 0, seed + 1);
+    const GatherLayout& pick = 4 * lay.passes8() + lay.passes4() <= 4 * col.passes8() + col.passes4() ? lay : col;
+    if (passes) {
+        passes[0] = col.passes8();
+        passes[1] = col.passes4();
+        passes[2] = pick.passes8();
+        passes[3] = pick.passes4();
+    }
+    slot_spin = pick.slot_spin();
+    remap.assign((size_t)2 * E, 0);
+    const std::vector<int32_t>& order = pick.neighbours();
+    int64_t p0 = 0;
+    for (int i = 0; i < n; ++i) {
+        const int32_t* sorted = &nbr[(size_t)i * kD];
+        const int32_t* chosen = &order[(size_t)i * kD];
+        for (int r = 0; r < deg[i]; ++r)
+            remap[p0 + r] = (int32_t)(std::find(chosen, chosen + deg[i], sorted[r]) - chosen);
+        p0 += deg[i];
+    }
+    return true;
+}
+
+}  // namespace moq

@@ -10,6 +10,7 @@
 #include <vector>
 #include <cmath>
 
+#include "gather_layout.cuh"
 #include "moq_common.cuh"
 
 namespace moq {
@@ -85,11 +86,13 @@ __global__ void k_fill(const int32_t* __restrict__ ei, const int32_t* __restrict
     }
 }
 
-// One warp per row: each entry's final slot is the number of row entries with a smaller
-// column (deterministic, whatever order the atomics filled the row in). Equal columns
-// mean a repeated edge.
+// One warp per row: each entry's rank is the number of row entries with a smaller column
+// (deterministic, whatever order the atomics filled the row in); it lands at position rank of
+// the row, or at remap[p0 + rank] when a gather order is given. Equal columns mean a repeated
+// edge.
 __global__ void k_sort_rows(int32_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col_tmp,
-                            const int32_t* __restrict__ eid_tmp, int32_t* col, int32_t* eid, int32_t* status)
+                            const int32_t* __restrict__ eid_tmp, const int32_t* __restrict__ remap, int32_t* col, int32_t* eid,
+                            int32_t* status)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -105,8 +108,9 @@ __global__ void k_sort_rows(int32_t n, const int32_t* __restrict__ rowptr, const
                 rank += (cq < c);
                 dup |= (cq == c) && (q != p);
             }
-            col[p0 + rank] = c;
-            eid[p0 + rank] = eid_tmp[p];
+            const int32_t at = remap ? remap[p0 + rank] : rank;
+            col[p0 + at] = c;
+            eid[p0 + at] = eid_tmp[p];
             if (dup) atomicOr(status, kStatusDuplicateEdge);
         }
     }
@@ -236,6 +240,35 @@ struct SlabPlan {
 
 extern "C" {
 
+int moq_plan_gather_layout(int32_t n, int64_t E, const int32_t* ei, const int32_t* ej, int32_t* slot_spin, int32_t* gather,
+                           int64_t* passes)
+{
+    using namespace moq;
+    if (!ei || !ej || !slot_spin || !gather) return fail(MOQ_ERR_ARG, "moq_plan_gather_layout: NULL pointer");
+    std::vector<int32_t> order, remap;
+    if (!plan_gather_layout(n, E, ei, ej, order, remap, passes))
+        return fail(MOQ_ERR_UNSUPPORTED, "moq_plan_gather_layout: graph outside the sparse samplers' range (n=%d, E=%lld)", n,
+                    (long long)E);
+    std::copy(order.begin(), order.end(), slot_spin);
+    // rows by spin, neighbours by column, then placed by remap
+    std::vector<int32_t> deg(n, 0), rowptr(n + 1, 0), sorted((size_t)2 * E);
+    for (int64_t e = 0; e < E; ++e) {
+        ++deg[ei[e]];
+        ++deg[ej[e]];
+    }
+    for (int i = 0; i < n; ++i) rowptr[i + 1] = rowptr[i] + deg[i];
+    std::vector<int32_t> fill(rowptr.begin(), rowptr.end() - 1);
+    for (int64_t e = 0; e < E; ++e) {
+        sorted[fill[ei[e]]++] = ej[e];
+        sorted[fill[ej[e]]++] = ei[e];
+    }
+    for (int i = 0; i < n; ++i) {
+        std::sort(sorted.begin() + rowptr[i], sorted.begin() + rowptr[i + 1]);
+        for (int r = 0; r < deg[i]; ++r) gather[rowptr[i] + remap[rowptr[i] + r]] = sorted[rowptr[i] + r];
+    }
+    return MOQ_OK;
+}
+
 int moq_create_instance(int32_t n, int32_t K, int64_t E, const int32_t* ei, const int32_t* ej, const int32_t* w,
                         void* stream, moq_instance** out)
 {
@@ -256,7 +289,8 @@ int moq_create_instance(int32_t n, int32_t K, int64_t E, const int32_t* ei, cons
     h->words = (n + 63) / 64;
     cudaGetDevice(&h->device);
 
-    int32_t *deg = nullptr, *cursor = nullptr, *col_tmp = nullptr, *eid_tmp = nullptr, *eid = nullptr, *status = nullptr;
+    int32_t *deg = nullptr, *cursor = nullptr, *col_tmp = nullptr, *eid_tmp = nullptr, *eid = nullptr, *status = nullptr,
+            *remap_d = nullptr;
     unsigned long long* sums = nullptr;
     void* tmp_slab = nullptr;
     int rc = MOQ_OK;
@@ -265,7 +299,10 @@ int moq_create_instance(int32_t n, int32_t K, int64_t E, const int32_t* ei, cons
     // sampler slots in order of decreasing degree (stable), so that warps of the on-chip
     // sampler hold spins of equal degree where the graph allows it (host side, from the
     // edge list; validated on the device below)
-    std::vector<int32_t> order(n), inv(n);
+    // For graphs the on-chip sampler takes (n <= 1024, degrees <= 8) the slots and the gather
+    // order of each CSR row come from plan_gather_layout (against shared-memory bank conflicts;
+    // MOQ_SB_LAYOUT=0 keeps the plain layout below, rows by column).
+    std::vector<int32_t> order(n), inv(n), remap;
     {
         std::vector<int32_t> dgr(n, 0);
         for (int64_t e = 0; e < E; ++e) {
@@ -274,6 +311,11 @@ int moq_create_instance(int32_t n, int32_t K, int64_t E, const int32_t* ei, cons
         }
         for (int32_t i = 0; i < n; ++i) order[i] = i;
         std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return dgr[a] > dgr[b]; });
+        const char* env = getenv("MOQ_SB_LAYOUT");
+        if (!(env && atoi(env) == 0)) {
+            std::vector<int32_t> planned;
+            if (plan_gather_layout(n, E, ei, ej, planned, remap)) order.swap(planned);
+        }
         for (int32_t q = 0; q < n; ++q) inv[order[q]] = q;
     }
     const int nmom = 2 * K + K * (K - 1) / 2;  // weight moments after the 3K sums
@@ -292,6 +334,7 @@ int moq_create_instance(int32_t n, int32_t K, int64_t E, const int32_t* ei, cons
     tmp.add(&col_tmp, h->nnz);
     tmp.add(&eid_tmp, h->nnz);
     tmp.add(&eid, h->nnz);
+    if (!remap.empty()) tmp.add(&remap_d, h->nnz);
     tmp.add(&status, 2);
     tmp.add(&sums, 3 * K + nmom);
     {
@@ -311,6 +354,8 @@ int moq_create_instance(int32_t n, int32_t K, int64_t E, const int32_t* ei, cons
     }
     MOQ_STEP(cu(cudaMemcpyAsync(h->slot_spin, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st), "copy slot order"));
     MOQ_STEP(cu(cudaMemcpyAsync(h->spin_slot, inv.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st), "copy slot order"));
+    if (remap_d)
+        MOQ_STEP(cu(cudaMemcpyAsync(remap_d, remap.data(), sizeof(int32_t) * h->nnz, cudaMemcpyHostToDevice, st), "copy gather order"));
     MOQ_STEP(cu(cudaMemsetAsync(deg, 0, sizeof(int32_t) * (n + 1), st), "memset"));
     MOQ_STEP(cu(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * n, st), "memset"));
     MOQ_STEP(cu(cudaMemsetAsync(status, 0, sizeof(int32_t) * 2, st), "memset"));
@@ -324,7 +369,7 @@ int moq_create_instance(int32_t n, int32_t K, int64_t E, const int32_t* ei, cons
     k_scan_rowptr<<<1, 1024, 0, st>>>(deg, n, h->rowptr);
     k_fill<<<gE, tb, 0, st>>>(h->ei, h->ej, E, n, h->rowptr, cursor, col_tmp, eid_tmp);
     const int gRows = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)n * 32, tb), 148 * 16));
-    k_sort_rows<<<gRows, tb, 0, st>>>(n, h->rowptr, col_tmp, eid_tmp, h->col, eid, status);
+    k_sort_rows<<<gRows, tb, 0, st>>>(n, h->rowptr, col_tmp, eid_tmp, remap_d, h->col, eid, status);
     k_entry_weights<<<gNNZ, tb, 0, st>>>(K, h->nnz, E, eid, h->w, h->wn);
     k_row_sums<<<gN, tb, 0, st>>>(n, K, h->nnz, h->rowptr, h->wn, h->rowsum, status + 1);
     k_weight_sums<<<gE, tb, 0, st>>>(K, E, h->w, sums);

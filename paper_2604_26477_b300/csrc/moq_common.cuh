@@ -129,7 +129,7 @@ struct moq_instance {
     int32_t* col = nullptr;     // nnz, rows sorted by column
     int32_t* wn = nullptr;      // K x nnz weights of the CSR entries (objective-major)
     int64_t* rowsum = nullptr;  // n x K integer row sums sum_j J^(k)_ij
-    int32_t* slot_spin = nullptr;  // sampler slot -> spin, by decreasing degree
+    int32_t* slot_spin = nullptr;  // sampler slot -> spin (gather_layout.cuh)
     int32_t* spin_slot = nullptr;  // spin -> sampler slot
     void* slab = nullptr;          // the one device allocation the arrays above live in
     moq_instance_info info{};

@@ -16,6 +16,7 @@
 
 #include <cuda_fp16.h>
 
+#include "gather_layout.cuh"
 #include "sb_common.cuh"
 
 namespace moq {
@@ -28,7 +29,7 @@ struct SbArgs {
     int64_t nnz;
     const int32_t* rowptr;
     const int32_t* col;
-    const int32_t* slot_spin;  // slot -> spin (decreasing degree)
+    const int32_t* slot_spin;  // slot -> spin (gather_layout.cuh)
     const int32_t* spin_slot;  // spin -> slot
     const int32_t* wn;
     const int64_t* rowsum;
@@ -1011,17 +1012,7 @@ const void* kernel_of_variant(int dmax, bool noise, bool pair, int pump)
 // the 148 SMs when R is small.
 int choose_rb(int n, int R)
 {
-    const int hi = std::max(1, std::min(32, 256 / n));
-    int rb = 1;
-    double best = -1.0;
-    for (int c = 1; c <= hi; ++c) {
-        const int threads = n * c;
-        const double util = (double)threads / (32.0 * (double)((threads + 31) / 32));
-        if (util > best + 0.01) {
-            best = util;
-            rb = c;
-        }
-    }
+    int rb = fullest_warp_rb(n);
     if (const char* env = getenv("MOQ_SB_RB")) {
         int v = atoi(env);
         if (v >= 1) rb = std::min(v, 1024 / n);

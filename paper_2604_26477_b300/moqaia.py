@@ -67,6 +67,7 @@ _sigs = {
     "moq_default_params": (None, [C.POINTER(moq_sample_params)]),
     "moq_create_instance": (C.c_int, [_i32, _i32, _i64, _vp, _vp, _vp, _vp, C.POINTER(_vp)]),
     "moq_create_instance_dense": (C.c_int, [_i32, _i32, _vp, _vp, C.POINTER(_vp)]),
+    "moq_plan_gather_layout": (C.c_int, [_i32, _i64, _vp, _vp, _vp, _vp, _vp]),
     "moq_destroy_instance": (None, [_vp]),
     "moq_instance_get_info": (C.c_int, [_vp, C.POINTER(moq_instance_info)]),
     "moq_sample": (C.c_int, [_vp, _vp, _i32, C.POINTER(moq_sample_params), _u64, _u64, _vp, _vp]),
@@ -217,6 +218,20 @@ def moq_create_instance_dense(n, K, J_upper, stream=None) -> C.c_void_p:
     h = C.c_void_p()
     _check(_lib.moq_create_instance_dense(n, K, pj, _stream(stream), C.byref(h)), "moq_create_instance_dense")
     return h
+
+
+def moq_plan_gather_layout(n, ei, ej):
+    """Host-only: (slot_spin[n], gather[2E], passes[4]) as moq_create_instance lays the graph out."""
+    ei_, pei = _hptr(ei, np.int32)
+    ej_, pej = _hptr(ej, np.int32)
+    if ei_.size != ej_.size:
+        raise ValueError("ei and ej must have the same length")
+    slot = np.zeros(n, np.int32)
+    gather = np.zeros(2 * ei_.size, np.int32)
+    passes = np.zeros(4, np.int64)
+    _check(_lib.moq_plan_gather_layout(n, ei_.size, pei, pej, slot.ctypes.data_as(_vp), gather.ctypes.data_as(_vp),
+                                       passes.ctypes.data_as(_vp)), "moq_plan_gather_layout")
+    return slot, gather, passes
 
 
 def moq_destroy_instance(h):
