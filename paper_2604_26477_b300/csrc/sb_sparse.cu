@@ -312,17 +312,15 @@ __host__ __device__ inline size_t sb_smem_bytes2(int Rb, int W, int pump_table_s
            align_up(sizeof(unsigned long long) * (size_t)Rb * W, 16) + sizeof(float) * (size_t)pump_table_steps;
 }
 
-// Set-up of the replica pair (r0, r0 + 1) on spin i, shared by the FP32 and FP16 pair
-// kernels: both rows of -c0 J(c) in FP32 (c0 reduced over the block's replicas in red[]:
-// 4 * Rp words), the neighbours' phi indices and the start state. Contains two block barriers.
+// Rows of J(c) of spin i for the replica pair (r0, r0 + 1), before the c0 scaling: the
+// couplings of its neighbours (zero past its degree), their phi indices spin_slot[c] * Rp + lp,
+// and the sums that c0 is reduced from (sabs = sum_d |J(c)_id|, srow = sum_j J(c)_ij).
 template <int DMAX>
-__device__ __forceinline__ void pair_setup(const SbArgs& a, int tid, int i, int lp, int Rp, int r0, unsigned* red,
-                                           float (&jc0)[DMAX], float (&jc1)[DMAX], int (&nb)[DMAX], float& x0, float& y0,
-                                           float& x1, float& y1)
+__device__ __forceinline__ void pair_rows(const SbArgs& a, int i, int lp, int Rp, int r0, float (&jc0)[DMAX], float (&jc1)[DMAX],
+                                          int (&nb)[DMAX], float& sabs0, float& sabs1, float& srow0, float& srow1)
 {
-    const int n = a.n, Rb = 2 * Rp, r1 = r0 + 1;
-    const bool act0 = r0 < a.R, act1 = r1 < a.R;
-    const int rs0 = act0 ? r0 : 0, rs1 = act1 ? r1 : 0;
+    const int r1 = r0 + 1;
+    const int rs0 = r0 < a.R ? r0 : 0, rs1 = r1 < a.R ? r1 : 0;
     float lam0[kMaxK], lam1[kMaxK];
 #pragma unroll
     for (int k = 0; k < kMaxK; ++k) {
@@ -331,7 +329,8 @@ __device__ __forceinline__ void pair_setup(const SbArgs& a, int tid, int i, int 
     }
     const int p0 = a.rowptr[i];
     const int deg = a.rowptr[i + 1] - p0;
-    float sabs0 = 0.0f, sabs1 = 0.0f;
+    sabs0 = 0.0f;
+    sabs1 = 0.0f;
 #pragma unroll
     for (int d = 0; d < DMAX; ++d) {
         float v0 = 0.0f, v1 = 0.0f;
@@ -353,7 +352,8 @@ __device__ __forceinline__ void pair_setup(const SbArgs& a, int tid, int i, int 
         sabs0 += fabsf(v0);
         sabs1 += fabsf(v1);
     }
-    float srow0 = 0.0f, srow1 = 0.0f;
+    srow0 = 0.0f;
+    srow1 = 0.0f;
 #pragma unroll
     for (int k = 0; k < kMaxK; ++k)
         if (k < a.K) {
@@ -361,24 +361,16 @@ __device__ __forceinline__ void pair_setup(const SbArgs& a, int tid, int i, int 
             srow0 = fmaf(lam0[k], w, srow0);
             srow1 = fmaf(lam1[k], w, srow1);
         }
-    for (int q = tid; q < 2 * Rb; q += blockDim.x) red[q] = 0u;  // 2 Rb = 4 Rp may exceed n Rp threads (n < 4)
-    __syncthreads();
-    atomicMax(&red[2 * lp], __float_as_uint(fabsf(srow0)));
-    atomicMax(&red[2 * lp + 1], __float_as_uint(fabsf(srow1)));
-    atomicMax(&red[Rb + 2 * lp], __float_as_uint(sabs0));
-    atomicMax(&red[Rb + 2 * lp + 1], __float_as_uint(sabs1));
-    __syncthreads();
-    {
-        const float mx0 = __uint_as_float(red[2 * lp]), mxa0 = __uint_as_float(red[Rb + 2 * lp]);
-        const float mx1 = __uint_as_float(red[2 * lp + 1]), mxa1 = __uint_as_float(red[Rb + 2 * lp + 1]);
-        const float c00 = mx0 > 0.0f ? 1.0f / mx0 : (mxa0 > 0.0f ? 1.0f / mxa0 : 1.0f);
-        const float c01 = mx1 > 0.0f ? 1.0f / mx1 : (mxa1 > 0.0f ? 1.0f / mxa1 : 1.0f);
-#pragma unroll
-        for (int d = 0; d < DMAX; ++d) {
-            jc0[d] *= -c00;
-            jc1[d] *= -c01;
-        }
-    }
+}
+
+// c0 of a replica from its block maxima of |srow| and sabs, and the rows scaled by -c0
+__device__ __forceinline__ float c0_of(float mx, float mxa) { return mx > 0.0f ? 1.0f / mx : (mxa > 0.0f ? 1.0f / mxa : 1.0f); }
+
+// Start state of spin i for the pair: the given one, or init_amp times uniforms on [-1, 1)
+__device__ __forceinline__ void pair_start(const SbArgs& a, int i, int r0, float& x0, float& y0, float& x1, float& y1)
+{
+    const int n = a.n, r1 = r0 + 1;
+    const bool act0 = r0 < a.R, act1 = r1 < a.R;
     if (a.x_init) {
         x0 = (act0 ? a.x_init[(int64_t)r0 * n + i] : 0.0f) + 0.0f;
         y0 = (act0 && a.y_init) ? a.y_init[(int64_t)r0 * n + i] : 0.0f;
@@ -392,6 +384,34 @@ __device__ __forceinline__ void pair_setup(const SbArgs& a, int tid, int i, int 
         x1 = __fmul_rn(a.init_amp, signed_unit(o1.x)) + 0.0f;
         y1 = __fmul_rn(a.init_amp, signed_unit(o1.y));
     }
+}
+
+// Set-up of the replica pair (r0, r0 + 1) on spin i, shared by the FP32 and FP16 pair
+// kernels: both rows of -c0 J(c) in FP32 (c0 reduced over the block's replicas in red[]:
+// 4 * Rp words), the neighbours' phi indices and the start state. Contains two block barriers.
+template <int DMAX>
+__device__ __forceinline__ void pair_setup(const SbArgs& a, int tid, int i, int lp, int Rp, int r0, unsigned* red,
+                                           float (&jc0)[DMAX], float (&jc1)[DMAX], int (&nb)[DMAX], float& x0, float& y0,
+                                           float& x1, float& y1)
+{
+    const int Rb = 2 * Rp;
+    float sabs0, sabs1, srow0, srow1;
+    pair_rows<DMAX>(a, i, lp, Rp, r0, jc0, jc1, nb, sabs0, sabs1, srow0, srow1);
+    for (int q = tid; q < 2 * Rb; q += blockDim.x) red[q] = 0u;  // 2 Rb = 4 Rp may exceed n Rp threads (n < 4)
+    __syncthreads();
+    atomicMax(&red[2 * lp], __float_as_uint(fabsf(srow0)));
+    atomicMax(&red[2 * lp + 1], __float_as_uint(fabsf(srow1)));
+    atomicMax(&red[Rb + 2 * lp], __float_as_uint(sabs0));
+    atomicMax(&red[Rb + 2 * lp + 1], __float_as_uint(sabs1));
+    __syncthreads();
+    const float c00 = c0_of(__uint_as_float(red[2 * lp]), __uint_as_float(red[Rb + 2 * lp]));
+    const float c01 = c0_of(__uint_as_float(red[2 * lp + 1]), __uint_as_float(red[Rb + 2 * lp + 1]));
+#pragma unroll
+    for (int d = 0; d < DMAX; ++d) {
+        jc0[d] *= -c00;
+        jc1[d] *= -c01;
+    }
+    pair_start(a, i, r0, x0, y0, x1, y1);
 }
 
 template <int VARIANT, int DMAX, bool NOISE, int PUMP>
@@ -532,6 +552,194 @@ cudaError_t launch_pump2(const SbArgs& a, int pump, dim3 grid, dim3 block, size_
     case kPumpScheduleCap: return launch_one2<VARIANT, DMAX, NOISE, kPumpScheduleCap>(a, grid, block, smem, st);
     default: return launch_one2<VARIANT, DMAX, NOISE, kPumpSchedule>(a, grid, block, smem, st);
     }
+}
+
+// ---- two spins per thread -------------------------------------------------------------
+// For large graphs the pair form's blocks (n threads, one per spin) leave one block per SM,
+// whose every step ends in a barrier over all of it. This form runs one replica pair per block
+// with S = n / 2 rounded up to whole warps threads, thread t holding slots t and S + t (the
+// second idle past n): blocks of at most 512 threads, two resident per SM, and two independent
+// force chains per thread between barriers. phi keeps the pair form's layout (one float2 per
+// slot), so both gathers of a thread follow the slot order's bank plan. Each replica's
+// arithmetic and noise counters are those of k_sb_sparse2 (and k_sb_sparse): the same bits.
+constexpr int kTwoSpinThreads = 512;
+
+inline int two_spin_threads(int n) { return (int)(ceil_div((n + 1) / 2, 32) * 32); }
+
+template <int VARIANT, int DMAX, bool NOISE, int PUMP>
+__global__ void __launch_bounds__(kTwoSpinThreads, 2) k_sb_sparse2s(const SbArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = a.n, S = blockDim.x;
+    float2* phiA = reinterpret_cast<float2*>(smem_raw);
+    float2* phiB = phiA + kPhiStride;
+    unsigned* red = reinterpret_cast<unsigned*>(phiB + kPhiStride);  // 4 words
+    unsigned long long* wb = reinterpret_cast<unsigned long long*>(smem_raw + sizeof(float) * 4 * kPhiStride + align_up(sizeof(unsigned) * 4, 16));
+    const int tid = threadIdx.x;
+    const bool hasB = S + tid < n;
+    const int iA = a.slot_spin[tid];
+    const int iB = hasB ? a.slot_spin[S + tid] : iA;  // idle half: spin A again (harmless in the maxima)
+    const int r0 = 2 * blockIdx.x, r1 = r0 + 1;
+    float jA0[DMAX], jA1[DMAX], jB0[DMAX], jB1[DMAX];
+    int nbA[DMAX], nbB[DMAX];
+    float sA0, sA1, wA0, wA1, sB0, sB1, wB0, wB1;
+    pair_rows<DMAX>(a, iA, 0, 1, r0, jA0, jA1, nbA, sA0, sA1, wA0, wA1);
+    pair_rows<DMAX>(a, iB, 0, 1, r0, jB0, jB1, nbB, sB0, sB1, wB0, wB1);
+    if (tid < 4) red[tid] = 0u;
+    __syncthreads();
+    atomicMax(&red[0], __float_as_uint(fmaxf(fabsf(wA0), fabsf(wB0))));
+    atomicMax(&red[1], __float_as_uint(fmaxf(fabsf(wA1), fabsf(wB1))));
+    atomicMax(&red[2], __float_as_uint(fmaxf(sA0, sB0)));
+    atomicMax(&red[3], __float_as_uint(fmaxf(sA1, sB1)));
+    __syncthreads();
+    float2 jA[DMAX], jB[DMAX];
+    {
+        const float c00 = c0_of(__uint_as_float(red[0]), __uint_as_float(red[2]));
+        const float c01 = c0_of(__uint_as_float(red[1]), __uint_as_float(red[3]));
+#pragma unroll
+        for (int d = 0; d < DMAX; ++d) {
+            jA[d] = make_float2(jA0[d] * -c00, jA1[d] * -c01);
+            jB[d] = make_float2(jB0[d] * -c00, jB1[d] * -c01);
+        }
+    }
+    float2 xA, yA, xB, yB;
+    pair_start(a, iA, r0, xA.x, yA.x, xA.y, yA.y);
+    pair_start(a, iB, r0, xB.x, yB.x, xB.y, yB.y);
+    phiA[tid] = make_float2(phi_of<VARIANT>(xA.x), phi_of<VARIANT>(xA.y));
+    if (hasB) phiA[S + tid] = make_float2(phi_of<VARIANT>(xB.x), phi_of<VARIANT>(xB.y));
+    __syncthreads();
+    const float2 dt2 = make_float2(a.dt, a.dt), kappa2 = make_float2(a.kappa, a.kappa);
+    const float2 dta02 = make_float2(a.dt * a.a0, a.dt * a.a0);
+    const float a0 = a.a0, a0inv = a.a0inv;
+    const float* sched = a.schedule;
+    const int T = a.T;
+    auto cm_at = [&](int m, float mf) -> float {
+        return pump_base(PUMP) == kPumpInline ? fmaf(a0inv, mf, -a0) : (__ldg(sched + m) - a0);
+    };
+    auto block8 = [&](int m, int i, int r) -> uint4 {
+        return NOISE ? Philox4x32::block(make_uint4((uint32_t)(m >> 3), (uint32_t)i, a.rep_off + (uint32_t)r, a.round32), a.key0, a.key1)
+                     : make_uint4(0u, 0u, 0u, 0u);
+    };
+    auto noise4 = [&](uint32_t wa, uint32_t wbb, float (&e)[4]) {
+        if (NOISE) {
+            const float2 p = box_muller16(wa), q = box_muller16(wbb);
+            e[0] = p.x; e[1] = p.y; e[2] = q.x; e[3] = q.y;
+        }
+    };
+    // one step of both spins: gathers, packed updates, phi written, barrier
+    auto step = [&](const float2* rd, float2* wr, float cm, float ea0, float ea1, float eb0, float eb1) {
+        float2 fA = make_float2(0.0f, 0.0f), fB = fA;
+#pragma unroll
+        for (int d = 0; d < DMAX; ++d) {
+            fA = __ffma2_rn(jA[d], rd[nbA[d]], fA);
+            fB = __ffma2_rn(jB[d], rd[nbB[d]], fB);
+        }
+        sb_update2<NOISE>(fA, make_float2(cm, cm), make_float2(ea0, ea1), dt2, kappa2, dta02, xA, yA);
+        sb_update2<NOISE>(fB, make_float2(cm, cm), make_float2(eb0, eb1), dt2, kappa2, dta02, xB, yB);
+        wr[tid] = make_float2(phi_of<VARIANT>(xA.x), phi_of<VARIANT>(xA.y));
+        if (hasB) wr[S + tid] = make_float2(phi_of<VARIANT>(xB.x), phi_of<VARIANT>(xB.y));
+        __syncthreads();
+    };
+    auto four_steps = [&](int m, float mf, const float (&e)[4], const float (&g)[4], const float (&u)[4], const float (&v)[4]) {
+        step(phiA, phiB, cm_at(m, mf), e[0], g[0], u[0], v[0]);
+        step(phiB, phiA, cm_at(m + 1, mf + 1.0f), e[1], g[1], u[1], v[1]);
+        step(phiA, phiB, cm_at(m + 2, mf + 2.0f), e[2], g[2], u[2], v[2]);
+        step(phiB, phiA, cm_at(m + 3, mf + 3.0f), e[3], g[3], u[3], v[3]);
+    };
+    auto noise_at = [&](int m, float (&e)[4], float (&g)[4], float (&u)[4], float (&v)[4]) {
+        if (NOISE) {
+            const bool hi = (m & 4) != 0;
+            const uint4 o = block8(m, iA, r0), q = block8(m, iA, r1), ob = block8(m, iB, r0), qb = block8(m, iB, r1);
+            noise4(hi ? o.z : o.x, hi ? o.w : o.y, e);
+            noise4(hi ? q.z : q.x, hi ? q.w : q.y, g);
+            noise4(hi ? ob.z : ob.x, hi ? ob.w : ob.y, u);
+            noise4(hi ? qb.z : qb.x, hi ? qb.w : qb.y, v);
+        }
+    };
+    int m = 0;
+    float mf = 0.0f;
+    if (NOISE) {
+        // the Gaussians two steps at a time (one Philox word per replica and spin), which keeps
+        // fewer of them live than four at a time
+        auto two_steps = [&](int mm, float mmf, uint32_t wa, uint32_t wbb, uint32_t wc, uint32_t wd) {
+            const float2 pa = box_muller16(wa), pb = box_muller16(wbb), pc = box_muller16(wc), pd = box_muller16(wd);
+            step(phiA, phiB, cm_at(mm, mmf), pa.x, pb.x, pc.x, pd.x);
+            step(phiB, phiA, cm_at(mm + 1, mmf + 1.0f), pa.y, pb.y, pc.y, pd.y);
+        };
+        for (; m + 8 <= T; m += 8) {
+            const uint4 o = block8(m, iA, r0), q = block8(m, iA, r1), ob = block8(m, iB, r0), qb = block8(m, iB, r1);
+            two_steps(m, mf, o.x, q.x, ob.x, qb.x);
+            two_steps(m + 2, mf + 2.0f, o.y, q.y, ob.y, qb.y);
+            two_steps(m + 4, mf + 4.0f, o.z, q.z, ob.z, qb.z);
+            two_steps(m + 6, mf + 6.0f, o.w, q.w, ob.w, qb.w);
+            mf += 8.0f;
+        }
+    }
+    for (; m + 4 <= T; m += 4) {
+        float e[4] = {0.0f, 0.0f, 0.0f, 0.0f}, g[4] = {0.0f, 0.0f, 0.0f, 0.0f}, u[4] = {0.0f, 0.0f, 0.0f, 0.0f},
+              v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        noise_at(m, e, g, u, v);
+        four_steps(m, mf, e, g, u, v);
+        mf += 4.0f;
+    }
+    if (m < T) {
+        float e[4] = {0.0f, 0.0f, 0.0f, 0.0f}, g[4] = {0.0f, 0.0f, 0.0f, 0.0f}, u[4] = {0.0f, 0.0f, 0.0f, 0.0f},
+              v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        noise_at(m, e, g, u, v);
+        step(phiA, phiB, cm_at(m, mf), e[0], g[0], u[0], v[0]);
+        if (m + 1 < T) step(phiB, phiA, cm_at(m + 1, mf + 1.0f), e[1], g[1], u[1], v[1]);
+        if (m + 2 < T) step(phiA, phiB, cm_at(m + 2, mf + 2.0f), e[2], g[2], u[2], v[2]);
+    }
+    const int W = a.W;
+    for (int t = tid; t < 2 * W; t += blockDim.x) wb[t] = 0ull;
+    __syncthreads();
+    if (xA.x < 0.0f) atomicOr(&wb[iA >> 6], 1ull << (iA & 63));
+    if (xA.y < 0.0f) atomicOr(&wb[W + (iA >> 6)], 1ull << (iA & 63));
+    if (hasB && xB.x < 0.0f) atomicOr(&wb[iB >> 6], 1ull << (iB & 63));
+    if (hasB && xB.y < 0.0f) atomicOr(&wb[W + (iB >> 6)], 1ull << (iB & 63));
+    __syncthreads();
+    for (int t = tid; t < 2 * W; t += blockDim.x) {
+        const int r2 = r0 + t / W;
+        if (r2 < a.R) a.bits[(int64_t)r2 * W + (t % W)] = wb[t];
+    }
+    auto out = [&](int i, float2 x, float2 y) {
+        if (r0 < a.R) {
+            if (a.x_out) a.x_out[(int64_t)r0 * n + i] = x.x;
+            if (a.y_out) a.y_out[(int64_t)r0 * n + i] = y.x;
+        }
+        if (r1 < a.R) {
+            if (a.x_out) a.x_out[(int64_t)r1 * n + i] = x.y;
+            if (a.y_out) a.y_out[(int64_t)r1 * n + i] = y.y;
+        }
+    };
+    out(iA, xA, yA);
+    if (hasB) out(iB, xB, yB);
+}
+
+__host__ __device__ inline size_t sb_smem_bytes2s(int W) { return sizeof(float) * 4 * kPhiStride + 16 + align_up(sizeof(unsigned long long) * 2 * (size_t)W, 16); }
+
+template <int VARIANT, int DMAX, bool NOISE, int PUMP>
+cudaError_t launch_one2s(const SbArgs& a, dim3 grid, dim3 block, size_t smem, cudaStream_t st)
+{
+    auto k = k_sb_sparse2s<VARIANT, DMAX, NOISE, PUMP>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, block, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// degree bounds 3 and 4; the pump from the schedule or inline
+template <int VARIANT>
+cudaError_t launch_variant2s(const SbArgs& a, int dmax, bool noise, bool schedule, dim3 grid, dim3 block, size_t smem, cudaStream_t st)
+{
+#define MOQ_2S(D, N) (schedule ? launch_one2s<VARIANT, D, N, kPumpSchedule>(a, grid, block, smem, st) \
+                               : launch_one2s<VARIANT, D, N, kPumpInline>(a, grid, block, smem, st))
+    switch (dmax) {
+    case 3: return noise ? MOQ_2S(3, true) : MOQ_2S(3, false);
+    case 4: return noise ? MOQ_2S(4, true) : MOQ_2S(4, false);
+    default: return cudaErrorInvalidValue;
+    }
+#undef MOQ_2S
 }
 
 // ---- float16 state: the paper's precision ---------------------------------------------
@@ -1173,6 +1381,22 @@ extern "C" int moq_sample(const moq_instance* inst, const float* lambda, int32_t
             const int v = atoi(env);
             if (v == 0) pair = false;
             if (v == 1 && dmax <= 4) pair = true;
+        }
+    }
+    // graphs of more than 640 spins (one pair-form block per SM): two spins per thread when the
+    // grid of replica pairs still fills two waves (MOQ_SB_TWOSPIN = 0 / 1 forces the choice)
+    {
+        bool two_spin = dmax <= 4 && a.n > kCapThreads && ceil_div(R, 2) >= 4 * 148;
+        if (const char* env = getenv("MOQ_SB_TWOSPIN")) two_spin = atoi(env) != 0 && dmax <= 4 && a.n > 32;
+        if (two_spin) {
+            a.Rb = 2;
+            const dim3 block2((unsigned)two_spin_threads(a.n)), grid2((unsigned)ceil_div(R, 2));
+            const size_t smem2 = sb_smem_bytes2s(a.W);
+            const bool sched = p->schedule != nullptr;
+            const cudaError_t e2 = (p->variant == MOQ_DSB) ? launch_variant2s<MOQ_DSB>(a, dmax, noise, sched, grid2, block2, smem2, as_stream(stream))
+                                                           : launch_variant2s<MOQ_BSB>(a, dmax, noise, sched, grid2, block2, smem2, as_stream(stream));
+            if (e2 != cudaSuccess) return cuda_fail(e2, "moq_sample launch (two spins per thread)");
+            return MOQ_OK;
         }
     }
     const Shape& sh = pair ? two : one;

@@ -763,3 +763,46 @@ def test_exhaustive_front_matches_brute_force(M, P, oracle):
     assert arch.hypervolume(ref) == oracle.hypervolume(cuts[keep], ref)
     assert np.array_equal(oracle.cuts(src, gb), gc)  # each representative has its cut vector
     arch.close()
+
+
+@pytest.mark.parametrize("variant,alpha", [("dsb", 0.1), ("bsb", 0.0), ("bsb", 0.2)])
+@pytest.mark.parametrize("n,d,R", [(1024, 3, 601), (700, 3, 1021), (650, 4, 999), (100, 3, 37)])
+def test_two_spins_per_thread_give_the_pair_form_bits(M, P, monkeypatch, variant, alpha, n, d, R):
+    # two spins per thread (taken by default for n > 640; MOQ_SB_TWOSPIN forces either form):
+    # each replica's arithmetic and noise counters are the pair form's, ragged R and T included
+    src = wl.random_regular(n, 45, K=3, d=d)
+    inst = P.Instance(src)
+    lam = torch.from_numpy(wl.dirichlet_lambdas(R, 3, 7)).cuda()
+    out = {}
+    for two in ("0", "1"):
+        monkeypatch.setenv("MOQ_SB_TWOSPIN", two)
+        monkeypatch.setenv("MOQ_SB_PAIR", "1")
+        xo = torch.zeros((R, n), device="cuda")
+        yo = torch.zeros((R, n), device="cuda")
+        bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+        p = M.moq_default_params(variant=variant, steps=203, dt=0.5, alpha=alpha, x_out=xo, y_out=yo)
+        M.moq_sample(inst.handle, lam, R, p, 9, 3, bits)
+        out[two] = (bits.cpu(), xo.cpu(), yo.cpu())
+    for a, b in zip(out["0"], out["1"]):
+        assert torch.equal(a, b)
+
+
+def test_two_spins_per_thread_from_a_given_state_and_schedule(M, P, monkeypatch):
+    n, R, T = 900, 300, 120
+    src = wl.random_regular(n, 46, K=3)
+    inst = P.Instance(src)
+    lam = torch.from_numpy(wl.dirichlet_lambdas(R, 3, 8)).cuda()
+    g = torch.Generator().manual_seed(4)
+    x0 = (torch.rand((R, n), generator=g) - 0.5).cuda()
+    y0 = (0.2 * torch.randn((R, n), generator=g)).cuda()
+    sched = torch.linspace(0.0, 1.3, T).float().cuda()
+    out = {}
+    for two in ("0", "1"):
+        monkeypatch.setenv("MOQ_SB_TWOSPIN", two)
+        monkeypatch.setenv("MOQ_SB_PAIR", "1")
+        xo = torch.zeros((R, n), device="cuda")
+        bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+        p = M.moq_default_params(steps=T, dt=0.5, alpha=0.1, x_init=x0, y_init=y0, x_out=xo, schedule=sched)
+        M.moq_sample(inst.handle, lam, R, p, 8, 0, bits)
+        out[two] = (bits.cpu(), xo.cpu())
+    assert torch.equal(out["0"][0], out["1"][0]) and torch.equal(out["0"][1], out["1"][1])
