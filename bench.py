@@ -59,6 +59,15 @@ def peak_alu_tops():
     return 148 * 128 * 2.032e9 / 1e12
 
 
+def peak_xu_tops():
+    """Special-function (MUFU / XU pipe) peak: 148 SMs x 16 lanes x 2032 MHz; ncu's XU pipe-cycle
+    counter of the sparse sampler (38 % busy for 2 MUFU ops per update at 1.53 ms) agrees."""
+    return 148 * 16 * 2.032e9 / 1e12
+
+
+MUFU_PER_SPIN_UPDATE = 2.0  # Box-Muller per two Gaussians: lg2, sqrt, sin, cos
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -367,7 +376,12 @@ def gpu_arm(args, rank, world):
                                            else "sb_sparse_precision_n42_K4.txt"),
                 "peak_source": "derived: 148 SMs x 128 FP32/INT32 lanes x 2032 MHz max SM clock",
                 "ops_per_spin_update": ops, "kernel_ms": sample_avg * 1e3,
-                "hbm_peak_measured_gbs": peaks.get("hbm_gbs")}
+                "hbm_peak_measured_gbs": peaks.get("hbm_gbs"),
+                # the special-function work on its own pipe (counted at full rate in ops above)
+                "xu": {"bound": "xu", "mufu_per_spin_update": MUFU_PER_SPIN_UPDATE,
+                       "achieved": MUFU_PER_SPIN_UPDATE * R * n * T / sample_avg / 1e12, "peak": peak_xu_tops(),
+                       "unit": "Tmufu/s", "frac": MUFU_PER_SPIN_UPDATE * R * n * T / sample_avg / 1e12 / peak_xu_tops(),
+                       "peak_source": "derived: 148 SMs x 16 MUFU lanes x 2032 MHz"}}
     return {"value": value, "ms_per_step": dev_s / args.steps * 1e3, "wall_s": t_wall, "e2e": e2e,
             "roofline": roofline, "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps,
             "front_last": fronts[-1], "hv_last": int(hvs[-1]), "sampling_only_value": units / samp_s, "bsb": bsb,
