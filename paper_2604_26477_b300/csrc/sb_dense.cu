@@ -308,10 +308,19 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     constexpr int kCk = chunk_elems<F8>();
     const int np = a.n_pad, nchunks = np / kCk;
     const int cid = blockIdx.x, nctas = gridDim.x;
-    // tile g = (spin block g % n_ib, replica block g / n_ib)
+    // Tile g: replica block by replica block over all spin blocks; the split form (J and J_res,
+    // 50 MB at n = 2048) walks the spin blocks in two halves (when their count is even), so that
+    // a wave of 148 tiles reads half of J and J_res with the phi rows of about 18 replica blocks,
+    // a working set the L2 keeps across the waves of that half (DRAM reads per step 505 -> 382
+    // MB); the one-operand forms keep the plain order, whose J the L2 already keeps (halves
+    // would read phi twice: 197 -> 223 MB)
+    const int halves = (PREC == kPrecSplit && n_ib % 2 == 0 && n_ib >= 4) ? 2 : 1;
+    const int ib_h = n_ib / halves;
+    const int per_half = n_groups / halves;
     auto tile_of = [&](int g, int& i0, int& r0) {
-        i0 = (g % n_ib) * kTileM;
-        r0 = (g / n_ib) * kTileN;
+        const int h = g / per_half, rem = g - h * per_half;
+        i0 = (h * ib_h + rem % ib_h) * kTileM;
+        r0 = (rem / ib_h) * kTileN;
     };
 
     if (warp == 0) {
@@ -490,8 +499,10 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                     for (int q = 0; q < 8; ++q) {
                         const int r = r0 + col0 + q;
                         const bool v = r < a.R;
-                        xs[q] = v ? a.x[(int64_t)r * np + i] : 0.0f;
-                        ys[q] = v ? a.y[(int64_t)r * np + i] : 0.0f;
+                        // x and y stream through once per step: loads and stores marked
+                        // evict-first, so that L2 keeps the operand tiles (J, phi) instead
+                        xs[q] = v ? __ldcs(a.x + (int64_t)r * np + i) : 0.0f;
+                        ys[q] = v ? __ldcs(a.y + (int64_t)r * np + i) : 0.0f;
                         eta[q] = 0.0f;
                     }
                     if (NOISE) {
@@ -512,8 +523,8 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                             const int64_t at = (int64_t)r * np + i;
                             float xv = xs[q], yv = ys[q];
                             sb_update<NOISE>(f[q], cm, eta[q], a.dt, a.kappa, a.dta0, xv, yv);
-                            a.x[at] = xv;
-                            a.y[at] = yv;
+                            __stcs(a.x + at, xv);
+                            __stcs(a.y + at, yv);
                             if (F8) {
                                 a.phi8_out[at] = __nv_fp8_e4m3(phi_of<VARIANT>(xv));
                             } else {
