@@ -22,7 +22,7 @@
 //  2. orders: each visited spin takes the order of its reads (among all orders when the degree
 //     is at most 4) that gives the fewest passes, 8-byte passes weighted 4 to 1 over 4-byte ones
 //     (the FP32 pair and float16 four-replica forms gather 8 bytes, the single-replica and
-//     float16 pair forms 4); slot exchanges judged by the same count follow.
+//     float16 pair forms 4); the counts are updated read by read, so a try costs O(rounds x Rb).
 // Neighbour order changes only the order of the force's FP32 sums; slot order changes nothing.
 #pragma once
 
@@ -118,33 +118,43 @@ public:
         refresh();
     }
 
-    // `sweeps` passes over all spins choosing each one's best read order, then `slot_moves`
-    // exchanges of two slots, both by the weighted pass count
-    void order_reads(int sweeps, int64_t slot_moves, uint64_t seed)
+    // `sweeps` passes over all spins, each taking the order of its reads with the fewest weighted
+    // passes (a uniform choice among equal ones, which walks plateaus). The counts are kept per
+    // cell and updated read by read (Counts below), so trying an order costs O(rounds x Rb).
+    void order_reads(int sweeps, uint64_t seed)
     {
         if (D_ < 1) return;
-        std::vector<int> hs, ws;
+        Counts cnt(*this);
         uint64_t rs = seed ^ 0x5851F42D4C957F2Dull;
+        int hs[4], ws[4];
         for (int sw = 0; sw < sweeps; ++sw) {
             for (int u = 0; u < n_; ++u) {
                 const int dg = deg_[u];
                 if (dg < 2) continue;
-                hs.clear();
-                ws.clear();
-                threads_of(u, hs, ws);
+                const int t0 = slot_of_[u] * rb_, t1 = t0 + rb_ - 1;
+                int nh = 0, nw = 0;
+                for (int h = t0 / 16; h <= t1 / 16; ++h) hs[nh++] = h;
+                for (int w = t0 / 32; w <= t1 / 32; ++w) ws[nw++] = w;
+                auto cost = [&]() {
+                    int64_t c = 0;
+                    for (int d = 0; d < dg; ++d) {
+                        for (int q = 0; q < nh; ++q) c += 4 * cnt.max8[hs[q] * D_ + d];
+                        for (int q = 0; q < nw; ++q) c += cnt.max4[ws[q] * D_ + d];
+                    }
+                    return c;
+                };
                 int32_t* row = &nbr_[(size_t)u * kMaxDeg];
                 int32_t best[kMaxDeg], cur[kMaxDeg];
                 std::copy(row, row + dg, best);
-                int64_t best_cost = weighted(hs, ws, dg);
+                int64_t best_cost = cost();
                 if (dg <= 4) {
-                    // the best order, a uniform choice among equal ones (walks plateaus)
                     std::copy(row, row + dg, cur);
                     std::sort(cur, cur + dg);
                     int ties = 0;
                     best_cost = INT64_MAX;
                     do {
-                        std::copy(cur, cur + dg, row);
-                        const int64_t c = recompute(hs, ws, dg);
+                        cnt.set_row(u, cur);
+                        const int64_t c = cost();
                         if (c < best_cost) {
                             best_cost = c;
                             ties = 1;
@@ -158,43 +168,94 @@ public:
                     for (int k = 0; k < 24; ++k) {
                         const uint64_t r = next(s);
                         const int a = (int)(r % (uint64_t)dg), b = (int)((r >> 20) % (uint64_t)dg);
-                        std::copy(best, best + dg, row);
-                        std::swap(row[a], row[b]);
-                        const int64_t c = recompute(hs, ws, dg);
+                        std::copy(best, best + dg, cur);
+                        std::swap(cur[a], cur[b]);
+                        cnt.set_row(u, cur);
+                        const int64_t c = cost();
                         if (c <= best_cost) {
                             best_cost = c;
-                            std::copy(row, row + dg, best);
+                            std::copy(cur, cur + dg, best);
                         }
                     }
                 }
-                std::copy(best, best + dg, row);
-                recompute(hs, ws, dg);
+                cnt.set_row(u, best);
             }
         }
-        uint64_t s = seed;
-        for (int64_t m = 0; m < slot_moves && n_ > 1; ++m) {
-            const uint64_t r = next(s);
-            const int u = (int)((r >> 8) % (uint64_t)n_);
-            int v = (int)((r >> 36) % (uint64_t)(n_ - 1));
-            if (v >= u) ++v;
-            hs.clear();
-            ws.clear();
-            threads_of(u, hs, ws);
-            threads_of(v, hs, ws);
-            for (int q = 0; q < deg_[u]; ++q) threads_of(nbr_[(size_t)u * kMaxDeg + q], hs, ws);
-            for (int q = 0; q < deg_[v]; ++q) threads_of(nbr_[(size_t)v * kMaxDeg + q], hs, ws);
-            dedup(hs);
-            dedup(ws);
-            const int64_t before = weighted(hs, ws, D_);
-            swap_slots(u, v);
-            if (recompute(hs, ws, D_) > before) {
-                swap_slots(u, v);
-                recompute(hs, ws, D_);
-            }
-        }
+        refresh();
     }
 
 private:
+    // Per cell (half-warp or warp, round) the multiplicity of every word read, the distinct words
+    // per bank, how many banks hold each count, and the largest count (the cell's passes).
+    struct Counts {
+        GatherLayout& L;
+        std::vector<uint8_t> mult8, mult4, bank8, bank4;
+        std::vector<uint16_t> hist8, hist4;
+        std::vector<int> max8, max4;
+
+        explicit Counts(GatherLayout& l) : L(l)
+        {
+            const size_t c8 = (size_t)L.H_ * L.D_, c4 = (size_t)L.W_ * L.D_;
+            mult8.assign(c8 * L.T_, 0);
+            mult4.assign(c4 * L.T_, 0);
+            bank8.assign(c8 * 16, 0);
+            bank4.assign(c4 * 32, 0);
+            hist8.assign(c8 * 17, 0);
+            hist4.assign(c4 * 33, 0);
+            max8.assign(c8, 0);
+            max4.assign(c4, 0);
+            for (size_t c = 0; c < c8; ++c) hist8[c * 17] = 16;
+            for (size_t c = 0; c < c4; ++c) hist4[c * 33] = 32;
+            for (int t = 0; t < L.T_; ++t)
+                for (int d = 0; d < L.D_; ++d) add(t, d, L.word_of(t, d), +1);
+        }
+
+        void add(int t, int d, int word, int sign)
+        {
+            bump(t >> 4, d, word, sign, 16, mult8, bank8, hist8, max8);
+            bump(t >> 5, d, word, sign, 32, mult4, bank4, hist4, max4);
+        }
+
+        void bump(int g, int d, int word, int sign, int banks, std::vector<uint8_t>& mult, std::vector<uint8_t>& bank,
+                  std::vector<uint16_t>& hist, std::vector<int>& mx)
+        {
+            const size_t c = (size_t)g * L.D_ + d;
+            uint8_t& m = mult[c * L.T_ + word];
+            if (sign > 0 ? m++ != 0 : --m != 0) return;  // a word already (still) read: no bank change
+            uint8_t& b = bank[c * banks + word % banks];
+            uint16_t* h = &hist[c * (banks + 1)];
+            --h[b];
+            b = (uint8_t)(b + sign);
+            ++h[b];
+            if (b > mx[c]) mx[c] = b;
+            while (mx[c] > 0 && h[mx[c]] == 0) --mx[c];
+        }
+
+        // spin u's reads in the given order (rounds below its degree)
+        void set_row(int u, const int32_t* order)
+        {
+            int32_t* row = &L.nbr_[(size_t)u * kMaxDeg];
+            for (int d = 0; d < L.deg_[u]; ++d) {
+                if (row[d] == order[d]) continue;
+                for (int lp = 0; lp < L.rb_; ++lp) {
+                    const int t = L.slot_of_[u] * L.rb_ + lp;
+                    add(t, d, L.slot_of_[row[d]] * L.rb_ + lp, -1);
+                    add(t, d, L.slot_of_[order[d]] * L.rb_ + lp, +1);
+                }
+                row[d] = order[d];
+            }
+        }
+    };
+
+    // the word thread t reads in round d
+    int word_of(int t, int d) const
+    {
+        const int sl = t / rb_, lp = t - sl * rb_;
+        const int i = spin_at_[sl];
+        const int c = d < deg_[i] ? nbr_[(size_t)i * kMaxDeg + d] : i;
+        return slot_of_[c] * rb_ + lp;
+    }
+
     static int64_t sum(const std::vector<int>& v)
     {
         int64_t c = 0;
@@ -210,12 +271,6 @@ private:
         return z ^ (z >> 31);
     }
 
-    static void dedup(std::vector<int>& v)
-    {
-        std::sort(v.begin(), v.end());
-        v.erase(std::unique(v.begin(), v.end()), v.end());
-    }
-
     void refresh()
     {
         for (int h = 0; h < H_; ++h)
@@ -229,14 +284,6 @@ private:
         std::swap(slot_of_[u], slot_of_[v]);
         spin_at_[slot_of_[u]] = u;
         spin_at_[slot_of_[v]] = v;
-    }
-
-    // the half-warps and warps holding spin x's threads (appended)
-    void threads_of(int x, std::vector<int>& hs, std::vector<int>& ws) const
-    {
-        const int t0 = slot_of_[x] * rb_, t1 = t0 + rb_ - 1;
-        for (int h = t0 / 16; h <= t1 / 16; ++h) hs.push_back(h);
-        for (int w = t0 / 32; w <= t1 / 32; ++w) ws.push_back(w);
     }
 
     // passes of the `len` threads from t0 in round d, words distinct modulo `banks`
@@ -259,28 +306,6 @@ private:
             mx = std::max(mx, ++cnt[word % banks]);
         }
         return mx;
-    }
-
-    // weighted passes of rounds < dn in the given cells, from the cache
-    int64_t weighted(const std::vector<int>& hs, const std::vector<int>& ws, int dn) const
-    {
-        int64_t c = 0;
-        for (int d = 0; d < dn; ++d) {
-            for (int h : hs) c += 4 * c8_[h * D_ + d];
-            for (int w : ws) c += c4_[w * D_ + d];
-        }
-        return c;
-    }
-
-    // the same, recomputed into the cache
-    int64_t recompute(const std::vector<int>& hs, const std::vector<int>& ws, int dn)
-    {
-        int64_t c = 0;
-        for (int d = 0; d < dn; ++d) {
-            for (int h : hs) c += 4 * (c8_[h * D_ + d] = passes(16 * h, 16, d, 16));
-            for (int w : ws) c += (c4_[w * D_ + d] = passes(32 * w, 32, d, 32));
-        }
-        return c;
     }
 
     // read (i, d), spin i's round-d read (its d-th neighbour, or itself past its degree):
@@ -350,8 +375,10 @@ inline bool plan_gather_layout(int n, int64_t E, const int32_t* ei, const int32_
     const uint64_t seed = 0x243F6A8885A308D3ull ^ ((uint64_t)n << 32) ^ (uint64_t)E;
     GatherLayout col(n, fullest_warp_rb(n), nbr, deg);
     GatherLayout lay = col;
-    lay.balance_slots(10LL * n, seed, 0.0);
-    lay.order_reads(10, 0, seed + 1);
+    // effort: 3n slot exchanges, 3 to 10 order sweeps (more for small graphs); 10 sweeps at
+    // n = 1024 buy 3 of 383 8-byte passes for twice the time (a few ms per build)
+    lay.balance_slots(3LL * n, seed, 0.0);
+    lay.order_reads(std::max(3, std::min(10, 3000 / n)), seed + 1);
     const GatherLayout& pick = 4 * lay.passes8() + lay.passes4() <= 4 * col.passes8() + col.passes4() ? lay : col;
     if (passes) {
         passes[0] = col.passes8();

@@ -7,6 +7,7 @@ Everything here is marshalling and orchestration; each computation is one C-ABI 
 """
 from __future__ import annotations
 
+import os
 import time
 
 import numpy as np
@@ -72,6 +73,25 @@ class Instance:
             self.close()
         except Exception:
             pass
+
+
+def create_instances(srcs, stream=None, threads=None):
+    """``Instance`` of every source, built on host threads (the build's host part, the samplers'
+    shared-memory layout, runs in parallel; the device part is ordered on ``stream``)."""
+    import concurrent.futures
+
+    srcs = list(srcs)
+    if len(srcs) < 2:
+        return [Instance(s, stream) for s in srcs]
+    dev = torch.cuda.current_device()
+
+    def build(s):
+        torch.cuda.set_device(dev)
+        return Instance(s, stream)
+
+    workers = threads or min(len(srcs), os.cpu_count() or 1, 16)
+    with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
+        return list(ex.map(build, srcs))
 
 
 class Archive:
@@ -461,7 +481,7 @@ def time_to_target_batch(srcs, targets, params, R: int, seed: int = 0, max_round
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     B = len(srcs)
-    insts = [Instance(s) for s in srcs]
+    insts = create_instances(srcs)
     archs = [Archive(s.n, s.K, capacity=capacity, max_batch=R) for s in srcs]
     K = insts[0].K
     active = list(range(B))
