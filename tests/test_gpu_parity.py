@@ -806,3 +806,65 @@ def test_two_spins_per_thread_from_a_given_state_and_schedule(M, P, monkeypatch)
         M.moq_sample(inst.handle, lam, R, p, 8, 0, bits)
         out[two] = (bits.cpu(), xo.cpu())
     assert torch.equal(out["0"][0], out["1"][0]) and torch.equal(out["0"][1], out["1"][1])
+
+
+@pytest.mark.parametrize("layout", ["0", "1"])
+@pytest.mark.parametrize("form", ["single", "pair", "two_spin"])
+@pytest.mark.parametrize("name,variant", [("reg3_n1024_K3", "dsb"), ("reg3_n1024_K3", "bsb"), ("heavyhex_K4", "bsb")])
+def test_force_matches_fp64_in_every_form_and_layout(M, P, oracle, monkeypatch, layout, form, name, variant):
+    # the one-step force of every FP32 sparse form, on the bank-conflict layout (gather order
+    # changes the FP32 summation order only) and on the plain one, within the normwise bound
+    monkeypatch.setenv("MOQ_SB_LAYOUT", layout)
+    monkeypatch.setenv("MOQ_SB_PAIR", "0" if form == "single" else "1")
+    monkeypatch.setenv("MOQ_SB_TWOSPIN", "1" if form == "two_spin" else "0")
+    src = INSTANCES[name]()
+    inst = P.Instance(src)
+    R = 41
+    lam = wl.dirichlet_lambdas(R, src.K, 5)
+    rng = np.random.default_rng(2)
+    x0 = rng.uniform(-0.5, 0.5, (R, src.n)).astype(np.float32)
+    dt = 2.0 ** -10
+    y_out = torch.zeros((R, src.n), dtype=torch.float32, device="cuda")
+    x_out = torch.zeros_like(y_out)
+    p = M.moq_default_params(variant=variant, steps=1, dt=dt, a0=1.0, alpha=0.0,
+                             schedule=torch.ones(1, device="cuda"), x_init=_dev(x0, torch.float32),
+                             y_init=torch.zeros((R, src.n), device="cuda"), x_out=x_out, y_out=y_out)
+    bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+    M.moq_sample(inst.handle, _dev(lam, torch.float32), R, p, 0, 0, bits)
+    ref = oracle.sb(src, lam.astype(np.float64), variant=variant, steps=1, dt=dt, a0=1.0, alpha=0.0,
+                    schedule=[1.0], x_init=x0.astype(np.float64), y_init=np.zeros((R, src.n)))
+    f_gpu = y_out.cpu().numpy().astype(np.float64) / dt
+    phi = np.where(x0 >= 0, 1.0, -1.0) if variant == "dsb" else x0.astype(np.float64)
+    scale = _abs_force_scale(src, lam, phi, ref["c0"])
+    err = np.abs(f_gpu - ref["y"] / dt)
+    assert np.all(err <= FORCE_RTOL * scale + 1e-30), float((err / np.maximum(scale, 1e-30)).max())
+    assert np.allclose(x_out.cpu().numpy(), ref["x"], rtol=0, atol=1e-6)
+    got = wl.bits_to_signs(bits.cpu().numpy().view(np.uint64), src.n) < 0
+    assert np.array_equal(got, x_out.cpu().numpy() < 0)
+
+
+@pytest.mark.parametrize("n,R", [(641, 1), (641, 2), (999, 3), (1023, 5), (700, 64)])
+def test_two_spins_and_quads_at_shape_edges(M, P, monkeypatch, n, R):
+    # odd n, the first size past the block limit of the pair forms, replica counts below one
+    # block: the two-spin (FP32) and four-replica (FP16) forms against their pair forms, bit for bit
+    if n % 2:  # a 3-regular graph on n - 1 spins and one more spin joined to two of them
+        base = wl.random_regular(n - 1, 47, K=3)
+        ei = np.concatenate([base.ei, np.array([0, 1], np.int32)])
+        ej = np.concatenate([base.ej, np.array([n - 1, n - 1], np.int32)])
+        w = np.concatenate([base.w, np.array([[5, -7], [3, 9], [-2, 4]], np.int32)], axis=1)
+        src = wl.Instance(n, ei, ej, w)
+    else:
+        src = wl.random_regular(n, 47, K=3)
+    inst = P.Instance(src)
+    lam = torch.from_numpy(wl.dirichlet_lambdas(R, 3, 9)).cuda()
+    for prec, knob in (("fp32", "MOQ_SB_TWOSPIN"), ("fp16", "MOQ_SB_QUAD")):
+        out = {}
+        for v in ("0", "1"):
+            monkeypatch.setenv(knob, v)
+            monkeypatch.setenv("MOQ_SB_PAIR", "1")
+            xo = torch.zeros((R, src.n), device="cuda")
+            bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+            p = M.moq_default_params(steps=77, dt=0.5, alpha=0.1, precision=prec, x_out=xo)
+            M.moq_sample(inst.handle, lam, R, p, 10, 1, bits)
+            out[v] = (bits.cpu(), xo.cpu())
+        assert torch.equal(out["0"][0], out["1"][0]) and torch.equal(out["0"][1], out["1"][1]), prec
