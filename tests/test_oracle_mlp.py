@@ -120,3 +120,22 @@ def test_bf16_variant_rounds_within_its_bound(oracle):
     rel = np.linalg.norm(gb - g) / np.linalg.norm(g)
     assert 1e-5 < rel < 8 * 2.0 ** -8
     assert 0 < abs(Lb - L) / L < 8 * 2.0 ** -8
+
+
+def test_gradient_descent_fits_a_tiny_dataset_exactly(oracle):
+    # the exact-fit check: 6 points, 4 targets each, and a network with many more parameters
+    # than targets; plain gradient descent on the oracle's loss gradient drives the loss to ~0
+    # (a sign error or a dropped term in the gradient stalls it far above)
+    rng = np.random.default_rng(4)
+    X, T = rng.normal(size=(6, DIN)), rng.uniform(-1, 1, size=(6, DOUT))
+    p = rng.normal(0, 0.3, oracle.mlp_param_count(DIN, H, DOUT))
+    loss0, _ = oracle.mlp_loss_grad(p, X, T, DIN, H, DOUT)
+    m, v = np.zeros_like(p), np.zeros_like(p)
+    for t in range(1, 3001):  # Adam on the oracle's gradient
+        loss, g = oracle.mlp_loss_grad(p, X, T, DIN, H, DOUT)
+        m = 0.9 * m + 0.1 * g
+        v = 0.999 * v + 0.001 * g * g
+        p -= 1e-2 * (m / (1 - 0.9 ** t)) / (np.sqrt(v / (1 - 0.999 ** t)) + 1e-12)
+    loss, _ = oracle.mlp_loss_grad(p, X, T, DIN, H, DOUT)
+    assert loss < 1e-6 * loss0 and loss < 1e-6, (loss0, loss)
+    assert np.allclose(oracle.mlp_forward(p, X, DIN, H, DOUT), T, atol=2e-3)
