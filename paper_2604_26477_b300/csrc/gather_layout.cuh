@@ -375,10 +375,11 @@ inline bool plan_gather_layout(int n, int64_t E, const int32_t* ei, const int32_
     const uint64_t seed = 0x243F6A8885A308D3ull ^ ((uint64_t)n << 32) ^ (uint64_t)E;
     GatherLayout col(n, fullest_warp_rb(n), nbr, deg);
     GatherLayout lay = col;
-    // effort: 3n slot exchanges, 3 to 10 order sweeps (more for small graphs); 10 sweeps at
-    // n = 1024 buy 3 of 383 8-byte passes for twice the time (a few ms per build)
+    // effort: 3n slot exchanges and 3 order sweeps (0.2 ms at n = 42, 3 ms at n = 1024, which is
+    // part of every time-to-target clock); 10 sweeps buy 3 of 383 8-byte passes at n = 1024 and
+    // 3 of 40 at n = 42 for three times the time
     lay.balance_slots(3LL * n, seed, 0.0);
-    lay.order_reads(std::max(3, std::min(10, 3000 / n)), seed + 1);
+    lay.order_reads(3, seed + 1);
     const GatherLayout& pick = 4 * lay.passes8() + lay.passes4() <= 4 * col.passes8() + col.passes4() ? lay : col;
     if (passes) {
         passes[0] = col.passes8();
