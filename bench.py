@@ -458,8 +458,13 @@ def batching_arm(args, rank, world):
     insts = P.create_instances(srcs)
     batch = P.Batch(insts, [R] * len(insts))
     batch.lam.copy_(torch.from_numpy(wl.dirichlet_lambdas(batch.total_R, K, 99 + rank)))
-    params = M.moq_default_params(variant="dsb", steps=T, dt=0.5, alpha=0.15)
-    tile, timings = batch.tune(params, probe_steps=64)
+    fp16 = getattr(args, "precision", "fp32") == "fp16"
+    params = M.moq_default_params(variant="dsb", steps=T, dt=0.5, alpha=0.15, precision=args.precision if fp16 else "fp32")
+    if fp16:  # the float16 form runs through per-instance launches only
+        batch.set_tiles(0, 0)
+        tile, timings = (0, 0), {}
+    else:
+        tile, timings = batch.tune(params, probe_steps=64)
     archives = [P.Archive(s.n, K, capacity=1 << 14, max_batch=R) for s in srcs]
     s = torch.cuda.Stream(device=dev)
     sp = s.cuda_stream
@@ -500,19 +505,20 @@ def batching_arm(args, rank, world):
     dev_s = shard.max_over_ranks([sum(a.elapsed_time(b) for a, b in ev) / 1e3])[0]
     units = float(sum(src.n for src in srcs)) * R * T * args.steps
     value = shard.sum_over_ranks([units])[0] / dev_s
-    ops = ops_per_spin_update(float(np.mean([2.0 * src.E / src.n for src in srcs])))
+    ops = (ops_per_spin_update_fp16 if fp16 else ops_per_spin_update)(float(np.mean([2.0 * src.E / src.n for src in srcs])))
     achieved = ops * units / dev_s / 1e12
     fronts = [a.size() for a in archives]
     return {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_s / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16" if fp16 else "f32", "data": "synthetic",
             "config": {"workload": f"batching: {len(srcs)} random 3-regular instances n~U[42,1024] even, K=3, "
                                    f"weights {{-100..100}}\\{{0}}, R={R} each, dsb T={T} dt=0.5 alpha=0.15; step = "
                                    "CUDA graph of the batched sampler (persistent tile or per-instance launches, chosen by the "
                                    "autotuner) + batched cuts + per-instance Pareto merge",
                        "sum_n": int(sum(src.n for src in srcs)), "tile": list(tile), "tile_timings_ms": timings,
                        "l2": "flushed (256 MB write) before every step"},
-            "roofline": {"bound": "alu", "kernel": ("k_sb_sparse per instance" if tuple(tile) == (0, 0) else "k_sb_batch")
+            "roofline": {"bound": "alu", "kernel": (("k_sb_sparse_h per instance (float16)" if fp16 else "k_sb_sparse per instance")
+                                                    if tuple(tile) == (0, 0) else "k_sb_batch")
                          + " (whole step timed)", "achieved": achieved,
                          "peak": peak_alu_tops(), "unit": "Tops/s", "frac": achieved / peak_alu_tops(),
                          "ops_per_spin_update": ops},
