@@ -306,7 +306,7 @@ def gpu_arm(args, rank, world):
     # pinned host memory, and the step's result -- the hypervolume and the front itself (cut
     # vectors, configurations, sample indices) -- read back to the host every step
     # (the same two-stage pipeline: the copy-in and sampling of step s + 1 overlap step s's tail)
-    e2e_steps = max(1, min(args.steps, 10))
+    e2e_steps = max(1, min(args.steps, 20))
     lam_host = torch.from_numpy(np.stack([wl.dirichlet_lambdas(R * world, K, 777 + s)[first:first + R]
                                           for s in range(e2e_steps)])).pin_memory()
     lam_devs = [torch.empty_like(lam_host[0], device=dev) for _ in range(2)]
