@@ -161,3 +161,21 @@ def test_batch_time_to_target_reaches_every_instance(M, P, oracle, batched, lear
     res = P.time_to_target_batch(srcs, targets, params, R, seed=1, max_rounds=64, batched=batched, learned=learned)
     assert res["reached"] and all(1 <= r <= res["rounds"] for r in res["rounds_per_instance"])
     assert res["samples"] <= R * len(srcs) * res["rounds"]
+
+
+def test_parallel_instance_builds_match_sequential_ones(M, P):
+    # pipeline.create_instances builds on host threads (the layout planning runs in parallel):
+    # every instance is the sequential build's, so the samples are the same bits
+    srcs = _srcs()
+    seq = [P.Instance(s) for s in srcs]
+    par = P.create_instances(srcs)
+    p = M.moq_default_params(steps=90, dt=0.5, alpha=0.1)
+    for a, b, src in zip(seq, par, srcs):
+        assert a.info == b.info
+        lam = torch.from_numpy(wl.dirichlet_lambdas(70, 3, 12)).cuda()
+        out = []
+        for inst in (a, b):
+            bits = torch.zeros((70, inst.W), dtype=torch.int64, device="cuda")
+            M.moq_sample(inst.handle, lam, 70, p, 3, 1, bits)
+            out.append(bits.cpu())
+        assert torch.equal(out[0], out[1])
