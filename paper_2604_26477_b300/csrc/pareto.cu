@@ -8,7 +8,8 @@
 //    equal candidate has a lower index;
 //  - member a survives iff no candidate dominates it (a dominated member is dominated by
 //    some surviving vector too, since domination is transitive and the sets are finite).
-// Both tests are all-pairs over shared-memory tiles on a 2-D grid (a tile of vectors x a
+// The tests run either one warp per tested vector (k_dominated_warp, the default) or, as below,
+// all-pairs over shared-memory tiles on a 2-D grid (a tile of vectors x a
 // chunk of the vectors they are compared with, so even one tile of candidates fills the
 // GPU), with a block-wide early exit once every thread's vector is known to be dominated;
 // blocks only ever set "dominated" flags (zeroed per call). Survivors are compacted in order --
@@ -266,6 +267,62 @@ __global__ void __launch_bounds__(kTile) k_dominated_archive(const int64_t* __re
         __syncthreads();
     }
 }
+
+// ---- one warp per tested vector ----------------------------------------------------
+// The same tests with one warp per tested vector: its lanes take 32 comparators at a time,
+// read straight from global memory (coalesced; the eight warps of a block read the same
+// comparators, which L1 keeps), and the warp stops at the first chunk that holds a dominator
+// (a vote), so a vector dominated early costs a few chunks where the tile form keeps a whole
+// warp scanning until its last vector is decided.
+//   MODE 0: a candidate against the archive (>= everywhere: dominated, or an equal member,
+//           whose index is lower);
+//   MODE 1: a candidate against the candidates (dominated, or equal with a lower index);
+//   MODE 2: an archive member against the candidates (strictly dominated).
+// Counts may live on the device (the archive size, the compacted survivors); flags already
+// set are skipped and only ever set.
+template <int KT, int MODE>
+__global__ void __launch_bounds__(kTile) k_dominated_warp(const int64_t* __restrict__ vecs, int64_t n_vecs,
+                                                          const int64_t* __restrict__ n_vecs_dev, const int64_t* __restrict__ cmp,
+                                                          int64_t n_cmp, const int64_t* __restrict__ n_cmp_dev, int32_t* flag)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nv = n_vecs_dev ? min(n_vecs, *n_vecs_dev) : n_vecs;
+    const int64_t nc = n_cmp_dev ? min(n_cmp, *n_cmp_dev) : n_cmp;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < nv; c += nw) {
+        if (flag[c]) continue;  // the same word for every lane
+        int64_t u[KT];
+#pragma unroll
+        for (int k = 0; k < KT; ++k) u[k] = vecs[c * KT + k];
+        bool dom = false;
+        for (int64_t base = 0; base < nc && !dom; base += 32) {
+            const int64_t j = base + lane;
+            bool d = false;
+            if (j < nc) {
+                bool ge = true, gt = false;
+#pragma unroll
+                for (int k = 0; k < KT; ++k) {
+                    const int64_t v = cmp[j * KT + k];
+                    ge &= v >= u[k];
+                    gt |= v > u[k];
+                }
+                d = ge && (MODE == 0 || gt || (MODE == 1 && j < c));
+            }
+            dom = __any_sync(kFull, d);
+        }
+        if (dom && lane == 0) flag[c] = 1;
+    }
+}
+
+// The filter form: one warp per tested vector (default) or a thread per vector over
+// shared-memory tiles (MOQ_FILTER_FORM=thread)
+bool warp_filter()
+{
+    const char* env = getenv("MOQ_FILTER_FORM");
+    return !(env && env[0] == 't');
+}
+
+unsigned warp_grid(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kTile / 32), 148 * 16)); }
 
 // ---- large batches: deduplication and survivors ----------------------------------
 // A batch of many samples holds few distinct cut vectors and, once the archive has grown,
@@ -543,16 +600,28 @@ cudaError_t launch_filters(moq_archive* a, const int64_t* cuts, int64_t M, cudaS
     if (e == cudaSuccess && M > 0) e = cudaMemsetAsync(a->flag_cand, 0, sizeof(int32_t) * M, st);
     if (e != cudaSuccess) return e;
     if (M > 0) {
-        e = cudaMemsetAsync(a->range, 0xff, sizeof(unsigned long long) * KT, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(a->range + KT, 0, sizeof(unsigned long long) * KT, st);
-        if (e != cudaSuccess) return e;
-        k_value_range<KT><<<148, kTile, 0, st>>>(a->cuts[a->cur], a->d_count, cuts, M, a->range);
+        const bool wf = warp_filter();
+        if (!wf) {  // the value range decides the tile form's packed comparisons
+            e = cudaMemsetAsync(a->range, 0xff, sizeof(unsigned long long) * KT, st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(a->range + KT, 0, sizeof(unsigned long long) * KT, st);
+            if (e != cudaSuccess) return e;
+            k_value_range<KT><<<148, kTile, 0, st>>>(a->cuts[a->cur], a->d_count, cuts, M, a->range);
+        }
         const unsigned nchunks = (unsigned)ceil_div(M, kChunk), gtiles = (unsigned)ceil_div(M, kTile);
         const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(a->cap, kTile), 32));
         if (M < a->large_min) {
-            k_dominated_candidates<KT><<<dim3(gtiles, kArchChunks + nchunks), kTile, 0, st>>>(
-                a->cuts[a->cur], a->d_count, cuts, M, a->flag_cand, a->range, kArchChunks, nullptr);
-            k_dominated_archive<KT><<<dim3(gx, nchunks), kTile, 0, st>>>(a->cuts[a->cur], a->d_count, cuts, M, a->flag_arch, nullptr);
+            if (wf) {
+                k_dominated_warp<KT, 0><<<warp_grid(M), kTile, 0, st>>>(cuts, M, nullptr, a->cuts[a->cur], a->cap, a->d_count,
+                                                                         a->flag_cand);
+                k_dominated_warp<KT, 1><<<warp_grid(M), kTile, 0, st>>>(cuts, M, nullptr, cuts, M, nullptr, a->flag_cand);
+                k_dominated_warp<KT, 2><<<warp_grid(a->cap), kTile, 0, st>>>(a->cuts[a->cur], a->cap, a->d_count, cuts, M, nullptr,
+                                                                              a->flag_arch);
+            } else {
+                k_dominated_candidates<KT><<<dim3(gtiles, kArchChunks + nchunks), kTile, 0, st>>>(
+                    a->cuts[a->cur], a->d_count, cuts, M, a->flag_cand, a->range, kArchChunks, nullptr);
+                k_dominated_archive<KT><<<dim3(gx, nchunks), kTile, 0, st>>>(a->cuts[a->cur], a->d_count, cuts, M, a->flag_arch,
+                                                                              nullptr);
+            }
         } else {
             const unsigned g256 = (unsigned)ceil_div(M, 256);
             e = cudaMemsetAsync(a->table, 0xff, sizeof(int32_t) * ((size_t)a->table_mask + 1), st);
@@ -561,14 +630,24 @@ cudaError_t launch_filters(moq_archive* a, const int64_t* cuts, int64_t M, cudaS
             if (e != cudaSuccess) return e;
             k_dedup_insert<KT><<<g256, 256, 0, st>>>(cuts, M, a->table, a->table_mask);
             k_dedup_mark<KT><<<g256, 256, 0, st>>>(cuts, M, a->table, a->table_mask, a->flag_cand);
-            k_dominated_candidates<KT><<<dim3(gtiles, kArchChunks), kTile, 0, st>>>(a->cuts[a->cur], a->d_count, cuts, M,
-                                                                                   a->flag_cand, a->range, kArchChunks, nullptr);
+            if (wf)
+                k_dominated_warp<KT, 0><<<warp_grid(M), kTile, 0, st>>>(cuts, M, nullptr, a->cuts[a->cur], a->cap, a->d_count,
+                                                                         a->flag_cand);
+            else
+                k_dominated_candidates<KT><<<dim3(gtiles, kArchChunks), kTile, 0, st>>>(a->cuts[a->cur], a->d_count, cuts, M,
+                                                                                       a->flag_cand, a->range, kArchChunks, nullptr);
             k_compact_survivors<KT><<<g256, 256, 0, st>>>(cuts, M, a->flag_cand, a->ccuts, a->cidx,
                                                           reinterpret_cast<unsigned long long*>(a->d_m));
-            k_dominated_candidates<KT><<<dim3(gtiles, nchunks), kTile, 0, st>>>(a->cuts[a->cur], a->d_count, a->ccuts, M, a->cflag,
-                                                                               a->range, 0, a->d_m);
-            k_dominated_archive<KT><<<dim3(gx, nchunks), kTile, 0, st>>>(a->cuts[a->cur], a->d_count, a->ccuts, M, a->flag_arch,
-                                                                         a->d_m);
+            if (wf) {
+                k_dominated_warp<KT, 1><<<warp_grid(M), kTile, 0, st>>>(a->ccuts, M, a->d_m, a->ccuts, M, a->d_m, a->cflag);
+                k_dominated_warp<KT, 2><<<warp_grid(a->cap), kTile, 0, st>>>(a->cuts[a->cur], a->cap, a->d_count, a->ccuts, M, a->d_m,
+                                                                              a->flag_arch);
+            } else {
+                k_dominated_candidates<KT><<<dim3(gtiles, nchunks), kTile, 0, st>>>(a->cuts[a->cur], a->d_count, a->ccuts, M,
+                                                                                   a->cflag, a->range, 0, a->d_m);
+                k_dominated_archive<KT><<<dim3(gx, nchunks), kTile, 0, st>>>(a->cuts[a->cur], a->d_count, a->ccuts, M, a->flag_arch,
+                                                                             a->d_m);
+            }
             k_survivor_flags_back<<<g256, 256, 0, st>>>(a->d_m, a->cflag, a->cidx, a->flag_cand);
         }
     }

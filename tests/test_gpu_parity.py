@@ -195,7 +195,10 @@ def _run_archive(M, P, oracle, cuts, bits, n, batches, capacity=1 << 14):
 @pytest.mark.parametrize("K,span,Mtot", [(2, 40, 3000), (3, 12, 5000), (4, 6, 4000), (8, 3, 2000), (3, 1000, 20000),
                                          # batches of 2^13 and more take the dedup / survivor path
                                          (2, 40, 90000), (4, 6, 150000), (3, 1000, 120000), (6, 4, 70000)])
-def test_pareto_archive_bit_exact(M, P, oracle, K, span, Mtot):
+@pytest.mark.parametrize("form", ["warp", "thread"])
+def test_pareto_archive_bit_exact(M, P, oracle, monkeypatch, K, span, Mtot, form):
+    # both dominance forms (one warp per tested vector, or a thread per vector over tiles)
+    monkeypatch.setenv("MOQ_FILTER_FORM", form)
     rng = np.random.default_rng(K * 7 + span)
     cuts = rng.integers(-span, span, size=(Mtot, K)).astype(np.int64)
     n = 70
@@ -207,7 +210,9 @@ def test_pareto_archive_bit_exact(M, P, oracle, K, span, Mtot):
 
 
 @pytest.mark.parametrize("K,Mtot,span,noise", [(3, 100000, 100, 6), (4, 80000, 30, 3)])
-def test_pareto_large_batches_with_large_fronts(M, P, oracle, K, Mtot, span, noise):
+@pytest.mark.parametrize("form", ["warp", "thread"])
+def test_pareto_large_batches_with_large_fronts(M, P, oracle, monkeypatch, K, Mtot, span, noise, form):
+    monkeypatch.setenv("MOQ_FILTER_FORM", form)
     # candidates near a simplex surface (fronts of thousands of points) with many exact
     # duplicates, merged in batches above and below 2^13: the dedup / survivor path and the
     # plain path must both keep the definition's front and the lowest index per vector
@@ -227,7 +232,9 @@ def test_pareto_large_batches_with_large_fronts(M, P, oracle, K, Mtot, span, noi
     (3, -(1 << 62), 1 << 63),  # near the int64 limits
     (6, 123, 30000),          # two packed words
 ])
-def test_pareto_packed_and_plain_ranges(M, P, oracle, K, offset, width):
+@pytest.mark.parametrize("form", ["warp", "thread"])
+def test_pareto_packed_and_plain_ranges(M, P, oracle, monkeypatch, K, offset, width, form):
+    monkeypatch.setenv("MOQ_FILTER_FORM", form)
     # the filter packs vectors into 16-bit lanes only when every objective spans fewer than
     # 2^15 values; both sides of that switch must give the definition's front
     rng = np.random.default_rng(K + width % 97)
