@@ -225,7 +225,9 @@ def gpu_arm(args, rank, world):
     lam_all = torch.from_numpy(np.stack([wl.dirichlet_lambdas(R * world, K, 10_000 + s)[first:first + R]
                                          for s in range(nsteps)])).to(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 126 MB L2
-    launches_per_step = 1 + 1 + 12 + 5  # sample, cuts, Pareto merge (12: dedup path), hypervolume (5 for K = 4)
+    # sample, cuts, Pareto merge (dedup path: 11 kernels with the warp-form dominance tests, 12
+    # with the tile form), hypervolume (5 for K = 4)
+    launches_per_step = 1 + 1 + (12 if os.environ.get("MOQ_FILTER_FORM", "warp").startswith("t") else 11) + 5
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
     fronts, hvs = [], []
@@ -603,8 +605,10 @@ def dense_arm(args, rank, world):
             "sampling_only_value": units / samp_s * world, "sampler_ms": samp_s / args.steps * 1e3,
             "clocks": clk.summary(), "front_points_last_step": front, "hv_last_step": int(hv[0]),
             "plain_fp32": plain, "operand_forms": forms, "forms_hv": forms_hv,
-            # c0, init, T steps, readout; cuts: signs, two products, finish; merge 12; HV 4
-            "gpu_launches": (T + 3 + 4 + 12 + 4) * args.steps}
+            # c0, init, T steps, readout; cuts: signs, two products, finish; merge (dedup path) 11
+            # with the warp-form dominance tests, 12 with the tile form; HV 4
+            "gpu_launches": (T + 3 + 4 + (12 if os.environ.get("MOQ_FILTER_FORM", "warp").startswith("t") else 11) + 4)
+                            * args.steps}
 
 
 def dense_plain_fp32(args, M, inst, d, lam, src):
