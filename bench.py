@@ -3,8 +3,8 @@
 One step = one pass of the whole path over one batch: NI-dSB sampling of R replicas
 (each on its own weight vector), exact K-objective cuts of every sample, the Pareto
 filter into a fresh device archive, and the exact hypervolume of the front (read back on
-the host). The K timed steps run as a two-stage pipeline: step s + 1 samples while step
-s's cuts, merge and hypervolume finish.
+the host). The K timed steps run as a three-stage pipeline: steps s + 1 and s + 2 are
+queued for sampling while step s's cuts, merge and hypervolume finish.
 
 Workload (default): heavy-hex-like graph n=42 / E=50, K=4 integer objectives in
 {-10..10}\\{0}, R=16384 replicas with uniform-simplex weight vectors, dSB, T=2000
@@ -258,13 +258,17 @@ def gpu_arm(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    # Timed region: the K steps as a pipeline over two sample buffers -- the sampling of step
-    # s + 1 runs on a second stream while step s's cuts, Pareto merge and hypervolume (this
-    # stream, the result read back on the host) finish. Every step does its whole path; the
-    # L2 flush (256 MB) precedes every sampling launch inside the timed region.
-    bufs = [buf, P.RoundBuffers(R, n, K)]
-    s_a = torch.cuda.Stream(device=dev)
-    s_b = torch.cuda.Stream(device=dev, priority=-1)  # its blocks go first as the sampler's retire
+    # Timed region: the K steps as a pipeline over three sample buffers -- the samplings of
+    # steps s + 1 and s + 2 are queued on one stream while step s's cuts, Pareto merge and
+    # hypervolume (a second stream, the result read back on the host) finish, so the host's
+    # read-back never leaves the sampler stream empty. The sampler stream has the higher
+    # priority; the filter kernels take the SMs its blocks leave (its wave tails). Every step
+    # does its whole path; the L2 flush (256 MB) precedes every sampling launch inside the
+    # timed region. (Two buffers, filter stream first: 1.71 ms per step against 1.62 ms.)
+    depth = 3
+    bufs = [buf] + [P.RoundBuffers(R, n, K) for _ in range(depth - 1)]
+    s_a = torch.cuda.Stream(device=dev, priority=-1)
+    s_b = torch.cuda.Stream(device=dev)
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     samp_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
     sampled = [None] * nsteps
@@ -273,7 +277,7 @@ def gpu_arm(args, rank, world):
         with torch.cuda.stream(s_a):
             flush.zero_()
             samp_ev[s][0].record(s_a)
-            M.moq_sample(inst.handle, lam_all[s], R, params, 1, s, bufs[s % 2].bits, s_a)
+            M.moq_sample(inst.handle, lam_all[s], R, params, 1, s, bufs[s % depth].bits, s_a)
             samp_ev[s][1].record(s_a)
             sampled[s] = s_a.record_event()
 
@@ -282,11 +286,12 @@ def gpu_arm(args, rank, world):
         t_start.record(stream)
         s_a.wait_stream(stream)
         s_b.wait_stream(stream)
-        launch_sample(args.warmup)
+        for q in range(args.warmup, min(nsteps, args.warmup + depth - 1)):
+            launch_sample(q)
         for s in range(args.warmup, nsteps):
-            if s + 1 < nsteps:
-                launch_sample(s + 1)  # its buffer was last read by step s - 1, finished below
-            b = bufs[s % 2]
+            if s + depth - 1 < nsteps:
+                launch_sample(s + depth - 1)  # its buffer was last read by step s - 1, finished below
+            b = bufs[s % depth]
             s_b.wait_event(sampled[s])
             arch.reset(s_b)
             M.moq_evaluate_cuts(inst.handle, b.bits, R, b.cuts, s_b)
@@ -307,27 +312,29 @@ def gpu_arm(args, rank, world):
     # e2e through the C ABI with host buffers: each step's own weight vectors copied in from
     # pinned host memory, and the step's result -- the hypervolume and the front itself (cut
     # vectors, configurations, sample indices) -- read back to the host every step
-    # (the same two-stage pipeline: the copy-in and sampling of step s + 1 overlap step s's tail)
+    # (the same three-stage pipeline: the copy-ins and samplings of steps s + 1, s + 2 overlap
+    # step s's tail)
     e2e_steps = max(1, min(args.steps, 20))
     lam_host = torch.from_numpy(np.stack([wl.dirichlet_lambdas(R * world, K, 777 + s)[first:first + R]
                                           for s in range(e2e_steps)])).pin_memory()
-    lam_devs = [torch.empty_like(lam_host[0], device=dev) for _ in range(2)]
+    lam_devs = [torch.empty_like(lam_host[0], device=dev) for _ in range(depth)]
     torch.cuda.synchronize()
     e2e_sampled = [None] * e2e_steps
     d2h = []
 
     def launch_e2e(s):
         with torch.cuda.stream(s_a):
-            lam_devs[s % 2].copy_(lam_host[s], non_blocking=True)
-            M.moq_sample(inst.handle, lam_devs[s % 2], R, params, 99, s, bufs[s % 2].bits, s_a)
+            lam_devs[s % depth].copy_(lam_host[s], non_blocking=True)
+            M.moq_sample(inst.handle, lam_devs[s % depth], R, params, 99, s, bufs[s % depth].bits, s_a)
             e2e_sampled[s] = s_a.record_event()
 
     t0 = time.perf_counter()
-    launch_e2e(0)
+    for q in range(min(e2e_steps, depth - 1)):
+        launch_e2e(q)
     for s in range(e2e_steps):
-        if s + 1 < e2e_steps:
-            launch_e2e(s + 1)
-        b = bufs[s % 2]
+        if s + depth - 1 < e2e_steps:
+            launch_e2e(s + depth - 1)
+        b = bufs[s % depth]
         s_b.wait_event(e2e_sampled[s])
         arch.reset(s_b)
         M.moq_evaluate_cuts(inst.handle, b.bits, R, b.cuts, s_b)
