@@ -875,3 +875,28 @@ def test_two_spins_and_quads_at_shape_edges(M, P, monkeypatch, n, R):
             M.moq_sample(inst.handle, lam, R, p, 10, 1, bits)
             out[v] = (bits.cpu(), xo.cpu())
         assert torch.equal(out["0"][0], out["1"][0]) and torch.equal(out["0"][1], out["1"][1]), prec
+
+
+@pytest.mark.parametrize("Mtot", [3000, 20000])
+def test_pareto_candidates_at_an_8_byte_offset(M, P, oracle, Mtot):
+    # candidate cut vectors that start 8 bytes past a 16-byte boundary take the filter's
+    # scalar loads (K = 4 rows are otherwise read in 16-byte pieces): the same front
+    K, n = 4, 42
+    rng = np.random.default_rng(Mtot)
+    cuts = rng.integers(-30, 30, size=(Mtot, K)).astype(np.int64)
+    cuts[::9] = cuts[4]
+    bits = wl.random_sign_bits(Mtot, n, 3)
+    raw = torch.zeros(Mtot * K + 1, dtype=torch.int64, device="cuda")
+    view = raw[1:].view(Mtot, K)
+    view.copy_(torch.from_numpy(cuts))
+    assert view.data_ptr() % 16 == 8
+    fronts = []
+    for c in (view, _dev(cuts, torch.int64)):
+        arch = P.Archive(n, K, capacity=1 << 14, max_batch=Mtot)
+        arch.merge(c, _bits_dev(bits), Mtot, 0)
+        fronts.append(arch.copy_out())
+        arch.close()
+    for a, b in zip(*fronts):
+        assert np.array_equal(a, b)
+    keep = oracle.pareto_filter(cuts)  # pool indices (ascending) of the distinct non-dominated vectors
+    assert np.array_equal(fronts[0][0], cuts[keep]) and np.array_equal(fronts[0][2], keep)
