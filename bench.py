@@ -59,6 +59,11 @@ def peak_alu_tops():
     return 148 * 128 * 2.032e9 / 1e12
 
 
+# L2 flush between timed steps: a write larger than the 126 MB L2 (160 MiB = 168 MB)
+FLUSH_MIB = 160
+FLUSH_NOTE = f"flushed ({FLUSH_MIB} MiB write, > the 126 MB L2) before every step"
+
+
 def peak_xu_tops():
     """Special-function (MUFU / XU pipe) peak: 148 SMs x 16 lanes x 2032 MHz; ncu's XU pipe-cycle
     counter of the sparse sampler (38 % busy for 2 MUFU ops per update at 1.53 ms) agrees."""
@@ -224,7 +229,7 @@ def gpu_arm(args, rank, world):
     # inputs resident in HBM before the timed region: one weight-vector batch per step
     lam_all = torch.from_numpy(np.stack([wl.dirichlet_lambdas(R * world, K, 10_000 + s)[first:first + R]
                                          for s in range(nsteps)])).to(dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 126 MB L2
+    flush = torch.empty(FLUSH_MIB * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 126 MB L2
     # sample, cuts, Pareto merge (dedup path: 11 kernels with the warp-form dominance tests, 12
     # with the tile form), hypervolume (5 for K = 4)
     launches_per_step = 1 + 1 + (12 if os.environ.get("MOQ_FILTER_FORM", "warp").startswith("t") else 11) + 5
@@ -263,7 +268,7 @@ def gpu_arm(args, rank, world):
     # hypervolume (a second stream, the result read back on the host) finish, so the host's
     # read-back never leaves the sampler stream empty. The sampler stream has the higher
     # priority; the filter kernels take the SMs its blocks leave (its wave tails). Every step
-    # does its whole path; the L2 flush (256 MB) precedes every sampling launch inside the
+    # does its whole path; the L2 flush (FLUSH_MIB) precedes every sampling launch inside the
     # timed region. (Two buffers, filter stream first: 1.71 ms per step against 1.62 ms.)
     depth = 3
     bufs = [buf] + [P.RoundBuffers(R, n, K) for _ in range(depth - 1)]
@@ -495,7 +500,7 @@ def batching_arm(args, rank, world):
     # sampler (one persistent launch, or one per instance in per-instance mode), batched cuts,
     # and per merge of 4096 candidates: value range, two dominance passes, count, scan, scatter, set count
     launches = (len(insts) if tuple(tile) == (0, 0) else 1) + 1 + 7 * len(archives)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flush = torch.empty(FLUSH_MIB * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
         g.replay()
     torch.cuda.synchronize()
@@ -525,7 +530,7 @@ def batching_arm(args, rank, world):
                                    "CUDA graph of the batched sampler (persistent tile or per-instance launches, chosen by the "
                                    "autotuner) + batched cuts + per-instance Pareto merge",
                        "sum_n": int(sum(src.n for src in srcs)), "tile": list(tile), "tile_timings_ms": timings,
-                       "l2": "flushed (256 MB write) before every step"},
+                       "l2": FLUSH_NOTE},
             "roofline": {"bound": "alu", "kernel": (("k_sb_sparse_h per instance (float16)" if fp16 else "k_sb_sparse per instance")
                                                     if tuple(tile) == (0, 0) else "k_sb_batch")
                          + " (whole step timed)", "achieved": achieved,
@@ -1080,11 +1085,11 @@ def plain_config_block(args):
     buf = P.RoundBuffers(R, src.n, src.K)
     nst = args.warmup + args.steps
     lam_all = torch.from_numpy(np.stack([wl.dirichlet_lambdas(R, 3, 500 + s) for s in range(nst)])).cuda()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush = torch.empty(FLUSH_MIB * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     out = {"workload": "plain: heavy-hex-like n=42 E=50 K=3 weights {-10..10}\\{0}, R=1024 uniform-simplex lambda, "
                        "FP32 dSB T=1000 dt=0.5; step = sampling + cuts + Pareto + hypervolume (read back)",
-           "steps": args.steps, "warmup": args.warmup, "l2": "flushed (256 MB write) before every step"}
+           "steps": args.steps, "warmup": args.warmup, "l2": FLUSH_NOTE}
     hv = [0]
     for alpha in (0.15, 0.0):
         params = M.moq_default_params(variant="dsb", steps=T, dt=0.5, alpha=alpha)
@@ -1135,7 +1140,7 @@ def fp16_block(args):
     buf = P.RoundBuffers(R, src.n, src.K)
     nst = args.warmup + max(1, min(args.steps, 10))
     lam_all = torch.from_numpy(np.stack([wl.dirichlet_lambdas(R, w["K"], 10_000 + s) for s in range(nst)])).cuda()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush = torch.empty(FLUSH_MIB * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     out = {"workload": "precision (n=42, K=4, R=16384, NI-dSB T=2000 dt=0.5 alpha=0.1), both forms in one process",
            "steps": nst - args.warmup}
@@ -1343,7 +1348,7 @@ def main():
                           f"alpha={w['alpha']}, cuts + Pareto + hypervolume per step",
               "n": w["n"], "K": w["K"], "R": w["R"], "T": w["T"], "variant": w["variant"], "dt": w["dt"],
               "alpha": w["alpha"], "precision": args.precision,
-              "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas x{world}",
+              "l2": FLUSH_NOTE, "parallelism": f"replicas x{world}",
               "timing": "K steps timed as one region (CUDA events): step s+1 samples on a second stream while step s's "
                         "cuts, merge and hypervolume finish; the hypervolume of every step is read back on the host",
               "prewarm_s": args.prewarm}
