@@ -879,8 +879,8 @@ def test_two_spins_and_quads_at_shape_edges(M, P, monkeypatch, n, R):
 
 @pytest.mark.parametrize("Mtot", [3000, 20000])
 def test_pareto_candidates_at_an_8_byte_offset(M, P, oracle, Mtot):
-    # candidate cut vectors that start 8 bytes past a 16-byte boundary take the filter's
-    # scalar loads (K = 4 rows are otherwise read in 16-byte pieces): the same front
+    # candidate cut vectors that start 8 bytes past a 16-byte boundary (a view into a larger
+    # tensor): the same front as from an aligned copy, and the definition's
     K, n = 4, 42
     rng = np.random.default_rng(Mtot)
     cuts = rng.integers(-30, 30, size=(Mtot, K)).astype(np.int64)
