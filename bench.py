@@ -1349,8 +1349,9 @@ def main():
               "n": w["n"], "K": w["K"], "R": w["R"], "T": w["T"], "variant": w["variant"], "dt": w["dt"],
               "alpha": w["alpha"], "precision": args.precision,
               "l2": FLUSH_NOTE, "parallelism": f"replicas x{world}",
-              "timing": "K steps timed as one region (CUDA events): step s+1 samples on a second stream while step s's "
-                        "cuts, merge and hypervolume finish; the hypervolume of every step is read back on the host",
+              "timing": "K steps timed as one region (CUDA events): steps s+1 and s+2 are queued on the (high-priority) "
+                        "sampler stream while step s's cuts, merge and hypervolume finish on a second stream; the "
+                        "hypervolume of every step is read back on the host",
               "prewarm_s": args.prewarm}
 
     if args.impl == "reference":
