@@ -469,7 +469,9 @@ def batching_arm(args, rank, world):
     torch.cuda.set_device(dev)
     R, T, K = 4096, 1500, 3
     srcs = wl.uneven_regular_batch(args.batch_instances, seed=77 + rank, K=K, wmax=100)
-    insts = P.create_instances(srcs)
+    t_build = time.perf_counter()
+    insts = P.create_instances(srcs, layout_effort=args.layout_effort)  # builds are not timed
+    t_build = time.perf_counter() - t_build
     batch = P.Batch(insts, [R] * len(insts))
     batch.lam.copy_(torch.from_numpy(wl.dirichlet_lambdas(batch.total_R, K, 99 + rank)))
     fp16 = getattr(args, "precision", "fp32") == "fp16"
@@ -530,7 +532,7 @@ def batching_arm(args, rank, world):
                                    "CUDA graph of the batched sampler (persistent tile or per-instance launches, chosen by the "
                                    "autotuner) + batched cuts + per-instance Pareto merge",
                        "sum_n": int(sum(src.n for src in srcs)), "tile": list(tile), "tile_timings_ms": timings,
-                       "l2": FLUSH_NOTE},
+                       "layout_effort": args.layout_effort, "build_s": t_build, "l2": FLUSH_NOTE},
             "roofline": {"bound": "alu", "kernel": (("k_sb_sparse_h per instance (float16)" if fp16 else "k_sb_sparse per instance")
                                                     if tuple(tile) == (0, 0) else "k_sb_batch")
                          + " (whole step timed)", "achieved": achieved,
@@ -1328,6 +1330,9 @@ def main():
     ap.add_argument("--dense-fp8-steps", type=int, default=300,
                     help="SB steps per operand form (BF16, E4M3, split) in the dense workload's comparison (0: skip it)")
     ap.add_argument("--batch-instances", type=int, default=256)
+    ap.add_argument("--layout-effort", type=int, default=1000,
+                    help="slot exchanges per spin of the longer shared-memory layout search for the batching "
+                         "workload's instance builds (regular graphs; outside the timed region; 0: default planner)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and not args.cpu_baseline_worker:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

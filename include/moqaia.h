@@ -125,7 +125,10 @@ int moq_create_instance_dense(int32_t n, int32_t K, const int32_t* J_upper, void
  * lengths the degrees); passes[4] or NULL: 8-byte and 4-byte shared-memory passes of one
  * gather step over all warps for the column layout, then for the chosen one. Setting
  * MOQ_SB_LAYOUT=0 in the environment makes moq_create_instance keep slots by decreasing
- * degree and rows by column. Errors: MOQ_ERR_ARG (NULL outputs), MOQ_ERR_UNSUPPORTED (n
+ * degree and rows by column; MOQ_SB_LAYOUT_EFFORT=m > 0 adds, for regular graphs whose blocks
+ * hold one replica per slot, a longer search (m * n slot exchanges, about 0.15 ms per exchange
+ * per spin at n = 1024: worth it for long jobs) aimed at the 8-byte gathers, kept where it is
+ * better; both are read on every call. Errors: MOQ_ERR_ARG (NULL outputs), MOQ_ERR_UNSUPPORTED (n
  * outside [2, 1024], a degree above 8, an invalid or repeated edge, E = 0). */
 int moq_plan_gather_layout(int32_t n, int64_t E, const int32_t* ei, const int32_t* ej, int32_t* slot_spin, int32_t* gather,
                            int64_t* passes);

@@ -27,6 +27,7 @@
 #pragma once
 
 #include <stdint.h>
+#include <stdlib.h>
 
 #include <algorithm>
 #include <cmath>
@@ -82,6 +83,15 @@ public:
     int64_t ideal4() const { return (int64_t)W_ * D_; }
     const std::vector<int32_t>& slot_spin() const { return spin_at_; }
     const std::vector<int32_t>& neighbours() const { return nbr_; }  // gather order, rows of kMaxDeg
+
+    // take the given slot order and gather rows (a permutation of each row's neighbours)
+    void set_layout(const std::vector<int32_t>& slot_spin, const std::vector<int32_t>& rows)
+    {
+        spin_at_ = slot_spin;
+        for (int s = 0; s < n_; ++s) slot_of_[spin_at_[s]] = s;
+        nbr_ = rows;
+        refresh();
+    }
 
     void balance_slots(int64_t moves, uint64_t seed, double temp)
     {
@@ -347,6 +357,284 @@ private:
 
 namespace moq {
 
+// One replica per block slot (Rb = 1) on a graph whose spins all have degree D: thread t holds
+// slot t, so a read's 8-byte bank is the position (slot mod 16) of the read spin inside its own
+// half-warp, and a half-warp's round is conflict-free when its 16 reads hit 16 distinct
+// positions. If every position takes exactly D of a half-warp's reads, the reads of that
+// half-warp split into D rounds of 16 distinct positions (a D-regular bipartite multigraph of
+// spins and positions is the union of D perfect matchings, König), found by alternating paths.
+// The slots are chosen by annealing the sum of squared (half-warp, position) loads with two
+// moves: exchanging spins of the same position between half-warps (only those two half-warps'
+// loads change) and exchanging the positions of two spins of one half-warp (their neighbours'
+// half-warps change). Every second move is aimed: it takes a cell above D (kept in a list) and
+// moves one of its reads, by sending the reading spin to another half-warp or the read spin to
+// another position. Half-warps left with a load above D keep the column order for the local
+// order search that follows.
+class TransversalPlan {
+public:
+    static constexpr int kD = GatherLayout::kMaxDeg;
+
+    TransversalPlan(int n, int D, const std::vector<int32_t>& nbr) : n_(n), D_(D), H_((n + 15) / 16), nbr_(nbr)
+    {
+        slot_of_.resize(n_);
+        spin_at_.resize(n_);
+        for (int i = 0; i < n_; ++i) slot_of_[i] = spin_at_[i] = i;
+        cnt_.assign((size_t)n_ * 16, 0);
+        load_.assign((size_t)H_ * 16, 0);
+        for (int i = 0; i < n_; ++i)
+            for (int q = 0; q < D_; ++q) ++cnt_[(size_t)i * 16 + pos(nbr_[(size_t)i * kD + q])];
+        for (int i = 0; i < n_; ++i)
+            for (int k = 0; k < 16; ++k) load_[(size_t)half(i) * 16 + k] += cnt_[(size_t)i * 16 + k];
+        excess_ = excess();
+        at_.assign((size_t)H_ * 16, -1);
+        for (int c = 0; c < H_ * 16; ++c)
+            if (load_[c] > D_) {
+                at_[c] = (int)over_.size();
+                over_.push_back(c);
+            }
+    }
+
+    void anneal(int64_t moves, uint64_t seed, double temp)
+    {
+        uint64_t s = seed;
+        for (int64_t m = 0; m < moves; ++m) {
+            const uint64_t r = splitmix(s);
+            const double t = temp * (1.0 - (double)m / (double)moves);
+            int u = (int)((r >> 8) % (uint64_t)n_);
+            if (((r >> 4) & 1) && excess_ > 0) {  // aimed at a cell above D
+                const int cell = over_[(size_t)((r >> 40) % (uint64_t)over_.size())];
+                const int h = cell >> 4, k = cell & 15;
+                // a spin of half h with a neighbour at position k (reservoir pick)
+                const int lo = h * 16, cntv = std::min(16, n_ - lo);
+                int seen = 0;
+                uint64_t z = splitmix(s);
+                for (int a = 0; a < cntv; ++a) {
+                    const int x = spin_at_[lo + a];
+                    if (cnt_[(size_t)x * 16 + k] == 0) continue;
+                    if ((z >> 8) % (uint64_t)(++seen) == 0) u = x;
+                    z = z * 6364136223846793005ull + 1442695040888963407ull;
+                }
+                if (seen == 0) continue;
+                if ((r & 7) < 4) {  // u to another half-warp, same position
+                    const int h2 = (int)((r >> 32) % (uint64_t)H_);
+                    const int sv = h2 * 16 + pos(u);
+                    if (h2 == h || sv >= n_) continue;
+                    const int v = spin_at_[sv];
+                    if (keep(halves_delta(u, v), t, s)) swap_halves(u, v);
+                } else {  // u's neighbour at position k to another position of its half-warp
+                    int c = -1;
+                    for (int q = 0; q < D_ && c < 0; ++q)
+                        if (pos(nbr_[(size_t)u * kD + q]) == k) c = nbr_[(size_t)u * kD + q];
+                    const int hc = half(c), lc = hc * 16, cc = std::min(16, n_ - lc);
+                    if (cc < 2) continue;
+                    int sv = lc + (int)((r >> 32) % (uint64_t)(cc - 1));
+                    if (sv >= slot_of_[c]) ++sv;
+                    const int v = spin_at_[sv];
+                    const int64_t d = swap_positions(c, v);
+                    if (!keep(d, t, s)) swap_positions(c, v);
+                }
+                continue;
+            }
+            if ((r & 7) < 5) {  // same position, another half-warp
+                const int h2 = (int)((r >> 32) % (uint64_t)H_);
+                const int sv = h2 * 16 + pos(u);
+                if (h2 == half(u) || sv >= n_) continue;
+                const int v = spin_at_[sv];
+                if (keep(halves_delta(u, v), t, s)) swap_halves(u, v);
+            } else {  // two positions of one half-warp
+                const int h = half(u), lo = h * 16, cntv = std::min(16, n_ - lo);
+                if (cntv < 2) continue;
+                int sv = lo + (int)((r >> 32) % (uint64_t)(cntv - 1));
+                if (sv >= slot_of_[u]) ++sv;
+                const int v = spin_at_[sv];
+                const int64_t d = swap_positions(u, v);
+                if (!keep(d, t, s)) swap_positions(u, v);
+            }
+        }
+    }
+
+    // rows (n x kD): each spin's reads in rounds 0..D-1 -- König's split for the half-warps
+    // whose positions all take at most D reads, the column order elsewhere; returns how many
+    // half-warps were split
+    int rounds(std::vector<int32_t>& rows) const
+    {
+        rows = nbr_;
+        int done = 0;
+        for (int h = 0; h < H_; ++h) {
+            bool ok = true;
+            for (int k = 0; k < 16; ++k) ok &= load_[(size_t)h * 16 + k] <= D_;
+            if (ok && color_half(h, rows)) ++done;
+        }
+        return done;
+    }
+
+    const std::vector<int32_t>& slot_spin() const { return spin_at_; }
+
+    // reads above D summed over the (half-warp, position) cells
+    int64_t excess() const
+    {
+        int64_t e = 0;
+        for (int L : load_) e += std::max(0, L - D_);
+        return e;
+    }
+
+private:
+    static uint64_t splitmix(uint64_t& s)
+    {
+        uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+    static bool keep(int64_t d, double t, uint64_t& s)
+    {
+        if (d <= 0) return true;
+        if (t <= 0.0) return false;
+        return (double)(splitmix(s) >> 11) * 0x1.0p-53 < std::exp(-(double)d / t);
+    }
+    int pos(int i) const { return slot_of_[i] & 15; }
+    int half(int i) const { return slot_of_[i] >> 4; }
+
+    // load (h, k) += sign, returns the change of the sum of squares
+    int64_t add(int h, int k, int sign)
+    {
+        int& L = load_[(size_t)h * 16 + k];
+        const int64_t d = sign > 0 ? 2 * L + 1 : 1 - 2 * L;
+        excess_ += sign > 0 ? (L >= D_) : -(L > D_);
+        L += sign;
+        const int cell = h * 16 + k;
+        if (L > D_ && at_[cell] < 0) {
+            at_[cell] = (int)over_.size();
+            over_.push_back(cell);
+        } else if (L <= D_ && at_[cell] >= 0) {
+            const int last = over_.back();
+            over_[at_[cell]] = last;
+            at_[last] = at_[cell];
+            over_.pop_back();
+            at_[cell] = -1;
+        }
+        return d;
+    }
+
+    // the change of the sum of squares that swap_halves(u, v) would make
+    int64_t halves_delta(int u, int v) const
+    {
+        const int* cu = &cnt_[(size_t)u * 16];
+        const int* cv = &cnt_[(size_t)v * 16];
+        const int* Lu = &load_[(size_t)half(u) * 16];
+        const int* Lv = &load_[(size_t)half(v) * 16];
+        int64_t d = 0;
+        for (int k = 0; k < 16; ++k) {
+            const int x = cv[k] - cu[k];
+            d += (int64_t)x * (2 * (Lu[k] - Lv[k]) + 2 * x);
+        }
+        return d;
+    }
+
+    int64_t swap_halves(int u, int v)
+    {
+        const int hu = half(u), hv = half(v);
+        int64_t d = 0;
+        for (int k = 0; k < 16; ++k) {
+            const int a = cnt_[(size_t)u * 16 + k], b = cnt_[(size_t)v * 16 + k];
+            for (int q = 0; q < b - a; ++q) d += add(hu, k, +1) + add(hv, k, -1);
+            for (int q = 0; q < a - b; ++q) d += add(hu, k, -1) + add(hv, k, +1);
+        }
+        std::swap(slot_of_[u], slot_of_[v]);
+        spin_at_[slot_of_[u]] = u;
+        spin_at_[slot_of_[v]] = v;
+        return d;
+    }
+
+    // spin x leaves position a for b: its neighbours' counts and half-warp loads follow
+    int64_t relocate(int x, int a, int b)
+    {
+        int64_t d = 0;
+        for (int q = 0; q < D_; ++q) {
+            const int c = nbr_[(size_t)x * kD + q];
+            --cnt_[(size_t)c * 16 + a];
+            ++cnt_[(size_t)c * 16 + b];
+            d += add(half(c), a, -1) + add(half(c), b, +1);
+        }
+        return d;
+    }
+
+    int64_t swap_positions(int u, int v)
+    {
+        const int pu = pos(u), pv = pos(v);
+        int64_t d = relocate(u, pu, pv) + relocate(v, pv, pu);
+        std::swap(slot_of_[u], slot_of_[v]);
+        spin_at_[slot_of_[u]] = u;
+        spin_at_[slot_of_[v]] = v;
+        return d;
+    }
+
+    // D-edge-colouring of half-warp h's (spin, position) multigraph, colours = rounds
+    bool color_half(int h, std::vector<int32_t>& rows) const
+    {
+        const int lo = h * 16, m = std::min(16, n_ - lo);
+        // at[side][node][colour] = edge index or -1; side 0 = spins (0..m-1), 1 = positions
+        std::vector<int> at(2 * 16 * D_, -1), col(m * D_, -1), eu(m * D_), ev(m * D_), ec(m * D_);
+        auto A = [&](int side, int node, int c) -> int& { return at[((size_t)side * 16 + node) * D_ + c]; };
+        for (int a = 0; a < m; ++a) {
+            const int i = spin_at_[lo + a];
+            for (int q = 0; q < D_; ++q) {
+                const int e = a * D_ + q;
+                eu[e] = a;
+                ev[e] = pos(nbr_[(size_t)i * kD + q]);
+                ec[e] = nbr_[(size_t)i * kD + q];
+            }
+        }
+        for (int e = 0; e < m * D_; ++e) {
+            const int u = eu[e], v = ev[e];
+            int a = -1, b = -1;
+            for (int c = 0; c < D_ && a < 0; ++c)
+                if (A(0, u, c) < 0) a = c;
+            for (int c = 0; c < D_ && b < 0; ++c)
+                if (A(1, v, c) < 0) b = c;
+            if (a < 0 || b < 0) return false;
+            if (A(1, v, a) >= 0) {
+                // flip the a/b path from v: alternately a-edges and b-edges, starting with a
+                int node = v, side = 1, c1 = a, c2 = b;
+                std::vector<int> path;
+                for (int f = A(side, node, c1); f >= 0; f = A(side, node, c1)) {
+                    path.push_back(f);
+                    node = side == 1 ? eu[f] : ev[f];
+                    side ^= 1;
+                    std::swap(c1, c2);
+                }
+                for (int f : path) {
+                    A(0, eu[f], col[f]) = -1;
+                    A(1, ev[f], col[f]) = -1;
+                }
+                for (int f : path) {
+                    col[f] = col[f] == a ? b : a;
+                    A(0, eu[f], col[f]) = f;
+                    A(1, ev[f], col[f]) = f;
+                }
+            }
+            col[e] = a;
+            A(0, u, a) = e;
+            A(1, v, a) = e;
+        }
+        for (int a = 0; a < m; ++a) {
+            const int i = spin_at_[lo + a];
+            for (int q = 0; q < D_; ++q) rows[(size_t)i * kD + col[a * D_ + q]] = ec[a * D_ + q];
+        }
+        return true;
+    }
+
+    int n_, D_, H_;
+    std::vector<int32_t> nbr_, slot_of_, spin_at_;
+    std::vector<int> cnt_, load_;
+    int64_t excess_ = 0;
+    std::vector<int> over_, at_;  // the cells above D, each cell's index there (-1: none)
+};
+
+}  // namespace moq
+
+namespace moq {
+
 // The layout for the graph (ei, ej) of n spins, E edges: slot_spin (n, slot -> spin) and remap
 // (2E entries): row i's neighbour of rank r by column goes to position remap[rowptr_i + r] of
 // the row, rows in spin order with rowptr from the degrees. Returns false, leaving both
@@ -380,16 +668,37 @@ inline bool plan_gather_layout(int n, int64_t E, const int32_t* ei, const int32_
     // 3 of 40 at n = 42 for three times the time
     lay.balance_slots(3LL * n, seed, 0.0);
     lay.order_reads(3, seed + 1);
-    const GatherLayout& pick = 4 * lay.passes8() + lay.passes4() <= 4 * col.passes8() + col.passes4() ? lay : col;
+    const GatherLayout* pick = 4 * lay.passes8() + lay.passes4() <= 4 * col.passes8() + col.passes4() ? &lay : &col;
+    // One replica per block slot on a regular graph: MOQ_SB_LAYOUT_EFFORT = m > 0 also runs the
+    // transversal plan with m * n exchanges and keeps it where it is better. It is off by default
+    // because it costs more than a short job gains: at n = 1024, m = 1000 takes 0.15 s and cuts
+    // the 8-byte passes from 382 to 254 (192 without conflicts), about 5 % of an FP32 sampling
+    // launch of the two-spin form, 1 % of a float16 one
+    int D = 0;
+    bool regular = true;
+    for (int i = 0; i < n; ++i) D = std::max(D, (int)deg[i]);
+    for (int i = 0; i < n; ++i) regular &= deg[i] == D;
+    int64_t effort = 0;
+    if (const char* env = getenv("MOQ_SB_LAYOUT_EFFORT")) effort = std::max(0, atoi(env));
+    GatherLayout tl = col;
+    if (effort > 0 && fullest_warp_rb(n) == 1 && regular && D >= 2) {
+        TransversalPlan tp(n, D, nbr);
+        tp.anneal(effort * n, seed + 2, 0.0);
+        std::vector<int32_t> rows;
+        tp.rounds(rows);
+        tl.set_layout(tp.slot_spin(), rows);
+        tl.order_reads(3, seed + 3);
+        if (4 * tl.passes8() + tl.passes4() < 4 * pick->passes8() + pick->passes4()) pick = &tl;
+    }
     if (passes) {
         passes[0] = col.passes8();
         passes[1] = col.passes4();
-        passes[2] = pick.passes8();
-        passes[3] = pick.passes4();
+        passes[2] = pick->passes8();
+        passes[3] = pick->passes4();
     }
-    slot_spin = pick.slot_spin();
+    slot_spin = pick->slot_spin();
     remap.assign((size_t)2 * E, 0);
-    const std::vector<int32_t>& order = pick.neighbours();
+    const std::vector<int32_t>& order = pick->neighbours();
     int64_t p0 = 0;
     for (int i = 0; i < n; ++i) {
         const int32_t* sorted = &nbr[(size_t)i * kD];

@@ -75,23 +75,35 @@ class Instance:
             pass
 
 
-def create_instances(srcs, stream=None, threads=None):
+def create_instances(srcs, stream=None, threads=None, layout_effort=None):
     """``Instance`` of every source, built on host threads (the build's host part, the samplers'
-    shared-memory layout, runs in parallel; the device part is ordered on ``stream``)."""
+    shared-memory layout, runs in parallel; the device part is ordered on ``stream``).
+    ``layout_effort`` = m > 0 runs the longer layout search (m slot exchanges per spin, for
+    regular graphs) for these builds, through ``MOQ_SB_LAYOUT_EFFORT``, restored afterwards."""
     import concurrent.futures
 
     srcs = list(srcs)
-    if len(srcs) < 2:
-        return [Instance(s, stream) for s in srcs]
-    dev = torch.cuda.current_device()
+    old = os.environ.get("MOQ_SB_LAYOUT_EFFORT")
+    if layout_effort is not None:
+        os.environ["MOQ_SB_LAYOUT_EFFORT"] = str(int(layout_effort))
+    try:
+        if len(srcs) < 2:
+            return [Instance(s, stream) for s in srcs]
+        dev = torch.cuda.current_device()
 
-    def build(s):
-        torch.cuda.set_device(dev)
-        return Instance(s, stream)
+        def build(s):
+            torch.cuda.set_device(dev)
+            return Instance(s, stream)
 
-    workers = threads or min(len(srcs), os.cpu_count() or 1, 16)
-    with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
-        return list(ex.map(build, srcs))
+        workers = threads or min(len(srcs), os.cpu_count() or 1, 16)
+        with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
+            return list(ex.map(build, srcs))
+    finally:
+        if layout_effort is not None:
+            if old is None:
+                os.environ.pop("MOQ_SB_LAYOUT_EFFORT", None)
+            else:
+                os.environ["MOQ_SB_LAYOUT_EFFORT"] = old
 
 
 class Archive:

@@ -815,13 +815,15 @@ def test_two_spins_per_thread_from_a_given_state_and_schedule(M, P, monkeypatch)
     assert torch.equal(out["0"][0], out["1"][0]) and torch.equal(out["0"][1], out["1"][1])
 
 
-@pytest.mark.parametrize("layout", ["0", "1"])
+@pytest.mark.parametrize("layout", ["0", "1", "long"])
 @pytest.mark.parametrize("form", ["single", "pair", "two_spin"])
 @pytest.mark.parametrize("name,variant", [("reg3_n1024_K3", "dsb"), ("reg3_n1024_K3", "bsb"), ("heavyhex_K4", "bsb")])
 def test_force_matches_fp64_in_every_form_and_layout(M, P, oracle, monkeypatch, layout, form, name, variant):
     # the one-step force of every FP32 sparse form, on the bank-conflict layout (gather order
-    # changes the FP32 summation order only) and on the plain one, within the normwise bound
-    monkeypatch.setenv("MOQ_SB_LAYOUT", layout)
+    # changes the FP32 summation order only), with the longer search for regular graphs, and
+    # on the plain one, within the normwise bound
+    monkeypatch.setenv("MOQ_SB_LAYOUT", "0" if layout == "0" else "1")
+    monkeypatch.setenv("MOQ_SB_LAYOUT_EFFORT", "300" if layout == "long" else "0")  # the longer search
     monkeypatch.setenv("MOQ_SB_PAIR", "0" if form == "single" else "1")
     monkeypatch.setenv("MOQ_SB_TWOSPIN", "1" if form == "two_spin" else "0")
     src = INSTANCES[name]()

@@ -128,3 +128,26 @@ def test_layout_rejects_what_the_samplers_do_not_take(M):
         M.moq_plan_gather_layout(1026, big.ei, big.ej)
     with pytest.raises(M.MoqError):
         M.moq_plan_gather_layout(4, np.array([0, 0], np.int32), np.array([1, 1], np.int32))  # repeated edge
+
+
+def test_longer_search_on_regular_graphs(M, monkeypatch):
+    # MOQ_SB_LAYOUT_EFFORT = 1000: the transversal search on a random 3-regular graph (one replica
+    # per slot) is valid, deterministic, counted as the bank model counts it, and removes a good
+    # part of the 8-byte passes the default planner leaves
+    src = wl.random_regular(1024, 5, K=3)
+    _, _, base = M.moq_plan_gather_layout(src.n, src.ei, src.ej)
+    monkeypatch.setenv("MOQ_SB_LAYOUT_EFFORT", "1000")
+    slot, gather, p = M.moq_plan_gather_layout(src.n, src.ei, src.ej)
+    rows, chosen = _check_valid(src.n, src.ei, src.ej, slot, gather)
+    assert tuple(p[2:]) == _passes(src.n, slot, chosen)
+    slot2, gather2, _ = M.moq_plan_gather_layout(src.n, src.ei, src.ej)
+    assert np.array_equal(slot, slot2) and np.array_equal(gather, gather2)
+    assert p[2] <= 0.8 * base[2] and p[3] <= base[3] + 4, (base, p)
+    assert p[2] >= 3 * 64  # one pass per half-warp and round at best
+    # irregular graphs and blocks of several replicas keep the default planner
+    for g in (wl.random_graph(150, 0.02, 4, K=3), wl.heavy_hex_like(1001, K=4)):
+        monkeypatch.setenv("MOQ_SB_LAYOUT_EFFORT", "0")
+        a = M.moq_plan_gather_layout(g.n, g.ei, g.ej)
+        monkeypatch.setenv("MOQ_SB_LAYOUT_EFFORT", "1000")
+        b = M.moq_plan_gather_layout(g.n, g.ei, g.ej)
+        assert all(np.array_equal(x, y) for x, y in zip(a, b))
