@@ -3,8 +3,8 @@
 One step = one pass of the whole path over one batch: NI-dSB sampling of R replicas
 (each on its own weight vector), exact K-objective cuts of every sample, the Pareto
 filter into a fresh device archive, and the exact hypervolume of the front (read back on
-the host). The K timed steps run as a three-stage pipeline: steps s + 1 and s + 2 are
-queued for sampling while step s's cuts, merge and hypervolume finish.
+the host). The K timed steps run as a pipeline: steps s + 1 to s + 5 are queued for
+sampling while step s's cuts, merge and hypervolume finish.
 
 Workload (default): heavy-hex-like graph n=42 / E=50, K=4 integer objectives in
 {-10..10}\\{0}, R=16384 replicas with uniform-simplex weight vectors, dSB, T=2000
@@ -20,6 +20,7 @@ on the data path); timings are the max over ranks.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -263,14 +264,18 @@ def gpu_arm(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    # Timed region: the K steps as a pipeline over three sample buffers -- the samplings of
-    # steps s + 1 and s + 2 are queued on one stream while step s's cuts, Pareto merge and
+    # Timed region: the K steps as a pipeline over `depth` sample buffers -- the samplings of
+    # steps s + 1 to s + depth - 1 are queued on one stream while step s's cuts, Pareto merge and
     # hypervolume (a second stream, the result read back on the host) finish, so the host's
     # read-back never leaves the sampler stream empty. The sampler stream has the higher
     # priority; the filter kernels take the SMs its blocks leave (its wave tails). Every step
     # does its whole path; the L2 flush (FLUSH_MIB) precedes every sampling launch inside the
-    # timed region. (Two buffers, filter stream first: 1.71 ms per step against 1.62 ms.)
-    depth = 3
+    # timed region. (Two buffers, filter stream first: 1.71 ms per step against 1.62 ms. More
+    # buffers keep the sampler stream fed when the host thread falls behind -- a step's filter
+    # work takes the SMs only in the sampler's wave tails, and the host waits for its result:
+    # with three, some runs showed 0.07-0.6 ms gaps between samplings, with four one run in
+    # four 1.75 ms per step, with six 1.614-1.621 ms in all runs.)
+    depth = args.pipeline_depth
     bufs = [buf] + [P.RoundBuffers(R, n, K) for _ in range(depth - 1)]
     s_a = torch.cuda.Stream(device=dev, priority=-1)
     s_b = torch.cuda.Stream(device=dev)
@@ -286,6 +291,8 @@ def gpu_arm(args, rank, world):
             samp_ev[s][1].record(s_a)
             sampled[s] = s_a.record_event()
 
+    gc.collect()
+    gc.disable()  # no collector pauses on the host thread that feeds the pipeline
     with ClockSampler(dev.index) as clk:
         t_wall = time.perf_counter()
         t_start.record(stream)
@@ -307,6 +314,7 @@ def gpu_arm(args, rank, world):
         t_end.record(stream)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
+    gc.enable()
     fronts.append(arch.size())
     sample_ms = [samp_ev[s][0].elapsed_time(samp_ev[s][1]) for s in range(args.warmup, nsteps)]
     dev_s = t_start.elapsed_time(t_end) / 1e3
@@ -316,39 +324,60 @@ def gpu_arm(args, rank, world):
 
     # e2e through the C ABI with host buffers: each step's own weight vectors copied in from
     # pinned host memory, and the step's result -- the hypervolume and the front itself (cut
-    # vectors, configurations, sample indices) -- read back to the host every step
-    # (the same three-stage pipeline: the copy-ins and samplings of steps s + 1, s + 2 overlap
-    # step s's tail)
-    e2e_steps = max(1, min(args.steps, 20))
+    # vectors, configurations, sample indices) -- read back to the host every step, into the
+    # archive's page-locked buffers. The same pipeline: the weight vectors of step
+    # s + depth - 1 are copied in on a third stream (once sampling s - 1, their buffer's last
+    # reader, is done) while the queued samplings and step s's tail run; a few untimed steps
+    # first, like the device-timed leg's warm-up. No L2 flush here: the path a caller runs.
+    e2e_steps = max(1, min(args.steps, 200))
+    e2e_warm = min(3, max(1, args.warmup))
     lam_host = torch.from_numpy(np.stack([wl.dirichlet_lambdas(R * world, K, 777 + s)[first:first + R]
                                           for s in range(e2e_steps)])).pin_memory()
     lam_devs = [torch.empty_like(lam_host[0], device=dev) for _ in range(depth)]
-    torch.cuda.synchronize()
-    e2e_sampled = [None] * e2e_steps
+    s_c = torch.cuda.Stream(device=dev)
     d2h = []
 
-    def launch_e2e(s):
-        with torch.cuda.stream(s_a):
-            lam_devs[s % depth].copy_(lam_host[s], non_blocking=True)
-            M.moq_sample(inst.handle, lam_devs[s % depth], R, params, 99, s, bufs[s % depth].bits, s_a)
-            e2e_sampled[s] = s_a.record_event()
+    def e2e_run(nst):
+        sampled, copied = [None] * nst, [None] * nst
 
+        def copy_in(s):
+            with torch.cuda.stream(s_c):
+                if s >= depth:
+                    s_c.wait_event(sampled[s - depth])
+                lam_devs[s % depth].copy_(lam_host[s], non_blocking=True)
+                copied[s] = s_c.record_event()
+
+        def launch_e2e(s):
+            with torch.cuda.stream(s_a):
+                s_a.wait_event(copied[s])
+                M.moq_sample(inst.handle, lam_devs[s % depth], R, params, 99, s, bufs[s % depth].bits, s_a)
+                sampled[s] = s_a.record_event()
+
+        for q in range(min(nst, depth - 1)):
+            copy_in(q)
+            launch_e2e(q)
+        for s in range(nst):
+            if s + depth - 1 < nst:
+                copy_in(s + depth - 1)
+                launch_e2e(s + depth - 1)
+            b = bufs[s % depth]
+            s_b.wait_event(sampled[s])
+            arch.reset(s_b)
+            M.moq_evaluate_cuts(inst.handle, b.bits, R, b.cuts, s_b)
+            arch.merge(b.cuts, b.bits, R, 0, stream=s_b)
+            arch.hypervolume(inst.ref, s_b)
+            fc, fb, fi = arch.copy_out(s_b, reuse=True)  # the front on the host
+            d2h.append(16 + 4 + 8 + fc.nbytes + fb.nbytes + fi.nbytes)  # HV + status, size, front
+        torch.cuda.synchronize()
+
+    e2e_run(e2e_warm)
+    d2h.clear()
+    gc.collect()
+    gc.disable()
     t0 = time.perf_counter()
-    for q in range(min(e2e_steps, depth - 1)):
-        launch_e2e(q)
-    for s in range(e2e_steps):
-        if s + depth - 1 < e2e_steps:
-            launch_e2e(s + depth - 1)
-        b = bufs[s % depth]
-        s_b.wait_event(e2e_sampled[s])
-        arch.reset(s_b)
-        M.moq_evaluate_cuts(inst.handle, b.bits, R, b.cuts, s_b)
-        arch.merge(b.cuts, b.bits, R, 0, stream=s_b)
-        arch.hypervolume(inst.ref, s_b)
-        fc, fb, fi = arch.copy_out(s_b)  # the front on the host
-        d2h.append(16 + 4 + 8 + fc.nbytes + fb.nbytes + fi.nbytes)  # HV + status, size, front
-    torch.cuda.synchronize()
+    e2e_run(e2e_steps)
     e2e_s = time.perf_counter() - t0
+    gc.enable()
     e2e = {"value": R * n * T * e2e_steps / e2e_s * world, "unit": METRIC,
            "h2d_bytes_per_step": R * K * 4, "d2h_bytes_per_step": int(np.mean(d2h)),
            "steps": e2e_steps, "result_read_back": "hypervolume and the whole front (cuts, configurations, indices)"}
@@ -1319,6 +1348,8 @@ def main():
                     help="precision (the default line), the batching or dense configuration, or the paper's protocol")
     ap.add_argument("--paper-rounds", type=int, default=20)
     ap.add_argument("--prewarm", type=float, default=0.5, help="seconds of untimed sampler launches before the warm-up steps")
+    ap.add_argument("--pipeline-depth", type=int, default=6,
+                    help="sample buffers of the pipelined precision step (samplings queued ahead: depth - 1)")
     ap.add_argument("--time-scale", type=float, default=1.0, help="scales the appendix_e runtime limits (5 s / 10 s)")
     ap.add_argument("--dense-n", type=int, default=2000)
     ap.add_argument("--dense-replicas", type=int, default=8192)
@@ -1354,9 +1385,9 @@ def main():
               "n": w["n"], "K": w["K"], "R": w["R"], "T": w["T"], "variant": w["variant"], "dt": w["dt"],
               "alpha": w["alpha"], "precision": args.precision,
               "l2": FLUSH_NOTE, "parallelism": f"replicas x{world}",
-              "timing": "K steps timed as one region (CUDA events): steps s+1 and s+2 are queued on the (high-priority) "
-                        "sampler stream while step s's cuts, merge and hypervolume finish on a second stream; the "
-                        "hypervolume of every step is read back on the host",
+              "timing": f"K steps timed as one region (CUDA events): steps s+1 to s+{args.pipeline_depth - 1} are queued "
+                        "on the (high-priority) sampler stream while step s's cuts, merge and hypervolume finish on a "
+                        "second stream; the hypervolume of every step is read back on the host",
               "prewarm_s": args.prewarm}
 
     if args.impl == "reference":

@@ -304,6 +304,20 @@ def moq_archive_copy_out(a, K, W, stream=None):
     return cuts[:F], bits[:F], idx[:F]
 
 
+def moq_archive_copy_out_into(a, cuts, bits, index, stream=None) -> int:
+    """Copies the front into caller-owned host arrays (cuts (cap,K) int64, bits (cap,W) uint64
+    or int64, index (cap,) int64, C-contiguous; page-locked memory makes each copy one DMA) and
+    returns the front's size F; only the first min(F, cap) rows are written."""
+    cap = index.shape[0]
+    for arr, name in ((cuts, "cuts"), (bits, "bits"), (index, "index")):
+        if not arr.flags["C_CONTIGUOUS"] or arr.dtype.itemsize != 8 or arr.shape[0] != cap:
+            raise ValueError(f"moq_archive_copy_out_into: {name} must be C-contiguous 8-byte rows, {cap} of them")
+    n = C.c_int64()
+    _check(_lib.moq_archive_copy_out(a, cuts.ctypes.data_as(_vp), bits.ctypes.data_as(_vp), index.ctypes.data_as(_vp),
+                                     cap, C.byref(n), _stream(stream)), "moq_archive_copy_out")
+    return int(n.value)
+
+
 def moq_archive_device_view(a):
     cuts, bits, idx, size = _vp(), _vp(), _vp(), _vp()
     _check(_lib.moq_archive_device_view(a, C.byref(cuts), C.byref(bits), C.byref(idx), C.byref(size)),

@@ -123,8 +123,28 @@ class Archive:
     def hypervolume(self, ref, stream=None):
         return M.moq_hypervolume(self.handle, ref, stream)
 
-    def copy_out(self, stream=None):
-        return M.moq_archive_copy_out(self.handle, self.K, self.W, stream)
+    def copy_out(self, stream=None, reuse=False):
+        """The front on the host: (cuts (F,K) int64, bits (F,W) uint64, index (F,) int64). With
+        ``reuse`` the copies land in page-locked buffers kept by the archive (one DMA each, no
+        staging through pageable memory, grown to the next power of two when the front
+        outgrows them); the arrays returned are views of those buffers, overwritten by the
+        next ``copy_out(reuse=True)``."""
+        if not reuse:
+            return M.moq_archive_copy_out(self.handle, self.K, self.W, stream)
+        need = 1024
+        while True:
+            pin = getattr(self, "_pinned", None)
+            if pin is None or pin[2].shape[0] < need:
+                rows = 1 << max(10, (need - 1).bit_length())
+                keep = [torch.empty((rows, self.K), dtype=torch.int64, pin_memory=True),
+                        torch.empty((rows, self.W), dtype=torch.int64, pin_memory=True),
+                        torch.empty((rows,), dtype=torch.int64, pin_memory=True)]
+                self._pinned_keep = keep  # the page-locked tensors behind the numpy views
+                pin = self._pinned = (keep[0].numpy(), keep[1].numpy().view(np.uint64), keep[2].numpy())
+            F = M.moq_archive_copy_out_into(self.handle, *pin, stream=stream)
+            if F <= pin[2].shape[0]:
+                return pin[0][:F], pin[1][:F], pin[2][:F]
+            need = F
 
     def reset(self, stream=None):
         M.moq_archive_reset(self.handle, stream)

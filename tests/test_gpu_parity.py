@@ -248,6 +248,27 @@ def test_pareto_packed_and_plain_ranges(M, P, oracle, monkeypatch, K, offset, wi
     _run_archive(M, P, oracle, cuts, bits, n, [list(range(0, 1800)), list(range(1800, Mtot))])
 
 
+def test_copy_out_into_page_locked_buffers(M, P):
+    # the archive's reused page-locked copy equals the plain copy: an empty front, a small one,
+    # and a front of 3000 mutually non-dominated vectors, which outgrows the first 1024-row
+    # buffers; a caller-owned array of the wrong row size is refused before any copy
+    n, K = 70, 2
+    arch = P.Archive(n, K, capacity=1 << 13, max_batch=4096)
+    for m, base in ((0, 0), (5, 10), (3000, 1000)):
+        arch.reset()
+        if m:
+            anti = np.array([[i, 5000 - i] for i in range(m)], np.int64)
+            arch.merge(_dev(anti, torch.int64), _bits_dev(wl.random_sign_bits(m, n, m)), m, base)
+        want = arch.copy_out()
+        got = arch.copy_out(reuse=True)
+        assert len(got[2]) == m and all(np.array_equal(a, b) for a, b in zip(want, got))
+        assert got[1].dtype == np.uint64 and got[0].shape == (m, K) and got[1].shape == (m, 2)
+    assert arch._pinned[2].shape[0] == 4096
+    bad = (np.zeros((8, K), np.int64), np.zeros((8, 2), np.uint64), np.zeros(9, np.int64))
+    with pytest.raises(ValueError):
+        M.moq_archive_copy_out_into(arch.handle, *bad)
+
+
 def test_pareto_edge_cases(M, P, oracle):
     n, K = 42, 3
     arch = P.Archive(n, K, capacity=8, max_batch=64)
