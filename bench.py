@@ -232,8 +232,9 @@ def gpu_arm(args, rank, world):
                                          for s in range(nsteps)])).to(dev)
     flush = torch.empty(FLUSH_MIB * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 126 MB L2
     # sample, cuts, Pareto merge (dedup path: 11 kernels with the warp-form dominance tests, 12
-    # with the tile form), hypervolume (5 for K = 4)
-    launches_per_step = 1 + 1 + (12 if os.environ.get("MOQ_FILTER_FORM", "warp").startswith("t") else 11) + 5
+    # with the tile form), hypervolume (6 for K = 4: ranks, orders, permutation, the 32-bit and
+    # the 128-bit slab kernels -- one of them returns at once -- and the sum)
+    launches_per_step = 1 + 1 + (12 if os.environ.get("MOQ_FILTER_FORM", "warp").startswith("t") else 11) + 6
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
     fronts, hvs = [], []

@@ -36,6 +36,7 @@ struct HvWs {
     int64_t *o0_y0, *o0_y1, *o2_y2;
     int32_t *o0_r2, *o0_r3, *o2_r2, *o2_r3;
     int32_t* fv;     // number of points kept
+    int32_t* wide;   // K = 4: set when some kept point has y_k - r_k >= 2^32 (k < 3)
     i128* result;
     int32_t* flags;
 };
@@ -62,6 +63,7 @@ __host__ __device__ inline HvWs carve(void* base, int64_t F, int K)
     w.o2_r3 = w.o2_r2 + F;
     p += al256(40 * (size_t)F);
     w.fv = reinterpret_cast<int32_t*>(p);
+    w.wide = reinterpret_cast<int32_t*>(p + 4);
     w.result = reinterpret_cast<i128*>(p + 16);
     w.flags = reinterpret_cast<int32_t*>(p + 32);
     return w;
@@ -161,6 +163,27 @@ __device__ i128 block_sum(i128 v, i128* red)
     const i128 out = red[0];
     __syncthreads();
     return out;
+}
+
+__device__ __forceinline__ i128 shfl_down_i128(i128 v, int o)
+{
+    const uint64_t lo = __shfl_down_sync(0xffffffffu, (uint64_t)v, o);
+    const uint64_t hi = __shfl_down_sync(0xffffffffu, (uint64_t)((unsigned __int128)v >> 64), o);
+    return (i128)(((unsigned __int128)hi << 64) | lo);
+}
+
+// The block's sum (integer: independent of the order of the additions) in thread 0 only:
+// warp shuffles, one barrier, and thread 0 adds the warp sums.
+__device__ i128 block_sum_to0(i128 v, i128* warp_red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += shfl_down_i128(v, o);
+    if ((threadIdx.x & 31) == 0) warp_red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    i128 s = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += warp_red[w];
+    return s;
 }
 
 // K = 2: slab t along y_1 (order_1); length = max of y_0 over ranks <= t.
@@ -271,19 +294,27 @@ __device__ __forceinline__ int block_excl_scan_int(int v, int* warp_sums, int* t
     return res;
 }
 
-// The K = 4 point data in y_0 order and in y_2 order (positions past the kept count unused).
-__global__ void __launch_bounds__(kThreads) k_hv_permute4(const int64_t* __restrict__ pts, int64_t F, HvWs ws)
+// The K = 4 point data in y_0 order and in y_2 order (positions past the kept count unused),
+// and the flag that sends the slabs to the 128-bit walk: some kept point lies 2^32 or more
+// above the reference point in y_0, y_1 or y_2 (kept points lie at or above it, so the
+// differences, taken modulo 2^64, are exact).
+__global__ void __launch_bounds__(kThreads) k_hv_permute4(const int64_t* __restrict__ pts, int64_t F, Ref4 ref, HvWs ws)
 {
     const int64_t q = blockIdx.x * (int64_t)kThreads + threadIdx.x;
     if (q >= *ws.fv) return;
     const int32_t p0 = ws.order[q], p2 = ws.order[2 * F + q];
-    ws.o0_y0[q] = pts[(int64_t)p0 * 4];
-    ws.o0_y1[q] = pts[(int64_t)p0 * 4 + 1];
+    const int64_t y0 = pts[(int64_t)p0 * 4], y1 = pts[(int64_t)p0 * 4 + 1], y2 = pts[(int64_t)p2 * 4 + 2];
+    ws.o0_y0[q] = y0;
+    ws.o0_y1[q] = y1;
     ws.o0_r2[q] = ws.rank[2 * F + p0];
     ws.o0_r3[q] = ws.rank[3 * F + p0];
-    ws.o2_y2[q] = pts[(int64_t)p2 * 4 + 2];
+    ws.o2_y2[q] = y2;
     ws.o2_r2[q] = ws.rank[2 * F + p2];
     ws.o2_r3[q] = ws.rank[3 * F + p2];
+    constexpr uint64_t kMax32 = 0xFFFFFFFFull;
+    if ((uint64_t)y0 - (uint64_t)ref.r[0] > kMax32 || (uint64_t)y1 - (uint64_t)ref.r[1] > kMax32 ||
+        (uint64_t)y2 - (uint64_t)ref.r[2] > kMax32)
+        atomicOr(ws.wide, 1);
 }
 
 // K = 4 with the slab's points compacted: block b takes slab t = F-1-b (the largest slabs
@@ -297,6 +328,7 @@ constexpr int kHv4CompactMax = 6144;
 
 __global__ void __launch_bounds__(kThreads) k_hv4_compact(const int64_t* __restrict__ pts, int64_t F, Ref4 ref, HvWs ws)
 {
+    if (*ws.wide == 0) return;  // k_hv4_narrow takes every slab
     extern __shared__ __align__(16) unsigned char sm[];
     int64_t* s_u0 = reinterpret_cast<int64_t*>(sm);
     int64_t* s_u1 = s_u0 + F;
@@ -403,6 +435,140 @@ __global__ void __launch_bounds__(kThreads) k_hv4_compact(const int64_t* __restr
         acc += (i128)h3 * area;
     }
     const i128 sum = block_sum(acc, red);
+    if (threadIdx.x == 0) ws.partial[t] = (i128)h4 * sum;
+}
+
+// K = 4 with every kept point less than 2^32 above the reference point in y_0, y_1 and y_2 (the
+// flag k_hv_permute4 leaves clear): k_hv4_compact's slabs, sub-slabs and sums, on 32-bit
+// offsets from the reference point. A staircase area is at most the product of its two
+// largest offsets, below 2^64, so the walk adds unsigned 64-bit products; each sub-slab's
+// height times its area, and the slab's sum, are 128-bit as before. 20 B of shared memory per
+// point instead of 32 (more resident blocks: the walk is latency-bound) and a shorter step.
+__global__ void __launch_bounds__(kThreads) k_hv4_narrow(const int64_t* __restrict__ pts, int64_t F, Ref4 ref, HvWs ws)
+{
+    if (*ws.wide != 0) return;  // k_hv4_compact takes every slab
+    extern __shared__ __align__(16) unsigned char sm[];
+    uint2* s_w = reinterpret_cast<uint2*>(sm);               // (y_1 - r_1, rank_2) in y_0 order
+    uint32_t* s_u0 = reinterpret_cast<uint32_t*>(s_w + F);  // y_0 - r_0 in y_0 order
+    uint32_t* s_v2 = s_u0 + F;  // y_2 - r_2 in y_2 order; after packing, the sub-slab heights
+    int32_t* s_q2 = reinterpret_cast<int32_t*>(s_v2 + F);  // rank_2 in y_2 order; after packing, per sub-slab
+    __shared__ i128 red[kThreads / 32];
+    __shared__ int warp_sums[kThreads / 32];
+    const int Fv = *ws.fv;
+    const int64_t t = F - 1 - (int64_t)blockIdx.x;
+    const int32_t* ord3 = ws.order + 3 * F;
+    int64_t h4 = 0;
+    if (t < Fv) {
+        const int64_t top = pts[(int64_t)ord3[t] * 4 + 3];
+        const int64_t below = (t + 1 < Fv) ? pts[(int64_t)ord3[t + 1] * 4 + 3] : ref.r[3];
+        h4 = top - below;
+    }
+    if (h4 <= 0) {  // uniform over the block
+        if (threadIdx.x == 0) ws.partial[t] = 0;
+        return;
+    }
+    // the points of rank_3 <= t in both orders, as in k_hv4_compact
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int kWarps = kThreads / 32;
+    const int seg = ((Fv + kWarps - 1) / kWarps + 31) & ~31;
+    const int lo = wid * seg, hi = min(Fv, lo + seg);
+    __shared__ int wc0[kWarps], wc2[kWarps];
+    // four chunks of 32 positions per round, their loads issued together (the scan is
+    // latency-bound: every slab reads the whole rank_3 column of both orders)
+    constexpr int kU = 4;
+    int n0 = 0, n2 = 0;
+    for (int base = lo; base < hi; base += 32 * kU) {  // warp-uniform trip count (ballots below)
+        int a0[kU], a2[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int q = base + 32 * u + lane;
+            a0[u] = q < hi ? ws.o0_r3[q] : 0x7fffffff;
+            a2[u] = q < hi ? ws.o2_r3[q] : 0x7fffffff;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            n0 += __popc(__ballot_sync(0xffffffffu, a0[u] <= t));
+            n2 += __popc(__ballot_sync(0xffffffffu, a2[u] <= t));
+        }
+    }
+    if (lane == 0) {
+        wc0[wid] = n0;
+        wc2[wid] = n2;
+    }
+    __syncthreads();
+    int pos0 = 0, pos2 = 0, cnt0 = 0;
+    for (int w = 0; w < kWarps; ++w) {
+        if (w < wid) {
+            pos0 += wc0[w];
+            pos2 += wc2[w];
+        }
+        cnt0 += wc0[w];
+    }
+    const unsigned below = (1u << lane) - 1u;
+    for (int base = lo; base < hi; base += 32 * kU) {
+        bool f0[kU], f2[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int q = base + 32 * u + lane;
+            f0[u] = q < hi && ws.o0_r3[q] <= t;
+            f2[u] = q < hi && ws.o2_r3[q] <= t;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int q = base + 32 * u + lane;
+            const unsigned b0 = __ballot_sync(0xffffffffu, f0[u]), b2 = __ballot_sync(0xffffffffu, f2[u]);
+            if (f0[u]) {
+                const int at = pos0 + __popc(b0 & below);
+                s_w[at] = make_uint2((uint32_t)((uint64_t)ws.o0_y1[q] - (uint64_t)ref.r[1]), (uint32_t)ws.o0_r2[q]);
+                s_u0[at] = (uint32_t)((uint64_t)ws.o0_y0[q] - (uint64_t)ref.r[0]);
+            }
+            if (f2[u]) {
+                const int at = pos2 + __popc(b2 & below);
+                s_v2[at] = (uint32_t)((uint64_t)ws.o2_y2[q] - (uint64_t)ref.r[2]);
+                s_q2[at] = ws.o2_r2[q];
+            }
+            pos0 += __popc(b0);
+            pos2 += __popc(b2);
+        }
+    }
+    __syncthreads();
+    const int c = cnt0;  // == t + 1
+    // non-empty sub-slabs packed in place (the order of reads and writes of k_hv4_compact)
+    int nsub = 0;
+    for (int base = 0; base < c; base += kThreads) {
+        const int s = base + threadIdx.x;
+        uint32_t h3 = 0;
+        int32_t rs = 0;
+        if (s < c) {
+            h3 = s_v2[s] - (s + 1 < c ? s_v2[s + 1] : 0u);
+            rs = s_q2[s];
+        }
+        int tot;
+        const int pos = nsub + block_excl_scan_int(h3 > 0 ? 1 : 0, warp_sums, &tot);
+        if (h3 > 0) {
+            s_v2[pos] = h3;
+            s_q2[pos] = rs;
+        }
+        nsub += tot;
+    }
+    __syncthreads();
+    i128 acc = 0;
+    for (int j = threadIdx.x; j < nsub; j += kThreads) {
+        const uint32_t h3 = s_v2[j];
+        const uint32_t rs = (uint32_t)s_q2[j];
+        uint64_t area = 0;
+        uint32_t best1 = 0;
+#pragma unroll 4
+        for (int q = 0; q < c; ++q) {
+            const uint2 w = s_w[q];
+            if (w.y <= rs && w.x > best1) {
+                area += (uint64_t)s_u0[q] * (uint64_t)(w.x - best1);
+                best1 = w.x;
+            }
+        }
+        acc += (i128)h3 * (i128)area;
+    }
+    const i128 sum = block_sum_to0(acc, red);
     if (threadIdx.x == 0) ws.partial[t] = (i128)h4 * sum;
 }
 
@@ -624,7 +790,7 @@ int hv_points_impl(const int64_t* pts, int64_t F, int32_t K, const int64_t* ref,
     HvWs ws = carve(workspace, F, K);
     Ref4 r{};
     for (int k = 0; k < K; ++k) r.r[k] = ref[k];
-    MOQ_CUDA_TRY(cudaMemsetAsync(ws.fv, 0, sizeof(int32_t), st));
+    MOQ_CUDA_TRY(cudaMemsetAsync(ws.fv, 0, 2 * sizeof(int32_t), st));  // fv and wide
     MOQ_CUDA_TRY(cudaMemsetAsync(ws.rank, 0, sizeof(int32_t) * (size_t)K * F, st));
     const unsigned gF = (unsigned)ceil_div(F, kThreads);
     const dim3 gRank((unsigned)ceil_div(F, kRankTile), (unsigned)std::min<int64_t>(ceil_div(F, kRankChunk), 65535));
@@ -645,11 +811,14 @@ int hv_points_impl(const int64_t* pts, int64_t F, int32_t K, const int64_t* ref,
     default:
         k_hv_rank_count<4><<<gRank, kRankTile, 0, st>>>(pts, F, r, ws);
         k_hv_rank_order<4><<<gF, kThreads, 0, st>>>(pts, F, r, ws);
-        k_hv_permute4<<<gF, kThreads, 0, st>>>(pts, F, ws);
+        k_hv_permute4<<<gF, kThreads, 0, st>>>(pts, F, r, ws);
         if (F <= kHv4CompactMax) {
-            const size_t smem = (size_t)32 * F;
-            MOQ_CUDA_TRY(cudaFuncSetAttribute(k_hv4_compact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_hv4_compact<<<(unsigned)F, kThreads, smem, st>>>(pts, F, r, ws);
+            // both launched; the flag k_hv_permute4 leaves decides which one does the slabs
+            const size_t smem_n = (size_t)20 * F, smem_w = (size_t)32 * F;
+            MOQ_CUDA_TRY(cudaFuncSetAttribute(k_hv4_narrow, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_n));
+            MOQ_CUDA_TRY(cudaFuncSetAttribute(k_hv4_compact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w));
+            k_hv4_narrow<<<(unsigned)F, kThreads, smem_n, st>>>(pts, F, r, ws);
+            k_hv4_compact<<<(unsigned)F, kThreads, smem_w, st>>>(pts, F, r, ws);
         } else {
             k_hv4_stream<<<(unsigned)F, kThreads, 0, st>>>(pts, F, r, ws);
         }

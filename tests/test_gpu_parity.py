@@ -319,6 +319,23 @@ def test_hv_bit_exact(M, oracle, K, F, span):
     assert _hv_points(M, pts, ref) == oracle.hypervolume(pts, ref)
 
 
+@pytest.mark.parametrize("k", [0, 1, 2])
+@pytest.mark.parametrize("offset", [(1 << 32) - 1, 1 << 32, 1 << 45])
+def test_hv4_walk_widths(M, oracle, k, offset):
+    # K = 4 fronts within the shared-memory form take the 32-bit walk while every kept point
+    # lies less than 2^32 above the reference point in y_0, y_1 and y_2, the 128-bit walk
+    # otherwise: one point of a 900-point front is lifted to `offset` above the reference in
+    # objective k (2^32 - 1: still 32-bit; 2^32 and 2^45: 128-bit), with a negative reference
+    rng = np.random.default_rng(11 + k)
+    F = 900
+    pts = rng.integers(0, 60, size=(F, 4)).astype(np.int64)
+    pts[:, -1] = 180 - pts[:, :-1].sum(axis=1) + rng.integers(0, 3, F)
+    ref = np.array([-5, -3, -2, -1], np.int64)
+    pts[17, k] = ref[k] + offset
+    want = oracle.hypervolume(pts[oracle.pareto_filter(pts)], ref)
+    assert _hv_points(M, pts, ref) == want
+
+
 @pytest.mark.parametrize("K,F", [(3, 7000), (4, 7000)])
 def test_hv_large_mostly_dominated(M, oracle, K, F):
     # beyond the shared-memory fast path: many points, few of them on the front; the
