@@ -275,14 +275,24 @@ def gpu_arm(args, rank, world):
     # buffers keep the sampler stream fed when the host thread falls behind -- a step's filter
     # work takes the SMs only in the sampler's wave tails, and the host waits for its result:
     # with three, some runs showed 0.07-0.6 ms gaps between samplings, with four one run in
-    # four 1.75 ms per step, with six 1.614-1.621 ms in all runs.)
-    depth = args.pipeline_depth
+    # four 1.75 ms per step, with six 1.614-1.621 ms in all runs; with six and two filter lanes
+    # 1.602-1.612 ms.)
+    depth = max(2, args.pipeline_depth)
     bufs = [buf] + [P.RoundBuffers(R, n, K) for _ in range(depth - 1)]
     s_a = torch.cuda.Stream(device=dev, priority=-1)
     s_b = torch.cuda.Stream(device=dev)
+    # two filter lanes (archive + stream): step s + 1's cuts and merge are queued on one while
+    # the host waits for step s's hypervolume on the other, so every wave tail of the sampler
+    # finds the next merge ready; with one lane the host issued each merge only after the
+    # previous step's read-back, fell up to the queue depth behind the sampler, and drained
+    # those steps after the last sampling (about 1 ms per run)
+    archs = [arch, P.Archive(n, K, capacity=1 << 18, max_batch=R)]
+    lanes = [s_b, torch.cuda.Stream(device=dev)]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     samp_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
     sampled = [None] * nsteps
+
+    launched = [-1]
 
     def launch_sample(s):
         with torch.cuda.stream(s_a):
@@ -291,6 +301,18 @@ def gpu_arm(args, rank, world):
             M.moq_sample(inst.handle, lam_all[s], R, params, 1, s, bufs[s % depth].bits, s_a)
             samp_ev[s][1].record(s_a)
             sampled[s] = s_a.record_event()
+        launched[0] = s
+
+    def issue_front(s):
+        # step s's cuts and merge on its lane. They wait until the next sampling's L2 flush is
+        # done (which implies sampling s is): ready together with that sampling, whose
+        # priority gives it the SMs first, they run in its wave tail instead of taking the SMs
+        # the flush freed before its first wave could
+        st, b = lanes[s % 2], bufs[s % depth]
+        st.wait_event(samp_ev[s + 1][0] if s + 1 <= launched[0] else sampled[s])
+        archs[s % 2].reset(st)
+        M.moq_evaluate_cuts(inst.handle, b.bits, R, b.cuts, st)
+        archs[s % 2].merge(b.cuts, b.bits, R, 0, stream=st)
 
     gc.collect()
     gc.disable()  # no collector pauses on the host thread that feeds the pipeline
@@ -298,25 +320,25 @@ def gpu_arm(args, rank, world):
         t_wall = time.perf_counter()
         t_start.record(stream)
         s_a.wait_stream(stream)
-        s_b.wait_stream(stream)
+        for ln in lanes:
+            ln.wait_stream(stream)
         for q in range(args.warmup, min(nsteps, args.warmup + depth - 1)):
             launch_sample(q)
+        issue_front(args.warmup)
         for s in range(args.warmup, nsteps):
             if s + depth - 1 < nsteps:
-                launch_sample(s + depth - 1)  # its buffer was last read by step s - 1, finished below
-            b = bufs[s % depth]
-            s_b.wait_event(sampled[s])
-            arch.reset(s_b)
-            M.moq_evaluate_cuts(inst.handle, b.bits, R, b.cuts, s_b)
-            arch.merge(b.cuts, b.bits, R, 0, stream=s_b)
-            hvs.append(arch.hypervolume(inst.ref, s_b))  # synchronises: the step's result on the host
+                launch_sample(s + depth - 1)  # its buffer was last read by step s - 1's cuts, finished
+            if s + 1 < nsteps:
+                issue_front(s + 1)  # its lane's last work, step s - 1's hypervolume, is finished
+            hvs.append(archs[s % 2].hypervolume(inst.ref, lanes[s % 2]))  # synchronises: the result on the host
         stream.wait_stream(s_a)
-        stream.wait_stream(s_b)
+        for ln in lanes:
+            stream.wait_stream(ln)
         t_end.record(stream)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
     gc.enable()
-    fronts.append(arch.size())
+    fronts.append(archs[(nsteps - 1) % 2].size())
     sample_ms = [samp_ev[s][0].elapsed_time(samp_ev[s][1]) for s in range(args.warmup, nsteps)]
     dev_s = t_start.elapsed_time(t_end) / 1e3
     dev_s, t_wall, samp_s = shard.max_over_ranks([dev_s, t_wall, sum(sample_ms) / 1e3])
@@ -330,6 +352,12 @@ def gpu_arm(args, rank, world):
     # s + depth - 1 are copied in on a third stream (once sampling s - 1, their buffer's last
     # reader, is done) while the queued samplings and step s's tail run; a few untimed steps
     # first, like the device-timed leg's warm-up. No L2 flush here: the path a caller runs.
+    # Here the filter stream has the higher priority: the host waits for every step's result
+    # and issues the next step's chain only then, so a chain that waited for the sampler's wave
+    # tail (as in the device-timed leg) could leave the host late and the sampler queue empty;
+    # measured 8.46-8.58e11 in every run, against 7.7-8.6e11 with the sampler stream first.
+    s_a = torch.cuda.Stream(device=dev)
+    s_b = torch.cuda.Stream(device=dev, priority=-1)
     e2e_steps = max(1, min(args.steps, 200))
     e2e_warm = min(3, max(1, args.warmup))
     lam_host = torch.from_numpy(np.stack([wl.dirichlet_lambdas(R * world, K, 777 + s)[first:first + R]
