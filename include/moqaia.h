@@ -350,9 +350,8 @@ int moq_hypervolume_points(const int64_t* pts, int64_t F, int32_t K, const int64
  * (16384) of up to 4 objectives, about 1.4 MB on every GPU that loads the library,
  * held until the process exits. The call allocates nothing; the caller still owns pts,
  * ref and out, and the 20 result bytes are read back into the call's own stack frame (no
- * pinned host buffer either). The first call on a device looks up that device's address
- * of the array (make it before any stream capture); the address stays valid for the life
- * of the device's context, so do not call this across a cudaDeviceReset. Every call
+ * pinned host buffer either). Every call looks up the current device's address of the
+ * array, so a cudaDeviceReset between calls, which can move it, is harmless. Every call
  * shares the one array and leaves its contents behind, so calls that overlap on the GPU
  * (e.g. from two streams at once) race; calls in sequence are safe (the call
  * synchronises its stream).

@@ -16,7 +16,6 @@
 // Slab contributions are reduced per block in int128 and summed by a final block.
 // Points with some y_k < r_k span an empty box and are left out.
 #include <algorithm>
-#include <mutex>
 
 #include "moq_common.cuh"
 
@@ -883,27 +882,15 @@ constexpr size_t kNoAllocBytes = 2 * round256(sizeof(int32_t) * 4 * kNoAllocMaxP
 
 static __device__ __align__(256) unsigned char g_hv_noalloc_scratch[kNoAllocBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mutex;
-void* g_noalloc_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device. The symbol's host-side
-// name is only a stand-in, so the address is looked up once per device (with that
-// device current) and cached. A cudaDeviceReset (or any teardown of the device's primary
-// context) reloads the module and can move the array, so the cached address is only valid
-// for the life of the context it was taken in.
+// Device address of the scratch array on the current device. The symbol's host-side name is
+// only a stand-in, so the address is looked up, with the device current, on every call
+// (cheap next to the call's own synchronisation): a cudaDeviceReset, or any teardown of the
+// device's primary context, reloads the module and can move the array.
 int noalloc_scratch(void** out)
 {
-    int dev = 0;
-    MOQ_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return fail(MOQ_ERR_UNSUPPORTED, "device index %d >= %d", dev, kMaxDevices);
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        MOQ_CUDA_TRY(cudaGetSymbolAddress(&p, g_hv_noalloc_scratch));
-        g_noalloc_ptr[dev] = p;
-    }
-    *out = g_noalloc_ptr[dev];
+    void* p = nullptr;
+    MOQ_CUDA_TRY(cudaGetSymbolAddress(&p, g_hv_noalloc_scratch));
+    *out = p;
     return MOQ_OK;
 }
 
