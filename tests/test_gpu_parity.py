@@ -890,10 +890,12 @@ def test_force_matches_fp64_in_every_form_and_layout(M, P, oracle, monkeypatch, 
     assert np.array_equal(got, x_out.cpu().numpy() < 0)
 
 
-@pytest.mark.parametrize("n,R", [(641, 1), (641, 2), (999, 3), (1023, 5), (700, 64)])
+@pytest.mark.parametrize("n,R", [(641, 1), (641, 2), (999, 3), (1023, 5), (700, 64), (896, 3), (898, 2)])
 def test_two_spins_and_quads_at_shape_edges(M, P, monkeypatch, n, R):
     # odd n, the first size past the block limit of the pair forms, replica counts below one
-    # block: the two-spin (FP32) and four-replica (FP16) forms against their pair forms, bit for bit
+    # block, the last size of the two-spin build bounded for 448 threads (896) and the first
+    # past it (898): the two-spin (FP32) and four-replica (FP16) forms against their pair
+    # forms, bit for bit
     if n % 2:  # a 3-regular graph on n - 1 spins and one more spin joined to two of them
         base = wl.random_regular(n - 1, 47, K=3)
         ei = np.concatenate([base.ei, np.array([0, 1], np.int32)])
