@@ -269,9 +269,9 @@ __global__ void __launch_bounds__(kTile) k_dominated_archive(const int64_t* __re
 }
 
 // ---- one warp per tested vector ----------------------------------------------------
-// The same tests with one warp per tested vector: its lanes take 32 comparators at a time,
+// The same tests with one warp per tested vector: its lanes take 128 comparators at a time,
 // read straight from global memory (coalesced; the eight warps of a block read the same
-// comparators, which L1 keeps), and the warp stops at the first chunk that holds a dominator
+// comparators, which L1 keeps), and the warp stops after the first 128 that hold a dominator
 // (a vote), so a vector dominated early costs a few chunks where the tile form keeps a whole
 // warp scanning until its last vector is decided.
 //   MODE 0: a candidate against the archive (>= everywhere: dominated, or an equal member,
@@ -280,10 +280,29 @@ __global__ void __launch_bounds__(kTile) k_dominated_archive(const int64_t* __re
 //   MODE 2: an archive member against the candidates (strictly dominated).
 // Counts may live on the device (the archive size, the compacted survivors); flags already
 // set are skipped and only ever set.
+// K int64 values of one vector, in 16-byte loads when K is even and the array is 16-byte
+// aligned (then every row is)
+template <int KT>
+__device__ __forceinline__ void load_vec(const int64_t* __restrict__ p, int64_t (&v)[KT], bool vec16)
+{
+    if (KT % 2 == 0 && vec16) {
+#pragma unroll
+        for (int k = 0; k < KT; k += 2) {
+            const longlong2 w = __ldg(reinterpret_cast<const longlong2*>(p + k));
+            v[k] = w.x;
+            v[k + 1] = w.y;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < KT; ++k) v[k] = __ldg(p + k);
+    }
+}
+
 template <int KT, int MODE>
 __global__ void __launch_bounds__(kTile) k_dominated_warp(const int64_t* __restrict__ vecs, int64_t n_vecs,
                                                           const int64_t* __restrict__ n_vecs_dev, const int64_t* __restrict__ cmp,
-                                                          int64_t n_cmp, const int64_t* __restrict__ n_cmp_dev, int32_t* flag)
+                                                          int64_t n_cmp, const int64_t* __restrict__ n_cmp_dev, int32_t* flag,
+                                                          bool vec16)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nv = n_vecs_dev ? min(n_vecs, *n_vecs_dev) : n_vecs;
@@ -294,19 +313,25 @@ __global__ void __launch_bounds__(kTile) k_dominated_warp(const int64_t* __restr
         int64_t u[KT];
 #pragma unroll
         for (int k = 0; k < KT; ++k) u[k] = vecs[c * KT + k];
+        // four chunks of 32 per vote: their loads are in flight together (the test is bound
+        // by the latency of the comparator loads, not by the comparisons)
         bool dom = false;
-        for (int64_t base = 0; base < nc && !dom; base += 32) {
-            const int64_t j = base + lane;
+        for (int64_t base = 0; base < nc && !dom; base += 4 * 32) {
             bool d = false;
-            if (j < nc) {
-                bool ge = true, gt = false;
 #pragma unroll
-                for (int k = 0; k < KT; ++k) {
-                    const int64_t v = cmp[j * KT + k];
-                    ge &= v >= u[k];
-                    gt |= v > u[k];
+            for (int q = 0; q < 4; ++q) {
+                const int64_t j = base + 32 * q + lane;
+                if (j < nc) {
+                    int64_t v[KT];
+                    load_vec<KT>(cmp + j * KT, v, vec16);
+                    bool ge = true, gt = false;
+#pragma unroll
+                    for (int k = 0; k < KT; ++k) {
+                        ge &= v[k] >= u[k];
+                        gt |= v[k] > u[k];
+                    }
+                    d |= ge && (MODE == 0 || gt || (MODE == 1 && j < c));
                 }
-                d = ge && (MODE == 0 || gt || (MODE == 1 && j < c));
             }
             dom = __any_sync(kFull, d);
         }
@@ -321,6 +346,8 @@ bool warp_filter()
     const char* env = getenv("MOQ_FILTER_FORM");
     return !(env && env[0] == 't');
 }
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 unsigned warp_grid(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kTile / 32), 148 * 16)); }
 
@@ -612,10 +639,11 @@ cudaError_t launch_filters(moq_archive* a, const int64_t* cuts, int64_t M, cudaS
         if (M < a->large_min) {
             if (wf) {
                 k_dominated_warp<KT, 0><<<warp_grid(M), kTile, 0, st>>>(cuts, M, nullptr, a->cuts[a->cur], a->cap, a->d_count,
-                                                                         a->flag_cand);
-                k_dominated_warp<KT, 1><<<warp_grid(M), kTile, 0, st>>>(cuts, M, nullptr, cuts, M, nullptr, a->flag_cand);
+                                                                         a->flag_cand, aligned16(a->cuts[a->cur]));
+                k_dominated_warp<KT, 1><<<warp_grid(M), kTile, 0, st>>>(cuts, M, nullptr, cuts, M, nullptr, a->flag_cand,
+                                                                         aligned16(cuts));
                 k_dominated_warp<KT, 2><<<warp_grid(a->cap), kTile, 0, st>>>(a->cuts[a->cur], a->cap, a->d_count, cuts, M, nullptr,
-                                                                              a->flag_arch);
+                                                                              a->flag_arch, aligned16(cuts));
             } else {
                 k_dominated_candidates<KT><<<dim3(gtiles, kArchChunks + nchunks), kTile, 0, st>>>(
                     a->cuts[a->cur], a->d_count, cuts, M, a->flag_cand, a->range, kArchChunks, nullptr);
@@ -632,16 +660,17 @@ cudaError_t launch_filters(moq_archive* a, const int64_t* cuts, int64_t M, cudaS
             k_dedup_mark<KT><<<g256, 256, 0, st>>>(cuts, M, a->table, a->table_mask, a->flag_cand);
             if (wf)
                 k_dominated_warp<KT, 0><<<warp_grid(M), kTile, 0, st>>>(cuts, M, nullptr, a->cuts[a->cur], a->cap, a->d_count,
-                                                                         a->flag_cand);
+                                                                         a->flag_cand, aligned16(a->cuts[a->cur]));
             else
                 k_dominated_candidates<KT><<<dim3(gtiles, kArchChunks), kTile, 0, st>>>(a->cuts[a->cur], a->d_count, cuts, M,
                                                                                        a->flag_cand, a->range, kArchChunks, nullptr);
             k_compact_survivors<KT><<<g256, 256, 0, st>>>(cuts, M, a->flag_cand, a->ccuts, a->cidx,
                                                           reinterpret_cast<unsigned long long*>(a->d_m));
             if (wf) {
-                k_dominated_warp<KT, 1><<<warp_grid(M), kTile, 0, st>>>(a->ccuts, M, a->d_m, a->ccuts, M, a->d_m, a->cflag);
+                k_dominated_warp<KT, 1><<<warp_grid(M), kTile, 0, st>>>(a->ccuts, M, a->d_m, a->ccuts, M, a->d_m, a->cflag,
+                                                                         aligned16(a->ccuts));
                 k_dominated_warp<KT, 2><<<warp_grid(a->cap), kTile, 0, st>>>(a->cuts[a->cur], a->cap, a->d_count, a->ccuts, M, a->d_m,
-                                                                              a->flag_arch);
+                                                                              a->flag_arch, aligned16(a->ccuts));
             } else {
                 k_dominated_candidates<KT><<<dim3(gtiles, nchunks), kTile, 0, st>>>(a->cuts[a->cur], a->d_count, a->ccuts, M,
                                                                                    a->cflag, a->range, 0, a->d_m);
