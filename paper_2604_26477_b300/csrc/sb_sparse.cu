@@ -44,7 +44,22 @@ struct SbArgs {
     float* y_out;
     uint32_t key0, key1, round32, rep_off;
     uint64_t* bits;
+    uint32_t rk0[10], rk1[10];  // Philox round keys: key0 + r * W0, key1 + r * W1
 };
+
+// The noise block of the samplers' step loops: Philox4x32-10 with the round keys taken from
+// the kernel parameters (constant operands) instead of bumped per round; the same words as
+// Philox4x32::block(c, key0, key1)
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const SbArgs& a)
+{
+#pragma unroll
+    for (int rnd = 0; rnd < 10; ++rnd) {
+        const uint64_t p0 = (uint64_t)Philox4x32::kM0 * c.x;
+        const uint64_t p1 = (uint64_t)Philox4x32::kM1 * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ a.rk0[rnd], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ a.rk1[rnd], (uint32_t)p0);
+    }
+    return c;
+}
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -174,8 +189,7 @@ __global__ void __launch_bounds__(1024) k_sb_sparse(const SbArgs a)
     };
     // one Philox4x32-10 block per eight steps: word q gives the Gaussians of steps 2q, 2q+1
     auto block8 = [&](int m) -> uint4 {
-        return NOISE ? Philox4x32::block(make_uint4((uint32_t)(m >> 3), (uint32_t)i, a.rep_off + (uint32_t)r, a.round32),
-                                         a.key0, a.key1)
+        return NOISE ? philox_rk(make_uint4((uint32_t)(m >> 3), (uint32_t)i, a.rep_off + (uint32_t)r, a.round32), a)
                      : make_uint4(0u, 0u, 0u, 0u);
     };
     // the Gaussians of four consecutive steps from two words
@@ -455,7 +469,7 @@ __global__ void __launch_bounds__(PUMP >= 3 ? kCapThreads : 1024, PUMP >= 3 ? 2 
         return pump_base(PUMP) == kPumpTable ? pump_t[m] : (pump_base(PUMP) == kPumpInline ? fmaf(a0inv, mf, -a0) : (__ldg(sched + m) - a0));
     };
     auto block8 = [&](int m, int r) -> uint4 {
-        return NOISE ? Philox4x32::block(make_uint4((uint32_t)(m >> 3), (uint32_t)i, a.rep_off + (uint32_t)r, a.round32), a.key0, a.key1)
+        return NOISE ? philox_rk(make_uint4((uint32_t)(m >> 3), (uint32_t)i, a.rep_off + (uint32_t)r, a.round32), a)
                      : make_uint4(0u, 0u, 0u, 0u);
     };
     auto noise4 = [&](uint32_t wa, uint32_t wbb, float (&e)[4]) {
@@ -635,7 +649,7 @@ __global__ void __launch_bounds__(MAXT, 2) k_sb_sparse2s(const SbArgs a)
         return pump_base(PUMP) == kPumpInline ? fmaf(a0inv, mf, -a0) : (__ldg(sched + m) - a0);
     };
     auto block8 = [&](int m, int i, int r) -> uint4 {
-        return NOISE ? Philox4x32::block(make_uint4((uint32_t)(m >> 3), (uint32_t)i, a.rep_off + (uint32_t)r, a.round32), a.key0, a.key1)
+        return NOISE ? philox_rk(make_uint4((uint32_t)(m >> 3), (uint32_t)i, a.rep_off + (uint32_t)r, a.round32), a)
                      : make_uint4(0u, 0u, 0u, 0u);
     };
     auto noise4 = [&](uint32_t wa, uint32_t wbb, float (&e)[4]) {
@@ -851,7 +865,7 @@ __global__ void __launch_bounds__(PUMP >= 3 ? kCapThreads : 1024, PUMP >= 3 ? 2 
         return __float2half2_rn(pump_base(PUMP) == kPumpInline ? fmaf(a0inv, mf, -a0) : (__ldg(sched + m) - a0));
     };
     auto block8 = [&](int m, int r) -> uint4 {
-        return NOISE ? Philox4x32::block(make_uint4((uint32_t)(m >> 3), (uint32_t)i, a.rep_off + (uint32_t)r, a.round32), a.key0, a.key1)
+        return NOISE ? philox_rk(make_uint4((uint32_t)(m >> 3), (uint32_t)i, a.rep_off + (uint32_t)r, a.round32), a)
                      : make_uint4(0u, 0u, 0u, 0u);
     };
     // the Gaussians of four steps of both replicas, rounded to FP16 (lane 0: r0, lane 1: r1)
@@ -1005,7 +1019,7 @@ __global__ void __launch_bounds__(1024) k_sb_sparse_h4(const SbArgs a)
         return __float2half2_rn(pump_base(PUMP) == kPumpInline ? fmaf(a0inv, mf, -a0) : (__ldg(sched + m) - a0));
     };
     auto block8 = [&](int m, int r) -> uint4 {
-        return NOISE ? Philox4x32::block(make_uint4((uint32_t)(m >> 3), (uint32_t)i, a.rep_off + (uint32_t)r, a.round32), a.key0, a.key1)
+        return NOISE ? philox_rk(make_uint4((uint32_t)(m >> 3), (uint32_t)i, a.rep_off + (uint32_t)r, a.round32), a)
                      : make_uint4(0u, 0u, 0u, 0u);
     };
     auto noise4 = [&](uint32_t wa, uint32_t wbb, uint32_t va, uint32_t vb, __half2 (&eg)[4]) {
@@ -1297,6 +1311,10 @@ extern "C" int moq_sample(const moq_instance* inst, const float* lambda, int32_t
     a.y_out = p->y_out;
     a.key0 = (uint32_t)seed;
     a.key1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        a.rk0[r] = a.key0 + (uint32_t)r * Philox4x32::kW0;
+        a.rk1[r] = a.key1 + (uint32_t)r * Philox4x32::kW1;
+    }
     a.round32 = (uint32_t)round;
     a.rep_off = p->replica_offset;
     a.bits = bits;
