@@ -100,15 +100,18 @@ __device__ __forceinline__ uint32_t word_of(const uint4& o, int q)
 // Two standard normals from one 32-bit word by Box-Muller on its 16-bit halves:
 // u1 = (low + 1) 2^-16 in (0, 1], u2 = high 2^-16 in [0, 1), rho = sqrt(-2 ln u1),
 // theta = 2 pi u2 -> (rho cos theta, rho sin theta). Each uniform is built exactly from
-// the bits of 1 + h 2^-16 (no integer conversion); the angle is evaluated as
-// 2 pi (u2 - 1/2) + pi so the fast sine/cosine see [-pi, pi).
+// the bits of 1 + h 2^-16 (no integer conversion). The angle is evaluated as
+// 2 pi (u2 - 1/2) + pi, so the fast sine/cosine see [-pi, pi): one multiply-add on
+// f = 1 + u2, f 2 pi - 3 pi. The radius uses ln u1 = ln 2 log2 u1, one multiply by -2 ln 2.
 __device__ __forceinline__ float2 box_muller16(uint32_t w)
 {
+    constexpr float kTwoPi = 6.2831853071795864f, kThreePi = 9.4247779607693797f;
+    constexpr float kMinus2Ln2 = -1.3862943611198906f;
     const float u1 = __uint_as_float(0x3F800000u | ((w & 0xFFFFu) << 7)) - (1.0f - 0x1p-16f);
-    const float u2c = __uint_as_float(0x3F800000u | ((w >> 9) & 0x7FFF80u)) - 1.5f;
-    const float rho = sqrt_approx(-2.0f * __logf(u1));
+    const float f2 = __uint_as_float(0x3F800000u | ((w >> 9) & 0x7FFF80u));
+    const float rho = sqrt_approx(kMinus2Ln2 * __log2f(u1));
     float s, c;
-    __sincosf(6.2831853071795864f * u2c, &s, &c);
+    __sincosf(fmaf(f2, kTwoPi, -kThreePi), &s, &c);
     return make_float2(-rho * c, -rho * s);
 }
 
