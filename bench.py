@@ -267,7 +267,7 @@ def gpu_arm(args, rank, world):
     torch.cuda.synchronize()
     # Timed region: the K steps as a pipeline over `depth` sample buffers -- the samplings of
     # steps s + 1 to s + depth - 1 are queued on one stream while step s's cuts, Pareto merge and
-    # hypervolume (a second stream, the result read back on the host) finish, so the host's
+    # hypervolume (a filter stream, the result read back on the host) finish, so the host's
     # read-back never leaves the sampler stream empty. The sampler stream has the higher
     # priority; the filter kernels take the SMs its blocks leave (its wave tails). Every step
     # does its whole path; the L2 flush (FLUSH_MIB) precedes every sampling launch inside the
@@ -1415,8 +1415,9 @@ def main():
               "alpha": w["alpha"], "precision": args.precision,
               "l2": FLUSH_NOTE, "parallelism": f"replicas x{world}",
               "timing": f"K steps timed as one region (CUDA events): steps s+1 to s+{args.pipeline_depth - 1} are queued "
-                        "on the (high-priority) sampler stream while step s's cuts, merge and hypervolume finish on a "
-                        "second stream; the hypervolume of every step is read back on the host",
+                        "on the (high-priority) sampler stream while step s's cuts, merge and hypervolume finish on one of "
+                        "two filter lanes (archive + stream, alternating by step); the hypervolume of every step is "
+                        "read back on the host",
               "prewarm_s": args.prewarm}
 
     if args.impl == "reference":
