@@ -50,6 +50,8 @@ extern "C" {
 #define MOQ_BSB 1 /* ballistic SB: phi(x) = x */
 #define MOQ_PREC_FP32 0 /* state and step arithmetic in FP32 */
 #define MOQ_PREC_FP16 1 /* state and step arithmetic in FP16, the paper's float16 (moq_sample) */
+#define MOQ_LAYOUT_PLAIN -1  /* moq_create_instance_layout: slots by decreasing degree, rows by column */
+#define MOQ_LAYOUT_DEFAULT 0 /* moq_create_instance_layout: the bank-conflict planner at its default effort */
 
 typedef struct moq_instance moq_instance;
 typedef struct moq_archive moq_archive;
@@ -108,6 +110,17 @@ void moq_default_params(moq_sample_params* p);
  * Ownership: inputs are copied; *out is owned by the caller until destroyed. */
 int moq_create_instance(int32_t n, int32_t K, int64_t E, const int32_t* ei, const int32_t* ej,
                         const int32_t* w, void* stream, moq_instance** out);
+/* a1 with the sparse samplers' memory layout chosen by the caller instead of the environment
+ * (the layout is an implementation detail with no counterpart in the paper; it changes the
+ * order of the FP32 force sums only, see moq_plan_gather_layout): layout = MOQ_LAYOUT_PLAIN
+ * keeps slots by decreasing degree and rows by column (no host search: 0.2 ms for a 1024-spin
+ * build instead of several ms, the better choice when the instance is sampled for only a few
+ * short rounds), MOQ_LAYOUT_DEFAULT runs the bank-conflict planner, m > 0 adds the longer
+ * search with m slot exchanges per spin. Reads no environment variable, so builds on several
+ * host threads may each pass their own layout. Everything else is moq_create_instance.
+ * Errors: MOQ_ERR_ARG (layout < MOQ_LAYOUT_PLAIN), then those of moq_create_instance. */
+int moq_create_instance_layout(int32_t n, int32_t K, int64_t E, const int32_t* ei, const int32_t* ej,
+                               const int32_t* w, int32_t layout, void* stream, moq_instance** out);
 /* a1 for a dense weight matrix: J_upper (host, K x n(n-1)/2, row k = objective k) holds
  * J^(k)_ij for the pairs i < j in row order ((0,1), (0,2), .., (0,n-1), (1,2), ..). The
  * pairs with a non-zero weight in some objective become the edges, in that order; the
@@ -125,7 +138,7 @@ int moq_create_instance_dense(int32_t n, int32_t K, const int32_t* J_upper, void
  * lengths the degrees); passes[4] or NULL: 8-byte and 4-byte shared-memory passes of one
  * gather step over all warps for the column layout, then for the chosen one. Setting
  * MOQ_SB_LAYOUT=0 in the environment makes moq_create_instance keep slots by decreasing
- * degree and rows by column; MOQ_SB_LAYOUT_EFFORT=m > 0 adds, for regular graphs whose blocks
+ * degree and rows by column (moq_create_instance_layout takes the choice as an argument); MOQ_SB_LAYOUT_EFFORT=m > 0 adds, for regular graphs whose blocks
  * hold one replica per slot, a longer search (m * n slot exchanges, about 0.15 ms per exchange
  * per spin at n = 1024: worth it for long jobs) aimed at the 8-byte gathers, kept where it is
  * better; both are read on every call. Errors: MOQ_ERR_ARG (NULL outputs), MOQ_ERR_UNSUPPORTED (n
@@ -336,6 +349,19 @@ int moq_archive_device_view(const moq_archive* a, const int64_t** cuts, const ui
  * Synchronises. Errors: MOQ_ERR_ARG, MOQ_ERR_UNSUPPORTED (K > 4),
  * MOQ_ERR_OVERFLOW (product of the K side lengths >= 2^125), MOQ_ERR_CUDA. */
 int moq_hypervolume(const moq_archive* a, const int64_t* ref, moq_hv* out, void* stream);
+/* a8 for several archives at once, the stop test of a driver over many instances (the
+ * repeat-until-covered loop of "Results and discussion", one hypervolume per instance and
+ * round): out[i] = moq_hypervolume(archives[i], refs + i*K), the same exact integer value,
+ * with two synchronisations of `stream` in all instead of two per archive (the front sizes
+ * are read back together, then every archive's computation is queued and the results are
+ * read back together). archives: `count` handles of one K (2..4); refs: host, count x K,
+ * row i = the reference point of archive i; out: host, count results (zero for an empty
+ * front). Errors: MOQ_ERR_ARG (count < 0, NULL, archives of different K),
+ * MOQ_ERR_UNSUPPORTED (K > 4), MOQ_ERR_CAPACITY (an archive overflowed: reported for the
+ * first such archive, every such latch cleared, as moq_archive_size does), MOQ_ERR_OVERFLOW,
+ * MOQ_ERR_CUDA; on an error the outputs past the failing archive are left zero. */
+int moq_hypervolume_many(const moq_archive* const* archives, const int64_t* refs, int32_t count, moq_hv* out,
+                         void* stream);
 /* The same for an arbitrary point set: pts device F x K int64 (need not be
  * non-dominated). workspace: device scratch of moq_hypervolume_workspace_size(F, K)
  * bytes, 256-byte aligned, owned by the caller. */

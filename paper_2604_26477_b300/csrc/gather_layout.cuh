@@ -642,7 +642,7 @@ namespace moq {
 // holds an invalid or repeated edge (the device checks report those). `passes`, if given,
 // receives the 8-byte and 4-byte passes of the column layout and of the chosen one.
 inline bool plan_gather_layout(int n, int64_t E, const int32_t* ei, const int32_t* ej, std::vector<int32_t>& slot_spin,
-                               std::vector<int32_t>& remap, int64_t* passes = nullptr)
+                               std::vector<int32_t>& remap, int64_t* passes, int64_t effort)
 {
     constexpr int kD = GatherLayout::kMaxDeg;
     if (n < 2 || n > 1024 || E <= 0) return false;
@@ -669,8 +669,8 @@ inline bool plan_gather_layout(int n, int64_t E, const int32_t* ei, const int32_
     lay.balance_slots(3LL * n, seed, 0.0);
     lay.order_reads(3, seed + 1);
     const GatherLayout* pick = 4 * lay.passes8() + lay.passes4() <= 4 * col.passes8() + col.passes4() ? &lay : &col;
-    // One replica per block slot on a regular graph: MOQ_SB_LAYOUT_EFFORT = m > 0 also runs the
-    // transversal plan with m * n exchanges and keeps it where it is better. It is off by default
+    // One replica per block slot on a regular graph: effort = m > 0 also runs the transversal
+    // plan with m * n exchanges and keeps it where it is better. It is off by default
     // because it costs more than a short job gains: at n = 1024, m = 1000 takes 0.15 s and cuts
     // the 8-byte passes from 382 to 254 (192 without conflicts), about 5 % of an FP32 sampling
     // launch of the two-spin form, 1 % of a float16 one
@@ -678,8 +678,6 @@ inline bool plan_gather_layout(int n, int64_t E, const int32_t* ei, const int32_
     bool regular = true;
     for (int i = 0; i < n; ++i) D = std::max(D, (int)deg[i]);
     for (int i = 0; i < n; ++i) regular &= deg[i] == D;
-    int64_t effort = 0;
-    if (const char* env = getenv("MOQ_SB_LAYOUT_EFFORT")) effort = std::max(0, atoi(env));
     GatherLayout tl = col;
     if (effort > 0 && fullest_warp_rb(n) == 1 && regular && D >= 2) {
         TransversalPlan tp(n, D, nbr);

@@ -770,23 +770,15 @@ int64_t moq_hypervolume_workspace_size(int64_t F, int32_t K)
 
 namespace moq {
 // The hypervolume of F points in the caller's workspace. With pinned_readback the result
-// words come back through this host thread's kept pinned buffer (allocated on the thread's
-// first call); without it they land in this stack frame, so the call allocates nothing on
-// the host or the device.
-int hv_points_impl(const int64_t* pts, int64_t F, int32_t K, const int64_t* ref, void* workspace, moq_hv* out, void* stream,
-                   bool pinned_readback)
+// words come back through a pinned buffer leased from the library's kept pinned pages (the
+// process's first leases allocate a page); without it they land in this stack frame, so the
+// call allocates nothing on the host or the device.
+// Queues the whole hypervolume computation of F > 0 points (2 <= K <= 4) on `st`: the
+// 128-bit result lands in ws.result and the overflow flag in ws.flags of the returned
+// workspace view. No synchronisation.
+int hv_launch(const int64_t* pts, int64_t F, int32_t K, const int64_t* ref, void* workspace, cudaStream_t st, HvWs& ws)
 {
-    if (!ref || !out || !workspace) return fail(MOQ_ERR_ARG, "moq_hypervolume_points: NULL argument");
-    if (F < 0 || F >= ((int64_t)1 << 31)) return fail(MOQ_ERR_ARG, "moq_hypervolume_points: F out of range");
-    if (K < 2) return fail(MOQ_ERR_ARG, "moq_hypervolume_points: K=%d < 2", K);
-    if (K > 4) return fail(MOQ_ERR_UNSUPPORTED, "moq_hypervolume_points: K=%d > 4", K);
-    if (F > 0 && !pts) return fail(MOQ_ERR_ARG, "moq_hypervolume_points: NULL points");
-    if (((uintptr_t)workspace) % 256) return fail(MOQ_ERR_ARG, "moq_hypervolume_points: workspace not 256-byte aligned");
-    out->lo = out->hi = 0;
-    out->approx = 0.0;
-    if (F == 0) return MOQ_OK;
-    cudaStream_t st = as_stream(stream);
-    HvWs ws = carve(workspace, F, K);
+    ws = carve(workspace, F, K);
     Ref4 r{};
     for (int k = 0; k < K; ++k) r.r[k] = ref[k];
     MOQ_CUDA_TRY(cudaMemsetAsync(ws.fv, 0, 2 * sizeof(int32_t), st));  // fv and wide
@@ -826,12 +818,32 @@ int hv_points_impl(const int64_t* pts, int64_t F, int32_t K, const int64_t* ref,
     }
     k_hv_final<<<1, kThreads, 0, st>>>(pts, F, K, r, nparts, ws);
     MOQ_LAUNCH_CHECK("moq_hypervolume launch");
+    return MOQ_OK;
+}
+
+int hv_points_impl(const int64_t* pts, int64_t F, int32_t K, const int64_t* ref, void* workspace, moq_hv* out, void* stream,
+                   bool pinned_readback)
+{
+    if (!ref || !out || !workspace) return fail(MOQ_ERR_ARG, "moq_hypervolume_points: NULL argument");
+    if (F < 0 || F >= ((int64_t)1 << 31)) return fail(MOQ_ERR_ARG, "moq_hypervolume_points: F out of range");
+    if (K < 2) return fail(MOQ_ERR_ARG, "moq_hypervolume_points: K=%d < 2", K);
+    if (K > 4) return fail(MOQ_ERR_UNSUPPORTED, "moq_hypervolume_points: K=%d > 4", K);
+    if (F > 0 && !pts) return fail(MOQ_ERR_ARG, "moq_hypervolume_points: NULL points");
+    if (((uintptr_t)workspace) % 256) return fail(MOQ_ERR_ARG, "moq_hypervolume_points: workspace not 256-byte aligned");
+    out->lo = out->hi = 0;
+    out->approx = 0.0;
+    if (F == 0) return MOQ_OK;
+    cudaStream_t st = as_stream(stream);
+    HvWs ws;
+    const int rc = hv_launch(pts, F, K, ref, workspace, st, ws);
+    if (rc != MOQ_OK) return rc;
     struct Result {
         i128 v;
         int32_t flags;
     } local;
-    Result* pin = pinned_readback ? static_cast<Result*>(pinned_scratch(sizeof(Result))) : nullptr;
-    Result& host = pin ? *pin : local;
+    PinnedLease lease(sizeof(Result), pinned_readback);
+    lease.arm(st);
+    Result& host = lease.p ? *static_cast<Result*>(lease.p) : local;
     MOQ_CUDA_TRY(cudaMemcpyAsync(&host.v, ws.result, sizeof(i128), cudaMemcpyDeviceToHost, st));
     MOQ_CUDA_TRY(cudaMemcpyAsync(&host.flags, ws.flags, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     MOQ_CUDA_TRY(cudaStreamSynchronize(st));
@@ -860,6 +872,83 @@ int moq_hypervolume(const moq_archive* a, const int64_t* ref, moq_hv* out, void*
     int rc = moq_archive_size(a, &F, stream);
     if (rc != MOQ_OK) return rc;
     return moq_hypervolume_points(a->cuts[a->cur], F, a->K, ref, a->hv_ws, out, stream);
+}
+
+int moq_hypervolume_many(const moq_archive* const* archives, const int64_t* refs, int32_t count, moq_hv* out, void* stream)
+{
+    using namespace moq;
+    if (count < 0) return fail(MOQ_ERR_ARG, "moq_hypervolume_many: count=%d < 0", count);
+    if (count == 0) return MOQ_OK;
+    if (!archives || !refs || !out) return fail(MOQ_ERR_ARG, "moq_hypervolume_many: NULL argument");
+    for (int32_t i = 0; i < count; ++i) {
+        if (!archives[i]) return fail(MOQ_ERR_ARG, "moq_hypervolume_many: archive %d is NULL", i);
+        if (archives[i]->K != archives[0]->K) return fail(MOQ_ERR_ARG, "moq_hypervolume_many: archives of different K");
+    }
+    const int K = archives[0]->K;
+    if (K > 4) return fail(MOQ_ERR_UNSUPPORTED, "moq_hypervolume_many: K=%d > 4", K);
+    for (int32_t i = 0; i < count; ++i) {
+        out[i].lo = out[i].hi = 0;
+        out[i].approx = 0.0;
+    }
+    cudaStream_t st = as_stream(stream);
+    // per archive: front size and status, then the result and its overflow flag, in one
+    // leased pinned buffer; chunks of kPer archives per lease
+    struct Slot {
+        int64_t size;
+        int32_t status;
+        int32_t flags;
+        i128 v;
+    };
+    constexpr int32_t kPer = 4096 / sizeof(Slot);
+    Slot fallback[kPer];
+    PinnedLease lease(sizeof(Slot) * kPer);
+    lease.arm(st);
+    Slot* slot = lease.p ? static_cast<Slot*>(lease.p) : fallback;
+    for (int32_t c0 = 0; c0 < count; c0 += kPer) {
+        const int32_t c1 = std::min(count, c0 + kPer);
+        for (int32_t i = c0; i < c1; ++i) {
+            MOQ_CUDA_TRY(cudaMemcpyAsync(&slot[i - c0].size, archives[i]->d_count, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            MOQ_CUDA_TRY(cudaMemcpyAsync(&slot[i - c0].status, archives[i]->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        }
+        MOQ_CUDA_TRY(cudaStreamSynchronize(st));
+        int32_t full = -1;
+        for (int32_t i = c0; i < c1; ++i)
+            if (slot[i - c0].status & kStatusCapacity) {
+                // as moq_archive_size: report the capacity error once and clear the latch
+                MOQ_CUDA_TRY(cudaMemsetAsync(archives[i]->d_status, 0, sizeof(int32_t), st));
+                if (full < 0) full = i;
+            }
+        if (full >= 0) {
+            MOQ_CUDA_TRY(cudaStreamSynchronize(st));
+            return fail(MOQ_ERR_CAPACITY, "moq_hypervolume_many: archive %d: capacity %lld exceeded; the archive was left unchanged",
+                        full, (long long)archives[full]->cap);
+        }
+        int32_t queued = 0;
+        for (int32_t i = c0; i < c1; ++i) {
+            const moq_archive* a = archives[i];
+            const int64_t F = slot[i - c0].size;
+            slot[i - c0].flags = 0;
+            if (F <= 0) continue;
+            if (F >= ((int64_t)1 << 31)) return fail(MOQ_ERR_ARG, "moq_hypervolume_many: archive %d: front too large", i);
+            HvWs ws;
+            const int rc = hv_launch(a->cuts[a->cur], F, K, refs + (int64_t)i * K, a->hv_ws, st, ws);
+            if (rc != MOQ_OK) return rc;
+            MOQ_CUDA_TRY(cudaMemcpyAsync(&slot[i - c0].v, ws.result, sizeof(i128), cudaMemcpyDeviceToHost, st));
+            MOQ_CUDA_TRY(cudaMemcpyAsync(&slot[i - c0].flags, ws.flags, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            ++queued;
+        }
+        if (queued) MOQ_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int32_t i = c0; i < c1; ++i) {
+            if (slot[i - c0].size <= 0) continue;
+            if (slot[i - c0].flags & 1)
+                return fail(MOQ_ERR_OVERFLOW, "moq_hypervolume_many: archive %d: side-length product reaches 2^125", i);
+            const i128 v = slot[i - c0].v;
+            out[i].lo = (int64_t)(uint64_t)v;
+            out[i].hi = (int64_t)(v >> 64);
+            out[i].approx = (double)v;
+        }
+    }
+    return MOQ_OK;
 }
 
 }  // extern "C"

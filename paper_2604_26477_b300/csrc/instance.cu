@@ -235,6 +235,25 @@ struct SlabPlan {
     }
 };
 
+// MOQ_SB_LAYOUT_EFFORT = m > 0: the longer layout search (read on every call)
+int64_t layout_effort_from_env()
+{
+    const char* env = getenv("MOQ_SB_LAYOUT_EFFORT");
+    return env ? std::max(0, atoi(env)) : 0;
+}
+
+// moq_create_instance's layout from the environment: MOQ_SB_LAYOUT=0 keeps the plain layout,
+// else the planner with MOQ_SB_LAYOUT_EFFORT's longer search
+int32_t layout_from_env()
+{
+    const char* env = getenv("MOQ_SB_LAYOUT");
+    if (env && atoi(env) == 0) return MOQ_LAYOUT_PLAIN;
+    return (int32_t)std::min<int64_t>(layout_effort_from_env(), INT32_MAX);
+}
+
+int create_instance_impl(int32_t n, int32_t K, int64_t E, const int32_t* ei, const int32_t* ej, const int32_t* w,
+                         int32_t layout, void* stream, moq_instance** out);
+
 }  // namespace
 }  // namespace moq
 
@@ -246,7 +265,7 @@ int moq_plan_gather_layout(int32_t n, int64_t E, const int32_t* ei, const int32_
     using namespace moq;
     if (!ei || !ej || !slot_spin || !gather) return fail(MOQ_ERR_ARG, "moq_plan_gather_layout: NULL pointer");
     std::vector<int32_t> order, remap;
-    if (!plan_gather_layout(n, E, ei, ej, order, remap, passes))
+    if (!plan_gather_layout(n, E, ei, ej, order, remap, passes, layout_effort_from_env()))
         return fail(MOQ_ERR_UNSUPPORTED, "moq_plan_gather_layout: graph outside the sparse samplers' range (n=%d, E=%lld)", n,
                     (long long)E);
     std::copy(order.begin(), order.end(), slot_spin);
@@ -269,10 +288,29 @@ int moq_plan_gather_layout(int32_t n, int64_t E, const int32_t* ei, const int32_
     return MOQ_OK;
 }
 
+
 int moq_create_instance(int32_t n, int32_t K, int64_t E, const int32_t* ei, const int32_t* ej, const int32_t* w,
                         void* stream, moq_instance** out)
 {
-    using namespace moq;
+    return moq::create_instance_impl(n, K, E, ei, ej, w, moq::layout_from_env(), stream, out);
+}
+
+int moq_create_instance_layout(int32_t n, int32_t K, int64_t E, const int32_t* ei, const int32_t* ej, const int32_t* w,
+                               int32_t layout, void* stream, moq_instance** out)
+{
+    if (out) *out = nullptr;
+    if (layout < MOQ_LAYOUT_PLAIN)
+        return moq::fail(MOQ_ERR_ARG, "moq_create_instance_layout: layout=%d below MOQ_LAYOUT_PLAIN", layout);
+    return moq::create_instance_impl(n, K, E, ei, ej, w, layout, stream, out);
+}
+
+}  // extern "C"
+
+namespace moq {
+namespace {
+int create_instance_impl(int32_t n, int32_t K, int64_t E, const int32_t* ei, const int32_t* ej, const int32_t* w,
+                         int32_t layout, void* stream, moq_instance** out)
+{
     if (!out) return fail(MOQ_ERR_ARG, "moq_create_instance: out is NULL");
     *out = nullptr;
     if (n < 2 || n > (1 << 24)) return fail(MOQ_ERR_ARG, "moq_create_instance: n=%d outside [2, 2^24]", n);
@@ -301,7 +339,8 @@ int moq_create_instance(int32_t n, int32_t K, int64_t E, const int32_t* ei, cons
     // edge list; validated on the device below)
     // For graphs the on-chip sampler takes (n <= 1024, degrees <= 8) the slots and the gather
     // order of each CSR row come from plan_gather_layout (against shared-memory bank conflicts;
-    // MOQ_SB_LAYOUT=0 keeps the plain layout below, rows by column).
+    // layout = MOQ_LAYOUT_PLAIN keeps the plain layout below, rows by column; m > 0 adds the
+    // longer search with m exchanges per spin).
     std::vector<int32_t> order(n), inv(n), remap;
     {
         std::vector<int32_t> dgr(n, 0);
@@ -311,10 +350,9 @@ int moq_create_instance(int32_t n, int32_t K, int64_t E, const int32_t* ei, cons
         }
         for (int32_t i = 0; i < n; ++i) order[i] = i;
         std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return dgr[a] > dgr[b]; });
-        const char* env = getenv("MOQ_SB_LAYOUT");
-        if (!(env && atoi(env) == 0)) {
+        if (layout != MOQ_LAYOUT_PLAIN) {
             std::vector<int32_t> planned;
-            if (plan_gather_layout(n, E, ei, ej, planned, remap)) order.swap(planned);
+            if (plan_gather_layout(n, E, ei, ej, planned, remap, nullptr, layout)) order.swap(planned);
         }
         for (int32_t q = 0; q < n; ++q) inv[order[q]] = q;
     }
@@ -382,8 +420,9 @@ int moq_create_instance(int32_t n, int32_t K, int64_t E, const int32_t* ei, cons
         long long sums[3 * kMaxK + 2 * kMaxK + kMaxK * (kMaxK - 1) / 2];
         int32_t status[2];
     } local;
-    ReadBack* pin = static_cast<ReadBack*>(pinned_scratch(sizeof(ReadBack)));
-    ReadBack& rb = pin ? *pin : local;
+    PinnedLease lease(sizeof(ReadBack));
+    lease.arm(st);
+    ReadBack& rb = lease.p ? *static_cast<ReadBack*>(lease.p) : local;
     int32_t* hstatus = rb.status;
     long long* hsums = rb.sums;
     MOQ_STEP(cu(cudaMemcpyAsync(hstatus, status, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, st), "read status"));
@@ -410,6 +449,10 @@ int moq_create_instance(int32_t n, int32_t K, int64_t E, const int32_t* ei, cons
     *out = h;
     return MOQ_OK;
 }
+}  // namespace
+}  // namespace moq
+
+extern "C" {
 
 void moq_destroy_instance(moq_instance* inst) { moq::free_instance(inst); }
 

@@ -34,14 +34,32 @@ inline cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 // One device slab per handle and lifetime class from a library-owned memory pool that keeps
 // freed memory; slab_alloc is ordered on `st`; slab_free waits for the device first,
 // slab_free_async frees in the order of `st` (a slab only `st` used). Pinned
-// 64-byte host slots for read-backs. Offsets inside a slab are rounded up with slab_align.
+// 64-byte host slots for the read-backs of a handle. Offsets inside a slab are rounded up with slab_align.
 size_t slab_align(size_t bytes);
 cudaError_t slab_alloc(void** p, size_t bytes, cudaStream_t st);
 void slab_free(void* p);
 void slab_free_async(void* p, cudaStream_t st);  // once everything queued on st before it is done
 cudaError_t pinned_slot_alloc(void** p);
 void pinned_slot_free(void* p);
-void* pinned_scratch(size_t bytes);  // this host thread's pinned read-back buffer (NULL if pinning fails)
+// Pinned read-back buffer of up to 4 KB for the length of one synchronising call (NULL if
+// bytes is larger or pinning fails); PinnedLease returns it on scope exit, after waiting for
+// the stream it was armed with, so no copy queued into it can outlive the lease.
+void* pinned_lease_acquire(size_t bytes);
+void pinned_lease_release(void* p);
+struct PinnedLease {
+    void* p;
+    cudaStream_t st = nullptr;
+    bool armed = false;
+    explicit PinnedLease(size_t bytes, bool want = true) : p(want ? pinned_lease_acquire(bytes) : nullptr) {}
+    void arm(cudaStream_t s) { st = s; armed = true; }
+    ~PinnedLease()
+    {
+        if (p && armed) cudaStreamSynchronize(st);
+        pinned_lease_release(p);
+    }
+    PinnedLease(const PinnedLease&) = delete;
+    PinnedLease& operator=(const PinnedLease&) = delete;
+};
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 

@@ -7,7 +7,8 @@
 // such as a time-to-target measurement. Here a handle takes one slab per lifetime class from
 // a memory pool that keeps what is freed (release threshold: unlimited), so after the first
 // handle of a size the allocation is a pool lookup; pinned read-back words come from 64-byte
-// slots carved out of 64 KB pinned pages that are kept for the life of the process.
+// slots (one per archive) or 4 KB leases (one per synchronising call) carved out of 64 KB
+// pinned pages that are kept for the life of the process.
 #include <mutex>
 #include <vector>
 
@@ -45,9 +46,11 @@ cudaError_t pool_of(int device, cudaMemPool_t* out)
     return cudaSuccess;
 }
 
-constexpr size_t kSlotBytes = 64, kPageBytes = 64 * 1024;
+constexpr size_t kSlotBytes = 64, kPageBytes = 64 * 1024, kLeaseBytes = 4096;
 std::mutex g_slot_mutex;
 std::vector<void*> g_free_slots;
+std::mutex g_lease_mutex;
+std::vector<void*> g_free_leases;
 
 }  // namespace
 
@@ -101,21 +104,29 @@ void pinned_slot_free(void* p)
     g_free_slots.push_back(p);
 }
 
-void* pinned_scratch(size_t bytes)
+void* pinned_lease_acquire(size_t bytes)
 {
-    // per host thread, grown on demand and kept (a copy into pageable memory is staged by
-    // the driver and costs more than the bytes)
-    thread_local void* buf = nullptr;
-    thread_local size_t cap = 0;
-    if (cap < bytes) {
-        void* p = nullptr;
-        const size_t want = bytes < 4096 ? 4096 : bytes;
-        if (cudaMallocHost(&p, want) != cudaSuccess) return nullptr;
-        if (buf) cudaFreeHost(buf);
-        buf = p;
-        cap = want;
+    // buffers of kLeaseBytes carved from pinned pages that are kept for the life of the
+    // process, shared by all host threads: a thread's first read-back costs no page-locked
+    // allocation (each cudaMallocHost takes about a millisecond, serialised across threads)
+    // and a thread that exits leaves nothing behind
+    if (bytes > kLeaseBytes) return nullptr;
+    std::lock_guard<std::mutex> lock(g_lease_mutex);
+    if (g_free_leases.empty()) {
+        void* page = nullptr;
+        if (cudaMallocHost(&page, kPageBytes) != cudaSuccess) return nullptr;
+        for (size_t off = kPageBytes; off > 0; off -= kLeaseBytes) g_free_leases.push_back(static_cast<char*>(page) + off - kLeaseBytes);
     }
-    return buf;
+    void* p = g_free_leases.back();
+    g_free_leases.pop_back();
+    return p;
+}
+
+void pinned_lease_release(void* p)
+{
+    if (!p) return;
+    std::lock_guard<std::mutex> lock(g_lease_mutex);
+    g_free_leases.push_back(p);
 }
 
 }  // namespace moq

@@ -26,6 +26,8 @@ MOQ_ERR_OVERFLOW = -6
 MOQ_ERR_UNSUPPORTED = -7
 MOQ_DSB = 0
 MOQ_BSB = 1
+MOQ_LAYOUT_PLAIN = -1
+MOQ_LAYOUT_DEFAULT = 0
 MOQ_PREC_FP32 = 0
 MOQ_PREC_FP16 = 1
 MOQ_MLP_CUDA_CORES = 0
@@ -66,6 +68,7 @@ _vp, _i32, _i64, _u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
 _sigs = {
     "moq_default_params": (None, [C.POINTER(moq_sample_params)]),
     "moq_create_instance": (C.c_int, [_i32, _i32, _i64, _vp, _vp, _vp, _vp, C.POINTER(_vp)]),
+    "moq_create_instance_layout": (C.c_int, [_i32, _i32, _i64, _vp, _vp, _vp, _i32, _vp, C.POINTER(_vp)]),
     "moq_create_instance_dense": (C.c_int, [_i32, _i32, _vp, _vp, C.POINTER(_vp)]),
     "moq_plan_gather_layout": (C.c_int, [_i32, _i64, _vp, _vp, _vp, _vp, _vp]),
     "moq_destroy_instance": (None, [_vp]),
@@ -81,6 +84,7 @@ _sigs = {
     "moq_archive_copy_out": (C.c_int, [_vp, _vp, _vp, _vp, _i64, C.POINTER(_i64), _vp]),
     "moq_archive_device_view": (C.c_int, [_vp, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp)]),
     "moq_hypervolume": (C.c_int, [_vp, _vp, C.POINTER(moq_hv), _vp]),
+    "moq_hypervolume_many": (C.c_int, [C.POINTER(_vp), _vp, _i32, C.POINTER(moq_hv), _vp]),
     "moq_hypervolume_workspace_size": (_i64, [_i64, _i32]),
     "moq_hypervolume_points": (C.c_int, [_vp, _i64, _i32, _vp, _vp, C.POINTER(moq_hv), _vp]),
     "moq_hypervolume_noalloc_max_points": (_i64, []),
@@ -200,14 +204,20 @@ def moq_default_params(**overrides) -> moq_sample_params:
     return p
 
 
-def moq_create_instance(n, K, E, ei, ej, w, stream=None) -> C.c_void_p:
+def moq_create_instance(n, K, E, ei, ej, w, stream=None, layout=None) -> C.c_void_p:
+    """``layout=None``: ``moq_create_instance`` (layout from the environment); else
+    ``moq_create_instance_layout`` with MOQ_LAYOUT_PLAIN, MOQ_LAYOUT_DEFAULT or an effort m > 0."""
     ei_, pei = _hptr(ei, np.int32)
     ej_, pej = _hptr(ej, np.int32)
     w_, pw = _hptr(w, np.int32)
     if ei_.size != E or ej_.size != E or w_.size != K * E:
         raise ValueError("edge arrays must have E entries and w K*E")
     h = C.c_void_p()
-    _check(_lib.moq_create_instance(n, K, E, pei, pej, pw, _stream(stream), C.byref(h)), "moq_create_instance")
+    if layout is None:
+        _check(_lib.moq_create_instance(n, K, E, pei, pej, pw, _stream(stream), C.byref(h)), "moq_create_instance")
+    else:
+        _check(_lib.moq_create_instance_layout(n, K, E, pei, pej, pw, int(layout), _stream(stream), C.byref(h)),
+               "moq_create_instance_layout")
     return h
 
 
@@ -330,6 +340,18 @@ def moq_hypervolume(a, ref, stream=None) -> int:
     out = moq_hv()
     _check(_lib.moq_hypervolume(a, pref, C.byref(out), _stream(stream)), "moq_hypervolume")
     return out.value()
+
+
+def moq_hypervolume_many(archives, refs, stream=None) -> list:
+    """Exact hypervolumes of several archives of one K (refs: count x K), two synchronisations in all."""
+    count = len(archives)
+    refs_, pref = _hptr(refs, np.int64)
+    if count and (refs_.size % count or refs_.size // count < 2):
+        raise ValueError("refs must hold one reference point (K >= 2 entries) per archive")
+    hs = (_vp * max(count, 1))(*[a.value if isinstance(a, C.c_void_p) else a for a in archives])
+    out = (moq_hv * max(count, 1))()
+    _check(_lib.moq_hypervolume_many(hs, pref, count, out, _stream(stream)), "moq_hypervolume_many")
+    return [out[i].value() for i in range(count)]
 
 
 def moq_hypervolume_workspace_size(F, K) -> int:

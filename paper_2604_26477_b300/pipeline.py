@@ -8,6 +8,7 @@ Everything here is marshalling and orchestration; each computation is one C-ABI 
 from __future__ import annotations
 
 import os
+import threading
 import time
 
 import numpy as np
@@ -56,9 +57,9 @@ def exhaustive_front(inst: "Instance", chunk_log2: int = 20, stream=None):
 class Instance:
     """Device copy of an MO-MaxCut instance (``moq_create_instance``)."""
 
-    def __init__(self, inst, stream=None):
+    def __init__(self, inst, stream=None, layout=None):
         self.src = inst
-        self.handle = M.moq_create_instance(inst.n, inst.K, inst.E, inst.ei, inst.ej, inst.w, stream)
+        self.handle = M.moq_create_instance(inst.n, inst.K, inst.E, inst.ei, inst.ej, inst.w, stream, layout)
         self.info = M.moq_instance_get_info(self.handle)
         self.n, self.K, self.W = inst.n, inst.K, self.info["words"]
         self.ref = np.array(self.info["ref_point"], np.int64)
@@ -75,35 +76,42 @@ class Instance:
             pass
 
 
-def create_instances(srcs, stream=None, threads=None, layout_effort=None):
-    """``Instance`` of every source, built on host threads (the build's host part, the samplers'
-    shared-memory layout, runs in parallel; the device part is ordered on ``stream``).
-    ``layout_effort`` = m > 0 runs the longer layout search (m slot exchanges per spin, for
-    regular graphs) for these builds, through ``MOQ_SB_LAYOUT_EFFORT``, restored afterwards."""
+_build_streams = threading.local()
+
+
+def create_instances(srcs, stream=None, threads=None, layout_effort=None, layout=None):
+    """``Instance`` of every source, built on host threads: the build's host part (the
+    samplers' shared-memory layout) runs in parallel, and the device part of each build is
+    ordered on a stream of its own thread -- on one shared stream the builds' pageable
+    copies, kernels and synchronisations queue behind one another. Every build has finished
+    on the device when this returns, so the instances are ready for any stream, ``stream``
+    included. ``layout``: as ``moq_create_instance_layout`` (None: from the environment),
+    one for all or a list with one per source; ``layout_effort`` = m > 0 is the same as
+    ``layout=m`` (the longer layout search, m slot exchanges per spin, for regular graphs)."""
     import concurrent.futures
 
     srcs = list(srcs)
-    old = os.environ.get("MOQ_SB_LAYOUT_EFFORT")
     if layout_effort is not None:
-        os.environ["MOQ_SB_LAYOUT_EFFORT"] = str(int(layout_effort))
-    try:
-        if len(srcs) < 2:
-            return [Instance(s, stream) for s in srcs]
-        dev = torch.cuda.current_device()
+        layout = int(layout_effort)
+    layouts = list(layout) if isinstance(layout, (list, tuple)) else [layout] * len(srcs)
+    if len(layouts) != len(srcs):
+        raise ValueError("one layout per source")
+    if len(srcs) < 2:
+        return [Instance(s, stream, lay) for s, lay in zip(srcs, layouts)]
+    dev = torch.cuda.current_device()
 
-        def build(s):
-            torch.cuda.set_device(dev)
-            return Instance(s, stream)
+    def build(job):
+        s, lay = job
+        torch.cuda.set_device(dev)
+        if not hasattr(_build_streams, "s"):
+            _build_streams.s = torch.cuda.Stream(device=dev)
+        return Instance(s, _build_streams.s, lay)
 
-        workers = threads or min(len(srcs), os.cpu_count() or 1, 16)
-        with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
-            return list(ex.map(build, srcs))
-    finally:
-        if layout_effort is not None:
-            if old is None:
-                os.environ.pop("MOQ_SB_LAYOUT_EFFORT", None)
-            else:
-                os.environ["MOQ_SB_LAYOUT_EFFORT"] = old
+    # the builds start after the work queued so far (on the caller's stream, or anywhere)
+    stream.synchronize() if isinstance(stream, torch.cuda.Stream) else torch.cuda.synchronize(dev)
+    workers = threads or min(len(srcs), os.cpu_count() or 1, 16)
+    with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
+        return list(ex.map(build, zip(srcs, layouts)))
 
 
 class Archive:
@@ -119,6 +127,14 @@ class Archive:
 
     def size(self, stream=None):
         return M.moq_archive_size(self.handle, stream)
+
+    @staticmethod
+    def hypervolume_many(archives, refs, stream=None):
+        """Exact hypervolume of every archive's front (one K), two synchronisations in all."""
+        if not archives:
+            return []
+        return M.moq_hypervolume_many([a.handle for a in archives], np.stack([np.asarray(r, np.int64) for r in refs]),
+                                      stream)
 
     def hypervolume(self, ref, stream=None):
         return M.moq_hypervolume(self.handle, ref, stream)
@@ -359,20 +375,42 @@ class LearnedProposer:
             pass
 
 
+def round_layout(params, n=None):
+    """The samplers' memory layout the round drivers build with, by the sampler's precision
+    and the graph size.
+
+    The bank-conflict planner is host work inside every time-to-target clock (0.2 ms at
+    n = 42, 3-12 ms at n = 1024 depending on the host). The float16 samplers gather 4-byte
+    half2 words and gain little from it, the FP32 pair forms gather 8-byte words and gain
+    4-16 %. Measured on 16 random 3-regular instances (n = 118..1020, 1024 replicas per
+    round, 8 seeds): the 16 builds took 24-33 ms with the planner against 9-10 ms without;
+    float16 NI-dSB (T = 3000) batched reached 99 % of the plain sampler's hypervolume in
+    66 ms without the planner against 89 ms with it (99.9 %: 287 against 300 ms), while plain
+    FP32 dSB one instance at a time took 80 against 83 ms at 99 % but 885 against 714 ms at
+    99.9 % (60 rounds). On small graphs the planner gains about 1 % (n = 42: 44 against 39
+    8-byte passes per gather step) for 0.2 ms or more of a sub-millisecond clock. So float16
+    rounds and graphs of up to 128 spins build with the plain layout, larger FP32 ones with
+    the planner.
+    """
+    fp16 = getattr(params, "precision", M.MOQ_PREC_FP32) == M.MOQ_PREC_FP16
+    return M.MOQ_LAYOUT_PLAIN if fp16 or (n is not None and n <= 128) else M.MOQ_LAYOUT_DEFAULT
+
+
 def time_to_target(src, target_hv: int, params, R: int, seed: int = 0, max_rounds: int = 1000,
                    capacity=1 << 18, learned: bool = False, proposer_kwargs=None, dense: bool = False,
-                   dense_form: str = "bf16"):
+                   dense_form: str = "bf16", layout=None):
     """Repeat sampling rounds until the archive's hypervolume reaches ``target_hv``.
 
-    The clock covers instance construction, every round (weight vectors, sampling, cuts,
-    Pareto merge, the surrogate's training and proposal when ``learned``) and the
-    hypervolume checks (one synchronisation per round).
+    The clock covers instance construction (with the samplers' memory ``layout``; None:
+    ``round_layout(params, n)``), every round (weight vectors, sampling, cuts, Pareto merge, the
+    surrogate's training and proposal when ``learned``) and the hypervolume checks (one
+    synchronisation per round).
     Returns dict(seconds, rounds, samples, hv, front, reached, trace) with trace a list of
     (samples, hv) after each round.
     """
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    inst = Instance(src)
+    inst = Instance(src, layout=round_layout(params, src.n) if layout is None else layout)
     arch = Archive(src.n, src.K, capacity=capacity, max_batch=R)
     buf = RoundBuffers(R, src.n, src.K)
     dh = M.moq_dense_create(inst.handle, R) if dense else None
@@ -497,7 +535,8 @@ class BatchLearnedProposer:
 
 
 def time_to_target_batch(srcs, targets, params, R: int, seed: int = 0, max_rounds: int = 256, batched: bool = True,
-                         learned: bool = False, tiles=(0, 0), capacity=1 << 18, proposer_kwargs=None):
+                         learned: bool = False, tiles=(0, 0), capacity=1 << 18, proposer_kwargs=None,
+                         layout=None):
     """Rounds over a set of instances until every instance's archive reaches its target
     hypervolume (the job is done when the whole set is).
 
@@ -505,15 +544,17 @@ def time_to_target_batch(srcs, targets, params, R: int, seed: int = 0, max_round
     over the instances still short of their target (``moq_batch_set_replicas`` drops the
     others), tile shape ``tiles`` ((0, 0): per-instance launches over internal streams);
     else one ``sample_round`` per such instance in turn. Every instance has its own archive,
-    and after each round every active instance's hypervolume is checked (one synchronisation
-    each). ``learned`` adds the batch surrogate (``BatchLearnedProposer``). The clock covers
-    instance construction, every round and the checks.
+    and after each round every active instance's hypervolume is checked. ``learned`` adds the
+    batch surrogate (``BatchLearnedProposer``). The clock covers instance construction (on
+    host threads, with the samplers' memory ``layout``; None: ``round_layout(params, n)``),
+    every round and the checks (the active instances' hypervolumes with one
+    ``moq_hypervolume_many`` call per round, two synchronisations).
     Returns dict(seconds, rounds, samples, reached, rounds_per_instance).
     """
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     B = len(srcs)
-    insts = create_instances(srcs)
+    insts = create_instances(srcs, layout=[round_layout(params, s.n) for s in srcs] if layout is None else layout)
     archs = [Archive(s.n, s.K, capacity=capacity, max_batch=R) for s in srcs]
     K = insts[0].K
     active = list(range(B))
@@ -545,8 +586,9 @@ def time_to_target_batch(srcs, targets, params, R: int, seed: int = 0, max_round
         samples += R * len(active)
         rounds += 1
         still = []
-        for b in active:
-            if archs[b].hypervolume(insts[b].ref) >= targets[b]:
+        hvs = Archive.hypervolume_many([archs[b] for b in active], [insts[b].ref for b in active])
+        for b, hv in zip(active, hvs):
+            if hv >= targets[b]:
                 done_at[b] = rounds
             else:
                 still.append(b)

@@ -51,3 +51,17 @@ def test_last_status_and_message_follow_a_rejected_call():
     assert b"n" in lib.moq_last_error_message()
     lib.moq_default_params(None)  # a call that cannot fail leaves the status as it was
     assert lib.moq_last_status() == -1
+
+
+def test_layout_argument_is_checked_before_device_work():
+    # moq_create_instance_layout rejects a layout below MOQ_LAYOUT_PLAIN before any CUDA call
+    from paper_2604_26477_b300 import build
+    lib = ctypes.CDLL(build.build())
+    lib.moq_last_error_message.restype = ctypes.c_char_p
+    out = ctypes.c_void_p(1)
+    ei = (ctypes.c_int32 * 1)(0)
+    ej = (ctypes.c_int32 * 1)(1)
+    w = (ctypes.c_int32 * 2)(1, 1)
+    rc = lib.moq_create_instance_layout(2, 2, 1, ei, ej, w, -2, None, ctypes.byref(out))
+    assert rc == -1 and out.value is None
+    assert b"layout" in lib.moq_last_error_message()

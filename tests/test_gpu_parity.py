@@ -364,6 +364,43 @@ def test_hv4_large_fronts_streamed(M, oracle, span, F, noise):
     assert _hv_points(M, pts, ref) == want  # dominated points add nothing
 
 
+@pytest.mark.parametrize("K,count", [(2, 131), (3, 9), (4, 6)])
+def test_hv_many_equals_one_call_per_archive(M, P, oracle, K, count):
+    # moq_hypervolume_many over archives of one K (more than one 128-archive chunk for K = 2,
+    # empty archives and fronts of different sizes included) gives each archive's exact
+    # hypervolume: the oracle's on the oracle's filter of its candidates, and moq_hypervolume's
+    rng = np.random.default_rng(K * 1000 + count)
+    n = 70
+    archs, refs, want = [], [], []
+    for i in range(count):
+        arch = P.Archive(n, K, capacity=1 << 14, max_batch=4096)
+        m = 0 if i % 5 == 3 else int(rng.integers(1, 3000 if K < 4 else 800))
+        span = int(rng.integers(20, 10 ** 6))
+        c = rng.integers(0, span, size=(max(m, 1), K)).astype(np.int64)
+        if K >= 3 and m:
+            c[: m // 2, -1] = 2 * span - c[: m // 2, :-1].sum(axis=1)
+        ref = rng.integers(-span // 4, span // 8, size=K).astype(np.int64)
+        if m:
+            arch.merge(_dev(c[:m], torch.int64), _bits_dev(wl.random_sign_bits(m, n, i)), m, 0)
+            front = c[:m][oracle.pareto_filter(c[:m])]
+            want.append(oracle.hypervolume(front, ref))
+        else:
+            want.append(0)
+        archs.append(arch)
+        refs.append(ref)
+    got = P.Archive.hypervolume_many(archs, refs)
+    assert got == want
+    assert got == [a.hypervolume(r) for a, r in zip(archs, refs)]
+    assert P.Archive.hypervolume_many(archs, refs) == want  # a second call on the same archives
+    other = P.Archive(n, 5, capacity=64, max_batch=64)
+    with pytest.raises(M.MoqError) as e:
+        P.Archive.hypervolume_many([archs[0], other], [np.zeros(5, np.int64), np.zeros(5, np.int64)])
+    assert e.value.code == M.MOQ_ERR_ARG
+    other.close()
+    for a in archs:
+        a.close()
+
+
 def test_hv_edge_cases(M, oracle):
     ref = np.zeros(3, np.int64)
     assert _hv_points(M, np.zeros((0, 3), np.int64), ref) == 0
@@ -942,3 +979,36 @@ def test_pareto_candidates_at_an_8_byte_offset(M, P, oracle, Mtot):
         assert np.array_equal(a, b)
     keep = oracle.pareto_filter(cuts)  # pool indices (ascending) of the distinct non-dominated vectors
     assert np.array_equal(fronts[0][0], cuts[keep]) and np.array_equal(fronts[0][2], keep)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_layout_argument_reproduces_the_environment_choice(M, P, monkeypatch, precision):
+    # moq_create_instance_layout with MOQ_LAYOUT_PLAIN, MOQ_LAYOUT_DEFAULT and an effort m > 0
+    # builds the instances that moq_create_instance builds under MOQ_SB_LAYOUT=0, the default
+    # environment and MOQ_SB_LAYOUT_EFFORT=m: the same samples and end states, bit for bit; and
+    # the argument wins over the environment
+    src = wl.random_regular(300, 11, K=3)
+    R, T = 203, 90
+    lam = _dev(wl.dirichlet_lambdas(R, src.K, 4), torch.float32)
+
+    def sample(inst):
+        bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+        xo = torch.zeros((R, src.n), device="cuda")
+        p = M.moq_default_params(steps=T, dt=0.5, alpha=0.1, x_out=xo, precision=precision)
+        M.moq_sample(inst.handle, lam, R, p, 5, 1, bits)
+        torch.cuda.synchronize()
+        out = (bits.cpu(), xo.cpu())
+        inst.close()
+        return out
+
+    cases = [("0", "0", M.MOQ_LAYOUT_PLAIN), ("1", "0", M.MOQ_LAYOUT_DEFAULT), ("1", "300", 300)]
+    for env_layout, env_effort, arg in cases:
+        monkeypatch.setenv("MOQ_SB_LAYOUT", env_layout)
+        monkeypatch.setenv("MOQ_SB_LAYOUT_EFFORT", env_effort)
+        by_env = sample(P.Instance(src))
+        monkeypatch.setenv("MOQ_SB_LAYOUT", "1" if env_layout == "0" else "0")  # the argument wins
+        by_arg = sample(P.Instance(src, layout=arg))
+        assert torch.equal(by_env[0], by_arg[0]) and torch.equal(by_env[1], by_arg[1])
+    with pytest.raises(M.MoqError):
+        P.Instance(src, layout=-2)
