@@ -397,6 +397,20 @@ def test_hv_many_equals_one_call_per_archive(M, P, oracle, K, count):
         P.Archive.hypervolume_many([archs[0], other], [np.zeros(5, np.int64), np.zeros(5, np.int64)])
     assert e.value.code == M.MOQ_ERR_ARG
     other.close()
+    # an archive whose merge overflowed: the call reports it (as moq_archive_size does) and
+    # clears the latch, so the next call gives every hypervolume again
+    small = P.Archive(n, K, capacity=8, max_batch=64)
+    anti = np.zeros((9, K), np.int64)
+    anti[:, 0] = np.arange(9)
+    anti[:, 1] = 20 - np.arange(9)
+    with pytest.raises(M.MoqError):  # the merge itself reports the overflow
+        small.merge(_dev(anti, torch.int64), _bits_dev(wl.random_sign_bits(9, n, 5)), 9, 0, want_size=True)
+    small.merge(_dev(anti, torch.int64), _bits_dev(wl.random_sign_bits(9, n, 5)), 9, 0)  # latched, not read
+    with pytest.raises(M.MoqError) as e:
+        P.Archive.hypervolume_many([archs[1], small], [refs[1], np.zeros(K, np.int64)])
+    assert e.value.code == M.MOQ_ERR_CAPACITY
+    assert P.Archive.hypervolume_many([archs[1], small], [refs[1], np.zeros(K, np.int64)]) == [want[1], 0]
+    small.close()
     for a in archs:
         a.close()
 
