@@ -573,19 +573,20 @@ __global__ void __launch_bounds__(kScanBlock) k_scatter(const ScatterArgs s)
     const int64_t b = blockIdx.x;
     const int64_t total = s.blockoff[s.nb];
     const bool overflow = total > s.cap;
-    if (b < s.nbA && b * kScanBlock >= F) return;  // empty archive slots
     if (overflow) {
-        // keep the archive as it was: copy members to the same slots
-        if (b >= s.nbA) return;
+        // latch the overflow first (block 0 also covers an empty archive), then keep the
+        // archive as it was: copy members to the same slots
+        if (b == 0 && threadIdx.x == 0) atomicOr(s.status, kStatusCapacity);
+        if (b >= s.nbA || b * kScanBlock >= F) return;
         const int64_t q = b * kScanBlock + threadIdx.x;
         if (q < F) {
             for (int k = 0; k < s.K; ++k) s.new_cuts[q * s.K + k] = s.old_cuts[q * s.K + k];
             for (int w = 0; w < s.W; ++w) s.new_bits[q * s.W + w] = s.old_bits[q * s.W + w];
             s.new_index[q] = s.old_index[q];
         }
-        if (b == 0 && threadIdx.x == 0) atomicOr(s.status, kStatusCapacity);
         return;
     }
+    if (b < s.nbA && b * kScanBlock >= F) return;  // empty archive slots
     const int32_t v = flag_at(b, threadIdx.x, s.nbA, F, s.M, s.flag_arch, s.flag_cand);
     int32_t tot;
     const int32_t local = block_excl_scan(v, warp_sums, &tot);

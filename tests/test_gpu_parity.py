@@ -289,6 +289,13 @@ def test_pareto_edge_cases(M, P, oracle):
         arch.merge(_dev(anti, torch.int64), _bits_dev(wl.random_sign_bits(9, n, 2)), 9, 300, want_size=True)
     assert e.value.code == M.MOQ_ERR_CAPACITY
     assert arch.copy_out()[2].tolist() == [100]
+    # the same into an empty archive: reported too, and the archive stays empty
+    empty_arch = P.Archive(n, K, capacity=8, max_batch=64)
+    with pytest.raises(M.MoqError) as e:
+        empty_arch.merge(_dev(anti, torch.int64), _bits_dev(wl.random_sign_bits(9, n, 2)), 9, 300, want_size=True)
+    assert e.value.code == M.MOQ_ERR_CAPACITY
+    assert empty_arch.size() == 0
+    empty_arch.close()
     with pytest.raises(M.MoqError):
         arch.merge(_dev(np.zeros((65, K), np.int64), torch.int64), _bits_dev(wl.random_sign_bits(65, n, 3)), 65, 0)
 
