@@ -80,12 +80,13 @@ _build_streams = threading.local()
 
 
 def create_instances(srcs, stream=None, threads=None, layout_effort=None, layout=None):
-    """``Instance`` of every source, built on host threads: the build's host part (the
-    samplers' shared-memory layout) runs in parallel, and the device part of each build is
-    ordered on a stream of its own thread -- on one shared stream the builds' pageable
-    copies, kernels and synchronisations queue behind one another. Every build has finished
-    on the device when this returns, so the instances are ready for any stream, ``stream``
-    included. ``layout``: as ``moq_create_instance_layout`` (None: from the environment),
+    """``Instance`` of every source, built on host threads where some build plans its layout:
+    the build's host part (the samplers' shared-memory layout) runs in parallel, and the
+    device part of each build is ordered on a stream of its own thread -- on one shared
+    stream the builds' pageable copies, kernels and synchronisations queue behind one another.
+    Builds with the plain layout alone run one after another on the calling thread. Every
+    build has finished on the device when this returns, so the instances are ready for any
+    stream, ``stream`` included. ``layout``: as ``moq_create_instance_layout`` (None: from the environment),
     one for all or a list with one per source; ``layout_effort`` = m > 0 is the same as
     ``layout=m`` (the longer layout search, m slot exchanges per spin, for regular graphs)."""
     import concurrent.futures
@@ -96,7 +97,9 @@ def create_instances(srcs, stream=None, threads=None, layout_effort=None, layout
     layouts = list(layout) if isinstance(layout, (list, tuple)) else [layout] * len(srcs)
     if len(layouts) != len(srcs):
         raise ValueError("one layout per source")
-    if len(srcs) < 2:
+    if len(srcs) < 2 or all(lay == M.MOQ_LAYOUT_PLAIN for lay in layouts):
+        # no host planning to overlap: one thread, where the builds' CUDA calls do not
+        # contend for the driver (16 plain builds: 12 ms on 16 threads against 4 ms here)
         return [Instance(s, stream, lay) for s, lay in zip(srcs, layouts)]
     dev = torch.cuda.current_device()
 
@@ -376,21 +379,23 @@ class LearnedProposer:
 
 
 def round_layout(params, n=None):
-    """The samplers' memory layout the round drivers build with, by the sampler's precision
-    and the graph size.
+    """The samplers' memory layout the round drivers build with by default, by the sampler's
+    precision and the graph size.
 
     The bank-conflict planner is host work inside every time-to-target clock (0.2 ms at
-    n = 42, 3-12 ms at n = 1024 depending on the host). The float16 samplers gather 4-byte
-    half2 words and gain little from it, the FP32 pair forms gather 8-byte words and gain
-    4-16 %. Measured on 16 random 3-regular instances (n = 118..1020, 1024 replicas per
-    round, 8 seeds): the 16 builds took 24-33 ms with the planner against 9-10 ms without;
-    float16 NI-dSB (T = 3000) batched reached 99 % of the plain sampler's hypervolume in
-    66 ms without the planner against 89 ms with it (99.9 %: 287 against 300 ms), while plain
-    FP32 dSB one instance at a time took 80 against 83 ms at 99 % but 885 against 714 ms at
-    99.9 % (60 rounds). On small graphs the planner gains about 1 % (n = 42: 44 against 39
-    8-byte passes per gather step) for 0.2 ms or more of a sub-millisecond clock. So float16
-    rounds and graphs of up to 128 spins build with the plain layout, larger FP32 ones with
-    the planner.
+    n = 42, 3-12 ms at n = 1024 depending on the host; 16 builds of n = 68..932 took 24-33 ms
+    on 16 threads against 2.4-3.9 ms for plain builds on one thread). The float16 samplers
+    gather 4-byte half2 words and gain little from it, the FP32 pair forms gather 8-byte
+    words and gain 4-16 % per launch. Measured on 16 random 3-regular instances (1024
+    replicas per round, 8 seeds): float16 NI-dSB (T = 3000) batched reached 99 % of the plain
+    sampler's hypervolume in 60 ms with the plain layout against 82 ms with the planner
+    (99.9 %: 277 against 300 ms); plain FP32 dSB one instance at a time took 71 against 83 ms
+    at 99 % (6 rounds) but 876 against 716 ms at 99.9 % (60 rounds), so for FP32 the planner
+    pays back only over long jobs, and callers that know theirs is short pass
+    ``layout=M.MOQ_LAYOUT_PLAIN``. On small graphs the planner gains about 1 % (n = 42: 44
+    against 39 8-byte passes per gather step) for 0.2 ms or more of a sub-millisecond clock.
+    So float16 rounds and graphs of up to 128 spins build with the plain layout, larger FP32
+    ones with the planner.
     """
     fp16 = getattr(params, "precision", M.MOQ_PREC_FP32) == M.MOQ_PREC_FP16
     return M.MOQ_LAYOUT_PLAIN if fp16 or (n is not None and n <= 128) else M.MOQ_LAYOUT_DEFAULT
