@@ -581,6 +581,7 @@ struct moq_mlp {
     float* cand_pred = nullptr;
     float* cand_score = nullptr;
     float* consts = nullptr;
+    void* slab = nullptr;  // the one device allocation the arrays above live in
 };
 
 namespace moq {
@@ -589,10 +590,7 @@ namespace {
 void free_mlp(moq_mlp* m)
 {
     if (!m) return;
-    for (void* p : {(void*)m->master, (void*)m->w16, (void*)m->grad, (void*)m->adam_m, (void*)m->adam_v, (void*)m->partial,
-                    (void*)m->loss_part, (void*)m->cand, (void*)m->cand_in, (void*)m->cand_pred, (void*)m->cand_score, (void*)m->consts,
-                    (void*)m->status})
-        cudaFree(p);
+    slab_free(m->slab);
     delete m;
 }
 
@@ -641,32 +639,39 @@ int moq_mlp_create(int32_t d_in, int32_t d_out, int32_t max_batch, int32_t max_c
     m->max_cand = max_candidates;
     m->max_blocks = (int)ceil_div(max_batch, kRows);
     m->P = mlp_shape(d_in, d_out).P;
-    cudaError_t e = cudaSuccess;
-    auto al = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
-    al((void**)&m->master, sizeof(float) * m->P);
-    al((void**)&m->w16, sizeof(__nv_bfloat16) * m->P);
-    al((void**)&m->grad, sizeof(float) * m->P);
-    al((void**)&m->adam_m, sizeof(float) * m->P);
-    al((void**)&m->adam_v, sizeof(float) * m->P);
-    al((void**)&m->partial, sizeof(float) * m->P * m->max_blocks);
-    al((void**)&m->loss_part, sizeof(float) * (m->max_blocks + 1));
-    al((void**)&m->cand, sizeof(float) * max_candidates * d_out);
-    al((void**)&m->cand_in, sizeof(float) * max_candidates * d_in);
-    al((void**)&m->cand_pred, sizeof(float) * max_candidates * d_out);
-    al((void**)&m->cand_score, sizeof(float) * max_candidates);
-    al((void**)&m->consts, sizeof(float) * 64);
-    al((void**)&m->status, sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMemset(m->status, 0, sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMemset(m->adam_m, 0, sizeof(float) * m->P);
-    if (e == cudaSuccess) e = cudaMemset(m->adam_v, 0, sizeof(float) * m->P);
-    if (e == cudaSuccess) e = cudaMemset(m->grad, 0, sizeof(float) * m->P);
+    // one slab from the library's memory pool for all arrays (ordered on the legacy stream;
+    // with a cudaMalloc per array a handle cost about a millisecond to create and as much to
+    // free, inside every learned time-to-target clock)
+    std::vector<std::pair<void**, size_t>> parts = {
+        {(void**)&m->master, sizeof(float) * m->P}, {(void**)&m->w16, sizeof(__nv_bfloat16) * m->P},
+        {(void**)&m->grad, sizeof(float) * m->P}, {(void**)&m->adam_m, sizeof(float) * m->P},
+        {(void**)&m->adam_v, sizeof(float) * m->P}, {(void**)&m->partial, sizeof(float) * m->P * m->max_blocks},
+        {(void**)&m->loss_part, sizeof(float) * (m->max_blocks + 1)}, {(void**)&m->cand, sizeof(float) * max_candidates * d_out},
+        {(void**)&m->cand_in, sizeof(float) * max_candidates * d_in}, {(void**)&m->cand_pred, sizeof(float) * max_candidates * d_out},
+        {(void**)&m->cand_score, sizeof(float) * max_candidates}, {(void**)&m->consts, sizeof(float) * 64},
+        {(void**)&m->status, sizeof(int32_t)}};
+    size_t total = 0;
+    for (auto& pr : parts) total += slab_align(pr.second);
+    const cudaStream_t st0 = cudaStreamLegacy;
+    cudaError_t e = slab_alloc(&m->slab, total, st0);
     if (e == cudaSuccess) {
-        k_mlp_init<<<64, 256>>>(m->master, m->w16, d_in, d_out, (uint32_t)seed, (uint32_t)(seed >> 32));
+        size_t off = 0;
+        for (auto& pr : parts) {
+            *pr.first = static_cast<char*>(m->slab) + off;
+            off += slab_align(pr.second);
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->status, 0, sizeof(int32_t), st0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->adam_m, 0, sizeof(float) * m->P, st0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->adam_v, 0, sizeof(float) * m->P, st0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->grad, 0, sizeof(float) * m->P, st0);
+    if (e == cudaSuccess) {
+        k_mlp_init<<<64, 256, 0, st0>>>(m->master, m->w16, d_in, d_out, (uint32_t)seed, (uint32_t)(seed >> 32));
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_smem_bytes());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_smem_bytes());
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st0);  // ready for any stream
     if (e != cudaSuccess) {
         free_mlp(m);
         return cuda_fail(e, "moq_mlp_create");
