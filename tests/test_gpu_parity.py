@@ -300,6 +300,48 @@ def test_pareto_edge_cases(M, P, oracle):
         arch.merge(_dev(np.zeros((65, K), np.int64), torch.int64), _bits_dev(wl.random_sign_bits(65, n, 3)), 65, 0)
 
 
+@pytest.mark.parametrize("K", [2, 3, 4])
+def test_capacity_overflow_on_every_merge_path(M, P, K):
+    # a merge whose front would exceed the archive's capacity is reported and leaves the
+    # archive as it was: on the large-batch path (dedup, survivors; 9000 candidates), into an
+    # empty and into a non-empty archive, and through moq_archive_merge
+    n = 50
+    rng = np.random.default_rng(K)
+    anti = np.zeros((9000, K), np.int64)
+    anti[:, 0] = np.arange(9000)
+    anti[:, 1] = 20000 - np.arange(9000)
+    anti = anti[rng.permutation(9000)]
+    bits = _bits_dev(wl.random_sign_bits(9000, n, 3))
+    arch = P.Archive(n, K, capacity=100, max_batch=9000)
+    with pytest.raises(M.MoqError) as e:
+        arch.merge(_dev(anti, torch.int64), bits, 9000, 0, want_size=True)
+    assert e.value.code == M.MOQ_ERR_CAPACITY
+    assert arch.size() == 0
+    few = np.zeros((50, K), np.int64)
+    few[:, 0] = 30000 + np.arange(50)
+    few[:, 1] = 30000 - np.arange(50)
+    assert arch.merge(_dev(few, torch.int64), bits[:50], 50, 10 ** 6, want_size=True) == 50
+    before = arch.copy_out()
+    with pytest.raises(M.MoqError) as e:  # 9000 more, none dominated by the 50: overflow
+        big = anti.copy()
+        big[:, 0] += 40000
+        arch.merge(_dev(big, torch.int64), bits, 9000, 0, want_size=True)
+    assert e.value.code == M.MOQ_ERR_CAPACITY
+    after = arch.copy_out()
+    assert all(np.array_equal(x, y) for x, y in zip(before, after))
+    # archive into archive: 9 mutually non-dominated members into an empty archive of 8 slots
+    src = P.Archive(n, K, capacity=64, max_batch=64)
+    assert src.merge(_dev(anti[:9], torch.int64), bits[:9], 9, 0, want_size=True) == 9
+    dst = P.Archive(n, K, capacity=8, max_batch=64)
+    dst.merge_from(src)
+    with pytest.raises(M.MoqError) as e:
+        dst.size()
+    assert e.value.code == M.MOQ_ERR_CAPACITY
+    assert dst.size() == 0  # the latch is cleared once reported
+    for a in (arch, src, dst):
+        a.close()
+
+
 # ----------------------------------------------------------------------------- a8
 def _hv_points(M, pts, ref):
     F, K = pts.shape
