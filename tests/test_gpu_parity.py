@@ -125,6 +125,41 @@ def test_instance_rejects_bad_input(M):
     assert e.value.code == M.MOQ_ERR_ARG
 
 
+@pytest.mark.parametrize("n,edges", [(5, []), (2, [(0, 1)]), (7, [(0, 3), (2, 6)])])
+def test_degenerate_graphs_through_the_whole_path(M, P, oracle, n, edges):
+    # no edges, one edge between the only two spins, isolated spins beside two edges: the build,
+    # both precisions and variants of the sampler, the cuts, the merge and the hypervolume all run
+    # and give the oracle's integer results on the sampled configurations
+    K, R = 3, 37
+    rng = np.random.default_rng(n)
+    ei = np.array([e[0] for e in edges], np.int32)
+    ej = np.array([e[1] for e in edges], np.int32)
+    w = rng.choice(np.r_[np.arange(-10, 0), np.arange(1, 11)], size=(K, len(edges))).astype(np.int32)
+    src = wl.Instance(n, ei, ej, w, name=f"degenerate_n{n}_E{len(edges)}")
+    inst = P.Instance(src)
+    assert inst.info["E"] == len(edges) and inst.info["weight_sum"] == [int(x) for x in w.astype(np.int64).sum(axis=1)]
+    assert list(inst.ref) == list(oracle.reference_point(src))
+    lam = _dev(wl.dirichlet_lambdas(R, K, 3), torch.float32)
+    for precision in ("fp32", "fp16"):
+        for variant in ("dsb", "bsb"):
+            bits = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+            p = M.moq_default_params(variant=variant, steps=50, dt=0.5, alpha=0.1, precision=precision)
+            M.moq_sample(inst.handle, lam, R, p, 9, 0, bits)
+            cuts = torch.zeros((R, K), dtype=torch.int64, device="cuda")
+            M.moq_evaluate_cuts(inst.handle, bits, R, cuts)
+            hb = bits.cpu().numpy().view(np.uint64)
+            want = oracle.cuts(src, hb)
+            assert np.array_equal(cuts.cpu().numpy(), want)
+            arch = P.Archive(n, K, capacity=64, max_batch=R)
+            arch.merge(cuts, bits, R, 0)
+            front = want[oracle.pareto_filter(want)]
+            gc, _, _ = arch.copy_out()
+            assert sorted(map(tuple, gc.tolist())) == sorted(map(tuple, front.tolist()))
+            assert arch.hypervolume(inst.ref) == oracle.hypervolume(front, inst.ref)
+            arch.close()
+    inst.close()
+
+
 # ----------------------------------------------------------------------------- a6
 @pytest.mark.parametrize("name", list(INSTANCES))
 def test_cuts_bit_exact(M, P, oracle, name):
