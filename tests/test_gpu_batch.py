@@ -179,3 +179,36 @@ def test_parallel_instance_builds_match_sequential_ones(M, P):
             M.moq_sample(inst.handle, lam, 70, p, 3, 1, bits)
             out.append(bits.cpu())
         assert torch.equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("tile", [(1024, 1), (256, 4), (0, 0)])
+def test_batch_with_degenerate_instances(M, P, oracle, tile):
+    # a batch holding a graph without edges, the two-spin graph and isolated spins beside a
+    # regular graph: every instance's samples equal its single-instance call, cuts the oracle's
+    e0 = np.zeros(0, np.int32)
+    srcs = [wl.Instance(5, e0, e0, np.zeros((3, 0), np.int32), name="edgeless5"),
+            wl.Instance(2, np.array([0], np.int32), np.array([1], np.int32), np.array([[3], [-2], [7]], np.int32),
+                        name="pair2"),
+            wl.Instance(7, np.array([0, 2], np.int32), np.array([3, 6], np.int32),
+                        np.array([[1, -4], [2, 2], [-9, 5]], np.int32), name="isolated7"),
+            wl.random_regular(200, 12, K=3)]
+    insts = [P.Instance(s) for s in srcs]
+    reps = [19, 64, 7, 45]
+    b = P.Batch(insts, reps)
+    b.lam.copy_(torch.from_numpy(wl.dirichlet_lambdas(b.total_R, 3, 23)))
+    b.set_tiles(*tile)
+    params = M.moq_default_params(variant="dsb", steps=97, dt=0.5, alpha=0.15)
+    b.sample(params, seed=4, round_=1)
+    b.evaluate_cuts()
+    for k, (src, inst) in enumerate(zip(srcs, insts)):
+        R = int(b.replicas[k])
+        lam = b.lam[int(b.rep_off[k]):int(b.rep_off[k + 1])].contiguous()
+        single = torch.zeros((R, inst.W), dtype=torch.int64, device="cuda")
+        p1 = M.moq_default_params(variant="dsb", steps=97, dt=0.5, alpha=0.15, replica_offset=int(b.rep_off[k]))
+        M.moq_sample(inst.handle, lam, R, p1, 4, 1, single)
+        assert torch.equal(b.bits_of(k), single), (src.name, tile)
+        bits = b.bits_of(k).cpu().numpy().view(np.uint64)
+        assert np.array_equal(b.cuts_of(k).cpu().numpy(), oracle.cuts(src, bits)), src.name
+    b.close()
+    for h in insts:
+        h.close()
