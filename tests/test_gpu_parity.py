@@ -499,6 +499,22 @@ def test_hv_many_equals_one_call_per_archive(M, P, oracle, K, count):
         a.close()
 
 
+@pytest.mark.parametrize("F", [6143, 6144, 6145])
+@pytest.mark.parametrize("wide", [False, True])
+def test_hv4_at_the_shared_memory_limit(M, oracle, F, wide):
+    # K = 4 point sets at the largest size the shared-memory slab kernels take (6144) and one
+    # point either side, mostly on a front with ties; with one coordinate lifted 2^40 above the
+    # reference the 128-bit walk runs instead of the 32-bit one
+    rng = np.random.default_rng(F + 7 * wide)
+    pts = rng.integers(0, 40, size=(F, 4)).astype(np.int64)
+    pts[:, -1] = 120 - pts[:, :-1].sum(axis=1) + rng.integers(0, 2, F)
+    if wide:
+        pts[5, 0] = 1 << 40
+    ref = np.array([-1, -2, 0, -3], np.int64)
+    want = oracle.hypervolume(pts[oracle.pareto_filter(pts)], ref)
+    assert _hv_points(M, pts, ref) == want
+
+
 def test_hv_edge_cases(M, oracle):
     ref = np.zeros(3, np.int64)
     assert _hv_points(M, np.zeros((0, 3), np.int64), ref) == 0
