@@ -75,3 +75,8 @@ def test_noalloc_rejects_sizes_beyond_its_fixed_scratch(M):
     with pytest.raises(M.MoqError) as e:
         M.moq_hypervolume_points_noalloc(pts, limit + 1, 3, np.zeros(3, np.int64))
     assert e.value.code == M.MOQ_ERR_CAPACITY and "limit" in str(e.value)
+    # exactly at the limit, four objectives (the streamed slab kernels): the whole array in use
+    full = _points(6, limit, 4, 90)
+    ref = np.zeros(4, np.int64)
+    dev = torch.from_numpy(full).cuda()
+    assert M.moq_hypervolume_points_noalloc(dev, limit, 4, ref) == _with_workspace(M, dev, limit, 4, ref)
