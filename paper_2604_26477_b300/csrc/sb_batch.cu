@@ -285,6 +285,7 @@ struct moq_batch {
     const int32_t** d_ej = nullptr;
     const int32_t** d_w = nullptr;
     int64_t* d_E = nullptr;
+    void* slab = nullptr;  // the one device allocation the arrays above live in
 };
 
 namespace moq {
@@ -293,13 +294,7 @@ namespace {
 void free_batch(moq_batch* b)
 {
     if (!b) return;
-    cudaFree(b->d_insts);
-    cudaFree(b->d_items);
-    cudaFree(b->d_queue);
-    cudaFree(b->d_ei);
-    cudaFree(b->d_ej);
-    cudaFree(b->d_w);
-    cudaFree(b->d_E);
+    slab_free(b->slab);
     for (cudaStream_t s : b->lanes) cudaStreamDestroy(s);
     for (cudaEvent_t e : b->lane_done) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
@@ -432,18 +427,30 @@ int moq_batch_create(const moq_instance* const* insts, int32_t count, const int3
         ej[i] = insts[i]->ej;
         w[i] = insts[i]->w;
     }
-    cudaError_t e = cudaMalloc((void**)&b->d_insts, sizeof(BatchInst) * count);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_items, sizeof(BatchItem) * items_cap);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_queue, sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_ei, sizeof(void*) * count);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_ej, sizeof(void*) * count);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_w, sizeof(void*) * count);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_E, sizeof(int64_t) * count);
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_insts, b->h_insts.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_ei, ei.data(), sizeof(void*) * count, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_ej, ej.data(), sizeof(void*) * count, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_w, w.data(), sizeof(void*) * count, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_E, b->h_E.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice);
+    // one slab from the library's memory pool for the handle's device arrays, filled on the
+    // legacy stream and synchronised once
+    const std::pair<void**, size_t> parts[] = {
+        {(void**)&b->d_insts, sizeof(BatchInst) * count}, {(void**)&b->d_items, sizeof(BatchItem) * items_cap},
+        {(void**)&b->d_queue, sizeof(int32_t)}, {(void**)&b->d_ei, sizeof(void*) * count},
+        {(void**)&b->d_ej, sizeof(void*) * count}, {(void**)&b->d_w, sizeof(void*) * count},
+        {(void**)&b->d_E, sizeof(int64_t) * count}};
+    size_t total = 0;
+    for (const auto& pr : parts) total += slab_align(pr.second);
+    const cudaStream_t st0 = cudaStreamLegacy;
+    cudaError_t e = slab_alloc(&b->slab, total, st0);
+    if (e == cudaSuccess) {
+        size_t off = 0;
+        for (const auto& pr : parts) {
+            *pr.first = static_cast<char*>(b->slab) + off;
+            off += slab_align(pr.second);
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_insts, b->h_insts.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice, st0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_ei, ei.data(), sizeof(void*) * count, cudaMemcpyHostToDevice, st0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_ej, ej.data(), sizeof(void*) * count, cudaMemcpyHostToDevice, st0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_w, w.data(), sizeof(void*) * count, cudaMemcpyHostToDevice, st0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_E, b->h_E.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice, st0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st0);
     if (e != cudaSuccess) {
         free_batch(b);
         return cuda_fail(e, "moq_batch_create");
