@@ -573,11 +573,15 @@ __global__ void __launch_bounds__(kScanBlock) k_scatter(const ScatterArgs s)
     const int64_t b = blockIdx.x;
     const int64_t total = s.blockoff[s.nb];
     const bool overflow = total > s.cap;
+    if (b < s.nbA && b * kScanBlock >= F) {  // empty archive slots
+        // block 0 latches an overflow here too, when the archive is empty
+        if (b == 0 && threadIdx.x == 0 && overflow) atomicOr(s.status, kStatusCapacity);
+        return;
+    }
     if (overflow) {
-        // latch the overflow first (block 0 also covers an empty archive), then keep the
-        // archive as it was: copy members to the same slots
+        // keep the archive as it was: copy members to the same slots
         if (b == 0 && threadIdx.x == 0) atomicOr(s.status, kStatusCapacity);
-        if (b >= s.nbA || b * kScanBlock >= F) return;
+        if (b >= s.nbA) return;
         const int64_t q = b * kScanBlock + threadIdx.x;
         if (q < F) {
             for (int k = 0; k < s.K; ++k) s.new_cuts[q * s.K + k] = s.old_cuts[q * s.K + k];
@@ -586,7 +590,6 @@ __global__ void __launch_bounds__(kScanBlock) k_scatter(const ScatterArgs s)
         }
         return;
     }
-    if (b < s.nbA && b * kScanBlock >= F) return;  // empty archive slots
     const int32_t v = flag_at(b, threadIdx.x, s.nbA, F, s.M, s.flag_arch, s.flag_cand);
     int32_t tot;
     const int32_t local = block_excl_scan(v, warp_sums, &tot);
