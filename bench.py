@@ -328,7 +328,9 @@ def gpu_arm(args, rank, world):
     # work takes the SMs only in the sampler's wave tails, and the host waits for its result:
     # with three, some runs showed 0.07-0.6 ms gaps between samplings, with four one run in
     # four 1.75 ms per step, with six 1.614-1.621 ms in all runs; with six and two filter lanes
-    # 1.602-1.612 ms.)
+    # 1.602-1.612 ms. Measured in one call on the current kernels, three runs each: this order
+    # 1.566-1.573 ms; the filter lanes at the higher priority 1.572-1.629 ms, their chains
+    # preempting the sampler's blocks; each chain gated on its own sampling only 1.582-1.596 ms.)
     depth = max(2, args.pipeline_depth)
     bufs = [buf] + [P.RoundBuffers(R, n, K) for _ in range(depth - 1)]
     s_a = torch.cuda.Stream(device=dev, priority=-1)
