@@ -600,6 +600,7 @@ int moq_evaluate_cuts_batch(const moq_batch* b, const uint64_t* bits_all, int64_
     if (!b || !bits_all || !cuts_all) return fail(MOQ_ERR_ARG, "moq_evaluate_cuts_batch: NULL argument");
     int maxR = 0;
     for (const BatchInst& in : b->h_insts) maxR = std::max(maxR, in.R);
+    if (maxR == 0) return MOQ_OK;  // no instance has an active replica: nothing to evaluate
     const dim3 grid((unsigned)ceil_div(maxR, 256), (unsigned)b->count);
     k_cuts_batch<<<grid, 256, 0, as_stream(stream)>>>(b->d_insts, b->d_ei, b->d_ej, b->d_w, b->d_E, bits_all, cuts_all, b->K);
     MOQ_LAUNCH_CHECK("moq_evaluate_cuts_batch launch");

@@ -212,3 +212,51 @@ def test_batch_with_degenerate_instances(M, P, oracle, tile):
     b.close()
     for h in insts:
         h.close()
+
+
+@pytest.mark.parametrize("tile", [(512, 2), (0, 0)])
+def test_zero_sized_calls(M, P, tile):
+    # nothing to do is not an error: no replicas, no samples, no weight vectors, a batch whose
+    # instances all have zero active replicas; the outputs around them stay untouched
+    src = wl.random_regular(100, 3, K=3)
+    inst = P.Instance(src)
+    lam = torch.zeros((1, 3), dtype=torch.float32, device="cuda")
+    bits = torch.full((1, inst.W), 7, dtype=torch.int64, device="cuda")
+    for precision in ("fp32", "fp16"):
+        M.moq_sample(inst.handle, lam, 0, M.moq_default_params(steps=10, precision=precision), 1, 0, bits)
+    cuts = torch.full((1, 3), -5, dtype=torch.int64, device="cuda")
+    M.moq_evaluate_cuts(inst.handle, bits, 0, cuts)
+    M.moq_lambda_dirichlet(3, 0, 1, 0, lam)
+    arch = P.Archive(src.n, 3, capacity=16, max_batch=16)
+    assert arch.merge(cuts, bits, 0, 0, want_size=True) == 0
+    torch.cuda.synchronize()
+    assert int(bits.min()) == 7 and int(bits.max()) == 7 and int(cuts.min()) == -5 and int(cuts.max()) == -5
+    insts = [inst, P.Instance(wl.heavy_hex_like(1003, K=3))]
+    b = P.Batch(insts, [8, 8])
+    b.set_tiles(*tile)
+    M.moq_batch_set_replicas(b.handle, np.zeros(2, np.int32))
+    b.bits.fill_(3)
+    b.cuts.fill_(-1)
+    b.sample(M.moq_default_params(steps=10), seed=1, round_=0)
+    b.evaluate_cuts()
+    torch.cuda.synchronize()
+    assert int(b.bits.min()) == 3 and int(b.bits.max()) == 3 and int(b.cuts.min()) == -1 and int(b.cuts.max()) == -1
+    b.close()
+    # the dense samplers and the dense cut evaluation with no replicas
+    d = M.moq_dense_create(inst.handle, 64)
+    d32 = M.moq_dense_fp32_create(inst.handle, 64)
+    try:
+        p = M.moq_default_params(steps=10)
+        M.moq_sample_dense(d, lam, 0, p, 1, 0, bits)
+        M.moq_sample_dense_fp8(d, lam, 0, p, 1, 0, bits)
+        M.moq_sample_dense_split(d, lam, 0, p, 1, 0, bits)
+        M.moq_sample_dense_fp32(d32, lam, 0, p, 1, 0, bits)
+        M.moq_dense_evaluate_cuts(d, bits, 0, cuts)
+        torch.cuda.synchronize()
+        assert int(bits.min()) == 7 and int(bits.max()) == 7 and int(cuts.min()) == -5 and int(cuts.max()) == -5
+    finally:
+        M.moq_dense_destroy(d)
+        M.moq_dense_fp32_destroy(d32)
+    arch.close()
+    for h in insts:
+        h.close()
